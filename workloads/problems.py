@@ -102,40 +102,42 @@ def random_problem(seed: int, N: int = 6, brauer: bool = False,
     boxes (random sigma per cell), a coil loop that avoids them."""
     rng = np.random.default_rng(seed)
     sig = np.zeros((N, N, N))
-    nbox = int(rng.integers(1, 3))
+    nbox = int(rng.integers(1, 3)) if N > 5 else 1
     for _ in range(nbox):
         lo = rng.integers(1, N - 2, size=3)
         ext = rng.integers(1, 3, size=3)
+        if N <= 5:
+            ext[2] = 1            # leave a free node plane for the coil
         hi = np.minimum(lo + ext, N - 1)
         sig[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = rng.uniform(1e5, 5e6, size=tuple(hi[::-1] - lo[::-1]))
     br = ((sig > 0) & brauer).astype(np.uint8)
-    # coil in the lowest interior node plane whose loop edges touch no conductor:
-    # try planes and shrinking squares, keep the first loop clear of conductors.
+    # first rectangular loop (largest side first, scanning node planes and
+    # positions) whose edges touch no conducting cell
     cond = sig > 0
-    for k in range(1, N):
-        for L in range(N - 2, 1, -1):
-            c0 = (N - L) // 2
-            i0, j0, i1, j1 = c0, c0, c0 + L, c0 + L
-            if i0 < 1 or i1 > N - 1:
+
+    def touches(k, i0, j0, i1, j1):
+        for kk in (k - 1, k):
+            if not 0 <= kk < N:
                 continue
-            # cells touching the loop: cells adjacent to node plane k along the square
-            ks = [kk for kk in (k - 1, k) if 0 <= kk < N]
-            touch = False
-            for kk in ks:
-                for (a, b, fixed, axis) in ((i0, i1, j0, 'x'), (i0, i1, j1, 'x'), (j0, j1, i0, 'y'), (j0, j1, i1, 'y')):
-                    for t in range(a, b):
-                        for f in (fixed - 1, fixed):
-                            if not (0 <= f < N):
-                                continue
-                            if axis == 'x' and cond[kk, f, t]:
-                                touch = True
-                            if axis == 'y' and cond[kk, t, f]:
-                                touch = True
-            if not touch:
-                return Problem(N=N, h=1.0e-3, sigma_cell=sig, brauer_cell=br,
-                               coil_k=k, coil_i0=i0, coil_j0=j0, coil_i1=i1,
-                               coil_j1=j1, amplitude=amplitude, n_steps=20,
-                               name=f"random-{seed}-{N}^3")
+            for t in range(i0, i1):
+                for f in (j0 - 1, j0, j1 - 1, j1):
+                    if 0 <= f < N and cond[kk, f, t]:
+                        return True
+            for t in range(j0, j1):
+                for f in (i0 - 1, i0, i1 - 1, i1):
+                    if 0 <= f < N and cond[kk, t, f]:
+                        return True
+        return False
+
+    for L in range(N - 2, 0, -1):
+        for k in range(1, N):
+            for i0 in range(1, N - L):
+                for j0 in range(1, N - L):
+                    if not touches(k, i0, j0, i0 + L, j0 + L):
+                        return Problem(N=N, h=1.0e-3, sigma_cell=sig, brauer_cell=br,
+                                       coil_k=k, coil_i0=i0, coil_j0=j0, coil_i1=i0 + L,
+                                       coil_j1=j0 + L, amplitude=amplitude, n_steps=20,
+                                       name=f"random-{seed}-{N}^3")
     raise ValueError("no coil placement clear of the conductors")
 
 
