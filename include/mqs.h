@@ -1,0 +1,242 @@
+/*
+ * mqs.h - C ABI of the GB300 (sm_103a) library for the semi-explicit
+ * eddy-current time stepper with multiple right-hand side start vectors.
+ *
+ * Method (Dutine, Clemens, Schoeps, "Multiple Right-Hand Side Techniques in
+ * Semi-Explicit Time Integration Methods for Transient Eddy Current
+ * Problems"):
+ *   Sec. II, eq. (DAE)   edge unknowns split into conducting a_c and
+ *                        nonconducting a_n;
+ *   Sec. II, eq. (SC)    generalised Schur complement
+ *                        K_S(a_c) = K_c(a_c) - K_cn K_n^+ K_cn^T;
+ *   Sec. II, eq. (ODE)   M_c da_c/dt + K_S a_c = -K_cn K_n^+ j;
+ *   Sec. II, eq. (acm)   explicit Euler update of a_c (source sign as in (ODE));
+ *   Sec. II, eq. (CFL)   dt <= 2 / lambda_max(M_c^-1 K_S), power method;
+ *   Sec. III, eq. (mrhs) K_n a_p = j_p solved by PCG every step;
+ *   Sec. III, eq. (SPE_x0) subspace projection extrapolation start vector;
+ *   Sec. III, eqs. (SVD),(relSV2),(keepInfo),(POD_x0) POD start vector.
+ *
+ * Discretisation: Cartesian finite-integration grid of n^3 cells of spacing
+ * h, lowest-order edge unknowns, homogeneous Dirichlet on the outer surface.
+ *
+ * DEVICE / EDGE LAYOUT.  Every full edge vector ("layout vector") holds
+ * 3 n^3 doubles: component c in {x, y, z} occupies [c n^3, (c+1) n^3), and
+ * the edge of component c whose lower node is (i, j, k) sits at
+ *     c n^3 + i + n (j + n k),   0 <= i, j, k < n.
+ * Edges with a node index n (all of them Dirichlet) are not stored; stored
+ * Dirichlet edges (index 0 in a direction normal to the edge) hold zero.
+ * "n-edges" are interior edges none of whose four cells conducts; "c-edges"
+ * are the other interior edges.  Compact conducting vectors (a_c) list the
+ * c-edges in increasing layout index, i.e. ordered by (component, k, j, i).
+ *
+ * Cell arrays are n^3 entries, flat index i + n (j + n k).
+ *
+ * CONVENTIONS.  Every call returns an int status: MQS_OK (0) or a negative
+ * MQS_ERR_* code; mqs_last_error() gives a text for the last failure on a
+ * handle.  A handle owns all its device memory (allocated in mqs_setup,
+ * released by mqs_destroy).  Pointers without a _dev suffix are host
+ * pointers; _dev calls take device pointers and a cudaStream_t passed as
+ * void* (NULL = the handle's stream) and do not synchronise the host.  No
+ * caller pointer is retained after a call returns.  All arithmetic is
+ * IEEE FP64.  A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef MQS_H
+#define MQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MQS_OK                  0
+#define MQS_ERR_ARG            -1   /* invalid argument or size            */
+#define MQS_ERR_CUDA           -2   /* CUDA runtime error                  */
+#define MQS_ERR_OOM            -3   /* device allocation failed            */
+#define MQS_ERR_NOT_CONVERGED  -4   /* PCG reached maxit                   */
+#define MQS_ERR_BREAKDOWN      -5   /* PCG p.Kp <= 0                       */
+#define MQS_ERR_NAN            -6   /* non-finite value met                */
+#define MQS_ERR_UNSTABLE       -7   /* explicit Euler state blew up        */
+#define MQS_ERR_TIMEOUT        -8   /* a bounded device wait gave up       */
+#define MQS_ERR_UNIMPLEMENTED  -9
+
+#define MQS_START_ZERO 0            /* x0 = 0                              */
+#define MQS_START_PREV 1            /* x0 = solution of the previous step  */
+#define MQS_START_SPE  2            /* eq. (SPE_x0), last spe_depth sols   */
+#define MQS_START_POD  3            /* eq. (POD_x0), last pod_snapshots    */
+
+typedef struct mqs_handle mqs_handle;
+
+/* Grid: n cells per axis (2 <= n <= 800), spacing h metres. */
+typedef struct { int n; double h; } mqs_grid;
+
+/* Materials.  sigma_cell: n^3 conductivities (S/m, >= 0).  brauer_cell:
+ * n^3 flags (1 = reluctivity nu(B) = k1 exp(k2 B^2) + k3, else nu0), or
+ * NULL; a flagged cell must conduct.  nu0 = reluctivity of every other cell. */
+typedef struct {
+    const double*  sigma_cell;
+    const uint8_t* brauer_cell;
+    double nu0, k1, k2, k3;
+} mqs_materials;
+
+/* Coil: one loop of edges in node plane plane_k around the node square
+ * [i0, i1] x [j0, j1], counter-clockwise seen from +z (the distribution X_S
+ * of Sec. II, J_S = X_S i_S(t)); current i(t) = amplitude sin(2 pi freq t)
+ * (waveform 0) or amplitude (1 - exp(-t / tau)) (waveform 1, Sec. IV).
+ * The loop must lie on interior n-edges. */
+typedef struct {
+    int plane_k, i0, j0, i1, j1;
+    double amplitude, freq_hz;
+    int waveform;
+    double tau;
+} mqs_coil;
+
+/* Options.  tol: PCG stopping rule ||b - K_n x||_2 <= tol ||b||_2 (true
+ * residual).  maxit: PCG iteration cap.  start_mode: MQS_START_*.
+ * spe_depth (1..16), pod_snapshots (1..40), eps_pod (POD truncation
+ * sigma_i/sigma_1 >= eps_pod, eq. (relSV2)), eps_lin (SPE drop tolerance).
+ * dt: explicit Euler step (s); may be set later with mqs_set_dt.
+ * rhs_time: 0 = source at t_m (as printed in eq. (acm)), 1 = at t_{m-1}. */
+typedef struct {
+    double tol;
+    int    maxit;
+    int    start_mode;
+    int    spe_depth;
+    int    pod_snapshots;
+    double eps_pod;
+    double eps_lin;
+    double dt;
+    int    rhs_time;
+    int    reserved;
+} mqs_options;
+
+typedef struct {
+    int    n;             /* cells per axis                                 */
+    long   n_layout;      /* 3 n^3: length of a layout vector               */
+    long   n_c;           /* number of c-edges (length of a_c)              */
+    long   n_n;           /* number of n-edges (unknowns of K_n)            */
+    int    box_lo[3];     /* node range of the conducting region [lo, hi)   */
+    int    box_hi[3];
+} mqs_layout_info;
+
+typedef struct {
+    int    iterations;    /* products K_n p inside the PCG loop             */
+    int    status;        /* MQS_OK or MQS_ERR_*                            */
+    int    rank;          /* SPE columns kept / POD k (0 otherwise)         */
+    int    reserved;
+    double relres;        /* final true ||b - K_n w|| / ||b||               */
+    double start_relres;  /* ||b - K_n x0|| / ||b||                          */
+    double pod_info;      /* eq. (keepInfo) ratio, POD mode (else 0)        */
+} mqs_step_stats;
+
+typedef struct {
+    int    iterations;
+    int    status;
+    double relres;
+    double start_relres;
+} mqs_pcg_info;
+
+/* mqs_setup: Sec. II eq. (DAE).  conductor_mask: n^3 flags selecting the
+ * conducting region Omega_c (flagged cells must have sigma > 0, the others
+ * are treated as nonconducting whatever their sigma), or NULL to take
+ * sigma > 0.  Classifies edges, builds the per-edge
+ * conductivity M_c (h * mean sigma of the four cells of an edge), the coil
+ * distribution and all device buffers.  K_n = C_n^T M_nu C_n is applied
+ * matrix-free: every face touching an n-edge has reluctivity nu0, so K_n is
+ * (nu0/h) times an integer stencil and its Jacobi diagonal is the uniform
+ * 4 nu0/h.  State after setup: a_c = 0, t = 0, m = 0, empty history.
+ * Errors: MQS_ERR_ARG (sizes, coil not on n-edges, nonconducting Brauer
+ * cell, no conducting cell), MQS_ERR_OOM, MQS_ERR_CUDA.  On failure *out is
+ * NULL and nothing is leaked. */
+int mqs_setup(const mqs_grid* grid, const mqs_materials* mat,
+              const uint8_t* conductor_mask, const mqs_coil* coil,
+              const mqs_options* opts, mqs_handle** out);
+
+int mqs_destroy(mqs_handle* h);
+
+/* Copies a NUL-terminated text of the last error (possibly empty). */
+int mqs_last_error(const mqs_handle* h, char* buf, size_t len);
+
+int mqs_layout(const mqs_handle* h, mqs_layout_info* info);
+
+/* mqs_set_dt / mqs_get_dt: the explicit Euler step (eq. (acm)). */
+int mqs_set_dt(mqs_handle* h, double dt);
+int mqs_get_dt(const mqs_handle* h, double* dt);
+
+/* mqs_set_options: replaces tol, maxit, start_mode, spe_depth,
+ * pod_snapshots, eps_pod, eps_lin, rhs_time (dt is kept unless > 0).
+ * Changing start_mode, spe_depth or pod_snapshots clears the history. */
+int mqs_set_options(mqs_handle* h, const mqs_options* opts);
+
+/* mqs_lambda_max: eq. (CFL) - power method on M_c^-1/2 K_S(0) M_c^-1/2,
+ * Rayleigh quotient, every application of K_S using one PCG solve of K_n
+ * (tolerance pcg_tol).  v0: host vector of n_c entries (the start vector;
+ * random numbers are the caller's).  Stops when |dlambda| < rtol lambda or
+ * after maxit iterations.  Returns lambda_max (1/s) and the iterations. */
+int mqs_lambda_max(mqs_handle* h, const double* v0, double pcg_tol,
+                   double rtol, int maxit, double* lambda_max, int* iters);
+
+/* mqs_step: nsteps explicit Euler steps (eq. (acm) with the source sign of
+ * eq. (ODE)); each step m:
+ *   b   = i(t) X_s - K_cn^T a_c^{m-1}        on n-edges   (eq. (mrhs))
+ *   x0  = start vector (zero / previous / SPE / POD)
+ *   w   = PCG(K_n, b, x0)                    (= a_n, eq. (a_n))
+ *   a_c = a_c - dt M_c^-1 (K(a)[a_c; w])_c   (Brauer nu re-evaluated per cell)
+ * then w and K_n w join the start-vector history.  per_step: host array of
+ * nsteps records or NULL.  Returns the first non-OK step status (the step
+ * loop still completes), MQS_ERR_ARG if dt is unset. */
+int mqs_step(mqs_handle* h, int nsteps, mqs_step_stats* per_step);
+
+/* State access.  a_c: n_c doubles in compact c-edge order. */
+int mqs_get_state(mqs_handle* h, double* a_c, size_t n_c, double* t, long* m);
+int mqs_set_state(mqs_handle* h, const double* a_c, size_t n_c, double t, long m);
+int mqs_get_state_dev(mqs_handle* h, double* a_c_dev, size_t n_c, void* stream);
+int mqs_set_state_dev(mqs_handle* h, const double* a_c_dev, size_t n_c, void* stream);
+/* Copies the latest PCG solution w (layout vector, zero off n-edges). */
+int mqs_get_solution(mqs_handle* h, double* w_layout);
+int mqs_reset_history(mqs_handle* h);
+
+/* pcg_solve: Sec. III eq. (mrhs) - Jacobi-preconditioned CG for K_n x = b
+ * with the handle's K_n.  b, x: layout vectors (host); entries of b off
+ * n-edges are ignored, x is read as the start vector and overwritten with
+ * the solution (zero off n-edges).  Stops on the true relative residual.
+ * info may be NULL.  Returns MQS_OK, MQS_ERR_NOT_CONVERGED,
+ * MQS_ERR_BREAKDOWN, MQS_ERR_NAN or MQS_ERR_TIMEOUT. */
+int pcg_solve(mqs_handle* h, const double* b, double* x, double tol,
+              int maxit, mqs_pcg_info* info);
+int pcg_solve_dev(mqs_handle* h, const double* b_dev, double* x_dev,
+                  double tol, int maxit, mqs_pcg_info* info, void* stream);
+
+/* mqs_apply_kn: y = K_n x for layout vectors (host); entries off n-edges of
+ * x are ignored and those of y are set to zero. */
+int mqs_apply_kn(mqs_handle* h, const double* x, double* y);
+int mqs_apply_kn_dev(mqs_handle* h, const double* x_dev, double* y_dev, void* stream);
+
+/* mqs_conductor_rate: F = (K(a)[a_c; w])_c with the Brauer reluctivity
+ * evaluated at a (the bracket of eq. (acm) after the single solve).  a_c:
+ * n_c doubles, w: layout vector, F: n_c doubles (host). */
+int mqs_conductor_rate(mqs_handle* h, const double* a_c, const double* w, double* F);
+
+/* History for the start vectors (Sec. III).  mqs_push_history appends a
+ * solution w (layout vector, host) as the newest entry; K_n w is computed
+ * by the library (during mqs_step it is a by-product of the PCG residual). */
+int mqs_push_history(mqs_handle* h, const double* w);
+
+/* spe_start: eq. (SPE_x0) for right-hand side b (layout, host) over the
+ * span of the newest spe_depth history entries.  x0: layout output.
+ * rank_used: columns kept after the linear-dependence drop (may be NULL). */
+int spe_start(mqs_handle* h, const double* b, double* x0, int* rank_used);
+
+/* pod_basis: eqs. (SVD), (relSV2), (keepInfo) for the newest pod_snapshots
+ * history entries: *k kept singular values, sigma (pod_snapshots doubles,
+ * descending, zero-filled), *info_ratio.  Any output may be NULL. */
+int pod_basis(mqs_handle* h, int* k, double* sigma, double* info_ratio);
+
+/* pod_start: eq. (POD_x0) for right-hand side b (layout, host). */
+int pod_start(mqs_handle* h, const double* b, double* x0, int* k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MQS_H */

@@ -1,0 +1,314 @@
+"""ctypes binding of ``libmqs.so`` (argument marshalling only).
+
+Every compute step runs in the CUDA library; this module converts numpy
+arrays (host calls) or torch CUDA tensors (``*_dev`` calls) to plain pointers
+and sizes.  Loading fails loudly if the compiled library is absent: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmqs.so")
+
+MQS_OK = 0
+ERRORS = {-1: "MQS_ERR_ARG", -2: "MQS_ERR_CUDA", -3: "MQS_ERR_OOM", -4: "MQS_ERR_NOT_CONVERGED",
+          -5: "MQS_ERR_BREAKDOWN", -6: "MQS_ERR_NAN", -7: "MQS_ERR_UNSTABLE", -8: "MQS_ERR_TIMEOUT",
+          -9: "MQS_ERR_UNIMPLEMENTED"}
+START_ZERO, START_PREV, START_SPE, START_POD = 0, 1, 2, 3
+
+EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_dt", "mqs_get_dt",
+           "mqs_set_options", "mqs_lambda_max", "mqs_step", "mqs_get_state", "mqs_set_state",
+           "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution", "mqs_reset_history",
+           "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev", "mqs_conductor_rate",
+           "mqs_push_history", "spe_start", "pod_basis", "pod_start")
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int), ("h", C.c_double)]
+
+
+class Materials(C.Structure):
+    _fields_ = [("sigma_cell", C.POINTER(C.c_double)), ("brauer_cell", C.POINTER(C.c_uint8)),
+                ("nu0", C.c_double), ("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double)]
+
+
+class Coil(C.Structure):
+    _fields_ = [("plane_k", C.c_int), ("i0", C.c_int), ("j0", C.c_int), ("i1", C.c_int), ("j1", C.c_int),
+                ("amplitude", C.c_double), ("freq_hz", C.c_double), ("waveform", C.c_int), ("tau", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
+                ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
+                ("dt", C.c_double), ("rhs_time", C.c_int), ("reserved", C.c_int)]
+
+
+class LayoutInfo(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_layout", C.c_long), ("n_c", C.c_long), ("n_n", C.c_long),
+                ("box_lo", C.c_int * 3), ("box_hi", C.c_int * 3)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rank", C.c_int), ("reserved", C.c_int),
+                ("relres", C.c_double), ("start_relres", C.c_double), ("pod_info", C.c_double)]
+
+
+class PcgInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double),
+                ("start_relres", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libmqs.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1611_06721_gb300.build.build() "
+                           "(the library has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, D, I, L, V = C.POINTER, C.c_double, C.c_int, C.c_long, C.c_void_p
+    H = V
+    sig = {
+        "mqs_setup": ([P(Grid), P(Materials), P(C.c_uint8), P(Coil), P(Options), P(H)], I),
+        "mqs_destroy": ([H], I),
+        "mqs_last_error": ([H, C.c_char_p, C.c_size_t], I),
+        "mqs_layout": ([H, P(LayoutInfo)], I),
+        "mqs_set_dt": ([H, D], I),
+        "mqs_get_dt": ([H, P(D)], I),
+        "mqs_set_options": ([H, P(Options)], I),
+        "mqs_lambda_max": ([H, P(D), D, D, I, P(D), P(I)], I),
+        "mqs_step": ([H, I, P(StepStats)], I),
+        "mqs_get_state": ([H, P(D), C.c_size_t, P(D), P(L)], I),
+        "mqs_set_state": ([H, P(D), C.c_size_t, D, L], I),
+        "mqs_get_state_dev": ([H, V, C.c_size_t, V], I),
+        "mqs_set_state_dev": ([H, V, C.c_size_t, V], I),
+        "mqs_get_solution": ([H, P(D)], I),
+        "mqs_reset_history": ([H], I),
+        "pcg_solve": ([H, P(D), P(D), D, I, P(PcgInfo)], I),
+        "pcg_solve_dev": ([H, V, V, D, I, P(PcgInfo), V], I),
+        "mqs_apply_kn": ([H, P(D), P(D)], I),
+        "mqs_apply_kn_dev": ([H, V, V, V], I),
+        "mqs_conductor_rate": ([H, P(D), P(D), P(D)], I),
+        "mqs_push_history": ([H, P(D)], I),
+        "spe_start": ([H, P(D), P(D), P(I)], I),
+        "pod_basis": ([H, P(I), P(D), P(D)], I),
+        "pod_start": ([H, P(D), P(D), P(I)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+class MqsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+@dataclass
+class SolverOptions:
+    tol: float = 1e-10
+    maxit: int = 100000
+    start_mode: int = START_ZERO
+    spe_depth: int = 8
+    pod_snapshots: int = 20
+    eps_pod: float = 1e-4
+    eps_lin: float = 1e-10
+    dt: float = 0.0
+    rhs_time: int = 0
+
+    def c(self):
+        return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
+                       self.eps_pod, self.eps_lin, self.dt, self.rhs_time, 0)
+
+
+class Solver:
+    """One handle of the library: grid, materials, coil and options."""
+
+    def __init__(self, n, h, sigma_cell, brauer_cell, nu0, k1, k2, k3, coil, options: SolverOptions,
+                 conductor_mask=None):
+        self.lib = load()
+        self._sigma = _f64(sigma_cell, n ** 3)
+        self._brauer = None if brauer_cell is None else np.ascontiguousarray(brauer_cell, dtype=np.uint8).reshape(-1)
+        mat = Materials(_dp(self._sigma),
+                        None if self._brauer is None else self._brauer.ctypes.data_as(C.POINTER(C.c_uint8)),
+                        nu0, k1, k2, k3)
+        mask = None
+        if conductor_mask is not None:
+            self._mask = np.ascontiguousarray(conductor_mask, dtype=np.uint8).reshape(-1)
+            mask = self._mask.ctypes.data_as(C.POINTER(C.c_uint8))
+        self.options = options
+        h_ = C.c_void_p()
+        rc = self.lib.mqs_setup(C.byref(Grid(n, h)), C.byref(mat), mask, C.byref(Coil(*coil)),
+                                C.byref(options.c()), C.byref(h_))
+        if rc != MQS_OK:
+            raise MqsError(rc, "mqs_setup failed (see stderr)")
+        self.h = h_
+        info = LayoutInfo()
+        self._check(self.lib.mqs_layout(self.h, C.byref(info)))
+        self.n = info.n
+        self.n_layout = info.n_layout
+        self.n_c = info.n_c
+        self.n_n = info.n_n
+
+    @classmethod
+    def from_problem(cls, p, options: SolverOptions, conductor_mask=None):
+        coil = (p.coil_k, p.coil_i0, p.coil_j0, p.coil_i1, p.coil_j1, p.amplitude, p.freq, p.waveform, p.tau)
+        return cls(p.N, p.h, p.sigma_cell, p.brauer_cell, p.nu0, p.k1, p.k2, p.k3, coil, options,
+                   conductor_mask)
+
+    def _check(self, rc, allow=()):
+        if rc != MQS_OK and rc not in allow:
+            buf = C.create_string_buffer(512)
+            self.lib.mqs_last_error(self.h, buf, 512)
+            raise MqsError(rc, buf.value.decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mqs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ---------------------------------------------------------------
+    def set_dt(self, dt):
+        self._check(self.lib.mqs_set_dt(self.h, dt))
+
+    def get_dt(self):
+        d = C.c_double()
+        self._check(self.lib.mqs_get_dt(self.h, C.byref(d)))
+        return d.value
+
+    def set_options(self, options: SolverOptions):
+        self._check(self.lib.mqs_set_options(self.h, C.byref(options.c())))
+        self.options = options
+
+    def reset_history(self):
+        self._check(self.lib.mqs_reset_history(self.h))
+
+    def lambda_max(self, v0, pcg_tol=1e-12, rtol=1e-8, maxit=2000):
+        v0 = _f64(v0, self.n_c)
+        lam, it = C.c_double(), C.c_int()
+        self._check(self.lib.mqs_lambda_max(self.h, _dp(v0), pcg_tol, rtol, maxit, C.byref(lam), C.byref(it)))
+        return lam.value, it.value
+
+    # -- time stepping -----------------------------------------------------------------
+    def step(self, nsteps, allow_fail=False):
+        st = (StepStats * max(nsteps, 1))()
+        rc = self.lib.mqs_step(self.h, nsteps, st)
+        if not allow_fail:
+            self._check(rc)
+        return rc, [st[q] for q in range(nsteps)]
+
+    def mqs_step(self, nsteps):
+        return self.step(nsteps)[1]
+
+    def get_state(self):
+        a = np.empty(self.n_c)
+        t, m = C.c_double(), C.c_long()
+        self._check(self.lib.mqs_get_state(self.h, _dp(a), a.size, C.byref(t), C.byref(m)))
+        return a, t.value, m.value
+
+    def set_state(self, a_c, t=0.0, m=0):
+        a = _f64(a_c, self.n_c)
+        self._check(self.lib.mqs_set_state(self.h, _dp(a), a.size, t, m))
+
+    def get_state_dev(self, out, stream=0):
+        self._check(self.lib.mqs_get_state_dev(self.h, C.c_void_p(out.data_ptr()), self.n_c,
+                                               C.c_void_p(stream)))
+
+    def set_state_dev(self, a, stream=0):
+        self._check(self.lib.mqs_set_state_dev(self.h, C.c_void_p(a.data_ptr()), self.n_c, C.c_void_p(stream)))
+
+    def get_solution(self):
+        w = np.empty(self.n_layout)
+        self._check(self.lib.mqs_get_solution(self.h, _dp(w)))
+        return w
+
+    # -- stand-alone operations -------------------------------------------------------
+    def pcg_solve(self, b, x0=None, tol=1e-10, maxit=100000, allow_fail=False):
+        b = _f64(b, self.n_layout)
+        x = np.zeros(self.n_layout) if x0 is None else _f64(x0, self.n_layout).copy()
+        info = PcgInfo()
+        rc = self.lib.pcg_solve(self.h, _dp(b), _dp(x), tol, maxit, C.byref(info))
+        if not allow_fail:
+            self._check(rc)
+        return x, info
+
+    def pcg_solve_dev(self, b, x, tol=1e-10, maxit=100000, stream=0, allow_fail=False):
+        info = PcgInfo()
+        rc = self.lib.pcg_solve_dev(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), tol, maxit,
+                                    C.byref(info), C.c_void_p(stream))
+        if not allow_fail:
+            self._check(rc)
+        return info
+
+    def apply_kn(self, x):
+        x = _f64(x, self.n_layout)
+        y = np.empty(self.n_layout)
+        self._check(self.lib.mqs_apply_kn(self.h, _dp(x), _dp(y)))
+        return y
+
+    def apply_kn_dev(self, x, y, stream=0):
+        self._check(self.lib.mqs_apply_kn_dev(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                              C.c_void_p(stream)))
+
+    def conductor_rate(self, a_c, w):
+        a = _f64(a_c, self.n_c)
+        w = _f64(w, self.n_layout)
+        F = np.empty(self.n_c)
+        self._check(self.lib.mqs_conductor_rate(self.h, _dp(a), _dp(w), _dp(F)))
+        return F
+
+    def push_history(self, w):
+        w = _f64(w, self.n_layout)
+        self._check(self.lib.mqs_push_history(self.h, _dp(w)))
+
+    def spe_start(self, b):
+        b = _f64(b, self.n_layout)
+        x0 = np.empty(self.n_layout)
+        r = C.c_int()
+        self._check(self.lib.spe_start(self.h, _dp(b), _dp(x0), C.byref(r)))
+        return x0, r.value
+
+    def pod_basis(self):
+        k, info = C.c_int(), C.c_double()
+        sig = np.zeros(self.options.pod_snapshots)
+        self._check(self.lib.pod_basis(self.h, C.byref(k), _dp(sig), C.byref(info)))
+        return k.value, sig, info.value
+
+    def pod_start(self, b):
+        b = _f64(b, self.n_layout)
+        x0 = np.empty(self.n_layout)
+        k = C.c_int()
+        self._check(self.lib.pod_start(self.h, _dp(b), _dp(x0), C.byref(k)))
+        return x0, k.value

@@ -1,0 +1,792 @@
+// C ABI of the library: handle life cycle, the explicit Euler step driver and
+// the stand-alone entry points declared in include/mqs.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include "mqs_kernels.h"
+#include "mrhs.h"
+
+using namespace mqs;
+
+struct mqs_handle {
+  int n = 0;
+  long long n3 = 0, len = 0;
+  double h = 0, nu0 = 0, k1 = 0, k2 = 0, k3 = 0;
+  mqs_coil coil{};
+  mqs_options opt{};
+  double dt = 0.0, t = 0.0;
+  long m = 0;
+  long n_c = 0, n_n = 0;
+  int cb_lo[3], cb_hi[3], clo[3], chi[3];
+  Box rhs_box{}, full{};
+  bool any_brauer = false;
+  cudaStream_t st = nullptr;
+  int nblk = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  // device buffers
+  uint8_t* cflags = nullptr;
+  int* cidx = nullptr;
+  double *invmc = nullptr, *isqmc = nullptr;
+  uint8_t* brauer = nullptr;
+  double* nu = nullptr;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *lx = nullptr, *b = nullptr;
+  double *xu = nullptr, *bu = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  double *ac_full = nullptr, *ac = nullptr, *ac2 = nullptr, *cvec = nullptr, *cvec2 = nullptr;
+  double* part = nullptr;
+  unsigned* bar = nullptr;
+  int* derr = nullptr;
+  PcgResult* pres = nullptr;
+  double* spe_D[kMaxSpe] = {};
+  double* spe_LD[kMaxSpe] = {};
+  int spe_m = 0;
+  double* pod_X[kMaxPod] = {};
+  double* pod_LX[kMaxPod] = {};
+  double *pod_G = nullptr, *pod_A = nullptr;
+  int pod_m = 0, pod_next = 0;
+  double *tspart = nullptr, *coef = nullptr, *sigma = nullptr, *scal = nullptr;
+  SmallOut* small = nullptr;
+  mqs_step_stats* dstats = nullptr;
+  int dstats_cap = 0;
+  DevGeom dg{};
+  CondGeom cg{};
+};
+
+namespace {
+
+int fail(mqs_handle* H, int code, const char* msg) {
+  if (H) H->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      H->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #call;      \
+      return MQS_ERR_CUDA;                                                         \
+    }                                                                              \
+  } while (0)
+#define RK(call)                                                                   \
+  do {                                                                             \
+    int r_ = (call);                                                               \
+    if (r_ != MQS_OK) {                                                            \
+      if (H->err.empty()) H->err = "kernel launch failed: " #call;                 \
+      return r_;                                                                   \
+    }                                                                              \
+  } while (0)
+
+template <class T>
+int dalloc(mqs_handle* H, T** ptr, size_t count) {
+  void* v = nullptr;
+  if (cudaMalloc(&v, count * sizeof(T) + 64) != cudaSuccess) {
+    cudaGetLastError();
+    H->err = "device allocation failed";
+    return MQS_ERR_OOM;
+  }
+  H->allocs.push_back(v);
+  *ptr = static_cast<T*>(v);
+  return MQS_OK;
+}
+
+// ---- small elementwise kernels -------------------------------------------------------
+// y = mask_n * s * v  (layout vectors)
+__global__ void mask_scale_kernel(Geom g, const double* v, double* y, double s) {
+  const long long len = 3 * g.n3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / g.n3);
+    const long long pos = e - c * g.n3;
+    const int i = (int)(pos % g.n), j = (int)((pos / g.n) % g.n), k = (int)(pos / ((long long)g.n * g.n));
+    y[e] = (nmask(g, i, j, k) >> c & 1u) ? s * v[e] : 0.0;
+  }
+}
+
+// power method pieces over the n_c conducting unknowns (one block)
+__global__ void power_prep_kernel(int n_c, const double* v, const double* isq, double* u) {
+  for (int q = threadIdx.x + blockIdx.x * blockDim.x; q < n_c; q += blockDim.x * gridDim.x) u[q] = v[q] * isq[q];
+}
+__global__ void power_update_kernel(int n_c, const double* F, const double* isq, double* v, double* out) {
+  __shared__ double red[2][32];
+  double a = 0.0, zz = 0.0;
+  for (int q = threadIdx.x; q < n_c; q += blockDim.x) {
+    const double z = F[q] * isq[q];
+    a = fma(v[q], z, a);
+    zz = fma(z, z, zz);
+  }
+  a = warp_sum(a); zz = warp_sum(zz);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) { red[0][w] = a; red[1][w] = zz; }
+  __syncthreads();
+  __shared__ double nz;
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int t = 0; t < nw; ++t) { s0 += red[0][t]; s1 += red[1][t]; }
+    nz = sqrt(s1);
+    out[0] = s0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n_c; q += blockDim.x) v[q] = F[q] * isq[q] / nz;
+}
+
+__global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, mqs_step_stats* dst) {
+  mqs_step_stats s;
+  s.iterations = pr->iterations;
+  s.status = pr->status;
+  s.rank = use_small ? so->rank : 0;
+  s.reserved = 0;
+  s.relres = pr->relres;
+  s.start_relres = pr->start_relres;
+  s.pod_info = (use_small == 2) ? so->info : 0.0;
+  *dst = s;
+}
+
+__global__ void rhs_current_kernel(double* out, double scale, double amp, double freq, int waveform, double tau,
+                                   double t) {
+  // i_S(t) of Sec. II / Sec. IV, times h/nu0
+  const double i_t = (waveform == 0) ? amp * sin(2.0 * 3.141592653589793 * freq * t) : amp * (1.0 - exp(-t / tau));
+  out[0] = scale * i_t;
+}
+
+int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t st) {
+  mask_scale_kernel<<<H->nblk * 2, 256, 0, st>>>(H->dg.g, v, y, s);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+int run_pcg(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st) {
+  CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
+  return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
+                    st);
+}
+
+int read_pcg(mqs_handle* H, mqs_pcg_info* info, cudaStream_t st) {
+  PcgResult pr{};
+  int derr = 0;
+  CK(cudaMemcpyAsync(&pr, H->pres, sizeof(pr), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&derr, H->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (info) { info->iterations = pr.iterations; info->status = pr.status; info->relres = pr.relres; info->start_relres = pr.start_relres; }
+  if (derr != 0) return fail(H, derr, "a bounded grid barrier wait timed out");
+  if (pr.status != MQS_OK) H->err = "PCG did not converge";
+  return pr.status;
+}
+
+VecSet vs(double* const* a, int m) {
+  VecSet s{};
+  for (int p = 0; p < kMaxVec; ++p) s.v[p] = (p < m) ? a[p] : (m > 0 ? a[0] : nullptr);
+  return s;
+}
+MutVecSet mvs(double* const* a, int m) {
+  MutVecSet s{};
+  for (int p = 0; p < kMaxVec; ++p) s.v[p] = (p < m) ? a[p] : (m > 0 ? a[0] : nullptr);
+  return s;
+}
+
+// push solution w (layout, physical units) with L w into the active history
+int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t st) {
+  const int mode = H->opt.start_mode;
+  if (mode == MQS_START_SPE) {
+    const int d = H->opt.spe_depth;
+    const int mn = H->spe_m + 1 < d ? H->spe_m + 1 : d;
+    RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, st));
+    H->spe_m = mn;
+  } else if (mode == MQS_START_POD) {
+    const int np = H->opt.pod_snapshots;
+    const int slot = H->pod_next;
+    CK(cudaMemcpyAsync(H->pod_X[slot], w, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(H->pod_LX[slot], lw, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+    const int mn = H->pod_m + 1 < np ? H->pod_m + 1 : np;
+    RK(pod_push(vs(H->pod_X, mn), H->pod_X[slot], H->pod_LX[slot], mn, slot, H->len, H->tspart, H->pod_G,
+                H->pod_A, st));
+    H->pod_m = mn;
+    H->pod_next = (slot + 1) % np;
+  }
+  return MQS_OK;
+}
+
+// start vector into x for right-hand side b (scaled units); sets H->small
+int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int* used_small) {
+  *used_small = 0;
+  switch (H->opt.start_mode) {
+    case MQS_START_ZERO:
+      CK(cudaMemsetAsync(x, 0, sizeof(double) * H->len, st));
+      break;
+    case MQS_START_PREV:
+      break;
+    case MQS_START_SPE:
+      RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), vs(H->spe_LD, H->opt.spe_depth), H->spe_m, b, x, H->len,
+                H->opt.eps_lin, H->tspart, H->coef, H->small, st));
+      *used_small = 1;
+      if (H->spe_m == 0) *used_small = 0;
+      break;
+    case MQS_START_POD:
+      RK(pod_x0(vs(H->pod_X, H->opt.pod_snapshots), H->pod_m, H->pod_G, H->pod_A, b, x, H->len, H->opt.eps_pod,
+                H->tspart, H->coef, H->sigma, H->small, st));
+      *used_small = H->pod_m > 0 ? 2 : 0;
+      break;
+    default:
+      return fail(H, MQS_ERR_ARG, "unknown start mode");
+  }
+  return MQS_OK;
+}
+
+int validate_options(const mqs_options* o, std::string& why) {
+  if (!(o->tol > 0.0) || o->tol >= 1.0) { why = "tol must lie in (0, 1)"; return MQS_ERR_ARG; }
+  if (o->maxit < 1) { why = "maxit must be positive"; return MQS_ERR_ARG; }
+  if (o->start_mode < 0 || o->start_mode > 3) { why = "unknown start mode"; return MQS_ERR_ARG; }
+  if (o->spe_depth < 1 || o->spe_depth > kMaxSpe) { why = "spe_depth must be in [1, 16]"; return MQS_ERR_ARG; }
+  if (o->pod_snapshots < 1 || o->pod_snapshots > kMaxPod) { why = "pod_snapshots must be in [1, 40]"; return MQS_ERR_ARG; }
+  if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
+  if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
+  return MQS_OK;
+}
+
+int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, const uint8_t* cmask,
+             const mqs_coil* coil, const mqs_options* opts) {
+  const int n = grid->n;
+  if (n < 2 || n > 800) return fail(H, MQS_ERR_ARG, "grid n must be in [2, 800]");
+  if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return fail(H, MQS_ERR_ARG, "grid spacing must be positive");
+  if (!mat->sigma_cell) return fail(H, MQS_ERR_ARG, "sigma_cell is NULL");
+  if (!(mat->nu0 > 0.0)) return fail(H, MQS_ERR_ARG, "nu0 must be positive");
+  std::string why;
+  if (validate_options(opts, why) != MQS_OK) return fail(H, MQS_ERR_ARG, why.c_str());
+  H->n = n;
+  H->n3 = (long long)n * n * n;
+  H->len = 3 * H->n3;
+  H->h = grid->h;
+  H->nu0 = mat->nu0; H->k1 = mat->k1; H->k2 = mat->k2; H->k3 = mat->k3;
+  H->coil = *coil;
+  H->opt = *opts;
+  H->dt = opts->dt;
+  const long long n3 = H->n3;
+  // conducting cells
+  std::vector<double> sig(n3);
+  std::vector<uint8_t> br(n3, 0);
+  int lo[3] = {n, n, n}, hi[3] = {0, 0, 0};
+  for (long long c = 0; c < n3; ++c) {
+    const double s = mat->sigma_cell[c];
+    if (!(s >= 0.0) || !std::isfinite(s)) return fail(H, MQS_ERR_ARG, "sigma must be finite and >= 0");
+    bool cond = cmask ? (cmask[c] != 0) : (s > 0.0);
+    if (cmask && cmask[c] && !(s > 0.0)) return fail(H, MQS_ERR_ARG, "a masked conducting cell has sigma <= 0");
+    sig[c] = cond ? s : 0.0;
+    if (mat->brauer_cell && mat->brauer_cell[c]) {
+      if (!cond) return fail(H, MQS_ERR_ARG, "a Brauer (nonlinear) cell must conduct");
+      br[c] = 1;
+      H->any_brauer = true;
+    }
+    if (cond) {
+      const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+      const int v[3] = {i, j, k};
+      for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], v[a]); hi[a] = std::max(hi[a], v[a] + 1); }
+    }
+  }
+  if (hi[0] == 0) return fail(H, MQS_ERR_ARG, "no conducting cell");
+  for (int a = 0; a < 3; ++a) {
+    H->clo[a] = lo[a]; H->chi[a] = hi[a];
+    H->cb_lo[a] = lo[a]; H->cb_hi[a] = std::min(hi[a] + 1, n);
+  }
+  auto cellsig = [&](int i, int j, int k) -> double {
+    if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) return 0.0;
+    return sig[i + (long long)n * (j + (long long)n * k)];
+  };
+  // c-edges: interior edges with a conducting neighbour cell (M_kappa > 0)
+  const int w0 = H->cb_hi[0] - H->cb_lo[0], w1 = H->cb_hi[1] - H->cb_lo[1], w2 = H->cb_hi[2] - H->cb_lo[2];
+  std::vector<uint8_t> cf((size_t)w0 * w1 * w2, 0);
+  std::vector<int> cidx;
+  std::vector<double> invmc, isqmc;
+  for (int c = 0; c < 3; ++c)
+    for (int k = H->cb_lo[2]; k < H->cb_hi[2]; ++k)
+      for (int j = H->cb_lo[1]; j < H->cb_hi[1]; ++j)
+        for (int i = H->cb_lo[0]; i < H->cb_hi[0]; ++i) {
+          bool interior = (c == 0) ? (j > 0 && k > 0) : (c == 1) ? (i > 0 && k > 0) : (i > 0 && j > 0);
+          if (!interior) continue;
+          double s = 0.0;
+          for (int da = -1; da <= 0; ++da)
+            for (int db = -1; db <= 0; ++db) {
+              if (c == 0) s += cellsig(i, j + da, k + db);
+              else if (c == 1) s += cellsig(i + da, j, k + db);
+              else s += cellsig(i + da, j + db, k);
+            }
+          if (!(s > 0.0)) continue;
+          const double mk = H->h * s * 0.25;        // M_kappa = h * mean sigma of 4 cells
+          cf[(i - H->cb_lo[0]) + (size_t)w0 * ((j - H->cb_lo[1]) + (size_t)w1 * (k - H->cb_lo[2]))] |= (uint8_t)(1u << c);
+          cidx.push_back((int)(c * n3 + i + (long long)n * (j + (long long)n * k)));
+          invmc.push_back(1.0 / mk);
+          isqmc.push_back(1.0 / std::sqrt(mk));
+        }
+  H->n_c = (long)cidx.size();
+  H->n_n = 3L * n * (long)(n - 1) * (n - 1) - H->n_c;
+  // coil on interior n-edges
+  const mqs_coil& cl = *coil;
+  if (cl.plane_k < 1 || cl.plane_k > n - 1 || cl.i0 < 1 || cl.j0 < 1 || cl.i1 > n - 1 || cl.j1 > n - 1 ||
+      cl.i0 >= cl.i1 || cl.j0 >= cl.j1)
+    return fail(H, MQS_ERR_ARG, "coil loop must lie strictly inside the grid");
+  if (cl.waveform != 0 && cl.waveform != 1) return fail(H, MQS_ERR_ARG, "unknown waveform");
+  if (cl.waveform == 1 && !(cl.tau > 0.0)) return fail(H, MQS_ERR_ARG, "tau must be positive");
+  auto isc = [&](int c, int i, int j, int k) -> bool {
+    if (i < H->cb_lo[0] || j < H->cb_lo[1] || k < H->cb_lo[2] || i >= H->cb_hi[0] || j >= H->cb_hi[1] || k >= H->cb_hi[2])
+      return false;
+    return (cf[(i - H->cb_lo[0]) + (size_t)w0 * ((j - H->cb_lo[1]) + (size_t)w1 * (k - H->cb_lo[2]))] >> c) & 1u;
+  };
+  for (int i = cl.i0; i < cl.i1; ++i)
+    if (isc(0, i, cl.j0, cl.plane_k) || isc(0, i, cl.j1, cl.plane_k))
+      return fail(H, MQS_ERR_ARG, "coil edges must not touch a conducting cell");
+  for (int j = cl.j0; j < cl.j1; ++j)
+    if (isc(1, cl.i0, j, cl.plane_k) || isc(1, cl.i1, j, cl.plane_k))
+      return fail(H, MQS_ERR_ARG, "coil edges must not touch a conducting cell");
+  // right-hand side region: conductor-coupled n-edges and the coil loop
+  for (int a = 0; a < 3; ++a) {
+    H->rhs_box.lo[a] = std::max(lo[a] - 1, 0);
+    H->rhs_box.hi[a] = std::min(hi[a] + 2, n);
+  }
+  const int clo3[3] = {cl.i0, cl.j0, cl.plane_k}, chi3[3] = {cl.i1 + 1, cl.j1 + 1, cl.plane_k + 1};
+  for (int a = 0; a < 3; ++a) {
+    H->rhs_box.lo[a] = std::min(H->rhs_box.lo[a], clo3[a]);
+    H->rhs_box.hi[a] = std::max(H->rhs_box.hi[a], std::min(chi3[a], n));
+  }
+  H->full = Box{{0, 0, 0}, {n, n, n}};
+  // device
+  CK(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking));
+  RK(pcg_max_blocks(&H->nblk));
+  const size_t L = (size_t)H->len;
+  const long ccells = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  RK(dalloc(H, &H->cflags, cf.size()));
+  RK(dalloc(H, &H->cidx, std::max<long>(H->n_c, 1)));
+  RK(dalloc(H, &H->invmc, std::max<long>(H->n_c, 1)));
+  RK(dalloc(H, &H->isqmc, std::max<long>(H->n_c, 1)));
+  RK(dalloc(H, &H->brauer, ccells));
+  RK(dalloc(H, &H->nu, ccells));
+  for (double** v : {&H->x, &H->r, &H->p, &H->q, &H->lx, &H->b, &H->xu, &H->bu, &H->tmp, &H->tmp2, &H->ac_full})
+    RK(dalloc(H, v, L));
+  for (double** v : {&H->ac, &H->ac2, &H->cvec, &H->cvec2}) RK(dalloc(H, v, std::max<long>(H->n_c, 1)));
+  RK(dalloc(H, &H->part, (size_t)8 * H->nblk));
+  RK(dalloc(H, &H->bar, 1));
+  RK(dalloc(H, &H->derr, 1));
+  RK(dalloc(H, &H->pres, 1));
+  RK(dalloc(H, &H->tspart, (size_t)5 * ts_nblk() * kTileSlots));
+  RK(dalloc(H, &H->coef, kMaxVec));
+  RK(dalloc(H, &H->sigma, kMaxVec));
+  RK(dalloc(H, &H->scal, 4));
+  RK(dalloc(H, &H->small, 1));
+  RK(dalloc(H, &H->pod_G, kMaxPod * kMaxPod));
+  RK(dalloc(H, &H->pod_A, kMaxPod * kMaxPod));
+  for (int a = 0; a < kMaxSpe; ++a) { RK(dalloc(H, &H->spe_D[a], L)); RK(dalloc(H, &H->spe_LD[a], L)); }
+  // POD ring allocated on first use of that mode
+  std::vector<uint8_t> brbox(ccells);
+  for (int k = lo[2]; k < hi[2]; ++k)
+    for (int j = lo[1]; j < hi[1]; ++j)
+      for (int i = lo[0]; i < hi[0]; ++i)
+        brbox[(i - lo[0]) + (size_t)(hi[0] - lo[0]) * ((j - lo[1]) + (size_t)(hi[1] - lo[1]) * (k - lo[2]))] =
+            br[i + (long long)n * (j + (long long)n * k)];
+  CK(cudaMemcpy(H->cflags, cf.data(), cf.size(), cudaMemcpyHostToDevice));
+  if (H->n_c) {
+    CK(cudaMemcpy(H->cidx, cidx.data(), sizeof(int) * H->n_c, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(H->invmc, invmc.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(H->isqmc, isqmc.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(H->brauer, brbox.data(), ccells, cudaMemcpyHostToDevice));
+  for (double* v : {H->x, H->r, H->p, H->q, H->lx, H->b, H->xu, H->bu, H->tmp, H->tmp2, H->ac_full})
+    CK(cudaMemset(v, 0, sizeof(double) * L));
+  CK(cudaMemset(H->ac, 0, sizeof(double) * std::max<long>(H->n_c, 1)));
+  CK(cudaMemset(H->pod_G, 0, sizeof(double) * kMaxPod * kMaxPod));
+  CK(cudaMemset(H->pod_A, 0, sizeof(double) * kMaxPod * kMaxPod));
+  H->dg.g.n = n;
+  H->dg.g.n3 = n3;
+  for (int a = 0; a < 3; ++a) { H->dg.g.cb_lo[a] = H->cb_lo[a]; H->dg.g.cb_hi[a] = H->cb_hi[a]; }
+  H->dg.g.cflags = H->cflags;
+  for (int a = 0; a < 3; ++a) { H->cg.clo[a] = lo[a]; H->cg.chi[a] = hi[a]; }
+  H->cg.n_c = (int)H->n_c;
+  H->cg.c_idx = H->cidx;
+  H->cg.inv_mc = H->invmc;
+  H->cg.brauer = H->brauer;
+  H->cg.nu = H->nu;
+  H->cg.nu0 = H->nu0; H->cg.k1 = H->k1; H->cg.k2 = H->k2; H->cg.k3 = H->k3; H->cg.h = H->h;
+  CK(cudaDeviceSynchronize());
+  return MQS_OK;
+}
+
+int ensure_pod(mqs_handle* H) {
+  if (H->pod_X[0]) return MQS_OK;
+  for (int a = 0; a < kMaxPod; ++a) {
+    RK(dalloc(H, &H->pod_X[a], H->len));
+    RK(dalloc(H, &H->pod_LX[a], H->len));
+  }
+  return MQS_OK;
+}
+
+void clear_history(mqs_handle* H) {
+  H->spe_m = 0;
+  H->pod_m = 0;
+  H->pod_next = 0;
+}
+
+int ensure_stats(mqs_handle* H, int nsteps) {
+  if (H->dstats_cap >= nsteps) return MQS_OK;
+  int cap = std::max(nsteps, 256);
+  RK(dalloc(H, &H->dstats, cap));
+  H->dstats_cap = cap;
+  return MQS_OK;
+}
+
+// conductor update for the state currently in H->ac / H->ac_full with w = x
+int conductor_step(mqs_handle* H, const double* w, double dt, cudaStream_t st) {
+  if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st));
+  else RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, true, st));
+  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st));
+  std::swap(H->ac, H->ac2);
+  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+  return MQS_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+int mqs_setup(const mqs_grid* grid, const mqs_materials* mat, const uint8_t* conductor_mask, const mqs_coil* coil,
+              const mqs_options* opts, mqs_handle** out) {
+  if (!out) return MQS_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !mat || !coil || !opts) return MQS_ERR_ARG;
+  mqs_handle* H = new (std::nothrow) mqs_handle();
+  if (!H) return MQS_ERR_OOM;
+  int rc = do_setup(H, grid, mat, conductor_mask, coil, opts);
+  if (rc != MQS_OK) {
+    fprintf(stderr, "mqs_setup: %s\n", H->err.c_str());
+    mqs_destroy(H);
+    return rc;
+  }
+  *out = H;
+  return MQS_OK;
+}
+
+int mqs_destroy(mqs_handle* H) {
+  if (!H) return MQS_OK;
+  if (H->st) cudaStreamSynchronize(H->st);
+  for (void* v : H->allocs) cudaFree(v);
+  if (H->st) cudaStreamDestroy(H->st);
+  delete H;
+  return MQS_OK;
+}
+
+int mqs_last_error(const mqs_handle* H, char* buf, size_t len) {
+  if (!H || !buf || len == 0) return MQS_ERR_ARG;
+  snprintf(buf, len, "%s", H->err.c_str());
+  return MQS_OK;
+}
+
+int mqs_layout(const mqs_handle* H, mqs_layout_info* info) {
+  if (!H || !info) return MQS_ERR_ARG;
+  info->n = H->n;
+  info->n_layout = (long)H->len;
+  info->n_c = H->n_c;
+  info->n_n = H->n_n;
+  for (int a = 0; a < 3; ++a) { info->box_lo[a] = H->cb_lo[a]; info->box_hi[a] = H->cb_hi[a]; }
+  return MQS_OK;
+}
+
+int mqs_set_dt(mqs_handle* H, double dt) {
+  if (!H) return MQS_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(H, MQS_ERR_ARG, "dt must be positive");
+  H->dt = dt;
+  return MQS_OK;
+}
+
+int mqs_get_dt(const mqs_handle* H, double* dt) {
+  if (!H || !dt) return MQS_ERR_ARG;
+  *dt = H->dt;
+  return MQS_OK;
+}
+
+int mqs_set_options(mqs_handle* H, const mqs_options* o) {
+  if (!H || !o) return MQS_ERR_ARG;
+  std::string why;
+  if (validate_options(o, why) != MQS_OK) return fail(H, MQS_ERR_ARG, why.c_str());
+  const bool reset = o->start_mode != H->opt.start_mode || o->spe_depth != H->opt.spe_depth ||
+                     o->pod_snapshots != H->opt.pod_snapshots;
+  const double dt = H->dt;
+  H->opt = *o;
+  H->dt = (o->dt > 0.0) ? o->dt : dt;
+  if (reset) clear_history(H);
+  return MQS_OK;
+}
+
+int mqs_reset_history(mqs_handle* H) {
+  if (!H) return MQS_ERR_ARG;
+  clear_history(H);
+  return MQS_OK;
+}
+
+int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
+  if (!H || nsteps < 0) return MQS_ERR_ARG;
+  if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
+  if (nsteps == 0) return MQS_OK;
+  cudaStream_t st = H->st;
+  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
+  RK(ensure_stats(H, nsteps));
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  for (int s = 0; s < nsteps; ++s) {
+    const long m = H->m + 1;
+    const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+    // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
+    rhs_current_kernel<<<1, 1, 0, st>>>(H->scal, H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz,
+                                        H->coil.waveform, H->coil.tau, t_src);
+    RK(launch_rhs(H->dg, H->ac_full, H->b, H->scal, coil, H->rhs_box, st));
+    // (a3) start vector
+    int used_small = 0;
+    RK(start_vector(H, H->b, H->x, st, &used_small));
+    // (a4) PCG
+    CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
+    RK(launch_pcg(H->dg, H->b, H->x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, H->opt.tol,
+                  H->opt.maxit, H->nblk, st));
+    // (a5) conducting update, eq. (acm)
+    RK(conductor_step(H, H->x, H->dt, st));
+    // (a6) history
+    RK(history_push(H, H->x, H->lx, st));
+    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->dstats + s);
+    H->m = m;
+    H->t = m * H->dt;
+  }
+  std::vector<mqs_step_stats> hs(nsteps);
+  int derr = 0;
+  CK(cudaMemcpyAsync(hs.data(), H->dstats, sizeof(mqs_step_stats) * nsteps, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&derr, H->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (per_step) memcpy(per_step, hs.data(), sizeof(mqs_step_stats) * nsteps);
+  if (derr != 0) return fail(H, derr, "a bounded grid barrier wait timed out");
+  for (int s = 0; s < nsteps; ++s)
+    if (hs[s].status != MQS_OK) {
+      H->err = "PCG failed in a time step";
+      return hs[s].status;
+    }
+  return MQS_OK;
+}
+
+int mqs_get_state(mqs_handle* H, double* a_c, size_t n_c, double* t, long* m) {
+  if (!H) return MQS_ERR_ARG;
+  if (a_c) {
+    if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
+    CK(cudaMemcpyAsync(a_c, H->ac, sizeof(double) * n_c, cudaMemcpyDeviceToHost, H->st));
+  }
+  CK(cudaStreamSynchronize(H->st));
+  if (t) *t = H->t;
+  if (m) *m = H->m;
+  return MQS_OK;
+}
+
+int mqs_set_state(mqs_handle* H, const double* a_c, size_t n_c, double t, long m) {
+  if (!H || !a_c) return MQS_ERR_ARG;
+  if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
+  CK(cudaMemcpyAsync(H->ac, a_c, sizeof(double) * n_c, cudaMemcpyHostToDevice, H->st));
+  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  H->t = t;
+  H->m = m;
+  return MQS_OK;
+}
+
+int mqs_get_state_dev(mqs_handle* H, double* a_c_dev, size_t n_c, void* stream) {
+  if (!H || !a_c_dev) return MQS_ERR_ARG;
+  if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
+  cudaStream_t st = stream ? (cudaStream_t)stream : H->st;
+  if (st != H->st) CK(cudaStreamSynchronize(H->st));
+  CK(cudaMemcpyAsync(a_c_dev, H->ac, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, st));
+  return MQS_OK;
+}
+
+int mqs_set_state_dev(mqs_handle* H, const double* a_c_dev, size_t n_c, void* stream) {
+  if (!H || !a_c_dev) return MQS_ERR_ARG;
+  if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
+  cudaStream_t st = stream ? (cudaStream_t)stream : H->st;
+  if (st != H->st) CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(H->ac, a_c_dev, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, H->st));
+  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  if (st != H->st) CK(cudaStreamSynchronize(H->st));
+  return MQS_OK;
+}
+
+int mqs_get_solution(mqs_handle* H, double* w) {
+  if (!H || !w) return MQS_ERR_ARG;
+  CK(cudaMemcpyAsync(w, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToHost, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  return MQS_OK;
+}
+
+int pcg_solve_dev(mqs_handle* H, const double* b_dev, double* x_dev, double tol, int maxit, mqs_pcg_info* info,
+                  void* stream) {
+  if (!H || !b_dev || !x_dev) return MQS_ERR_ARG;
+  if (!(tol > 0.0) || maxit < 1) return fail(H, MQS_ERR_ARG, "tol must be positive and maxit >= 1");
+  cudaStream_t st = stream ? (cudaStream_t)stream : H->st;
+  if (st != H->st) CK(cudaStreamSynchronize(H->st));
+  RK(mask_scale(H, b_dev, H->bu, H->h / H->nu0, st));
+  RK(mask_scale(H, x_dev, H->xu, 1.0, st));
+  RK(run_pcg(H, H->bu, H->xu, tol, maxit, st));
+  CK(cudaMemcpyAsync(x_dev, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+  return read_pcg(H, info, st);
+}
+
+int pcg_solve(mqs_handle* H, const double* b, double* x, double tol, int maxit, mqs_pcg_info* info) {
+  if (!H || !b || !x) return MQS_ERR_ARG;
+  if (!(tol > 0.0) || maxit < 1) return fail(H, MQS_ERR_ARG, "tol must be positive and maxit >= 1");
+  cudaStream_t st = H->st;
+  CK(cudaMemcpyAsync(H->tmp, b, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(H->tmp2, x, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
+  RK(mask_scale(H, H->tmp2, H->xu, 1.0, st));
+  RK(run_pcg(H, H->bu, H->xu, tol, maxit, st));
+  CK(cudaMemcpyAsync(x, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
+  return read_pcg(H, info, st);
+}
+
+int mqs_apply_kn_dev(mqs_handle* H, const double* x_dev, double* y_dev, void* stream) {
+  if (!H || !x_dev || !y_dev) return MQS_ERR_ARG;
+  cudaStream_t st = stream ? (cudaStream_t)stream : H->st;
+  if (st != H->st) CK(cudaStreamSynchronize(H->st));
+  RK(mask_scale(H, x_dev, H->tmp2, 1.0, st));
+  RK(launch_apply_L(H->dg, H->tmp2, y_dev, H->nu0 / H->h, H->full, st));
+  return MQS_OK;
+}
+
+int mqs_apply_kn(mqs_handle* H, const double* x, double* y) {
+  if (!H || !x || !y) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  CK(cudaMemcpyAsync(H->tmp, x, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
+  RK(launch_apply_L(H->dg, H->tmp2, H->tmp, H->nu0 / H->h, H->full, st));
+  CK(cudaMemcpyAsync(y, H->tmp, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int mqs_conductor_rate(mqs_handle* H, const double* a_c, const double* w, double* F) {
+  if (!H || !a_c || !w || !F) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  CK(cudaMemcpyAsync(H->cvec, a_c, sizeof(double) * H->n_c, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(H->tmp, w, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
+  CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
+  RK(launch_scatter_c(H->cg, H->cvec, H->xu, 1.0, st));
+  RK(launch_cell_nu(H->dg, H->cg, H->xu, H->tmp2, !H->any_brauer, st));
+  RK(launch_cond_update(H->dg, H->cg, H->xu, H->tmp2, 1.0, H->cvec, H->cvec2, 0.0, st));
+  CK(cudaMemcpyAsync(F, H->cvec2, sizeof(double) * H->n_c, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol, int maxit, double* lambda_max,
+                   int* iters) {
+  if (!H || !v0 || !lambda_max) return MQS_ERR_ARG;
+  if (!(pcg_tol > 0.0) || !(rtol > 0.0) || maxit < 1) return fail(H, MQS_ERR_ARG, "bad power-method settings");
+  cudaStream_t st = H->st;
+  double nv = 0.0;
+  for (long q = 0; q < H->n_c; ++q) nv += v0[q] * v0[q];
+  if (!(nv > 0.0)) return fail(H, MQS_ERR_ARG, "v0 must be nonzero");
+  std::vector<double> vn(v0, v0 + H->n_c);
+  for (double& v : vn) v /= std::sqrt(nv);
+  CK(cudaMemcpyAsync(H->cvec, vn.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->tmp, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->scal + 2, 0, sizeof(double), st));
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  double lam = 0.0, lam_old = 0.0;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
+    power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
+    RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
+    RK(launch_rhs(H->dg, H->tmp, H->bu, H->scal + 2, coil, H->rhs_box, st));
+    RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
+    // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
+    RK(launch_cell_nu(H->dg, H->cg, H->tmp, H->xu, true, st));
+    RK(launch_cond_update(H->dg, H->cg, H->tmp, H->xu, 1.0, H->cvec2, H->ac2, 0.0, st));
+    power_update_kernel<<<1, 1024, 0, st>>>((int)H->n_c, H->ac2, H->isqmc, H->cvec, H->scal + 1);
+    PcgResult pr{};
+    CK(cudaMemcpyAsync(&lam, H->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&pr, H->pres, sizeof(pr), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (pr.status != MQS_OK) return fail(H, pr.status, "PCG failed inside the power method");
+    if (it > 1 && std::fabs(lam - lam_old) < rtol * std::fabs(lam)) break;
+    lam_old = lam;
+  }
+  // the scratch a_c buffer ac2 was used; restore nothing (ac holds the state)
+  *lambda_max = lam;
+  if (iters) *iters = it > maxit ? maxit : it;
+  return MQS_OK;
+}
+
+int mqs_push_history(mqs_handle* H, const double* w) {
+  if (!H || !w) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
+  CK(cudaMemcpyAsync(H->tmp, w, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
+  RK(launch_apply_L(H->dg, H->tmp2, H->tmp, 1.0, H->full, st));
+  if (H->opt.start_mode == MQS_START_PREV)
+    CK(cudaMemcpyAsync(H->x, H->tmp2, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+  RK(history_push(H, H->tmp2, H->tmp, st));
+  CK(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int spe_start(mqs_handle* H, const double* b, double* x0, int* rank_used) {
+  if (!H || !b || !x0) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  CK(cudaMemcpyAsync(H->tmp, b, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
+  const int d = H->opt.spe_depth;
+  RK(spe_x0(vs(H->spe_D, d), vs(H->spe_LD, d), H->spe_m, H->bu, H->xu, H->len, H->opt.eps_lin, H->tspart, H->coef,
+            H->small, st));
+  SmallOut so{};
+  CK(cudaMemcpyAsync(x0, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
+  if (H->spe_m > 0) CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (rank_used) *rank_used = so.rank;
+  return MQS_OK;
+}
+
+int pod_basis(mqs_handle* H, int* k, double* sigma, double* info_ratio) {
+  if (!H) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  SmallOut so{};
+  const int np = H->opt.pod_snapshots;
+  std::vector<double> sg(kMaxVec, 0.0);
+  if (H->pod_m > 0) {
+    CK(cudaMemsetAsync(H->sigma, 0, sizeof(double) * kMaxVec, st));
+    CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
+    RK(pod_x0(vs(H->pod_X, np), H->pod_m, H->pod_G, H->pod_A, H->bu, nullptr, H->len, H->opt.eps_pod, H->tspart,
+              H->coef, H->sigma, H->small, st));
+    CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sg.data(), H->sigma, sizeof(double) * kMaxVec, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (k) *k = so.rank;
+  if (info_ratio) *info_ratio = so.info;
+  if (sigma) for (int a = 0; a < np; ++a) sigma[a] = (a < H->pod_m) ? sg[a] : 0.0;
+  return MQS_OK;
+}
+
+int pod_start(mqs_handle* H, const double* b, double* x0, int* k) {
+  if (!H || !b || !x0) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  if (H->pod_m == 0) {
+    memset(x0, 0, sizeof(double) * H->len);
+    if (k) *k = 0;
+    return MQS_OK;
+  }
+  CK(cudaMemcpyAsync(H->tmp, b, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
+  RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
+  RK(pod_x0(vs(H->pod_X, H->opt.pod_snapshots), H->pod_m, H->pod_G, H->pod_A, H->bu, H->xu, H->len,
+            H->opt.eps_pod, H->tspart, H->coef, H->sigma, H->small, st));
+  SmallOut so{};
+  CK(cudaMemcpyAsync(x0, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (k) *k = so.rank;
+  return MQS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Right-hand side assembly, stand-alone stencil application and the
+// conducting-region update of the explicit Euler step (Sec. II, eq. (acm)).
+#include <cmath>
+#include "mqs_kernels.h"
+
+namespace mqs {
+
+struct EpiApply {  // y = scale * t on n-edges, zero elsewhere
+  double* y; long long n3; double scale;
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
+    y[e] = (m & 1u) ? scale * tx : 0.0;
+    y[e + n3] = (m & 2u) ? scale * ty : 0.0;
+    y[e + 2 * n3] = (m & 4u) ? scale * tz : 0.0;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) apply_L_kernel(Geom g, const double* s, double* y, double scale, Box box) {
+  __shared__ SweepSmem sm;
+  EpiApply ep{y, g.n3, scale};
+  sweep_L(g, s, box, blockIdx.x, gridDim.x, sm, ep);
+}
+
+// coil distribution X_s of one edge (Sec. II, J_S = X_S i_S(t))
+__device__ __forceinline__ double coil_xs(const CoilGeom& c, int comp, int i, int j, int k) {
+  if (k != c.k) return 0.0;
+  if (comp == 0 && i >= c.i0 && i < c.i1) return (j == c.j0) ? 1.0 : (j == c.j1) ? -1.0 : 0.0;
+  if (comp == 1 && j >= c.j0 && j < c.j1) return (i == c.i1) ? 1.0 : (i == c.i0) ? -1.0 : 0.0;
+  return 0.0;
+}
+
+struct EpiRhs {  // b = coil_scale X_s - t on n-edges (eq. (mrhs), scaled by h/nu0)
+  double* b; long long n3; int n; double coil_scale; CoilGeom coil;
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
+    const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((long long)n * n));
+    const double t[3] = {tx, ty, tz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      b[e + c * n3] = (m >> c & 1u) ? fma(coil_scale, coil_xs(coil, c, i, j, k), -t[c]) : 0.0;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) rhs_kernel(Geom g, const double* ac, double* b,
+                                                     const double* coil_scale, CoilGeom coil, Box box) {
+  __shared__ SweepSmem sm;
+  EpiRhs ep{b, g.n3, g.n, *coil_scale, coil};
+  sweep_L(g, ac, box, blockIdx.x, gridDim.x, sm, ep);
+}
+
+static int stencil_grid(const Box& box) {
+  long long ntx = (box.hi[0] - box.lo[0] + 31) / 32, nty = (box.hi[1] - box.lo[1] + kTY - 1) / kTY;
+  long long T = ntx * nty * (box.hi[2] - box.lo[2]);
+  long long blocks = (T + 3) / 4;              // about four plane-tiles per block
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st) {
+  apply_L_kernel<<<stencil_grid(box), kBlock, 0, st>>>(dg.g, s, y, scale, box);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, const double* coil_scale, CoilGeom coil,
+               Box box, cudaStream_t st) {
+  rhs_kernel<<<stencil_grid(box), kBlock, 0, st>>>(dg.g, ac_full, b, coil_scale, coil, box);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+// ---- conducting region ------------------------------------------------------------
+__device__ __forceinline__ double lda(const double* ac, const double* w, double sw, int n, long long n3, int c,
+                                      int i, int j, int k) {
+  return fma(sw, ld(w, n, n3, c, i, j, k), ld(ac, n, n3, c, i, j, k));
+}
+// face fluxes of a = ac + sw w
+__device__ __forceinline__ double fbx(const double* ac, const double* w, double sw, int n, long long n3, int i,
+                                      int j, int k) {
+  return (lda(ac, w, sw, n, n3, 1, i, j, k) - lda(ac, w, sw, n, n3, 2, i, j, k)) +
+         (lda(ac, w, sw, n, n3, 2, i, j + 1, k) - lda(ac, w, sw, n, n3, 1, i, j, k + 1));
+}
+__device__ __forceinline__ double fby(const double* ac, const double* w, double sw, int n, long long n3, int i,
+                                      int j, int k) {
+  return (lda(ac, w, sw, n, n3, 2, i, j, k) - lda(ac, w, sw, n, n3, 0, i, j, k)) +
+         (lda(ac, w, sw, n, n3, 0, i, j, k + 1) - lda(ac, w, sw, n, n3, 2, i + 1, j, k));
+}
+__device__ __forceinline__ double fbz(const double* ac, const double* w, double sw, int n, long long n3, int i,
+                                      int j, int k) {
+  return (lda(ac, w, sw, n, n3, 0, i, j, k) - lda(ac, w, sw, n, n3, 1, i, j, k)) +
+         (lda(ac, w, sw, n, n3, 1, i + 1, j, k) - lda(ac, w, sw, n, n3, 0, i, j + 1, k));
+}
+
+__global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const double* w, int at_zero) {
+  const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1], wz = cg.chi[2] - cg.clo[2];
+  const long long ncell = (long long)wx * wy * wz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    if (!cg.brauer[q]) { cg.nu[q] = cg.nu0; continue; }
+    double B2 = 0.0;
+    if (!at_zero) {
+      const int i = cg.clo[0] + (int)(q % wx), j = cg.clo[1] + (int)((q / wx) % wy),
+                k = cg.clo[2] + (int)(q / ((long long)wx * wy));
+      const int n = g.n;
+      const long long n3 = g.n3;
+      const double sx = fbx(ac, w, 1.0, n, n3, i, j, k) + fbx(ac, w, 1.0, n, n3, i + 1, j, k);
+      const double sy = fby(ac, w, 1.0, n, n3, i, j, k) + fby(ac, w, 1.0, n, n3, i, j + 1, k);
+      const double sz = fbz(ac, w, 1.0, n, n3, i, j, k) + fbz(ac, w, 1.0, n, n3, i, j, k + 1);
+      const double s = 2.0 * cg.h * cg.h;
+      B2 = (sx * sx + sy * sy + sz * sz) / (s * s);
+    }
+    cg.nu[q] = fma(cg.k1, exp(cg.k2 * B2), cg.k3);   // Brauer nu(B) = k1 exp(k2 B^2) + k3
+  }
+}
+
+__device__ __forceinline__ double cell_nu(const CondGeom& cg, int i, int j, int k) {
+  if (i < cg.clo[0] || j < cg.clo[1] || k < cg.clo[2] || i >= cg.chi[0] || j >= cg.chi[1] || k >= cg.chi[2])
+    return cg.nu0;
+  const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1];
+  return cg.nu[(i - cg.clo[0]) + wx * ((j - cg.clo[1]) + (long long)wy * (k - cg.clo[2]))];
+}
+
+// F_e = sum over the four faces f of e of C_fe M_nu[f] (C a)_f with
+// M_nu[f] = (nu of the two cells of f) / (2h); a_c update of eq. (acm).
+__global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const double* w, double sw,
+                                   const double* a_in, double* a_out, double dt) {
+  const int n = g.n;
+  const long long n3 = g.n3;
+  const double ih2 = 0.5 / cg.h;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cg.n_c; q += gridDim.x * blockDim.x) {
+    const long long e = cg.c_idx[q];
+    const int c = (int)(e / n3);
+    const long long pos = e - c * n3;
+    const int i = (int)(pos % n), j = (int)((pos / n) % n), k = (int)(pos / ((long long)n * n));
+    double F;
+    if (c == 0) {
+      const double m1 = (cell_nu(cg, i, j, k - 1) + cell_nu(cg, i, j, k)) * ih2;        // z-face (i,j,k)
+      const double m2 = (cell_nu(cg, i, j - 1, k - 1) + cell_nu(cg, i, j - 1, k)) * ih2; // z-face (i,j-1,k)
+      const double m3 = (cell_nu(cg, i, j - 1, k) + cell_nu(cg, i, j, k)) * ih2;        // y-face (i,j,k)
+      const double m4 = (cell_nu(cg, i, j - 1, k - 1) + cell_nu(cg, i, j, k - 1)) * ih2; // y-face (i,j,k-1)
+      F = m1 * fbz(ac, w, sw, n, n3, i, j, k) - m2 * fbz(ac, w, sw, n, n3, i, j - 1, k) -
+          m3 * fby(ac, w, sw, n, n3, i, j, k) + m4 * fby(ac, w, sw, n, n3, i, j, k - 1);
+    } else if (c == 1) {
+      const double m1 = (cell_nu(cg, i - 1, j, k - 1) + cell_nu(cg, i - 1, j, k)) * ih2; // z-face (i-1,j,k)
+      const double m2 = (cell_nu(cg, i, j, k - 1) + cell_nu(cg, i, j, k)) * ih2;        // z-face (i,j,k)
+      const double m3 = (cell_nu(cg, i - 1, j, k) + cell_nu(cg, i, j, k)) * ih2;        // x-face (i,j,k)
+      const double m4 = (cell_nu(cg, i - 1, j, k - 1) + cell_nu(cg, i, j, k - 1)) * ih2; // x-face (i,j,k-1)
+      F = m1 * fbz(ac, w, sw, n, n3, i - 1, j, k) - m2 * fbz(ac, w, sw, n, n3, i, j, k) +
+          m3 * fbx(ac, w, sw, n, n3, i, j, k) - m4 * fbx(ac, w, sw, n, n3, i, j, k - 1);
+    } else {
+      const double m1 = (cell_nu(cg, i - 1, j - 1, k) + cell_nu(cg, i, j - 1, k)) * ih2; // x-face (i,j-1,k)
+      const double m2 = (cell_nu(cg, i - 1, j, k) + cell_nu(cg, i, j, k)) * ih2;        // x-face (i,j,k)
+      const double m3 = (cell_nu(cg, i, j - 1, k) + cell_nu(cg, i, j, k)) * ih2;        // y-face (i,j,k)
+      const double m4 = (cell_nu(cg, i - 1, j - 1, k) + cell_nu(cg, i - 1, j, k)) * ih2; // y-face (i-1,j,k)
+      F = m1 * fbx(ac, w, sw, n, n3, i, j - 1, k) - m2 * fbx(ac, w, sw, n, n3, i, j, k) +
+          m3 * fby(ac, w, sw, n, n3, i, j, k) - m4 * fby(ac, w, sw, n, n3, i - 1, j, k);
+    }
+    a_out[q] = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a_in[q]) : F;
+  }
+}
+
+__global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, double* ac_full, double scale) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_c; q += gridDim.x * blockDim.x)
+    ac_full[c_idx[q]] = scale * a_c[q];
+}
+
+int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
+                   cudaStream_t st) {
+  const long long ncell = (long long)(cg.chi[0] - cg.clo[0]) * (cg.chi[1] - cg.clo[1]) * (cg.chi[2] - cg.clo[2]);
+  int blocks = (int)((ncell + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  cell_nu_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, at_zero ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
+                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st) {
+  int blocks = (cg.n_c + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st) {
+  int blocks = (cg.n_c + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  scatter_c_kernel<<<blocks, 256, 0, st>>>(cg.n_c, cg.c_idx, a_c, ac_full, scale);
+  return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+}  // namespace mqs

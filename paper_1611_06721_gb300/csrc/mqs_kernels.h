@@ -1,0 +1,56 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include "mqs_internal.cuh"
+
+namespace mqs {
+
+struct PcgResult {
+  int iterations;
+  int status;
+  double relres;
+  double start_relres;
+};
+
+struct DevGeom {
+  Geom g;                 // device view (cflags points to device memory)
+};
+
+int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
+               double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
+               cudaStream_t st);
+int pcg_max_blocks(int* nblk);
+
+// y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
+int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);
+
+// b = s X_s - L ac on n-edges of `box` with s = *coil_scale (device) = the
+// coil current times h/nu0 (the scaled right-hand side of eq. (mrhs)); the
+// coil is the loop (plane_k, i0, j0, i1, j1).
+struct CoilGeom { int k, i0, j0, i1, j1; };
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, const double* coil_scale, CoilGeom coil,
+               Box box, cudaStream_t st);
+
+// Conductor region kernels (eq. (acm)).
+struct CondGeom {
+  int clo[3], chi[3];     // cell box of the conducting cells
+  int n_c;
+  const int* c_idx;       // layout index of every c-edge (compact order)
+  const double* inv_mc;   // 1 / M_c per c-edge
+  const uint8_t* brauer;  // flags over the cell box (1 = Brauer)
+  double* nu;             // reluctivity over the cell box
+  double nu0, k1, k2, k3, h;
+};
+// nu per cell of the cell box from a = ac_full + w (nonlinear cells); if
+// `at_zero` the Brauer law is evaluated at B = 0.
+int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
+                   cudaStream_t st);
+// F = (K(a) a)_c at every c-edge (a = ac_full + sign_w * w).  If dt != 0:
+// a_c_out = a_c_in - dt F / M_c, else F is written to a_c_out.
+int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
+                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st);
+// scatter compact a_c into the layout vector ac_full (c-edges only)
+int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st);
+
+
+}  // namespace mqs

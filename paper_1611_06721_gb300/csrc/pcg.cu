@@ -1,0 +1,232 @@
+// Jacobi-preconditioned CG for K_n x = b (Sec. III, eq. (mrhs)) as one
+// persistent cooperative kernel per solve.
+//
+// K_n = (nu0/h) L with the integer stencil L and diag(K_n) = 4 nu0/h on every
+// n-edge, so Jacobi-PCG on (K_n, b) produces the same iterates as CG on
+// (L, b h/nu0); the kernel runs the latter (no preconditioner multiply, no
+// stencil scaling).  Per iteration, with one grid barrier after each of the
+// two reductions of the Hestenes-Stiefel recurrences:
+//   phase A  t = L r;  q = t + beta q;  p = r + beta p;  pq = p.q
+//            (q = L p by linearity, so the stencil reads r, which is final)
+//   phase B  x += alpha p;  r -= alpha q;  rr = r.r
+// Convergence ||r|| <= tol ||b|| is confirmed on the true residual b - L x,
+// whose stencil output L x is kept for the start-vector history.
+#include <cmath>
+#include "mqs_internal.cuh"
+#include "mqs_kernels.h"
+
+namespace mqs {
+
+struct PcgArgs {
+  Geom g;
+  Box full;
+  const double* b;
+  double* x;
+  double* r;
+  double* p;
+  double* q;
+  double* lx;
+  double* part;       // 4 * 2 * nblk partial sums
+  unsigned* bar;      // barrier counter (zero at launch)
+  int* err;           // device error word (zero at launch)
+  PcgResult* out;
+  double tol2;
+  int maxit;
+  long long spin;
+};
+
+struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
+  const double* b; double* r; double* lx; long long n3;
+  double rr = 0.0, bb = 0.0;
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
+    const double t[3] = {tx, ty, tz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long idx = e + c * n3;
+      if (m >> c & 1u) {
+        const double bv = b[idx];
+        const double rv = bv - t[c];
+        r[idx] = rv; lx[idx] = t[c];
+        rr = fma(rv, rv, rr); bb = fma(bv, bv, bb);
+      } else {
+        r[idx] = 0.0; lx[idx] = 0.0;
+      }
+    }
+  }
+};
+
+struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
+  double* p; double* q; long long n3; double beta; bool first;
+  double pq = 0.0;
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double sx, double sy,
+                             double sz) {
+    const double t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long idx = e + c * n3;
+      double qn = 0.0, pn = 0.0;
+      if (m >> c & 1u) {
+        qn = first ? t[c] : fma(beta, q[idx], t[c]);
+        pn = first ? s[c] : fma(beta, p[idx], s[c]);
+        pq = fma(pn, qn, pq);
+      }
+      q[idx] = qn; p[idx] = pn;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kBlock, 1) pcg_kernel(PcgArgs a) {
+  __shared__ SweepSmem sm;
+  __shared__ double red[2 * 32];
+  __shared__ double gs[2];
+  const int nb = gridDim.x, bid = blockIdx.x;
+  unsigned nbar = 0;
+  int slot = 0;
+  const long long len = 3 * a.g.n3;
+  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
+
+  // reduction helper: block sums -> partial slots -> barrier -> global sums
+  auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
+    double v[2] = {v0, v1};
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
+    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
+    if (threadIdx.x < 32) {
+      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
+      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
+    }
+    __syncthreads();
+    s0 = gs[0]; s1 = gs[1];
+    slot ^= 1;
+    return true;
+  };
+
+  int status = MQS_OK, it = 0;
+  double rr = 0.0, bb = 0.0, start_rel = 0.0, relres = 0.0;
+  // initial residual r = b - L x0
+  {
+    EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm, ep);
+    if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
+  }
+  if (bb == 0.0) {  // zero right-hand side: x = 0 after 0 iterations
+    for (long long e = tid; e < len; e += nth) { a.x[e] = 0.0; a.r[e] = 0.0; a.lx[e] = 0.0; }
+    if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{0, MQS_OK, 0.0, 0.0};
+    return;
+  }
+  start_rel = sqrt(rr / bb);
+  bool need_true = false;
+  if (!isfinite(rr) || !isfinite(bb)) {
+    status = MQS_ERR_NAN;
+  } else if (rr > a.tol2 * bb) {
+    double beta = 0.0;
+    bool first = true;
+    int restarts = 0;
+    for (;;) {
+      double pq = 0.0, dummy;
+      {
+        EpiDirection ep{a.p, a.q, a.g.n3, beta, first};
+        sweep_L(a.g, a.r, a.full, bid, nb, sm, ep);
+        if (!reduce2(ep.pq, 0.0, pq, dummy)) return;
+      }
+      ++it;
+      if (!(pq > 0.0)) { status = isnan(pq) ? MQS_ERR_NAN : MQS_ERR_BREAKDOWN; need_true = true; break; }
+      const double alpha = rr / pq;
+      double rn = 0.0;
+      {
+        // x += alpha p, r -= alpha q over the whole layout, two double2 per thread per pass
+        double acc0 = 0.0, acc1 = 0.0;
+        const long long half = len >> 1;
+        double2* x2 = reinterpret_cast<double2*>(a.x);
+        double2* r2 = reinterpret_cast<double2*>(a.r);
+        const double2* p2 = reinterpret_cast<const double2*>(a.p);
+        const double2* q2 = reinterpret_cast<const double2*>(a.q);
+        long long e = tid;
+        for (; e + nth < half; e += 2 * nth) {
+          const double2 pa = p2[e], qa = q2[e], xa = x2[e], ra = r2[e];
+          const double2 pb = p2[e + nth], qb = q2[e + nth], xb = x2[e + nth], rb = r2[e + nth];
+          double2 xo, ro;
+          xo.x = fma(alpha, pa.x, xa.x); xo.y = fma(alpha, pa.y, xa.y);
+          ro.x = fma(-alpha, qa.x, ra.x); ro.y = fma(-alpha, qa.y, ra.y);
+          x2[e] = xo; r2[e] = ro;
+          acc0 = fma(ro.x, ro.x, acc0); acc1 = fma(ro.y, ro.y, acc1);
+          xo.x = fma(alpha, pb.x, xb.x); xo.y = fma(alpha, pb.y, xb.y);
+          ro.x = fma(-alpha, qb.x, rb.x); ro.y = fma(-alpha, qb.y, rb.y);
+          x2[e + nth] = xo; r2[e + nth] = ro;
+          acc0 = fma(ro.x, ro.x, acc0); acc1 = fma(ro.y, ro.y, acc1);
+        }
+        for (; e < half; e += nth) {
+          const double2 pa = p2[e], qa = q2[e], xa = x2[e], ra = r2[e];
+          double2 xo, ro;
+          xo.x = fma(alpha, pa.x, xa.x); xo.y = fma(alpha, pa.y, xa.y);
+          ro.x = fma(-alpha, qa.x, ra.x); ro.y = fma(-alpha, qa.y, ra.y);
+          x2[e] = xo; r2[e] = ro;
+          acc0 = fma(ro.x, ro.x, acc0); acc1 = fma(ro.y, ro.y, acc1);
+        }
+        if ((len & 1) && tid == 0) {
+          const long long t = len - 1;
+          a.x[t] = fma(alpha, a.p[t], a.x[t]);
+          const double re = fma(-alpha, a.q[t], a.r[t]);
+          a.r[t] = re;
+          acc0 = fma(re, re, acc0);
+        }
+        if (!reduce2(acc0 + acc1, 0.0, rn, dummy)) return;
+      }
+      if (!isfinite(rn)) { status = MQS_ERR_NAN; need_true = true; break; }
+      if (rn <= a.tol2 * bb) {
+        EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+        sweep_L(a.g, a.x, a.full, bid, nb, sm, ep);
+        double rt, bt;
+        if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+        if (rt <= a.tol2 * bb || restarts >= 8) {
+          relres = sqrt(rt / bb);
+          status = (rt <= a.tol2 * bb) ? MQS_OK : MQS_ERR_NOT_CONVERGED;
+          break;
+        }
+        rr = rt; first = true; beta = 0.0; ++restarts;   // restart from the true residual
+      } else {
+        beta = rn / rr; rr = rn; first = false;
+      }
+      if (it >= a.maxit) { status = MQS_ERR_NOT_CONVERGED; need_true = true; break; }
+    }
+  } else {
+    relres = start_rel;  // the start vector already satisfies the tolerance
+  }
+  if (need_true) {
+    EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm, ep);
+    double rt, bt;
+    if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+    relres = sqrt(rt / bb);
+  }
+  if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{it, status, relres, start_rel};
+}
+
+int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
+               double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
+               cudaStream_t st) {
+  PcgArgs a;
+  a.g = dg.g;
+  a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
+  a.b = b; a.x = x; a.r = r; a.p = p; a.q = q; a.lx = lx;
+  a.part = part; a.bar = bar; a.err = err; a.out = out;
+  a.tol2 = tol * tol; a.maxit = maxit;
+  a.spin = 1ll << 24;   // ~1-2 s of polling before a barrier gives up
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+int pcg_max_blocks(int* nblk) {
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel, kBlock, 0) != cudaSuccess) return MQS_ERR_CUDA;
+  if (occ < 1) return MQS_ERR_CUDA;
+  *nblk = nsm;  // one persistent block per SM
+  return MQS_OK;
+}
+
+}  // namespace mqs

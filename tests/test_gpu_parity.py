@@ -1,0 +1,263 @@
+"""GPU parity: every row of the hot path through the C ABI against the FP64
+oracle on the same seeded inputs.
+
+Tolerances: stencil / conductor rate 1e-12 relative (FP64 summation order);
+gauge-invariant solve results (K_cn w, a_c) 1e-9 per solve and 1e-8 after all
+steps at PCG relative residual 1e-10 (the bar stated for the FP64 path);
+PCG iteration counts within a few iterations (rounding decides the last one).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.stepper import START_POD, START_PREV, START_SPE, START_ZERO
+from tests.helpers import layout_to_oracle, oracle_to_layout, rel
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as p
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return p
+
+
+def make(pkg, p, **kw):
+    return pkg.Solver.from_problem(p, pkg.SolverOptions(**kw))
+
+
+def golden():
+    with open(os.path.join(HERE, "golden", "linear_block_16.json")) as f:
+        return json.load(f)
+
+
+# ---- (a4) the K_n stencil -------------------------------------------------------------
+@pytest.mark.parametrize("N", [4, 16, 35, 64])
+def test_apply_kn_matches_assembled_matrix(pkg, N):
+    p = W.scaled_nonlinear(N) if N >= 8 else W.random_problem(1, N)
+    d = O.Discretization(p)
+    s = make(pkg, p)
+    x_l = W.random_vector(N, 3 * N ** 3)
+    y = s.apply_kn(x_l)
+    x_o = layout_to_oracle(N, x_l)
+    y_o = np.zeros(d.grid.n_edges)
+    y_o[d.n_idx] = d.K_n @ x_o[d.n_idx]
+    y_ref = oracle_to_layout(N, y_o)
+    scale = 4 * p.nu0 / p.h * np.abs(x_l).max()
+    assert np.abs(y - y_ref).max() <= 1e-13 * scale
+    s.close()
+
+
+# ---- (a4) PCG ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [16, 35])
+def test_pcg_solve_matches_oracle(pkg, N):
+    p = W.scaled_nonlinear(N)
+    d = O.Discretization(p)
+    s = make(pkg, p)
+    a_c = W.random_vector(7, d.n_c) * 1e-9
+    b_n = 3.0 * d.X_s[d.n_idx] - d.K_cn.T @ a_c
+    ref = O.pcg_jacobi(d.K_n, b_n, None, d.D, tol=1e-10)
+    b_o = np.zeros(d.grid.n_edges)
+    b_o[d.n_idx] = b_n
+    x_l, info = s.pcg_solve(oracle_to_layout(N, b_o), tol=1e-10)
+    x_n = layout_to_oracle(N, x_l)[d.n_idx]
+    assert info.status == 0 and info.relres <= 1e-10
+    assert abs(info.iterations - ref.iterations) <= 3
+    assert rel(d.K_cn @ x_n, d.K_cn @ ref.x) < 1e-9
+    assert np.linalg.norm(b_n - d.K_n @ x_n) <= 1.01e-10 * np.linalg.norm(b_n)
+    s.close()
+
+
+def test_pcg_edge_cases(pkg):
+    p = W.config_linear_block()
+    d = O.Discretization(p)
+    s = make(pkg, p)
+    L = 3 * p.N ** 3
+    x, info = s.pcg_solve(np.zeros(L))                       # zero right-hand side
+    assert info.status == 0 and info.iterations == 0 and not x.any()
+    b_o = np.zeros(d.grid.n_edges)
+    b_o[d.n_idx] = d.X_s[d.n_idx]
+    b = oracle_to_layout(p.N, b_o)
+    xs, info = s.pcg_solve(b, tol=1e-12)
+    _, info2 = s.pcg_solve(b, x0=xs, tol=1e-10)              # start at the solution
+    assert info2.iterations == 0 and info2.status == 0
+    _, info3 = s.pcg_solve(b, tol=1e-10, maxit=2, allow_fail=True)
+    assert info3.status == -4                                # MQS_ERR_NOT_CONVERGED
+    bn = b.copy()
+    bn[np.flatnonzero(b)[0]] = np.nan
+    _, info4 = s.pcg_solve(bn, allow_fail=True)
+    assert info4.status == -6                                # MQS_ERR_NAN
+    # entries off the n-edges are ignored
+    junk = b.copy()
+    junk[:p.N ** 2] += 1.0                                   # Dirichlet x-edges at k = 0
+    x5, _ = s.pcg_solve(junk, tol=1e-12)
+    assert rel(d.K_cn @ layout_to_oracle(p.N, x5)[d.n_idx], d.K_cn @ layout_to_oracle(p.N, xs)[d.n_idx]) < 1e-9
+    s.close()
+
+
+# ---- (a5) conductor rate with the Brauer law ----------------------------------------------
+def test_conductor_rate_matches_oracle(pkg):
+    p = W.scaled_nonlinear(16, amplitude=2e3)
+    d = O.Discretization(p)
+    s = make(pkg, p)
+    a_c = W.random_vector(3, d.n_c) * 2e-6            # |B| up to a few tesla: strongly nonlinear
+    w_n = W.random_vector(4, d.n_n) * 2e-6
+    a_full = d.full(a_c, w_n)
+    assert d.cell_flux_density(a_full)[d.brauer].max() > 1.0
+    F_ref = d.apply_K(a_full, a_full)[d.c_idx]
+    F = s.conductor_rate(a_c, oracle_to_layout(p.N, d.full(None, w_n)))
+    assert rel(F, F_ref) < 1e-12
+    s.close()
+
+
+# ---- (a7) CFL step by the power method -------------------------------------------------------
+def test_lambda_max_matches_oracle(pkg):
+    g = golden()
+    p = W.config_linear_block()
+    s = make(pkg, p)
+    lam, it = s.lambda_max(W.power_start_vector(s.n_c))
+    assert lam == pytest.approx(g["lambda_max"], rel=1e-6)
+    s.close()
+
+
+# ---- full steps (a2-a6), 16^3 linear block, 200 steps, every start vector ---------------------
+@pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_PREV, "prev"), (START_SPE, "spe8"),
+                                       (START_POD, "pod20")])
+def test_explicit_euler_parity_linear_block(pkg, mode, name):
+    g = golden()
+    p = W.config_linear_block()
+    s = make(pkg, p, start_mode=mode, spe_depth=8, pod_snapshots=20, dt=g["dt"], tol=1e-10)
+    stats = s.mqs_step(g["steps"])
+    a_c, t, m = s.get_state()
+    ref = np.array(g["runs"][name]["a_c"])
+    assert m == g["steps"]
+    assert rel(a_c, ref) < 1e-8
+    its = np.array([st.iterations for st in stats])
+    assert abs(its.mean() - g["runs"][name]["mean_iterations"]) <= 1.0
+    assert all(st.status == 0 and st.relres <= 1e-10 for st in stats)
+    s.close()
+
+
+# ---- nonlinear iron, ragged size, step-by-step against the oracle -------------------------------
+@pytest.mark.parametrize("mode", [START_ZERO, START_SPE, START_POD])
+def test_nonlinear_parity(pkg, mode):
+    p = W.scaled_nonlinear(24, amplitude=5e4)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    steps = 25
+    ref = O.run_explicit_euler(d, dt, steps, start_mode=mode, spe_depth=4, pod_snapshots=10, tol=1e-10)
+    s = make(pkg, p, start_mode=mode, spe_depth=4, pod_snapshots=10, dt=dt, tol=1e-10)
+    stats = s.mqs_step(steps)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, ref.a_c) < 1e-8
+    w = layout_to_oracle(p.N, s.get_solution())[d.n_idx]
+    assert rel(d.K_cn @ w, d.K_cn @ ref.w) < 1e-8
+    its = np.array([st.iterations for st in stats])
+    assert np.abs(its - ref.iterations).max() <= 3
+    s.close()
+
+
+# ---- (a3, a6) start vectors as stand-alone calls ------------------------------------------------
+def _window(d, p, steps, dt, depth):
+    r = O.run_explicit_euler(d, dt, steps, start_mode=START_ZERO, tol=1e-12, spe_depth=depth,
+                             pod_snapshots=depth, history=(hist := []))
+    return r, hist
+
+
+def test_spe_start_matches_oracle(pkg):
+    p = W.config_linear_block()
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    hist = []
+    O.run_explicit_euler(d, dt, 12, start_mode=START_SPE, spe_depth=6, tol=1e-12, history=hist)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=6)
+    for w in reversed(hist):                              # oldest first
+        s.push_history(oracle_to_layout(p.N, d.full(None, w)))
+    a_c = W.random_vector(5, d.n_c) * 1e-12
+    b_n = 0.7 * d.X_s[d.n_idx] - d.K_cn.T @ a_c
+    x_ref, rank_ref = O.spe_start(d.K_n, hist, b_n)
+    x_l, rank = s.spe_start(oracle_to_layout(p.N, d.full(None, b_n)))
+    x_n = layout_to_oracle(p.N, x_l)[d.n_idx]
+    nb = np.linalg.norm(b_n)
+    r_gpu = np.linalg.norm(b_n - d.K_n @ x_n) / nb
+    r_ref = np.linalg.norm(b_n - d.K_n @ x_ref) / nb
+    assert r_gpu <= 1.5 * r_ref + 1e-12
+    assert rel(d.K_cn @ x_n, d.K_cn @ x_ref) < 1e-6
+    for w in hist:                                        # Galerkin orthogonality
+        assert abs(w @ (b_n - d.K_n @ x_n)) <= 1e-8 * np.linalg.norm(w) * nb
+    assert 1 <= rank <= 6
+    s.close()
+
+
+def test_pod_basis_matches_oracle(pkg):
+    p = W.config_linear_block()
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    hist = []
+    O.run_explicit_euler(d, dt, 15, start_mode=START_POD, pod_snapshots=12, tol=1e-12, history=hist)
+    s = make(pkg, p, start_mode=START_POD, pod_snapshots=12)
+    for w in reversed(hist):
+        s.push_history(oracle_to_layout(p.N, d.full(None, w)))
+    k, sig, info = s.pod_basis()
+    b_n = 0.3 * d.X_s[d.n_idx]
+    x_ref, k_ref, sig_ref, info_ref = O.pod_start(d.K_n, hist, b_n)
+    assert k == k_ref
+    big = sig_ref >= 1e-6 * sig_ref[0]
+    assert np.allclose(sig[:len(sig_ref)][big], sig_ref[big], rtol=1e-8)
+    # the method of snapshots resolves sigma_i only to about sqrt(eps) sigma_1,
+    # so the information ratio (a sum over all sigma_i) agrees to ~ m * 1.5e-8
+    assert info == pytest.approx(info_ref, abs=len(sig_ref) * 2e-8)
+    x_l, k2 = s.pod_start(oracle_to_layout(p.N, d.full(None, b_n)))
+    x_n = layout_to_oracle(p.N, x_l)[d.n_idx]
+    assert rel(d.K_cn @ x_n, d.K_cn @ x_ref) < 1e-6
+    s.close()
+
+
+# ---- state round trip and checkpoint/resume ----------------------------------------------------------
+def test_checkpoint_resume_is_exact(pkg):
+    g = golden()
+    p = W.config_linear_block()
+    s = make(pkg, p, start_mode=START_ZERO, dt=g["dt"])
+    s.mqs_step(10)
+    a10, t10, m10 = s.get_state()
+    s.mqs_step(5)
+    a15, _, _ = s.get_state()
+    s.set_state(a10, t10, m10)
+    s.mqs_step(5)
+    b15, _, m = s.get_state()
+    assert m == 15 and np.array_equal(a15, b15)
+    s.close()
+
+
+# ---- full-size workload (64^3 nonlinear iron), sampled against the oracle -----------------------------
+def test_full_size_nonlinear_first_steps(pkg):
+    p = W.config_nonlinear_iron()
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    steps = 2
+    ref = O.run_explicit_euler(d, dt, steps, start_mode=START_ZERO, tol=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10)
+    s.mqs_step(steps)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, ref.a_c) < 1e-8
+    # properties over a longer GPU run: SPE and zero start agree, SPE saves iterations
+    s2 = make(pkg, p, start_mode=START_ZERO, dt=dt, tol=1e-10)
+    st_spe = s.mqs_step(18)
+    st_zero = s2.mqs_step(20)
+    a1, _, _ = s.get_state()
+    a2, _, _ = s2.get_state()
+    assert rel(a1, a2) < 1e-8
+    assert np.mean([x.iterations for x in st_spe[-8:]]) < 0.5 * np.mean([x.iterations for x in st_zero[-8:]])
+    s.close()
+    s2.close()
