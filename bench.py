@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: explicit time steps per second of the semi-explicit eddy-current
+time stepper (Schur-complement ODE, explicit Euler, one Jacobi-PCG solve of
+K_n per step at relative residual 1e-10, SPE start vectors of depth 8) on the
+64^3 Brauer-iron workload (24x24x16 iron block, sigma 2e6 S/m, 40x40 coil,
+500 A at 50 Hz), FP64, one handle per GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` = time steps per second over the K timed steps
+(device time of each step by CUDA events on the library's stream, L2 flushed
+by a 256 MiB write between steps).  `e2e` = the same metric through the host
+C ABI (state in and out of pinned host memory every step, wall clock).
+With N > 1 (torchrun) every rank advances an independent replica (no data
+exchange: the single-instance path does not shard) and `value` counts the
+steps of all ranks over the slowest rank's time.  `--impl reference` times the
+FP64 CPU oracle (the correctness reference) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "explicit time steps/sec and PCG iters/step at rel-residual 1e-10; stencil HBM GB/s vs peak"
+WORKLOAD = "nonlinear-iron-64^3 (Brauer iron 24x24x16, sigma 2e6 S/m, coil 40x40 at z=32, 500 A 50 Hz)"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+FLOPS_PER_ITER = 16                                   # stencil 6 adds + 5 FMAs, per unknown
+FLOPS_PER_RESIDUAL = 9                                # stencil 6 + subtract 1 + FMA 2, per unknown
+BYTES_PER_ITER = 48                                   # x, r, p read and written once, per unknown
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------------------
+def oracle_sample(steps: int, budget_s: float):
+    """Time the FP64 oracle on the same workload (first `steps` steps, SPE
+    depth 8, tol 1e-10), stopping early once `budget_s` seconds are used."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    p = W.config_nonlinear_iron()
+    t0 = time.perf_counter()
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    setup = time.perf_counter() - t0
+    hist, a_c, its, done = [], None, [], 0
+    t1 = time.perf_counter()
+    for m in range(steps):
+        r = O.run_explicit_euler(d, dt, 1, start_mode=O.stepper.START_SPE, spe_depth=8, tol=1e-10,
+                                 a_c0=a_c, m0=m, history=hist)
+        a_c = r.a_c
+        its.append(int(r.iterations[0]))
+        done += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    el = time.perf_counter() - t1
+    return {"steps_per_s": done / el, "steps": done, "seconds": el, "setup_s": setup,
+            "iters_per_step": float(np.mean(its)), "threads": 1}
+
+
+def run_oracle_subprocess(steps, budget_s):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(steps),
+                          "--oracle-budget", str(budget_s)], capture_output=True, text=True, env=env,
+                         cwd=ROOT)
+    if res.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.lines = []
+        self.proc = None
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if gpu_id:
+                cmd += ["-i", gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def reduce_max(value, dist, device=None):
+    """Maximum of a float over ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ----------------------------------------------------------------------------------------
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    total = args.warmup + args.steps
+    budget = float(args.reference_budget)
+    s = oracle_sample(total, budget)
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": s["steps_per_s"], "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": s["steps"], "warmup": 0, "ms_per_step": 1e3 / s["steps_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": 64, "start_vector": "spe8", "tol": 1e-10},
+            "iters_per_step": s["iters_per_step"],
+            "cpu_baseline": {"value": s["steps_per_s"], "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {s['steps']} explicit Euler steps of the workload "
+                                       f"(of {total} requested, {budget:.0f} s budget), single thread, "
+                                       f"setup {s['setup_s']:.1f} s excluded"},
+            "e2e": {"value": s["steps_per_s"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, ws, local, dist):
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = W.config_nonlinear_iron()
+    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8)
+    s = pkg.Solver.from_problem(p, opts)
+    stream = torch.cuda.Stream(device=dev)
+    s.set_stream(stream.cuda_stream)
+    # setup: dt = 0.9 * 2 / lambda_max(M_c^-1 K_S) by the power method (eq. (CFL))
+    t0 = time.perf_counter()
+    lam, pit = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
+    dt = 0.9 * 2.0 / lam
+    s.set_dt(dt)
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        if args.warmup:
+            s.step(args.warmup)
+        torch.cuda.synchronize(dev)
+        barrier(dist, dev)
+        try:
+            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            gpu_id = None
+        clocks = ClockSampler(gpu_id)
+        s.timing_enable(True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        iters, statuses = [], []
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            rc, st = s.step(1, allow_fail=True)
+            ends[k].record(stream)
+            iters.append(st[0].iterations)
+            statuses.append(st[0].status)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        tm = s.timing_get()
+        s.timing_enable(False)
+        barrier(dist, dev)
+    ms_max = reduce_max(ms, dist, dev)
+    value = ws * args.steps / (ms_max * 1e-3)
+    # end to end through the host C ABI: a_c in from pinned memory, step, a_c out
+    e2e = None
+    if args.e2e_steps > 0:
+        a_host = torch.empty(s.n_c, dtype=torch.float64, pin_memory=True).numpy()
+        a_cur, t_cur, m_cur = s.get_state()
+        a_host[:] = a_cur
+        torch.cuda.synchronize(dev)
+        barrier(dist, dev)
+        t1 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.set_state(a_host, t_cur, m_cur)
+            s.step(1, allow_fail=True)
+            a_new, t_cur, m_cur = s.get_state()
+            a_host[:] = a_new
+        el = time.perf_counter() - t1
+        el_max = reduce_max(el, dist, dev)
+        e2e = {"value": ws * args.e2e_steps / el_max, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.n_c,
+               "d2h_bytes_per_step": 8 * s.n_c + 48, "steps": args.e2e_steps}
+    n_n = s.n_n
+    its = np.array(iters)
+    flops = n_n * (FLOPS_PER_ITER * its.sum() + 2 * FLOPS_PER_RESIDUAL * len(its))
+    achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
+    hbm = n_n * BYTES_PER_ITER * its.sum() / (tm["ms_pcg"] * 1e-3) / 1e9
+    peaks = measured_peaks()
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": 64, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
+                       "start_vector": "spe8", "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
+                       "l2": "flushed between timed steps by a 256 MiB write",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "iters_per_step": float(its.mean()),
+            "phases_ms_per_step": {k: tm[k] / args.steps for k in ("ms_rhs", "ms_start", "ms_pcg",
+                                                                     "ms_conductor", "ms_history")},
+            "roofline": {"bound": "alu", "kernel": "pcg_kernel", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": args.traffic,
+                         "note": "FP64 FMA=2 flop; peak derived: 152 SM x 2 FMA/clk x 2 x 2070 MHz"},
+            "stencil_hbm_view": {"algorithmic_GBps": hbm, "peak_GBps": peaks.get("hbm_gbs"),
+                                 "frac": hbm / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                                 "note": "48 B/unknown/iteration; the 64^3 PCG working set is L2-resident"},
+            "clocks": clk, "gpu_launches": int(tm["launches"]), "pcg_launches": int(tm["pcg_launches"]),
+            "failed_steps": int(sum(1 for x in statuses if x != 0)),
+            "setup": {"power_iterations": pit, "seconds": setup_s}}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            c = run_oracle_subprocess(args.cpu_steps, args.cpu_budget)
+            line["cpu_baseline"] = {"value": c["steps_per_s"], "unit": "steps/s", "cores": c["threads"],
+                                    "kind": "oracle",
+                                    "sample": f"first {c['steps']} explicit Euler steps of the same workload "
+                                              f"(SPE 8, tol 1e-10) on one host thread, setup excluded"}
+        except Exception as e:  # the GPU line is still valid without it
+            line["cpu_baseline"] = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {e}"[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def single_solve():
+    """One zero-start PCG solve of K_n w = 100 X_s on the workload (twice)."""
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    p = W.config_nonlinear_iron()
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7))
+    n = p.N
+    b = np.zeros(3 * n ** 3)
+    k = p.coil_k
+    for i in range(p.coil_i0, p.coil_i1):          # coil loop in the device layout
+        b[i + n * (p.coil_j0 + n * k)] += 100.0
+        b[i + n * (p.coil_j1 + n * k)] -= 100.0
+    for j in range(p.coil_j0, p.coil_j1):
+        b[n ** 3 + p.coil_i1 + n * (j + n * k)] += 100.0
+        b[n ** 3 + p.coil_i0 + n * (j + n * k)] -= 100.0
+    for _ in range(2):
+        x, info = s.pcg_solve(b, tol=1e-10)
+    print(json.dumps({"iterations": info.iterations, "relres": info.relres}))
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--power-maxit", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--reference-budget", type=float, default=150.0)
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
+    ap.add_argument("--single-solve", action="store_true",
+                    help="run one zero-start PCG solve of the workload twice (profiling)")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=25.0, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample, args.oracle_budget)), flush=True)
+        return
+    if args.single_solve:
+        single_solve()
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("at least 3 warm-up steps")
+    rank, ws, local, dist = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+    else:
+        run_ours(args, rank, ws, local, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
