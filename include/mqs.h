@@ -218,6 +218,28 @@ int mqs_apply_kn_dev(mqs_handle* h, const double* x_dev, double* y_dev, void* st
  * n_c doubles, w: layout vector, F: n_c doubles (host). */
 int mqs_conductor_rate(mqs_handle* h, const double* a_c, const double* w, double* F);
 
+/* mqs_set_stream: later work of the handle goes to `stream` (a
+ * cudaStream_t passed as void*; NULL = the handle's own stream).  Work already
+ * queued on the previous stream is waited for first. */
+int mqs_set_stream(mqs_handle* h, void* stream);
+
+/* Per-phase device time of mqs_step, measured with CUDA events recorded on
+ * the handle's stream around each phase of every step while timing is on:
+ * right-hand side (a2), start vector (a3), PCG (a4), conductor update (a5),
+ * history (a6).  `launches` counts every kernel the library launched inside
+ * those steps and `pcg_launches` the PCG kernels among them. */
+typedef struct {
+    double ms_rhs, ms_start, ms_pcg, ms_conductor, ms_history;
+    long   launches;
+    long   pcg_launches;
+    long   steps;
+} mqs_timing;
+
+/* on != 0 starts (and resets) the accumulation, 0 stops it. */
+int mqs_timing_enable(mqs_handle* h, int on);
+/* Waits for the stream and returns the accumulated times and counts. */
+int mqs_timing_get(mqs_handle* h, mqs_timing* out);
+
 /* History for the start vectors (Sec. III).  mqs_push_history appends a
  * solution w (layout vector, host) as the newest entry; K_n w is computed
  * by the library (during mqs_step it is a by-product of the PCG residual). */
@@ -235,6 +257,31 @@ int pod_basis(mqs_handle* h, int* k, double* sigma, double* info_ratio);
 
 /* pod_start: eq. (POD_x0) for right-hand side b (layout, host). */
 int pod_start(mqs_handle* h, const double* b, double* x0, int* k);
+
+/* mqs_pcg_solve_noalloc: the same Jacobi-PCG solve as pcg_solve_dev, as a
+ * stateless call that allocates no device memory.  (The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc, e.g. a
+ * host application whose device memory belongs to its own pool allocator, or
+ * a real-time loop where an allocation, which may synchronise the device, is
+ * not allowed.)
+ * Inputs and outputs are the caller's device pointers: cell_mask_dev (n^3
+ * bytes, nonzero = conducting cell), b_dev (layout vector, K_n units),
+ * x_dev (layout vector: start vector in, solution out; entries off n-edges
+ * are set to zero; 16-byte aligned, as cudaMalloc returns).  n, h, nu0: grid cells per axis, spacing, reluctivity.
+ * Scratch: one file-scope device array sized for n <= MQS_NOALLOC_MAX_N
+ * (about 13.4 MB), held by every GPU that loads the library until the
+ * process exits.  Larger n returns MQS_ERR_ARG (message on stderr).  The
+ * first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other host threads) race; serialise them.
+ * Blocks the host until the solve finishes; info (host) may be NULL.
+ * Returns MQS_OK or the PCG status (MQS_ERR_NOT_CONVERGED, _BREAKDOWN,
+ * _NAN, _TIMEOUT), MQS_ERR_ARG or MQS_ERR_CUDA. */
+#define MQS_NOALLOC_MAX_N 48
+int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t* cell_mask_dev,
+                          const double* b_dev, double* x_dev, double tol, int maxit,
+                          mqs_pcg_info* info, void* stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,8 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_set_options", "mqs_lambda_max", "mqs_step", "mqs_get_state", "mqs_set_state",
            "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution", "mqs_reset_history",
            "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev", "mqs_conductor_rate",
-           "mqs_push_history", "spe_start", "pod_basis", "pod_start")
+           "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
+           "mqs_timing_get", "mqs_pcg_solve_noalloc")
 
 
 class Grid(C.Structure):
@@ -57,6 +58,12 @@ class LayoutInfo(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rank", C.c_int), ("reserved", C.c_int),
                 ("relres", C.c_double), ("start_relres", C.c_double), ("pod_info", C.c_double)]
+
+
+class Timing(C.Structure):
+    _fields_ = [("ms_rhs", C.c_double), ("ms_start", C.c_double), ("ms_pcg", C.c_double),
+                ("ms_conductor", C.c_double), ("ms_history", C.c_double), ("launches", C.c_long),
+                ("pcg_launches", C.c_long), ("steps", C.c_long)]
 
 
 class PcgInfo(C.Structure):
@@ -103,6 +110,10 @@ def load():
         "spe_start": ([H, P(D), P(D), P(I)], I),
         "pod_basis": ([H, P(I), P(D), P(D)], I),
         "pod_start": ([H, P(D), P(D), P(I)], I),
+        "mqs_set_stream": ([H, V], I),
+        "mqs_timing_enable": ([H, I], I),
+        "mqs_timing_get": ([H, P(Timing)], I),
+        "mqs_pcg_solve_noalloc": ([I, D, D, V, V, V, D, I, P(PcgInfo), V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -221,6 +232,18 @@ class Solver:
         self._check(self.lib.mqs_lambda_max(self.h, _dp(v0), pcg_tol, rtol, maxit, C.byref(lam), C.byref(it)))
         return lam.value, it.value
 
+    def set_stream(self, stream):
+        """Route later work to a cudaStream_t given as an int (0 = own stream)."""
+        self._check(self.lib.mqs_set_stream(self.h, C.c_void_p(stream)))
+
+    def timing_enable(self, on=True):
+        self._check(self.lib.mqs_timing_enable(self.h, 1 if on else 0))
+
+    def timing_get(self):
+        t = Timing()
+        self._check(self.lib.mqs_timing_get(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Timing._fields_}
+
     # -- time stepping -----------------------------------------------------------------
     def step(self, nsteps, allow_fail=False):
         st = (StepStats * max(nsteps, 1))()
@@ -312,3 +335,13 @@ class Solver:
         k = C.c_int()
         self._check(self.lib.pod_start(self.h, _dp(b), _dp(x0), C.byref(k)))
         return x0, k.value
+
+
+def pcg_solve_noalloc(n, h, nu0, cell_mask, b, x, tol=1e-10, maxit=100000, stream=0):
+    """mqs_pcg_solve_noalloc on torch CUDA tensors (cell_mask uint8 n^3, b and
+    x float64 layout vectors); x is overwritten.  Returns (status, PcgInfo)."""
+    lib = load()
+    info = PcgInfo()
+    rc = lib.mqs_pcg_solve_noalloc(n, h, nu0, C.c_void_p(cell_mask.data_ptr()), C.c_void_p(b.data_ptr()),
+                                   C.c_void_p(x.data_ptr()), tol, maxit, C.byref(info), C.c_void_p(stream))
+    return rc, info

@@ -1,0 +1,133 @@
+// Jacobi-PCG solve of K_n x = b that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: a host application whose device memory
+// is owned entirely by its own pool allocator, or a real-time loop in which an
+// allocation (which may synchronise the device) is not allowed.  This entry
+// point serves them: the caller passes inputs and outputs, and every scratch
+// vector lives in one file-scope device array of fixed size, reserved by every
+// GPU that loads the library until the process exits.
+#include <cstdint>
+#include <cstdio>
+#include "mqs_kernels.h"
+
+using namespace mqs;
+
+namespace {
+
+constexpr int kMaxN = MQS_NOALLOC_MAX_N;
+constexpr long long kMaxLen = 3LL * kMaxN * kMaxN * kMaxN;          // doubles per layout vector
+constexpr long long kFlagDoubles = ((long long)kMaxN * kMaxN * kMaxN + 7) / 8;
+constexpr int kMaxBlocks = 256;
+// r, p, q, L x, scaled b | 8 x kMaxBlocks partial sums | conductor flags | barrier, error, result
+constexpr long long kOffR = 0, kOffP = kMaxLen, kOffQ = 2 * kMaxLen, kOffLx = 3 * kMaxLen, kOffB = 4 * kMaxLen;
+constexpr long long kOffPart = 5 * kMaxLen;
+constexpr long long kOffFlags = kOffPart + 8LL * kMaxBlocks;
+constexpr long long kOffTail = kOffFlags + kFlagDoubles;
+constexpr long long kScratchDoubles = kOffTail + 8;
+
+static __device__ __align__(256) double g_scratch[kScratchDoubles];
+
+// scratch address per device, filled once with that device current
+constexpr int kMaxDevices = 64;
+static double* s_addr[kMaxDevices] = {};
+
+// bit c of flags[pos] set iff edge (c; pos) touches a conducting cell
+__global__ void cell_flags_kernel(int n, const uint8_t* cell, uint8_t* flags) {
+  const long long n3 = (long long)n * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((long long)n * n));
+    auto c = [&](int a, int b, int d) -> unsigned {
+      if (a < 0 || b < 0 || d < 0 || a >= n || b >= n || d >= n) return 0u;
+      return cell[a + (long long)n * (b + (long long)n * d)] ? 1u : 0u;
+    };
+    unsigned f = 0u;
+    if (c(i, j - 1, k - 1) | c(i, j, k - 1) | c(i, j - 1, k) | c(i, j, k)) f |= 1u;
+    if (c(i - 1, j, k - 1) | c(i, j, k - 1) | c(i - 1, j, k) | c(i, j, k)) f |= 2u;
+    if (c(i - 1, j - 1, k) | c(i, j - 1, k) | c(i - 1, j, k) | c(i, j, k)) f |= 4u;
+    flags[e] = (uint8_t)f;
+  }
+}
+
+// bs = (h/nu0) b on n-edges, 0 elsewhere; x zeroed off the n-edges
+__global__ void prepare_kernel(Geom g, const double* b, double* bs, double* x, double s) {
+  const long long len = 3 * g.n3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / g.n3);
+    const long long pos = e - c * g.n3;
+    const int i = (int)(pos % g.n), j = (int)((pos / g.n) % g.n), k = (int)(pos / ((long long)g.n * g.n));
+    const bool on = (nmask(g, i, j, k) >> c) & 1u;
+    bs[e] = on ? s * b[e] : 0.0;
+    if (!on) x[e] = 0.0;
+  }
+}
+
+int scratch_address(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MQS_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return MQS_ERR_ARG;
+  if (!s_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      fprintf(stderr, "mqs_pcg_solve_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return MQS_ERR_CUDA;
+    }
+    s_addr[dev] = static_cast<double*>(p);
+  }
+  *out = s_addr[dev];
+  return MQS_OK;
+}
+
+}  // namespace
+
+extern "C" int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t* cell_mask_dev, const double* b_dev,
+                                     double* x_dev, double tol, int maxit, mqs_pcg_info* info, void* stream) {
+  if (n < 2 || n > kMaxN) {
+    fprintf(stderr, "mqs_pcg_solve_noalloc: n = %d outside [2, %d] (the static scratch size)\n", n, kMaxN);
+    return MQS_ERR_ARG;
+  }
+  if (!(h > 0.0) || !(nu0 > 0.0) || !(tol > 0.0) || maxit < 1 || !cell_mask_dev || !b_dev || !x_dev)
+    return MQS_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(x_dev) % 16 != 0 || reinterpret_cast<uintptr_t>(b_dev) % 8 != 0) {
+    fprintf(stderr, "mqs_pcg_solve_noalloc: x_dev must be 16-byte and b_dev 8-byte aligned\n");
+    return MQS_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc != MQS_OK) return rc;
+  int nblk = 0;
+  rc = pcg_max_blocks(&nblk);
+  if (rc != MQS_OK) return rc;
+  if (nblk > kMaxBlocks) nblk = kMaxBlocks;
+  uint8_t* flags = reinterpret_cast<uint8_t*>(base + kOffFlags);
+  unsigned* bar = reinterpret_cast<unsigned*>(base + kOffTail);
+  int* err = reinterpret_cast<int*>(base + kOffTail + 1);
+  PcgResult* res = reinterpret_cast<PcgResult*>(base + kOffTail + 2);
+  DevGeom dg{};
+  dg.g.n = n;
+  dg.g.n3 = (long long)n * n * n;
+  for (int a = 0; a < 3; ++a) { dg.g.cb_lo[a] = 0; dg.g.cb_hi[a] = n; }
+  dg.g.cflags = flags;
+  const int eb = 2 * 152;
+  cell_flags_kernel<<<eb, 256, 0, st>>>(n, cell_mask_dev, flags);
+  prepare_kernel<<<eb, 256, 0, st>>>(dg.g, b_dev, base + kOffB, x_dev, h / nu0);
+  if (cudaGetLastError() != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MQS_ERR_CUDA;
+  rc = launch_pcg(dg, base + kOffB, x_dev, base + kOffR, base + kOffP, base + kOffQ, base + kOffLx,
+                  base + kOffPart, bar, err, res, tol, maxit, nblk, st);
+  if (rc != MQS_OK) return rc;
+  PcgResult pr{};
+  int derr = 0;
+  if (cudaMemcpyAsync(&pr, res, sizeof(pr), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaMemcpyAsync(&derr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MQS_ERR_CUDA;
+  if (info) {
+    info->iterations = pr.iterations;
+    info->status = pr.status;
+    info->relres = pr.relres;
+    info->start_relres = pr.start_relres;
+  }
+  if (derr != 0) return derr;
+  return pr.status;
+}
