@@ -50,6 +50,12 @@ struct mqs_handle {
   SmallOut* small = nullptr;
   mqs_step_stats* dstats = nullptr;
   int dstats_cap = 0;
+  cudaStream_t own_st = nullptr;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  long launches = 0, pcg_launches = 0, tsteps = 0;
   DevGeom dg{};
   CondGeom cg{};
 };
@@ -232,6 +238,27 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
   return MQS_OK;
 }
 
+// kernels launched by start_vector / history_push for the current state
+long start_launches(const mqs_handle* H) {
+  switch (H->opt.start_mode) {
+    case MQS_START_SPE: {
+      const int m = H->spe_m;  // value before this step's push
+      return m == 0 ? 0 : (m > 8 ? 5 : 3);
+    }
+    case MQS_START_POD:
+      return H->pod_m == 0 ? 0 : (H->pod_m + 7) / 8 + 2;
+    default:
+      return 0;
+  }
+}
+long history_launches(const mqs_handle* H) {
+  switch (H->opt.start_mode) {
+    case MQS_START_SPE: return 1;
+    case MQS_START_POD: return (H->pod_m + 7) / 8 + 1;   // after the push
+    default: return 0;
+  }
+}
+
 int validate_options(const mqs_options* o, std::string& why) {
   if (!(o->tol > 0.0) || o->tol >= 1.0) { why = "tol must lie in (0, 1)"; return MQS_ERR_ARG; }
   if (o->maxit < 1) { why = "maxit must be positive"; return MQS_ERR_ARG; }
@@ -350,6 +377,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   H->full = Box{{0, 0, 0}, {n, n, n}};
   // device
   CK(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking));
+  H->own_st = H->st;
   RK(pcg_max_blocks(&H->nblk));
   const size_t L = (size_t)H->len;
   const long ccells = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
@@ -406,6 +434,21 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   H->cg.nu0 = H->nu0; H->cg.k1 = H->k1; H->cg.k2 = H->k2; H->cg.k3 = H->k3; H->cg.h = H->h;
   CK(cudaDeviceSynchronize());
   return MQS_OK;
+}
+
+// events for the per-phase timing (pool reused across steps)
+cudaEvent_t next_event(mqs_handle* H) {
+  if (H->ev_used == H->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    H->ev_pool.push_back(e);
+  }
+  return H->ev_pool[H->ev_used++];
+}
+void mark(mqs_handle* H) {
+  if (!H->timing) return;
+  cudaEvent_t e = next_event(H);
+  if (e) cudaEventRecord(e, H->st);
 }
 
 int ensure_pod(mqs_handle* H) {
@@ -467,7 +510,8 @@ int mqs_destroy(mqs_handle* H) {
   if (!H) return MQS_OK;
   if (H->st) cudaStreamSynchronize(H->st);
   for (void* v : H->allocs) cudaFree(v);
-  if (H->st) cudaStreamDestroy(H->st);
+  for (cudaEvent_t e : H->ev_pool) cudaEventDestroy(e);
+  if (H->own_st) cudaStreamDestroy(H->own_st);
   delete H;
   return MQS_OK;
 }
@@ -531,22 +575,36 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
   for (int s = 0; s < nsteps; ++s) {
     const long m = H->m + 1;
     const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+    long nl = 0;
+    mark(H);
     // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
     rhs_current_kernel<<<1, 1, 0, st>>>(H->scal, H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz,
                                         H->coil.waveform, H->coil.tau, t_src);
     RK(launch_rhs(H->dg, H->ac_full, H->b, H->scal, coil, H->rhs_box, st));
+    nl += 2;
+    mark(H);
     // (a3) start vector
     int used_small = 0;
     RK(start_vector(H, H->b, H->x, st, &used_small));
+    nl += start_launches(H);
+    mark(H);
     // (a4) PCG
     CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
     RK(launch_pcg(H->dg, H->b, H->x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, H->opt.tol,
                   H->opt.maxit, H->nblk, st));
+    nl += 1;
+    mark(H);
     // (a5) conducting update, eq. (acm)
     RK(conductor_step(H, H->x, H->dt, st));
+    nl += 3;
+    mark(H);
     // (a6) history
     RK(history_push(H, H->x, H->lx, st));
+    nl += history_launches(H);
     record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->dstats + s);
+    nl += 1;
+    mark(H);
+    if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
     H->m = m;
     H->t = m * H->dt;
   }
@@ -715,6 +773,43 @@ int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol,
   // the scratch a_c buffer ac2 was used; restore nothing (ac holds the state)
   *lambda_max = lam;
   if (iters) *iters = it > maxit ? maxit : it;
+  return MQS_OK;
+}
+
+int mqs_set_stream(mqs_handle* H, void* stream) {
+  if (!H) return MQS_ERR_ARG;
+  cudaStream_t ns = stream ? (cudaStream_t)stream : H->own_st;
+  if (ns != H->st) {
+    CK(cudaStreamSynchronize(H->st));
+    H->st = ns;
+  }
+  return MQS_OK;
+}
+
+int mqs_timing_enable(mqs_handle* H, int on) {
+  if (!H) return MQS_ERR_ARG;
+  CK(cudaStreamSynchronize(H->st));
+  H->timing = on != 0;
+  if (on) { H->ev_used = 0; H->launches = 0; H->pcg_launches = 0; H->tsteps = 0; }
+  return MQS_OK;
+}
+
+int mqs_timing_get(mqs_handle* H, mqs_timing* out) {
+  if (!H || !out) return MQS_ERR_ARG;
+  CK(cudaStreamSynchronize(H->st));
+  double acc[5] = {0, 0, 0, 0, 0};
+  // six marks per step: phases between consecutive marks
+  for (size_t s = 0; s + 6 <= H->ev_used; s += 6)
+    for (int ph = 0; ph < 5; ++ph) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, H->ev_pool[s + ph], H->ev_pool[s + ph + 1]));
+      acc[ph] += ms;
+    }
+  out->ms_rhs = acc[0]; out->ms_start = acc[1]; out->ms_pcg = acc[2]; out->ms_conductor = acc[3];
+  out->ms_history = acc[4];
+  out->launches = H->launches;
+  out->pcg_launches = H->pcg_launches;
+  out->steps = H->tsteps;
   return MQS_OK;
 }
 

@@ -7,6 +7,7 @@ namespace mqs {
 
 struct EpiApply {  // y = scale * t on n-edges, zero elsewhere
   double* y; long long n3; double scale;
+  __device__ void prefetch(long long) {}
   __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
     y[e] = (m & 1u) ? scale * tx : 0.0;
     y[e + n3] = (m & 2u) ? scale * ty : 0.0;
@@ -30,6 +31,7 @@ __device__ __forceinline__ double coil_xs(const CoilGeom& c, int comp, int i, in
 
 struct EpiRhs {  // b = coil_scale X_s - t on n-edges (eq. (mrhs), scaled by h/nu0)
   double* b; long long n3; int n; double coil_scale; CoilGeom coil;
+  __device__ void prefetch(long long) {}
   __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
     const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((long long)n * n));
     const double t[3] = {tx, ty, tz};

@@ -23,10 +23,13 @@
 
 namespace mqs {
 
-constexpr int kTY = 8;                  // row warps per stencil block
-constexpr int kWarps = kTY + 1;         // + one warp for the j0-1 halo row
-constexpr int kBlock = 32 * kWarps;     // 288 threads
+constexpr int kTY = 4;                  // row warps per stencil group (tile 32 x kTY)
+constexpr int kGroupWarps = kTY + 1;    // + one warp for the j0-1 halo row
+constexpr int kGroups = 2;              // independent groups per block (own named barrier)
+constexpr int kWarps = kGroups * kGroupWarps;
+constexpr int kBlock = 32 * kWarps;     // 320 threads
 constexpr int kMaxSeg = 32;             // planes per segment (x halo: one per lane)
+constexpr int kPcgBlocksPerSM = 1;      // co-resident PCG blocks per SM
 
 struct Box { int lo[3]; int hi[3]; };
 
@@ -63,51 +66,49 @@ __device__ __forceinline__ double ld(const double* __restrict__ v, int n, long l
   return v[c * n3 + pidx(n, i, j, k)];
 }
 
+struct SweepGroupSmem {
+  double fz[2][kGroupWarps][32];
+  double fx[2][kGroupWarps][32];
+  double hz[2][kTY];                    // x halo: bz, by at (i0 - 1, j0 + row)
+  double hy[2][kTY];
+};
 struct SweepSmem {
-  double fz[2][kWarps][32];
-  double fx[2][kWarps][32];
+  SweepGroupSmem g[kGroups];
 };
 
-// Face fluxes bz, by at (i, j, k) (used for the x halo).
-__device__ __forceinline__ void flux_zy(const double* __restrict__ s, int n, long long n3, int i, int j,
-                                        int k, double& bz, double& by) {
-  double x0 = ld(s, n, n3, 0, i, j, k), y0 = ld(s, n, n3, 1, i, j, k), z0 = ld(s, n, n3, 2, i, j, k);
-  double yi = ld(s, n, n3, 1, i + 1, j, k), zi = ld(s, n, n3, 2, i + 1, j, k);
-  double xj = ld(s, n, n3, 0, i, j + 1, k), xk = ld(s, n, n3, 0, i, j, k + 1);
-  bz = (x0 - y0) + (yi - xj);
-  by = (z0 - x0) + (xk - zi);
-}
-
-// Face fluxes bz, bx at (i, j, k) (used for the y halo row).
-__device__ __forceinline__ void flux_zx(const double* __restrict__ s, int n, long long n3, int i, int j,
-                                        int k, double& bz, double& bx) {
-  double x0 = ld(s, n, n3, 0, i, j, k), y0 = ld(s, n, n3, 1, i, j, k), z0 = ld(s, n, n3, 2, i, j, k);
-  double yi = ld(s, n, n3, 1, i + 1, j, k), xj = ld(s, n, n3, 0, i, j + 1, k);
-  double zj = ld(s, n, n3, 2, i, j + 1, k), yk = ld(s, n, n3, 1, i, j, k + 1);
-  bz = (x0 - y0) + (yi - xj);
-  bx = (y0 - z0) + (zj - yk);
+// barrier over the kGroupWarps warps of stencil group `grp` (ids 1.. ; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kGroupWarps * 32) : "memory");
 }
 
 // Applies t = L s over the positions of `box`, calling
 //   epi(e, mask, tx, ty, tz, sx, sy, sz)
-// once per position (e = i + n(j + n k); mask from nmask; t unmasked; s the
+// once per position (after epi.prefetch(e), which may start its loads early) (e = i + n(j + n k); mask from nmask; t unmasked; s the
 // source values at the position).  Work is split into plane-tiles of 32 x kTY
-// positions; part `part` of `nparts` takes a contiguous range of them and
-// marches each tile column along z so every face flux is formed once (plus
-// one halo row, one halo column and one warm-up plane per segment).
+// positions; each of the kGroups warp groups of the block is one part (of
+// nparts * kGroups), takes a contiguous range of plane-tiles and marches each
+// tile column along z so every face flux is formed once (plus one halo row,
+// one halo column and one warm-up plane per segment).  Groups synchronise on
+// their own named barrier, so one group's plane step never waits for the other.  Index
+// arithmetic is 32-bit and incremental along the march (3 n^3 < 2^31 for
+// n <= 800); bounds tests are hoisted out of the plane loop.
 // Must be called by all kBlock threads of the block.
 template <class Epi>
 __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& box, int part, int nparts,
                         SweepSmem& sm, Epi& epi) {
   const int n = g.n;
-  const long long n3 = g.n3;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n2 = n * n;
+  const int n3 = (int)g.n3;
+  const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
+  SweepGroupSmem& sg = sm.g[grp];
   const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
   const long long T = (long long)ntx * nty * nz;
-  long long u = T * part / nparts;
-  const long long u1 = T * (part + 1) / nparts;
+  const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
+  long long u = T * gp / gn;
+  const long long u1 = T * (gp + 1) / gn;
+  const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
   while (u < u1) {
     const long long tc = u / nz;
     const int ka = (int)(u % nz);
@@ -119,63 +120,129 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
     const int j0 = box.lo[1] + (int)(tc / ntx) * kTY;
     const int ks = box.lo[2] + ka, ke = ks + len;
     const int i = i0 + lane;
-    __syncthreads();  // smem reuse across segments
+    group_sync(grp);  // smem reuse across segments
     if (w < kTY) {
       const int j = j0 + w;
       const bool act = (i < box.hi[0]) && (j < box.hi[1]);
       const bool col = (i < n) && (j < n);
-      // x halo (i0 - 1, j, ks + lane) for the whole segment, one plane per lane
-      double hz = 0.0, hy = 0.0;
-      if (i0 >= 1 && j < n && lane < len) flux_zy(s, n, n3, i0 - 1, j, ks + lane, hz, hy);
-      // own column values at plane ks - 1 (warm-up) or ks
-      double x0 = 0.0, y0 = 0.0, z0 = 0.0, bxm = 0.0, bym = 0.0;
-      int k = ks - 1;
-      if (k >= 0 && col) {
-        x0 = ld(s, n, n3, 0, i, j, k); y0 = ld(s, n, n3, 1, i, j, k); z0 = ld(s, n, n3, 2, i, j, k);
-        double zi = ld(s, n, n3, 2, i + 1, j, k), zj = ld(s, n, n3, 2, i, j + 1, k);
-        double xk = ld(s, n, n3, 0, i, j, k + 1), yk = ld(s, n, n3, 1, i, j, k + 1);
-        bxm = (y0 - z0) + (zj - yk);
-        bym = (z0 - x0) + (xk - zi);
+      const bool vi1 = col && (i + 1 < n), vj1 = col && (j + 1 < n);
+      // column part of the n-edge mask: x needs j,k > 0; y needs i,k > 0; z needs i,j > 0
+      const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
+      const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
+      const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
+      const double* __restrict__ sx_ = s;
+      const double* __restrict__ sy_ = s + n3;
+      const double* __restrict__ sz_ = s + 2 * n3;
+      int o = col ? i + n * (j + n * ks) : 0;     // position of plane ks
+      // all loads of the segment start issued together: warm-up plane ks - 1,
+      // plane ks (own, x+1 and y+1 neighbours) and own values of plane ks + 1
+      const bool wu = (ks >= 1) && col;
+      const int om = o - n2;
+      const double xm = wu ? sx_[om] : 0.0, ym = wu ? sy_[om] : 0.0, zm = wu ? sz_[om] : 0.0;
+      const double zim = (wu && vi1) ? sz_[om + 1] : 0.0, zjm = (wu && vj1) ? sz_[om + n] : 0.0;
+      double x0 = 0.0, y0 = 0.0, z0 = 0.0;
+      double yi = 0.0, zi = 0.0, xj = 0.0, zj = 0.0, xk = 0.0, yk = 0.0, zk = 0.0;
+      if (col) {
+        x0 = sx_[o]; y0 = sy_[o]; z0 = sz_[o];
+        if (vi1) { yi = sy_[o + 1]; zi = sz_[o + 1]; }
+        if (vj1) { xj = sx_[o + n]; zj = sz_[o + n]; }
+        if (ks + 1 < n) { xk = sx_[o + n2]; yk = sy_[o + n2]; zk = sz_[o + n2]; }
       }
-      if (col) { x0 = ld(s, n, n3, 0, i, j, ks); y0 = ld(s, n, n3, 1, i, j, ks); z0 = ld(s, n, n3, 2, i, j, ks); }
+      if (act) epi.prefetch(o);
+      // warm-up fluxes bx, by at plane ks - 1 (zero when ks = 0: unused there)
+      double bxm = 0.0, bym = 0.0;
+      if (wu) {
+        bxm = (ym - zm) + (zjm - y0);
+        bym = (zm - xm) + (x0 - zim);
+      }
       int buf = 0;
-      for (k = ks; k < ke; ++k) {
-        double bx = 0.0, by = 0.0, bz = 0.0, xk = 0.0, yk = 0.0, zk = 0.0;
+      for (int k = ks; k < ke; ++k, o += n2) {
+        // issue the next plane's loads first
+        double nyi = 0.0, nzi = 0.0, nxj = 0.0, nzj = 0.0, nxk = 0.0, nyk = 0.0, nzk = 0.0;
+        const int o1 = o + n2;
+        if (col && k + 1 < ke) {
+          if (vi1) { nyi = sy_[o1 + 1]; nzi = sz_[o1 + 1]; }
+          if (vj1) { nxj = sx_[o1 + n]; nzj = sz_[o1 + n]; }
+          if (k + 2 < n) { nxk = sx_[o1 + n2]; nyk = sy_[o1 + n2]; nzk = sz_[o1 + n2]; }
+        }
+        double bx = 0.0, by = 0.0, bz = 0.0;
         if (col) {
-          const double yi = ld(s, n, n3, 1, i + 1, j, k), zi = ld(s, n, n3, 2, i + 1, j, k);
-          const double xj = ld(s, n, n3, 0, i, j + 1, k), zj = ld(s, n, n3, 2, i, j + 1, k);
-          xk = ld(s, n, n3, 0, i, j, k + 1); yk = ld(s, n, n3, 1, i, j, k + 1); zk = ld(s, n, n3, 2, i, j, k + 1);
           bx = (y0 - z0) + (zj - yk);
           by = (z0 - x0) + (xk - zi);
           bz = (x0 - y0) + (yi - xj);
         }
-        sm.fz[buf][w + 1][lane] = bz;
-        sm.fx[buf][w + 1][lane] = bx;
-        __syncthreads();
+        sg.fz[buf][w + 1][lane] = bz;
+        sg.fx[buf][w + 1][lane] = bx;
+        group_sync(grp);
         double bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
-        const double hzk = __shfl_sync(0xffffffffu, hz, k - ks), hyk = __shfl_sync(0xffffffffu, hy, k - ks);
-        if (lane == 0) { bzi = hzk; byi = hyk; }
-        const double bzj = sm.fz[buf][w][lane], bxj = sm.fx[buf][w][lane];
+        if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
+        const double bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {
           const double tx = (bz - bzj) + (bym - by);
           const double ty = (bzi - bz) + (bx - bxm);
           const double tz = (bxj - bx) + (by - byi);
-          epi(pidx(n, i, j, k), nmask(g, i, j, k), tx, ty, tz, x0, y0, z0);
+          unsigned m = mcol & (k > 0 ? 7u : 4u);
+          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
+          epi(o, m, tx, ty, tz, x0, y0, z0);
+          if (k + 1 < ke) epi.prefetch(o1);
         }
         bxm = bx; bym = by;
         x0 = xk; y0 = yk; z0 = zk;
+        yi = nyi; zi = nzi; xj = nxj; zj = nzj; xk = nxk; yk = nyk; zk = nzk;
         buf ^= 1;
       }
     } else {
-      // halo row j0 - 1: bz and bx of every plane of the segment
+      // halo warp: per plane, bz and bx of row j0 - 1 (all lanes) and the x halo
+      // bz, by at (i0 - 1, j0 + r) for rows r < kTY (lanes r); the next plane's
+      // loads are issued before this plane's arithmetic.
       const int jh = j0 - 1;
+      const bool hrow = (jh >= 0) && (i < n);
+      const int jr = j0 + lane;
+      const bool hcol = (i0 >= 1) && (lane < kTY) && (jr < n);
+      const long long nn3 = g.n3;
+      double a[7], c[8];
+      auto load_row = [&](int k, double* v) {
+        v[0] = ld(s, n, nn3, 0, i, jh, k); v[1] = ld(s, n, nn3, 1, i, jh, k); v[2] = ld(s, n, nn3, 2, i, jh, k);
+        v[3] = ld(s, n, nn3, 1, i + 1, jh, k); v[4] = ld(s, n, nn3, 0, i, jh + 1, k);
+        v[5] = ld(s, n, nn3, 2, i, jh + 1, k); v[6] = ld(s, n, nn3, 1, i, jh, k + 1);
+      };
+      auto load_col = [&](int k, double* v) {
+        v[0] = ld(s, n, nn3, 0, i0 - 1, jr, k); v[1] = ld(s, n, nn3, 1, i0, jr, k);
+        v[2] = ld(s, n, nn3, 0, i0 - 1, jr + 1, k); v[3] = ld(s, n, nn3, 1, i0 - 1, jr, k);
+        v[4] = ld(s, n, nn3, 2, i0 - 1, jr, k); v[5] = ld(s, n, nn3, 0, i0 - 1, jr, k + 1);
+        v[6] = ld(s, n, nn3, 2, i0, jr, k);
+        v[7] = 0.0;
+      };
+#pragma unroll
+      for (int q = 0; q < 7; ++q) a[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c[q] = 0.0;
+      if (hrow) load_row(ks, a);
+      if (hcol) load_col(ks, c);
       int buf = 0;
       for (int k = ks; k < ke; ++k) {
-        double bz = 0.0, bx = 0.0;
-        if (jh >= 0 && i < n) flux_zx(s, n, n3, i, jh, k, bz, bx);
-        sm.fz[buf][0][lane] = bz;
-        sm.fx[buf][0][lane] = bx;
-        __syncthreads();
+        double na[7], nc[8];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) na[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) nc[q] = 0.0;
+        if (k + 1 < ke) {
+          if (hrow) load_row(k + 1, na);
+          if (hcol) load_col(k + 1, nc);
+        }
+        // bz = x + y(i+1) - x(j+1) - y ; bx = y + z(j+1) - y(k+1) - z
+        sg.fz[buf][0][lane] = hrow ? (a[0] - a[1]) + (a[3] - a[4]) : 0.0;
+        sg.fx[buf][0][lane] = hrow ? (a[1] - a[2]) + (a[5] - a[6]) : 0.0;
+        if (lane < kTY) {
+          // bz = x + y(i0) - x(j+1) - y ; by = z + x(k+1) - z(i0) - x
+          sg.hz[buf][lane] = hcol ? (c[0] - c[3]) + (c[1] - c[2]) : 0.0;
+          sg.hy[buf][lane] = hcol ? (c[4] - c[0]) + (c[5] - c[6]) : 0.0;
+        }
+        group_sync(grp);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) a[q] = na[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c[q] = nc[q];
         buf ^= 1;
       }
     }
@@ -231,22 +298,21 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 }
 
 // All blocks of a co-resident grid meet here; `target` = gridDim.x * (number
-// of barriers passed so far, this one included).  A wait longer than `spin`
-// polls records MQS_ERR_TIMEOUT in *err and returns false.
+// of barriers passed so far, this one included).  Thread 0 publishes the
+// block's prior writes with a release-add (ordered after the CTA barrier) and
+// polls with acquire loads; a wait longer than `spin` polls records
+// MQS_ERR_TIMEOUT in *err and returns false (the block then leaves the kernel;
+// the other blocks time out at their next barrier).
 __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, long long spin, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    __threadfence();
     red_release_add(ctr, 1u);
     long long polls = 0;
     while (ld_acquire(ctr) < target) {
       if (++polls > spin) { atomicExch(err, MQS_ERR_TIMEOUT); ok = 0; break; }
-      __nanosleep(20);
     }
-    __threadfence();
-    if (ok && *((volatile int*)err) != 0) ok = 0;
   }
   __syncthreads();
   return ok != 0;

@@ -24,18 +24,43 @@ namespace mqs {
 constexpr int kTS = 256;        // threads of the tall-skinny kernels
 
 // ---- difference table push ---------------------------------------------------------
-__global__ void diff_push_kernel(MutVecSet D, MutVecSet LD, const double* w, const double* lw, int m_old, int m_new,
-                                 long long len) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x) {
+// All old entries of an element are loaded before any is overwritten (the
+// table columns are distinct arrays, but the compiler cannot know it), two
+// elements per thread per pass as double2.
+template <int MAXD>
+__global__ void __launch_bounds__(kTS) diff_push_kernel(MutVecSet D, MutVecSet LD, const double* __restrict__ w,
+                                                       const double* __restrict__ lw, int m_old, int m_new,
+                                                       long long len) {
+  const long long half = len >> 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < half; e += stride) {
+    double2 od[MAXD], ol[MAXD];
+#pragma unroll
+    for (int p = 0; p < MAXD; ++p)
+      if (p < m_old) {
+        od[p] = reinterpret_cast<const double2*>(D.v[p])[e];
+        ol[p] = reinterpret_cast<const double2*>(LD.v[p])[e];
+      }
+    double2 t = reinterpret_cast<const double2*>(w)[e], tl = reinterpret_cast<const double2*>(lw)[e];
+#pragma unroll
+    for (int p = 0; p < MAXD; ++p)
+      if (p < m_new) {
+        reinterpret_cast<double2*>(D.v[p])[e] = t;
+        reinterpret_cast<double2*>(LD.v[p])[e] = tl;
+        if (p < m_old) {
+          t.x -= od[p].x; t.y -= od[p].y;
+          tl.x -= ol[p].x; tl.y -= ol[p].y;
+        }
+      }
+  }
+  if ((len & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long e = len - 1;
+    double od[MAXD], ol[MAXD];
+    for (int p = 0; p < m_old && p < MAXD; ++p) { od[p] = D.v[p][e]; ol[p] = LD.v[p][e]; }
     double t = w[e], tl = lw[e];
-    for (int p = 0; p < m_new; ++p) {
-      const double o = (p < m_old) ? D.v[p][e] : 0.0;
-      const double ol = (p < m_old) ? LD.v[p][e] : 0.0;
-      D.v[p][e] = t;
-      LD.v[p][e] = tl;
-      t -= o;
-      tl -= ol;
+    for (int p = 0; p < m_new && p < MAXD; ++p) {
+      D.v[p][e] = t; LD.v[p][e] = tl;
+      if (p < m_old) { t -= od[p]; tl -= ol[p]; }
     }
   }
 }
@@ -109,11 +134,25 @@ __global__ void lincomb_kernel(VecSet V, const double* coef, int m, long long le
 }
 
 // ---- small dense kernels (one block) ----------------------------------------------------
-// fixed-order sum over blocks of one partial slot
+// fixed-order sum over blocks of one partial slot (serial; small callers)
 __device__ double sum_part(const double* part, int nblk, int slot) {
   double s = 0.0;
   for (int q = 0; q < nblk; ++q) s += part[(size_t)q * kTileSlots + slot];
   return s;
+}
+
+// out[t] = sum over blocks of partial slot slots[t], t < ns: one warp per
+// slot, lanes strided over the blocks, then a fixed shuffle tree.
+__device__ void sum_parts_warp(const double* part, int nblk, const int* tiles, const int* slots, int ns,
+                               double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = w; t < ns; t += nw) {
+    const double* pt = part + (size_t)tiles[t] * nblk * kTileSlots;
+    double s = 0.0;
+    for (int q = lane; q < nblk; q += 32) s += pt[(size_t)q * kTileSlots + slots[t]];
+    s = warp_sum(s);
+    if (lane == 0) out[t] = s;
+  }
 }
 
 // Pivoted (in order) Cholesky of the symmetric m x m matrix H (row-major in
@@ -182,19 +221,34 @@ __device__ int chol_drop_solve(double* H, double* g, double* y, int m, double dr
 __global__ void spe_solve_kernel(const double* part, int nblk, int m, double drop2, double* coef,
                                  SmallOut* out) {
   __shared__ double H[kMaxSpe * kMaxSpe], Ls[kMaxSpe * kMaxSpe], g[kMaxSpe], y[kMaxSpe];
+  __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
+  __shared__ int tiles[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe], slots[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
   __shared__ int keep[kMaxSpe];
-  // tiles: 0 = (0,0) diag [+ g rows 0..7]; 1 = (0,1) off-diag; 2 = (1,1) diag [+ g rows 8..15]
+  // entries (q, p), q >= p, live in tile 0 = rows/cols 0..7, tile 1 = (p < 8 <= q),
+  // tile 2 = 8..15; g (D^T b) rows 0..7 in tile 0 and 8..15 in tile 2
+  const int npair = m * (m + 1) / 2;
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int qq = 0; qq < m; ++qq)
+      for (int pp = 0; pp <= qq; ++pp, ++t) {
+        if (qq < 8) { tiles[t] = 0; slots[t] = pp * 8 + qq; }
+        else if (pp < 8) { tiles[t] = 1; slots[t] = pp * 8 + (qq - 8); }
+        else { tiles[t] = 2; slots[t] = (pp - 8) * 8 + (qq - 8); }
+      }
+    for (int p = 0; p < m; ++p, ++t) {
+      tiles[t] = (p < 8) ? 0 : 2;
+      slots[t] = 64 + (p % 8);
+    }
+  }
+  __syncthreads();
+  sum_parts_warp(part, nblk, tiles, slots, npair + m, vals);
+  __syncthreads();
   for (int s = threadIdx.x; s < m * m; s += blockDim.x) {
     const int p = s / m, q = s % m;
     const int pp = p < q ? p : q, qq = p < q ? q : p;
-    int tile, slot;
-    if (qq < 8) { tile = 0; slot = pp * 8 + qq; }
-    else if (pp < 8) { tile = 1; slot = pp * 8 + (qq - 8); }
-    else { tile = 2; slot = (pp - 8) * 8 + (qq - 8); }
-    H[s] = sum_part(part + (size_t)tile * nblk * kTileSlots, nblk, slot);
+    H[s] = vals[qq * (qq + 1) / 2 + pp];
   }
-  for (int p = threadIdx.x; p < m; p += blockDim.x)
-    g[p] = (p < 8) ? sum_part(part, nblk, 64 + p) : sum_part(part + (size_t)2 * nblk * kTileSlots, nblk, 64 + p - 8);
+  for (int p = threadIdx.x; p < m; p += blockDim.x) g[p] = vals[npair + p];
   __syncthreads();
   const int nk = chol_drop_solve(H, g, y, m, drop2, 1e-13, Ls, keep);
   for (int p = threadIdx.x; p < m; p += blockDim.x) coef[p] = y[p];
@@ -375,7 +429,9 @@ static int chk() { return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_C
 
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, cudaStream_t st) {
-  diff_push_kernel<<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  if (m_new <= 4) diff_push_kernel<4><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else if (m_new <= 8) diff_push_kernel<8><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else diff_push_kernel<16><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   return chk();
 }
 
@@ -400,7 +456,7 @@ int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0
     for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 0]; B2.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
     dots_kernel<true><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
   }
-  spe_solve_kernel<<<1, 256, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
+  spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
   lincomb_kernel<<<nb, kTS, 0, st>>>(D, coef, m, len, x0);
   return chk();
 }

@@ -17,7 +17,7 @@ namespace {
 constexpr int kMaxN = MQS_NOALLOC_MAX_N;
 constexpr long long kMaxLen = 3LL * kMaxN * kMaxN * kMaxN;          // doubles per layout vector
 constexpr long long kFlagDoubles = ((long long)kMaxN * kMaxN * kMaxN + 7) / 8;
-constexpr int kMaxBlocks = 256;
+constexpr int kMaxBlocks = 512;
 // r, p, q, L x, scaled b | 8 x kMaxBlocks partial sums | conductor flags | barrier, error, result
 constexpr long long kOffR = 0, kOffP = kMaxLen, kOffQ = 2 * kMaxLen, kOffLx = 3 * kMaxLen, kOffB = 4 * kMaxLen;
 constexpr long long kOffPart = 5 * kMaxLen;

@@ -38,13 +38,18 @@ struct PcgArgs {
 struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
   const double* b; double* r; double* lx; long long n3;
   double rr = 0.0, bb = 0.0;
+  double bp[3];
+  __device__ void prefetch(long long e) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bp[c] = b[e + c * n3];
+  }
   __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
     const double t[3] = {tx, ty, tz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long idx = e + c * n3;
       if (m >> c & 1u) {
-        const double bv = b[idx];
+        const double bv = bp[c];
         const double rv = bv - t[c];
         r[idx] = rv; lx[idx] = t[c];
         rr = fma(rv, rv, rr); bb = fma(bv, bv, bb);
@@ -58,6 +63,12 @@ struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
 struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
   double* p; double* q; long long n3; double beta; bool first;
   double pq = 0.0;
+  double pp[3], qp[3];
+  __device__ void prefetch(long long e) {
+    if (first) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { pp[c] = p[e + c * n3]; qp[c] = q[e + c * n3]; }
+  }
   __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double sx, double sy,
                              double sz) {
     const double t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
@@ -66,8 +77,8 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
       const long long idx = e + c * n3;
       double qn = 0.0, pn = 0.0;
       if (m >> c & 1u) {
-        qn = first ? t[c] : fma(beta, q[idx], t[c]);
-        pn = first ? s[c] : fma(beta, p[idx], s[c]);
+        qn = first ? t[c] : fma(beta, qp[c], t[c]);
+        pn = first ? s[c] : fma(beta, pp[c], s[c]);
         pq = fma(pn, qn, pq);
       }
       q[idx] = qn; p[idx] = pn;
@@ -75,7 +86,7 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
   }
 };
 
-__global__ void __launch_bounds__(kBlock, 1) pcg_kernel(PcgArgs a) {
+__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a) {
   __shared__ SweepSmem sm;
   __shared__ double red[2 * 32];
   __shared__ double gs[2];
@@ -225,7 +236,7 @@ int pcg_max_blocks(int* nblk) {
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MQS_ERR_CUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel, kBlock, 0) != cudaSuccess) return MQS_ERR_CUDA;
   if (occ < 1) return MQS_ERR_CUDA;
-  *nblk = nsm;  // one persistent block per SM
+  *nblk = nsm * (occ < kPcgBlocksPerSM ? occ : kPcgBlocksPerSM);  // persistent, co-resident blocks
   return MQS_OK;
 }
 
