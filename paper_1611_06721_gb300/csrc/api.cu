@@ -34,7 +34,7 @@ struct mqs_handle {
   double* nu = nullptr;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *lx = nullptr, *b = nullptr;
   double *xu = nullptr, *bu = nullptr, *tmp = nullptr, *tmp2 = nullptr;
-  double *ac_full = nullptr, *ac = nullptr, *ac2 = nullptr, *cvec = nullptr, *cvec2 = nullptr;
+  double *ac_full = nullptr, *ac_full2 = nullptr, *ac = nullptr, *ac2 = nullptr, *cvec = nullptr, *cvec2 = nullptr;
   double* part = nullptr;
   unsigned* bar = nullptr;
   int* derr = nullptr;
@@ -147,13 +147,6 @@ __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_s
   s.start_relres = pr->start_relres;
   s.pod_info = (use_small == 2) ? so->info : 0.0;
   *dst = s;
-}
-
-__global__ void rhs_current_kernel(double* out, double scale, double amp, double freq, int waveform, double tau,
-                                   double t) {
-  // i_S(t) of Sec. II / Sec. IV, times h/nu0
-  const double i_t = (waveform == 0) ? amp * sin(2.0 * 3.141592653589793 * freq * t) : amp * (1.0 - exp(-t / tau));
-  out[0] = scale * i_t;
 }
 
 int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t st) {
@@ -387,7 +380,8 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->isqmc, std::max<long>(H->n_c, 1)));
   RK(dalloc(H, &H->brauer, ccells));
   RK(dalloc(H, &H->nu, ccells));
-  for (double** v : {&H->x, &H->r, &H->p, &H->q, &H->lx, &H->b, &H->xu, &H->bu, &H->tmp, &H->tmp2, &H->ac_full})
+  for (double** v : {&H->x, &H->r, &H->p, &H->q, &H->lx, &H->b, &H->xu, &H->bu, &H->tmp, &H->tmp2, &H->ac_full,
+                     &H->ac_full2})
     RK(dalloc(H, v, L));
   for (double** v : {&H->ac, &H->ac2, &H->cvec, &H->cvec2}) RK(dalloc(H, v, std::max<long>(H->n_c, 1)));
   RK(dalloc(H, &H->part, (size_t)8 * H->nblk));
@@ -416,7 +410,11 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
     CK(cudaMemcpy(H->isqmc, isqmc.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(H->brauer, brbox.data(), ccells, cudaMemcpyHostToDevice));
-  for (double* v : {H->x, H->r, H->p, H->q, H->lx, H->b, H->xu, H->bu, H->tmp, H->tmp2, H->ac_full})
+  {
+    std::vector<double> nuinit(ccells, H->nu0);   // linear cells keep nu0 (cell_nu_kernel runs only with Brauer cells)
+    CK(cudaMemcpy(H->nu, nuinit.data(), sizeof(double) * ccells, cudaMemcpyHostToDevice));
+  }
+  for (double* v : {H->x, H->r, H->p, H->q, H->lx, H->b, H->xu, H->bu, H->tmp, H->tmp2, H->ac_full, H->ac_full2})
     CK(cudaMemset(v, 0, sizeof(double) * L));
   CK(cudaMemset(H->ac, 0, sizeof(double) * std::max<long>(H->n_c, 1)));
   CK(cudaMemset(H->pod_G, 0, sizeof(double) * kMaxPod * kMaxPod));
@@ -474,13 +472,13 @@ int ensure_stats(mqs_handle* H, int nsteps) {
   return MQS_OK;
 }
 
-// conductor update for the state currently in H->ac / H->ac_full with w = x
+// conductor update for the state currently in H->ac / H->ac_full with w = x;
+// the new state goes to the other compact and layout buffers, then they swap
 int conductor_step(mqs_handle* H, const double* w, double dt, cudaStream_t st) {
   if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st));
-  else RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, true, st));
-  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st));
+  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st, H->ac_full2));
   std::swap(H->ac, H->ac2);
-  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+  std::swap(H->ac_full, H->ac_full2);
   return MQS_OK;
 }
 
@@ -578,10 +576,9 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
     long nl = 0;
     mark(H);
     // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
-    rhs_current_kernel<<<1, 1, 0, st>>>(H->scal, H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz,
-                                        H->coil.waveform, H->coil.tau, t_src);
-    RK(launch_rhs(H->dg, H->ac_full, H->b, H->scal, coil, H->rhs_box, st));
-    nl += 2;
+    const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+    RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->rhs_box, st));
+    nl += 1;
     mark(H);
     // (a3) start vector
     int used_small = 0;
@@ -596,7 +593,7 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
     mark(H);
     // (a5) conducting update, eq. (acm)
     RK(conductor_step(H, H->x, H->dt, st));
-    nl += 3;
+    nl += H->any_brauer ? 2 : 1;
     mark(H);
     // (a6) history
     RK(history_push(H, H->x, H->lx, st));
@@ -748,7 +745,7 @@ int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol,
   CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
   CK(cudaMemsetAsync(H->tmp, 0, sizeof(double) * H->len, st));
   CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
-  CK(cudaMemsetAsync(H->scal + 2, 0, sizeof(double), st));
+  const CoilDrive nodrv{H->h / H->nu0, 0.0, 0.0, 1.0, 0.0, 0};
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   double lam = 0.0, lam_old = 0.0;
   int it = 0;
@@ -756,7 +753,7 @@ int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol,
     // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
     power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
     RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
-    RK(launch_rhs(H->dg, H->tmp, H->bu, H->scal + 2, coil, H->rhs_box, st));
+    RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->rhs_box, st));
     RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
     // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
     RK(launch_cell_nu(H->dg, H->cg, H->tmp, H->xu, true, st));

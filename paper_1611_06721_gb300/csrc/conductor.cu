@@ -41,10 +41,13 @@ struct EpiRhs {  // b = coil_scale X_s - t on n-edges (eq. (mrhs), scaled by h/n
   }
 };
 
-__global__ void __launch_bounds__(kBlock) rhs_kernel(Geom g, const double* ac, double* b,
-                                                     const double* coil_scale, CoilGeom coil, Box box) {
+__global__ void __launch_bounds__(kBlock) rhs_kernel(Geom g, const double* ac, double* b, CoilDrive drv,
+                                                     CoilGeom coil, Box box) {
   __shared__ SweepSmem sm;
-  EpiRhs ep{b, g.n3, g.n, *coil_scale, coil};
+  // coil current i_S(t) (Sec. II, J_S = X_S i_S(t); ramp of Sec. IV) times h/nu0
+  const double i_t = (drv.waveform == 0) ? drv.amplitude * sin(2.0 * 3.141592653589793 * drv.freq * drv.t)
+                                         : drv.amplitude * (1.0 - exp(-drv.t / drv.tau));
+  EpiRhs ep{b, g.n3, g.n, drv.scale * i_t, coil};
   sweep_L(g, ac, box, blockIdx.x, gridDim.x, sm, ep);
 }
 
@@ -62,9 +65,9 @@ int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, 
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
-int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, const double* coil_scale, CoilGeom coil,
-               Box box, cudaStream_t st) {
-  rhs_kernel<<<stencil_grid(box), kBlock, 0, st>>>(dg.g, ac_full, b, coil_scale, coil, box);
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, Box box,
+               cudaStream_t st) {
+  rhs_kernel<<<stencil_grid(box), kBlock, 0, st>>>(dg.g, ac_full, b, drive, coil, box);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
@@ -122,7 +125,7 @@ __device__ __forceinline__ double cell_nu(const CondGeom& cg, int i, int j, int 
 // F_e = sum over the four faces f of e of C_fe M_nu[f] (C a)_f with
 // M_nu[f] = (nu of the two cells of f) / (2h); a_c update of eq. (acm).
 __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const double* w, double sw,
-                                   const double* a_in, double* a_out, double dt) {
+                                   const double* a_in, double* a_out, double dt, double* ac_out) {
   const int n = g.n;
   const long long n3 = g.n3;
   const double ih2 = 0.5 / cg.h;
@@ -154,7 +157,9 @@ __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const 
       F = m1 * fbx(ac, w, sw, n, n3, i, j - 1, k) - m2 * fbx(ac, w, sw, n, n3, i, j, k) +
           m3 * fby(ac, w, sw, n, n3, i, j, k) - m4 * fby(ac, w, sw, n, n3, i - 1, j, k);
     }
-    a_out[q] = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a_in[q]) : F;
+    const double v = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a_in[q]) : F;
+    a_out[q] = v;
+    if (ac_out) ac_out[e] = v;      // the other layout buffer (read and written buffers differ)
   }
 }
 
@@ -174,11 +179,12 @@ int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full,
 }
 
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
-                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st) {
+                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
+                       double* ac_full_out) {
   int blocks = (cg.n_c + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt);
+  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -199,26 +199,33 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
       const bool hrow = (jh >= 0) && (i < n);
       const int jr = j0 + lane;
       const bool hcol = (i0 >= 1) && (lane < kTY) && (jr < n);
-      const long long nn3 = g.n3;
+      const bool hi1 = hrow && (i + 1 < n), hj1 = hcol && (jr + 1 < n);
+      const double* __restrict__ sx_ = s;
+      const double* __restrict__ sy_ = s + n3;
+      const double* __restrict__ sz_ = s + 2 * n3;
+      int oh = hrow ? i + n * (jh + n * ks) : 0;          // halo row position, plane ks
+      int oc = hcol ? (i0 - 1) + n * (jr + n * ks) : 0;   // halo column position, plane ks
       double a[7], c[8];
-      auto load_row = [&](int k, double* v) {
-        v[0] = ld(s, n, nn3, 0, i, jh, k); v[1] = ld(s, n, nn3, 1, i, jh, k); v[2] = ld(s, n, nn3, 2, i, jh, k);
-        v[3] = ld(s, n, nn3, 1, i + 1, jh, k); v[4] = ld(s, n, nn3, 0, i, jh + 1, k);
-        v[5] = ld(s, n, nn3, 2, i, jh + 1, k); v[6] = ld(s, n, nn3, 1, i, jh, k + 1);
+      auto load_row = [&](int k, int o, double* v) {
+        v[0] = sx_[o]; v[1] = sy_[o]; v[2] = sz_[o];
+        v[3] = hi1 ? sy_[o + 1] : 0.0;
+        v[4] = sx_[o + n]; v[5] = sz_[o + n];
+        v[6] = (k + 1 < n) ? sy_[o + n2] : 0.0;
       };
-      auto load_col = [&](int k, double* v) {
-        v[0] = ld(s, n, nn3, 0, i0 - 1, jr, k); v[1] = ld(s, n, nn3, 1, i0, jr, k);
-        v[2] = ld(s, n, nn3, 0, i0 - 1, jr + 1, k); v[3] = ld(s, n, nn3, 1, i0 - 1, jr, k);
-        v[4] = ld(s, n, nn3, 2, i0 - 1, jr, k); v[5] = ld(s, n, nn3, 0, i0 - 1, jr, k + 1);
-        v[6] = ld(s, n, nn3, 2, i0, jr, k);
+      auto load_col = [&](int k, int o, double* v) {
+        v[0] = sx_[o]; v[1] = sy_[o + 1];
+        v[2] = hj1 ? sx_[o + n] : 0.0;
+        v[3] = sy_[o]; v[4] = sz_[o];
+        v[5] = (k + 1 < n) ? sx_[o + n2] : 0.0;
+        v[6] = sz_[o + 1];
         v[7] = 0.0;
       };
 #pragma unroll
       for (int q = 0; q < 7; ++q) a[q] = 0.0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) c[q] = 0.0;
-      if (hrow) load_row(ks, a);
-      if (hcol) load_col(ks, c);
+      if (hrow) load_row(ks, oh, a);
+      if (hcol) load_col(ks, oc, c);
       int buf = 0;
       for (int k = ks; k < ke; ++k) {
         double na[7], nc[8];
@@ -227,9 +234,11 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
 #pragma unroll
         for (int q = 0; q < 8; ++q) nc[q] = 0.0;
         if (k + 1 < ke) {
-          if (hrow) load_row(k + 1, na);
-          if (hcol) load_col(k + 1, nc);
+          if (hrow) load_row(k + 1, oh + n2, na);
+          if (hcol) load_col(k + 1, oc + n2, nc);
         }
+        oh += n2;
+        oc += n2;
         // bz = x + y(i+1) - x(j+1) - y ; bx = y + z(j+1) - y(k+1) - z
         sg.fz[buf][0][lane] = hrow ? (a[0] - a[1]) + (a[3] - a[4]) : 0.0;
         sg.fx[buf][0][lane] = hrow ? (a[1] - a[2]) + (a[5] - a[6]) : 0.0;

@@ -24,12 +24,13 @@ int pcg_max_blocks(int* nblk);
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
 int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);
 
-// b = s X_s - L ac on n-edges of `box` with s = *coil_scale (device) = the
-// coil current times h/nu0 (the scaled right-hand side of eq. (mrhs)); the
-// coil is the loop (plane_k, i0, j0, i1, j1).
+// b = s X_s - L ac on n-edges of `box` with s = scale * i_S(t) (the scaled
+// right-hand side of eq. (mrhs), scale = h/nu0); the coil is the loop
+// (plane_k, i0, j0, i1, j1); amplitude 0 gives b = -L ac.
 struct CoilGeom { int k, i0, j0, i1, j1; };
-int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, const double* coil_scale, CoilGeom coil,
-               Box box, cudaStream_t st);
+struct CoilDrive { double scale, amplitude, freq, tau, t; int waveform; };
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, Box box,
+               cudaStream_t st);
 
 // Conductor region kernels (eq. (acm)).
 struct CondGeom {
@@ -46,9 +47,12 @@ struct CondGeom {
 int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
                    cudaStream_t st);
 // F = (K(a) a)_c at every c-edge (a = ac_full + sign_w * w).  If dt != 0:
-// a_c_out = a_c_in - dt F / M_c, else F is written to a_c_out.
+// a_c_out = a_c_in - dt F / M_c, else F is written to a_c_out.  If
+// ac_full_out is given (a layout buffer other than ac_full), the result is
+// also written there at the c-edges.
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
-                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st);
+                       double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
+                       double* ac_full_out = nullptr);
 // scatter compact a_c into the layout vector ac_full (c-edges only)
 int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st);
 

@@ -68,69 +68,149 @@ __global__ void __launch_bounds__(kTS) diff_push_kernel(MutVecSet D, MutVecSet L
 // ---- tiled dot products ------------------------------------------------------------
 // part[blk * kTileSlots + p*8 + q] = sum_e A_p[e] B_q[e]   (p < ma, q < mb; q >= p if diag)
 // part[blk * kTileSlots + 64 + q]  = sum_e B_q[e] c[e]     (if c != nullptr)
-template <bool DIAG>
-__global__ void __launch_bounds__(kTS) dots_kernel(VecSet A, VecSet B, const double* c, int ma, int mb,
-                                                   long long len, double* part) {
-  double acc[8][8], accc[8];
+// The diagonal tile keeps only the 36 accumulators of its triangle; the c
+// products are skipped where c vanishes (the right-hand side of eq. (mrhs) is
+// zero away from the conductor and the coil).
+enum DotsMode { kTri = 0, kFull = 1, kRow2 = 2, kConly = 3 };
+
+// 8x8 slot (p*8 + q) of the t-th upper-triangle product, in the order p, then q >= p
+__constant__ int c_tri_slot[36] = {0,  1,  2,  3,  4,  5,  6,  7,  9,  10, 11, 12, 13, 14, 15, 18, 19, 20,
+                                   21, 22, 23, 27, 28, 29, 30, 31, 36, 37, 38, 39, 45, 46, 47, 54, 55, 63};
+
+template <int MODE>
+__global__ void __launch_bounds__(kTS, (MODE == kFull) ? 1 : 2) dots_kernel(VecSet A, VecSet B, const double* c,
+                                                                            int ma, int mb, long long len,
+                                                                            double* part) {
+  constexpr bool DIAG = (MODE == kTri);
+  constexpr int MA = (MODE == kRow2) ? 2 : (MODE == kConly ? 0 : 8);
+  constexpr int NACC = DIAG ? 36 : (MA * 8 > 0 ? MA * 8 : 1);
+  double acc[NACC], accc[8];
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    accc[p] = 0.0;
+  for (int t = 0; t < NACC; ++t) acc[t] = 0.0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[p][q] = 0.0;
-  }
+  for (int q = 0; q < 8; ++q) accc[q] = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
        e += (long long)gridDim.x * blockDim.x) {
-    double a[8], b[8];
+    double a[MA > 0 ? MA : 1], b[8];
 #pragma unroll
-    for (int p = 0; p < 8; ++p) a[p] = (p < ma) ? A.v[p][e] : 0.0;
+    for (int p = 0; p < MA; ++p) a[p] = (p < ma) ? A.v[p][e] : 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) b[q] = (q < mb) ? B.v[q][e] : 0.0;
+    int t = 0;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      if (p < ma) {
+    for (int p = 0; p < MA; ++p) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((!DIAG || q >= p) && q < mb) acc[p][q] = fma(a[p], b[q], acc[p][q]);
-      }
+      for (int q = (DIAG ? p : 0); q < 8; ++q, ++t)
+        if (p < ma && q < mb) acc[t] = fma(a[p], b[q], acc[t]);
     }
     if (c != nullptr) {
       const double ce = c[e];
+      if (ce != 0.0) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < mb) accc[q] = fma(b[q], ce, accc[q]);
+        for (int q = 0; q < 8; ++q)
+          if (q < mb) accc[q] = fma(b[q], ce, accc[q]);
+      }
     }
   }
-  __shared__ double red[kTS / 32][kTileSlots];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ double red[kTS / 32][kTileSlots];
+  if (MODE == kFull) {
+    // rare (more than 8 SPE columns): plain butterfly sums
+    int t = 0;
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+      for (int q = 0; q < 8; ++q, ++t) {
+        const double x = warp_sum(acc[t]);
+        if (lane == 0) red[wp][p * 8 + q] = x;
+      }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const double v = warp_sum(acc[p][q]);
-      if (lane == 0) red[wp][p * 8 + q] = v;
+      const double x = warp_sum(accc[q]);
+      if (lane == 0) red[wp][64 + q] = x;
     }
-    const double v = warp_sum(accc[p]);
-    if (lane == 0) red[wp][64 + p] = v;
+  } else {
+    // Warp reduce-scatter over 48 slots (the products, then the 8 c products):
+    // lane pairs exchange the half they do not keep, four times, then one
+    // butterfly step; 48 additions per lane instead of 5 per slot.
+    double v[48];
+#pragma unroll
+    for (int t = 0; t < 48; ++t) v[t] = 0.0;
+    constexpr int NP = DIAG ? 36 : MA * 8;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) v[t] = acc[t];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[36 + q] = accc[q];
+#pragma unroll
+    for (int half = 24, off = 16; off >= 2; half >>= 1, off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const double keep = up ? v[i + half] : v[i];
+        const double send = up ? v[i] : v[i + half];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
+    if ((lane & 1) == 0) {
+      const int base = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) + 3 * ((lane >> 1) & 1);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int sl = base + i;
+        int dst = -1;
+        if (sl >= 36) dst = (sl < 44) ? 64 + (sl - 36) : -1;
+        else if (DIAG) dst = c_tri_slot[sl];
+        else if (sl < MA * 8) dst = sl;
+        if (dst >= 0) red[wp][dst] = v[i];
+      }
+    }
+    // slots no lane writes (lower triangle, unused rows) are zero
+    for (int t = lane; t < 64; t += 32) {
+      const int p = t / 8, q = t % 8;
+      const bool used = DIAG ? (q >= p) : (p < MA);
+      if (!used) red[wp][t] = 0.0;
+    }
   }
   __syncthreads();
-  for (int s = threadIdx.x; s < kTileSlots; s += blockDim.x) {
+  for (int s2 = threadIdx.x; s2 < kTileSlots; s2 += blockDim.x) {
     double t = 0.0;
-    for (int q = 0; q < kTS / 32; ++q) t += red[q][s];
-    part[(size_t)blockIdx.x * kTileSlots + s] = t;
+    for (int q = 0; q < kTS / 32; ++q) t += red[q][s2];
+    part[(size_t)blockIdx.x * kTileSlots + s2] = t;
   }
 }
 
 // ---- linear combination x = sum_p coef[p] V_p -------------------------------------
-__global__ void lincomb_kernel(VecSet V, const double* coef, int m, long long len, double* x) {
+template <int MAXM>
+__global__ void __launch_bounds__(kTS) lincomb_kernel(VecSet V, const double* coef, int m, long long len,
+                                                      double* x) {
   __shared__ double cf[kMaxVec];
-  for (int p = threadIdx.x; p < m; p += blockDim.x) cf[p] = coef[p];
+  for (int p = threadIdx.x; p < kMaxVec; p += blockDim.x) cf[p] = (p < m) ? coef[p] : 0.0;
   __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+  const long long half = len >> 1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < half;
        e += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < m; ++p) s = fma(cf[p], V.v[p][e], s);
-    x[e] = s;
+    double2 v[MAXM];
+#pragma unroll
+    for (int p = 0; p < MAXM; ++p) v[p] = (p < m) ? reinterpret_cast<const double2*>(V.v[p])[e] : double2{0.0, 0.0};
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int p = 0; p < MAXM; ++p) { sx = fma(cf[p], v[p].x, sx); sy = fma(cf[p], v[p].y, sy); }
+    reinterpret_cast<double2*>(x)[e] = double2{sx, sy};
   }
+  if ((len & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int p = 0; p < m; ++p) s = fma(cf[p], V.v[p][len - 1], s);
+    x[len - 1] = s;
+  }
+}
+
+static void launch_lincomb(const VecSet& V, const double* coef, int m, long long len, double* x, int nb,
+                           cudaStream_t st) {
+  nb *= 4;   // memory-latency bound: more resident warps
+  if (m <= 8) lincomb_kernel<8><<<nb, kTS, 0, st>>>(V, coef, m, len, x);
+  else if (m <= 16) lincomb_kernel<16><<<nb, kTS, 0, st>>>(V, coef, m, len, x);
+  else lincomb_kernel<40><<<nb, kTS, 0, st>>>(V, coef, m, len, x);
 }
 
 // ---- small dense kernels (one block) ----------------------------------------------------
@@ -142,80 +222,122 @@ __device__ double sum_part(const double* part, int nblk, int slot) {
 }
 
 // out[t] = sum over blocks of partial slot slots[t], t < ns: one warp per
-// slot, lanes strided over the blocks, then a fixed shuffle tree.
+// slot, lanes strided over the blocks (all loads issued before the adds),
+// then a fixed shuffle tree.
 __device__ void sum_parts_warp(const double* part, int nblk, const int* tiles, const int* slots, int ns,
                                double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = w; t < ns; t += nw) {
-    const double* pt = part + (size_t)tiles[t] * nblk * kTileSlots;
+    const double* pt = part + (size_t)tiles[t] * nblk * kTileSlots + slots[t];
+    double v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int q = lane + 32 * r;
+      v[r] = (q < nblk) ? pt[(size_t)q * kTileSlots] : 0.0;
+    }
     double s = 0.0;
-    for (int q = lane; q < nblk; q += 32) s += pt[(size_t)q * kTileSlots + slots[t]];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) s += v[r];
+    for (int q = lane + 512; q < nblk; q += 32) s += pt[(size_t)q * kTileSlots];
     s = warp_sum(s);
     if (lane == 0) out[t] = s;
   }
 }
 
 // Pivoted (in order) Cholesky of the symmetric m x m matrix H (row-major in
-// smem), dropping column j when its pivot v satisfies v*H_jj <= drop2*H_00
-// (scaled-unit diagonal) or v <= rel_floor.  Solves H y = g on the kept
-// columns; dropped entries of y are zero.  Returns the number kept.
-// Executed by the whole block; H and g in shared memory are overwritten.
+// smem, m <= 64), dropping column j when its pivot v satisfies
+// v*H_jj <= drop2*H_00 (scaled-unit diagonal) or v <= rel_floor.  Solves
+// H y = g on the kept columns; dropped entries of y are zero.  Returns the
+// number kept.  Run by the first warp with one matrix row per lane (rows
+// lane and lane + 32): right-looking factorisation and row-oriented
+// substitutions, a broadcast shuffle per step instead of block barriers or
+// per-row reductions.  One reciprocal square root per pivot and no divisions
+// (FP64 divide and square root are long dependent sequences on this GPU).
+// H and g in shared memory are overwritten; Ls is unused scratch.
 __device__ int chol_drop_solve(double* H, double* g, double* y, int m, double drop2, double rel_floor,
-                               double* Ls, int* keep) {
-  __shared__ double sc[kMaxVec];
-  __shared__ int nk;
-  __shared__ double piv;
-  __shared__ int kj;
+                               double* /*Ls*/, int* keep) {
+  __shared__ int nk_s;
   const int tid = threadIdx.x;
-  for (int p = tid; p < m; p += blockDim.x) sc[p] = (H[p * m + p] > 0.0) ? 1.0 / sqrt(H[p * m + p]) : 0.0;
-  __syncthreads();
-  for (int s = tid; s < m * m; s += blockDim.x) {
-    const int p = s / m, q = s % m;
-    Ls[s] = 0.0;
-    H[s] *= sc[p] * sc[q];
-  }
-  if (tid == 0) nk = 0;
-  __syncthreads();
-  const double h00 = (sc[0] > 0.0) ? 1.0 / (sc[0] * sc[0]) : 0.0;
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      double v = H[j * m + j];
-      for (int t = 0; t < j; ++t) v -= Ls[j * m + t] * Ls[j * m + t];
-      const double hjj = (sc[j] > 0.0) ? 1.0 / (sc[j] * sc[j]) : 0.0;
-      kj = (sc[j] > 0.0 && v > rel_floor && v * hjj > drop2 * h00) ? 1 : 0;
-      piv = kj ? sqrt(v) : 0.0;
-      keep[j] = kj;
-      if (kj) { Ls[j * m + j] = piv; ++nk; }
+  if (tid < 32) {
+    const int lane = tid;
+    const int r0 = lane, r1 = lane + 32;
+    const bool h0 = r0 < m, h1 = r1 < m;
+    // scaling to unit diagonal
+    const double d0 = h0 ? H[r0 * m + r0] : 0.0, d1 = h1 ? H[r1 * m + r1] : 0.0;
+    const double s0 = (d0 > 0.0) ? rsqrt(d0) : 0.0, s1 = (d1 > 0.0) ? rsqrt(d1) : 0.0;
+    const double hd00 = __shfl_sync(0xffffffffu, d0, 0);
+    // scale row r (lane) : H_rc *= s_r s_c ; s_c from its owner lane
+    for (int c = 0; c < m; ++c) {
+      const double sc_c = (c < 32) ? __shfl_sync(0xffffffffu, s0, c) : __shfl_sync(0xffffffffu, s1, c - 32);
+      if (h0) H[r0 * m + c] *= s0 * sc_c;
+      if (h1) H[r1 * m + c] *= s1 * sc_c;
     }
-    __syncthreads();
-    if (kj) {
-      for (int i = j + 1 + tid; i < m; i += blockDim.x) {
-        double v = H[i * m + j];
-        for (int t = 0; t < j; ++t) v -= Ls[i * m + t] * Ls[j * m + t];
-        Ls[i * m + j] = v / piv;
+    __syncwarp();
+    int nk = 0;
+    double inv0 = 0.0, inv1 = 0.0;
+    for (int j = 0; j < m; ++j) {
+      // owner of row j decides the pivot (its row holds the updated H_jj)
+      const bool own0 = (j == r0), own1 = (j == r1);
+      double v = 0.0, dj = 0.0;
+      if (own0) { v = H[j * m + j]; dj = d0; }
+      if (own1) { v = H[j * m + j]; dj = d1; }
+      const int src = j & 31;
+      v = __shfl_sync(0xffffffffu, v, src);
+      dj = __shfl_sync(0xffffffffu, dj, src);
+      const double sj = (dj > 0.0) ? 1.0 : 0.0;
+      const bool kj = sj > 0.0 && v > rel_floor && v * dj > drop2 * hd00;
+      const double r = kj ? rsqrt(v) : 0.0;
+      if (own0) inv0 = r;
+      if (own1) inv1 = r;
+      if (lane == 0) keep[j] = kj ? 1 : 0;
+      nk += kj ? 1 : 0;
+      // column j of L: L_ij = H_ij r (i > j), L_jj = v r; rows below update their trailing part
+      if (kj) {
+        if (h0 && r0 > j) H[r0 * m + j] *= r;
+        if (h1 && r1 > j) H[r1 * m + j] *= r;
+        if (own0 || own1) H[j * m + j] = v * r;
+        __syncwarp();
+        if (h0 && r0 > j) {
+          const double l = H[r0 * m + j];
+          for (int k = j + 1; k <= r0; ++k) H[r0 * m + k] = fma(-l, H[k * m + j], H[r0 * m + k]);
+        }
+        if (h1 && r1 > j) {
+          const double l = H[r1 * m + j];
+          for (int k = j + 1; k <= r1; ++k) H[r1 * m + k] = fma(-l, H[k * m + j], H[r1 * m + k]);
+        }
+      } else {
+        if (h0 && r0 > j) H[r0 * m + j] = 0.0;
+        if (h1 && r1 > j) H[r1 * m + j] = 0.0;
       }
+      __syncwarp();
     }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    // forward: L z = S g ; backward: L^T u = z ; y = S u   (dropped rows zero)
-    double z[kMaxVec];
-    for (int i = 0; i < m; ++i) {
-      if (!keep[i]) { z[i] = 0.0; continue; }
-      double v = g[i] * sc[i];
-      for (int t = 0; t < i; ++t) v -= Ls[i * m + t] * z[t];
-      z[i] = v / Ls[i * m + i];
+    // forward L z = S g: z_t finalised by its owner, then broadcast
+    double a0 = h0 ? g[r0] * s0 : 0.0, a1 = h1 ? g[r1] * s1 : 0.0;
+    double z0 = 0.0, z1 = 0.0;
+    for (int t = 0; t < m; ++t) {
+      double zt = 0.0;
+      if (t == r0) { z0 = a0 * inv0; zt = z0; }
+      if (t == r1) { z1 = a1 * inv1; zt = z1; }
+      zt = __shfl_sync(0xffffffffu, zt, t & 31);
+      if (h0 && r0 > t) a0 = fma(-H[r0 * m + t], zt, a0);
+      if (h1 && r1 > t) a1 = fma(-H[r1 * m + t], zt, a1);
     }
-    for (int i = m - 1; i >= 0; --i) {
-      if (!keep[i]) { y[i] = 0.0; continue; }
-      double v = z[i];
-      for (int t = i + 1; t < m; ++t) v -= Ls[t * m + i] * y[t];
-      y[i] = v / Ls[i * m + i];
+    // backward L^T u = z
+    double b0 = z0, b1 = z1, u0 = 0.0, u1 = 0.0;
+    for (int t = m - 1; t >= 0; --t) {
+      double ut = 0.0;
+      if (t == r0) { u0 = b0 * inv0; ut = u0; }
+      if (t == r1) { u1 = b1 * inv1; ut = u1; }
+      ut = __shfl_sync(0xffffffffu, ut, t & 31);
+      if (h0 && r0 < t) b0 = fma(-H[t * m + r0], ut, b0);
+      if (h1 && r1 < t) b1 = fma(-H[t * m + r1], ut, b1);
     }
-    for (int i = 0; i < m; ++i) y[i] *= sc[i];
+    if (h0) y[r0] = u0 * s0;
+    if (h1) y[r1] = u1 * s1;
+    if (lane == 0) nk_s = nk;
   }
   __syncthreads();
-  return nk;
+  return nk_s;
 }
 
 __global__ void spe_solve_kernel(const double* part, int nblk, int m, double drop2, double* coef,
@@ -447,17 +569,17 @@ int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0
   // ones, which the recursion carries accurately (the images of high orders
   // accumulate its rounding relative to their small size).
   VecSet A0 = LD, B0 = D;
-  dots_kernel<true><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
+  dots_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
   if (m > 8) {
     VecSet A1, B1;
     for (int p = 0; p < 8; ++p) { A1.v[p] = LD.v[p]; B1.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_kernel<false><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, m - 8, len, part + (size_t)nb * kTileSlots);
+    dots_kernel<kFull><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, m - 8, len, part + (size_t)nb * kTileSlots);
     VecSet A2, B2;
     for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 0]; B2.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_kernel<true><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
+    dots_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
   }
   spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
-  lincomb_kernel<<<nb, kTS, 0, st>>>(D, coef, m, len, x0);
+  launch_lincomb(D, coef, m, len, x0, nb, st);
   return chk();
 }
 
@@ -470,7 +592,7 @@ int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot
     Aw.v[0] = w; Aw.v[1] = lw;
     const int mb = (m - 8 * t) < 8 ? (m - 8 * t) : 8;
     for (int q = 0; q < 8; ++q) Bx.v[q] = X.v[8 * t + (q < mb ? q : 0)];
-    dots_kernel<false><<<nb, kTS, 0, st>>>(Aw, Bx, nullptr, 2, mb, len, part + (size_t)t * nb * kTileSlots);
+    dots_kernel<kRow2><<<nb, kTS, 0, st>>>(Aw, Bx, nullptr, 2, mb, len, part + (size_t)t * nb * kTileSlots);
   }
   pod_row_kernel<<<1, 64, 0, st>>>(part, nb, m, slot_new, G, A);
   return chk();
@@ -488,10 +610,10 @@ int pod_x0(const VecSet& X, int m, const double* G, const double* A, const doubl
     VecSet Ax;
     const int mb = (m - 8 * t) < 8 ? (m - 8 * t) : 8;
     for (int q = 0; q < 8; ++q) Ax.v[q] = X.v[8 * t + (q < mb ? q : 0)];
-    dots_kernel<false><<<nb, kTS, 0, st>>>(Ax, Ax, b, 0, mb, len, part + (size_t)t * nb * kTileSlots);
+    dots_kernel<kConly><<<nb, kTS, 0, st>>>(Ax, Ax, b, 0, mb, len, part + (size_t)t * nb * kTileSlots);
   }
   pod_solve_kernel<<<1, 256, 0, st>>>(G, A, part, nb, m, eps_pod, coef, sigma, out);
-  if (x0) lincomb_kernel<<<nb, kTS, 0, st>>>(X, coef, m, len, x0);
+  if (x0) launch_lincomb(X, coef, m, len, x0, nb, st);
   return chk();
 }
 
