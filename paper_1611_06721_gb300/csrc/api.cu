@@ -50,6 +50,7 @@ struct mqs_handle {
   SmallOut* small = nullptr;
   mqs_step_stats* dstats = nullptr;
   int dstats_cap = 0;
+  bool lx_valid = false;   // lx holds L x for the step solution x
   cudaStream_t own_st = nullptr;
   // timing
   bool timing = false;
@@ -155,6 +156,7 @@ int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t
 }
 
 int run_pcg(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st) {
+  H->lx_valid = false;   // lx is reused as scratch
   CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
   return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
                     st);
@@ -205,26 +207,44 @@ int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t 
   return MQS_OK;
 }
 
-// start vector into x for right-hand side b (scaled units); sets H->small
-int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int* used_small) {
+// start vector into x for right-hand side b (scaled units); sets H->small.
+// *init tells the PCG how to form the initial residual (see launch_pcg):
+// with the images L x0 known from the history, r = b - L x0 is written here.
+__global__ void sub_kernel(const double* b, const double* lx, double* r, long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
+    r[e] = b[e] - lx[e];
+}
+
+int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int* used_small, int* init) {
   *used_small = 0;
+  *init = 0;
   switch (H->opt.start_mode) {
     case MQS_START_ZERO:
-      CK(cudaMemsetAsync(x, 0, sizeof(double) * H->len, st));
+      *init = 2;
       break;
     case MQS_START_PREV:
+      if (H->lx_valid) {
+        sub_kernel<<<H->nblk * 4, 256, 0, st>>>(b, H->lx, H->r, H->len);
+        *init = 1;
+      }
       break;
     case MQS_START_SPE:
+      if (H->spe_m == 0) { *init = 2; break; }
+      // r = b - L x0 by the PCG's own stencil pass: forming it from the recursion
+      // images costs a second read of the table and, measured, more iterations
       RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), vs(H->spe_LD, H->opt.spe_depth), H->spe_m, b, x, H->len,
                 H->opt.eps_lin, H->tspart, H->coef, H->small, st));
       *used_small = 1;
-      if (H->spe_m == 0) *used_small = 0;
+      *init = 0;
       break;
-    case MQS_START_POD:
+    case MQS_START_POD: {
+      if (H->pod_m == 0) { *init = 2; break; }
       RK(pod_x0(vs(H->pod_X, H->opt.pod_snapshots), H->pod_m, H->pod_G, H->pod_A, b, x, H->len, H->opt.eps_pod,
                 H->tspart, H->coef, H->sigma, H->small, st));
-      *used_small = H->pod_m > 0 ? 2 : 0;
+      *used_small = 2;
+      *init = 0;
       break;
+    }
     default:
       return fail(H, MQS_ERR_ARG, "unknown start mode");
   }
@@ -240,6 +260,8 @@ long start_launches(const mqs_handle* H) {
     }
     case MQS_START_POD:
       return H->pod_m == 0 ? 0 : (H->pod_m + 7) / 8 + 2;
+    case MQS_START_PREV:
+      return H->lx_valid ? 1 : 0;
     default:
       return 0;
   }
@@ -581,14 +603,15 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
     nl += 1;
     mark(H);
     // (a3) start vector
-    int used_small = 0;
-    RK(start_vector(H, H->b, H->x, st, &used_small));
+    int used_small = 0, init = 0;
     nl += start_launches(H);
+    RK(start_vector(H, H->b, H->x, st, &used_small, &init));
     mark(H);
     // (a4) PCG
     CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
     RK(launch_pcg(H->dg, H->b, H->x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, H->opt.tol,
-                  H->opt.maxit, H->nblk, st));
+                  H->opt.maxit, H->nblk, st, init));
+    H->lx_valid = true;
     nl += 1;
     mark(H);
     // (a5) conducting update, eq. (acm)
@@ -817,8 +840,10 @@ int mqs_push_history(mqs_handle* H, const double* w) {
   CK(cudaMemcpyAsync(H->tmp, w, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
   RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
   RK(launch_apply_L(H->dg, H->tmp2, H->tmp, 1.0, H->full, st));
-  if (H->opt.start_mode == MQS_START_PREV)
+  if (H->opt.start_mode == MQS_START_PREV) {
     CK(cudaMemcpyAsync(H->x, H->tmp2, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+    H->lx_valid = false;
+  }
   RK(history_push(H, H->tmp2, H->tmp, st));
   CK(cudaStreamSynchronize(st));
   return MQS_OK;

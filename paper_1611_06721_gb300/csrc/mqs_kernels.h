@@ -16,9 +16,11 @@ struct DevGeom {
   Geom g;                 // device view (cflags points to device memory)
 };
 
+// init: 0 = the kernel forms r = b - L x; 1 = r holds b - L x already;
+// 2 = zero start (the kernel sets x = 0, r = b).
 int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
                double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
-               cudaStream_t st);
+               cudaStream_t st, int init = 0);
 int pcg_max_blocks(int* nblk);
 
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).

@@ -205,6 +205,47 @@ __global__ void __launch_bounds__(kTS) lincomb_kernel(VecSet V, const double* co
   }
 }
 
+// x = sum_p coef[p] V_p and r = b - sum_p coef[p] W_p (W_p = L V_p): the start
+// vector and its residual in one pass (no stencil needed)
+template <int MAXM>
+__global__ void __launch_bounds__(kTS) lincomb_res_kernel(VecSet V, VecSet W, const double* coef, int m,
+                                                          const double* b, long long len, double* x, double* r) {
+  __shared__ double cf[kMaxVec];
+  for (int p = threadIdx.x; p < kMaxVec; p += blockDim.x) cf[p] = (p < m) ? coef[p] : 0.0;
+  __syncthreads();
+  const long long half = len >> 1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < half;
+       e += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
+#pragma unroll
+    for (int p = 0; p < MAXM; ++p) {
+      if (p < m) {
+        const double2 v = reinterpret_cast<const double2*>(V.v[p])[e];
+        const double2 w = reinterpret_cast<const double2*>(W.v[p])[e];
+        sx = fma(cf[p], v.x, sx); sy = fma(cf[p], v.y, sy);
+        tx = fma(cf[p], w.x, tx); ty = fma(cf[p], w.y, ty);
+      }
+    }
+    const double2 bb = reinterpret_cast<const double2*>(b)[e];
+    reinterpret_cast<double2*>(x)[e] = double2{sx, sy};
+    reinterpret_cast<double2*>(r)[e] = double2{bb.x - tx, bb.y - ty};
+  }
+  if ((len & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0, t = 0.0;
+    for (int p = 0; p < m; ++p) { s = fma(cf[p], V.v[p][len - 1], s); t = fma(cf[p], W.v[p][len - 1], t); }
+    x[len - 1] = s;
+    r[len - 1] = b[len - 1] - t;
+  }
+}
+
+static void launch_lincomb_res(const VecSet& V, const VecSet& W, const double* coef, int m, const double* b,
+                               long long len, double* x, double* r, int nb, cudaStream_t st) {
+  nb *= 4;
+  if (m <= 8) lincomb_res_kernel<8><<<nb, kTS, 0, st>>>(V, W, coef, m, b, len, x, r);
+  else if (m <= 16) lincomb_res_kernel<16><<<nb, kTS, 0, st>>>(V, W, coef, m, b, len, x, r);
+  else lincomb_res_kernel<40><<<nb, kTS, 0, st>>>(V, W, coef, m, b, len, x, r);
+}
+
 static void launch_lincomb(const VecSet& V, const double* coef, int m, long long len, double* x, int nb,
                            cudaStream_t st) {
   nb *= 4;   // memory-latency bound: more resident warps
@@ -558,7 +599,7 @@ int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const dou
 }
 
 int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st) {
+           double* part, double* coef, SmallOut* out, cudaStream_t st, double* r0) {
   const int nb = ts_blocks();
   if (m <= 0) {
     if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
@@ -579,7 +620,8 @@ int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0
     dots_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
   }
   spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
-  launch_lincomb(D, coef, m, len, x0, nb, st);
+  if (r0) launch_lincomb_res(D, LD, coef, m, b, len, x0, r0, nb, st);
+  else launch_lincomb(D, coef, m, len, x0, nb, st);
   return chk();
 }
 
@@ -599,7 +641,8 @@ int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot
 }
 
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
-           double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st) {
+           double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st,
+           const VecSet* LX, double* r0) {
   const int nb = ts_blocks();
   if (m <= 0) {
     if (x0 && cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
@@ -613,7 +656,8 @@ int pod_x0(const VecSet& X, int m, const double* G, const double* A, const doubl
     dots_kernel<kConly><<<nb, kTS, 0, st>>>(Ax, Ax, b, 0, mb, len, part + (size_t)t * nb * kTileSlots);
   }
   pod_solve_kernel<<<1, 256, 0, st>>>(G, A, part, nb, m, eps_pod, coef, sigma, out);
-  if (x0) launch_lincomb(X, coef, m, len, x0, nb, st);
+  if (x0 && r0 && LX) launch_lincomb_res(X, *LX, coef, m, b, len, x0, r0, nb, st);
+  else if (x0) launch_lincomb(X, coef, m, len, x0, nb, st);
   return chk();
 }
 

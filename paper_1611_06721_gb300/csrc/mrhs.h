@@ -17,11 +17,13 @@ int ts_nblk();
 // partial-sum buffer needed: 5 tiles * ts_nblk() * kTileSlots doubles
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, cudaStream_t st);
+// x0 = Galerkin start; if r0 is given also r0 = b - L x0 from the stored images
 int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st);
+           double* part, double* coef, SmallOut* out, cudaStream_t st, double* r0 = nullptr);
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st);
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
-           double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st);
+           double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st,
+           const VecSet* LX = nullptr, double* r0 = nullptr);
 
 }  // namespace mqs

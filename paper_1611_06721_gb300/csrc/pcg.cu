@@ -33,6 +33,7 @@ struct PcgArgs {
   double tol2;
   int maxit;
   long long spin;
+  int init;           // 0: r = b - L x (stencil); 1: r given (start vector's image known); 2: x = 0, r = b
 };
 
 struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
@@ -115,11 +116,21 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a)
 
   int status = MQS_OK, it = 0;
   double rr = 0.0, bb = 0.0, start_rel = 0.0, relres = 0.0;
-  // initial residual r = b - L x0
-  {
+  // initial residual
+  if (a.init == 0) {            // r = b - L x0 by the stencil
     EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
     sweep_L(a.g, a.x, a.full, bid, nb, sm, ep);
     if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
+  } else {                      // r given (init 1) or x0 = 0 so r = b (init 2): sums only
+    double s0 = 0.0, s1 = 0.0;
+    for (long long e = tid; e < len; e += nth) {
+      const double be = a.b[e];
+      double re;
+      if (a.init == 2) { re = be; a.r[e] = be; a.x[e] = 0.0; } else { re = a.r[e]; }
+      s0 = fma(re, re, s0);
+      s1 = fma(be, be, s1);
+    }
+    if (!reduce2(s0, s1, rr, bb)) return;
   }
   if (bb == 0.0) {  // zero right-hand side: x = 0 after 0 iterations
     for (long long e = tid; e < len; e += nth) { a.x[e] = 0.0; a.r[e] = 0.0; a.lx[e] = 0.0; }
@@ -128,6 +139,19 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a)
   }
   start_rel = sqrt(rr / bb);
   bool need_true = false;
+  if (a.init != 0 && isfinite(rr) && isfinite(bb) && rr <= a.tol2 * bb) {
+    // the start vector's residual came from stored images: confirm it on the
+    // true residual (which also yields L x for the history)
+    EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm, ep);
+    double rt, bt;
+    if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+    if (rt <= a.tol2 * bb) {
+      if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{0, MQS_OK, sqrt(rt / bb), start_rel};
+      return;
+    }
+    rr = rt;   // iterate from the true residual
+  }
   if (!isfinite(rr) || !isfinite(bb)) {
     status = MQS_ERR_NAN;
   } else if (rr > a.tol2 * bb) {
@@ -202,7 +226,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a)
       if (it >= a.maxit) { status = MQS_ERR_NOT_CONVERGED; need_true = true; break; }
     }
   } else {
-    relres = start_rel;  // the start vector already satisfies the tolerance
+    relres = start_rel;  // the start vector already satisfies the tolerance (true residual)
   }
   if (need_true) {
     EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a)
 
 int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
                double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
-               cudaStream_t st) {
+               cudaStream_t st, int init) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -224,6 +248,7 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
   a.part = part; a.bar = bar; a.err = err; a.out = out;
   a.tol2 = tol * tol; a.maxit = maxit;
   a.spin = 1ll << 24;   // ~1-2 s of polling before a barrier gives up
+  a.init = init;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
