@@ -240,6 +240,16 @@ int mqs_timing_enable(mqs_handle* h, int on);
 /* Waits for the stream and returns the accumulated times and counts. */
 int mqs_timing_get(mqs_handle* h, mqs_timing* out);
 
+/* mqs_selftest_barrier_timeout: launches the persistent kernels' grid
+ * barrier with an arrival count that can never be reached and a wait limit
+ * of `polls` polls (about 100 ns each), so every block gives up, records
+ * MQS_ERR_TIMEOUT and returns (a poll is one L2 round trip, under a
+ * microsecond).  Used to test that a stuck device wait ends with an error
+ * status while the context stays usable.  Returns the status
+ * the kernel recorded (MQS_ERR_TIMEOUT expected), MQS_ERR_CUDA on a launch
+ * failure.  Allocates a few bytes of device memory for the flag. */
+int mqs_selftest_barrier_timeout(long long polls);
+
 /* History for the start vectors (Sec. III).  mqs_push_history appends a
  * solution w (layout vector, host) as the newest entry; K_n w is computed
  * by the library (during mqs_step it is a by-product of the PCG residual). */

@@ -27,7 +27,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution", "mqs_reset_history",
            "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev", "mqs_conductor_rate",
            "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
-           "mqs_timing_get", "mqs_pcg_solve_noalloc")
+           "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout")
 
 
 class Grid(C.Structure):
@@ -114,6 +114,7 @@ def load():
         "mqs_timing_enable": ([H, I], I),
         "mqs_timing_get": ([H, P(Timing)], I),
         "mqs_pcg_solve_noalloc": ([I, D, D, V, V, V, D, I, P(PcgInfo), V], I),
+        "mqs_selftest_barrier_timeout": ([C.c_longlong], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -247,12 +247,18 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
   a.b = b; a.x = x; a.r = r; a.p = p; a.q = q; a.lx = lx;
   a.part = part; a.bar = bar; a.err = err; a.out = out;
   a.tol2 = tol * tol; a.maxit = maxit;
-  a.spin = 1ll << 24;   // ~1-2 s of polling before a barrier gives up
+  a.spin = 1ll << 21;   // about a second of polling before a barrier gives up
   a.init = init;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+// every block waits at a barrier whose target exceeds the grid size
+__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) barrier_selftest_kernel(unsigned* ctr, int* err,
+                                                                                    long long polls) {
+  grid_barrier(ctr, gridDim.x + 1, polls, err);
 }
 
 int pcg_max_blocks(int* nblk) {
@@ -266,3 +272,26 @@ int pcg_max_blocks(int* nblk) {
 }
 
 }  // namespace mqs
+
+extern "C" int mqs_selftest_barrier_timeout(long long polls) {
+  using namespace mqs;
+  if (polls < 1) return MQS_ERR_ARG;
+  int nblk = 0;
+  if (pcg_max_blocks(&nblk) != MQS_OK) return MQS_ERR_CUDA;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 64) != cudaSuccess) return MQS_ERR_OOM;
+  unsigned* ctr = static_cast<unsigned*>(mem);
+  int* err = reinterpret_cast<int*>(static_cast<char*>(mem) + 16);
+  int rc = MQS_ERR_CUDA;
+  if (cudaMemset(mem, 0, 64) == cudaSuccess) {
+    void* args[] = {&ctr, &err, &polls};
+    if (cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(nblk), dim3(kBlock), args, 0, 0) ==
+            cudaSuccess &&
+        cudaDeviceSynchronize() == cudaSuccess) {
+      int h = 0;
+      if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) rc = h;
+    }
+  }
+  cudaFree(mem);
+  return rc;
+}

@@ -261,3 +261,46 @@ def test_full_size_nonlinear_first_steps(pkg):
     assert np.mean([x.iterations for x in st_spe[-8:]]) < 0.5 * np.mean([x.iterations for x in st_zero[-8:]])
     s.close()
     s2.close()
+
+
+# ---- other readings of the step and the paper-sized grid ---------------------------------------
+@pytest.mark.parametrize("rhs_time,waveform", [(1, 0), (0, 1), (1, 1)])
+def test_source_time_level_and_ramp_waveform(pkg, rhs_time, waveform):
+    p = W.config_linear_block().with_(waveform=waveform, tau=0.5)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 30, start_mode=START_SPE, spe_depth=8, tol=1e-10, rhs_time=rhs_time)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, rhs_time=rhs_time)
+    s.mqs_step(30)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, ref.a_c) < 1e-8
+    s.close()
+
+
+def test_fused_solve_matches_the_literal_two_solve_reading(pkg):
+    # eq. (acm) with K_n^+ applied to j and to K_cn^T a_c separately (oracle)
+    # equals the single solve of the library
+    p = W.config_linear_block()
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    lit = O.run_explicit_euler(d, dt, 30, start_mode=START_ZERO, tol=1e-12, literal=True)
+    s = make(pkg, p, start_mode=START_ZERO, dt=dt, tol=1e-12)
+    s.mqs_step(30)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, lit.a_c) < 1e-8
+    s.close()
+
+
+def test_paper_sized_grid(pkg):
+    # 22^3 cells: 3*22*21^2 = 29106 interior edges, the ~30k dofs of the coarse TEAM 10 mesh
+    p = W.scaled_nonlinear(22, amplitude=2e4)
+    d = O.Discretization(p)
+    assert d.n_c + d.n_n == 29106
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 40, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10)
+    stats = s.mqs_step(40)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, ref.a_c) < 1e-8
+    assert abs(np.mean([x.iterations for x in stats]) - ref.iterations.mean()) <= 2.0
+    s.close()
