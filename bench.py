@@ -201,7 +201,7 @@ def run_ours(args, rank, ws, local, dist):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     p = W.config_nonlinear_iron()
-    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8)
+    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, pcg_variant=args.pcg_variant)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -270,6 +270,7 @@ def run_ours(args, rank, ws, local, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": 64, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
                        "start_vector": "spe8", "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
+                       "pcg": "two reductions per iteration" if args.pcg_variant == 0 else "one reduction per iteration",
                        "l2": "flushed between timed steps by a 256 MiB write",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters_per_step": float(its.mean()),
@@ -339,6 +340,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
+    ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
+                    help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

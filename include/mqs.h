@@ -97,7 +97,8 @@ typedef struct {
  * spe_depth (1..16), pod_snapshots (1..40), eps_pod (POD truncation
  * sigma_i/sigma_1 >= eps_pod, eq. (relSV2)), eps_lin (SPE drop tolerance).
  * dt: explicit Euler step (s); may be set later with mqs_set_dt.
- * rhs_time: 0 = source at t_m (as printed in eq. (acm)), 1 = at t_{m-1}. */
+ * rhs_time: 0 = source at t_m (as printed in eq. (acm)), 1 = at t_{m-1}.
+ * pcg_variant: see the field. */
 typedef struct {
     double tol;
     int    maxit;
@@ -108,7 +109,10 @@ typedef struct {
     double eps_lin;
     double dt;
     int    rhs_time;
-    int    reserved;
+    int    pcg_variant;   /* 0: two grid reductions per iteration (Hestenes-Stiefel
+                             recurrences, default); 1: one reduction (Chronopoulos-
+                             Gear recurrences, one fused stencil pass per
+                             iteration). Same iterates in exact arithmetic. */
 } mqs_options;
 
 typedef struct {

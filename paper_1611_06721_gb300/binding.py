@@ -47,7 +47,7 @@ class Coil(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
-                ("dt", C.c_double), ("rhs_time", C.c_int), ("reserved", C.c_int)]
+                ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -152,10 +152,11 @@ class SolverOptions:
     eps_lin: float = 1e-10
     dt: float = 0.0
     rhs_time: int = 0
+    pcg_variant: int = 0
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
-                       self.eps_pod, self.eps_lin, self.dt, self.rhs_time, 0)
+                       self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant)
 
 
 class Solver:

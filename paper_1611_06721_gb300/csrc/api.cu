@@ -51,6 +51,7 @@ struct mqs_handle {
   mqs_step_stats* dstats = nullptr;
   int dstats_cap = 0;
   bool lx_valid = false;   // lx holds L x for the step solution x
+  double *r1 = nullptr, *w0 = nullptr, *w1 = nullptr, *s1 = nullptr;   // one-reduction PCG buffers
   cudaStream_t own_st = nullptr;
   // timing
   bool timing = false;
@@ -155,11 +156,21 @@ int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
+// the PCG kernel selected by opt.pcg_variant
+int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init) {
+  if (H->opt.pcg_variant == 1) {
+    const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
+    return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
+                            H->nblk, st, init);
+  }
+  return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
+                    st, init);
+}
+
 int run_pcg(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st) {
   H->lx_valid = false;   // lx is reused as scratch
   CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
-  return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
-                    st);
+  return pcg_launch(H, b, x, tol, maxit, st, 0);
 }
 
 int read_pcg(mqs_handle* H, mqs_pcg_info* info, cudaStream_t st) {
@@ -282,6 +293,7 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (o->pod_snapshots < 1 || o->pod_snapshots > kMaxPod) { why = "pod_snapshots must be in [1, 40]"; return MQS_ERR_ARG; }
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->pcg_variant != 0 && o->pcg_variant != 1) { why = "pcg_variant must be 0 or 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
   return MQS_OK;
 }
@@ -403,7 +415,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->brauer, ccells));
   RK(dalloc(H, &H->nu, ccells));
   for (double** v : {&H->x, &H->r, &H->p, &H->q, &H->lx, &H->b, &H->xu, &H->bu, &H->tmp, &H->tmp2, &H->ac_full,
-                     &H->ac_full2})
+                     &H->ac_full2, &H->r1, &H->w0, &H->w1, &H->s1})
     RK(dalloc(H, v, L));
   for (double** v : {&H->ac, &H->ac2, &H->cvec, &H->cvec2}) RK(dalloc(H, v, std::max<long>(H->n_c, 1)));
   RK(dalloc(H, &H->part, (size_t)8 * H->nblk));
@@ -609,8 +621,7 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
     mark(H);
     // (a4) PCG
     CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
-    RK(launch_pcg(H->dg, H->b, H->x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, H->opt.tol,
-                  H->opt.maxit, H->nblk, st, init));
+    RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
     H->lx_valid = true;
     nl += 1;
     mark(H);

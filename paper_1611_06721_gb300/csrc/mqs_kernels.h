@@ -23,6 +23,13 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
                cudaStream_t st, int init = 0);
 int pcg_max_blocks(int* nblk);
 
+// one-reduction PCG (one fused stencil pass and one grid reduction per
+// iteration); needs five more layout vectors
+struct PcgExtra { double* r1; double* w0; double* w1; double* s0; double* s1; };
+int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
+                     const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
+                     int nblk, cudaStream_t st, int init = 0);
+
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
 int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);
 

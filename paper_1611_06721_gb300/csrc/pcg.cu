@@ -14,6 +14,7 @@
 #include <cmath>
 #include "mqs_internal.cuh"
 #include "mqs_kernels.h"
+#include "pcg_fused.cuh"
 
 namespace mqs {
 
@@ -236,6 +237,170 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a)
     relres = sqrt(rt / bb);
   }
   if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{it, status, relres, start_rel};
+}
+
+struct EpiApplyDot {  // w = t on n-edges (0 elsewhere); sums w.r with r the source values
+  double* w; long long n3;
+  double wr = 0.0;
+  __device__ void prefetch(long long) {}
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double sx, double sy,
+                             double sz) {
+    const double t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double wv = (m >> c & 1u) ? t[c] : 0.0;
+      w[e + c * n3] = wv;
+      wr = fma(wv, s[c], wr);
+    }
+  }
+};
+
+struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; };
+
+// The one-reduction form: after the initial residual r and w = L r, every
+// iteration is one fused pass (sweep_fused) and one grid reduction of
+// (gamma, delta).  Same iterates as the two-reduction kernel in exact
+// arithmetic; convergence is confirmed on the true residual as there.
+__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
+  __shared__ union { SweepSmem s; FusedSmemBlock f; } sm;
+  __shared__ double red[2 * 32];
+  __shared__ double gs[2];
+  const int nb = gridDim.x, bid = blockIdx.x;
+  unsigned nbar = 0;
+  int slot = 0;
+  const long long len = 3 * a.g.n3;
+  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
+  auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
+    double v[2] = {v0, v1};
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
+    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
+    if (threadIdx.x < 32) {
+      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
+      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
+    }
+    __syncthreads();
+    s0 = gs[0]; s1 = gs[1];
+    slot ^= 1;
+    return true;
+  };
+  auto rb = [&](int c) { return c ? fb.r1 : a.r; };
+  auto wb = [&](int c) { return c ? fb.w1 : fb.w0; };
+  auto sb = [&](int c) { return c ? fb.s1 : fb.s0; };
+  int status = MQS_OK, it = 0, cur = 0;
+  double rr = 0.0, bb = 0.0, start_rel = 0.0, relres = 0.0;
+  if (a.init == 0) {
+    EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
+  } else {
+    double s0 = 0.0, s1 = 0.0;
+    for (long long e = tid; e < len; e += nth) {
+      const double be = a.b[e];
+      double re;
+      if (a.init == 2) { re = be; a.r[e] = be; a.x[e] = 0.0; } else { re = a.r[e]; }
+      s0 = fma(re, re, s0);
+      s1 = fma(be, be, s1);
+    }
+    if (!reduce2(s0, s1, rr, bb)) return;
+  }
+  if (bb == 0.0) {
+    for (long long e = tid; e < len; e += nth) { a.x[e] = 0.0; a.r[e] = 0.0; a.lx[e] = 0.0; }
+    if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{0, MQS_OK, 0.0, 0.0};
+    return;
+  }
+  start_rel = sqrt(rr / bb);
+  if (a.init != 0 && isfinite(rr) && isfinite(bb) && rr <= a.tol2 * bb) {
+    EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    double rt, bt;
+    if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+    if (rt <= a.tol2 * bb) {
+      if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{0, MQS_OK, sqrt(rt / bb), start_rel};
+      return;
+    }
+    rr = rt;
+  }
+  bool need_true = false;
+  if (!isfinite(rr) || !isfinite(bb)) {
+    status = MQS_ERR_NAN;
+  } else if (rr > a.tol2 * bb) {
+    double gamma = rr, alpha = 0.0, beta = 0.0;
+    bool first = true;
+    int restarts = 0;
+    bool restart_w = true;     // w = L r must be formed for the current r
+    for (;;) {
+      if (restart_w) {
+        EpiApplyDot ep{wb(cur), a.g.n3};
+        sweep_L(a.g, rb(cur), a.full, bid, nb, sm.s, ep);
+        double delta, dummy;
+        if (!reduce2(ep.wr, 0.0, delta, dummy)) return;
+        if (!(delta > 0.0)) { status = isnan(delta) ? MQS_ERR_NAN : MQS_ERR_BREAKDOWN; need_true = true; break; }
+        alpha = gamma / delta;
+        beta = 0.0;
+        first = true;
+        restart_w = false;
+      }
+      FusedVecs v{a.x, a.p, rb(cur), wb(cur), sb(cur), rb(cur ^ 1), wb(cur ^ 1), sb(cur ^ 1), alpha, beta, first};
+      double g1 = 0.0, d1 = 0.0;
+      sweep_fused(a.g, v, a.full, bid, nb, sm.f, g1, d1);
+      double gn, dn;
+      if (!reduce2(g1, d1, gn, dn)) return;
+      ++it;
+      cur ^= 1;
+      if (!isfinite(gn) || !isfinite(dn)) { status = MQS_ERR_NAN; need_true = true; break; }
+      if (gn <= a.tol2 * bb) {
+        EpiResidual ep{a.b, rb(cur), a.lx, a.g.n3};
+        sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+        double rt, bt;
+        if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+        if (rt <= a.tol2 * bb || restarts >= 8) {
+          relres = sqrt(rt / bb);
+          status = (rt <= a.tol2 * bb) ? MQS_OK : MQS_ERR_NOT_CONVERGED;
+          break;
+        }
+        gamma = rt; ++restarts; restart_w = true;   // restart from the true residual
+      } else {
+        const double bnew = gn / gamma;
+        const double den = dn - bnew * gn / alpha;
+        if (!(den > 0.0)) { status = isnan(den) ? MQS_ERR_NAN : MQS_ERR_BREAKDOWN; need_true = true; break; }
+        beta = bnew;
+        alpha = gn / den;
+        gamma = gn;
+        first = false;
+      }
+      if (it >= a.maxit) { status = MQS_ERR_NOT_CONVERGED; need_true = true; break; }
+    }
+  } else {
+    relres = start_rel;
+  }
+  if (need_true) {
+    EpiResidual ep{a.b, rb(cur), a.lx, a.g.n3};
+    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    double rt, bt;
+    if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
+    relres = sqrt(rt / bb);
+  }
+  if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{it, status, relres, start_rel};
+}
+
+int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
+                     const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
+                     int nblk, cudaStream_t st, int init) {
+  PcgArgs a;
+  a.g = dg.g;
+  a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
+  a.b = b; a.x = x; a.r = r; a.p = p; a.q = nullptr; a.lx = lx;
+  a.part = part; a.bar = bar; a.err = err; a.out = out;
+  a.tol2 = tol * tol; a.maxit = maxit;
+  a.spin = 1ll << 21;
+  a.init = init;
+  FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1};
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
+  void* args[] = {&a, &fb};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
 int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,

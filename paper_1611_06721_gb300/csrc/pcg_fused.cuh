@@ -1,0 +1,284 @@
+// One-reduction PCG iteration (Chronopoulos-Gear form of the CG recurrences)
+// as a single stencil pass.  With w = L r and s = L p carried as vectors:
+//   p_i = r_i + beta p_{i-1},  s_i = w_i + beta s_{i-1},
+//   x_{i+1} = x_i + alpha p_i,  r_{i+1} = r_i - alpha s_i,
+//   w_{i+1} = L r_{i+1},  gamma = r_{i+1}.r_{i+1},  delta = w_{i+1}.r_{i+1};
+//   beta' = gamma'/gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha).
+// The stencil source r_{i+1} is formed once per position by its owner from
+// (r_i, w_i, s_{i-1}) - buffers nobody writes during the pass (r, s, w are
+// double-buffered) - and shared with the x+1 neighbour by shuffle and the y+1
+// neighbour through shared memory; the halo warp forms the tile halo.
+#pragma once
+#include "mqs_internal.cuh"
+
+namespace mqs {
+
+struct FusedVecs {
+  double* x;
+  double* p;
+  const double* r_in;   // r_i
+  const double* w_in;   // w_i = L r_i
+  const double* s_in;   // s_{i-1}
+  double* r_out;        // r_{i+1}
+  double* w_out;        // w_{i+1}
+  double* s_out;        // s_i
+  double alpha, beta;
+  bool first;           // beta = 0 and no previous p, s
+};
+
+struct FusedSmem {
+  // r_{i+1} of plane k (buffer k&1): rows j0-1 .. j0+kTY (index row+1),
+  // columns i0-1 .. i0+32 (index lane+1), three components
+  double src[2][3][kTY + 2][34];
+  double fz[2][kTY + 1][32];      // bz, bx of rows j0-1 .. j0+kTY-1
+  double fx[2][kTY + 1][32];
+  double hz[2][kTY];              // x halo: bz, by at (i0 - 1, j0 + row)
+  double hy[2][kTY];
+};
+struct FusedSmemBlock { FusedSmem g[kGroups]; };
+
+// r_{i+1} at one component position from the input buffers (no writes)
+__device__ __forceinline__ double fused_src(const FusedVecs& v, int off) {
+  const double sv = v.first ? v.w_in[off] : fma(v.beta, v.s_in[off], v.w_in[off]);
+  return fma(-v.alpha, sv, v.r_in[off]);
+}
+
+// Update of one owned position (3 components): writes p, x, s_out, r_out and
+// returns r_{i+1} in src[3].
+__device__ __forceinline__ void fused_update(const FusedVecs& v, int o, int n3, double* src) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int e = o + c * n3;
+    const double r = v.r_in[e], w = v.w_in[e];
+    const double s = v.first ? w : fma(v.beta, v.s_in[e], w);
+    const double p = v.first ? r : fma(v.beta, v.p[e], r);
+    const double x = v.x[e];
+    v.s_out[e] = s;
+    v.p[e] = p;
+    v.x[e] = fma(v.alpha, p, x);
+    const double rn = fma(-v.alpha, s, r);
+    v.r_out[e] = rn;
+    src[c] = rn;
+  }
+}
+
+// Loaded inputs of one position (3 components): r_i, w_i, s_{i-1}, p_{i-1}, x_i.
+struct FusedLoad {
+  double r[3], w[3], s[3], p[3], x[3];
+};
+
+__device__ __forceinline__ void fused_load(const FusedVecs& v, int o, int n3, bool owned, FusedLoad& L) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int e = o + c * n3;
+    L.r[c] = v.r_in[e];
+    L.w[c] = v.w_in[e];
+    L.s[c] = v.first ? 0.0 : v.s_in[e];
+    L.p[c] = (owned && !v.first) ? v.p[e] : 0.0;
+    L.x[c] = owned ? v.x[e] : 0.0;
+  }
+}
+
+// r_{i+1} from loaded inputs; when owned also writes p, x, s_out, r_out
+__device__ __forceinline__ void fused_apply(const FusedVecs& v, int o, int n3, bool owned, const FusedLoad& L,
+                                            double* src) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double sv = v.first ? L.w[c] : fma(v.beta, L.s[c], L.w[c]);
+    const double rn = fma(-v.alpha, sv, L.r[c]);
+    src[c] = rn;
+    if (owned) {
+      const int e = o + c * n3;
+      const double pv = v.first ? L.r[c] : fma(v.beta, L.p[c], L.r[c]);
+      v.s_out[e] = sv;
+      v.p[e] = pv;
+      v.x[e] = fma(v.alpha, pv, L.x[c]);
+      v.r_out[e] = rn;
+    }
+  }
+}
+
+// One fused pass over `box` for group-part `part` of `nparts` (block level,
+// as in sweep_L).  Accumulates gamma and delta into the caller's registers.
+__device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, int part, int nparts,
+                            FusedSmemBlock& smb, double& gamma, double& delta) {
+  const int n = g.n;
+  const int n2 = n * n;
+  const int n3 = (int)g.n3;
+  const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
+  FusedSmem& sg = smb.g[grp];
+  const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
+  if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
+  const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
+  const long long T = (long long)ntx * nty * nz;
+  const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
+  long long u = T * gp / gn;
+  const long long u1 = T * (gp + 1) / gn;
+  const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
+  while (u < u1) {
+    const long long tc = u / nz;
+    const int ka = (int)(u % nz);
+    int len = nz - ka;
+    if ((long long)len > u1 - u) len = (int)(u1 - u);
+    if (len > kMaxSeg) len = kMaxSeg;
+    u += len;
+    const int i0 = box.lo[0] + (int)(tc % ntx) * 32;
+    const int j0 = box.lo[1] + (int)(tc / ntx) * kTY;
+    const int ks = box.lo[2] + ka, ke = ks + len;
+    const int i = i0 + lane;
+    group_sync(grp);  // smem reuse across segments
+    if (w < kTY) {
+      const int j = j0 + w;
+      const bool act = (i < box.hi[0]) && (j < box.hi[1]);   // owned position
+      const bool col = (i < n) && (j < n);
+      const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
+      const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
+      const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
+      int o = col ? i + n * (j + n * ks) : 0;
+      // prologue: plane ks is owned -> update it; warm-up fluxes at ks - 1 from recomputed sources
+      double sk[3] = {0.0, 0.0, 0.0};
+      if (act) fused_update(v, o, n3, sk);
+      else if (col) { sk[0] = fused_src(v, o); sk[1] = fused_src(v, o + n3); sk[2] = fused_src(v, o + 2 * n3); }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sg.src[ks & 1][c][w + 1][lane + 1] = sk[c];
+      double bxm = 0.0, bym = 0.0;
+      if (ks >= 1 && col) {
+        const int om = o - n2;
+        const double xm = fused_src(v, om), ym = fused_src(v, om + n3), zm = fused_src(v, om + 2 * n3);
+        const double zim = (i + 1 < n) ? fused_src(v, om + 1 + 2 * n3) : 0.0;
+        const double zjm = (j + 1 < n) ? fused_src(v, om + n + 2 * n3) : 0.0;
+        bxm = (ym - zm) + (zjm - sk[1]);
+        bym = (zm - xm) + (sk[0] - zim);
+      }
+      group_sync(grp);
+      // inputs of plane ks+1, loaded ahead of use
+      FusedLoad ld1;
+      if (col && ks + 1 < n) fused_load(v, o + n2, n3, act && ks + 1 < ke, ld1);
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k, o += n2) {
+        const int nb = buf ^ 1;
+        // own r_{i+1} of plane k+1 from the inputs loaded during the previous step
+        double sk1[3] = {0.0, 0.0, 0.0};
+        if (col && k + 1 < n) fused_apply(v, o + n2, n3, act && k + 1 < ke, ld1, sk1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sg.src[nb][c][w + 1][lane + 1] = sk1[c];
+        // then issue the loads of plane k+2
+        if (col && k + 2 < n && k + 1 < ke) fused_load(v, o + 2 * n2, n3, act && k + 2 < ke, ld1);
+        // fluxes at plane k: own (k, k+1), x+1 and y+1 neighbours of plane k from smem
+        const double yi = sg.src[buf][1][w + 1][lane + 2], zi = sg.src[buf][2][w + 1][lane + 2];
+        const double xj = sg.src[buf][0][w + 2][lane + 1], zj = sg.src[buf][2][w + 2][lane + 1];
+        const double bx = (sk[1] - sk[2]) + (zj - sk1[1]);
+        const double by = (sk[2] - sk[0]) + (sk1[0] - zi);
+        const double bz = (sk[0] - sk[1]) + (yi - xj);
+        sg.fz[buf][w + 1][lane] = bz;
+        sg.fx[buf][w + 1][lane] = bx;
+        group_sync(grp);
+        double bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
+        if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
+        const double bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
+        if (act) {
+          const double tx = (bz - bzj) + (bym - by);
+          const double ty = (bzi - bz) + (bx - bxm);
+          const double tz = (bxj - bx) + (by - byi);
+          unsigned m = mcol & (k > 0 ? 7u : 4u);
+          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
+          const double t[3] = {tx, ty, tz};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double wv = (m >> c & 1u) ? t[c] : 0.0;
+            v.w_out[o + c * n3] = wv;
+            gamma = fma(sk[c], sk[c], gamma);
+            delta = fma(wv, sk[c], delta);
+          }
+        }
+        bxm = bx; bym = by;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sk[c] = sk1[c];
+        buf = nb;
+      }
+    } else {
+      // halo warp: r_{i+1} on the tile halo of plane k+1 (rows j0-1 and j0+kTY
+      // over columns i0-1..i0+32, columns i0-1 and i0+32 over the tile rows),
+      // then the halo fluxes of plane k: row j0-1 (bz, bx) and column i0-1 (bz, by)
+      constexpr int kSlots = 2 * 34 + 2 * kTY;
+      auto slot_pos = [&](int sl, int& hi, int& hj, int& row, int& cl) {
+        if (sl < 34) { hi = i0 - 1 + sl; hj = j0 - 1; row = 0; cl = sl; }
+        else if (sl < 68) { hi = i0 - 1 + (sl - 34); hj = j0 + kTY; row = kTY + 1; cl = sl - 34; }
+        else if (sl < 68 + kTY) { hi = i0 - 1; hj = j0 + (sl - 68); row = sl - 68 + 1; cl = 0; }
+        else { hi = i0 + 32; hj = j0 + (sl - 68 - kTY); row = sl - 68 - kTY + 1; cl = 33; }
+      };
+      // per lane up to three halo slots; their (r, w, s) inputs are loaded one
+      // plane ahead of use
+      constexpr int kHS = (kSlots + 31) / 32;
+      struct HaloIn { double r[3], w[3], s[3]; };
+      auto halo_load = [&](int kk, HaloIn* hin) {
+#pragma unroll
+        for (int q = 0; q < kHS; ++q) {
+          const int sl = lane + 32 * q;
+          int hi = -1, hj = -1, row = 0, cl = 0;
+          if (sl < kSlots) slot_pos(sl, hi, hj, row, cl);
+          const bool ok = sl < kSlots && hi >= 0 && hj >= 0 && hi < n && hj < n && kk >= 0 && kk < n;
+          const int oo = ok ? hi + n * (hj + n * kk) : 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : 0.0;
+            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : 0.0;
+            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : 0.0;
+          }
+        }
+      };
+      auto halo_store = [&](const HaloIn* hin, int bufw) {
+#pragma unroll
+        for (int q = 0; q < kHS; ++q) {
+          const int sl = lane + 32 * q;
+          if (sl >= kSlots) continue;
+          int hi, hj, row, cl;
+          slot_pos(sl, hi, hj, row, cl);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double sv = v.first ? hin[q].w[c] : fma(v.beta, hin[q].s[c], hin[q].w[c]);
+            sg.src[bufw][c][row][cl] = fma(-v.alpha, sv, hin[q].r[c]);
+          }
+        }
+      };
+      // consume a plane's inputs, then reuse the registers for the next loads
+      HaloIn h[kHS];
+      halo_load(ks, h);
+      halo_store(h, ks & 1);
+      halo_load(ks + 1, h);
+      group_sync(grp);
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k) {
+        const int nb = buf ^ 1;
+        halo_store(h, nb);                     // plane k+1, loaded during the previous step
+        if (k + 2 <= ke) halo_load(k + 2, h);  // in flight until the next step
+        __syncwarp();
+        // row j0-1 at column i: bz = x + y(i+1) - x(j0) - y ; bx = y + z(j0) - y(k+1) - z
+        {
+          const double x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
+          const double z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
+          const double xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
+          const double yk = sg.src[nb][1][0][lane + 1];
+          const bool hrow = (j0 >= 1) && (i < n);
+          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : 0.0;
+          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : 0.0;
+        }
+        // column i0-1 at row r: bz = x + y(i0) - x(j+1) - y ; by = z + x(k+1) - z(i0) - x
+        if (lane < kTY) {
+          const int r = lane + 1;
+          const double x0 = sg.src[buf][0][r][0], y0 = sg.src[buf][1][r][0], z0 = sg.src[buf][2][r][0];
+          const double yi = sg.src[buf][1][r][1], zi = sg.src[buf][2][r][1];
+          const double xj = sg.src[buf][0][r + 1][0];
+          const double xk = sg.src[nb][0][r][0];
+          const bool hcol = (i0 >= 1) && (j0 + lane < n);
+          sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : 0.0;
+          sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : 0.0;
+        }
+        group_sync(grp);
+        buf = nb;
+      }
+    }
+  }
+}
+
+}  // namespace mqs

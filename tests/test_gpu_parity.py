@@ -304,3 +304,23 @@ def test_paper_sized_grid(pkg):
     assert rel(a_c, ref.a_c) < 1e-8
     assert abs(np.mean([x.iterations for x in stats]) - ref.iterations.mean()) <= 2.0
     s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_both_pcg_variants_match_the_oracle(pkg, variant):
+    p = W.scaled_nonlinear(24, amplitude=5e4)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 20, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, pcg_variant=variant)
+    stats = s.mqs_step(20)
+    a_c, _, _ = s.get_state()
+    assert rel(a_c, ref.a_c) < 1e-8
+    assert np.abs(np.array([x.iterations for x in stats]) - ref.iterations).max() <= 3
+    b_o = np.zeros(d.grid.n_edges)
+    b_o[d.n_idx] = 2.0 * d.X_s[d.n_idx]
+    x, info = s.pcg_solve(oracle_to_layout(p.N, b_o), tol=1e-10)
+    res = O.pcg_jacobi(d.K_n, b_o[d.n_idx], None, d.D, tol=1e-10)
+    assert info.status == 0 and abs(info.iterations - res.iterations) <= 3
+    assert rel(d.K_cn @ layout_to_oracle(p.N, x)[d.n_idx], d.K_cn @ res.x) < 1e-9
+    s.close()
