@@ -201,7 +201,8 @@ def run_ours(args, rank, ws, local, dist):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     p = W.config_nonlinear_iron()
-    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, pcg_variant=args.pcg_variant)
+    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, pcg_variant=args.pcg_variant,
+                             precision=args.precision)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -267,8 +268,10 @@ def run_ours(args, rank, ws, local, dist):
     peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": 64, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
+                       "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
                        "start_vector": "spe8", "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
                        "pcg": "two reductions per iteration" if args.pcg_variant == 0 else "one reduction per iteration",
                        "l2": "flushed between timed steps by a 256 MiB write",
@@ -340,6 +343,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP64 PCG (default); 1: FP32 inner solves in FP64 refinement (same tolerance)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
                     help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
     ap.add_argument("--single-solve", action="store_true",

@@ -113,6 +113,12 @@ typedef struct {
                              recurrences, default); 1: one reduction (Chronopoulos-
                              Gear recurrences, one fused stencil pass per
                              iteration). Same iterates in exact arithmetic. */
+    int    precision;     /* 0: FP64 PCG (default); 1: FP64 iterative refinement
+                             around FP32 CG inner solves (stencil, vectors and
+                             products in FP32; residual, norms, convergence test
+                             and solution update in FP64; same tol). */
+    double inner_tol;     /* precision 1: smallest residual reduction an inner
+                             solve aims at (<= 0: 1e-5) */
 } mqs_options;
 
 typedef struct {
@@ -128,7 +134,7 @@ typedef struct {
     int    iterations;    /* products K_n p inside the PCG loop             */
     int    status;        /* MQS_OK or MQS_ERR_*                            */
     int    rank;          /* SPE columns kept / POD k (0 otherwise)         */
-    int    reserved;
+    int    refinements;   /* FP64 refinement steps (precision 1; else 0)    */
     double relres;        /* final true ||b - K_n w|| / ||b||               */
     double start_relres;  /* ||b - K_n x0|| / ||b||                          */
     double pod_info;      /* eq. (keepInfo) ratio, POD mode (else 0)        */

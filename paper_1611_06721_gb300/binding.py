@@ -47,7 +47,8 @@ class Coil(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
-                ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int)]
+                ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
+                ("inner_tol", C.c_double)]
 
 
 class LayoutInfo(C.Structure):
@@ -56,7 +57,7 @@ class LayoutInfo(C.Structure):
 
 
 class StepStats(C.Structure):
-    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rank", C.c_int), ("reserved", C.c_int),
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rank", C.c_int), ("refinements", C.c_int),
                 ("relres", C.c_double), ("start_relres", C.c_double), ("pod_info", C.c_double)]
 
 
@@ -153,10 +154,13 @@ class SolverOptions:
     dt: float = 0.0
     rhs_time: int = 0
     pcg_variant: int = 0
+    precision: int = 0
+    inner_tol: float = 0.0
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
-                       self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant)
+                       self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
+                       self.inner_tol)
 
 
 class Solver:

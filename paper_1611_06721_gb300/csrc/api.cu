@@ -52,6 +52,8 @@ struct mqs_handle {
   int dstats_cap = 0;
   bool lx_valid = false;   // lx holds L x for the step solution x
   double *r1 = nullptr, *w0 = nullptr, *w1 = nullptr, *s1 = nullptr;   // one-reduction PCG buffers
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;  // mixed precision
+  int* refin = nullptr;
   cudaStream_t own_st = nullptr;
   // timing
   bool timing = false;
@@ -139,12 +141,13 @@ __global__ void power_update_kernel(int n_c, const double* F, const double* isq,
   for (int q = threadIdx.x; q < n_c; q += blockDim.x) v[q] = F[q] * isq[q] / nz;
 }
 
-__global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, mqs_step_stats* dst) {
+__global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
+                              mqs_step_stats* dst) {
   mqs_step_stats s;
   s.iterations = pr->iterations;
   s.status = pr->status;
   s.rank = use_small ? so->rank : 0;
-  s.reserved = 0;
+  s.refinements = refin ? *refin : 0;
   s.relres = pr->relres;
   s.start_relres = pr->start_relres;
   s.pod_info = (use_small == 2) ? so->info : 0.0;
@@ -156,8 +159,21 @@ int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
-// the PCG kernel selected by opt.pcg_variant
+int ensure_mixed(mqs_handle* H) {
+  if (H->r32) return MQS_OK;
+  for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, H->len));
+  return MQS_OK;
+}
+
+// the PCG kernel selected by opt.precision and opt.pcg_variant
 int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init) {
+  if (H->opt.precision == 1) {
+    RK(ensure_mixed(H));
+    const MixedBufs mb{H->r32, H->p32, H->q32, H->d32};
+    const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-5;
+    return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
+                            maxit, H->nblk, st, init);
+  }
   if (H->opt.pcg_variant == 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
@@ -294,6 +310,8 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
   if (o->pcg_variant != 0 && o->pcg_variant != 1) { why = "pcg_variant must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return MQS_ERR_ARG; }
+  if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
   return MQS_OK;
 }
@@ -427,6 +445,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->sigma, kMaxVec));
   RK(dalloc(H, &H->scal, 4));
   RK(dalloc(H, &H->small, 1));
+  RK(dalloc(H, &H->refin, 1));
   RK(dalloc(H, &H->pod_G, kMaxPod * kMaxPod));
   RK(dalloc(H, &H->pod_A, kMaxPod * kMaxPod));
   for (int a = 0; a < kMaxSpe; ++a) { RK(dalloc(H, &H->spe_D[a], L)); RK(dalloc(H, &H->spe_LD[a], L)); }
@@ -632,7 +651,8 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
     // (a6) history
     RK(history_push(H, H->x, H->lx, st));
     nl += history_launches(H);
-    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->dstats + s);
+    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
+                                   H->dstats + s);
     nl += 1;
     mark(H);
     if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }

@@ -66,15 +66,18 @@ __device__ __forceinline__ double ld(const double* __restrict__ v, int n, long l
   return v[c * n3 + pidx(n, i, j, k)];
 }
 
-struct SweepGroupSmem {
-  double fz[2][kGroupWarps][32];
-  double fx[2][kGroupWarps][32];
-  double hz[2][kTY];                    // x halo: bz, by at (i0 - 1, j0 + row)
-  double hy[2][kTY];
+template <class T>
+struct SweepGroupSmemT {
+  T fz[2][kGroupWarps][32];
+  T fx[2][kGroupWarps][32];
+  T hz[2][kTY];                         // x halo: bz, by at (i0 - 1, j0 + row)
+  T hy[2][kTY];
 };
-struct SweepSmem {
-  SweepGroupSmem g[kGroups];
+template <class T>
+struct SweepSmemT {
+  SweepGroupSmemT<T> g[kGroups];
 };
+using SweepSmem = SweepSmemT<double>;
 
 // barrier over the kGroupWarps warps of stencil group `grp` (ids 1.. ; 0 is __syncthreads)
 __device__ __forceinline__ void group_sync(int grp) {
@@ -92,22 +95,24 @@ __device__ __forceinline__ void group_sync(int grp) {
 // their own named barrier, so one group's plane step never waits for the other.  Index
 // arithmetic is 32-bit and incremental along the march (3 n^3 < 2^31 for
 // n <= 800); bounds tests are hoisted out of the plane loop.
+// Templated on the value type T (double for the FP64 path, float for the
+// inner solves of the mixed-precision path); arithmetic is in T.
 // Must be called by all kBlock threads of the block.
-template <class Epi>
-__device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& box, int part, int nparts,
-                        SweepSmem& sm, Epi& epi) {
+template <class T, class Epi>
+__device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, int part, int nparts,
+                        SweepSmemT<T>& sm, Epi& epi) {
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
   const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
-  SweepGroupSmem& sg = sm.g[grp];
+  SweepGroupSmemT<T>& sg = sm.g[grp];
   const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
-  const long long T = (long long)ntx * nty * nz;
+  const long long ntiles = (long long)ntx * nty * nz;
   const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
-  long long u = T * gp / gn;
-  const long long u1 = T * (gp + 1) / gn;
+  long long u = ntiles * gp / gn;
+  const long long u1 = ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
   while (u < u1) {
     const long long tc = u / nz;
@@ -130,18 +135,18 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
       const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
       const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
       const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
-      const double* __restrict__ sx_ = s;
-      const double* __restrict__ sy_ = s + n3;
-      const double* __restrict__ sz_ = s + 2 * n3;
+      const T* __restrict__ sx_ = s;
+      const T* __restrict__ sy_ = s + n3;
+      const T* __restrict__ sz_ = s + 2 * n3;
       int o = col ? i + n * (j + n * ks) : 0;     // position of plane ks
       // all loads of the segment start issued together: warm-up plane ks - 1,
       // plane ks (own, x+1 and y+1 neighbours) and own values of plane ks + 1
       const bool wu = (ks >= 1) && col;
       const int om = o - n2;
-      const double xm = wu ? sx_[om] : 0.0, ym = wu ? sy_[om] : 0.0, zm = wu ? sz_[om] : 0.0;
-      const double zim = (wu && vi1) ? sz_[om + 1] : 0.0, zjm = (wu && vj1) ? sz_[om + n] : 0.0;
-      double x0 = 0.0, y0 = 0.0, z0 = 0.0;
-      double yi = 0.0, zi = 0.0, xj = 0.0, zj = 0.0, xk = 0.0, yk = 0.0, zk = 0.0;
+      const T xm = wu ? sx_[om] : T(0), ym = wu ? sy_[om] : T(0), zm = wu ? sz_[om] : T(0);
+      const T zim = (wu && vi1) ? sz_[om + 1] : T(0), zjm = (wu && vj1) ? sz_[om + n] : T(0);
+      T x0 = 0, y0 = 0, z0 = 0;
+      T yi = 0, zi = 0, xj = 0, zj = 0, xk = 0, yk = 0, zk = 0;
       if (col) {
         x0 = sx_[o]; y0 = sy_[o]; z0 = sz_[o];
         if (vi1) { yi = sy_[o + 1]; zi = sz_[o + 1]; }
@@ -150,7 +155,7 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
       }
       if (act) epi.prefetch(o);
       // warm-up fluxes bx, by at plane ks - 1 (zero when ks = 0: unused there)
-      double bxm = 0.0, bym = 0.0;
+      T bxm = 0, bym = 0;
       if (wu) {
         bxm = (ym - zm) + (zjm - y0);
         bym = (zm - xm) + (x0 - zim);
@@ -158,14 +163,14 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
       int buf = 0;
       for (int k = ks; k < ke; ++k, o += n2) {
         // issue the next plane's loads first
-        double nyi = 0.0, nzi = 0.0, nxj = 0.0, nzj = 0.0, nxk = 0.0, nyk = 0.0, nzk = 0.0;
+        T nyi = 0, nzi = 0, nxj = 0, nzj = 0, nxk = 0, nyk = 0, nzk = 0;
         const int o1 = o + n2;
         if (col && k + 1 < ke) {
           if (vi1) { nyi = sy_[o1 + 1]; nzi = sz_[o1 + 1]; }
           if (vj1) { nxj = sx_[o1 + n]; nzj = sz_[o1 + n]; }
           if (k + 2 < n) { nxk = sx_[o1 + n2]; nyk = sy_[o1 + n2]; nzk = sz_[o1 + n2]; }
         }
-        double bx = 0.0, by = 0.0, bz = 0.0;
+        T bx = 0, by = 0, bz = 0;
         if (col) {
           bx = (y0 - z0) + (zj - yk);
           by = (z0 - x0) + (xk - zi);
@@ -174,13 +179,13 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
         group_sync(grp);
-        double bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
+        T bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
-        const double bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
+        const T bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {
-          const double tx = (bz - bzj) + (bym - by);
-          const double ty = (bzi - bz) + (bx - bxm);
-          const double tz = (bxj - bx) + (by - byi);
+          const T tx = (bz - bzj) + (bym - by);
+          const T ty = (bzi - bz) + (bx - bxm);
+          const T tz = (bxj - bx) + (by - byi);
           unsigned m = mcol & (k > 0 ? 7u : 4u);
           if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
           epi(o, m, tx, ty, tz, x0, y0, z0);
@@ -200,39 +205,39 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
       const int jr = j0 + lane;
       const bool hcol = (i0 >= 1) && (lane < kTY) && (jr < n);
       const bool hi1 = hrow && (i + 1 < n), hj1 = hcol && (jr + 1 < n);
-      const double* __restrict__ sx_ = s;
-      const double* __restrict__ sy_ = s + n3;
-      const double* __restrict__ sz_ = s + 2 * n3;
+      const T* __restrict__ sx_ = s;
+      const T* __restrict__ sy_ = s + n3;
+      const T* __restrict__ sz_ = s + 2 * n3;
       int oh = hrow ? i + n * (jh + n * ks) : 0;          // halo row position, plane ks
       int oc = hcol ? (i0 - 1) + n * (jr + n * ks) : 0;   // halo column position, plane ks
-      double a[7], c[8];
-      auto load_row = [&](int k, int o, double* v) {
+      T a[7], c[8];
+      auto load_row = [&](int k, int o, T* v) {
         v[0] = sx_[o]; v[1] = sy_[o]; v[2] = sz_[o];
-        v[3] = hi1 ? sy_[o + 1] : 0.0;
+        v[3] = hi1 ? sy_[o + 1] : T(0);
         v[4] = sx_[o + n]; v[5] = sz_[o + n];
-        v[6] = (k + 1 < n) ? sy_[o + n2] : 0.0;
+        v[6] = (k + 1 < n) ? sy_[o + n2] : T(0);
       };
-      auto load_col = [&](int k, int o, double* v) {
+      auto load_col = [&](int k, int o, T* v) {
         v[0] = sx_[o]; v[1] = sy_[o + 1];
-        v[2] = hj1 ? sx_[o + n] : 0.0;
+        v[2] = hj1 ? sx_[o + n] : T(0);
         v[3] = sy_[o]; v[4] = sz_[o];
-        v[5] = (k + 1 < n) ? sx_[o + n2] : 0.0;
+        v[5] = (k + 1 < n) ? sx_[o + n2] : T(0);
         v[6] = sz_[o + 1];
-        v[7] = 0.0;
+        v[7] = T(0);
       };
 #pragma unroll
-      for (int q = 0; q < 7; ++q) a[q] = 0.0;
+      for (int q = 0; q < 7; ++q) a[q] = T(0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) c[q] = 0.0;
+      for (int q = 0; q < 8; ++q) c[q] = T(0);
       if (hrow) load_row(ks, oh, a);
       if (hcol) load_col(ks, oc, c);
       int buf = 0;
       for (int k = ks; k < ke; ++k) {
-        double na[7], nc[8];
+        T na[7], nc[8];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) na[q] = 0.0;
+        for (int q = 0; q < 7; ++q) na[q] = T(0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) nc[q] = 0.0;
+        for (int q = 0; q < 8; ++q) nc[q] = T(0);
         if (k + 1 < ke) {
           if (hrow) load_row(k + 1, oh + n2, na);
           if (hcol) load_col(k + 1, oc + n2, nc);
@@ -240,12 +245,12 @@ __device__ void sweep_L(const Geom& g, const double* __restrict__ s, const Box& 
         oh += n2;
         oc += n2;
         // bz = x + y(i+1) - x(j+1) - y ; bx = y + z(j+1) - y(k+1) - z
-        sg.fz[buf][0][lane] = hrow ? (a[0] - a[1]) + (a[3] - a[4]) : 0.0;
-        sg.fx[buf][0][lane] = hrow ? (a[1] - a[2]) + (a[5] - a[6]) : 0.0;
+        sg.fz[buf][0][lane] = hrow ? (a[0] - a[1]) + (a[3] - a[4]) : T(0);
+        sg.fx[buf][0][lane] = hrow ? (a[1] - a[2]) + (a[5] - a[6]) : T(0);
         if (lane < kTY) {
           // bz = x + y(i0) - x(j+1) - y ; by = z + x(k+1) - z(i0) - x
-          sg.hz[buf][lane] = hcol ? (c[0] - c[3]) + (c[1] - c[2]) : 0.0;
-          sg.hy[buf][lane] = hcol ? (c[4] - c[0]) + (c[5] - c[6]) : 0.0;
+          sg.hz[buf][lane] = hcol ? (c[0] - c[3]) + (c[1] - c[2]) : T(0);
+          sg.hy[buf][lane] = hcol ? (c[4] - c[0]) + (c[5] - c[6]) : T(0);
         }
         group_sync(grp);
 #pragma unroll

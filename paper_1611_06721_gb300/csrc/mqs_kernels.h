@@ -23,6 +23,12 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
                cudaStream_t st, int init = 0);
 int pcg_max_blocks(int* nblk);
 
+// mixed precision: FP64 iterative refinement around FP32 CG inner solves
+struct MixedBufs { float* r32; float* p32; float* q32; float* d32; };
+int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
+                     double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0);
+
 // one-reduction PCG (one fused stencil pass and one grid reduction per
 // iteration); needs five more layout vectors
 struct PcgExtra { double* r1; double* w0; double* w1; double* s0; double* s1; };

@@ -1,0 +1,238 @@
+// Mixed-precision solve of K_n x = b: FP64 iterative refinement around FP32
+// conjugate-gradient inner solves, as one persistent cooperative kernel.
+//
+// Outer (FP64): r = b - L x by the FP64 stencil (which also yields L x for the
+// start-vector history), ||r||, convergence test ||r|| <= tol ||b||, and the
+// update x += ||r|| d.  Inner (FP32): CG on L d = r/||r|| with the stencil,
+// vectors and products in FP32 (on this GPU FP32 arithmetic is 64x faster
+// than FP64), each dot product's per-thread partial sums in FP32 and its
+// cross-thread sum in FP64; it stops once its residual has dropped by
+// max(inner_tol, tol ||b|| / (2 ||r||)), i.e. as soon as the outer tolerance
+// can be met, or when FP32 stagnates.  Jacobi is folded into the scaling as
+// in the FP64 kernel (diag(K_n) is uniform).
+#include <cmath>
+#include "mqs_internal.cuh"
+#include "mqs_kernels.h"
+
+namespace mqs {
+
+struct MixedArgs {
+  Geom g;
+  Box full;
+  const double* b;
+  double* x;
+  double* r;
+  double* lx;
+  float* r32;
+  float* p32;
+  float* q32;
+  float* d32;
+  double* part;
+  unsigned* bar;
+  int* err;
+  PcgResult* out;
+  int* refinements;     // number of FP64 residual evaluations after the first
+  double tol2;
+  double inner_tol;
+  int maxit;            // cap on the total inner iterations
+  long long spin;
+  int init;             // as in the FP64 kernel: 0 stencil, 2 zero start
+};
+
+struct EpiResidualM {   // r = b - t, lx = t on n-edges; sums r.r and b.b (FP64)
+  const double* b; double* r; double* lx; long long n3;
+  double rr = 0.0, bb = 0.0;
+  double bp[3];
+  __device__ void prefetch(long long e) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bp[c] = b[e + c * n3];
+  }
+  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
+    const double t[3] = {tx, ty, tz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long idx = e + c * n3;
+      if (m >> c & 1u) {
+        const double bv = bp[c];
+        const double rv = bv - t[c];
+        r[idx] = rv; lx[idx] = t[c];
+        rr = fma(rv, rv, rr); bb = fma(bv, bv, bb);
+      } else {
+        r[idx] = 0.0; lx[idx] = 0.0;
+      }
+    }
+  }
+};
+
+struct EpiDirection32 {  // q = t + beta q, p = r + beta p on n-edges (FP32); sums p.q
+  float* p; float* q; long long n3; float beta; bool first;
+  float pq = 0.f;
+  float pp[3], qp[3];
+  __device__ void prefetch(long long e) {
+    if (first) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { pp[c] = p[e + c * n3]; qp[c] = q[e + c * n3]; }
+  }
+  __device__ void operator()(long long e, unsigned m, float tx, float ty, float tz, float sx, float sy, float sz) {
+    const float t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long idx = e + c * n3;
+      float qn = 0.f, pn = 0.f;
+      if (m >> c & 1u) {
+        qn = first ? t[c] : fmaf(beta, qp[c], t[c]);
+        pn = first ? s[c] : fmaf(beta, pp[c], s[c]);
+        pq = fmaf(pn, qn, pq);
+      }
+      q[idx] = qn; p[idx] = pn;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(MixedArgs a) {
+  __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; } sm;
+  __shared__ double red[2 * 32];
+  __shared__ double gs[2];
+  const int nb = gridDim.x, bid = blockIdx.x;
+  unsigned nbar = 0;
+  int slot = 0;
+  const long long len = 3 * a.g.n3;
+  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
+  auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
+    double v[2] = {v0, v1};
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
+    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
+    if (threadIdx.x < 32) {
+      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
+      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
+    }
+    __syncthreads();
+    s0 = gs[0]; s1 = gs[1];
+    slot ^= 1;
+    return true;
+  };
+  int status = MQS_OK, inner_total = 0, outer = 0;
+  double bb = 0.0, start_rel = 0.0, relres = 0.0;
+  if (a.init == 2) {
+    for (long long e = tid; e < len; e += nth) a.x[e] = 0.0;
+    double d0, d1;
+    if (!reduce2(0.0, 0.0, d0, d1)) return;   // x visible before the first residual
+  }
+  for (;;) {
+    // FP64 residual r = b - L x, its norm and L x
+    double rr;
+    {
+      EpiResidualM ep{a.b, a.r, a.lx, a.g.n3};
+      sweep_L<double>(a.g, a.x, a.full, bid, nb, sm.d, ep);
+      if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
+    }
+    if (outer == 0) {
+      if (bb == 0.0) {
+        for (long long e = tid; e < len; e += nth) { a.x[e] = 0.0; a.r[e] = 0.0; a.lx[e] = 0.0; }
+        if (bid == 0 && threadIdx.x == 0) { *a.out = PcgResult{0, MQS_OK, 0.0, 0.0}; *a.refinements = 0; }
+        return;
+      }
+      start_rel = sqrt(rr / bb);
+    }
+    relres = sqrt(rr / bb);
+    if (!isfinite(rr) || !isfinite(bb)) { status = MQS_ERR_NAN; break; }
+    if (rr <= a.tol2 * bb) { status = MQS_OK; break; }
+    if (inner_total >= a.maxit || outer >= 64) { status = MQS_ERR_NOT_CONVERGED; break; }
+    // inner FP32 CG on L d = r / ||r||
+    const double nr = sqrt(rr), inv = 1.0 / nr;
+    double rho;
+    {
+      float acc = 0.f;
+      for (long long e = tid; e < len; e += nth) {
+        const float v = (float)(a.r[e] * inv);
+        a.r32[e] = v;
+        a.d32[e] = 0.f;
+        acc = fmaf(v, v, acc);
+      }
+      double dummy;
+      if (!reduce2((double)acc, 0.0, rho, dummy)) return;
+    }
+    const double rho0 = rho;
+    const double target = fmax(a.inner_tol, 0.5 * sqrt(a.tol2 * bb) / nr);
+    const double stop2 = target * target * rho0;
+    float beta = 0.f;
+    bool first = true;
+    int it_in = 0;
+    while (inner_total < a.maxit) {
+      double pq, dummy;
+      {
+        EpiDirection32 ep{a.p32, a.q32, a.g.n3, beta, first};
+        sweep_L<float>(a.g, a.r32, a.full, bid, nb, sm.f, ep);
+        if (!reduce2((double)ep.pq, 0.0, pq, dummy)) return;
+      }
+      ++it_in; ++inner_total;
+      if (!(pq > 0.0)) break;                     // FP32 breakdown / stagnation: refine from here
+      const float alpha = (float)(rho / pq);
+      double rn;
+      {
+        float acc = 0.f;
+        const long long q4 = len >> 2;
+        float4* d4 = reinterpret_cast<float4*>(a.d32);
+        float4* r4 = reinterpret_cast<float4*>(a.r32);
+        const float4* p4 = reinterpret_cast<const float4*>(a.p32);
+        const float4* qq4 = reinterpret_cast<const float4*>(a.q32);
+        for (long long e = tid; e < q4; e += nth) {
+          const float4 pv = p4[e], qv = qq4[e];
+          float4 dv = d4[e], rv = r4[e];
+          dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
+          dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
+          rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
+          rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
+          d4[e] = dv; r4[e] = rv;
+          acc = fmaf(rv.x, rv.x, acc); acc = fmaf(rv.y, rv.y, acc);
+          acc = fmaf(rv.z, rv.z, acc); acc = fmaf(rv.w, rv.w, acc);
+        }
+        for (long long e = (q4 << 2) + tid; e < len; e += nth) {
+          a.d32[e] = fmaf(alpha, a.p32[e], a.d32[e]);
+          const float rv = fmaf(-alpha, a.q32[e], a.r32[e]);
+          a.r32[e] = rv;
+          acc = fmaf(rv, rv, acc);
+        }
+        if (!reduce2((double)acc, 0.0, rn, dummy)) return;
+      }
+      if (!isfinite(rn)) break;
+      if (rn <= stop2 || it_in >= 400) break;
+      beta = (float)(rn / rho);
+      rho = rn;
+      first = false;
+    }
+    // x += ||r|| d (FP64); barrier so the next residual sees every update
+    {
+      for (long long e = tid; e < len; e += nth) a.x[e] = fma(nr, (double)a.d32[e], a.x[e]);
+      double d0, d1;
+      if (!reduce2(0.0, 0.0, d0, d1)) return;
+    }
+    ++outer;
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    *a.out = PcgResult{inner_total, status, relres, start_rel};
+    *a.refinements = outer;
+  }
+}
+
+int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
+                     double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init) {
+  MixedArgs a;
+  a.g = dg.g;
+  a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
+  a.b = b; a.x = x; a.r = r; a.lx = lx;
+  a.r32 = mb.r32; a.p32 = mb.p32; a.q32 = mb.q32; a.d32 = mb.d32;
+  a.part = part; a.bar = bar; a.err = err; a.out = out; a.refinements = refinements;
+  a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
+  a.spin = 1ll << 21;
+  a.init = (init == 2) ? 2 : 0;
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
+}  // namespace mqs
