@@ -37,6 +37,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 FLOPS_PER_ITER = 16                                   # stencil 6 adds + 5 FMAs, per unknown
 FLOPS_PER_RESIDUAL = 9                                # stencil 6 + subtract 1 + FMA 2, per unknown
 BYTES_PER_ITER = 48                                   # x, r, p read and written once, per unknown
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2070 MHz
+# DRAM bytes (read + write) per launch of the PCG kernel on the 64^3 iron workload, from one
+# ncu capture of the current kernel build; keyed by (precision, pcg_variant).  The carried
+# vectors stay in L2, so the figure does not depend on the iteration count of the launch.
+PCG_TRAFFIC = {(0, 0): 12.753408e6 + 1.526528e6, (1, 0): 12.736768e6 + 1.789952e6}
 
 
 def measured_peaks():
@@ -226,7 +231,7 @@ def run_ours(args, rank, ws, local, dist):
         s.timing_enable(True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        iters, statuses = [], []
+        iters, statuses, refs = [], [], []
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
@@ -234,6 +239,7 @@ def run_ours(args, rank, ws, local, dist):
             ends[k].record(stream)
             iters.append(st[0].iterations)
             statuses.append(st[0].status)
+            refs.append(st[0].refinements)
         torch.cuda.synchronize(dev)
         clk = clocks.stop()
         ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
@@ -263,7 +269,22 @@ def run_ours(args, rank, ws, local, dist):
     n_n = s.n_n
     its = np.array(iters)
     flops = n_n * (FLOPS_PER_ITER * its.sum() + 2 * FLOPS_PER_RESIDUAL * len(its))
+    if args.precision == 1:
+        # inner FP32 iterations plus one FP64 residual per refinement
+        flops = n_n * (FLOPS_PER_ITER * its.sum() + FLOPS_PER_RESIDUAL * (len(its) + sum(refs)))
     achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
+    traffic = args.traffic if args.traffic is not None else PCG_TRAFFIC.get((args.precision, args.pcg_variant))
+    if args.precision == 0:
+        roof = {"bound": "alu", "kernel": "pcg_kernel" if args.pcg_variant == 0 else "pcg_fused_kernel",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "note": "FP64 FMA=2 flop; peak derived: 152 SM x 2 FMA/clk x 2 x 2070 MHz"}
+    else:
+        roof = {"bound": "alu", "kernel": "pcg_mixed_kernel", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": traffic,
+                "note": "FP32 inner iterations against the FP32 issue peak (152 SM x 128 FMA/clk x 2 x "
+                        "2070 MHz); the inner iteration is latency and grid-barrier bound"}
     hbm = n_n * BYTES_PER_ITER * its.sum() / (tm["ms_pcg"] * 1e-3) / 1e9
     peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
@@ -279,10 +300,7 @@ def run_ours(args, rank, ws, local, dist):
             "iters_per_step": float(its.mean()),
             "phases_ms_per_step": {k: tm[k] / args.steps for k in ("ms_rhs", "ms_start", "ms_pcg",
                                                                      "ms_conductor", "ms_history")},
-            "roofline": {"bound": "alu", "kernel": "pcg_kernel", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": args.traffic,
-                         "note": "FP64 FMA=2 flop; peak derived: 152 SM x 2 FMA/clk x 2 x 2070 MHz"},
+            "roofline": roof,
             "stencil_hbm_view": {"algorithmic_GBps": hbm, "peak_GBps": peaks.get("hbm_gbs"),
                                  "frac": hbm / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
                                  "note": "48 B/unknown/iteration; the 64^3 PCG working set is L2-resident"},

@@ -112,7 +112,9 @@ typedef struct {
     int    pcg_variant;   /* 0: two grid reductions per iteration (Hestenes-Stiefel
                              recurrences, default); 1: one reduction (Chronopoulos-
                              Gear recurrences, one fused stencil pass per
-                             iteration). Same iterates in exact arithmetic. */
+                             iteration). Same iterates in exact arithmetic.
+                             With precision 1 it selects the form of the FP32
+                             inner CG the same way. */
     int    precision;     /* 0: FP64 PCG (default); 1: FP64 iterative refinement
                              around FP32 CG inner solves (stencil, vectors and
                              products in FP32; residual, norms, convergence test

@@ -53,6 +53,7 @@ struct mqs_handle {
   bool lx_valid = false;   // lx holds L x for the step solution x
   double *r1 = nullptr, *w0 = nullptr, *w1 = nullptr, *s1 = nullptr;   // one-reduction PCG buffers
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;  // mixed precision
+  float *r32b = nullptr, *w32a = nullptr, *w32b = nullptr, *s32a = nullptr, *s32b = nullptr;  // its one-reduction form
   int* refin = nullptr;
   cudaStream_t own_st = nullptr;
   // timing
@@ -160,8 +161,10 @@ int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t
 }
 
 int ensure_mixed(mqs_handle* H) {
-  if (H->r32) return MQS_OK;
-  for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, H->len));
+  if (!H->r32)
+    for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, H->len));
+  if (H->opt.pcg_variant == 1 && !H->r32b)
+    for (float** v : {&H->r32b, &H->w32a, &H->w32b, &H->s32a, &H->s32b}) RK(dalloc(H, v, H->len));
   return MQS_OK;
 }
 
@@ -169,10 +172,10 @@ int ensure_mixed(mqs_handle* H) {
 int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init) {
   if (H->opt.precision == 1) {
     RK(ensure_mixed(H));
-    const MixedBufs mb{H->r32, H->p32, H->q32, H->d32};
+    const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-5;
     return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                            maxit, H->nblk, st, init);
+                            maxit, H->nblk, st, init, H->opt.pcg_variant);
   }
   if (H->opt.pcg_variant == 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};

@@ -24,10 +24,13 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
 int pcg_max_blocks(int* nblk);
 
 // mixed precision: FP64 iterative refinement around FP32 CG inner solves
-struct MixedBufs { float* r32; float* p32; float* q32; float* d32; };
+struct MixedBufs {
+  float* r32; float* p32; float* q32; float* d32;
+  float* r32b; float* w32a; float* w32b; float* s32a; float* s32b;   // one-reduction inner CG only
+};
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0);
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0, int variant = 0);
 
 // one-reduction PCG (one fused stencil pass and one grid reduction per
 // iteration); needs five more layout vectors

@@ -13,86 +13,100 @@
 
 namespace mqs {
 
-struct FusedVecs {
-  double* x;
-  double* p;
-  const double* r_in;   // r_i
-  const double* w_in;   // w_i = L r_i
-  const double* s_in;   // s_{i-1}
-  double* r_out;        // r_{i+1}
-  double* w_out;        // w_{i+1}
-  double* s_out;        // s_i
-  double alpha, beta;
+// fused multiply-add in the precision of the sweep
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class T>
+struct FusedVecsT {
+  T* x;
+  T* p;
+  const T* r_in;   // r_i
+  const T* w_in;   // w_i = L r_i
+  const T* s_in;   // s_{i-1}
+  T* r_out;        // r_{i+1}
+  T* w_out;        // w_{i+1}
+  T* s_out;        // s_i
+  T alpha, beta;
   bool first;           // beta = 0 and no previous p, s
 };
 
-struct FusedSmem {
+template <class T>
+struct FusedSmemT {
   // r_{i+1} of plane k (buffer k&1): rows j0-1 .. j0+kTY (index row+1),
   // columns i0-1 .. i0+32 (index lane+1), three components
-  double src[2][3][kTY + 2][34];
-  double fz[2][kTY + 1][32];      // bz, bx of rows j0-1 .. j0+kTY-1
-  double fx[2][kTY + 1][32];
-  double hz[2][kTY];              // x halo: bz, by at (i0 - 1, j0 + row)
-  double hy[2][kTY];
+  T src[2][3][kTY + 2][34];
+  T fz[2][kTY + 1][32];      // bz, bx of rows j0-1 .. j0+kTY-1
+  T fx[2][kTY + 1][32];
+  T hz[2][kTY];              // x halo: bz, by at (i0 - 1, j0 + row)
+  T hy[2][kTY];
 };
-struct FusedSmemBlock { FusedSmem g[kGroups]; };
+template <class T>
+struct FusedSmemBlockT { FusedSmemT<T> g[kGroups]; };
+using FusedVecs = FusedVecsT<double>;
+using FusedSmemBlock = FusedSmemBlockT<double>;
 
 // r_{i+1} at one component position from the input buffers (no writes)
-__device__ __forceinline__ double fused_src(const FusedVecs& v, int off) {
-  const double sv = v.first ? v.w_in[off] : fma(v.beta, v.s_in[off], v.w_in[off]);
-  return fma(-v.alpha, sv, v.r_in[off]);
+template <class T>
+__device__ __forceinline__ T fused_src(const FusedVecsT<T>& v, int off) {
+  const T sv = v.first ? v.w_in[off] : fmaT(v.beta, v.s_in[off], v.w_in[off]);
+  return fmaT(-v.alpha, sv, v.r_in[off]);
 }
 
 // Update of one owned position (3 components): writes p, x, s_out, r_out and
 // returns r_{i+1} in src[3].
-__device__ __forceinline__ void fused_update(const FusedVecs& v, int o, int n3, double* src) {
+template <class T>
+__device__ __forceinline__ void fused_update(const FusedVecsT<T>& v, int o, int n3, T* src) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int e = o + c * n3;
-    const double r = v.r_in[e], w = v.w_in[e];
-    const double s = v.first ? w : fma(v.beta, v.s_in[e], w);
-    const double p = v.first ? r : fma(v.beta, v.p[e], r);
-    const double x = v.x[e];
+    const T r = v.r_in[e], w = v.w_in[e];
+    const T s = v.first ? w : fmaT(v.beta, v.s_in[e], w);
+    const T p = v.first ? r : fmaT(v.beta, v.p[e], r);
+    const T x = v.x[e];
     v.s_out[e] = s;
     v.p[e] = p;
-    v.x[e] = fma(v.alpha, p, x);
-    const double rn = fma(-v.alpha, s, r);
+    v.x[e] = fmaT(v.alpha, p, x);
+    const T rn = fmaT(-v.alpha, s, r);
     v.r_out[e] = rn;
     src[c] = rn;
   }
 }
 
 // Loaded inputs of one position (3 components): r_i, w_i, s_{i-1}, p_{i-1}, x_i.
-struct FusedLoad {
-  double r[3], w[3], s[3], p[3], x[3];
+template <class T>
+struct FusedLoadT {
+  T r[3], w[3], s[3], p[3], x[3];
 };
 
-__device__ __forceinline__ void fused_load(const FusedVecs& v, int o, int n3, bool owned, FusedLoad& L) {
+template <class T>
+__device__ __forceinline__ void fused_load(const FusedVecsT<T>& v, int o, int n3, bool owned, FusedLoadT<T>& L) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int e = o + c * n3;
     L.r[c] = v.r_in[e];
     L.w[c] = v.w_in[e];
-    L.s[c] = v.first ? 0.0 : v.s_in[e];
-    L.p[c] = (owned && !v.first) ? v.p[e] : 0.0;
-    L.x[c] = owned ? v.x[e] : 0.0;
+    L.s[c] = v.first ? T(0) : v.s_in[e];
+    L.p[c] = (owned && !v.first) ? v.p[e] : T(0);
+    L.x[c] = owned ? v.x[e] : T(0);
   }
 }
 
 // r_{i+1} from loaded inputs; when owned also writes p, x, s_out, r_out
-__device__ __forceinline__ void fused_apply(const FusedVecs& v, int o, int n3, bool owned, const FusedLoad& L,
-                                            double* src) {
+template <class T>
+__device__ __forceinline__ void fused_apply(const FusedVecsT<T>& v, int o, int n3, bool owned, const FusedLoadT<T>& L,
+                                            T* src) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double sv = v.first ? L.w[c] : fma(v.beta, L.s[c], L.w[c]);
-    const double rn = fma(-v.alpha, sv, L.r[c]);
+    const T sv = v.first ? L.w[c] : fmaT(v.beta, L.s[c], L.w[c]);
+    const T rn = fmaT(-v.alpha, sv, L.r[c]);
     src[c] = rn;
     if (owned) {
       const int e = o + c * n3;
-      const double pv = v.first ? L.r[c] : fma(v.beta, L.p[c], L.r[c]);
+      const T pv = v.first ? L.r[c] : fmaT(v.beta, L.p[c], L.r[c]);
       v.s_out[e] = sv;
       v.p[e] = pv;
-      v.x[e] = fma(v.alpha, pv, L.x[c]);
+      v.x[e] = fmaT(v.alpha, pv, L.x[c]);
       v.r_out[e] = rn;
     }
   }
@@ -100,20 +114,21 @@ __device__ __forceinline__ void fused_apply(const FusedVecs& v, int o, int n3, b
 
 // One fused pass over `box` for group-part `part` of `nparts` (block level,
 // as in sweep_L).  Accumulates gamma and delta into the caller's registers.
-__device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, int part, int nparts,
-                            FusedSmemBlock& smb, double& gamma, double& delta) {
+template <class T>
+__device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& box, int part, int nparts,
+                            FusedSmemBlockT<T>& smb, T& gamma, T& delta) {
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
   const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
-  FusedSmem& sg = smb.g[grp];
+  FusedSmemT<T>& sg = smb.g[grp];
   const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
-  const long long T = (long long)ntx * nty * nz;
+  const long long ntiles = (long long)ntx * nty * nz;
   const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
-  long long u = T * gp / gn;
-  const long long u1 = T * (gp + 1) / gn;
+  long long u = ntiles * gp / gn;
+  const long long u1 = ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
   while (u < u1) {
     const long long tc = u / nz;
@@ -136,59 +151,59 @@ __device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, i
       const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
       int o = col ? i + n * (j + n * ks) : 0;
       // prologue: plane ks is owned -> update it; warm-up fluxes at ks - 1 from recomputed sources
-      double sk[3] = {0.0, 0.0, 0.0};
+      T sk[3] = {T(0), T(0), T(0)};
       if (act) fused_update(v, o, n3, sk);
       else if (col) { sk[0] = fused_src(v, o); sk[1] = fused_src(v, o + n3); sk[2] = fused_src(v, o + 2 * n3); }
 #pragma unroll
       for (int c = 0; c < 3; ++c) sg.src[ks & 1][c][w + 1][lane + 1] = sk[c];
-      double bxm = 0.0, bym = 0.0;
+      T bxm = T(0), bym = T(0);
       if (ks >= 1 && col) {
         const int om = o - n2;
-        const double xm = fused_src(v, om), ym = fused_src(v, om + n3), zm = fused_src(v, om + 2 * n3);
-        const double zim = (i + 1 < n) ? fused_src(v, om + 1 + 2 * n3) : 0.0;
-        const double zjm = (j + 1 < n) ? fused_src(v, om + n + 2 * n3) : 0.0;
+        const T xm = fused_src(v, om), ym = fused_src(v, om + n3), zm = fused_src(v, om + 2 * n3);
+        const T zim = (i + 1 < n) ? fused_src(v, om + 1 + 2 * n3) : T(0);
+        const T zjm = (j + 1 < n) ? fused_src(v, om + n + 2 * n3) : T(0);
         bxm = (ym - zm) + (zjm - sk[1]);
         bym = (zm - xm) + (sk[0] - zim);
       }
       group_sync(grp);
       // inputs of plane ks+1, loaded ahead of use
-      FusedLoad ld1;
+      FusedLoadT<T> ld1;
       if (col && ks + 1 < n) fused_load(v, o + n2, n3, act && ks + 1 < ke, ld1);
       int buf = ks & 1;
       for (int k = ks; k < ke; ++k, o += n2) {
         const int nb = buf ^ 1;
         // own r_{i+1} of plane k+1 from the inputs loaded during the previous step
-        double sk1[3] = {0.0, 0.0, 0.0};
+        T sk1[3] = {T(0), T(0), T(0)};
         if (col && k + 1 < n) fused_apply(v, o + n2, n3, act && k + 1 < ke, ld1, sk1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) sg.src[nb][c][w + 1][lane + 1] = sk1[c];
         // then issue the loads of plane k+2
         if (col && k + 2 < n && k + 1 < ke) fused_load(v, o + 2 * n2, n3, act && k + 2 < ke, ld1);
         // fluxes at plane k: own (k, k+1), x+1 and y+1 neighbours of plane k from smem
-        const double yi = sg.src[buf][1][w + 1][lane + 2], zi = sg.src[buf][2][w + 1][lane + 2];
-        const double xj = sg.src[buf][0][w + 2][lane + 1], zj = sg.src[buf][2][w + 2][lane + 1];
-        const double bx = (sk[1] - sk[2]) + (zj - sk1[1]);
-        const double by = (sk[2] - sk[0]) + (sk1[0] - zi);
-        const double bz = (sk[0] - sk[1]) + (yi - xj);
+        const T yi = sg.src[buf][1][w + 1][lane + 2], zi = sg.src[buf][2][w + 1][lane + 2];
+        const T xj = sg.src[buf][0][w + 2][lane + 1], zj = sg.src[buf][2][w + 2][lane + 1];
+        const T bx = (sk[1] - sk[2]) + (zj - sk1[1]);
+        const T by = (sk[2] - sk[0]) + (sk1[0] - zi);
+        const T bz = (sk[0] - sk[1]) + (yi - xj);
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
         group_sync(grp);
-        double bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
+        T bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
-        const double bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
+        const T bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {
-          const double tx = (bz - bzj) + (bym - by);
-          const double ty = (bzi - bz) + (bx - bxm);
-          const double tz = (bxj - bx) + (by - byi);
+          const T tx = (bz - bzj) + (bym - by);
+          const T ty = (bzi - bz) + (bx - bxm);
+          const T tz = (bxj - bx) + (by - byi);
           unsigned m = mcol & (k > 0 ? 7u : 4u);
           if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
-          const double t[3] = {tx, ty, tz};
+          const T t[3] = {tx, ty, tz};
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const double wv = (m >> c & 1u) ? t[c] : 0.0;
+            const T wv = (m >> c & 1u) ? t[c] : T(0);
             v.w_out[o + c * n3] = wv;
-            gamma = fma(sk[c], sk[c], gamma);
-            delta = fma(wv, sk[c], delta);
+            gamma = fmaT(sk[c], sk[c], gamma);
+            delta = fmaT(wv, sk[c], delta);
           }
         }
         bxm = bx; bym = by;
@@ -210,7 +225,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, i
       // per lane up to three halo slots; their (r, w, s) inputs are loaded one
       // plane ahead of use
       constexpr int kHS = (kSlots + 31) / 32;
-      struct HaloIn { double r[3], w[3], s[3]; };
+      struct HaloIn { T r[3], w[3], s[3]; };
       auto halo_load = [&](int kk, HaloIn* hin) {
 #pragma unroll
         for (int q = 0; q < kHS; ++q) {
@@ -221,9 +236,9 @@ __device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, i
           const int oo = ok ? hi + n * (hj + n * kk) : 0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : 0.0;
-            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : 0.0;
-            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : 0.0;
+            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : T(0);
+            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : T(0);
+            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : T(0);
           }
         }
       };
@@ -236,8 +251,8 @@ __device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, i
           slot_pos(sl, hi, hj, row, cl);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const double sv = v.first ? hin[q].w[c] : fma(v.beta, hin[q].s[c], hin[q].w[c]);
-            sg.src[bufw][c][row][cl] = fma(-v.alpha, sv, hin[q].r[c]);
+            const T sv = v.first ? hin[q].w[c] : fmaT(v.beta, hin[q].s[c], hin[q].w[c]);
+            sg.src[bufw][c][row][cl] = fmaT(-v.alpha, sv, hin[q].r[c]);
           }
         }
       };
@@ -255,24 +270,24 @@ __device__ void sweep_fused(const Geom& g, const FusedVecs& v, const Box& box, i
         __syncwarp();
         // row j0-1 at column i: bz = x + y(i+1) - x(j0) - y ; bx = y + z(j0) - y(k+1) - z
         {
-          const double x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
-          const double z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
-          const double xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
-          const double yk = sg.src[nb][1][0][lane + 1];
+          const T x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
+          const T z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
+          const T xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
+          const T yk = sg.src[nb][1][0][lane + 1];
           const bool hrow = (j0 >= 1) && (i < n);
-          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : 0.0;
-          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : 0.0;
+          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : T(0);
+          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : T(0);
         }
         // column i0-1 at row r: bz = x + y(i0) - x(j+1) - y ; by = z + x(k+1) - z(i0) - x
         if (lane < kTY) {
           const int r = lane + 1;
-          const double x0 = sg.src[buf][0][r][0], y0 = sg.src[buf][1][r][0], z0 = sg.src[buf][2][r][0];
-          const double yi = sg.src[buf][1][r][1], zi = sg.src[buf][2][r][1];
-          const double xj = sg.src[buf][0][r + 1][0];
-          const double xk = sg.src[nb][0][r][0];
+          const T x0 = sg.src[buf][0][r][0], y0 = sg.src[buf][1][r][0], z0 = sg.src[buf][2][r][0];
+          const T yi = sg.src[buf][1][r][1], zi = sg.src[buf][2][r][1];
+          const T xj = sg.src[buf][0][r + 1][0];
+          const T xk = sg.src[nb][0][r][0];
           const bool hcol = (i0 >= 1) && (j0 + lane < n);
-          sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : 0.0;
-          sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : 0.0;
+          sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : T(0);
+          sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : T(0);
         }
         group_sync(grp);
         buf = nb;

@@ -13,6 +13,7 @@
 #include <cmath>
 #include "mqs_internal.cuh"
 #include "mqs_kernels.h"
+#include "pcg_fused.cuh"
 
 namespace mqs {
 
@@ -27,6 +28,12 @@ struct MixedArgs {
   float* p32;
   float* q32;
   float* d32;
+  float* r32b;          // variant 1: second r buffer, w = L r and s = L p (both double-buffered)
+  float* w32a;
+  float* w32b;
+  float* s32a;
+  float* s32b;
+  int variant;          // inner CG: 0 two reductions per iteration, 1 one reduction (Chronopoulos-Gear)
   double* part;
   unsigned* bar;
   int* err;
@@ -89,8 +96,23 @@ struct EpiDirection32 {  // q = t + beta q, p = r + beta p on n-edges (FP32); su
   }
 };
 
+struct EpiApplyDot32 {  // w = t on n-edges (0 elsewhere, FP32); sums w.r with r the source values
+  float* w; long long n3;
+  float wr = 0.f;
+  __device__ void prefetch(long long) {}
+  __device__ void operator()(long long e, unsigned m, float tx, float ty, float tz, float sx, float sy, float sz) {
+    const float t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float wv = (m >> c & 1u) ? t[c] : 0.f;
+      w[e + c * n3] = wv;
+      wr = fmaf(wv, s[c], wr);
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(MixedArgs a) {
-  __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; } sm;
+  __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; FusedSmemBlockT<float> ff; } sm;
   __shared__ double red[2 * 32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
@@ -160,7 +182,41 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
     float beta = 0.f;
     bool first = true;
     int it_in = 0;
-    while (inner_total < a.maxit) {
+    if (a.variant == 1) {
+      // one reduction per inner iteration: w = L r once, then fused passes
+      // (p, s, d, r updates + w = L r_new + gamma, delta) with r, w, s double-buffered
+      auto rbuf = [&](int c) { return c ? a.r32b : a.r32; };
+      auto wbuf = [&](int c) { return c ? a.w32b : a.w32a; };
+      auto sbuf = [&](int c) { return c ? a.s32b : a.s32a; };
+      int cur = 0;
+      double delta, dummy;
+      {
+        EpiApplyDot32 ep{wbuf(0), a.g.n3};
+        sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
+        if (!reduce2((double)ep.wr, 0.0, delta, dummy)) return;
+      }
+      double gamma = rho;
+      bool ok = delta > 0.0;
+      double alpha = ok ? gamma / delta : 0.0, bet = 0.0;
+      while (ok && inner_total < a.maxit) {
+        FusedVecsT<float> v{a.d32, a.p32, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1),
+                            sbuf(cur ^ 1), (float)alpha, (float)bet, first};
+        float g1 = 0.f, d1 = 0.f;
+        sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
+        double gn, dn;
+        if (!reduce2((double)g1, (double)d1, gn, dn)) return;
+        ++it_in; ++inner_total;
+        cur ^= 1;
+        if (!isfinite(gn) || !isfinite(dn)) break;
+        if (gn <= stop2 || it_in >= 400) break;
+        const double bnew = gn / gamma;
+        const double den = dn - bnew * gn / alpha;
+        if (!(den > 0.0)) break;                  // FP32 breakdown / stagnation: refine from here
+        bet = bnew; alpha = gn / den; gamma = gn;
+        first = false;
+      }
+    }
+    while (a.variant == 0 && inner_total < a.maxit) {
       double pq, dummy;
       {
         EpiDirection32 ep{a.p32, a.q32, a.g.n3, beta, first};
@@ -219,12 +275,14 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
 
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init) {
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
   a.b = b; a.x = x; a.r = r; a.lx = lx;
   a.r32 = mb.r32; a.p32 = mb.p32; a.q32 = mb.q32; a.d32 = mb.d32;
+  a.r32b = mb.r32b; a.w32a = mb.w32a; a.w32b = mb.w32b; a.s32a = mb.s32a; a.s32b = mb.s32b;
+  a.variant = (variant == 1 && mb.r32b && mb.w32a && mb.w32b && mb.s32a && mb.s32b) ? 1 : 0;
   a.part = part; a.bar = bar; a.err = err; a.out = out; a.refinements = refinements;
   a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
   a.spin = 1ll << 21;

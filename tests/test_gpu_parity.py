@@ -327,10 +327,11 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant):
 
 
 # ---- mixed precision: FP32 inner solves inside FP64 refinement (same FP64 residual test) ----------
-def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, variant):
     p = W.scaled_nonlinear(35)
     d = O.Discretization(p)
-    s = make(pkg, p, precision=1)
+    s = make(pkg, p, precision=1, pcg_variant=variant)
     b_n = 3.0 * d.X_s[d.n_idx] - d.K_cn.T @ (W.random_vector(2, d.n_c) * 1e-9)
     b_o = np.zeros(d.grid.n_edges)
     b_o[d.n_idx] = b_n
@@ -343,26 +344,31 @@ def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg):
     s.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_SPE, "spe8")])
-def test_mixed_precision_steps_match_the_oracle(pkg, mode, name):
+def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, variant):
     g = golden()
     p = W.config_linear_block()
-    s = make(pkg, p, start_mode=mode, spe_depth=8, dt=g["dt"], tol=1e-10, precision=1)
+    s = make(pkg, p, start_mode=mode, spe_depth=8, dt=g["dt"], tol=1e-10, precision=1, pcg_variant=variant)
     stats = s.mqs_step(g["steps"])
     a_c, _, _ = s.get_state()
     err = rel(a_c, np.array(g["runs"][name]["a_c"]))
     assert err < 1e-8, err           # the mixed-precision bar is 1e-6; the FP64 residual test keeps it at 1e-8
     assert all(st.status == 0 and st.relres <= 1e-10 for st in stats)
-    assert sum(st.refinements for st in stats) >= len(stats) // 2    # most steps refine at least once
+    # a step that ran inner FP32 iterations applied at least one FP64 correction; a good SPE start
+    # often meets the FP64 test at the first residual and needs none
+    assert all(st.refinements >= 1 for st in stats if st.iterations > 0)
+    assert sum(st.refinements for st in stats) >= 1
     s.close()
 
 
-def test_mixed_precision_full_size_agrees_with_fp64(pkg):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_precision_full_size_agrees_with_fp64(pkg, variant):
     p = W.config_nonlinear_iron()
     d = O.Discretization(p)
     dt = O.dt_gershgorin(d)
     s64 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
-    s32 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=1)
+    s32 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=1, pcg_variant=variant)
     s64.mqs_step(30)
     st = s32.mqs_step(30)
     a64, _, _ = s64.get_state()
