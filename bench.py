@@ -33,6 +33,18 @@ if ROOT not in sys.path:
 
 METRIC = "explicit time steps/sec and PCG iters/step at rel-residual 1e-10; stencil HBM GB/s vs peak"
 WORKLOAD = "nonlinear-iron-64^3 (Brauer iron 24x24x16, sigma 2e6 S/m, coil 40x40 at z=32, 500 A 50 Hz)"
+
+
+def workload_name(p):
+    """Name of a scaled iron workload, from its description."""
+    import numpy as np
+    if p.N == 64:
+        return WORKLOAD
+    nz = np.nonzero(p.sigma_cell)
+    ext = [int(a.max() - a.min() + 1) for a in (nz[2], nz[1], nz[0])]
+    sig = float(p.sigma_cell[nz].max())
+    return (f"nonlinear-iron-{p.N}^3 (Brauer iron {ext[0]}x{ext[1]}x{ext[2]}, sigma {sig:.0e} S/m, "
+            f"coil {p.coil_i1 - p.coil_i0}x{p.coil_j1 - p.coil_j0} at z={p.coil_k}, {p.amplitude:g} A 50 Hz)")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FLOPS_PER_ITER = 16                                   # stencil 6 adds + 5 FMAs, per unknown
 FLOPS_PER_RESIDUAL = 9                                # stencil 6 + subtract 1 + FMA 2, per unknown
@@ -205,16 +217,23 @@ def run_ours(args, rank, ws, local, dist):
     import workloads as W
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    p = W.config_nonlinear_iron()
-    opts = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, pcg_variant=args.pcg_variant,
+    p = W.config_nonlinear_iron() if args.grid == 64 else W.scaled_nonlinear(args.grid)
+    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD}[args.start]
+    depth = args.depth if args.depth else (8 if args.start == "spe" else 20)
+    opts = pkg.SolverOptions(tol=1e-10, start_mode=mode,
+                             spe_depth=depth if args.start == "spe" else 8,
+                             pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
                              precision=args.precision)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
     # setup: dt = 0.9 * 2 / lambda_max(M_c^-1 K_S) by the power method (eq. (CFL))
     t0 = time.perf_counter()
-    lam, pit = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
-    dt = 0.9 * 2.0 / lam
+    if args.dt > 0:
+        lam, pit, dt = None, 0, args.dt                    # given step (no power method)
+    else:
+        lam, pit = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
+        dt = 0.9 * 2.0 / lam
     s.set_dt(dt)
     setup_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -273,7 +292,9 @@ def run_ours(args, rank, ws, local, dist):
         # inner FP32 iterations plus one FP64 residual per refinement
         flops = n_n * (FLOPS_PER_ITER * its.sum() + FLOPS_PER_RESIDUAL * (len(its) + sum(refs)))
     achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
-    traffic = args.traffic if args.traffic is not None else PCG_TRAFFIC.get((args.precision, args.pcg_variant))
+    traffic = args.traffic
+    if traffic is None and args.start == "spe" and depth == 8:
+        traffic = PCG_TRAFFIC.get((args.precision, args.pcg_variant))
     if args.precision == 0:
         roof = {"bound": "alu", "kernel": "pcg_kernel" if args.pcg_variant == 0 else "pcg_fused_kernel",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -291,9 +312,10 @@ def run_ours(args, rank, ws, local, dist):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": 64, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
+            "config": {"workload": workload_name(p), "grid": p.N, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
-                       "start_vector": "spe8", "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
+                       "start_vector": args.start + (str(depth) if args.start in ("spe", "pod") else ""),
+                       "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
                        "pcg": "two reductions per iteration" if args.pcg_variant == 0 else "one reduction per iteration",
                        "l2": "flushed between timed steps by a 256 MiB write",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
@@ -309,7 +331,7 @@ def run_ours(args, rank, ws, local, dist):
             "setup": {"power_iterations": pit, "seconds": setup_s}}
     if e2e:
         line["e2e"] = e2e
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu and args.grid == 64:
         try:
             c = run_oracle_subprocess(args.cpu_steps, args.cpu_budget)
             line["cpu_baseline"] = {"value": c["steps_per_s"], "unit": "steps/s", "cores": c["threads"],
@@ -324,28 +346,87 @@ def run_ours(args, rank, ws, local, dist):
     s.close()
 
 
+def coil_rhs(p, amp=100.0):
+    """Right-hand side amp * X_s (the coil loop) in the device layout."""
+    import numpy as np
+    n = p.N
+    b = np.zeros(3 * n ** 3)
+    k = p.coil_k
+    for i in range(p.coil_i0, p.coil_i1):
+        b[i + n * (p.coil_j0 + n * k)] += amp
+        b[i + n * (p.coil_j1 + n * k)] -= amp
+    for j in range(p.coil_j0, p.coil_j1):
+        b[n ** 3 + p.coil_i1 + n * (j + n * k)] += amp
+        b[n ** 3 + p.coil_i0 + n * (j + n * k)] -= amp
+    return b
+
+
 def single_solve():
     """One zero-start PCG solve of K_n w = 100 X_s on the workload (twice)."""
-    import numpy as np
     import __graft_entry__ as g
     g.build()
     import paper_1611_06721_gb300 as pkg
     import workloads as W
     p = W.config_nonlinear_iron()
     s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7))
-    n = p.N
-    b = np.zeros(3 * n ** 3)
-    k = p.coil_k
-    for i in range(p.coil_i0, p.coil_i1):          # coil loop in the device layout
-        b[i + n * (p.coil_j0 + n * k)] += 100.0
-        b[i + n * (p.coil_j1 + n * k)] -= 100.0
-    for j in range(p.coil_j0, p.coil_j1):
-        b[n ** 3 + p.coil_i1 + n * (j + n * k)] += 100.0
-        b[n ** 3 + p.coil_i0 + n * (j + n * k)] -= 100.0
+    b = coil_rhs(p)
     for _ in range(2):
         x, info = s.pcg_solve(b, tol=1e-10)
     print(json.dumps({"iterations": info.iterations, "relres": info.relres}))
     s.close()
+
+
+def size_sweep(sizes):
+    """Zero-start solves of K_n w = 100 X_s on the scaled iron workload at each grid
+    size, FP64 and mixed precision (one-reduction FP32 inner CG): time per PCG
+    iteration and the algorithmic bytes an iteration moves (x, r, p read and written
+    once: 48 B per unknown in FP64, 24 B in FP32), against the measured copy bandwidth.
+    The 64^3 vectors stay in L2; from 128^3 on the carried vectors exceed it.  One
+    JSON line per (size, precision)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = measured_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for n in sizes:
+        p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
+        for prec in (0, 1):
+            s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
+                                                             pcg_variant=prec))
+            stream = torch.cuda.Stream(device=dev)
+            s.set_stream(stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                b = torch.from_numpy(coil_rhs(p)).to(dev)
+                x = torch.zeros_like(b)
+                s.pcg_solve_dev(b, x, tol=1e-10, stream=stream.cuda_stream)      # warm-up
+                times, its = [], 0
+                for _ in range(3):
+                    x.zero_()
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    info = s.pcg_solve_dev(b, x, tol=1e-10, stream=stream.cuda_stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    times.append(e0.elapsed_time(e1))
+                    its = info.iterations
+            ms = statistics.median(times)
+            us_it = 1e3 * ms / max(its, 1)
+            gbs = (48 if prec == 0 else 24) * s.n_n / (us_it * 1e-6) / 1e9
+            print(json.dumps({"sweep": "zero-start solve", "workload": workload_name(p), "grid": n,
+                              "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
+                              "n_unknowns": int(s.n_n), "iterations": int(its), "relres": info.relres,
+                              "status": int(info.status), "ms_per_solve": ms, "us_per_iteration": us_it,
+                              "algorithmic_GBps": gbs, "hbm_peak_GBps": peaks.get("hbm_gbs"),
+                              "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}), flush=True)
+            s.close()
+            del b, x
+            torch.cuda.empty_cache()
 
 
 def main():
@@ -361,10 +442,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
+    ap.add_argument("--start", choices=["zero", "prev", "spe", "pod"], default="spe",
+                    help="start vector of each step's solve (default: SPE)")
+    ap.add_argument("--depth", type=int, default=0, help="SPE depth or POD snapshot count (default 8 / 20)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP64 PCG (default); 1: FP32 inner solves in FP64 refinement (same tolerance)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
                     help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
+    ap.add_argument("--grid", type=int, default=64,
+                    help="cells per axis of the iron workload (64: the benchmark; others scale it)")
+    ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
+    ap.add_argument("--sweep", type=str, default="",
+                    help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -375,6 +464,9 @@ def main():
         return
     if args.single_solve:
         single_solve()
+        return
+    if args.sweep:
+        size_sweep([int(v) for v in args.sweep.split(",") if v])
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("at least 3 warm-up steps")

@@ -377,3 +377,40 @@ def test_mixed_precision_full_size_agrees_with_fp64(pkg, variant):
     assert all(x.status == 0 for x in st)
     s64.close()
     s32.close()
+
+
+# ---- precision variant at 128^3: mixed precision against the FP64 GPU path at 128^3 and against
+# ---- the oracle at 48^3 (block 18x18x12, coil 30x30)
+def test_mixed_precision_48_matches_the_oracle(pkg):
+    p = W.scaled_nonlinear(48)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 8, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, precision=1, pcg_variant=1)
+    st = s.mqs_step(8)
+    a_c, _, _ = s.get_state()
+    err = rel(a_c, ref.a_c)
+    print(f"mixed precision vs oracle, 48^3, 8 steps: {err:.3e}")
+    assert err < 1e-8, err
+    assert all(x.status == 0 and x.relres <= 1e-10 for x in st)
+    s.close()
+
+
+def test_mixed_precision_128_agrees_with_fp64_over_1000_steps(pkg):
+    p = W.scaled_nonlinear(128)
+    # the Gershgorin step is local: the same at every size of the scaled family (pinned on the oracle)
+    dt = O.dt_gershgorin(O.Discretization(W.scaled_nonlinear(24)))
+    s64 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
+    s32 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=1, pcg_variant=1)
+    worst = 0.0
+    for _ in range(10):
+        st64 = s64.mqs_step(100)
+        st32 = s32.mqs_step(100)
+        assert all(x.status == 0 for x in st64) and all(x.status == 0 and x.relres <= 1e-10 for x in st32)
+        a64, _, _ = s64.get_state()
+        a32, _, _ = s32.get_state()
+        worst = max(worst, rel(a32, a64))
+    print(f"mixed precision vs FP64, 128^3, 1000 steps: max relative a_c difference {worst:.3e}")
+    assert worst < 1e-6, worst
+    s64.close()
+    s32.close()

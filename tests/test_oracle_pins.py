@@ -188,6 +188,19 @@ def test_power_iteration_matches_dense_lambda_max():
     assert lam == pytest.approx(lam_dense, rel=1e-8)
 
 
+def test_gershgorin_step_is_safe_and_local():
+    # the Gershgorin step never exceeds the CFL step of the dense Schur spectrum (eq. (CFL)) ...
+    p = W.scaled_nonlinear(8)
+    d = O.Discretization(p)
+    KS = _dense_schur(d)
+    lam_dense = sla.eigh(0.5 * (KS + KS.T), np.diag(d.M_c), eigvals_only=True).max()
+    assert O.dt_gershgorin(d) <= 0.9 * 2.0 / lam_dense
+    # ... and depends only on the local rows around the conductor, so it is the same at every
+    # size of the scaled iron family (which lets a large run take it from a small grid)
+    dts = [O.dt_gershgorin(O.Discretization(W.scaled_nonlinear(n))) for n in (16, 24, 32)]
+    assert dts[0] == dts[1] == dts[2]
+
+
 @pytest.mark.parametrize("which", ["top", "middle"])
 def test_explicit_euler_amplification_of_an_eigenmode(which):
     p = W.config_linear_block(N=6).with_(amplitude=0.0)
