@@ -429,6 +429,97 @@ def size_sweep(sizes):
             torch.cuda.empty_cache()
 
 
+def run_batch(args):
+    """Batched multi-query: `args.batch` independent instances (N from {32, 40, 48, 64},
+    sigma ~ U[1e6, 5e6] S/m, amplitude ~ U[100, 1000] A, Brauer iron; seeded) advanced
+    together (one stream each, PCG block counts proportional to the unknowns, the scale
+    picked by the batch's tuner during warm-up).  value = instance-steps per second
+    over the timed steps (device time from the fork of the streams to their join);
+    the baseline is every instance stepped alone with all SMs (device time per step,
+    a sample of steps each), as a plain loop over instances would run them."""
+    # the batch spreads its problems over 32 streams; CUDA maps streams onto this many
+    # hardware queues (read when the context is created)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sizes = tuple(int(v) for v in args.batch_grid.split(",")) if args.batch_grid else (32, 40, 48, 64)
+    probs = W.batched_instances(args.batch, sizes=sizes)
+    t0 = time.perf_counter()
+    # lambda_max of M_c^-1 K_S per grid size at sigma 2e6 (power method, eq. (CFL)); M_c is
+    # linear in sigma and K_S does not depend on it, so lambda_max scales as 1/sigma
+    lam_ref = {}
+    for n in sorted({p.N for p in probs}):
+        s = pkg.Solver.from_problem(W.scaled_nonlinear(n), pkg.SolverOptions(tol=1e-10))
+        lam_ref[n], _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8,
+                                     maxit=args.power_maxit)
+        s.close()
+    solvers = []
+    for p in probs:
+        sig = float(p.sigma_cell.max())
+        lam = lam_ref[p.N] * 2.0e6 / sig
+        solvers.append(pkg.Solver.from_problem(p, pkg.SolverOptions(
+            tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, precision=args.precision,
+            pcg_variant=args.pcg_variant, dt=0.9 * 2.0 / lam)))
+    setup_s = time.perf_counter() - t0
+    batch = pkg.Batch(solvers)
+    best = batch.tune(max(args.warmup // 4, 1))
+    batch.step(args.warmup)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+    rc, stats = batch.step(args.steps, allow_fail=True)
+    clk = clocks.stop()
+    ms = batch.last_ms()
+    batch.close()
+    its = np.array([[x.iterations for x in row] for row in stats], dtype=float)
+    failed = int(sum(1 for row in stats for x in row if x.status != 0))
+    value = len(solvers) * args.steps / (ms * 1e-3)
+    # baseline: each instance alone on the whole GPU
+    stream = torch.cuda.Stream(device=dev)
+    per_step_ms = []
+    sample = max(min(args.steps // 5, 50), 5)
+    for s in solvers:
+        s.set_stream(stream.cuda_stream)
+        s.step(2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(sample)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        per_step_ms.append(e0.elapsed_time(e1) / sample)
+        s.set_stream(0)
+    seq = len(solvers) / (sum(per_step_ms) * 1e-3)
+    sizes = {n: sum(1 for p in probs if p.N == n) for n in sorted({p.N for p in probs})}
+    line = {"metric": "batched explicit time steps/sec (instance-steps) at rel-residual 1e-10",
+            "value": value, "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{len(solvers)} instances, N from {set(sizes)} "
+                                   f"(count per N {sizes}), sigma U[1e6,5e6] S/m, coil 100-1000 A, "
+                                   f"Brauer iron, SPE 8, seed 1611",
+                       "n_unknowns": int(sum(s.n_n for s in solvers)),
+                       "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
+                       "blocks_scale": best, "l2": "working set larger than L2 (no flush)",
+                       "parallelism": "1 GPU, instances on 32 streams"},
+            "iters_per_step": float(its.mean()), "failed_steps": failed,
+            "single_instance": {"value": seq, "unit": "instance-steps/s",
+                                "note": f"each instance alone with all SMs, {sample} steps each"},
+            "speedup_vs_single_instance": value / seq,
+            "clocks": clk, "setup": {"seconds": setup_s, "lambda_ref": lam_ref}}
+    print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,6 +545,10 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
     ap.add_argument("--sweep", type=str, default="",
                     help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="advance this many seeded multi-query instances together (batched mode)")
+    ap.add_argument("--batch-grid", type=str, default="",
+                    help="comma-separated grid sizes the batched instances draw from (default 32,40,48,64)")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -467,6 +562,9 @@ def main():
         return
     if args.sweep:
         size_sweep([int(v) for v in args.sweep.split(",") if v])
+        return
+    if args.batch:
+        run_batch(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("at least 3 warm-up steps")

@@ -305,6 +305,56 @@ int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t* cell_mask_
                           const double* b_dev, double* x_dev, double tol, int maxit,
                           mqs_pcg_info* info, void* stream);
 
+/* ---- Batched multi-query ------------------------------------------------
+ * Sec. I motivates fast time stepping by many-query work (uncertainty
+ * quantification, optimisation: many runs of one model with different
+ * parameters).  A batch advances several handles -- each its own problem
+ * (grid, materials, coil, options, dt) -- together on one GPU.  Each handle's
+ * launches go to a stream of its own, and its persistent PCG kernels use a
+ * block count proportional to its unknowns, so that the solves of small
+ * problems run side by side on disjoint SMs instead of each taking the whole
+ * GPU in turn.  Per handle, the result equals an mqs_step run up to the
+ * summation order of the grid-wide reductions (which depends on the block
+ * count).
+ *
+ * mqs_set_blocks: persistent blocks of the handle's PCG kernels, 1 .. the SM
+ * count (0 = one block per SM, the default).  MQS_ERR_ARG above the SM count.
+ *
+ * mqs_batch_create: handles[0..count) stay owned by the caller, must be
+ * distinct, must outlive the batch and must not be stepped outside it while
+ * it exists.  blocks_scale (> 0; <= 0 selects 2.0) makes the block counts add
+ * up to about blocks_scale blocks per SM (each at least 1, at most one per
+ * SM): values above 1 oversubscribe, so that SMs released by solves that
+ * converge early are taken by others.  The batch creates min(count, 32)
+ * streams, shared by the handles round-robin (CUDA maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware queues, 8 unless the environment sets
+ * up to 32 before the CUDA context is created; set it to 32 for batches), and
+ * restores each handle's stream and block count on destroy.
+ * Errors: MQS_ERR_ARG, MQS_ERR_OOM, MQS_ERR_CUDA; on failure *out is NULL.
+ *
+ * mqs_batch_step: nsteps explicit-Euler steps (as mqs_step) of every handle.
+ * per_step (host, nullable) receives nsteps*count stats, step-major:
+ * per_step[s*count + i] is step s of handles[i].  Blocks until all finish.
+ * Returns MQS_OK or the first failing handle's status (its mqs_last_error
+ * holds the text).
+ *
+ * mqs_batch_last_ms: device time of the last mqs_batch_step (CUDA events from
+ * the fork of the streams to their join).
+ *
+ * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8 for trial_steps steps
+ * each -- real steps that advance every problem -- and keeps the fastest
+ * (returned in *best_scale, nullable).
+ * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts. */
+int mqs_set_blocks(mqs_handle* h, int nblk);
+typedef struct mqs_batch mqs_batch;
+int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale,
+                     mqs_batch** out);
+int mqs_batch_set_scale(mqs_batch* b, double blocks_scale);
+int mqs_batch_step(mqs_batch* b, int nsteps, mqs_step_stats* per_step);
+int mqs_batch_last_ms(mqs_batch* b, double* ms);
+int mqs_batch_tune(mqs_batch* b, int trial_steps, double* best_scale);
+int mqs_batch_destroy(mqs_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

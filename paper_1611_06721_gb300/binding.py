@@ -8,6 +8,7 @@ no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 import os
 from dataclasses import dataclass
 
@@ -27,7 +28,9 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution", "mqs_reset_history",
            "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev", "mqs_conductor_rate",
            "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
-           "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout")
+           "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout", "mqs_set_blocks",
+           "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms", "mqs_batch_tune",
+           "mqs_batch_destroy")
 
 
 class Grid(C.Structure):
@@ -116,6 +119,13 @@ def load():
         "mqs_timing_get": ([H, P(Timing)], I),
         "mqs_pcg_solve_noalloc": ([I, D, D, V, V, V, D, I, P(PcgInfo), V], I),
         "mqs_selftest_barrier_timeout": ([C.c_longlong], I),
+        "mqs_set_blocks": ([H, I], I),
+        "mqs_batch_create": ([P(H), I, D, P(V)], I),
+        "mqs_batch_set_scale": ([V, D], I),
+        "mqs_batch_step": ([V, I, P(StepStats)], I),
+        "mqs_batch_last_ms": ([V, P(D)], I),
+        "mqs_batch_tune": ([V, I, P(D)], I),
+        "mqs_batch_destroy": ([V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -206,6 +216,10 @@ class Solver:
         return rc
 
     def close(self):
+        batch = getattr(self, "_batch", None)
+        batch = batch() if batch is not None else None
+        if batch is not None:
+            batch.close()               # a batch must end before the handles it steps
         if getattr(self, "h", None):
             self.lib.mqs_destroy(self.h)
             self.h = None
@@ -260,6 +274,10 @@ class Solver:
 
     def mqs_step(self, nsteps):
         return self.step(nsteps)[1]
+
+    def set_blocks(self, nblk):
+        """Persistent blocks of this handle's PCG kernels (0 = one per SM)."""
+        self._check(self.lib.mqs_set_blocks(self.h, nblk))
 
     def get_state(self):
         a = np.empty(self.n_c)
@@ -351,3 +369,67 @@ def pcg_solve_noalloc(n, h, nu0, cell_mask, b, x, tol=1e-10, maxit=100000, strea
     rc = lib.mqs_pcg_solve_noalloc(n, h, nu0, C.c_void_p(cell_mask.data_ptr()), C.c_void_p(b.data_ptr()),
                                    C.c_void_p(x.data_ptr()), tol, maxit, C.byref(info), C.c_void_p(stream))
     return rc, info
+
+
+class Batch:
+    """Several solvers advanced together on one GPU (mqs_batch_*): each on its own
+    stream, PCG block counts proportional to the unknowns.  The solvers stay
+    owned by the caller and must outlive the batch."""
+
+    def __init__(self, solvers, blocks_scale=2.0):
+        self.lib = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[sv.h for sv in self.solvers])
+        b = C.c_void_p()
+        rc = self.lib.mqs_batch_create(arr, len(self.solvers), blocks_scale, C.byref(b))
+        if rc != MQS_OK:
+            raise MqsError(rc, "mqs_batch_create failed")
+        self.b = b
+        for sv in self.solvers:
+            sv._batch = weakref.ref(self)
+
+    def _check(self, rc):
+        if rc != MQS_OK:
+            msgs = []
+            for q, sv in enumerate(self.solvers):
+                buf = C.create_string_buffer(512)
+                self.lib.mqs_last_error(sv.h, buf, 512)
+                if buf.value:
+                    msgs.append(f"[{q}] {buf.value.decode()}")
+            raise MqsError(rc, "; ".join(msgs))
+        return rc
+
+    def step(self, nsteps, allow_fail=False):
+        """nsteps steps of every solver; returns (rc, stats[nsteps][count])."""
+        cnt = len(self.solvers)
+        st = (StepStats * max(nsteps * cnt, 1))()
+        rc = self.lib.mqs_batch_step(self.b, nsteps, st)
+        if not allow_fail:
+            self._check(rc)
+        return rc, [[st[s * cnt + q] for q in range(cnt)] for s in range(nsteps)]
+
+    def last_ms(self):
+        v = C.c_double()
+        self._check(self.lib.mqs_batch_last_ms(self.b, C.byref(v)))
+        return v.value
+
+    def set_scale(self, blocks_scale):
+        self._check(self.lib.mqs_batch_set_scale(self.b, blocks_scale))
+
+    def tune(self, trial_steps):
+        v = C.c_double()
+        self._check(self.lib.mqs_batch_tune(self.b, trial_steps, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mqs_batch_destroy(self.b)
+            self.b = None
+            for sv in self.solvers:
+                sv._batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,6 +1,8 @@
 // C ABI of the library: handle life cycle, the explicit Euler step driver and
 // the stand-alone entry points declared in include/mqs.h.
+#include <algorithm>
 #include <cmath>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -618,56 +620,64 @@ int mqs_reset_history(mqs_handle* H) {
   return MQS_OK;
 }
 
-int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
-  if (!H || nsteps < 0) return MQS_ERR_ARG;
-  if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
-  if (nsteps == 0) return MQS_OK;
+namespace {
+
+// Issues the launches of one explicit-Euler step of H on H->st (no host wait);
+// the step's statistics go to H->dstats[s].
+int enqueue_step(mqs_handle* H, int s) {
   cudaStream_t st = H->st;
-  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
-  RK(ensure_stats(H, nsteps));
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
-  for (int s = 0; s < nsteps; ++s) {
-    const long m = H->m + 1;
-    const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
-    long nl = 0;
-    mark(H);
-    // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
-    const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-    RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->rhs_box, st));
-    nl += 1;
-    mark(H);
-    // (a3) start vector
-    int used_small = 0, init = 0;
-    nl += start_launches(H);
-    RK(start_vector(H, H->b, H->x, st, &used_small, &init));
-    mark(H);
-    // (a4) PCG
-    CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
-    RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
-    H->lx_valid = true;
-    nl += 1;
-    mark(H);
-    // (a5) conducting update, eq. (acm)
-    RK(conductor_step(H, H->x, H->dt, st));
-    nl += H->any_brauer ? 2 : 1;
-    mark(H);
-    // (a6) history
-    RK(history_push(H, H->x, H->lx, st));
-    nl += history_launches(H);
-    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
-                                   H->dstats + s);
-    nl += 1;
-    mark(H);
-    if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
-    H->m = m;
-    H->t = m * H->dt;
-  }
-  std::vector<mqs_step_stats> hs(nsteps);
-  int derr = 0;
-  CK(cudaMemcpyAsync(hs.data(), H->dstats, sizeof(mqs_step_stats) * nsteps, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&derr, H->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (per_step) memcpy(per_step, hs.data(), sizeof(mqs_step_stats) * nsteps);
+  const long m = H->m + 1;
+  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+  long nl = 0;
+  mark(H);
+  // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
+  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->rhs_box, st));
+  nl += 1;
+  mark(H);
+  // (a3) start vector
+  int used_small = 0, init = 0;
+  nl += start_launches(H);
+  RK(start_vector(H, H->b, H->x, st, &used_small, &init));
+  mark(H);
+  // (a4) PCG
+  CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
+  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
+  H->lx_valid = true;
+  nl += 1;
+  mark(H);
+  // (a5) conducting update, eq. (acm)
+  RK(conductor_step(H, H->x, H->dt, st));
+  nl += H->any_brauer ? 2 : 1;
+  mark(H);
+  // (a6) history
+  RK(history_push(H, H->x, H->lx, st));
+  nl += history_launches(H);
+  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
+                                 H->dstats + s);
+  nl += 1;
+  mark(H);
+  if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
+  H->m = m;
+  H->t = m * H->dt;
+  return MQS_OK;
+}
+
+int prepare_steps(mqs_handle* H, int nsteps) {
+  if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
+  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
+  return ensure_stats(H, nsteps);
+}
+
+// Copies the step statistics of the last nsteps steps into hs (async on H->st).
+int fetch_stats(mqs_handle* H, int nsteps, mqs_step_stats* hs, int* derr) {
+  CK(cudaMemcpyAsync(hs, H->dstats, sizeof(mqs_step_stats) * nsteps, cudaMemcpyDeviceToHost, H->st));
+  CK(cudaMemcpyAsync(derr, H->derr, sizeof(int), cudaMemcpyDeviceToHost, H->st));
+  return MQS_OK;
+}
+
+int check_stats(mqs_handle* H, int nsteps, const mqs_step_stats* hs, int derr) {
   if (derr != 0) return fail(H, derr, "a bounded grid barrier wait timed out");
   for (int s = 0; s < nsteps; ++s)
     if (hs[s].status != MQS_OK) {
@@ -675,6 +685,21 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
       return hs[s].status;
     }
   return MQS_OK;
+}
+
+}  // namespace
+
+int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
+  if (!H || nsteps < 0) return MQS_ERR_ARG;
+  if (nsteps == 0) return (H->dt > 0.0) ? MQS_OK : fail(H, MQS_ERR_ARG, "dt is not set");
+  RK(prepare_steps(H, nsteps));
+  for (int s = 0; s < nsteps; ++s) RK(enqueue_step(H, s));
+  std::vector<mqs_step_stats> hs(nsteps);
+  int derr = 0;
+  RK(fetch_stats(H, nsteps, hs.data(), &derr));
+  CK(cudaStreamSynchronize(H->st));
+  if (per_step) memcpy(per_step, hs.data(), sizeof(mqs_step_stats) * nsteps);
+  return check_stats(H, nsteps, hs.data(), derr);
 }
 
 int mqs_get_state(mqs_handle* H, double* a_c, size_t n_c, double* t, long* m) {
@@ -941,3 +966,186 @@ int pod_start(mqs_handle* H, const double* b, double* x0, int* k) {
 }
 
 }  // extern "C"
+
+// ---- batched multi-query ---------------------------------------------------------------
+
+int mqs_set_blocks(mqs_handle* H, int nblk) {
+  if (!H || nblk < 0) return MQS_ERR_ARG;
+  int mx = 0;
+  RK(pcg_max_blocks(&mx));
+  if (nblk > mx) return fail(H, MQS_ERR_ARG, "more persistent blocks than can be co-resident");
+  CK(cudaStreamSynchronize(H->st));     // no solve with the old block count in flight
+  H->nblk = nblk == 0 ? mx : nblk;
+  return MQS_OK;
+}
+
+// status-only variants of CK / RK for calls that belong to no single handle
+#define BCK(call)                                         \
+  do {                                                    \
+    if ((call) != cudaSuccess) return MQS_ERR_CUDA;       \
+  } while (0)
+#define BRK(call)                                         \
+  do {                                                    \
+    int r_ = (call);                                      \
+    if (r_ != MQS_OK) return r_;                          \
+  } while (0)
+
+// streams of a batch: CUDA maps streams onto at most 32 hardware queues
+// (CUDA_DEVICE_MAX_CONNECTIONS), so more streams would only alias
+constexpr int kBatchStreams = 32;
+
+struct mqs_batch {
+  std::vector<mqs_handle*> hs;
+  std::vector<cudaStream_t> streams, saved_st;
+  std::vector<int> saved_nblk;
+  std::vector<cudaEvent_t> done;
+  cudaStream_t master = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double scale = 2.0;
+  float last_ms = 0.f;
+};
+
+namespace {
+
+// block counts proportional to the unknowns, scaled so that they add up to
+// about `scale` blocks per SM
+int batch_assign(mqs_batch* B) {
+  int mx = 0;
+  BRK(pcg_max_blocks(&mx));
+  double wsum = 0.0;
+  for (mqs_handle* H : B->hs) wsum += (double)H->n_n;
+  for (mqs_handle* H : B->hs) {
+    long nb = std::lround(B->scale * mx * (double)H->n_n / std::max(wsum, 1.0));
+    H->nblk = (int)std::min<long>(std::max<long>(nb, 1), mx);
+  }
+  return MQS_OK;
+}
+
+void batch_release(mqs_batch* B) {
+  for (cudaStream_t s : B->streams)
+    if (s) cudaStreamSynchronize(s);
+  for (size_t i = 0; i < B->hs.size(); ++i) {
+    B->hs[i]->st = B->saved_st[i];
+    B->hs[i]->nblk = B->saved_nblk[i];
+  }
+  for (cudaStream_t s : B->streams) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : B->done) if (e) cudaEventDestroy(e);
+  if (B->ev0) cudaEventDestroy(B->ev0);
+  if (B->ev1) cudaEventDestroy(B->ev1);
+  if (B->master) cudaStreamDestroy(B->master);
+  delete B;
+}
+
+}  // namespace
+
+int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale, mqs_batch** out) {
+  if (!out) return MQS_ERR_ARG;
+  *out = nullptr;
+  if (!handles || count < 1) return MQS_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i]) return MQS_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return MQS_ERR_ARG;
+  }
+  mqs_batch* B = new (std::nothrow) mqs_batch;
+  if (!B) return MQS_ERR_OOM;
+  B->scale = blocks_scale > 0.0 ? blocks_scale : 2.0;
+  bool ok = cudaStreamCreateWithFlags(&B->master, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&B->ev0) == cudaSuccess && cudaEventCreate(&B->ev1) == cudaSuccess;
+  const int ns = std::min(count, kBatchStreams);
+  for (int i = 0; ok && i < ns; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (s) B->streams.push_back(s);
+    if (e) B->done.push_back(e);
+  }
+  for (int i = 0; ok && i < count; ++i) {
+    mqs_handle* H = handles[i];
+    ok = cudaStreamSynchronize(H->st) == cudaSuccess;
+    if (!ok) break;
+    B->hs.push_back(H);
+    B->saved_st.push_back(H->st);
+    B->saved_nblk.push_back(H->nblk);
+    H->st = B->streams[i % ns];
+  }
+  if (!ok) { batch_release(B); return MQS_ERR_CUDA; }
+  const int rc = batch_assign(B);
+  if (rc != MQS_OK) { batch_release(B); return rc; }
+  *out = B;
+  return MQS_OK;
+}
+
+int mqs_batch_set_scale(mqs_batch* B, double blocks_scale) {
+  if (!B || !(blocks_scale > 0.0)) return MQS_ERR_ARG;
+  for (cudaStream_t s : B->streams) BCK(cudaStreamSynchronize(s));
+  B->scale = blocks_scale;
+  return batch_assign(B);
+}
+
+int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
+  if (!B || nsteps < 0) return MQS_ERR_ARG;
+  const int cnt = (int)B->hs.size();
+  for (mqs_handle* H : B->hs)
+    if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
+  if (nsteps == 0) return MQS_OK;
+  for (mqs_handle* H : B->hs) RK(prepare_steps(H, nsteps));
+  BCK(cudaEventRecord(B->ev0, B->master));
+  for (cudaStream_t s : B->streams) BCK(cudaStreamWaitEvent(s, B->ev0, 0));
+  int rc = MQS_OK;
+  // step-major issue order: every problem's step s is queued before any step s+1,
+  // so the streams advance side by side
+  for (int s = 0; s < nsteps && rc == MQS_OK; ++s)
+    for (int i = 0; i < cnt && rc == MQS_OK; ++i) rc = enqueue_step(B->hs[i], s);
+  for (size_t i = 0; i < B->streams.size(); ++i) {
+    BCK(cudaEventRecord(B->done[i], B->streams[i]));
+    BCK(cudaStreamWaitEvent(B->master, B->done[i], 0));
+  }
+  BCK(cudaEventRecord(B->ev1, B->master));
+  if (rc != MQS_OK) {
+    for (cudaStream_t s : B->streams) cudaStreamSynchronize(s);
+    return rc;
+  }
+  std::vector<mqs_step_stats> hs((size_t)nsteps * cnt);
+  std::vector<int> derr(cnt, 0);
+  for (int i = 0; i < cnt; ++i) BRK(fetch_stats(B->hs[i], nsteps, hs.data() + (size_t)i * nsteps, &derr[i]));
+  for (cudaStream_t s : B->streams) BCK(cudaStreamSynchronize(s));
+  BCK(cudaEventSynchronize(B->ev1));
+  BCK(cudaEventElapsedTime(&B->last_ms, B->ev0, B->ev1));
+  if (per_step)
+    for (int s = 0; s < nsteps; ++s)
+      for (int i = 0; i < cnt; ++i) per_step[(size_t)s * cnt + i] = hs[(size_t)i * nsteps + s];
+  for (int i = 0; i < cnt; ++i) {
+    const int r = check_stats(B->hs[i], nsteps, hs.data() + (size_t)i * nsteps, derr[i]);
+    if (r != MQS_OK && rc == MQS_OK) rc = r;
+  }
+  return rc;
+}
+
+int mqs_batch_last_ms(mqs_batch* B, double* ms) {
+  if (!B || !ms) return MQS_ERR_ARG;
+  *ms = B->last_ms;
+  return MQS_OK;
+}
+
+int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
+  if (!B || trial_steps < 1) return MQS_ERR_ARG;
+  static const double cand[] = {1.0, 2.0, 4.0, 8.0};
+  double best = B->scale, best_ms = 0.0;
+  bool have = false;
+  for (double c : cand) {
+    BRK(mqs_batch_set_scale(B, c));
+    BRK(mqs_batch_step(B, trial_steps, nullptr));
+    if (!have || B->last_ms < best_ms) { best = c; best_ms = B->last_ms; have = true; }
+  }
+  BRK(mqs_batch_set_scale(B, best));
+  if (best_scale) *best_scale = best;
+  return MQS_OK;
+}
+
+int mqs_batch_destroy(mqs_batch* B) {
+  if (!B) return MQS_ERR_ARG;
+  batch_release(B);
+  return MQS_OK;
+}

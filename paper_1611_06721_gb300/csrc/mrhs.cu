@@ -16,6 +16,7 @@
 // small symmetric eigenproblem G = V Lambda V^T (parallel-order Jacobi) gives
 // sigma_i = sqrt(lambda_i) and U = X V Sigma^-1, truncated at sigma_i/sigma_1
 // >= eps_pod; then x0 = U_k (U_k^T K_n U_k)^-1 U_k^T b in the small space.
+#include <algorithm>
 #include <cmath>
 #include "mrhs.h"
 
@@ -576,7 +577,7 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
 }
 
 // ---- host launchers --------------------------------------------------------------------
-static int ts_blocks() {
+static int ts_max_blocks() {
   static int nb = 0;
   if (nb == 0) {
     int dev = 0, nsm = 0;
@@ -586,21 +587,28 @@ static int ts_blocks() {
   }
   return nb;
 }
-int ts_nblk() { return ts_blocks(); }
+
+// blocks of a tall-skinny pass over len values: at least 8 values per thread, at
+// most two blocks per SM (small problems do not flood the GPU with empty blocks)
+static int ts_blocks(long long len) {
+  const long long want = (len + (long long)kTS * 8 - 1) / ((long long)kTS * 8);
+  return (int)std::min<long long>(std::max<long long>(want, 8), ts_max_blocks());
+}
+int ts_nblk() { return ts_max_blocks(); }
 
 static int chk() { return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA; }
 
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, cudaStream_t st) {
-  if (m_new <= 4) diff_push_kernel<4><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else if (m_new <= 8) diff_push_kernel<8><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else diff_push_kernel<16><<<ts_blocks(), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  if (m_new <= 4) diff_push_kernel<4><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else if (m_new <= 8) diff_push_kernel<8><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else diff_push_kernel<16><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   return chk();
 }
 
 int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
            double* part, double* coef, SmallOut* out, cudaStream_t st, double* r0) {
-  const int nb = ts_blocks();
+  const int nb = ts_blocks(len);
   if (m <= 0) {
     if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
     return MQS_OK;
@@ -627,7 +635,7 @@ int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0
 
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st) {
-  const int nb = ts_blocks();
+  const int nb = ts_blocks(len);
   const int ntile = (m + 7) / 8;
   for (int t = 0; t < ntile; ++t) {
     VecSet Aw, Bx;
@@ -643,7 +651,7 @@ int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
            double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st,
            const VecSet* LX, double* r0) {
-  const int nb = ts_blocks();
+  const int nb = ts_blocks(len);
   if (m <= 0) {
     if (x0 && cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
     return MQS_OK;

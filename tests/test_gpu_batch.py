@@ -1,0 +1,119 @@
+"""Batched multi-query (several independent problems advanced together on one GPU):
+every instance against the oracle, the batch against separate runs, persistent PCG
+kernels on few blocks, and the batch's argument checks."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.stepper import START_SPE
+from tests.helpers import layout_to_oracle, oracle_to_layout, rel
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as p
+    import torch
+    assert torch.cuda.is_available()
+    return p
+
+
+def _instances():
+    """(problem, options) pairs of different sizes, materials, coils and precisions."""
+    return [
+        (W.config_linear_block(), dict(start_mode=START_SPE, spe_depth=8)),
+        (W.scaled_nonlinear(20, sigma=3.1e6, amplitude=700.0), dict(start_mode=START_SPE, spe_depth=8)),
+        (W.scaled_nonlinear(24, sigma=1.4e6, amplitude=250.0), dict(start_mode=START_SPE, spe_depth=8,
+                                                                      precision=1, pcg_variant=1)),
+        (W.scaled_nonlinear(12, sigma=4.5e6, amplitude=900.0), dict(start_mode=1)),
+    ]
+
+
+def _solvers(pkg, steps_dt):
+    out = []
+    for (p, kw), dt in zip(_instances(), steps_dt):
+        out.append(pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, dt=dt, **kw)))
+    return out
+
+
+def _dts():
+    return [O.dt_gershgorin(O.Discretization(p)) for p, _ in _instances()]
+
+
+def test_batch_instances_match_the_oracle(pkg):
+    steps = 30
+    dts = _dts()
+    sv = _solvers(pkg, dts)
+    batch = pkg.Batch(sv)
+    _, stats = batch.step(steps)
+    assert all(x.status == 0 for row in stats for x in row)
+    assert batch.last_ms() > 0.0
+    for q, ((p, kw), dt) in enumerate(zip(_instances(), dts)):
+        d = O.Discretization(p)
+        ref = O.run_explicit_euler(d, dt, steps, start_mode=kw["start_mode"], spe_depth=kw.get("spe_depth", 8),
+                                   tol=1e-10)
+        a_c, t, m = sv[q].get_state()
+        assert m == steps and t == pytest.approx(steps * dt)
+        assert rel(a_c, ref.a_c) < 1e-8, (q, rel(a_c, ref.a_c))
+    batch.close()
+    for s in sv:
+        s.close()
+
+
+def test_batch_equals_separate_runs(pkg):
+    steps = 25
+    dts = _dts()
+    alone = _solvers(pkg, dts)
+    for s in alone:
+        s.mqs_step(steps)
+    sv = _solvers(pkg, dts)
+    batch = pkg.Batch(sv, blocks_scale=1.0)
+    batch.step(10)
+    batch.set_scale(4.0)                         # block counts may change between calls
+    batch.step(steps - 10)
+    for a, b in zip(alone, sv):
+        x, _, _ = a.get_state()
+        y, _, _ = b.get_state()
+        assert rel(y, x) < 1e-9                  # only the reductions' summation order differs
+    batch.close()
+    for s in alone + sv:
+        s.close()
+
+
+@pytest.mark.parametrize("nblk", [1, 3, 7])
+def test_pcg_on_few_persistent_blocks(pkg, nblk):
+    p = W.scaled_nonlinear(24)
+    d = O.Discretization(p)
+    b_o = np.zeros(d.grid.n_edges)
+    b_o[d.n_idx] = 5.0 * d.X_s[d.n_idx]
+    ref = O.pcg_jacobi(d.K_n, b_o[d.n_idx], None, d.D, tol=1e-10)
+    for prec, var in ((0, 0), (0, 1), (1, 1)):
+        s = pkg.Solver.from_problem(p, pkg.SolverOptions(precision=prec, pcg_variant=var))
+        s.set_blocks(nblk)
+        x, info = s.pcg_solve(oracle_to_layout(p.N, b_o), tol=1e-10)
+        assert info.status == 0 and info.relres <= 1e-10
+        assert rel(d.K_cn @ layout_to_oracle(p.N, x)[d.n_idx], d.K_cn @ ref.x) < 1e-9
+        s.close()
+
+
+def test_batch_tune_and_argument_checks(pkg):
+    dts = _dts()
+    sv = _solvers(pkg, dts)
+    with pytest.raises(pkg.MqsError):
+        pkg.Batch([sv[0], sv[0]])                # the same handle twice
+    with pytest.raises(pkg.MqsError):
+        sv[1].set_blocks(100000)                 # more blocks than SMs
+    batch = pkg.Batch(sv)
+    best = batch.tune(2)
+    assert best in (1.0, 2.0, 4.0, 8.0)
+    _, stats = batch.step(3)
+    assert all(x.status == 0 for row in stats for x in row)
+    sv[0].close()                                # closes the batch first
+    assert batch.b is None
+    for s in sv[1:]:
+        s.close()

@@ -152,13 +152,13 @@ def power_start_vector(n_c: int, seed: int = 1611) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(n_c)
 
 
-def batched_instances(count: int = 64, seed: int = 1611):
-    """Multi-query instances: N from {32, 40, 48, 64}, sigma ~ U[1e6, 5e6],
-    amplitude ~ U[100, 1000] A, Brauer iron scaled with N."""
+def batched_instances(count: int = 64, seed: int = 1611, sizes=(32, 40, 48, 64)):
+    """Multi-query instances: N from `sizes` (default {32, 40, 48, 64}), sigma ~
+    U[1e6, 5e6], amplitude ~ U[100, 1000] A, Brauer iron scaled with N."""
     rng = np.random.default_rng(seed)
     out = []
     for q in range(count):
-        N = int(rng.choice([32, 40, 48, 64]))
+        N = int(rng.choice(list(sizes)))
         sig = float(rng.uniform(1e6, 5e6))
         amp = float(rng.uniform(100.0, 1000.0))
         out.append(scaled_nonlinear(N, sigma=sig, amplitude=amp, n_steps=500).with_(name=f"instance-{q}-{N}^3"))
