@@ -520,6 +520,116 @@ def run_batch(args):
         s.close()
 
 
+def adjoint_fd_check(args, p, fresh):
+    """Central differences of J (solves at tol 1e-12) against the adjoint gradient:
+    random iron cells with a gradient of at least 1% of the largest, and the coil
+    amplitude, at relative steps 1e-6 and 1e-4."""
+    import numpy as np
+    sc = fresh(1e-12)
+    J12, g12, gI12, _ = sc.adjoint(args.steps)
+    sc.close()
+    sig = p.sigma_cell.reshape(-1)
+    g = g12.reshape(-1)
+    rng = np.random.default_rng(1611)
+    # random iron cells among those whose gradient is at least 1% of the largest (smaller ones
+    # fall below what a difference quotient of J resolves at this size)
+    cand = np.flatnonzero((sig > 0) & (np.abs(g) >= 1e-2 * np.abs(g).max()))
+    cells = rng.choice(cand, size=min(max(args.fd_params - 1, 0), cand.size), replace=False)
+    fd_err = {}
+    for h in (1e-6, 1e-4):
+        errs = []
+        for c in cells:
+            vals = []
+            for sgn in (1.0, -1.0):
+                sp = sig.copy()
+                sp[c] *= 1.0 + sgn * h
+                sv = fresh(1e-12, p.with_(sigma_cell=sp.reshape(p.sigma_cell.shape)))
+                vals.append(sv.loss(args.steps))
+                sv.close()
+            fd = (vals[0] - vals[1]) / (2.0 * h * sig[c])
+            errs.append(abs(g[c] - fd) / abs(fd))
+        vals = []
+        for sgn in (1.0, -1.0):
+            sv = fresh(1e-12, p.with_(amplitude=p.amplitude * (1.0 + sgn * h)))
+            vals.append(sv.loss(args.steps))
+            sv.close()
+        fdI = (vals[0] - vals[1]) / (2.0 * h * p.amplitude)
+        fd_err[f"h_rel={h:g}"] = {"max_rel_err_cells": max(errs) if errs else None,
+                                  "median_rel_err_cells": float(np.median(errs)) if errs else None,
+                                  "amplitude_rel_err": abs(gI12 - fdI) / abs(fdI)}
+    return fd_err, cells
+
+
+def run_adjoint(args):
+    """Gradient of the eddy-current loss J = sum_m dt F_m^T M_c^-1 F_m over the steps of
+    the 64^3 iron workload from rest (mqs_adjoint: forward steps recording the
+    conductor trajectory, then the reverse sweep with one K_n solve per step), FP64.
+    value = steps per second of forward + reverse; the forward steps alone are timed
+    on a second handle.  The gradient is checked against central differences
+    (relative step 1e-6, solves at tol 1e-12) on args.fd_params parameters:
+    conductivities of random iron cells and the coil amplitude."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = W.config_nonlinear_iron() if args.grid == 64 else W.scaled_nonlinear(args.grid)
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10))
+    lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
+    s.close()
+    dt = 0.9 * 2.0 / lam
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), out
+
+    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD}[args.start]
+    depth = args.depth if args.depth else (8 if args.start == "spe" else 20)
+    sopts = dict(start_mode=mode, spe_depth=depth if args.start == "spe" else 8,
+                 pod_snapshots=depth if args.start == "pod" else 20, dt=dt)
+
+    def fresh(tol, problem=None):
+        sv = pkg.Solver.from_problem(problem or p, pkg.SolverOptions(tol=tol, **sopts))
+        sv.set_stream(stream.cuda_stream)
+        return sv
+    sf = fresh(1e-10)
+    sf.adjoint(5)                                        # warm-up (allocations, first launches)
+    sf.close()
+    sf = fresh(1e-10)
+    ms_fwd, _ = timed(lambda: sf.step(args.steps))
+    sf.close()
+    sa = fresh(1e-10)
+    ms_adj, (J, gs, gI, info) = timed(lambda: sa.adjoint(args.steps))
+    sa.close()
+    fd_err, cells = {}, []
+    if args.fd_params > 0:
+        fd_err, cells = adjoint_fd_check(args, p, fresh)
+    line = {"metric": "adjoint gradient of the eddy-current loss (forward + reverse sweep), steps/s",
+            "value": args.steps / (ms_adj * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms_adj / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(p), "grid": p.N, "start": "rest", "tol": 1e-10,
+                       "start_vector": args.start + (str(depth) if args.start in ("spe", "pod") else "")
+                                       + " (forward and adjoint solves)", "dt_s": dt,
+                       "parameters": f"{int((p.sigma_cell > 0).sum())} cell conductivities + coil amplitude",
+                       "trajectory": "conductor state and rate of every step kept on the device"},
+            "forward_only_steps_per_s": args.steps / (ms_fwd * 1e-3),
+            "reverse_cost_vs_forward": (ms_adj - ms_fwd) / ms_fwd,
+            "objective_J": J, "grad_amplitude": gI,
+            "pcg_iterations": {"forward": int(info.forward_iterations), "adjoint": int(info.adjoint_iterations)},
+            "fd_check": {"tol": 1e-12, "cells": len(cells),
+                         "cells_from": "random iron cells with |dJ/dsigma| >= 1% of the largest", **fd_err}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,6 +659,9 @@ def main():
                     help="advance this many seeded multi-query instances together (batched mode)")
     ap.add_argument("--batch-grid", type=str, default="",
                     help="comma-separated grid sizes the batched instances draw from (default 32,40,48,64)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the adjoint gradient of the eddy-current loss and check it by central differences")
+    ap.add_argument("--fd-params", type=int, default=32, help="parameters checked by central differences")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -565,6 +678,9 @@ def main():
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("at least 3 warm-up steps")

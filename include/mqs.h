@@ -305,6 +305,45 @@ int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t* cell_mask_
                           const double* b_dev, double* x_dev, double tol, int maxit,
                           mqs_pcg_info* info, void* stream);
 
+/* ---- Discrete adjoint of the time loop ----------------------------------
+ * The paper's motivation for fast time stepping includes optimisation
+ * (Sec. I); this computes the gradient of the time-integrated eddy-current
+ * loss over the explicit-Euler steps of eqs. (ODE)/(acm)
+ *
+ *   J = sum_m dt e_m^T M_c e_m,  e_m = (a_c^m - a_c^{m-1}) / dt,
+ *
+ * (the FIT edge form of sum over cells of sigma |E|^2 dV with E = -da/dt on
+ * the conducting edges; J = sum_m dt F_m^T M_c^-1 F_m with F_m the bracket of
+ * eq. (acm)) with respect to every cell conductivity and the coil amplitude,
+ * by the reverse sweep of the discrete adjoint: per step one PCG solve with
+ * K_n (same kernels and start vectors as the time loop) and the transposed
+ * Jacobian of the Brauer face law on the conductor box.  dt, the edge classes
+ * and the coil waveform are held fixed.
+ *
+ * mqs_adjoint: runs nsteps steps from the handle's current state (recording
+ * a_c^{m-1} and F_m of every step on the device: 16 n_c bytes per step; no
+ * recomputation), evaluates J, then the reverse sweep.  grad_sigma_cell
+ * (host, n^3 in cell order i + n (j + n k), nullable) receives dJ/dsigma per
+ * cell (J per S/m, 0 for nonconducting cells).  info (nullable) receives J
+ * (in joules: W s of dissipated power, SI units of the grid), dJ/d
+ * amplitude and the PCG iteration totals.  Afterwards the handle is at the
+ * forward end state (time and step count advanced by nsteps) with an empty
+ * start-vector history (the reverse sweep used it for the adjoint solves) and
+ * mqs_get_solution holding the last adjoint solve.  Errors: MQS_ERR_ARG,
+ * MQS_ERR_OOM, MQS_ERR_CUDA and the PCG statuses of either sweep. */
+typedef struct {
+    double objective;        /* J                                               */
+    double grad_amplitude;   /* dJ / d(coil amplitude)                          */
+    long   forward_iterations;   /* PCG iterations of the forward steps         */
+    long   adjoint_iterations;   /* PCG iterations of the adjoint solves        */
+} mqs_adjoint_info;
+int mqs_adjoint(mqs_handle* h, int nsteps, double* grad_sigma_cell, mqs_adjoint_info* info);
+
+/* mqs_loss: the forward part of mqs_adjoint alone: nsteps steps from the
+ * current state and J over them (*objective, host, nullable); the handle
+ * advances as with mqs_step.  Errors as mqs_step. */
+int mqs_loss(mqs_handle* h, int nsteps, double* objective);
+
 /* ---- Batched multi-query ------------------------------------------------
  * Sec. I motivates fast time stepping by many-query work (uncertainty
  * quantification, optimisation: many runs of one model with different

@@ -55,20 +55,20 @@ class AdjointResult:
     a_c: np.ndarray             # final state
 
 
-def objective(disc: Discretization, dt, n_steps, tol=1e-13, rhs_time=0, a_c0=None):
+def objective(disc: Discretization, dt, n_steps, tol=1e-13, rhs_time=0, a_c0=None, m0=0):
     """Forward run only: J = sum_m dt F_m^T M_c^-1 F_m and the final state."""
-    J, _, _, _, a = _forward(disc, dt, n_steps, tol, rhs_time, a_c0)
+    J, _, _, _, a = _forward(disc, dt, n_steps, tol, rhs_time, a_c0, m0)
     return J, a
 
 
-def _forward(disc, dt, n_steps, tol, rhs_time, a_c0):
+def _forward(disc, dt, n_steps, tol, rhs_time, a_c0, m0=0):
     p = disc.problem
     jn = disc.X_s[disc.n_idx]
     a = np.zeros(disc.n_c) if a_c0 is None else np.array(a_c0, dtype=np.float64)
     a_prev, u_full, F_all, g_all = [], [], [], []
     J = 0.0
     unit = p.with_(amplitude=1.0)
-    for m in range(1, n_steps + 1):
+    for m in range(m0 + 1, m0 + n_steps + 1):
         t_src = (m if rhs_time == 0 else m - 1) * dt
         g = source_current(unit, t_src)
         b = p.amplitude * g * jn - disc.K_cn.T @ a
@@ -101,11 +101,11 @@ def face_law_jacobian(disc: Discretization, u_full):
 
 
 def adjoint_gradient(disc: Discretization, dt, n_steps, tol=1e-13, rhs_time=0, a_c0=None,
-                     nonlinear_term=True):
-    """J and dJ/d(sigma_cell), dJ/d(coil amplitude) by the reverse sweep above.
-    ``nonlinear_term=False`` drops the Brauer derivative from J_H (used by a test
-    to show that the term matters)."""
-    J, a_prev, u_full, (F_all, g_all), a_end = _forward(disc, dt, n_steps, tol, rhs_time, a_c0)
+                     nonlinear_term=True, m0=0):
+    """J and dJ/d(sigma_cell), dJ/d(coil amplitude) by the reverse sweep above, over
+    steps m0+1 .. m0+n_steps from a_c0.  ``nonlinear_term=False`` drops the Brauer
+    derivative from J_H (used by a test to show that the term matters)."""
+    J, a_prev, u_full, (F_all, g_all), a_end = _forward(disc, dt, n_steps, tol, rhs_time, a_c0, m0)
     jn = disc.X_s[disc.n_idx]
     Mc = disc.M_c
     lam = np.zeros(disc.n_c)

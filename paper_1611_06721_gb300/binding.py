@@ -30,7 +30,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
            "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout", "mqs_set_blocks",
            "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms", "mqs_batch_tune",
-           "mqs_batch_destroy")
+           "mqs_batch_destroy", "mqs_adjoint", "mqs_loss")
 
 
 class Grid(C.Structure):
@@ -57,6 +57,11 @@ class Options(C.Structure):
 class LayoutInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("n_layout", C.c_long), ("n_c", C.c_long), ("n_n", C.c_long),
                 ("box_lo", C.c_int * 3), ("box_hi", C.c_int * 3)]
+
+
+class AdjointInfo(C.Structure):
+    _fields_ = [("objective", C.c_double), ("grad_amplitude", C.c_double),
+                ("forward_iterations", C.c_long), ("adjoint_iterations", C.c_long)]
 
 
 class StepStats(C.Structure):
@@ -126,6 +131,8 @@ def load():
         "mqs_batch_last_ms": ([V, P(D)], I),
         "mqs_batch_tune": ([V, I, P(D)], I),
         "mqs_batch_destroy": ([V], I),
+        "mqs_adjoint": ([H, I, P(D), P(AdjointInfo)], I),
+        "mqs_loss": ([H, I, P(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -274,6 +281,21 @@ class Solver:
 
     def mqs_step(self, nsteps):
         return self.step(nsteps)[1]
+
+    def adjoint(self, nsteps):
+        """Gradient of the eddy-current loss J over nsteps steps from the current state
+        (mqs_adjoint): returns (J, dJ/dsigma per cell as an (N, N, N) array indexed
+        [k, j, i], dJ/d amplitude, AdjointInfo)."""
+        g = np.zeros(self.n ** 3)
+        info = AdjointInfo()
+        self._check(self.lib.mqs_adjoint(self.h, nsteps, _dp(g), C.byref(info)))
+        return info.objective, g.reshape(self.n, self.n, self.n), info.grad_amplitude, info
+
+    def loss(self, nsteps):
+        """The eddy-current loss J over nsteps steps from the current state (mqs_loss)."""
+        v = C.c_double()
+        self._check(self.lib.mqs_loss(self.h, nsteps, C.byref(v)))
+        return v.value
 
     def set_blocks(self, nblk):
         """Persistent blocks of this handle's PCG kernels (0 = one per SM)."""
@@ -433,3 +455,33 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def eddy_loss(sigma_cell, amplitude, problem, options: SolverOptions, nsteps):
+    """The eddy-current loss J over `nsteps` steps from rest as a differentiable torch
+    function of the cell conductivities (tensor [N, N, N] indexed [k, j, i]) and the coil
+    amplitude (0-d tensor); dt, the edge classes and the waveform come from `problem` /
+    `options` and stay fixed.  The forward call runs mqs_adjoint (J and both gradients
+    at once), backward scales the stored gradients."""
+    import torch
+
+    class _EddyLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, sig, amp):
+            sg = sig.detach().to("cpu", torch.float64).numpy()
+            p = problem.with_(sigma_cell=sg, amplitude=float(amp))
+            s = Solver.from_problem(p, options)
+            try:
+                J, g, gI, _ = s.adjoint(nsteps)
+            finally:
+                s.close()
+            ctx.save_for_backward(torch.from_numpy(g).to(sig.device, sig.dtype),
+                                  torch.tensor(gI, dtype=amp.dtype, device=amp.device))
+            return torch.tensor(J, dtype=torch.float64, device=sig.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g, gI = ctx.saved_tensors
+            return gout.to(g.dtype) * g, gout.to(gI.dtype) * gI
+
+    return _EddyLoss.apply(sigma_cell, amplitude)

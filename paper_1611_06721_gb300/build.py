@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libmqs.so")
-UNITS = ["pcg.cu", "pcg_mixed.cu", "conductor.cu", "mrhs.cu", "api.cu", "noalloc.cu"]
+UNITS = ["pcg.cu", "pcg_mixed.cu", "conductor.cu", "mrhs.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

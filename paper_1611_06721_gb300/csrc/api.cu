@@ -58,6 +58,14 @@ struct mqs_handle {
   float *r32b = nullptr, *w32a = nullptr, *w32b = nullptr, *s32a = nullptr, *s32b = nullptr;  // its one-reduction form
   int* refin = nullptr;
   cudaStream_t own_st = nullptr;
+  // adjoint (discrete adjoint of the time loop)
+  uint8_t* condbox = nullptr;              // conducting flag per cell of the cell box
+  long ccells = 0;                         // cells of the cell box
+  double *rec_a = nullptr, *rec_F = nullptr;   // recording targets of the next conductor update
+  double* traj = nullptr;                  // [2 x steps x n_c]: a^{m-1}, then F_m
+  long traj_cap = 0;
+  AdjBufs adj{};
+  double *adjJ = nullptr, *adj_sig = nullptr;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -469,6 +477,17 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   }
   CK(cudaMemcpy(H->brauer, brbox.data(), ccells, cudaMemcpyHostToDevice));
   {
+    std::vector<uint8_t> cbox(ccells);
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i)
+          cbox[(i - lo[0]) + (size_t)(hi[0] - lo[0]) * ((j - lo[1]) + (size_t)(hi[1] - lo[1]) * (k - lo[2]))] =
+              sig[i + (long long)n * (j + (long long)n * k)] > 0.0 ? 1 : 0;
+    RK(dalloc(H, &H->condbox, ccells));
+    CK(cudaMemcpy(H->condbox, cbox.data(), ccells, cudaMemcpyHostToDevice));
+    H->ccells = (long)ccells;
+  }
+  {
     std::vector<double> nuinit(ccells, H->nu0);   // linear cells keep nu0 (cell_nu_kernel runs only with Brauer cells)
     CK(cudaMemcpy(H->nu, nuinit.data(), sizeof(double) * ccells, cudaMemcpyHostToDevice));
   }
@@ -534,7 +553,7 @@ int ensure_stats(mqs_handle* H, int nsteps) {
 // the new state goes to the other compact and layout buffers, then they swap
 int conductor_step(mqs_handle* H, const double* w, double dt, cudaStream_t st) {
   if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st));
-  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st, H->ac_full2));
+  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st, H->ac_full2, H->rec_F, H->rec_a));
   std::swap(H->ac, H->ac2);
   std::swap(H->ac_full, H->ac_full2);
   return MQS_OK;
@@ -664,6 +683,44 @@ int enqueue_step(mqs_handle* H, int s) {
   return MQS_OK;
 }
 
+void dfree(mqs_handle* H, void* p) {
+  for (size_t i = 0; i < H->allocs.size(); ++i)
+    if (H->allocs[i] == p) {
+      cudaFree(p);
+      H->allocs.erase(H->allocs.begin() + (long)i);
+      return;
+    }
+}
+
+// trajectory storage for nsteps steps and the adjoint work buffers (first use)
+int ensure_adjoint(mqs_handle* H, int nsteps) {
+  if (H->traj_cap < nsteps) {
+    if (H->traj) { CK(cudaStreamSynchronize(H->st)); dfree(H, H->traj); H->traj = nullptr; H->traj_cap = 0; }
+    RK(dalloc(H, &H->traj, (size_t)2 * nsteps * H->n_c));
+    H->traj_cap = nsteps;
+  }
+  if (H->adj.lam) return MQS_OK;
+  const size_t L = (size_t)H->len;
+  const int ex = H->cg.chi[0] - H->cg.clo[0] + 1, ey = H->cg.chi[1] - H->cg.clo[1] + 1,
+            ez = H->cg.chi[2] - H->cg.clo[2] + 1;
+  const size_t nq = (size_t)3 * ex * ey * ez;
+  RK(dalloc(H, &H->adj.lam, H->n_c));
+  RK(dalloc(H, &H->adj.gmc, H->n_c));
+  RK(dalloc(H, &H->adj.mu_full, L));
+  RK(dalloc(H, &H->adj.ap_full, L));
+  RK(dalloc(H, &H->adj.tS, (size_t)3 * H->ccells));
+  RK(dalloc(H, &H->adj.gI, 1));
+  RK(dalloc(H, &H->adj.part, 1024));
+  RK(dalloc(H, &H->adj.qmap, nq));
+  RK(dalloc(H, &H->adjJ, 1));
+  RK(dalloc(H, &H->adj_sig, H->ccells));
+  CK(cudaMemsetAsync(H->adj.mu_full, 0, sizeof(double) * L, H->st));
+  CK(cudaMemsetAsync(H->adj.ap_full, 0, sizeof(double) * L, H->st));
+  CK(cudaMemsetAsync(H->adj.qmap, 0xff, sizeof(int) * nq, H->st));     // -1: not a c-edge
+  RK(launch_adj_qmap(H->dg, H->cg, H->adj, H->st));
+  return MQS_OK;
+}
+
 int prepare_steps(mqs_handle* H, int nsteps) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
@@ -700,6 +757,117 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
   CK(cudaStreamSynchronize(H->st));
   if (per_step) memcpy(per_step, hs.data(), sizeof(mqs_step_stats) * nsteps);
   return check_stats(H, nsteps, hs.data(), derr);
+}
+
+namespace {
+
+// forward steps recording a^{m-1} and F_m of every step, then J on the device
+int adjoint_forward(mqs_handle* H, int nsteps, int stats_steps) {
+  if (!H || nsteps < 1) return MQS_ERR_ARG;
+  if (H->n_c < 1) return fail(H, MQS_ERR_ARG, "no conducting edges");
+  RK(prepare_steps(H, stats_steps));
+  RK(ensure_adjoint(H, nsteps));
+  const long nc = H->n_c;
+  double* trajA = H->traj;
+  double* trajF = H->traj + (size_t)nsteps * nc;
+  for (int s = 0; s < nsteps; ++s) {
+    H->rec_a = trajA + (size_t)s * nc;
+    H->rec_F = trajF + (size_t)s * nc;
+    const int rc = enqueue_step(H, s);
+    if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
+  }
+  H->rec_a = H->rec_F = nullptr;
+  return launch_adj_objective(H->cg, trajF, nsteps, H->dt, H->adj, H->adjJ, H->st);
+}
+
+}  // namespace
+
+int mqs_loss(mqs_handle* H, int nsteps, double* objective) {
+  if (!H) return MQS_ERR_ARG;
+  RK(adjoint_forward(H, nsteps, nsteps));
+  std::vector<mqs_step_stats> hs(nsteps);
+  int derr = 0;
+  double J = 0.0;
+  RK(fetch_stats(H, nsteps, hs.data(), &derr));
+  CK(cudaMemcpyAsync(&J, H->adjJ, sizeof(double), cudaMemcpyDeviceToHost, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  RK(check_stats(H, nsteps, hs.data(), derr));
+  if (objective) *objective = J;
+  return MQS_OK;
+}
+
+int mqs_adjoint(mqs_handle* H, int nsteps, double* grad_sigma_cell, mqs_adjoint_info* info) {
+  if (!H) return MQS_ERR_ARG;
+  const long m0 = H->m;
+  RK(adjoint_forward(H, nsteps, 2 * nsteps));
+  cudaStream_t st = H->st;
+  const long nc = H->n_c;
+  double* trajA = H->traj;
+  double* trajF = H->traj + (size_t)nsteps * nc;
+  // reverse sweep; the start-vector history now follows the adjoint solves
+  clear_history(H);
+  H->lx_valid = false;
+  CK(cudaMemsetAsync(H->adj.lam, 0, sizeof(double) * nc, st));
+  CK(cudaMemsetAsync(H->adj.gmc, 0, sizeof(double) * nc, st));
+  CK(cudaMemsetAsync(H->adj.gI, 0, sizeof(double), st));
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  for (int m = nsteps; m >= 1; --m) {
+    const int s = nsteps - m;
+    RK(launch_adj_mu(H->cg, trajF + (size_t)(m - 1) * nc, H->adj, H->dt, st));
+    RK(launch_scatter_c(H->cg, trajA + (size_t)(m - 1) * nc, H->adj.ap_full, 1.0, st));
+    const long mabs = m0 + m;
+    const double t_src = (H->opt.rhs_time == 0 ? (double)mabs : (double)(mabs - 1)) * H->dt;
+    // b' = -(h/nu0) K_cn^T mu: the right-hand side stencil with the coil switched off
+    const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+    RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->rhs_box, st));
+    int used_small = 0, init = 0;
+    RK(start_vector(H, H->b, H->x, st, &used_small, &init));
+    CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
+    RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
+    H->lx_valid = true;
+    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
+                                   H->dstats + nsteps + s);
+    RK(history_push(H, H->x, H->lx, st));
+    RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
+    RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
+    const CoilDrive unit{1.0, 1.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+    RK(launch_adj_coil(H->dg, coil, unit, H->x, H->adj, st));
+  }
+  clear_history(H);            // holds adjoint solutions, not solutions of the time loop
+  H->lx_valid = false;
+  RK(launch_adj_sigma(H->dg, H->cg, H->condbox, H->adj, H->adj_sig, st));
+  std::vector<mqs_step_stats> hs((size_t)2 * nsteps);
+  std::vector<double> sg(H->ccells);
+  double J = 0.0, gI = 0.0;
+  int derr = 0;
+  RK(fetch_stats(H, 2 * nsteps, hs.data(), &derr));
+  CK(cudaMemcpyAsync(&J, H->adjJ, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&gI, H->adj.gI, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sg.data(), H->adj_sig, sizeof(double) * H->ccells, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  RK(check_stats(H, 2 * nsteps, hs.data(), derr));
+  if (grad_sigma_cell) {
+    const int n = H->n;
+    std::fill(grad_sigma_cell, grad_sigma_cell + (size_t)n * n * n, 0.0);
+    const int* lo = H->cg.clo;
+    const int* hi = H->cg.chi;
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i)
+          grad_sigma_cell[i + (size_t)n * (j + (size_t)n * k)] =
+              sg[(i - lo[0]) + (size_t)(hi[0] - lo[0]) * ((j - lo[1]) + (size_t)(hi[1] - lo[1]) * (k - lo[2]))];
+  }
+  if (info) {
+    info->objective = J;
+    info->grad_amplitude = gI;
+    info->forward_iterations = 0;
+    info->adjoint_iterations = 0;
+    for (int s = 0; s < nsteps; ++s) {
+      info->forward_iterations += hs[s].iterations;
+      info->adjoint_iterations += hs[nsteps + s].iterations;
+    }
+  }
+  return MQS_OK;
 }
 
 int mqs_get_state(mqs_handle* H, double* a_c, size_t n_c, double* t, long* m) {

@@ -2,6 +2,7 @@
 // conducting-region update of the explicit Euler step (Sec. II, eq. (acm)).
 #include <cmath>
 #include "mqs_kernels.h"
+#include "conductor_fit.cuh"
 
 namespace mqs {
 
@@ -72,27 +73,6 @@ int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive dr
 }
 
 // ---- conducting region ------------------------------------------------------------
-__device__ __forceinline__ double lda(const double* ac, const double* w, double sw, int n, long long n3, int c,
-                                      int i, int j, int k) {
-  return fma(sw, ld(w, n, n3, c, i, j, k), ld(ac, n, n3, c, i, j, k));
-}
-// face fluxes of a = ac + sw w
-__device__ __forceinline__ double fbx(const double* ac, const double* w, double sw, int n, long long n3, int i,
-                                      int j, int k) {
-  return (lda(ac, w, sw, n, n3, 1, i, j, k) - lda(ac, w, sw, n, n3, 2, i, j, k)) +
-         (lda(ac, w, sw, n, n3, 2, i, j + 1, k) - lda(ac, w, sw, n, n3, 1, i, j, k + 1));
-}
-__device__ __forceinline__ double fby(const double* ac, const double* w, double sw, int n, long long n3, int i,
-                                      int j, int k) {
-  return (lda(ac, w, sw, n, n3, 2, i, j, k) - lda(ac, w, sw, n, n3, 0, i, j, k)) +
-         (lda(ac, w, sw, n, n3, 0, i, j, k + 1) - lda(ac, w, sw, n, n3, 2, i + 1, j, k));
-}
-__device__ __forceinline__ double fbz(const double* ac, const double* w, double sw, int n, long long n3, int i,
-                                      int j, int k) {
-  return (lda(ac, w, sw, n, n3, 0, i, j, k) - lda(ac, w, sw, n, n3, 1, i, j, k)) +
-         (lda(ac, w, sw, n, n3, 1, i + 1, j, k) - lda(ac, w, sw, n, n3, 0, i, j + 1, k));
-}
-
 __global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const double* w, int at_zero) {
   const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1], wz = cg.chi[2] - cg.clo[2];
   const long long ncell = (long long)wx * wy * wz;
@@ -115,17 +95,11 @@ __global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const doub
   }
 }
 
-__device__ __forceinline__ double cell_nu(const CondGeom& cg, int i, int j, int k) {
-  if (i < cg.clo[0] || j < cg.clo[1] || k < cg.clo[2] || i >= cg.chi[0] || j >= cg.chi[1] || k >= cg.chi[2])
-    return cg.nu0;
-  const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1];
-  return cg.nu[(i - cg.clo[0]) + wx * ((j - cg.clo[1]) + (long long)wy * (k - cg.clo[2]))];
-}
-
 // F_e = sum over the four faces f of e of C_fe M_nu[f] (C a)_f with
 // M_nu[f] = (nu of the two cells of f) / (2h); a_c update of eq. (acm).
 __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const double* w, double sw,
-                                   const double* a_in, double* a_out, double dt, double* ac_out) {
+                                   const double* a_in, double* a_out, double dt, double* ac_out, double* F_out,
+                                   double* a_prev_out) {
   const int n = g.n;
   const long long n3 = g.n3;
   const double ih2 = 0.5 / cg.h;
@@ -157,7 +131,10 @@ __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const 
       F = m1 * fbx(ac, w, sw, n, n3, i, j - 1, k) - m2 * fbx(ac, w, sw, n, n3, i, j, k) +
           m3 * fby(ac, w, sw, n, n3, i, j, k) - m4 * fby(ac, w, sw, n, n3, i - 1, j, k);
     }
-    const double v = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a_in[q]) : F;
+    const double a0 = a_in[q];
+    const double v = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a0) : F;
+    if (F_out) F_out[q] = F;            // recorded trajectory (adjoint)
+    if (a_prev_out) a_prev_out[q] = a0;
     a_out[q] = v;
     if (ac_out) ac_out[e] = v;      // the other layout buffer (read and written buffers differ)
   }
@@ -180,11 +157,12 @@ int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full,
 
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
                        double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
-                       double* ac_full_out) {
+                       double* ac_full_out, double* F_out, double* a_prev_out) {
   int blocks = (cg.n_c + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out);
+  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out, F_out,
+                                             a_prev_out);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -67,12 +67,44 @@ int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full,
 // F = (K(a) a)_c at every c-edge (a = ac_full + sign_w * w).  If dt != 0:
 // a_c_out = a_c_in - dt F / M_c, else F is written to a_c_out.  If
 // ac_full_out is given (a layout buffer other than ac_full), the result is
-// also written there at the c-edges.
+// also written there at the c-edges.  F_out / a_prev_out (nullable) receive
+// F and a_c_in per c-edge (the recorded trajectory of the adjoint).
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
                        double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
-                       double* ac_full_out = nullptr);
+                       double* ac_full_out = nullptr, double* F_out = nullptr, double* a_prev_out = nullptr);
 // scatter compact a_c into the layout vector ac_full (c-edges only)
 int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st);
 
+
+// ---- discrete adjoint of the time loop (adjoint.cu) ----
+struct AdjBufs {
+  double* lam;            // [n_c] dJ/da^m
+  double* gmc;            // [n_c] dJ/dM_c accumulated
+  double* mu_full;        // layout: mu on c-edges, zero elsewhere
+  double* ap_full;        // layout: a^{m-1} on c-edges, zero elsewhere
+  double* tS;             // 3 x cell-box: t_c S_{c,d} per Brauer cell (0 elsewhere)
+  double* gI;             // [1] dJ/d(coil amplitude) accumulated
+  double* part;           // >= 1024 doubles of reduction scratch
+  int* qmap;              // 3 x (node box + 1)^3: compact c-index of an edge or -1
+};
+// mu = dt M_c^-1 (2F - lam) scattered to mu_full; gmc += dt F (lam - F) / M_c^2
+int launch_adj_mu(const CondGeom& cg, const double* F, const AdjBufs& ab, double dt, cudaStream_t st);
+// per Brauer cell: nu from a^{m-1} (into cg.nu) and t_c S_c from the forward fluxes of
+// ap_full and the adjoint fluxes of mu_full + x
+int launch_adj_cell(const DevGeom& dg, const CondGeom& cg, const double* x, const AdjBufs& ab, cudaStream_t st);
+// lam += (C^T J_H^T C [mu; x])_c
+int launch_adj_lambda(const DevGeom& dg, const CondGeom& cg, const double* x, const AdjBufs& ab, cudaStream_t st);
+// gI += -g(t) X_s . x over the coil loop (g: the unit-amplitude waveform of drv at drv.t)
+int launch_adj_coil(const DevGeom& dg, const CoilGeom& coil, const CoilDrive& drv, const double* x,
+                    const AdjBufs& ab, cudaStream_t st);
+// J = dt sum over steps and c-edges of F^2 / M_c  ->  *J_dev
+int launch_adj_objective(const CondGeom& cg, const double* F_traj, int nsteps, double dt, const AdjBufs& ab,
+                         double* J_dev, cudaStream_t st);
+// qmap from the compact c-edge list (node box lo = cg.clo, extent cg.chi - cg.clo + 1 per axis)
+int launch_adj_qmap(const DevGeom& dg, const CondGeom& cg, const AdjBufs& ab, cudaStream_t st);
+// dJ/dsigma per cell of the cell box: (h/4) * sum of gmc over the cell's c-edges where
+// cond[cell] != 0, else 0
+int launch_adj_sigma(const DevGeom& dg, const CondGeom& cg, const uint8_t* cond, const AdjBufs& ab, double* out,
+                     cudaStream_t st);
 
 }  // namespace mqs
