@@ -218,11 +218,13 @@ def run_ours(args, rank, ws, local, dist):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     p = W.config_nonlinear_iron() if args.grid == 64 else W.scaled_nonlinear(args.grid)
-    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD}[args.start]
-    depth = args.depth if args.depth else (8 if args.start == "spe" else 20)
+    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD,
+            "cspe": pkg.START_CSPE}[args.start]
+    depth = args.depth if args.depth else {"spe": 8, "cspe": 16}.get(args.start, 20)
     opts = pkg.SolverOptions(tol=1e-10, start_mode=mode,
-                             spe_depth=depth if args.start == "spe" else 8,
+                             spe_depth=depth if args.start in ("spe", "cspe") else 8,
                              pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
+                             cspe_period=args.cspe_period,
                              precision=args.precision)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
@@ -314,7 +316,8 @@ def run_ours(args, rank, ws, local, dist):
             "data": "synthetic",
             "config": {"workload": workload_name(p), "grid": p.N, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
-                       "start_vector": args.start + (str(depth) if args.start in ("spe", "pod") else ""),
+                       "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
+                                       + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
                        "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
                        "pcg": "two reductions per iteration" if args.pcg_variant == 0 else "one reduction per iteration",
                        "l2": "flushed between timed steps by a 256 MiB write",
@@ -591,10 +594,11 @@ def run_adjoint(args):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1), out
 
-    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD}[args.start]
-    depth = args.depth if args.depth else (8 if args.start == "spe" else 20)
-    sopts = dict(start_mode=mode, spe_depth=depth if args.start == "spe" else 8,
-                 pod_snapshots=depth if args.start == "pod" else 20, dt=dt)
+    mode = {"zero": pkg.START_ZERO, "prev": pkg.START_PREV, "spe": pkg.START_SPE, "pod": pkg.START_POD,
+            "cspe": pkg.START_CSPE}[args.start]
+    depth = args.depth if args.depth else {"spe": 8, "cspe": 16}.get(args.start, 20)
+    sopts = dict(start_mode=mode, spe_depth=depth if args.start in ("spe", "cspe") else 8,
+                 pod_snapshots=depth if args.start == "pod" else 20, dt=dt, cspe_period=args.cspe_period)
 
     def fresh(tol, problem=None):
         sv = pkg.Solver.from_problem(problem or p, pkg.SolverOptions(tol=tol, **sopts))
@@ -643,9 +647,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
-    ap.add_argument("--start", choices=["zero", "prev", "spe", "pod"], default="spe",
+    ap.add_argument("--start", choices=["zero", "prev", "spe", "pod", "cspe"], default="spe",
                     help="start vector of each step's solve (default: SPE)")
-    ap.add_argument("--depth", type=int, default=0, help="SPE depth or POD snapshot count (default 8 / 20)")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="SPE depth, CSPE column cap or POD snapshot count (default 8 / 16 / 20)")
+    ap.add_argument("--cspe-period", type=int, default=0, help="CSPE: steps between freezes (default 25)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP64 PCG (default); 1: FP32 inner solves in FP64 refinement (same tolerance)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],

@@ -65,6 +65,8 @@ extern "C" {
 #define MQS_START_PREV 1            /* x0 = solution of the previous step  */
 #define MQS_START_SPE  2            /* eq. (SPE_x0), last spe_depth sols   */
 #define MQS_START_POD  3            /* eq. (POD_x0), last pod_snapshots    */
+#define MQS_START_CSPE 4            /* eq. (SPE_x0) on the cascaded basis:
+                                       frozen past solutions + the newest  */
 
 typedef struct mqs_handle mqs_handle;
 
@@ -94,7 +96,7 @@ typedef struct {
 
 /* Options.  tol: PCG stopping rule ||b - K_n x||_2 <= tol ||b||_2 (true
  * residual).  maxit: PCG iteration cap.  start_mode: MQS_START_*.
- * spe_depth (1..16), pod_snapshots (1..40), eps_pod (POD truncation
+ * spe_depth (1..16; CSPE 1..19), pod_snapshots (1..40), eps_pod (POD truncation
  * sigma_i/sigma_1 >= eps_pod, eq. (relSV2)), eps_lin (SPE drop tolerance).
  * dt: explicit Euler step (s); may be set later with mqs_set_dt.
  * rhs_time: 0 = source at t_m (as printed in eq. (acm)), 1 = at t_{m-1}.
@@ -121,6 +123,17 @@ typedef struct {
                              and solution update in FP64; same tol). */
     double inner_tol;     /* precision 1: smallest residual reduction an inner
                              solve aims at (<= 0: 1e-5) */
+    int    cspe_period;   /* MQS_START_CSPE (Sec. III "cascaded SPE", Sec. IV):
+                             the basis holds frozen past solutions and one live
+                             column, the newest solution, replaced every step;
+                             every cspe_period steps (<= 0: 25) the live column
+                             is frozen and the basis grows, up to spe_depth
+                             columns (1..19, "below 20").  Frozen columns are
+                             kept K-orthonormal (two-pass Gram-Schmidt in the K
+                             inner product with the stored K-images, no stencil),
+                             the newest solution is projected against them every
+                             step.  mqs_push_history makes the pushed solution the
+                             newest column; columns are frozen only by steps. */
 } mqs_options;
 
 typedef struct {
@@ -207,6 +220,15 @@ int mqs_get_state_dev(mqs_handle* h, double* a_c_dev, size_t n_c, void* stream);
 int mqs_set_state_dev(mqs_handle* h, const double* a_c_dev, size_t n_c, void* stream);
 /* Copies the latest PCG solution w (layout vector, zero off n-edges). */
 int mqs_get_solution(mqs_handle* h, double* w_layout);
+/* mqs_solve_an: a_n^m of eq. (anm) for the current state: one PCG solve of
+ * K_n a_n = j^m_{s,n} - K_cn^T a_c^m (source at the time level the last step
+ * used, new conductor state), started from the step's solution w and run to
+ * the handle's tol.  (The step itself needs only w = K_n^+ (j^m - K_cn^T
+ * a_c^{m-1}); a_n^m is an output on request.)  a_n (host, layout vector,
+ * nullable) receives the solution; info (nullable) the PCG result.  The time
+ * loop's state, history and w are left as they were.  Errors: MQS_ERR_ARG,
+ * MQS_ERR_CUDA and the PCG statuses. */
+int mqs_solve_an(mqs_handle* h, double* a_n_layout, mqs_pcg_info* info);
 int mqs_reset_history(mqs_handle* h);
 
 /* pcg_solve: Sec. III eq. (mrhs) - Jacobi-preconditioned CG for K_n x = b

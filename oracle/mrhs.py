@@ -25,9 +25,17 @@ Readings of the printed equations used here:
 * the small Galerkin system is solved by Cholesky, or by a symmetric
   eigen-solve truncated at ``1e-14 lambda_max`` when Cholesky fails.
 
+CSPE (Sec. III, "cascaded SPE"; Sec. IV): only the last column of ``U_SPE``
+changes from step to step, so the products with the other columns are reused, and
+the number of columns grows during the run, staying below 20.  Reading of that
+policy (the paper gives no schedule): the basis holds frozen past solutions plus
+one live column, the newest solution; every ``period`` steps the live column is
+frozen (the solutions of steps P, 2P, 3P, ... are kept) until ``depth`` columns
+are reached, after which only the live column changes (``CspeBasis``).
+
 Parity: pinned (Galerkin orthogonality, orthonormality, exact recovery when the
 solution lies in the subspace, constructed snapshot matrices with known
-singular values).
+singular values, the CSPE column schedule).
 """
 from __future__ import annotations
 
@@ -96,3 +104,27 @@ def pod_start(K_n, snapshots, b, eps_pod=1e-4):
     k = int(np.count_nonzero(sig / sig[0] >= eps_pod))
     info = float(sig[:k].sum() / sig.sum())
     return galerkin_start(K_n, U[:, :k], b), k, sig, info
+
+
+class CspeBasis:
+    """Columns of the cascaded SPE basis: frozen past solutions and the live one."""
+
+    def __init__(self, period=25, depth=8):
+        self.period = period if period > 0 else 25
+        self.depth = depth
+        self.frozen = []        # oldest first
+        self.live = None
+        self.count = 0
+
+    def push(self, w):
+        """Record the solution of the step just finished (push number count+1)."""
+        self.count += 1
+        if self.live is not None and (self.count - 1) % self.period == 0 and len(self.frozen) + 1 < self.depth:
+            self.frozen.append(self.live)
+        self.live = np.array(w, dtype=np.float64)
+
+    def window(self):
+        """The basis columns, newest first (the live column, then the frozen ones)."""
+        if self.live is None:
+            return []
+        return [self.live] + self.frozen[::-1]

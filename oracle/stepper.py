@@ -31,11 +31,11 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-from .mrhs import pod_start, spe_start
+from .mrhs import CspeBasis, pod_start, spe_start
 from .operators import Discretization
 from .pcg import STATUS_OK, pcg_jacobi
 
-START_ZERO, START_PREV, START_SPE, START_POD = 0, 1, 2, 3
+START_ZERO, START_PREV, START_SPE, START_POD, START_CSPE = 0, 1, 2, 3, 4
 
 
 def source_current(problem, t):
@@ -111,7 +111,7 @@ class RunResult:
 def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
                        spe_depth=8, pod_snapshots=20, tol=1e-10, maxit=100000,
                        rhs_time=0, eps_lin=1e-10, eps_pod=1e-4, a_c0=None,
-                       m0=0, literal=False, history=None, source_scale=1.0):
+                       m0=0, literal=False, history=None, source_scale=1.0, cspe_period=25):
     """Run ``n_steps`` explicit Euler steps starting after step ``m0``.
 
     ``history`` (newest first) may carry earlier PCG solutions for the start
@@ -120,6 +120,7 @@ def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
     p = disc.problem
     a_c = np.zeros(disc.n_c) if a_c0 is None else np.array(a_c0, dtype=np.float64)
     hist = history if history is not None else []
+    cspe = CspeBasis(cspe_period, spe_depth)
     depth = max(spe_depth if start_mode == START_SPE else pod_snapshots if start_mode == START_POD else 1, 1)
     jn = disc.X_s[disc.n_idx]
     records = []
@@ -129,7 +130,9 @@ def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
         i_t = source_scale * source_current(p, t_src)
         b = i_t * jn - disc.K_cn.T @ a_c
         rank, info_ratio = 0, float("nan")
-        if start_mode == START_ZERO or not hist:
+        if start_mode == START_CSPE:
+            x0, rank = spe_start(disc.K_n, cspe.window(), b, eps_lin)
+        elif start_mode == START_ZERO or not hist:
             x0 = np.zeros(disc.n_n)
         elif start_mode == START_PREV:
             x0 = hist[0].copy()
@@ -157,4 +160,5 @@ def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
         a_c = a_c - dt * F / disc.M_c
         hist.insert(0, w.copy())
         del hist[depth:]
+        cspe.push(w)
     return RunResult(a_c, w, records)

@@ -21,7 +21,7 @@ MQS_OK = 0
 ERRORS = {-1: "MQS_ERR_ARG", -2: "MQS_ERR_CUDA", -3: "MQS_ERR_OOM", -4: "MQS_ERR_NOT_CONVERGED",
           -5: "MQS_ERR_BREAKDOWN", -6: "MQS_ERR_NAN", -7: "MQS_ERR_UNSTABLE", -8: "MQS_ERR_TIMEOUT",
           -9: "MQS_ERR_UNIMPLEMENTED"}
-START_ZERO, START_PREV, START_SPE, START_POD = 0, 1, 2, 3
+START_ZERO, START_PREV, START_SPE, START_POD, START_CSPE = 0, 1, 2, 3, 4
 
 EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_dt", "mqs_get_dt",
            "mqs_set_options", "mqs_lambda_max", "mqs_step", "mqs_get_state", "mqs_set_state",
@@ -30,7 +30,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
            "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout", "mqs_set_blocks",
            "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms", "mqs_batch_tune",
-           "mqs_batch_destroy", "mqs_adjoint", "mqs_loss")
+           "mqs_batch_destroy", "mqs_adjoint", "mqs_loss", "mqs_solve_an")
 
 
 class Grid(C.Structure):
@@ -51,7 +51,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("cspe_period", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -133,6 +133,7 @@ def load():
         "mqs_batch_destroy": ([V], I),
         "mqs_adjoint": ([H, I, P(D), P(AdjointInfo)], I),
         "mqs_loss": ([H, I, P(D)], I),
+        "mqs_solve_an": ([H, P(D), P(PcgInfo)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -173,11 +174,12 @@ class SolverOptions:
     pcg_variant: int = 0
     precision: int = 0
     inner_tol: float = 0.0
+    cspe_period: int = 0
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
-                       self.inner_tol)
+                       self.inner_tol, self.cspe_period)
 
 
 class Solver:
@@ -290,6 +292,13 @@ class Solver:
         info = AdjointInfo()
         self._check(self.lib.mqs_adjoint(self.h, nsteps, _dp(g), C.byref(info)))
         return info.objective, g.reshape(self.n, self.n, self.n), info.grad_amplitude, info
+
+    def solve_an(self):
+        """a_n^m of eq. (anm) for the current state (mqs_solve_an): (layout vector, PcgInfo)."""
+        a = np.empty(self.n_layout)
+        info = PcgInfo()
+        self._check(self.lib.mqs_solve_an(self.h, _dp(a), C.byref(info)))
+        return a, info
 
     def loss(self, nsteps):
         """The eddy-current loss J over nsteps steps from the current state (mqs_loss)."""

@@ -48,6 +48,12 @@ struct mqs_handle {
   double* pod_LX[kMaxPod] = {};
   double *pod_G = nullptr, *pod_A = nullptr;
   int pod_m = 0, pod_next = 0;
+  int cspe_k = 0;            // CSPE: K-orthonormal frozen columns (POD ring slots 0..k-1)
+  bool cspe_live = false;    // a newest solution exists (H->x)
+  bool cspe_projected = false;   // this step's start vector projected it (cspe_scal, work vectors valid)
+  bool cspe_froze = false;
+  double* cspe_scal = nullptr;
+  long cspe_count = 0;       // solutions pushed since the history was cleared
   double *tspart = nullptr, *coef = nullptr, *sigma = nullptr, *scal = nullptr;
   SmallOut* small = nullptr;
   mqs_step_stats* dstats = nullptr;
@@ -226,6 +232,11 @@ MutVecSet mvs(double* const* a, int m) {
 }
 
 // push solution w (layout, physical units) with L w into the active history
+CspeBufs cspe_bufs(mqs_handle* H) {
+  // frozen columns in POD ring slots 0..18, work vectors in the last two slots
+  return CspeBufs{H->pod_X, H->pod_LX, H->pod_X[kMaxPod - 1], H->pod_LX[kMaxPod - 1], H->pod_X[kMaxPod - 2],
+                  H->pod_LX[kMaxPod - 2], H->cspe_scal};
+}
 int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t st) {
   const int mode = H->opt.start_mode;
   if (mode == MQS_START_SPE) {
@@ -243,7 +254,24 @@ int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t 
                 H->pod_A, st));
     H->pod_m = mn;
     H->pod_next = (slot + 1) % np;
+  } else if (mode == MQS_START_CSPE) {
+    // push c (1-based): the newest solution of the previous step (projected by this step's
+    // start vector) is frozen when c-1 is a multiple of the period, so the frozen columns
+    // are the solutions of steps P, 2P, 3P, ...; the live column is always the newest
+    // solution (H->x, L x in H->lx), so nothing is copied otherwise
+    const int period = H->opt.cspe_period > 0 ? H->opt.cspe_period : 25;
+    H->cspe_count += 1;
+    H->cspe_froze = false;
+    if (H->cspe_live && H->cspe_projected && (H->cspe_count - 1) % period == 0 &&
+        H->cspe_k + 1 < H->opt.spe_depth) {
+      RK(cspe_freeze(cspe_bufs(H), H->cspe_k, H->len, st));
+      H->cspe_k += 1;
+      H->cspe_froze = true;
+    }
+    H->cspe_live = true;
+    H->cspe_projected = false;
   }
+  (void)w; (void)lw;
   return MQS_OK;
 }
 
@@ -277,6 +305,17 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
       *used_small = 1;
       *init = 0;
       break;
+    case MQS_START_CSPE:
+      if (!H->cspe_live) { *init = 2; break; }
+      // the live column is the newest solution, which the start vector overwrites in place
+      if (x != H->x) return fail(H, MQS_ERR_ARG, "CSPE start vector must be formed in the step's solution buffer");
+      if (!H->lx_valid) RK(launch_apply_L(H->dg, H->x, H->lx, 1.0, H->full, st));
+      RK(cspe_x0(cspe_bufs(H), H->cspe_k, H->x, H->lx, b, x, H->len, H->opt.eps_lin, H->tspart, H->coef, H->small,
+                 st));
+      H->cspe_projected = true;
+      *used_small = 1;
+      *init = 0;
+      break;
     case MQS_START_POD: {
       if (H->pod_m == 0) { *init = 2; break; }
       RK(pod_x0(vs(H->pod_X, H->opt.pod_snapshots), H->pod_m, H->pod_G, H->pod_A, b, x, H->len, H->opt.eps_pod,
@@ -302,6 +341,11 @@ long start_launches(const mqs_handle* H) {
       return H->pod_m == 0 ? 0 : (H->pod_m + 7) / 8 + 2;
     case MQS_START_PREV:
       return H->lx_valid ? 1 : 0;
+    case MQS_START_CSPE: {
+      if (!H->cspe_live) return 0;
+      const int k = H->cspe_k;
+      return (H->lx_valid ? 0 : 1) + (k + 8) / 8 + 3 + (k > 0 ? (k + 7) / 8 + 3 : 0) + (k + 8) / 8 + 3;
+    }
     default:
       return 0;
   }
@@ -310,6 +354,7 @@ long history_launches(const mqs_handle* H) {
   switch (H->opt.start_mode) {
     case MQS_START_SPE: return 1;
     case MQS_START_POD: return (H->pod_m + 7) / 8 + 1;   // after the push
+    case MQS_START_CSPE: return H->cspe_froze ? 1 : 0;
     default: return 0;
   }
 }
@@ -317,8 +362,13 @@ long history_launches(const mqs_handle* H) {
 int validate_options(const mqs_options* o, std::string& why) {
   if (!(o->tol > 0.0) || o->tol >= 1.0) { why = "tol must lie in (0, 1)"; return MQS_ERR_ARG; }
   if (o->maxit < 1) { why = "maxit must be positive"; return MQS_ERR_ARG; }
-  if (o->start_mode < 0 || o->start_mode > 3) { why = "unknown start mode"; return MQS_ERR_ARG; }
-  if (o->spe_depth < 1 || o->spe_depth > kMaxSpe) { why = "spe_depth must be in [1, 16]"; return MQS_ERR_ARG; }
+  if (o->start_mode < 0 || o->start_mode > 4) { why = "unknown start mode"; return MQS_ERR_ARG; }
+  if (o->start_mode == MQS_START_CSPE) {
+    if (o->spe_depth < 1 || o->spe_depth > kMaxCspe) { why = "CSPE spe_depth must be in [1, 19]"; return MQS_ERR_ARG; }
+  } else if (o->spe_depth < 1 || o->spe_depth > kMaxSpe) {
+    why = "spe_depth must be in [1, 16]";
+    return MQS_ERR_ARG;
+  }
   if (o->pod_snapshots < 1 || o->pod_snapshots > kMaxPod) { why = "pod_snapshots must be in [1, 40]"; return MQS_ERR_ARG; }
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
@@ -459,6 +509,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->scal, 4));
   RK(dalloc(H, &H->small, 1));
   RK(dalloc(H, &H->refin, 1));
+  RK(dalloc(H, &H->cspe_scal, 2));
   RK(dalloc(H, &H->pod_G, kMaxPod * kMaxPod));
   RK(dalloc(H, &H->pod_A, kMaxPod * kMaxPod));
   for (int a = 0; a < kMaxSpe; ++a) { RK(dalloc(H, &H->spe_D[a], L)); RK(dalloc(H, &H->spe_LD[a], L)); }
@@ -539,6 +590,10 @@ void clear_history(mqs_handle* H) {
   H->spe_m = 0;
   H->pod_m = 0;
   H->pod_next = 0;
+  H->cspe_k = 0;
+  H->cspe_live = false;
+  H->cspe_projected = false;
+  H->cspe_count = 0;
 }
 
 int ensure_stats(mqs_handle* H, int nsteps) {
@@ -625,7 +680,7 @@ int mqs_set_options(mqs_handle* H, const mqs_options* o) {
   std::string why;
   if (validate_options(o, why) != MQS_OK) return fail(H, MQS_ERR_ARG, why.c_str());
   const bool reset = o->start_mode != H->opt.start_mode || o->spe_depth != H->opt.spe_depth ||
-                     o->pod_snapshots != H->opt.pod_snapshots;
+                     o->pod_snapshots != H->opt.pod_snapshots || o->cspe_period != H->opt.cspe_period;
   const double dt = H->dt;
   H->opt = *o;
   H->dt = (o->dt > 0.0) ? o->dt : dt;
@@ -723,7 +778,7 @@ int ensure_adjoint(mqs_handle* H, int nsteps) {
 
 int prepare_steps(mqs_handle* H, int nsteps) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
-  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
+  if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
   return ensure_stats(H, nsteps);
 }
 
@@ -920,6 +975,22 @@ int mqs_get_solution(mqs_handle* H, double* w) {
   return MQS_OK;
 }
 
+int mqs_solve_an(mqs_handle* H, double* a_n, mqs_pcg_info* info) {
+  if (!H) return MQS_ERR_ARG;
+  cudaStream_t st = H->st;
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  const long m = H->m;
+  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+  // right-hand side j^m_{s,n} - K_cn^T a_c^m (eq. (anm)), scaled by h / nu0 as in a step
+  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
+  RK(launch_rhs(H->dg, H->ac_full, H->bu, drv, coil, H->rhs_box, st));
+  CK(cudaMemcpyAsync(H->xu, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+  RK(run_pcg(H, H->bu, H->xu, H->opt.tol, H->opt.maxit, st));
+  if (a_n) CK(cudaMemcpyAsync(a_n, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
+  return read_pcg(H, info, st);
+}
+
 int pcg_solve_dev(mqs_handle* H, const double* b_dev, double* x_dev, double tol, int maxit, mqs_pcg_info* info,
                   void* stream) {
   if (!H || !b_dev || !x_dev) return MQS_ERR_ARG;
@@ -1063,13 +1134,18 @@ int mqs_timing_get(mqs_handle* H, mqs_timing* out) {
 int mqs_push_history(mqs_handle* H, const double* w) {
   if (!H || !w) return MQS_ERR_ARG;
   cudaStream_t st = H->st;
-  if (H->opt.start_mode == MQS_START_POD) RK(ensure_pod(H));
+  if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
   CK(cudaMemcpyAsync(H->tmp, w, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
   RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
   RK(launch_apply_L(H->dg, H->tmp2, H->tmp, 1.0, H->full, st));
   if (H->opt.start_mode == MQS_START_PREV) {
     CK(cudaMemcpyAsync(H->x, H->tmp2, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
     H->lx_valid = false;
+  } else if (H->opt.start_mode == MQS_START_CSPE) {
+    // the pushed solution becomes the newest (live) column, with its image
+    CK(cudaMemcpyAsync(H->x, H->tmp2, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(H->lx, H->tmp, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+    H->lx_valid = true;
   }
   RK(history_push(H, H->tmp2, H->tmp, st));
   CK(cudaStreamSynchronize(st));

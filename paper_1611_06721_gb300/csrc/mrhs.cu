@@ -576,6 +576,40 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
   }
 }
 
+// ---- cascaded SPE (K-orthonormal frozen columns + the newest solution) ----
+__device__ __forceinline__ double tile_dot(const double* part, int nblk, int q) {
+  return sum_part(part + (size_t)(q / 8) * nblk * kTileSlots, nblk, 64 + (q % 8));
+}
+
+// coef = [1, -h_1 .. -h_k] with h_i = product i; scal[0] = product k (x.Lx) when with_norm
+__global__ void cspe_proj_kernel(const double* part, int nblk, int k, int with_norm, double* coef, double* scal) {
+  for (int q = threadIdx.x; q <= k; q += blockDim.x) coef[q] = (q == 0) ? 1.0 : -tile_dot(part, nblk, q - 1);
+  if (with_norm && threadIdx.x == 0) scal[0] = tile_dot(part, nblk, k);
+}
+
+// x0 coefficients [Q^T b, (z.b)/zeta] from partC (Q_i.b, then z.b) and partD (z.Lz)
+__global__ void cspe_coef_kernel(const double* partC, const double* partD, int nblk, int k, double drop2,
+                                 double* coef, double* scal, SmallOut* out) {
+  for (int q = threadIdx.x; q < k; q += blockDim.x) coef[q] = tile_dot(partC, nblk, q);
+  if (threadIdx.x == 0) {
+    const double zeta = tile_dot(partD, nblk, 0), zb = tile_dot(partC, nblk, k);
+    const bool keep = zeta > 0.0 && zeta > drop2 * scal[0];
+    coef[k] = keep ? zb / zeta : 0.0;
+    scal[1] = keep ? rsqrt(zeta) : 0.0;
+    out->rank = k + (keep ? 1 : 0);
+    out->info = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kTS) cspe_freeze_kernel(const double* z, const double* lz, double* q, double* p,
+                                                          long long len, const double* scal) {
+  const double s = scal[1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    q[e] = s * z[e];
+    p[e] = s * lz[e];
+  }
+}
+
 // ---- host launchers --------------------------------------------------------------------
 static int ts_max_blocks() {
   static int nb = 0;
@@ -666,6 +700,66 @@ int pod_x0(const VecSet& X, int m, const double* G, const double* A, const doubl
   pod_solve_kernel<<<1, 256, 0, st>>>(G, A, part, nb, m, eps_pod, coef, sigma, out);
   if (x0 && r0 && LX) launch_lincomb_res(X, *LX, coef, m, b, len, x0, r0, nb, st);
   else if (x0) launch_lincomb(X, coef, m, len, x0, nb, st);
+  return chk();
+}
+
+// products X_q . v for q < m (tiles of eight, kConly) into part tiles 0 .. ceil(m/8)-1
+static void dots_against(const VecSet& X, int m, const double* v, long long len, double* part, int nb,
+                         cudaStream_t st) {
+  for (int t = 0; t < (m + 7) / 8; ++t) {
+    VecSet Ax;
+    const int mb = (m - 8 * t) < 8 ? (m - 8 * t) : 8;
+    for (int q = 0; q < 8; ++q) Ax.v[q] = X.v[8 * t + (q < mb ? q : 0)];
+    dots_kernel<kConly><<<nb, kTS, 0, st>>>(Ax, Ax, v, 0, mb, len, part + (size_t)t * nb * kTileSlots);
+  }
+}
+
+int cspe_x0(const CspeBufs& cb, int k, const double* x, const double* lx, const double* b, double* x0,
+            long long len, double eps_lin, double* part, double* coef, SmallOut* out, cudaStream_t st) {
+  if (k < 0 || k + 1 > kMaxCspe) return MQS_ERR_ARG;
+  const int nb = ts_blocks(len);
+  double* partC = part;                                   // tiles 0 .. 2
+  double* partD = part + (size_t)3 * nb * kTileSlots;     // tile 3
+  VecSet PX{}, V{}, W{};
+  for (int i = 0; i < k; ++i) PX.v[i] = cb.P[i];
+  PX.v[k] = lx;
+  // pass 1: h = P^T x (= Q^T L x) and x.Lx; z = x - Q h, Lz = Lx - P h
+  dots_against(PX, k + 1, x, len, part, nb, st);
+  cspe_proj_kernel<<<1, 32, 0, st>>>(part, nb, k, 1, coef, cb.scal);
+  V.v[0] = x;
+  W.v[0] = lx;
+  for (int i = 0; i < k; ++i) { V.v[1 + i] = cb.Q[i]; W.v[1 + i] = cb.P[i]; }
+  launch_lincomb(V, coef, k + 1, len, cb.z, nb, st);
+  launch_lincomb(W, coef, k + 1, len, cb.lz, nb, st);
+  const double* zf = cb.z;
+  const double* lzf = cb.lz;
+  if (k > 0) {
+    // pass 2 (re-orthogonalisation against the rounding of pass 1)
+    dots_against(PX, k, cb.z, len, part, nb, st);
+    cspe_proj_kernel<<<1, 32, 0, st>>>(part, nb, k, 0, coef, cb.scal);
+    V.v[0] = cb.z;
+    W.v[0] = cb.lz;
+    launch_lincomb(V, coef, k + 1, len, cb.z2, nb, st);
+    launch_lincomb(W, coef, k + 1, len, cb.lz2, nb, st);
+    zf = cb.z2;
+    lzf = cb.lz2;
+  }
+  // Galerkin system on the K-orthonormal basis: c = Q^T b, z.b, zeta = z.Lz
+  VecSet QX{}, ZX{};
+  for (int i = 0; i < k; ++i) QX.v[i] = cb.Q[i];
+  QX.v[k] = zf;
+  ZX.v[0] = zf;
+  dots_against(QX, k + 1, b, len, partC, nb, st);
+  dots_against(ZX, 1, lzf, len, partD, nb, st);
+  cspe_coef_kernel<<<1, 32, 0, st>>>(partC, partD, nb, k, eps_lin * eps_lin, coef, cb.scal, out);
+  launch_lincomb(QX, coef, k + 1, len, x0, nb, st);
+  return chk();
+}
+
+int cspe_freeze(const CspeBufs& cb, int k, long long len, cudaStream_t st) {
+  const double* z = k > 0 ? cb.z2 : cb.z;
+  const double* lz = k > 0 ? cb.lz2 : cb.lz;
+  cspe_freeze_kernel<<<ts_blocks(len) * 2, kTS, 0, st>>>(z, lz, cb.Q[k], cb.P[k], len, cb.scal);
   return chk();
 }
 

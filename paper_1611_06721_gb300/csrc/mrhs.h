@@ -6,6 +6,7 @@ namespace mqs {
 
 constexpr int kMaxSpe = 16;
 constexpr int kMaxPod = 40;
+constexpr int kMaxCspe = 19;        // CSPE basis: frozen columns + the live one (below 20, Sec. IV)
 constexpr int kMaxVec = 40;
 constexpr int kTileSlots = 72;      // 8 x 8 products + 8 right-hand side products
 
@@ -25,5 +26,22 @@ int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
            double eps_pod, double* part, double* coef, double* sigma, SmallOut* out, cudaStream_t st,
            const VecSet* LX = nullptr, double* r0 = nullptr);
+
+// CSPE start vector (Sec. III, "cascaded SPE"): Galerkin projection of K_n x = b onto
+// span(Q_1 .. Q_k, x) with Q K-orthonormal frozen past solutions (images P = L Q) and x
+// the newest solution (lx = L x).  x is projected out against Q twice (vector-level
+// Gram-Schmidt in the K inner product, with the stored images: no stencil), giving z and
+// zeta = z.Lz; the new direction is dropped when zeta <= eps_lin^2 x.Lx.  Then
+// x0 = Q (Q^T b) + z (z^T b) / zeta.  x0 may be the buffer x.
+struct CspeBufs {
+  double* const* Q;       // k frozen columns
+  double* const* P;       // their images
+  double *z, *lz, *z2, *lz2;
+  double* scal;           // [2]: x.Lx, then 1/sqrt(zeta) (0 when the new direction is dropped)
+};
+int cspe_x0(const CspeBufs& cb, int k, const double* x, const double* lx, const double* b, double* x0,
+            long long len, double eps_lin, double* part, double* coef, SmallOut* out, cudaStream_t st);
+// freeze the projected newest solution of the last cspe_x0 as column k: Q_k = z / sqrt(zeta)
+int cspe_freeze(const CspeBufs& cb, int k, long long len, cudaStream_t st);
 
 }  // namespace mqs

@@ -310,14 +310,35 @@ def test_start_vectors_do_not_change_the_result():
     d = O.Discretization(p)
     dt = O.dt_gershgorin(d)
     ref = O.run_explicit_euler(d, dt, 30, start_mode=0, tol=1e-12)
-    for mode in (1, 2, 3):
-        r = O.run_explicit_euler(d, dt, 30, start_mode=mode, tol=1e-12, spe_depth=4, pod_snapshots=6)
+    for mode in (1, 2, 3, 4):
+        r = O.run_explicit_euler(d, dt, 30, start_mode=mode, tol=1e-12, spe_depth=4, pod_snapshots=6,
+                                 cspe_period=5)
         assert rel(r.a_c, ref.a_c) < 1e-8
     lit = O.run_explicit_euler(d, dt, 30, start_mode=0, tol=1e-12, literal=True)
     assert rel(lit.a_c, ref.a_c) < 1e-8
-    it = {m: O.run_explicit_euler(d, dt, 30, start_mode=m, tol=1e-12, spe_depth=4, pod_snapshots=6).iterations.sum()
-          for m in (0, 2)}
-    assert it[2] < it[0]
+    it = {m: O.run_explicit_euler(d, dt, 30, start_mode=m, tol=1e-12, spe_depth=4, pod_snapshots=6,
+                                  cspe_period=5).iterations.sum()
+          for m in (0, 2, 4)}
+    assert it[2] < it[0] and it[4] < it[0]
+
+
+def test_cspe_column_schedule():
+    # the live column is the newest solution; the solutions of steps P, 2P, ... are frozen
+    # until the basis holds `depth` columns (Sec. III cascaded SPE, Sec. IV growth below 20)
+    from oracle.mrhs import CspeBasis
+    c = CspeBasis(period=3, depth=4)
+    seen = {}
+    for step in range(1, 15):
+        c.push(np.array([float(step)]))
+        seen[step] = [int(v[0]) for v in c.window()]
+    assert seen[1] == [1] and seen[3] == [3]
+    assert seen[4] == [4, 3] and seen[6] == [6, 3]
+    assert seen[7] == [7, 6, 3] and seen[10] == [10, 9, 6, 3]
+    assert seen[14] == [14, 9, 6, 3]                     # depth reached: only the live column moves
+    c1 = CspeBasis(period=3, depth=1)
+    for step in range(1, 8):
+        c1.push(np.array([float(step)]))
+    assert [int(v[0]) for v in c1.window()] == [7]
 
 
 def test_mirror_symmetry_of_the_field():
