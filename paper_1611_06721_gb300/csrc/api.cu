@@ -301,7 +301,7 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
       // r = b - L x0 by the PCG's own stencil pass: forming it from the recursion
       // images costs a second read of the table and, measured, more iterations
       RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), vs(H->spe_LD, H->opt.spe_depth), H->spe_m, b, x, H->len,
-                H->opt.eps_lin, H->tspart, H->coef, H->small, st));
+                H->opt.eps_lin, H->tspart, H->coef, H->small, st, H->tmp2));
       *used_small = 1;
       *init = 0;
       break;
@@ -1159,7 +1159,7 @@ int spe_start(mqs_handle* H, const double* b, double* x0, int* rank_used) {
   RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
   const int d = H->opt.spe_depth;
   RK(spe_x0(vs(H->spe_D, d), vs(H->spe_LD, d), H->spe_m, H->bu, H->xu, H->len, H->opt.eps_lin, H->tspart, H->coef,
-            H->small, st));
+            H->small, st, H->tmp2));
   SmallOut so{};
   CK(cudaMemcpyAsync(x0, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
   if (H->spe_m > 0) CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));

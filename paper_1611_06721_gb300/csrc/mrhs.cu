@@ -610,6 +610,210 @@ __global__ void __launch_bounds__(kTS) cspe_freeze_kernel(const double* z, const
   }
 }
 
+// ---- SPE table in float-float (hi + lo FP32 pair, about 48 significant bits) ----
+// On this GPU FP64 arithmetic is about 68x slower than FP32, and the Galerkin
+// products of the SPE table are an FP64 multiply-add per table pair and element.
+// The table is therefore kept as float-float pairs (8 bytes per value, as FP64):
+// the backward differences, the Galerkin products and the linear combination run on
+// the FP32 pipes with error-free transformations (two-sum, FMA product error), and
+// FP64 is used only to convert the newest solution, its image and b in and x0 out.
+// __fadd_rn / __fmul_rn are never contracted into FMAs, which the error terms need.
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__device__ __forceinline__ double ff_join(float s, float e) { return (double)s + (double)e; }
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// a - b, both parts summed error-free (the difference of two close values keeps its
+// relative accuracy, as an FP64 subtraction does)
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) {
+  float2 s = ff_two_sum(a.x, -b.x);
+  const float2 t = ff_two_sum(a.y, -b.y);
+  s.y = __fadd_rn(s.y, t.x);
+  s = ff_fast_two_sum(s.x, s.y);
+  s.y = __fadd_rn(s.y, t.y);
+  return ff_fast_two_sum(s.x, s.y);
+}
+// (S, E) += a * b: S sums the rounded products, E their rounding errors (FMA), the
+// cross terms and the rounding of the S sums (two-sum)
+__device__ __forceinline__ void ff_mac(float2 a, float2 b, float& S, float& E) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(S, p), bb = __fsub_rn(s, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  S = s;
+  E = __fadd_rn(E, __fadd_rn(err, e));
+}
+// (S1, E1) += (S2, E2)
+__device__ __forceinline__ void ff_acc(float& S1, float& E1, float S2, float E2) {
+  const float2 t = ff_two_sum(S1, S2);
+  S1 = t.x;
+  E1 = __fadd_rn(__fadd_rn(E1, E2), t.y);
+}
+
+// new table D_0 = w, D_p = D_{p-1}^new - D_{p-1}^old (and likewise for the images)
+template <int MAXD>
+__global__ void __launch_bounds__(kTS) diff_push_ff_kernel(MutVecSet D, MutVecSet LD, const double* __restrict__ w,
+                                                          const double* __restrict__ lw, int m_old, int m_new,
+                                                          long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    float2 od[MAXD], ol[MAXD];
+#pragma unroll
+    for (int p = 0; p < MAXD; ++p)
+      if (p < m_old) {
+        od[p] = reinterpret_cast<const float2*>(D.v[p])[e];
+        ol[p] = reinterpret_cast<const float2*>(LD.v[p])[e];
+      }
+    float2 t = ff_split(w[e]), tl = ff_split(lw[e]);
+#pragma unroll
+    for (int p = 0; p < MAXD; ++p)
+      if (p < m_new) {
+        reinterpret_cast<float2*>(D.v[p])[e] = t;
+        reinterpret_cast<float2*>(LD.v[p])[e] = tl;
+        if (p < m_old) { t = ff_sub(t, od[p]); tl = ff_sub(tl, ol[p]); }
+      }
+  }
+}
+
+// Galerkin products of float-float tables (same slot layout as dots_kernel, FP64
+// partials per block): kTri: A_p . B_q, q >= p, plus B_q . c; kFull: all 64 pairs.
+template <int MODE>
+__global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, const double* c, int ma, int mb,
+                                                        long long len, double* part) {
+  constexpr bool DIAG = (MODE == kTri);
+  constexpr int NP = DIAG ? 36 : 64;
+  constexpr bool PIPE = DIAG;            // the 64-pair tile has no registers left for a second element
+  float S[NP], E[NP], Sc[8], Ec[8];
+#pragma unroll
+  for (int t = 0; t < NP; ++t) { S[t] = 0.f; E[t] = 0.f; }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { Sc[q] = 0.f; Ec[q] = 0.f; }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float2 a[8], b[8];
+  double ce = 0.0;
+  auto load = [&](long long e, float2* aa, float2* bb, double& cc) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p) aa[p] = (p < ma) ? reinterpret_cast<const float2*>(A.v[p])[e] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bb[q] = (q < mb) ? reinterpret_cast<const float2*>(B.v[q])[e] : make_float2(0.f, 0.f);
+    cc = (c != nullptr) ? c[e] : 0.0;
+  };
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (PIPE && e < len) load(e, a, b, ce);
+  for (; e < len; e += stride) {
+    // the next element's inputs are in flight while this one is reduced
+    float2 an[8], bn[8];
+    double cn = 0.0;
+    if (PIPE) {
+      if (e + stride < len) load(e + stride, an, bn, cn);
+    } else {
+      load(e, a, b, ce);
+    }
+    int t = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+#pragma unroll
+      for (int q = (DIAG ? p : 0); q < 8; ++q, ++t)
+        if (p < ma && q < mb) ff_mac(a[p], b[q], S[t], E[t]);
+    }
+    if (ce != 0.0) {
+      const float2 cf = ff_split(ce);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < mb) ff_mac(b[q], cf, Sc[q], Ec[q]);
+    }
+    if (PIPE) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) { a[p] = an[p]; b[p] = bn[p]; }
+      ce = cn;
+    }
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ double red[kTS / 32][kTileSlots];
+  if (MODE == kFull) {
+    // more than 8 SPE columns: butterfly sums per slot
+#pragma unroll
+    for (int t = 0; t < 64; ++t) {
+      float s = S[t], ee = E[t];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        ff_acc(s, ee, __shfl_xor_sync(0xffffffffu, s, off), __shfl_xor_sync(0xffffffffu, ee, off));
+      if (lane == 0) red[wp][t] = ff_join(s, ee);
+    }
+    if (lane < 8) red[wp][64 + lane] = 0.0;
+  } else {
+    // warp reduce-scatter over 48 slots (36 products, then 8 c products), as dots_kernel
+    float vs[48], ve[48];
+#pragma unroll
+    for (int t = 0; t < 48; ++t) { vs[t] = 0.f; ve[t] = 0.f; }
+#pragma unroll
+    for (int t = 0; t < 36; ++t) { vs[t] = S[t]; ve[t] = E[t]; }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { vs[36 + q] = Sc[q]; ve[36 + q] = Ec[q]; }
+#pragma unroll
+    for (int half = 24, off = 16; off >= 2; half >>= 1, off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const float ks = up ? vs[i + half] : vs[i], ke = up ? ve[i + half] : ve[i];
+        const float ss = up ? vs[i] : vs[i + half], se = up ? ve[i] : ve[i + half];
+        vs[i] = ks;
+        ve[i] = ke;
+        ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, ss, off), __shfl_xor_sync(0xffffffffu, se, off));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, vs[i], 1), __shfl_xor_sync(0xffffffffu, ve[i], 1));
+    if ((lane & 1) == 0) {
+      const int base = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) + 3 * ((lane >> 1) & 1);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int sl = base + i;
+        int dst = -1;
+        if (sl >= 36) dst = (sl < 44) ? 64 + (sl - 36) : -1;
+        else dst = c_tri_slot[sl];
+        if (dst >= 0) red[wp][dst] = ff_join(vs[i], ve[i]);
+      }
+    }
+    for (int t = lane; t < 64; t += 32) {
+      const int p = t / 8, q = t % 8;
+      if (q < p) red[wp][t] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int s2 = threadIdx.x; s2 < kTileSlots; s2 += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < kTS / 32; ++q) t += red[q][s2];
+    part[(size_t)blockIdx.x * kTileSlots + s2] = t;
+  }
+}
+
+// x = sum_p coef_p V_p with float-float V and FP64 coefficients
+template <int MAXM>
+__global__ void __launch_bounds__(kTS) lincomb_ff_kernel(VecSet V, const double* coef, int m, long long len,
+                                                        double* x) {
+  __shared__ float2 cf[kMaxVec];
+  for (int p = threadIdx.x; p < kMaxVec; p += blockDim.x) cf[p] = (p < m) ? ff_split(coef[p]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f, ee = 0.f;
+#pragma unroll
+    for (int p = 0; p < MAXM; ++p)
+      if (p < m) ff_mac(cf[p], reinterpret_cast<const float2*>(V.v[p])[e], s, ee);
+    x[e] = ff_join(s, ee);
+  }
+}
+
 // ---- host launchers --------------------------------------------------------------------
 static int ts_max_blocks() {
   static int nb = 0;
@@ -634,36 +838,39 @@ static int chk() { return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_C
 
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, cudaStream_t st) {
-  if (m_new <= 4) diff_push_kernel<4><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else if (m_new <= 8) diff_push_kernel<8><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else diff_push_kernel<16><<<ts_blocks(len), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  const int nb = ts_blocks(len) * 2;
+  if (m_new <= 4) diff_push_ff_kernel<4><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else if (m_new <= 8) diff_push_ff_kernel<8><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
+  else diff_push_ff_kernel<16><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   return chk();
 }
 
 int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st, double* r0) {
+           double* part, double* coef, SmallOut* out, cudaStream_t st, double* scratch) {
   const int nb = ts_blocks(len);
   if (m <= 0) {
     if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
     return MQS_OK;
   }
+  (void)scratch;   // b is split into float-float inside the product kernels
   // Entry (q, p), q >= p, of the Galerkin matrix is D_q . (K D_p): the
   // high-order differences are tested against the K-images of the low-order
   // ones, which the recursion carries accurately (the images of high orders
   // accumulate its rounding relative to their small size).
   VecSet A0 = LD, B0 = D;
-  dots_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
+  dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
   if (m > 8) {
     VecSet A1, B1;
     for (int p = 0; p < 8; ++p) { A1.v[p] = LD.v[p]; B1.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_kernel<kFull><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, m - 8, len, part + (size_t)nb * kTileSlots);
+    dots_ff_kernel<kFull><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, m - 8, len, part + (size_t)nb * kTileSlots);
     VecSet A2, B2;
     for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 0]; B2.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
+    dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
   }
   spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
-  if (r0) launch_lincomb_res(D, LD, coef, m, b, len, x0, r0, nb, st);
-  else launch_lincomb(D, coef, m, len, x0, nb, st);
+  const int nl = nb * 4;
+  if (m <= 8) lincomb_ff_kernel<8><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
+  else lincomb_ff_kernel<16><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   return chk();
 }
 

@@ -16,11 +16,13 @@ struct SmallOut { int rank; int pad; double info; };
 
 int ts_nblk();
 // partial-sum buffer needed: 5 tiles * ts_nblk() * kTileSlots doubles
+// SPE difference table D_p and images L D_p, stored as float-float pairs (8 bytes per
+// value, the buffers are FP64-sized): push the new solution w (FP64) and its image lw
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, cudaStream_t st);
-// x0 = Galerkin start; if r0 is given also r0 = b - L x0 from the stored images
+// x0 (FP64) = Galerkin start from the table; scratch: one layout vector (b in float-float)
 int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st, double* r0 = nullptr);
+           double* part, double* coef, SmallOut* out, cudaStream_t st, double* scratch);
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st);
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
