@@ -290,8 +290,8 @@ def run_ours(args, rank, ws, local, dist):
     n_n = s.n_n
     its = np.array(iters)
     flops = n_n * (FLOPS_PER_ITER * its.sum() + 2 * FLOPS_PER_RESIDUAL * len(its))
-    if args.precision == 1:
-        # inner FP32 iterations plus one FP64 residual per refinement
+    if args.precision != 0:
+        # inner iterations plus one FP64 residual per refinement
         flops = n_n * (FLOPS_PER_ITER * its.sum() + FLOPS_PER_RESIDUAL * (len(its) + sum(refs)))
     achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
     traffic = args.traffic
@@ -303,19 +303,21 @@ def run_ours(args, rank, ws, local, dist):
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "note": "FP64 FMA=2 flop; peak derived: 152 SM x 2 FMA/clk x 2 x 2070 MHz"}
     else:
-        roof = {"bound": "alu", "kernel": "pcg_mixed_kernel", "achieved": achieved,
+        roof = {"bound": "alu", "kernel": "pcg_mixed_kernel" if args.precision == 1 else "pcg_ff_kernel",
+                "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": traffic,
-                "note": "FP32 inner iterations against the FP32 issue peak (152 SM x 128 FMA/clk x 2 x "
-                        "2070 MHz); the inner iteration is latency and grid-barrier bound"}
+                "note": "inner iterations (FP32 or float-float) against the FP32 issue peak (152 SM x 128 FMA/clk"
+                        " x 2 x 2070 MHz); the inner iteration is latency and grid-barrier bound"}
     hbm = n_n * BYTES_PER_ITER * its.sum() / (tm["ms_pcg"] * 1e-3) / 1e9
     peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f32+f64", 2: "ff+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_name(p), "grid": p.N, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
-                       "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
+                       "precision": {0: "FP64", 1: "FP32 inner CG in FP64 refinement",
+                                     2: "float-float inner CG in FP64 refinement"}[args.precision],
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
                                        + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
                        "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
@@ -504,7 +506,7 @@ def run_batch(args):
     line = {"metric": "batched explicit time steps/sec (instance-steps) at rel-residual 1e-10",
             "value": value, "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f32+f64", 2: "ff+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"{len(solvers)} instances, N from {set(sizes)} "
                                    f"(count per N {sizes}), sigma U[1e6,5e6] S/m, coil 100-1000 A, "
@@ -652,8 +654,9 @@ def main():
     ap.add_argument("--depth", type=int, default=0,
                     help="SPE depth, CSPE column cap or POD snapshot count (default 8 / 16 / 20)")
     ap.add_argument("--cspe-period", type=int, default=0, help="CSPE: steps between freezes (default 25)")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
-                    help="0: FP64 PCG (default); 1: FP32 inner solves in FP64 refinement (same tolerance)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="0: FP64 PCG (default); 1: FP32 / 2: float-float inner solves in FP64 refinement "
+                         "(same tolerance)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
                     help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
     ap.add_argument("--grid", type=int, default=64,

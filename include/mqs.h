@@ -120,9 +120,12 @@ typedef struct {
     int    precision;     /* 0: FP64 PCG (default); 1: FP64 iterative refinement
                              around FP32 CG inner solves (stencil, vectors and
                              products in FP32; residual, norms, convergence test
-                             and solution update in FP64; same tol). */
-    double inner_tol;     /* precision 1: smallest residual reduction an inner
-                             solve aims at (<= 0: 1e-5) */
+                             and solution update in FP64; same tol); 2: the same
+                             refinement around float-float inner solves (value
+                             = FP32 hi + FP32 lo, about 48 bits, FP32 pipes;
+                             one-reduction form), which converge like FP64 CG. */
+    double inner_tol;     /* precision 1/2: smallest residual reduction an inner
+                             solve aims at (<= 0: 1e-5 / 1e-12) */
     int    cspe_period;   /* MQS_START_CSPE (Sec. III "cascaded SPE", Sec. IV):
                              the basis holds frozen past solutions and one live
                              column, the newest solution, replaced every step;

@@ -177,15 +177,23 @@ int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t
 }
 
 int ensure_mixed(mqs_handle* H) {
+  // 8 bytes per value: float-float inner vectors (precision 2); FP32 uses the first half
   if (!H->r32)
-    for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, H->len));
-  if (H->opt.pcg_variant == 1 && !H->r32b)
-    for (float** v : {&H->r32b, &H->w32a, &H->w32b, &H->s32a, &H->s32b}) RK(dalloc(H, v, H->len));
+    for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, 2 * H->len));
+  if ((H->opt.pcg_variant == 1 || H->opt.precision == 2) && !H->r32b)
+    for (float** v : {&H->r32b, &H->w32a, &H->w32b, &H->s32a, &H->s32b}) RK(dalloc(H, v, 2 * H->len));
   return MQS_OK;
 }
 
 // the PCG kernel selected by opt.precision and opt.pcg_variant
 int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init) {
+  if (H->opt.precision == 2) {
+    RK(ensure_mixed(H));
+    const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
+    const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-12;
+    return launch_pcg_ff(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
+                         maxit, H->nblk, st, init);
+  }
   if (H->opt.precision == 1) {
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
@@ -373,7 +381,7 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
   if (o->pcg_variant != 0 && o->pcg_variant != 1) { why = "pcg_variant must be 0 or 1"; return MQS_ERR_ARG; }
-  if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->precision < 0 || o->precision > 2) { why = "precision must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
   return MQS_OK;
@@ -728,7 +736,7 @@ int enqueue_step(mqs_handle* H, int s) {
   // (a6) history
   RK(history_push(H, H->x, H->lx, st));
   nl += history_launches(H);
-  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
+  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
                                  H->dstats + s);
   nl += 1;
   mark(H);
@@ -880,7 +888,7 @@ int mqs_adjoint(mqs_handle* H, int nsteps, double* grad_sigma_cell, mqs_adjoint_
     CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
     RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
     H->lx_valid = true;
-    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision == 1 ? H->refin : nullptr,
+    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
                                    H->dstats + nsteps + s);
     RK(history_push(H, H->x, H->lx, st));
     RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));

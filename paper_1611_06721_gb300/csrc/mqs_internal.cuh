@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/mqs.h"
+#include "ff.cuh"
 
 namespace mqs {
 
@@ -95,8 +96,8 @@ __device__ __forceinline__ void group_sync(int grp) {
 // their own named barrier, so one group's plane step never waits for the other.  Index
 // arithmetic is 32-bit and incremental along the march (3 n^3 < 2^31 for
 // n <= 800); bounds tests are hoisted out of the plane loop.
-// Templated on the value type T (double for the FP64 path, float for the
-// inner solves of the mixed-precision path); arithmetic is in T.
+// Templated on the value type T (double for the FP64 path, float or the
+// float-float ffv for the inner solves of the refined paths); arithmetic is in T.
 // Must be called by all kBlock threads of the block.
 template <class T, class Epi>
 __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, int part, int nparts,
@@ -179,7 +180,7 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
         group_sync(grp);
-        T bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
+        T bzi = shfl_up1(bz), byi = shfl_up1(by);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
         const T bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {

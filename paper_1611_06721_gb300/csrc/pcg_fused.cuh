@@ -188,7 +188,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
         group_sync(grp);
-        T bzi = __shfl_up_sync(0xffffffffu, bz, 1), byi = __shfl_up_sync(0xffffffffu, by, 1);
+        T bzi = shfl_up1(bz), byi = shfl_up1(by);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
         const T bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {

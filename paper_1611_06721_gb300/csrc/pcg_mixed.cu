@@ -273,6 +273,166 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
   }
 }
 
+// ---- precision 2: float-float inner CG in FP64 refinement ----------------------------
+// The outer loop is the one above (FP64 residual, norm, convergence test and update);
+// the inner solves run the one-reduction CG in float-float arithmetic (about 48 bits,
+// FP32 pipes), so they converge like FP64 CG and usually meet the outer tolerance in
+// one refinement, at the FP32 cost of the arithmetic.
+
+struct EpiApplyDotFF {  // w = t on n-edges (0 elsewhere); sums w.r with r the source values
+  ffv* w; long long n3;
+  ffv wr = ffv(0);
+  __device__ void prefetch(long long) {}
+  __device__ void operator()(long long e, unsigned m, ffv tx, ffv ty, ffv tz, ffv sx, ffv sy, ffv sz) {
+    const ffv t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const ffv wv = (m >> c & 1u) ? t[c] : ffv(0);
+      w[e + c * n3] = wv;
+      wr = fmaT(wv, s[c], wr);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedArgs a) {
+  __shared__ union { SweepSmemT<double> d; SweepSmemT<ffv> f; FusedSmemBlockT<ffv> ff; } sm;
+  __shared__ double red[2 * 32];
+  __shared__ double gs[2];
+  const int nb = gridDim.x, bid = blockIdx.x;
+  unsigned nbar = 0;
+  int slot = 0;
+  const long long len = 3 * a.g.n3;
+  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
+  auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
+    double v[2] = {v0, v1};
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
+    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
+    if (threadIdx.x < 32) {
+      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
+      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
+    }
+    __syncthreads();
+    s0 = gs[0]; s1 = gs[1];
+    slot ^= 1;
+    return true;
+  };
+  ffv* const rb0 = reinterpret_cast<ffv*>(a.r32);
+  ffv* const rb1 = reinterpret_cast<ffv*>(a.r32b);
+  ffv* const wb0 = reinterpret_cast<ffv*>(a.w32a);
+  ffv* const wb1 = reinterpret_cast<ffv*>(a.w32b);
+  ffv* const sb0 = reinterpret_cast<ffv*>(a.s32a);
+  ffv* const sb1 = reinterpret_cast<ffv*>(a.s32b);
+  ffv* const pf = reinterpret_cast<ffv*>(a.p32);
+  ffv* const df = reinterpret_cast<ffv*>(a.d32);
+  auto rbuf = [&](int c) { return c ? rb1 : rb0; };
+  auto wbuf = [&](int c) { return c ? wb1 : wb0; };
+  auto sbuf = [&](int c) { return c ? sb1 : sb0; };
+  int status = MQS_OK, inner_total = 0, outer = 0;
+  double bb = 0.0, start_rel = 0.0, relres = 0.0;
+  if (a.init == 2) {
+    for (long long e = tid; e < len; e += nth) a.x[e] = 0.0;
+    double d0, d1;
+    if (!reduce2(0.0, 0.0, d0, d1)) return;
+  }
+  for (;;) {
+    double rr;
+    {
+      EpiResidualM ep{a.b, a.r, a.lx, a.g.n3};
+      sweep_L<double>(a.g, a.x, a.full, bid, nb, sm.d, ep);
+      if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
+    }
+    if (outer == 0) {
+      if (bb == 0.0) {
+        for (long long e = tid; e < len; e += nth) { a.x[e] = 0.0; a.r[e] = 0.0; a.lx[e] = 0.0; }
+        if (bid == 0 && threadIdx.x == 0) { *a.out = PcgResult{0, MQS_OK, 0.0, 0.0}; *a.refinements = 0; }
+        return;
+      }
+      start_rel = sqrt(rr / bb);
+    }
+    relres = sqrt(rr / bb);
+    if (!isfinite(rr) || !isfinite(bb)) { status = MQS_ERR_NAN; break; }
+    if (rr <= a.tol2 * bb) { status = MQS_OK; break; }
+    if (inner_total >= a.maxit || outer >= 64) { status = MQS_ERR_NOT_CONVERGED; break; }
+    // inner float-float CG on L d = r / ||r||
+    const double nr = sqrt(rr), inv = 1.0 / nr;
+    double rho;
+    {
+      ffv acc(0);
+      for (long long e = tid; e < len; e += nth) {
+        const ffv v = ff_from(a.r[e] * inv);
+        rb0[e] = v;
+        df[e] = ffv(0);
+        acc = fmaT(v, v, acc);
+      }
+      double dummy;
+      if (!reduce2(ff_to(acc), 0.0, rho, dummy)) return;
+    }
+    const double target = fmax(a.inner_tol, 0.5 * sqrt(a.tol2 * bb) / nr);
+    const double stop2 = target * target * rho;
+    int it_in = 0, cur = 0;
+    double delta, dummy;
+    {
+      EpiApplyDotFF ep{wbuf(0), a.g.n3};
+      sweep_L<ffv>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
+      if (!reduce2(ff_to(ep.wr), 0.0, delta, dummy)) return;
+    }
+    double gamma = rho;
+    bool ok = delta > 0.0, first = true;
+    double alpha = ok ? gamma / delta : 0.0, bet = 0.0;
+    while (ok && inner_total < a.maxit) {
+      FusedVecsT<ffv> v{df, pf, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1), sbuf(cur ^ 1),
+                        ff_from(alpha), ff_from(bet), first};
+      ffv g1(0), d1(0);
+      sweep_fused<ffv>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
+      double gn, dn;
+      if (!reduce2(ff_to(g1), ff_to(d1), gn, dn)) return;
+      ++it_in; ++inner_total;
+      cur ^= 1;
+      if (!isfinite(gn) || !isfinite(dn)) break;
+      if (gn <= stop2 || it_in >= 400) break;
+      const double bnew = gn / gamma;
+      const double den = dn - bnew * gn / alpha;
+      if (!(den > 0.0)) break;                  // stagnation at the float-float floor: refine from here
+      bet = bnew; alpha = gn / den; gamma = gn;
+      first = false;
+    }
+    // x += ||r|| d (FP64); barrier so the next residual sees every update
+    {
+      for (long long e = tid; e < len; e += nth) a.x[e] = fma(nr, ff_to(df[e]), a.x[e]);
+      double d0, d1;
+      if (!reduce2(0.0, 0.0, d0, d1)) return;
+    }
+    ++outer;
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    *a.out = PcgResult{inner_total, status, relres, start_rel};
+    *a.refinements = outer;
+  }
+}
+
+int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
+                  double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
+                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init) {
+  MixedArgs a;
+  a.g = dg.g;
+  a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
+  a.b = b; a.x = x; a.r = r; a.lx = lx;
+  a.r32 = mb.r32; a.p32 = mb.p32; a.q32 = mb.q32; a.d32 = mb.d32;
+  a.r32b = mb.r32b; a.w32a = mb.w32a; a.w32b = mb.w32b; a.s32a = mb.s32a; a.s32b = mb.s32b;
+  a.variant = 1;
+  a.part = part; a.bar = bar; a.err = err; a.out = out; a.refinements = refinements;
+  a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
+  a.spin = 1ll << 21;
+  a.init = (init == 2) ? 2 : 0;
+  if (!mb.r32b || !mb.w32a || !mb.w32b || !mb.s32a || !mb.s32b) return MQS_ERR_ARG;
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_ff_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
+}
+
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                      double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant) {

@@ -327,11 +327,11 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant):
 
 
 # ---- mixed precision: FP32 inner solves inside FP64 refinement (same FP64 residual test) ----------
-@pytest.mark.parametrize("variant", [0, 1])
-def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, variant):
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
+def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, precision, variant):
     p = W.scaled_nonlinear(35)
     d = O.Discretization(p)
-    s = make(pkg, p, precision=1, pcg_variant=variant)
+    s = make(pkg, p, precision=precision, pcg_variant=variant)
     b_n = 3.0 * d.X_s[d.n_idx] - d.K_cn.T @ (W.random_vector(2, d.n_c) * 1e-9)
     b_o = np.zeros(d.grid.n_edges)
     b_o[d.n_idx] = b_n
@@ -344,12 +344,13 @@ def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, variant):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
 @pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_SPE, "spe8")])
-def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, variant):
+def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, precision, variant):
     g = golden()
     p = W.config_linear_block()
-    s = make(pkg, p, start_mode=mode, spe_depth=8, dt=g["dt"], tol=1e-10, precision=1, pcg_variant=variant)
+    s = make(pkg, p, start_mode=mode, spe_depth=8, dt=g["dt"], tol=1e-10, precision=precision,
+             pcg_variant=variant)
     stats = s.mqs_step(g["steps"])
     a_c, _, _ = s.get_state()
     err = rel(a_c, np.array(g["runs"][name]["a_c"]))
@@ -362,13 +363,13 @@ def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, variant):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_mixed_precision_full_size_agrees_with_fp64(pkg, variant):
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
+def test_mixed_precision_full_size_agrees_with_fp64(pkg, precision, variant):
     p = W.config_nonlinear_iron()
     d = O.Discretization(p)
     dt = O.dt_gershgorin(d)
     s64 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
-    s32 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=1, pcg_variant=variant)
+    s32 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=precision, pcg_variant=variant)
     s64.mqs_step(30)
     st = s32.mqs_step(30)
     a64, _, _ = s64.get_state()
