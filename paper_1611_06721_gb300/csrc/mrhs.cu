@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kTS) diff_push_kernel(MutVecSet D, MutVecSet L
 // The diagonal tile keeps only the 36 accumulators of its triangle; the c
 // products are skipped where c vanishes (the right-hand side of eq. (mrhs) is
 // zero away from the conductor and the coil).
-enum DotsMode { kTri = 0, kFull = 1, kRow2 = 2, kConly = 3 };
+enum DotsMode { kTri = 0, kFull = 1, kRow2 = 2, kConly = 3, kRect4 = 4, kTri4 = 5 };
 
 // 8x8 slot (p*8 + q) of the t-th upper-triangle product, in the order p, then q >= p
 __constant__ int c_tri_slot[36] = {0,  1,  2,  3,  4,  5,  6,  7,  9,  10, 11, 12, 13, 14, 15, 18, 19, 20,
@@ -277,9 +277,12 @@ __device__ void sum_parts_warp(const double* part, int nblk, const int* tiles, c
       const int q = lane + 32 * r;
       v[r] = (q < nblk) ? pt[(size_t)q * kTileSlots] : 0.0;
     }
-    double s = 0.0;
+    // pairwise (fixed order): four dependent FP64 additions instead of sixteen
 #pragma unroll
-    for (int r = 0; r < 16; ++r) s += v[r];
+    for (int w2 = 8; w2 >= 1; w2 >>= 1)
+#pragma unroll
+      for (int r = 0; r < w2; ++r) v[r] += v[r + w2];
+    double s = v[0];
     for (int q = lane + 512; q < nblk; q += 32) s += pt[(size_t)q * kTileSlots];
     s = warp_sum(s);
     if (lane == 0) out[t] = s;
@@ -382,21 +385,88 @@ __device__ int chol_drop_solve(double* H, double* g, double* y, int m, double dr
   return nk_s;
 }
 
-__global__ void spe_solve_kernel(const double* part, int nblk, int m, double drop2, double* coef,
+// chol_drop_solve for m <= 16 held in registers: lane r keeps row r of the scaled
+// matrix (compile-time indexed, every loop unrolled), column values travel by
+// shuffles.  Same pivot order, scaling, drop rule and substitutions as
+// chol_drop_solve; on this GPU every dependent FP64 step costs the FP64 unit's issue
+// time, so the register form keeps the serial chain short.  Called by warp 0.
+__device__ int chol_drop_solve16(const double* H, const double* g, double* y, int m, double drop2,
+                                 double rel_floor) {
+  constexpr int M = 16;
+  const int lane = threadIdx.x & 31;
+  const bool own = lane < m;
+  double h[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) h[c] = (own && c < m) ? H[lane * m + c] : 0.0;
+  double d = 0.0;
+#pragma unroll
+  for (int c = 0; c < M; ++c) if (c == lane) d = h[c];
+  const double sc = (own && d > 0.0) ? rsqrt(d) : 0.0;
+  const double hd00 = __shfl_sync(0xffffffffu, d, 0);
+#pragma unroll
+  for (int c = 0; c < M; ++c) h[c] *= sc * __shfl_sync(0xffffffffu, sc, c);
+  double inv = 0.0;
+  int nk = 0;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    if (j >= m) break;
+    const double v = __shfl_sync(0xffffffffu, h[j], j);      // updated pivot (row j)
+    const double dj = __shfl_sync(0xffffffffu, d, j);
+    const bool kj = dj > 0.0 && v > rel_floor && v * dj > drop2 * hd00;
+    const double r = kj ? rsqrt(v) : 0.0;
+    nk += kj ? 1 : 0;
+    if (lane == j) { inv = r; h[j] = v * r; }
+    const double lij = (lane > j) ? h[j] * r : 0.0;           // column j of L in rows below
+    if (lane > j) h[j] = lij;
+#pragma unroll
+    for (int k = j + 1; k < M; ++k) {
+      const double lkj = __shfl_sync(0xffffffffu, lij, k);
+      if (lane >= k) h[k] = fma(-lij, lkj, h[k]);
+    }
+  }
+  // forward L z = S g
+  double a = own ? g[lane] * sc : 0.0, z = 0.0;
+#pragma unroll
+  for (int t = 0; t < M; ++t) {
+    if (t >= m) break;
+    if (lane == t) z = a * inv;
+    const double zt = __shfl_sync(0xffffffffu, z, t);
+    if (lane > t) a = fma(-h[t], zt, a);
+  }
+  // backward L^T u = z: row t's entries go to the lanes of the columns
+  double b = z, u = 0.0;
+#pragma unroll
+  for (int t = M - 1; t >= 0; --t) {
+    if (t >= m) continue;
+    if (lane == t) u = b * inv;
+    const double ut = __shfl_sync(0xffffffffu, u, t);
+    double lti = 0.0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const double hv = __shfl_sync(0xffffffffu, h[i], t);
+      if (i == lane) lti = hv;
+    }
+    if (lane < t) b = fma(-lti, ut, b);
+  }
+  if (own) y[lane] = u * sc;
+  return nk;
+}
+
+__global__ void __launch_bounds__(512) spe_solve_kernel(const double* part, int nblk, int m, double drop2, double* coef,
                                  SmallOut* out) {
   __shared__ double H[kMaxSpe * kMaxSpe], Ls[kMaxSpe * kMaxSpe], g[kMaxSpe], y[kMaxSpe];
   __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
   __shared__ int tiles[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe], slots[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
   __shared__ int keep[kMaxSpe];
-  // entries (q, p), q >= p, live in tile 0 = rows/cols 0..7, tile 1 = (p < 8 <= q),
-  // tile 2 = 8..15; g (D^T b) rows 0..7 in tile 0 and 8..15 in tile 2
+  // entries (q, p), q >= p, live in tile 0 = rows/cols 0..7, tiles 1 and 3 = (p < 8 <= q,
+  // rows 8-11 and 12-15), tile 2 = 8..15; g (D^T b) rows 0..7 in tile 0 and 8..15 in tile 2
   const int npair = m * (m + 1) / 2;
   if (threadIdx.x == 0) {
     int t = 0;
     for (int qq = 0; qq < m; ++qq)
       for (int pp = 0; pp <= qq; ++pp, ++t) {
         if (qq < 8) { tiles[t] = 0; slots[t] = pp * 8 + qq; }
-        else if (pp < 8) { tiles[t] = 1; slots[t] = pp * 8 + (qq - 8); }
+        else if (pp < 8) { tiles[t] = qq < 12 ? 1 : 3; slots[t] = pp * 8 + (qq < 12 ? qq - 8 : qq - 12); }
         else { tiles[t] = 2; slots[t] = (pp - 8) * 8 + (qq - 8); }
       }
     for (int p = 0; p < m; ++p, ++t) {
@@ -414,9 +484,13 @@ __global__ void spe_solve_kernel(const double* part, int nblk, int m, double dro
   }
   for (int p = threadIdx.x; p < m; p += blockDim.x) g[p] = vals[npair + p];
   __syncthreads();
-  const int nk = chol_drop_solve(H, g, y, m, drop2, 1e-13, Ls, keep);
-  for (int p = threadIdx.x; p < m; p += blockDim.x) coef[p] = y[p];
-  if (threadIdx.x == 0) { out->rank = nk; out->info = 0.0; }
+  if (threadIdx.x < 32) {
+    const int nk = chol_drop_solve16(H, g, y, m, drop2, 1e-13);
+    __syncwarp();
+    if (threadIdx.x < m) coef[threadIdx.x] = y[threadIdx.x];
+    if (threadIdx.x == 0) { out->rank = nk; out->info = 0.0; }
+  }
+  (void)Ls; (void)keep;
 }
 
 // Gram row of a new snapshot: part tiles t = 0..ntile-1 hold (w, Lw) . X_q.
@@ -689,29 +763,33 @@ __global__ void __launch_bounds__(kTS) diff_push_ff_kernel(MutVecSet D, MutVecSe
 template <int MODE>
 __global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, const double* c, int ma, int mb,
                                                         long long len, double* part) {
-  constexpr bool DIAG = (MODE == kTri);
-  constexpr int NP = DIAG ? 36 : 64;
-  constexpr bool PIPE = DIAG;            // the 64-pair tile has no registers left for a second element
+  constexpr bool TRI4 = (MODE == kTri4);    // 4 x 4 lower triangle (rows 8-11 of a 12-column table)
+  constexpr bool DIAG = (MODE == kTri) || TRI4;
+  constexpr bool RECT = (MODE == kRect4);   // 8 columns of A x 4 rows of B
+  constexpr int NA = TRI4 ? 4 : 8;
+  constexpr int NB = (RECT || TRI4) ? 4 : 8;
+  constexpr int NP = (MODE == kTri) ? 36 : (TRI4 ? 10 : (RECT ? 32 : 64));
+  constexpr bool PIPE = DIAG || RECT;       // the 64-pair tile has no registers left for a second element
   float S[NP], E[NP], Sc[8], Ec[8];
 #pragma unroll
   for (int t = 0; t < NP; ++t) { S[t] = 0.f; E[t] = 0.f; }
 #pragma unroll
   for (int q = 0; q < 8; ++q) { Sc[q] = 0.f; Ec[q] = 0.f; }
   const long long stride = (long long)gridDim.x * blockDim.x;
-  float2 a[8], b[8];
+  float2 a[NA], b[NB];
   double ce = 0.0;
   auto load = [&](long long e, float2* aa, float2* bb, double& cc) {
 #pragma unroll
-    for (int p = 0; p < 8; ++p) aa[p] = (p < ma) ? reinterpret_cast<const float2*>(A.v[p])[e] : make_float2(0.f, 0.f);
+    for (int p = 0; p < NA; ++p) aa[p] = (p < ma) ? reinterpret_cast<const float2*>(A.v[p])[e] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) bb[q] = (q < mb) ? reinterpret_cast<const float2*>(B.v[q])[e] : make_float2(0.f, 0.f);
+    for (int q = 0; q < NB; ++q) bb[q] = (q < mb) ? reinterpret_cast<const float2*>(B.v[q])[e] : make_float2(0.f, 0.f);
     cc = (c != nullptr) ? c[e] : 0.0;
   };
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (PIPE && e < len) load(e, a, b, ce);
   for (; e < len; e += stride) {
     // the next element's inputs are in flight while this one is reduced
-    float2 an[8], bn[8];
+    float2 an[NA], bn[NB];
     double cn = 0.0;
     if (PIPE) {
       if (e + stride < len) load(e + stride, an, bn, cn);
@@ -720,26 +798,75 @@ __global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, con
     }
     int t = 0;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
+    for (int p = 0; p < NA; ++p) {
 #pragma unroll
-      for (int q = (DIAG ? p : 0); q < 8; ++q, ++t)
+      for (int q = (DIAG ? p : 0); q < NB; ++q, ++t)
         if (p < ma && q < mb) ff_mac(a[p], b[q], S[t], E[t]);
     }
-    if (ce != 0.0) {
+    if (!RECT && ce != 0.0) {
       const float2 cf = ff_split(ce);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < NB; ++q)
         if (q < mb) ff_mac(b[q], cf, Sc[q], Ec[q]);
     }
     if (PIPE) {
 #pragma unroll
-      for (int p = 0; p < 8; ++p) { a[p] = an[p]; b[p] = bn[p]; }
+      for (int p = 0; p < NA; ++p) a[p] = an[p];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) b[q] = bn[q];
       ce = cn;
     }
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   __shared__ double red[kTS / 32][kTileSlots];
-  if (MODE == kFull) {
+  if (TRI4) {
+    // ten products and four c products: butterfly sums per slot
+    int t = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = p; q < 4; ++q, ++t) {
+        float s2 = S[t], e2 = E[t];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+          ff_acc(s2, e2, __shfl_xor_sync(0xffffffffu, s2, off), __shfl_xor_sync(0xffffffffu, e2, off));
+        if (lane == 0) red[wp][p * 8 + q] = ff_join(s2, e2);
+      }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float s2 = Sc[q], e2 = Ec[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        ff_acc(s2, e2, __shfl_xor_sync(0xffffffffu, s2, off), __shfl_xor_sync(0xffffffffu, e2, off));
+      if (lane == 0) red[wp][64 + q] = ff_join(s2, e2);
+    }
+    for (int t2 = lane; t2 < kTileSlots; t2 += 32) {
+      const int p = t2 / 8, q = t2 % 8;
+      const bool used = (t2 < 64) ? (p < 4 && q < 4 && q >= p) : (t2 - 64 < 4);
+      if (!used) red[wp][t2] = 0.0;
+    }
+  } else if (RECT) {
+    // warp reduce-scatter over the 32 products: five halvings, lane l keeps product l
+    float vs[32], ve[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) { vs[t] = S[t]; ve[t] = E[t]; }
+#pragma unroll
+    for (int half = 16, off = 16; off >= 1; half >>= 1, off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const float ks = up ? vs[i + half] : vs[i], ke = up ? ve[i + half] : ve[i];
+        const float ss = up ? vs[i] : vs[i + half], se = up ? ve[i] : ve[i + half];
+        vs[i] = ks;
+        ve[i] = ke;
+        ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, ss, off), __shfl_xor_sync(0xffffffffu, se, off));
+      }
+    }
+    // product index lane = p * 4 + q (column p of A, row q of B) -> slot p * 8 + q
+    red[wp][(lane >> 2) * 8 + (lane & 3)] = ff_join(vs[0], ve[0]);
+    red[wp][(lane >> 2) * 8 + 4 + (lane & 3)] = 0.0;
+    if (lane < 8) red[wp][64 + lane] = 0.0;
+  } else if (MODE == kFull) {
     // more than 8 SPE columns: butterfly sums per slot
 #pragma unroll
     for (int t = 0; t < 64; ++t) {
@@ -806,10 +933,13 @@ __global__ void __launch_bounds__(kTS) lincomb_ff_kernel(VecSet V, const double*
   for (int p = threadIdx.x; p < kMaxVec; p += blockDim.x) cf[p] = (p < m) ? ff_split(coef[p]) : make_float2(0.f, 0.f);
   __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    float2 v[MAXM];
+#pragma unroll
+    for (int p = 0; p < MAXM; ++p) v[p] = (p < m) ? reinterpret_cast<const float2*>(V.v[p])[e] : make_float2(0.f, 0.f);
     float s = 0.f, ee = 0.f;
 #pragma unroll
     for (int p = 0; p < MAXM; ++p)
-      if (p < m) ff_mac(cf[p], reinterpret_cast<const float2*>(V.v[p])[e], s, ee);
+      if (p < m) ff_mac(cf[p], v[p], s, ee);
     x[e] = ff_join(s, ee);
   }
 }
@@ -860,16 +990,24 @@ int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0
   VecSet A0 = LD, B0 = D;
   dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
   if (m > 8) {
-    VecSet A1, B1;
-    for (int p = 0; p < 8; ++p) { A1.v[p] = LD.v[p]; B1.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_ff_kernel<kFull><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, m - 8, len, part + (size_t)nb * kTileSlots);
+    // rows 8.. of D against the first 8 images, in 8 x 4 tiles (tile 1: rows 8-11, tile 3: rows 12-15)
+    for (int h = 0; h < 2 && 8 + 4 * h < m; ++h) {
+      VecSet A1, B1;
+      const int r0 = 8 + 4 * h, rows = (m - r0) < 4 ? (m - r0) : 4;
+      for (int p = 0; p < 8; ++p) A1.v[p] = LD.v[p];
+      for (int q = 0; q < 8; ++q) B1.v[q] = D.v[q < rows ? r0 + q : r0];
+      dots_ff_kernel<kRect4><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, rows, len,
+                                                 part + (size_t)(h == 0 ? 1 : 3) * nb * kTileSlots);
+    }
     VecSet A2, B2;
-    for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 0]; B2.v[p] = D.v[8 + p < m ? 8 + p : 0]; }
-    dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
+    for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 8]; B2.v[p] = D.v[8 + p < m ? 8 + p : 8]; }
+    if (m <= 12) dots_ff_kernel<kTri4><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
+    else dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
   }
   spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
   const int nl = nb * 4;
   if (m <= 8) lincomb_ff_kernel<8><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
+  else if (m <= 12) lincomb_ff_kernel<12><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   else lincomb_ff_kernel<16><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   return chk();
 }
