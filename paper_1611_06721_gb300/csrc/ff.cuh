@@ -29,14 +29,28 @@ __device__ __forceinline__ ffv operator+(ffv a, ffv b) {
 }
 __device__ __forceinline__ ffv operator-(ffv a) { return ffv(-a.hi, -a.lo); }
 __device__ __forceinline__ ffv operator-(ffv a, ffv b) { return a + (-b); }
-// a * b + c
-__device__ __forceinline__ ffv fmaT(ffv a, ffv b, ffv c) {
+// a * b: the FP32 product and its exact error (FMA), plus the cross terms
+__device__ __forceinline__ ffv ff_mul(ffv a, ffv b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return ff_norm(p, e) + c;
+  return ff_norm(p, e);
 }
+// a * b + c
+__device__ __forceinline__ ffv fmaT(ffv a, ffv b, ffv c) { return ff_mul(a, b) + c; }
+// a / b: the FP32 quotient q1 corrected by the quotient of the float-float
+// remainder a - q1 b (Dekker's division; relative error about 2^-47)
+__device__ __forceinline__ ffv ff_div(ffv a, ffv b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float p = __fmul_rn(q1, b.hi);
+  float e = __fmaf_rn(q1, b.hi, -p);
+  e = __fmaf_rn(q1, b.lo, e);
+  const ffv r = a - ff_norm(p, e);
+  return ff_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+// a <= b for normalised values (|lo| at most half an ulp of hi)
+__device__ __forceinline__ bool ff_le(ffv a, ffv b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
 __device__ __forceinline__ ffv ff_from(double v) {
   const float hi = __double2float_rn(v);
   return ffv(hi, __double2float_rn(v - (double)hi));

@@ -271,36 +271,78 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of NV values per thread; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* >= NV*32 doubles */) {
+// Sums of two values over the block and the grid, deterministic (fixed order,
+// the same in every block) in T = double or the float-float ffv.  One FP64
+// warp instruction holds its sub-partition's FP64 unit for about 64 cycles on
+// this GPU (not pipelined; a dependent FP64 add with a shuffle ~110 cycles),
+// so the sums keep FP64 instructions and dependent steps few: a transposed
+// butterfly (the first exchange leaves value 0 in lanes 0-15 and value 1 in
+// lanes 16-31: five additions per warp for both values), the warp totals
+// summed by one warp, and the grid's block partials loaded all at once and
+// summed by two warps, one per value (two sub-partitions, two FP64 units).
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ ffv shfl_x(ffv v, int o) {
+  return ffv(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ double shfl_from(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ ffv shfl_from(ffv v, int l) {
+  return ffv(__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l));
+}
+__device__ __forceinline__ double ld_part(const double* p) { return *p; }
+__device__ __forceinline__ ffv ld_part(const ffv* p) {
+  const float2 f = *reinterpret_cast<const float2*>(p);
+  return ffv(f.x, f.y);
+}
+
+// lanes 0-15: the warp's sum of v0 (exact total in lane 0); lanes 16-31: of v1 (lane 16)
+template <class T>
+__device__ __forceinline__ T warp_sum2(T v0, T v1) {
+  const bool up = (threadIdx.x & 16) != 0;
+  T s = (up ? v1 : v0) + shfl_x(up ? v0 : v1, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) s = s + shfl_x(s, o);
+  return s;
+}
+
+// Block sums of (v0, v1); the totals land in thread 0 (t0 and t1).  red: 32 T
+// of shared memory; at most 16 warps.  Ends without a block barrier: red may be
+// reused only after the caller's next __syncthreads.
+template <class T>
+__device__ __forceinline__ void block_sum2(T v0, T v1, T* red, T& t0, T& t1) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int a = 0; a < NV; ++a) v[a] = warp_sum(v[a]);
+  const T s = warp_sum2(v0, v1);
+  if ((lane & 15) == 0) red[(lane >> 4) * 16 + w] = s;   // red[w] = v0 sums, red[16 + w] = v1 sums
   __syncthreads();
-  if (lane == 0) {
+  if (w == 0) {
+    T t = ((lane & 15) < nw) ? red[lane] : T(0);
 #pragma unroll
-    for (int a = 0; a < NV; ++a) red[a * 32 + w] = v[a];
+    for (int o = 8; o > 0; o >>= 1) t = t + shfl_x(t, o);
+    t0 = t;
+    t1 = shfl_from(t, 16);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+}
+
+// Sum of p[0..cnt) by one warp (every lane returns the same value in FP64;
+// lane 0's is the defined one).  Loads issue together, then a fixed chain.
+template <class T>
+__device__ __forceinline__ T warp_fixed_sum(const T* p, int cnt) {
+  const int lane = threadIdx.x & 31;
+  T v[8];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      double s = 0.0;
-      for (int q = 0; q < nw; ++q) s += red[a * 32 + q];
-      v[a] = s;
-    }
-  }
-  __syncthreads();
+  for (int q = 0; q < 8; ++q) v[q] = (lane + 32 * q < cnt) ? ld_part(p + lane + 32 * q) : T(0);
+  const int nq = (cnt + 31) >> 5;
+  T s = v[0];
+#pragma unroll
+  for (int q = 1; q < 8; ++q)
+    if (q < nq) s = s + v[q];
+  for (int q = lane + 256; q < cnt; q += 32) s = s + ld_part(p + q);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = s + shfl_x(s, o);
+  return s;
 }
 
 // Sum of part[0..cnt) computed identically by every caller (one warp).
-__device__ __forceinline__ double fixed_sum(const double* part, int cnt) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int q = lane; q < cnt; q += 32) s += part[q];
-  return warp_sum(s);
-}
+__device__ __forceinline__ double fixed_sum(const double* part, int cnt) { return warp_fixed_sum(part, cnt); }
 
 // ---- grid barrier with a bounded wait -------------------------------------------
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -331,6 +373,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, lon
   }
   __syncthreads();
   return ok != 0;
+}
+
+// Grid-wide sums of two values per thread, returned to every thread: block
+// sums into this block's partial slots, a grid barrier, then every block sums
+// the partials in the same fixed order.  part holds 2 slots x 4 x gridDim.x
+// entries of 8 bytes (the slot alternates: a block already at the next sum
+// cannot overwrite partials still being read); red: 32 T and gs: 2 T of shared
+// memory.  Returns false when the barrier timed out.  All threads must call.
+template <class T>
+__device__ __forceinline__ bool grid_sum2(T v0, T v1, T& s0, T& s1, void* part, int& slot, unsigned& nbar,
+                                          unsigned* bar, long long spin, int* err, T* red, T* gs) {
+  const int nb = gridDim.x, w = threadIdx.x >> 5;
+  T* p0 = reinterpret_cast<T*>(part) + (size_t)slot * 4 * nb;
+  T* p1 = p0 + nb;
+  T t0, t1;
+  block_sum2(v0, v1, red, t0, t1);
+  if (threadIdx.x == 0) { p0[blockIdx.x] = t0; p1[blockIdx.x] = t1; }
+  if (!grid_barrier(bar, nb * (++nbar), spin, err)) return false;
+  if (w < 2) {
+    const T t = warp_fixed_sum(w ? p1 : p0, nb);
+    if ((threadIdx.x & 31) == 0) gs[w] = t;
+  }
+  __syncthreads();
+  s0 = gs[0]; s1 = gs[1];
+  slot ^= 1;
+  return true;
 }
 
 }  // namespace mqs

@@ -90,29 +90,17 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
 
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a) {
   __shared__ SweepSmem sm;
-  __shared__ double red[2 * 32];
+  __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
   const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
-  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
 
   // reduction helper: block sums -> partial slots -> barrier -> global sums
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
-    double v[2] = {v0, v1};
-    block_sum<2>(v, red);
-    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
-    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
-    if (threadIdx.x < 32) {
-      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
-      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
-    }
-    __syncthreads();
-    s0 = gs[0]; s1 = gs[1];
-    slot ^= 1;
-    return true;
+    return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
   };
 
   int status = MQS_OK, it = 0;
@@ -263,27 +251,15 @@ struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; }
 // arithmetic; convergence is confirmed on the true residual as there.
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
   __shared__ union { SweepSmem s; FusedSmemBlock f; } sm;
-  __shared__ double red[2 * 32];
+  __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
   const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
-  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
-    double v[2] = {v0, v1};
-    block_sum<2>(v, red);
-    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
-    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
-    if (threadIdx.x < 32) {
-      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
-      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
-    }
-    __syncthreads();
-    s0 = gs[0]; s1 = gs[1];
-    slot ^= 1;
-    return true;
+    return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
   };
   auto rb = [&](int c) { return c ? fb.r1 : a.r; };
   auto wb = [&](int c) { return c ? fb.w1 : fb.w0; };

@@ -6,7 +6,7 @@
 // update x += ||r|| d.  Inner (FP32): CG on L d = r/||r|| with the stencil,
 // vectors and products in FP32 (on this GPU FP32 arithmetic is 64x faster
 // than FP64), each dot product's per-thread partial sums in FP32 and its
-// cross-thread sum in FP64; it stops once its residual has dropped by
+// cross-thread sum and the CG scalars in float-float; it stops once its residual has dropped by
 // max(inner_tol, tol ||b|| / (2 ||r||)), i.e. as soon as the outer tolerance
 // can be met, or when FP32 stagnates.  Jacobi is folded into the scaling as
 // in the FP64 kernel (diag(K_n) is uniform).
@@ -113,27 +113,20 @@ struct EpiApplyDot32 {  // w = t on n-edges (0 elsewhere, FP32); sums w.r with r
 
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(MixedArgs a) {
   __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; FusedSmemBlockT<float> ff; } sm;
-  __shared__ double red[2 * 32];
+  __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
   const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
-  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
-    double v[2] = {v0, v1};
-    block_sum<2>(v, red);
-    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
-    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
-    if (threadIdx.x < 32) {
-      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
-      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
-    }
-    __syncthreads();
-    s0 = gs[0]; s1 = gs[1];
-    slot ^= 1;
-    return true;
+    return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
+  };
+  // float-float sums (the inner solves' products): the same partial slots and barrier sequence
+  auto reduceF = [&](ffv v0, ffv v1, ffv& s0, ffv& s1) -> bool {
+    return grid_sum2<ffv>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, reinterpret_cast<ffv*>(red),
+                          reinterpret_cast<ffv*>(gs));
   };
   int status = MQS_OK, inner_total = 0, outer = 0;
   double bb = 0.0, start_rel = 0.0, relres = 0.0;
@@ -164,7 +157,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
     if (inner_total >= a.maxit || outer >= 64) { status = MQS_ERR_NOT_CONVERGED; break; }
     // inner FP32 CG on L d = r / ||r||
     const double nr = sqrt(rr), inv = 1.0 / nr;
-    double rho;
+    ffv rho;
     {
       float acc = 0.f;
       for (long long e = tid; e < len; e += nth) {
@@ -173,12 +166,13 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
         a.d32[e] = 0.f;
         acc = fmaf(v, v, acc);
       }
-      double dummy;
-      if (!reduce2((double)acc, 0.0, rho, dummy)) return;
+      ffv dummy;
+      if (!reduceF(ffv(acc, 0.f), ffv(0), rho, dummy)) return;
     }
-    const double rho0 = rho;
+    // the inner scalars (products, alpha, beta) are float-float: FP64 division
+    // and conversions are long dependent sequences on this GPU
     const double target = fmax(a.inner_tol, 0.5 * sqrt(a.tol2 * bb) / nr);
-    const double stop2 = target * target * rho0;
+    const ffv stop2 = ff_from(target * target * ff_to(rho));
     float beta = 0.f;
     bool first = true;
     int it_in = 0;
@@ -189,44 +183,44 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
       auto wbuf = [&](int c) { return c ? a.w32b : a.w32a; };
       auto sbuf = [&](int c) { return c ? a.s32b : a.s32a; };
       int cur = 0;
-      double delta, dummy;
+      ffv delta, dummy;
       {
         EpiApplyDot32 ep{wbuf(0), a.g.n3};
         sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
-        if (!reduce2((double)ep.wr, 0.0, delta, dummy)) return;
+        if (!reduceF(ffv(ep.wr, 0.f), ffv(0), delta, dummy)) return;
       }
-      double gamma = rho;
-      bool ok = delta > 0.0;
-      double alpha = ok ? gamma / delta : 0.0, bet = 0.0;
+      ffv gamma = rho;
+      bool ok = delta.hi > 0.f;
+      ffv alpha = ok ? ff_div(gamma, delta) : ffv(0), bet = ffv(0);
       while (ok && inner_total < a.maxit) {
         FusedVecsT<float> v{a.d32, a.p32, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1),
-                            sbuf(cur ^ 1), (float)alpha, (float)bet, first};
+                            sbuf(cur ^ 1), alpha.hi, bet.hi, first};
         float g1 = 0.f, d1 = 0.f;
         sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
-        double gn, dn;
-        if (!reduce2((double)g1, (double)d1, gn, dn)) return;
+        ffv gn, dn;
+        if (!reduceF(ffv(g1, 0.f), ffv(d1, 0.f), gn, dn)) return;
         ++it_in; ++inner_total;
         cur ^= 1;
-        if (!isfinite(gn) || !isfinite(dn)) break;
-        if (gn <= stop2 || it_in >= 400) break;
-        const double bnew = gn / gamma;
-        const double den = dn - bnew * gn / alpha;
-        if (!(den > 0.0)) break;                  // FP32 breakdown / stagnation: refine from here
-        bet = bnew; alpha = gn / den; gamma = gn;
+        if (!isfinite(gn.hi) || !isfinite(dn.hi)) break;
+        if (ff_le(gn, stop2) || it_in >= 400) break;
+        const ffv bnew = ff_div(gn, gamma);
+        const ffv den = dn - ff_div(ff_mul(bnew, gn), alpha);
+        if (!(den.hi > 0.f)) break;               // FP32 breakdown / stagnation: refine from here
+        bet = bnew; alpha = ff_div(gn, den); gamma = gn;
         first = false;
       }
     }
     while (a.variant == 0 && inner_total < a.maxit) {
-      double pq, dummy;
+      ffv pq, dummy;
       {
         EpiDirection32 ep{a.p32, a.q32, a.g.n3, beta, first};
         sweep_L<float>(a.g, a.r32, a.full, bid, nb, sm.f, ep);
-        if (!reduce2((double)ep.pq, 0.0, pq, dummy)) return;
+        if (!reduceF(ffv(ep.pq, 0.f), ffv(0), pq, dummy)) return;
       }
       ++it_in; ++inner_total;
-      if (!(pq > 0.0)) break;                     // FP32 breakdown / stagnation: refine from here
-      const float alpha = (float)(rho / pq);
-      double rn;
+      if (!(pq.hi > 0.f)) break;                  // FP32 breakdown / stagnation: refine from here
+      const float alpha = ff_div(rho, pq).hi;
+      ffv rn;
       {
         float acc = 0.f;
         const long long q4 = len >> 2;
@@ -251,11 +245,11 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(Mixe
           a.r32[e] = rv;
           acc = fmaf(rv, rv, acc);
         }
-        if (!reduce2((double)acc, 0.0, rn, dummy)) return;
+        if (!reduceF(ffv(acc, 0.f), ffv(0), rn, dummy)) return;
       }
-      if (!isfinite(rn)) break;
-      if (rn <= stop2 || it_in >= 400) break;
-      beta = (float)(rn / rho);
+      if (!isfinite(rn.hi)) break;
+      if (ff_le(rn, stop2) || it_in >= 400) break;
+      beta = ff_div(rn, rho).hi;
       rho = rn;
       first = false;
     }
@@ -296,27 +290,20 @@ struct EpiApplyDotFF {  // w = t on n-edges (0 elsewhere); sums w.r with r the s
 
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedArgs a) {
   __shared__ union { SweepSmemT<double> d; SweepSmemT<ffv> f; FusedSmemBlockT<ffv> ff; } sm;
-  __shared__ double red[2 * 32];
+  __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
   const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
-  auto part = [&](int v) { return a.part + ((size_t)(slot * 4 + v) * nb); };
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
-    double v[2] = {v0, v1};
-    block_sum<2>(v, red);
-    if (threadIdx.x == 0) { part(0)[bid] = v[0]; part(1)[bid] = v[1]; }
-    if (!grid_barrier(a.bar, nb * (++nbar), a.spin, a.err)) return false;
-    if (threadIdx.x < 32) {
-      const double t0 = fixed_sum(part(0), nb), t1 = fixed_sum(part(1), nb);
-      if (threadIdx.x == 0) { gs[0] = t0; gs[1] = t1; }
-    }
-    __syncthreads();
-    s0 = gs[0]; s1 = gs[1];
-    slot ^= 1;
-    return true;
+    return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
+  };
+  // float-float sums (the inner solves' products): the same partial slots and barrier sequence
+  auto reduceF = [&](ffv v0, ffv v1, ffv& s0, ffv& s1) -> bool {
+    return grid_sum2<ffv>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, reinterpret_cast<ffv*>(red),
+                          reinterpret_cast<ffv*>(gs));
   };
   ffv* const rb0 = reinterpret_cast<ffv*>(a.r32);
   ffv* const rb1 = reinterpret_cast<ffv*>(a.r32b);
@@ -357,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedAr
     if (inner_total >= a.maxit || outer >= 64) { status = MQS_ERR_NOT_CONVERGED; break; }
     // inner float-float CG on L d = r / ||r||
     const double nr = sqrt(rr), inv = 1.0 / nr;
-    double rho;
+    ffv rho;
     {
       ffv acc(0);
       for (long long e = tid; e < len; e += nth) {
@@ -366,36 +353,37 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedAr
         df[e] = ffv(0);
         acc = fmaT(v, v, acc);
       }
-      double dummy;
-      if (!reduce2(ff_to(acc), 0.0, rho, dummy)) return;
+      ffv dummy;
+      if (!reduceF(acc, ffv(0), rho, dummy)) return;
     }
+    // products and scalars stay float-float (no FP64 division or conversion in the loop)
     const double target = fmax(a.inner_tol, 0.5 * sqrt(a.tol2 * bb) / nr);
-    const double stop2 = target * target * rho;
+    const ffv stop2 = ff_from(target * target * ff_to(rho));
     int it_in = 0, cur = 0;
-    double delta, dummy;
+    ffv delta, dummy;
     {
       EpiApplyDotFF ep{wbuf(0), a.g.n3};
       sweep_L<ffv>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
-      if (!reduce2(ff_to(ep.wr), 0.0, delta, dummy)) return;
+      if (!reduceF(ep.wr, ffv(0), delta, dummy)) return;
     }
-    double gamma = rho;
-    bool ok = delta > 0.0, first = true;
-    double alpha = ok ? gamma / delta : 0.0, bet = 0.0;
+    ffv gamma = rho;
+    bool ok = delta.hi > 0.f, first = true;
+    ffv alpha = ok ? ff_div(gamma, delta) : ffv(0), bet = ffv(0);
     while (ok && inner_total < a.maxit) {
       FusedVecsT<ffv> v{df, pf, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1), sbuf(cur ^ 1),
-                        ff_from(alpha), ff_from(bet), first};
+                        alpha, bet, first};
       ffv g1(0), d1(0);
       sweep_fused<ffv>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
-      double gn, dn;
-      if (!reduce2(ff_to(g1), ff_to(d1), gn, dn)) return;
+      ffv gn, dn;
+      if (!reduceF(g1, d1, gn, dn)) return;
       ++it_in; ++inner_total;
       cur ^= 1;
-      if (!isfinite(gn) || !isfinite(dn)) break;
-      if (gn <= stop2 || it_in >= 400) break;
-      const double bnew = gn / gamma;
-      const double den = dn - bnew * gn / alpha;
-      if (!(den > 0.0)) break;                  // stagnation at the float-float floor: refine from here
-      bet = bnew; alpha = gn / den; gamma = gn;
+      if (!isfinite(gn.hi) || !isfinite(dn.hi)) break;
+      if (ff_le(gn, stop2) || it_in >= 400) break;
+      const ffv bnew = ff_div(gn, gamma);
+      const ffv den = dn - ff_div(ff_mul(bnew, gn), alpha);
+      if (!(den.hi > 0.f)) break;               // stagnation at the float-float floor: refine from here
+      bet = bnew; alpha = ff_div(gn, den); gamma = gn;
       first = false;
     }
     // x += ||r|| d (FP64); barrier so the next residual sees every update
