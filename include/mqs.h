@@ -216,6 +216,19 @@ int mqs_lambda_max(mqs_handle* h, const double* v0, double pcg_tol,
  * loop still completes), MQS_ERR_ARG if dt is unset. */
 int mqs_step(mqs_handle* h, int nsteps, mqs_step_stats* per_step);
 
+/* mqs_step in two halves.  mqs_step_enqueue issues the launches of nsteps
+ * steps on the handle's stream (the side stream of the SPE table push joined
+ * back at the end) and returns without waiting for the device, so the host can
+ * work (or record events in stream order) while the steps run; it may be called
+ * again before the finish (the steps queue up behind each other).
+ * mqs_step_finish(h, nsteps, per_step) then copies the statistics of all
+ * enqueued steps, waits for the stream and returns what mqs_step would have;
+ * nsteps must equal the total enqueued count.  A finish without an enqueue, or
+ * mqs_step while steps are enqueued, returns MQS_ERR_ARG; no other call may use
+ * the handle in between. */
+int mqs_step_enqueue(mqs_handle* h, int nsteps);
+int mqs_step_finish(mqs_handle* h, int nsteps, mqs_step_stats* per_step);
+
 /* State access.  a_c: n_c doubles in compact c-edge order. */
 int mqs_get_state(mqs_handle* h, double* a_c, size_t n_c, double* t, long* m);
 int mqs_set_state(mqs_handle* h, const double* a_c, size_t n_c, double t, long m);
@@ -262,9 +275,12 @@ int mqs_set_stream(mqs_handle* h, void* stream);
 
 /* Per-phase device time of mqs_step, measured with CUDA events recorded on
  * the handle's stream around each phase of every step while timing is on:
- * right-hand side (a2), start vector (a3), PCG (a4), conductor update (a5),
- * history (a6).  `launches` counts every kernel the library launched inside
- * those steps and `pcg_launches` the PCG kernels among them. */
+ * right-hand side (a2), start vector (a3), PCG (a4), history (a6; issued
+ * before the conductor update: with SPE only the fork of the table push to the
+ * side stream, whose time then shows where the main stream waits for it),
+ * conductor update (a5, with the step's statistics record).  `launches` counts
+ * every kernel the library launched inside those steps and `pcg_launches` the
+ * PCG kernels among them. */
 typedef struct {
     double ms_rhs, ms_start, ms_pcg, ms_conductor, ms_history;
     long   launches;

@@ -24,13 +24,13 @@ ERRORS = {-1: "MQS_ERR_ARG", -2: "MQS_ERR_CUDA", -3: "MQS_ERR_OOM", -4: "MQS_ERR
 START_ZERO, START_PREV, START_SPE, START_POD, START_CSPE = 0, 1, 2, 3, 4
 
 EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_dt", "mqs_get_dt",
-           "mqs_set_options", "mqs_lambda_max", "mqs_step", "mqs_get_state", "mqs_set_state",
-           "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution", "mqs_reset_history",
-           "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev", "mqs_conductor_rate",
-           "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream", "mqs_timing_enable",
-           "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout", "mqs_set_blocks",
-           "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms", "mqs_batch_tune",
-           "mqs_batch_destroy", "mqs_adjoint", "mqs_loss", "mqs_solve_an")
+           "mqs_set_options", "mqs_lambda_max", "mqs_step", "mqs_step_enqueue", "mqs_step_finish",
+           "mqs_get_state", "mqs_set_state", "mqs_get_state_dev", "mqs_set_state_dev", "mqs_get_solution",
+           "mqs_reset_history", "pcg_solve", "pcg_solve_dev", "mqs_apply_kn", "mqs_apply_kn_dev",
+           "mqs_conductor_rate", "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream",
+           "mqs_timing_enable", "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout",
+           "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
+           "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_loss", "mqs_solve_an")
 
 
 class Grid(C.Structure):
@@ -104,6 +104,8 @@ def load():
         "mqs_set_options": ([H, P(Options)], I),
         "mqs_lambda_max": ([H, P(D), D, D, I, P(D), P(I)], I),
         "mqs_step": ([H, I, P(StepStats)], I),
+        "mqs_step_enqueue": ([H, I], I),
+        "mqs_step_finish": ([H, I, P(StepStats)], I),
         "mqs_get_state": ([H, P(D), C.c_size_t, P(D), P(L)], I),
         "mqs_set_state": ([H, P(D), C.c_size_t, D, L], I),
         "mqs_get_state_dev": ([H, V, C.c_size_t, V], I),
@@ -283,6 +285,18 @@ class Solver:
 
     def mqs_step(self, nsteps):
         return self.step(nsteps)[1]
+
+    def step_enqueue(self, nsteps):
+        """Issue nsteps steps on the handle's stream without waiting (mqs_step_enqueue)."""
+        self._check(self.lib.mqs_step_enqueue(self.h, nsteps))
+
+    def step_finish(self, nsteps, allow_fail=False):
+        """Wait for enqueued steps: (rc, per-step stats) as step() returns (mqs_step_finish)."""
+        st = (StepStats * max(nsteps, 1))()
+        rc = self.lib.mqs_step_finish(self.h, nsteps, st)
+        if not allow_fail:
+            self._check(rc)
+        return rc, [st[q] for q in range(nsteps)]
 
     def adjoint(self, nsteps):
         """Gradient of the eddy-current loss J over nsteps steps from the current state

@@ -44,6 +44,13 @@ struct mqs_handle {
   double* spe_D[kMaxSpe] = {};
   double* spe_LD[kMaxSpe] = {};
   int spe_m = 0;
+  double *spe_hpart = nullptr, *spe_gpart = nullptr;   // Galerkin product partials of the table, g partials
+  // side stream: the SPE table push (with its products) runs beside the conductor
+  // update and the next right-hand side; the main stream joins before the table is read
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_pending = false;
+  int enqueued = 0;          // steps issued by mqs_step_enqueue and not yet finished
   double* pod_X[kMaxPod] = {};
   double* pod_LX[kMaxPod] = {};
   double *pod_G = nullptr, *pod_A = nullptr;
@@ -245,12 +252,30 @@ CspeBufs cspe_bufs(mqs_handle* H) {
   return CspeBufs{H->pod_X, H->pod_LX, H->pod_X[kMaxPod - 1], H->pod_LX[kMaxPod - 1], H->pod_X[kMaxPod - 2],
                   H->pod_LX[kMaxPod - 2], H->cspe_scal};
 }
+// the main stream waits for the side stream's work (no-op when none is pending)
+int join_side(mqs_handle* H) {
+  if (!H->side_pending) return MQS_OK;
+  CK(cudaStreamWaitEvent(H->st, H->ev_join, 0));
+  H->side_pending = false;
+  return MQS_OK;
+}
+
 int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t st) {
   const int mode = H->opt.start_mode;
   if (mode == MQS_START_SPE) {
     const int d = H->opt.spe_depth;
     const int mn = H->spe_m + 1 < d ? H->spe_m + 1 : d;
-    RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, st));
+    if (st == H->st) {
+      // fork: the push reads w and lw, which nothing on the main stream writes
+      // before the next start vector (which joins first)
+      CK(cudaEventRecord(H->ev_fork, st));
+      CK(cudaStreamWaitEvent(H->st2, H->ev_fork, 0));
+      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, H->st2));
+      CK(cudaEventRecord(H->ev_join, H->st2));
+      H->side_pending = true;
+    } else {
+      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, st));
+    }
     H->spe_m = mn;
   } else if (mode == MQS_START_POD) {
     const int np = H->opt.pod_snapshots;
@@ -294,6 +319,7 @@ __global__ void sub_kernel(const double* b, const double* lx, double* r, long lo
 int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int* used_small, int* init) {
   *used_small = 0;
   *init = 0;
+  RK(join_side(H));
   switch (H->opt.start_mode) {
     case MQS_START_ZERO:
       *init = 2;
@@ -308,8 +334,9 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
       if (H->spe_m == 0) { *init = 2; break; }
       // r = b - L x0 by the PCG's own stencil pass: forming it from the recursion
       // images costs a second read of the table and, measured, more iterations
-      RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), vs(H->spe_LD, H->opt.spe_depth), H->spe_m, b, x, H->len,
-                H->opt.eps_lin, H->tspart, H->coef, H->small, st, H->tmp2));
+      // b vanishes outside the right-hand side region, so g = D^T b is summed there
+      RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), H->spe_m, b, H->n, H->rhs_box, x, H->len, H->opt.eps_lin,
+                H->spe_hpart, H->spe_gpart, H->coef, H->small, st));
       *used_small = 1;
       *init = 0;
       break;
@@ -494,6 +521,9 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   // device
   CK(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking));
   H->own_st = H->st;
+  CK(cudaStreamCreateWithFlags(&H->st2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
   RK(pcg_max_blocks(&H->nblk));
   const size_t L = (size_t)H->len;
   const long ccells = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
@@ -512,6 +542,8 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->derr, 1));
   RK(dalloc(H, &H->pres, 1));
   RK(dalloc(H, &H->tspart, (size_t)5 * ts_nblk() * kTileSlots));
+  RK(dalloc(H, &H->spe_hpart, (size_t)4 * ts_nblk() * kTileSlots));
+  RK(dalloc(H, &H->spe_gpart, (size_t)spe_gblocks() * kSpeGSlots));
   RK(dalloc(H, &H->coef, kMaxVec));
   RK(dalloc(H, &H->sigma, kMaxVec));
   RK(dalloc(H, &H->scal, 4));
@@ -604,10 +636,15 @@ void clear_history(mqs_handle* H) {
   H->cspe_count = 0;
 }
 
-int ensure_stats(mqs_handle* H, int nsteps) {
+// room for nsteps records; the first `keep` records (steps enqueued and not yet
+// finished) move to a grown buffer in stream order
+int ensure_stats(mqs_handle* H, int nsteps, int keep = 0) {
   if (H->dstats_cap >= nsteps) return MQS_OK;
-  int cap = std::max(nsteps, 256);
+  const int cap = std::max(nsteps, std::max(2 * H->dstats_cap, 256));
+  mqs_step_stats* old = H->dstats;
   RK(dalloc(H, &H->dstats, cap));
+  if (keep > 0 && old)
+    CK(cudaMemcpyAsync(H->dstats, old, sizeof(mqs_step_stats) * keep, cudaMemcpyDeviceToDevice, H->st));
   H->dstats_cap = cap;
   return MQS_OK;
 }
@@ -647,9 +684,13 @@ int mqs_setup(const mqs_grid* grid, const mqs_materials* mat, const uint8_t* con
 int mqs_destroy(mqs_handle* H) {
   if (!H) return MQS_OK;
   if (H->st) cudaStreamSynchronize(H->st);
+  if (H->st2) cudaStreamSynchronize(H->st2);
   for (void* v : H->allocs) cudaFree(v);
   for (cudaEvent_t e : H->ev_pool) cudaEventDestroy(e);
   if (H->own_st) cudaStreamDestroy(H->own_st);
+  if (H->st2) cudaStreamDestroy(H->st2);
+  if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+  if (H->ev_join) cudaEventDestroy(H->ev_join);
   delete H;
   return MQS_OK;
 }
@@ -729,13 +770,14 @@ int enqueue_step(mqs_handle* H, int s) {
   H->lx_valid = true;
   nl += 1;
   mark(H);
+  // (a6) history first: the SPE push forks to the side stream here and runs beside
+  // the conductor update (both only read w and L w)
+  RK(history_push(H, H->x, H->lx, st));
+  nl += history_launches(H);
+  mark(H);
   // (a5) conducting update, eq. (acm)
   RK(conductor_step(H, H->x, H->dt, st));
   nl += H->any_brauer ? 2 : 1;
-  mark(H);
-  // (a6) history
-  RK(history_push(H, H->x, H->lx, st));
-  nl += history_launches(H);
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
                                  H->dstats + s);
   nl += 1;
@@ -784,14 +826,15 @@ int ensure_adjoint(mqs_handle* H, int nsteps) {
   return MQS_OK;
 }
 
-int prepare_steps(mqs_handle* H, int nsteps) {
+int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
-  return ensure_stats(H, nsteps);
+  return ensure_stats(H, nsteps, keep);
 }
 
 // Copies the step statistics of the last nsteps steps into hs (async on H->st).
 int fetch_stats(mqs_handle* H, int nsteps, mqs_step_stats* hs, int* derr) {
+  RK(join_side(H));
   CK(cudaMemcpyAsync(hs, H->dstats, sizeof(mqs_step_stats) * nsteps, cudaMemcpyDeviceToHost, H->st));
   CK(cudaMemcpyAsync(derr, H->derr, sizeof(int), cudaMemcpyDeviceToHost, H->st));
   return MQS_OK;
@@ -811,9 +854,29 @@ int check_stats(mqs_handle* H, int nsteps, const mqs_step_stats* hs, int derr) {
 
 int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
   if (!H || nsteps < 0) return MQS_ERR_ARG;
+  if (H->enqueued) return fail(H, MQS_ERR_ARG, "steps are enqueued: call mqs_step_finish first");
   if (nsteps == 0) return (H->dt > 0.0) ? MQS_OK : fail(H, MQS_ERR_ARG, "dt is not set");
-  RK(prepare_steps(H, nsteps));
-  for (int s = 0; s < nsteps; ++s) RK(enqueue_step(H, s));
+  RK(mqs_step_enqueue(H, nsteps));
+  return mqs_step_finish(H, nsteps, per_step);
+}
+
+int mqs_step_enqueue(mqs_handle* H, int nsteps) {
+  if (!H || nsteps < 1) return MQS_ERR_ARG;
+  if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
+  if (nsteps > (1 << 30) - H->enqueued) return fail(H, MQS_ERR_ARG, "too many steps enqueued");
+  const int base = H->enqueued;
+  int rc = prepare_steps(H, base + nsteps, base);
+  for (int s = 0; s < nsteps && rc == MQS_OK; ++s) rc = enqueue_step(H, base + s);
+  const int rj = join_side(H);          // also after a failed launch: nothing left running beside
+  if (rc != MQS_OK) { H->enqueued = 0; return rc; }
+  if (rj != MQS_OK) { H->enqueued = 0; return rj; }
+  H->enqueued = base + nsteps;
+  return MQS_OK;
+}
+
+int mqs_step_finish(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
+  if (!H || nsteps < 1 || nsteps != H->enqueued) return MQS_ERR_ARG;
+  H->enqueued = 0;
   std::vector<mqs_step_stats> hs(nsteps);
   int derr = 0;
   RK(fetch_stats(H, nsteps, hs.data(), &derr));
@@ -1124,15 +1187,16 @@ int mqs_timing_get(mqs_handle* H, mqs_timing* out) {
   if (!H || !out) return MQS_ERR_ARG;
   CK(cudaStreamSynchronize(H->st));
   double acc[5] = {0, 0, 0, 0, 0};
-  // six marks per step: phases between consecutive marks
+  // six marks per step: phases between consecutive marks, in issue order rhs, start,
+  // PCG, history (the fork of the SPE push), conductor (with the statistics record)
   for (size_t s = 0; s + 6 <= H->ev_used; s += 6)
     for (int ph = 0; ph < 5; ++ph) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, H->ev_pool[s + ph], H->ev_pool[s + ph + 1]));
       acc[ph] += ms;
     }
-  out->ms_rhs = acc[0]; out->ms_start = acc[1]; out->ms_pcg = acc[2]; out->ms_conductor = acc[3];
-  out->ms_history = acc[4];
+  out->ms_rhs = acc[0]; out->ms_start = acc[1]; out->ms_pcg = acc[2]; out->ms_history = acc[3];
+  out->ms_conductor = acc[4];
   out->launches = H->launches;
   out->pcg_launches = H->pcg_launches;
   out->steps = H->tsteps;
@@ -1156,6 +1220,7 @@ int mqs_push_history(mqs_handle* H, const double* w) {
     H->lx_valid = true;
   }
   RK(history_push(H, H->tmp2, H->tmp, st));
+  RK(join_side(H));
   CK(cudaStreamSynchronize(st));
   return MQS_OK;
 }
@@ -1166,8 +1231,9 @@ int spe_start(mqs_handle* H, const double* b, double* x0, int* rank_used) {
   CK(cudaMemcpyAsync(H->tmp, b, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
   RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
   const int d = H->opt.spe_depth;
-  RK(spe_x0(vs(H->spe_D, d), vs(H->spe_LD, d), H->spe_m, H->bu, H->xu, H->len, H->opt.eps_lin, H->tspart, H->coef,
-            H->small, st, H->tmp2));
+  RK(join_side(H));
+  RK(spe_x0(vs(H->spe_D, d), H->spe_m, H->bu, H->n, H->full, H->xu, H->len, H->opt.eps_lin, H->spe_hpart,
+            H->spe_gpart, H->coef, H->small, st));
   SmallOut so{};
   CK(cudaMemcpyAsync(x0, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
   if (H->spe_m > 0) CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));
@@ -1350,6 +1416,8 @@ int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
   // so the streams advance side by side
   for (int s = 0; s < nsteps && rc == MQS_OK; ++s)
     for (int i = 0; i < cnt && rc == MQS_OK; ++i) rc = enqueue_step(B->hs[i], s);
+  for (mqs_handle* H : B->hs)
+    if (join_side(H) != MQS_OK && rc == MQS_OK) rc = MQS_ERR_CUDA;   // side streams inside the timed span
   for (size_t i = 0; i < B->streams.size(); ++i) {
     BCK(cudaEventRecord(B->done[i], B->streams[i]));
     BCK(cudaStreamWaitEvent(B->master, B->done[i], 0));

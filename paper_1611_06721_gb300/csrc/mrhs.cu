@@ -263,32 +263,6 @@ __device__ double sum_part(const double* part, int nblk, int slot) {
   return s;
 }
 
-// out[t] = sum over blocks of partial slot slots[t], t < ns: one warp per
-// slot, lanes strided over the blocks (all loads issued before the adds),
-// then a fixed shuffle tree.
-__device__ void sum_parts_warp(const double* part, int nblk, const int* tiles, const int* slots, int ns,
-                               double* out) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = w; t < ns; t += nw) {
-    const double* pt = part + (size_t)tiles[t] * nblk * kTileSlots + slots[t];
-    double v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int q = lane + 32 * r;
-      v[r] = (q < nblk) ? pt[(size_t)q * kTileSlots] : 0.0;
-    }
-    // pairwise (fixed order): four dependent FP64 additions instead of sixteen
-#pragma unroll
-    for (int w2 = 8; w2 >= 1; w2 >>= 1)
-#pragma unroll
-      for (int r = 0; r < w2; ++r) v[r] += v[r + w2];
-    double s = v[0];
-    for (int q = lane + 512; q < nblk; q += 32) s += pt[(size_t)q * kTileSlots];
-    s = warp_sum(s);
-    if (lane == 0) out[t] = s;
-  }
-}
-
 // Pivoted (in order) Cholesky of the symmetric m x m matrix H (row-major in
 // smem, m <= 64), dropping column j when its pivot v satisfies
 // v*H_jj <= drop2*H_00 (scaled-unit diagonal) or v <= rel_floor.  Solves
@@ -385,14 +359,15 @@ __device__ int chol_drop_solve(double* H, double* g, double* y, int m, double dr
   return nk_s;
 }
 
-// chol_drop_solve for m <= 16 held in registers: lane r keeps row r of the scaled
+// chol_drop_solve for m <= M (8 or 16) held in registers: lane r keeps row r of the scaled
 // matrix (compile-time indexed, every loop unrolled), column values travel by
 // shuffles.  Same pivot order, scaling, drop rule and substitutions as
 // chol_drop_solve; on this GPU every dependent FP64 step costs the FP64 unit's issue
 // time, so the register form keeps the serial chain short.  Called by warp 0.
-__device__ int chol_drop_solve16(const double* H, const double* g, double* y, int m, double drop2,
-                                 double rel_floor) {
-  constexpr int M = 16;
+template <int M>
+__device__ int chol_drop_solve_reg(const double* H, const double* g, double* y, int m, double drop2,
+                                   double rel_floor) {
+  static_assert(M <= 32, "one row per lane");
   const int lane = threadIdx.x & 31;
   const bool own = lane < m;
   double h[M];
@@ -450,47 +425,6 @@ __device__ int chol_drop_solve16(const double* H, const double* g, double* y, in
   }
   if (own) y[lane] = u * sc;
   return nk;
-}
-
-__global__ void __launch_bounds__(512) spe_solve_kernel(const double* part, int nblk, int m, double drop2, double* coef,
-                                 SmallOut* out) {
-  __shared__ double H[kMaxSpe * kMaxSpe], Ls[kMaxSpe * kMaxSpe], g[kMaxSpe], y[kMaxSpe];
-  __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
-  __shared__ int tiles[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe], slots[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
-  __shared__ int keep[kMaxSpe];
-  // entries (q, p), q >= p, live in tile 0 = rows/cols 0..7, tiles 1 and 3 = (p < 8 <= q,
-  // rows 8-11 and 12-15), tile 2 = 8..15; g (D^T b) rows 0..7 in tile 0 and 8..15 in tile 2
-  const int npair = m * (m + 1) / 2;
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int qq = 0; qq < m; ++qq)
-      for (int pp = 0; pp <= qq; ++pp, ++t) {
-        if (qq < 8) { tiles[t] = 0; slots[t] = pp * 8 + qq; }
-        else if (pp < 8) { tiles[t] = qq < 12 ? 1 : 3; slots[t] = pp * 8 + (qq < 12 ? qq - 8 : qq - 12); }
-        else { tiles[t] = 2; slots[t] = (pp - 8) * 8 + (qq - 8); }
-      }
-    for (int p = 0; p < m; ++p, ++t) {
-      tiles[t] = (p < 8) ? 0 : 2;
-      slots[t] = 64 + (p % 8);
-    }
-  }
-  __syncthreads();
-  sum_parts_warp(part, nblk, tiles, slots, npair + m, vals);
-  __syncthreads();
-  for (int s = threadIdx.x; s < m * m; s += blockDim.x) {
-    const int p = s / m, q = s % m;
-    const int pp = p < q ? p : q, qq = p < q ? q : p;
-    H[s] = vals[qq * (qq + 1) / 2 + pp];
-  }
-  for (int p = threadIdx.x; p < m; p += blockDim.x) g[p] = vals[npair + p];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nk = chol_drop_solve16(H, g, y, m, drop2, 1e-13);
-    __syncwarp();
-    if (threadIdx.x < m) coef[threadIdx.x] = y[threadIdx.x];
-    if (threadIdx.x == 0) { out->rank = nk; out->info = 0.0; }
-  }
-  (void)Ls; (void)keep;
 }
 
 // Gram row of a new snapshot: part tiles t = 0..ntile-1 hold (w, Lw) . X_q.
@@ -758,44 +692,87 @@ __global__ void __launch_bounds__(kTS) diff_push_ff_kernel(MutVecSet D, MutVecSe
   }
 }
 
-// Galerkin products of float-float tables (same slot layout as dots_kernel, FP64
-// partials per block): kTri: A_p . B_q, q >= p, plus B_q . c; kFull: all 64 pairs.
+// ---- SPE products: float-float partial sums ---------------------------------------------
+// Every product kernel below accumulates (S, E) pairs per thread (ff_mac), reduces
+// them across the warp by a reduce-scatter (four halvings over lane offsets 16..2,
+// then a butterfly over offset 1: the even lanes end with NS/16 slots each), sums
+// the warps' pairs in shared memory and writes one normalised float-float partial
+// per slot and block (float2 in the 8-byte slots of the partial buffers).  The
+// small solve sums the partials of all blocks on the FP32 pipes as well.
+template <int NS>
+__device__ __forceinline__ void warp_scatter_ff(float (&vs)[NS], float (&ve)[NS]) {
+  static_assert(NS % 16 == 0, "slots in multiples of 16");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int half = NS / 2, off = 16; off >= 2; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float ks = up ? vs[i + half] : vs[i], ke = up ? ve[i + half] : ve[i];
+      const float ss = up ? vs[i] : vs[i + half], se = up ? ve[i] : ve[i + half];
+      vs[i] = ks;
+      ve[i] = ke;
+      ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, ss, off), __shfl_xor_sync(0xffffffffu, se, off));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NS / 16; ++i)
+    ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, vs[i], 1), __shfl_xor_sync(0xffffffffu, ve[i], 1));
+}
+
+// Block partials of NS slots: slot s goes to row[dst(s)] (dst < 0: not stored).
+// red: shared (kTS / 32) x NS float2.  All threads of the block call.
+template <int NS, class Dst>
+__device__ __forceinline__ void block_partials_ff(float (&vs)[NS], float (&ve)[NS], float2 (*red)[NS], Dst dst,
+                                                  float2* row) {
+  warp_scatter_ff<NS>(vs, ve);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  constexpr int FIN = NS / 16;
+  if ((lane & 1) == 0) {
+    const int base = FIN * (8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1));
+#pragma unroll
+    for (int i = 0; i < FIN; ++i) red[wp][base + i] = make_float2(vs[i], ve[i]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+    const int d = dst(s);
+    if (d < 0) continue;
+    float S = red[0][s].x, E = red[0][s].y;
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) ff_acc(S, E, red[q][s].x, red[q][s].y);
+    row[d] = ff_fast_two_sum(S, E);
+  }
+}
+
+// Galerkin products of float-float tables (slot layout of dots_kernel's tiles):
+// kTri: A_p . B_q, q >= p < 8; kRect4: 8 columns of A x 4 rows of B; kTri4: the
+// 4 x 4 triangle.  part: float2 partials, kTileSlots per block.
 template <int MODE>
-__global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, const double* c, int ma, int mb,
-                                                        long long len, double* part) {
-  constexpr bool TRI4 = (MODE == kTri4);    // 4 x 4 lower triangle (rows 8-11 of a 12-column table)
+__global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, int ma, int mb, long long len,
+                                                        float2* part) {
+  constexpr bool TRI4 = (MODE == kTri4);
   constexpr bool DIAG = (MODE == kTri) || TRI4;
-  constexpr bool RECT = (MODE == kRect4);   // 8 columns of A x 4 rows of B
+  constexpr bool RECT = (MODE == kRect4);
   constexpr int NA = TRI4 ? 4 : 8;
   constexpr int NB = (RECT || TRI4) ? 4 : 8;
-  constexpr int NP = (MODE == kTri) ? 36 : (TRI4 ? 10 : (RECT ? 32 : 64));
-  constexpr bool PIPE = DIAG || RECT;       // the 64-pair tile has no registers left for a second element
-  float S[NP], E[NP], Sc[8], Ec[8];
+  constexpr int NP = (MODE == kTri) ? 36 : (TRI4 ? 10 : 32);
+  constexpr int NS = (NP + 15) / 16 * 16;
+  float S[NS], E[NS];
 #pragma unroll
-  for (int t = 0; t < NP; ++t) { S[t] = 0.f; E[t] = 0.f; }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { Sc[q] = 0.f; Ec[q] = 0.f; }
+  for (int t = 0; t < NS; ++t) { S[t] = 0.f; E[t] = 0.f; }
   const long long stride = (long long)gridDim.x * blockDim.x;
   float2 a[NA], b[NB];
-  double ce = 0.0;
-  auto load = [&](long long e, float2* aa, float2* bb, double& cc) {
+  auto load = [&](long long e, float2* aa, float2* bb) {
 #pragma unroll
     for (int p = 0; p < NA; ++p) aa[p] = (p < ma) ? reinterpret_cast<const float2*>(A.v[p])[e] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < NB; ++q) bb[q] = (q < mb) ? reinterpret_cast<const float2*>(B.v[q])[e] : make_float2(0.f, 0.f);
-    cc = (c != nullptr) ? c[e] : 0.0;
   };
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (PIPE && e < len) load(e, a, b, ce);
+  if (e < len) load(e, a, b);
   for (; e < len; e += stride) {
     // the next element's inputs are in flight while this one is reduced
     float2 an[NA], bn[NB];
-    double cn = 0.0;
-    if (PIPE) {
-      if (e + stride < len) load(e + stride, an, bn, cn);
-    } else {
-      load(e, a, b, ce);
-    }
+    if (e + stride < len) load(e + stride, an, bn);
     int t = 0;
 #pragma unroll
     for (int p = 0; p < NA; ++p) {
@@ -803,126 +780,111 @@ __global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, con
       for (int q = (DIAG ? p : 0); q < NB; ++q, ++t)
         if (p < ma && q < mb) ff_mac(a[p], b[q], S[t], E[t]);
     }
-    if (!RECT && ce != 0.0) {
-      const float2 cf = ff_split(ce);
 #pragma unroll
-      for (int q = 0; q < NB; ++q)
-        if (q < mb) ff_mac(b[q], cf, Sc[q], Ec[q]);
-    }
-    if (PIPE) {
+    for (int p = 0; p < NA; ++p) a[p] = an[p];
 #pragma unroll
-      for (int p = 0; p < NA; ++p) a[p] = an[p];
-#pragma unroll
-      for (int q = 0; q < NB; ++q) b[q] = bn[q];
-      ce = cn;
-    }
+    for (int q = 0; q < NB; ++q) b[q] = bn[q];
   }
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  __shared__ double red[kTS / 32][kTileSlots];
-  if (TRI4) {
-    // ten products and four c products: butterfly sums per slot
-    int t = 0;
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = p; q < 4; ++q, ++t) {
-        float s2 = S[t], e2 = E[t];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-          ff_acc(s2, e2, __shfl_xor_sync(0xffffffffu, s2, off), __shfl_xor_sync(0xffffffffu, e2, off));
-        if (lane == 0) red[wp][p * 8 + q] = ff_join(s2, e2);
-      }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float s2 = Sc[q], e2 = Ec[q];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        ff_acc(s2, e2, __shfl_xor_sync(0xffffffffu, s2, off), __shfl_xor_sync(0xffffffffu, e2, off));
-      if (lane == 0) red[wp][64 + q] = ff_join(s2, e2);
-    }
-    for (int t2 = lane; t2 < kTileSlots; t2 += 32) {
-      const int p = t2 / 8, q = t2 % 8;
-      const bool used = (t2 < 64) ? (p < 4 && q < 4 && q >= p) : (t2 - 64 < 4);
-      if (!used) red[wp][t2] = 0.0;
-    }
-  } else if (RECT) {
-    // warp reduce-scatter over the 32 products: five halvings, lane l keeps product l
-    float vs[32], ve[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) { vs[t] = S[t]; ve[t] = E[t]; }
-#pragma unroll
-    for (int half = 16, off = 16; off >= 1; half >>= 1, off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int i = 0; i < half; ++i) {
-        const float ks = up ? vs[i + half] : vs[i], ke = up ? ve[i + half] : ve[i];
-        const float ss = up ? vs[i] : vs[i + half], se = up ? ve[i] : ve[i + half];
-        vs[i] = ks;
-        ve[i] = ke;
-        ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, ss, off), __shfl_xor_sync(0xffffffffu, se, off));
-      }
-    }
-    // product index lane = p * 4 + q (column p of A, row q of B) -> slot p * 8 + q
-    red[wp][(lane >> 2) * 8 + (lane & 3)] = ff_join(vs[0], ve[0]);
-    red[wp][(lane >> 2) * 8 + 4 + (lane & 3)] = 0.0;
-    if (lane < 8) red[wp][64 + lane] = 0.0;
-  } else if (MODE == kFull) {
-    // more than 8 SPE columns: butterfly sums per slot
-#pragma unroll
-    for (int t = 0; t < 64; ++t) {
-      float s = S[t], ee = E[t];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        ff_acc(s, ee, __shfl_xor_sync(0xffffffffu, s, off), __shfl_xor_sync(0xffffffffu, ee, off));
-      if (lane == 0) red[wp][t] = ff_join(s, ee);
-    }
-    if (lane < 8) red[wp][64 + lane] = 0.0;
+  __shared__ float2 red[kTS / 32][NS];
+  float2* row = part + (size_t)blockIdx.x * kTileSlots;
+  if (MODE == kTri) {
+    block_partials_ff<NS>(S, E, red, [](int s) { return s < 36 ? c_tri_slot[s] : -1; }, row);
+  } else if (TRI4) {
+    // product t of the 4 x 4 triangle (p, then q >= p) -> slot p * 8 + q
+    block_partials_ff<NS>(S, E, red, [](int s) {
+      const int p = s < 4 ? 0 : s < 7 ? 1 : s < 9 ? 2 : s < 10 ? 3 : -1;
+      const int q = s < 4 ? s : s < 7 ? s - 3 : s < 9 ? s - 5 : s - 6;
+      return p < 0 ? -1 : p * 8 + q;
+    }, row);
   } else {
-    // warp reduce-scatter over 48 slots (36 products, then 8 c products), as dots_kernel
-    float vs[48], ve[48];
+    // product p * 4 + q (column p of A, row q of B) -> slot p * 8 + q
+    block_partials_ff<NS>(S, E, red, [](int s) { return (s >> 2) * 8 + (s & 3); }, row);
+  }
+}
+
+// Push of the newest solution w (image lw) into the float-float table fused with the
+// Galerkin products of the new table (tile 0: D_q . LD_p, p <= q < m_new <= 8):
+// one pass over the table instead of a push and a second pass re-reading it.
+// New table: D_0 = w, D_p = D_{p-1}^new - D_{p-1}^old (and likewise the images).
+__global__ void __launch_bounds__(kTS, 1) spe_push_dots_kernel(MutVecSet D, MutVecSet LD, const double* __restrict__ w,
+                                                              const double* __restrict__ lw, int m_old, int m_new,
+                                                              long long len, float2* part) {
+  constexpr int M = 8;
+  float S[48], E[48];
 #pragma unroll
-    for (int t = 0; t < 48; ++t) { vs[t] = 0.f; ve[t] = 0.f; }
+  for (int t = 0; t < 48; ++t) { S[t] = 0.f; E[t] = 0.f; }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float2 od[M], ol[M];
+  double we = 0.0, lwe = 0.0;
+  auto load = [&](long long e, float2* a, float2* b, double& x, double& y) {
 #pragma unroll
-    for (int t = 0; t < 36; ++t) { vs[t] = S[t]; ve[t] = E[t]; }
+    for (int p = 0; p < M; ++p) {
+      a[p] = (p < m_old) ? reinterpret_cast<const float2*>(D.v[p])[e] : make_float2(0.f, 0.f);
+      b[p] = (p < m_old) ? reinterpret_cast<const float2*>(LD.v[p])[e] : make_float2(0.f, 0.f);
+    }
+    x = w[e];
+    y = lw[e];
+  };
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < len) load(e, od, ol, we, lwe);
+  for (; e < len; e += stride) {
+    float2 nd[M], nl[M];
+    double wn = 0.0, lwn = 0.0;
+    if (e + stride < len) load(e + stride, nd, nl, wn, lwn);
+    float2 cd[M], cl[M];
+    float2 t = ff_split(we), tl = ff_split(lwe);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { vs[36 + q] = Sc[q]; ve[36 + q] = Ec[q]; }
-#pragma unroll
-    for (int half = 24, off = 16; off >= 2; half >>= 1, off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int i = 0; i < half; ++i) {
-        const float ks = up ? vs[i + half] : vs[i], ke = up ? ve[i + half] : ve[i];
-        const float ss = up ? vs[i] : vs[i + half], se = up ? ve[i] : ve[i + half];
-        vs[i] = ks;
-        ve[i] = ke;
-        ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, ss, off), __shfl_xor_sync(0xffffffffu, se, off));
+    for (int p = 0; p < M; ++p) {
+      cd[p] = t;
+      cl[p] = tl;
+      if (p < m_new) {
+        reinterpret_cast<float2*>(D.v[p])[e] = t;
+        reinterpret_cast<float2*>(LD.v[p])[e] = tl;
       }
+      if (p + 1 < M && p < m_old) { t = ff_sub(t, od[p]); tl = ff_sub(tl, ol[p]); }
+    }
+    int k = 0;
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+#pragma unroll
+      for (int q = p; q < M; ++q, ++k)
+        if (q < m_new) ff_mac(cl[p], cd[q], S[k], E[k]);
     }
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-      ff_acc(vs[i], ve[i], __shfl_xor_sync(0xffffffffu, vs[i], 1), __shfl_xor_sync(0xffffffffu, ve[i], 1));
-    if ((lane & 1) == 0) {
-      const int base = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) + 3 * ((lane >> 1) & 1);
+    for (int p = 0; p < M; ++p) { od[p] = nd[p]; ol[p] = nl[p]; }
+    we = wn;
+    lwe = lwn;
+  }
+  __shared__ float2 red[kTS / 32][48];
+  block_partials_ff<48>(S, E, red, [](int s) { return s < 36 ? c_tri_slot[s] : -1; },
+                        part + (size_t)blockIdx.x * kTileSlots);
+}
+
+// g_q = D_q . b (q < m <= MAXM) over the edges of the positions in box (b is zero
+// elsewhere); float-float partials, kSpeGSlots per block.
+template <int MAXM>
+__global__ void __launch_bounds__(kTS) spe_g_kernel(VecSet D, const double* __restrict__ b, int m, int n, Box box,
+                                                    float2* gpart) {
+  const int bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
+  const int npos = bx * by * bz;
+  const long long n3 = (long long)n * n * n;
+  float S[16], E[16];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int sl = base + i;
-        int dst = -1;
-        if (sl >= 36) dst = (sl < 44) ? 64 + (sl - 36) : -1;
-        else dst = c_tri_slot[sl];
-        if (dst >= 0) red[wp][dst] = ff_join(vs[i], ve[i]);
-      }
-    }
-    for (int t = lane; t < 64; t += 32) {
-      const int p = t / 8, q = t % 8;
-      if (q < p) red[wp][t] = 0.0;
+  for (int q = 0; q < 16; ++q) { S[q] = 0.f; E[q] = 0.f; }
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < 3 * npos; u += gridDim.x * blockDim.x) {
+    const int c = u / npos, r = u - c * npos;
+    const int i = box.lo[0] + r % bx, j = box.lo[1] + (r / bx) % by, k = box.lo[2] + r / (bx * by);
+    const long long e = c * n3 + i + (long long)n * (j + (long long)n * k);
+    const double be = b[e];
+    if (be != 0.0) {
+      const float2 bf = ff_split(be);
+#pragma unroll
+      for (int q = 0; q < MAXM; ++q)
+        if (q < m) ff_mac(reinterpret_cast<const float2*>(D.v[q])[e], bf, S[q], E[q]);
     }
   }
-  __syncthreads();
-  for (int s2 = threadIdx.x; s2 < kTileSlots; s2 += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < kTS / 32; ++q) t += red[q][s2];
-    part[(size_t)blockIdx.x * kTileSlots + s2] = t;
-  }
+  __shared__ float2 red[kTS / 32][16];
+  block_partials_ff<16>(S, E, red, [](int s) { return s; }, gpart + (size_t)blockIdx.x * kSpeGSlots);
 }
 
 // x = sum_p coef_p V_p with float-float V and FP64 coefficients
@@ -941,6 +903,82 @@ __global__ void __launch_bounds__(kTS) lincomb_ff_kernel(VecSet V, const double*
     for (int p = 0; p < MAXM; ++p)
       if (p < m) ff_mac(cf[p], v[p], s, ee);
     x[e] = ff_join(s, ee);
+  }
+}
+
+// Sum over cnt blocks of one float-float partial (base[q * stride], q < cnt) by one
+// warp: loads issued together, a fixed pairwise tree, a shuffle butterfly; lane 0
+// holds the defined value.
+__device__ __forceinline__ ffv sum_parts_ff(const float2* base, int stride, int cnt) {
+  const int lane = threadIdx.x & 31;
+  ffv v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int q = lane + 32 * r;
+    const float2 f = (q < cnt) ? base[(size_t)q * stride] : make_float2(0.f, 0.f);
+    v[r] = ffv(f.x, f.y);
+  }
+#pragma unroll
+  for (int w2 = 8; w2 >= 1; w2 >>= 1)
+#pragma unroll
+    for (int r = 0; r < w2; ++r) v[r] = v[r] + v[r + w2];
+  ffv s = v[0];
+  for (int q = lane + 512; q < cnt; q += 32) {
+    const float2 f = base[(size_t)q * stride];
+    s = s + ffv(f.x, f.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = s + shfl_x(s, o);
+  return s;
+}
+
+// SPE small system: sums the product partials (entries (q, p), q >= p, of
+// H = D^T K D in tiles of 8: tile 0 rows/columns 0-7, tiles 1 and 3 rows 8-11 and
+// 12-15 against columns 0-7, tile 2 rows/columns 8-15) and g = D^T b, then the
+// pivoted Cholesky with the drop rule (register form, warp 0) and coef = y.
+__global__ void __launch_bounds__(512) spe_solve_kernel(const float2* hpart, int nbh, const float2* gpart, int nbg,
+                                                        int m, double drop2, double* coef, SmallOut* out) {
+  __shared__ double H[kMaxSpe * kMaxSpe], g[kMaxSpe], y[kMaxSpe];
+  __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
+  const int npair = m * (m + 1) / 2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = wid; t < npair + m; t += nw) {
+    const float2* base;
+    int stride, cnt;
+    if (t < npair) {
+      int qq = 0;
+      while ((qq + 1) * (qq + 2) / 2 <= t) ++qq;
+      const int pp = t - qq * (qq + 1) / 2;
+      int tile, slot;
+      if (qq < 8) { tile = 0; slot = pp * 8 + qq; }
+      else if (pp < 8) { tile = qq < 12 ? 1 : 3; slot = pp * 8 + (qq < 12 ? qq - 8 : qq - 12); }
+      else { tile = 2; slot = (pp - 8) * 8 + (qq - 8); }
+      base = hpart + (size_t)tile * nbh * kTileSlots + slot;
+      stride = kTileSlots;
+      cnt = nbh;
+    } else {
+      base = gpart + (t - npair);
+      stride = kSpeGSlots;
+      cnt = nbg;
+    }
+    const ffv s = sum_parts_ff(base, stride, cnt);
+    if (lane == 0) vals[t] = ff_to(s);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < m * m; s += blockDim.x) {
+    const int p = s / m, q = s % m;
+    const int pp = p < q ? p : q, qq = p < q ? q : p;
+    H[s] = vals[qq * (qq + 1) / 2 + pp];
+  }
+  for (int p = threadIdx.x; p < m; p += blockDim.x) g[p] = vals[npair + p];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // unrolled to the table width: every unrolled FP64 step costs its issue time
+    const int nk = (m <= 8) ? chol_drop_solve_reg<8>(H, g, y, m, drop2, 1e-13)
+                            : chol_drop_solve_reg<16>(H, g, y, m, drop2, 1e-13);
+    __syncwarp();
+    if (threadIdx.x < m) coef[threadIdx.x] = y[threadIdx.x];
+    if (threadIdx.x == 0) { out->rank = nk; out->info = 0.0; }
   }
 }
 
@@ -966,46 +1004,60 @@ int ts_nblk() { return ts_max_blocks(); }
 
 static int chk() { return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA; }
 
-int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
-             long long len, cudaStream_t st) {
-  const int nb = ts_blocks(len) * 2;
-  if (m_new <= 4) diff_push_ff_kernel<4><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else if (m_new <= 8) diff_push_ff_kernel<8><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  else diff_push_ff_kernel<16><<<nb, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
-  return chk();
+int spe_hblocks(long long len, int m) {
+  // the fused push + product pass keeps one block per SM (its registers); the
+  // separate product tiles (more than 8 columns) run ts_blocks blocks
+  return m <= 8 ? std::min(ts_blocks(len), ts_max_blocks() / 2) : ts_blocks(len);
 }
+int spe_gblocks() { return ts_max_blocks(); }
 
-int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st, double* scratch) {
-  const int nb = ts_blocks(len);
-  if (m <= 0) {
-    if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
-    return MQS_OK;
+int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
+             long long len, double* hpart, cudaStream_t st) {
+  float2* hp = reinterpret_cast<float2*>(hpart);
+  if (m_new <= 8) {
+    spe_push_dots_kernel<<<spe_hblocks(len, m_new), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len, hp);
+    return chk();
   }
-  (void)scratch;   // b is split into float-float inside the product kernels
+  diff_push_ff_kernel<16><<<ts_blocks(len) * 2, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   // Entry (q, p), q >= p, of the Galerkin matrix is D_q . (K D_p): the
   // high-order differences are tested against the K-images of the low-order
   // ones, which the recursion carries accurately (the images of high orders
   // accumulate its rounding relative to their small size).
-  VecSet A0 = LD, B0 = D;
-  dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, b, m < 8 ? m : 8, m < 8 ? m : 8, len, part);
-  if (m > 8) {
-    // rows 8.. of D against the first 8 images, in 8 x 4 tiles (tile 1: rows 8-11, tile 3: rows 12-15)
-    for (int h = 0; h < 2 && 8 + 4 * h < m; ++h) {
-      VecSet A1, B1;
-      const int r0 = 8 + 4 * h, rows = (m - r0) < 4 ? (m - r0) : 4;
-      for (int p = 0; p < 8; ++p) A1.v[p] = LD.v[p];
-      for (int q = 0; q < 8; ++q) B1.v[q] = D.v[q < rows ? r0 + q : r0];
-      dots_ff_kernel<kRect4><<<nb, kTS, 0, st>>>(A1, B1, nullptr, 8, rows, len,
-                                                 part + (size_t)(h == 0 ? 1 : 3) * nb * kTileSlots);
-    }
-    VecSet A2, B2;
-    for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 8]; B2.v[p] = D.v[8 + p < m ? 8 + p : 8]; }
-    if (m <= 12) dots_ff_kernel<kTri4><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
-    else dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, b, m - 8, m - 8, len, part + (size_t)2 * nb * kTileSlots);
+  const int nb = spe_hblocks(len, m_new), m = m_new;
+  VecSet A0{}, B0{};
+  for (int p = 0; p < 8; ++p) { A0.v[p] = LD.v[p]; B0.v[p] = D.v[p]; }
+  dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A0, B0, 8, 8, len, hp);
+  // rows 8.. of D against the first 8 images, in 8 x 4 tiles (tile 1: rows 8-11, tile 3: rows 12-15)
+  for (int h = 0; h < 2 && 8 + 4 * h < m; ++h) {
+    VecSet A1{}, B1{};
+    const int r0 = 8 + 4 * h, rows = (m - r0) < 4 ? (m - r0) : 4;
+    for (int p = 0; p < 8; ++p) A1.v[p] = LD.v[p];
+    for (int q = 0; q < 8; ++q) B1.v[q] = D.v[q < rows ? r0 + q : r0];
+    dots_ff_kernel<kRect4><<<nb, kTS, 0, st>>>(A1, B1, 8, rows, len, hp + (size_t)(h == 0 ? 1 : 3) * nb * kTileSlots);
   }
-  spe_solve_kernel<<<1, 512, 0, st>>>(part, nb, m, eps_lin * eps_lin, coef, out);
-  const int nl = nb * 4;
+  VecSet A2{}, B2{};
+  for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 8]; B2.v[p] = D.v[8 + p < m ? 8 + p : 8]; }
+  if (m <= 12) dots_ff_kernel<kTri4><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
+  else dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
+  return chk();
+}
+
+int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, double* x0, long long len,
+           double eps_lin, const double* hpart, double* gpart, double* coef, SmallOut* out, cudaStream_t st) {
+  if (m <= 0) {
+    if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
+    return MQS_OK;
+  }
+  if (m > kMaxSpe) return MQS_ERR_ARG;
+  // g: about one edge per thread (most of the region's b vanishes: latency, not bandwidth)
+  const long long edges = 3LL * (bbox.hi[0] - bbox.lo[0]) * (bbox.hi[1] - bbox.lo[1]) * (bbox.hi[2] - bbox.lo[2]);
+  const int nbg = (int)std::min<long long>(std::max<long long>((edges + kTS - 1) / kTS, 1), spe_gblocks());
+  float2* gp = reinterpret_cast<float2*>(gpart);
+  if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, gp);
+  else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, gp);
+  spe_solve_kernel<<<1, 512, 0, st>>>(reinterpret_cast<const float2*>(hpart), spe_hblocks(len, m), gp, nbg, m,
+                                      eps_lin * eps_lin, coef, out);
+  const int nl = ts_blocks(len) * 4;
   if (m <= 8) lincomb_ff_kernel<8><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   else if (m <= 12) lincomb_ff_kernel<12><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   else lincomb_ff_kernel<16><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);

@@ -16,13 +16,22 @@ struct SmallOut { int rank; int pad; double info; };
 
 int ts_nblk();
 // partial-sum buffer needed: 5 tiles * ts_nblk() * kTileSlots doubles
+constexpr int kSpeGSlots = 16;      // g = D^T b partials per block
 // SPE difference table D_p and images L D_p, stored as float-float pairs (8 bytes per
-// value, the buffers are FP64-sized): push the new solution w (FP64) and its image lw
+// value, the buffers are FP64-sized): push the new solution w (FP64) and its image lw,
+// and form the block partials of the Galerkin products D_q . L D_p (q >= p) of the new
+// table in hpart (4 tiles * ts_nblk() * kTileSlots 8-byte slots, float-float pairs)
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
-             long long len, cudaStream_t st);
-// x0 (FP64) = Galerkin start from the table; scratch: one layout vector (b in float-float)
-int spe_x0(const VecSet& D, const VecSet& LD, int m, const double* b, double* x0, long long len, double eps_lin,
-           double* part, double* coef, SmallOut* out, cudaStream_t st, double* scratch);
+             long long len, double* hpart, cudaStream_t st);
+// blocks of the product partials of a table of m columns (their layout in hpart)
+int spe_hblocks(long long len, int m);
+// gpart needed: spe_gblocks() * kSpeGSlots 8-byte slots
+int spe_gblocks();
+// x0 (FP64) = Galerkin start from the table of m columns, whose products spe_push left
+// in hpart: g = D^T b over the edges of the positions in bbox (b must vanish outside
+// it; n is the grid size), the small solve, x0 = D y
+int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, double* x0, long long len,
+           double eps_lin, const double* hpart, double* gpart, double* coef, SmallOut* out, cudaStream_t st);
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st);
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,

@@ -240,6 +240,35 @@ def test_checkpoint_resume_is_exact(pkg):
     s.close()
 
 
+def test_step_enqueue_finish_equals_step(pkg):
+    # the two halves of mqs_step (with the SPE table push on the side stream) give the
+    # bits of mqs_step, also with several enqueues before one finish; mqs_step while
+    # steps are enqueued and an unmatched finish are refused
+    p = W.scaled_nonlinear(16, amplitude=900.0)
+    dt = O.dt_gershgorin(O.Discretization(p))
+    a = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
+    b = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
+    _, sa = a.step(12)
+    for _ in range(2):
+        b.step_enqueue(4)
+        with pytest.raises(pkg.MqsError):
+            b.step(1)                                   # steps are enqueued
+        rc, sb = b.step_finish(4)
+        assert rc == 0 and all(x.status == 0 for x in sb)
+    for _ in range(4):
+        b.step_enqueue(1)                               # queued behind each other, one finish
+    rc, sb = b.step_finish(4)
+    assert rc == 0 and len(sb) == 4 and all(x.status == 0 and x.iterations > 0 for x in sb)
+    assert [x.iterations for x in sb] == [x.iterations for x in sa[8:]]
+    with pytest.raises(pkg.MqsError):
+        b.step_finish(4)
+    xa, ta, ma = a.get_state()
+    xb, tb, mb = b.get_state()
+    assert ma == mb == 12 and ta == tb and np.array_equal(xa, xb)
+    a.close()
+    b.close()
+
+
 # ---- full-size workload (64^3 nonlinear iron), sampled against the oracle -----------------------------
 def test_full_size_nonlinear_first_steps(pkg):
     p = W.config_nonlinear_iron()
