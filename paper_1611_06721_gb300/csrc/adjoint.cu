@@ -146,7 +146,7 @@ __global__ void adj_lambda_kernel(Geom g, CondGeom cg, const double* x, AdjBufs 
   }
 }
 
-// gI += -g(t) X_s . w' with g the unit-amplitude coil waveform (as in rhs_kernel)
+// gI += -g(t) X_s . w' with g the unit-amplitude coil waveform (as in the right-hand side kernel)
 __global__ void adj_coil_kernel(Geom g, CoilGeom coil, CoilDrive drv, const double* x, AdjBufs ab) {
   __shared__ double sh[256];
   const int n = g.n;

@@ -22,7 +22,9 @@ struct mqs_handle {
   long m = 0;
   long n_c = 0, n_n = 0;
   int cb_lo[3], cb_hi[3], clo[3], chi[3];
-  Box rhs_box{}, full{};
+  Box full{};
+  int* sup = nullptr;     // right-hand side support: layout indices where b may be nonzero (sorted)
+  int nsup = 0;
   bool any_brauer = false;
   cudaStream_t st = nullptr;
   int nblk = 0;
@@ -45,6 +47,8 @@ struct mqs_handle {
   double* spe_LD[kMaxSpe] = {};
   int spe_m = 0;
   double *spe_hpart = nullptr, *spe_gpart = nullptr;   // Galerkin product partials of the table, g partials
+  SpeFac* spe_fac = nullptr;     // factor of the table's small system (drop rule at fac_eps)
+  double fac_eps = -1.0;
   // side stream: the SPE table push (with its products) runs beside the conductor
   // update and the next right-hand side; the main stream joins before the table is read
   cudaStream_t st2 = nullptr;
@@ -260,6 +264,14 @@ int join_side(mqs_handle* H) {
   return MQS_OK;
 }
 
+// the table's factor again when eps_lin changed since the push (the products stay valid)
+int refactor_spe(mqs_handle* H, cudaStream_t st) {
+  if (H->fac_eps == H->opt.eps_lin) return MQS_OK;
+  RK(spe_factor(H->spe_hpart, H->spe_m, H->len, H->opt.eps_lin, H->spe_fac, st));
+  H->fac_eps = H->opt.eps_lin;
+  return MQS_OK;
+}
+
 int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t st) {
   const int mode = H->opt.start_mode;
   if (mode == MQS_START_SPE) {
@@ -270,13 +282,16 @@ int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t 
       // before the next start vector (which joins first)
       CK(cudaEventRecord(H->ev_fork, st));
       CK(cudaStreamWaitEvent(H->st2, H->ev_fork, 0));
-      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, H->st2));
+      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, H->opt.eps_lin,
+                  H->spe_fac, H->st2));
       CK(cudaEventRecord(H->ev_join, H->st2));
       H->side_pending = true;
     } else {
-      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, st));
+      RK(spe_push(mvs(H->spe_D, d), mvs(H->spe_LD, d), w, lw, H->spe_m, mn, H->len, H->spe_hpart, H->opt.eps_lin,
+                  H->spe_fac, st));
     }
     H->spe_m = mn;
+    H->fac_eps = H->opt.eps_lin;
   } else if (mode == MQS_START_POD) {
     const int np = H->opt.pod_snapshots;
     const int slot = H->pod_next;
@@ -334,9 +349,10 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
       if (H->spe_m == 0) { *init = 2; break; }
       // r = b - L x0 by the PCG's own stencil pass: forming it from the recursion
       // images costs a second read of the table and, measured, more iterations
-      // b vanishes outside the right-hand side region, so g = D^T b is summed there
-      RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), H->spe_m, b, H->n, H->rhs_box, x, H->len, H->opt.eps_lin,
-                H->spe_hpart, H->spe_gpart, H->coef, H->small, st));
+      // b vanishes off the right-hand side support, so g = D^T b is summed there
+      RK(refactor_spe(H, st));
+      RK(spe_x0(vs(H->spe_D, H->opt.spe_depth), H->spe_m, b, H->n, H->full, H->sup, H->nsup, x, H->len, H->spe_fac,
+                H->spe_gpart, H->coef, H->small, st));
       *used_small = 1;
       *init = 0;
       break;
@@ -369,8 +385,8 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
 long start_launches(const mqs_handle* H) {
   switch (H->opt.start_mode) {
     case MQS_START_SPE: {
-      const int m = H->spe_m;  // value before this step's push
-      return m == 0 ? 0 : (m > 8 ? 5 : 3);
+      const int m = H->spe_m;  // value before this step's push: g, substitutions, linear combination
+      return m == 0 ? 0 : 3;
     }
     case MQS_START_POD:
       return H->pod_m == 0 ? 0 : (H->pod_m + 7) / 8 + 2;
@@ -387,7 +403,10 @@ long start_launches(const mqs_handle* H) {
 }
 long history_launches(const mqs_handle* H) {
   switch (H->opt.start_mode) {
-    case MQS_START_SPE: return 1;
+    case MQS_START_SPE: {    // after the push: fused push + products (or push and tiles), factor
+      const int m = H->spe_m;
+      return m <= 8 ? 2 : 4 + (m > 12 ? 2 : 1);
+    }
     case MQS_START_POD: return (H->pod_m + 7) / 8 + 1;   // after the push
     case MQS_START_CSPE: return H->cspe_froze ? 1 : 0;
     default: return 0;
@@ -507,17 +526,35 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   for (int j = cl.j0; j < cl.j1; ++j)
     if (isc(1, cl.i0, j, cl.plane_k) || isc(1, cl.i1, j, cl.plane_k))
       return fail(H, MQS_ERR_ARG, "coil edges must not touch a conducting cell");
-  // right-hand side region: conductor-coupled n-edges and the coil loop
-  for (int a = 0; a < 3; ++a) {
-    H->rhs_box.lo[a] = std::max(lo[a] - 1, 0);
-    H->rhs_box.hi[a] = std::min(hi[a] + 2, n);
-  }
-  const int clo3[3] = {cl.i0, cl.j0, cl.plane_k}, chi3[3] = {cl.i1 + 1, cl.j1 + 1, cl.plane_k + 1};
-  for (int a = 0; a < 3; ++a) {
-    H->rhs_box.lo[a] = std::min(H->rhs_box.lo[a], clo3[a]);
-    H->rhs_box.hi[a] = std::max(H->rhs_box.hi[a], std::min(chi3[a], n));
-  }
   H->full = Box{{0, 0, 0}, {n, n, n}};
+  // right-hand side support: n-edges sharing a face with a c-edge (K_cn^T a_c can be
+  // nonzero only there) and the coil loop's edges; b vanishes on every other edge
+  std::vector<int> sup;
+  {
+    auto add = [&](int c, int i, int j, int k) {
+      if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) return;
+      const bool interior = (c == 0) ? (j > 0 && k > 0) : (c == 1) ? (i > 0 && k > 0) : (i > 0 && j > 0);
+      if (interior && !isc(c, i, j, k)) sup.push_back((int)(c * n3 + i + (long long)n * (j + (long long)n * k)));
+    };
+    // the four edges of the face with lower corner (i, j, k) and normal d (the stencil's flux formulas)
+    auto face = [&](int d, int i, int j, int k) {
+      if (d == 2) { add(0, i, j, k); add(1, i + 1, j, k); add(0, i, j + 1, k); add(1, i, j, k); }
+      else if (d == 0) { add(1, i, j, k); add(2, i, j + 1, k); add(1, i, j, k + 1); add(2, i, j, k); }
+      else { add(2, i, j, k); add(0, i, j, k + 1); add(2, i + 1, j, k); add(0, i, j, k); }
+    };
+    for (const int e : cidx) {
+      const int c = (int)(e / n3);
+      const long long pos = e - c * n3;
+      const int i = (int)(pos % n), j = (int)((pos / n) % n), k = (int)(pos / ((long long)n * n));
+      if (c == 0) { face(2, i, j, k); face(2, i, j - 1, k); face(1, i, j, k); face(1, i, j, k - 1); }
+      else if (c == 1) { face(2, i, j, k); face(2, i - 1, j, k); face(0, i, j, k); face(0, i, j, k - 1); }
+      else { face(0, i, j, k); face(0, i, j - 1, k); face(1, i, j, k); face(1, i - 1, j, k); }
+    }
+    for (int i = cl.i0; i < cl.i1; ++i) { add(0, i, cl.j0, cl.plane_k); add(0, i, cl.j1, cl.plane_k); }
+    for (int j = cl.j0; j < cl.j1; ++j) { add(1, cl.i1, j, cl.plane_k); add(1, cl.i0, j, cl.plane_k); }
+    std::sort(sup.begin(), sup.end());
+    sup.erase(std::unique(sup.begin(), sup.end()), sup.end());
+  }
   // device
   CK(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking));
   H->own_st = H->st;
@@ -544,6 +581,10 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->tspart, (size_t)5 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_hpart, (size_t)4 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_gpart, (size_t)spe_gblocks() * kSpeGSlots));
+  RK(dalloc(H, &H->spe_fac, 1));
+  H->nsup = (int)sup.size();
+  RK(dalloc(H, &H->sup, std::max<size_t>(sup.size(), 1)));
+  if (!sup.empty()) CK(cudaMemcpy(H->sup, sup.data(), sizeof(int) * sup.size(), cudaMemcpyHostToDevice));
   RK(dalloc(H, &H->coef, kMaxVec));
   RK(dalloc(H, &H->sigma, kMaxVec));
   RK(dalloc(H, &H->scal, 4));
@@ -756,7 +797,7 @@ int enqueue_step(mqs_handle* H, int s) {
   mark(H);
   // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
   const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->rhs_box, st));
+  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->sup, H->nsup, st));
   nl += 1;
   mark(H);
   // (a3) start vector
@@ -945,7 +986,7 @@ int mqs_adjoint(mqs_handle* H, int nsteps, double* grad_sigma_cell, mqs_adjoint_
     const double t_src = (H->opt.rhs_time == 0 ? (double)mabs : (double)(mabs - 1)) * H->dt;
     // b' = -(h/nu0) K_cn^T mu: the right-hand side stencil with the coil switched off
     const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-    RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->rhs_box, st));
+    RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->sup, H->nsup, st));
     int used_small = 0, init = 0;
     RK(start_vector(H, H->b, H->x, st, &used_small, &init));
     CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
@@ -1055,7 +1096,7 @@ int mqs_solve_an(mqs_handle* H, double* a_n, mqs_pcg_info* info) {
   // right-hand side j^m_{s,n} - K_cn^T a_c^m (eq. (anm)), scaled by h / nu0 as in a step
   const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
   CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
-  RK(launch_rhs(H->dg, H->ac_full, H->bu, drv, coil, H->rhs_box, st));
+  RK(launch_rhs(H->dg, H->ac_full, H->bu, drv, coil, H->sup, H->nsup, st));
   CK(cudaMemcpyAsync(H->xu, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
   RK(run_pcg(H, H->bu, H->xu, H->opt.tol, H->opt.maxit, st));
   if (a_n) CK(cudaMemcpyAsync(a_n, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
@@ -1145,7 +1186,7 @@ int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol,
     // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
     power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
     RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
-    RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->rhs_box, st));
+    RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->sup, H->nsup, st));
     RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
     // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
     RK(launch_cell_nu(H->dg, H->cg, H->tmp, H->xu, true, st));
@@ -1232,8 +1273,9 @@ int spe_start(mqs_handle* H, const double* b, double* x0, int* rank_used) {
   RK(mask_scale(H, H->tmp, H->bu, H->h / H->nu0, st));
   const int d = H->opt.spe_depth;
   RK(join_side(H));
-  RK(spe_x0(vs(H->spe_D, d), H->spe_m, H->bu, H->n, H->full, H->xu, H->len, H->opt.eps_lin, H->spe_hpart,
-            H->spe_gpart, H->coef, H->small, st));
+  if (H->spe_m > 0) RK(refactor_spe(H, st));
+  RK(spe_x0(vs(H->spe_D, d), H->spe_m, H->bu, H->n, H->full, nullptr, 0, H->xu, H->len, H->spe_fac, H->spe_gpart,
+            H->coef, H->small, st));
   SmallOut so{};
   CK(cudaMemcpyAsync(x0, H->xu, sizeof(double) * H->len, cudaMemcpyDeviceToHost, st));
   if (H->spe_m > 0) CK(cudaMemcpyAsync(&so, H->small, sizeof(so), cudaMemcpyDeviceToHost, st));

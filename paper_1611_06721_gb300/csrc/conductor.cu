@@ -30,26 +30,41 @@ __device__ __forceinline__ double coil_xs(const CoilGeom& c, int comp, int i, in
   return 0.0;
 }
 
-struct EpiRhs {  // b = coil_scale X_s - t on n-edges (eq. (mrhs), scaled by h/nu0)
-  double* b; long long n3; int n; double coil_scale; CoilGeom coil;
-  __device__ void prefetch(long long) {}
-  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
-    const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((long long)n * n));
-    const double t[3] = {tx, ty, tz};
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      b[e + c * n3] = (m >> c & 1u) ? fma(coil_scale, coil_xs(coil, c, i, j, k), -t[c]) : 0.0;
-  }
-};
+// face fluxes of one layout vector (zero outside the grid), grouped as in sweep_L
+__device__ __forceinline__ double flux_x(const double* a, int n, long long n3, int i, int j, int k) {
+  return (ld(a, n, n3, 1, i, j, k) - ld(a, n, n3, 2, i, j, k)) + (ld(a, n, n3, 2, i, j + 1, k) - ld(a, n, n3, 1, i, j, k + 1));
+}
+__device__ __forceinline__ double flux_y(const double* a, int n, long long n3, int i, int j, int k) {
+  return (ld(a, n, n3, 2, i, j, k) - ld(a, n, n3, 0, i, j, k)) + (ld(a, n, n3, 0, i, j, k + 1) - ld(a, n, n3, 2, i + 1, j, k));
+}
+__device__ __forceinline__ double flux_z(const double* a, int n, long long n3, int i, int j, int k) {
+  return (ld(a, n, n3, 0, i, j, k) - ld(a, n, n3, 1, i, j, k)) + (ld(a, n, n3, 1, i + 1, j, k) - ld(a, n, n3, 0, i, j + 1, k));
+}
 
-__global__ void __launch_bounds__(kBlock) rhs_kernel(Geom g, const double* ac, double* b, CoilDrive drv,
-                                                     CoilGeom coil, Box box) {
-  __shared__ SweepSmem sm;
-  // coil current i_S(t) (Sec. II, J_S = X_S i_S(t); ramp of Sec. IV) times h/nu0
+// b = coil_scale X_s - (L ac) at the listed n-edges only (the right-hand side's
+// support: edges sharing a face with a c-edge, and the coil); one edge per thread,
+// the same arithmetic and grouping as the sweep's, so b is bitwise the sweep's
+__global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac, double* b, CoilDrive drv,
+                                                       CoilGeom coil, const int* sup, int nsup) {
   const double i_t = (drv.waveform == 0) ? drv.amplitude * sin(2.0 * 3.141592653589793 * drv.freq * drv.t)
                                          : drv.amplitude * (1.0 - exp(-drv.t / drv.tau));
-  EpiRhs ep{b, g.n3, g.n, drv.scale * i_t, coil};
-  sweep_L(g, ac, box, blockIdx.x, gridDim.x, sm, ep);
+  const double cs = drv.scale * i_t;
+  const int n = g.n;
+  const long long n3 = g.n3;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsup; q += gridDim.x * blockDim.x) {
+    const int e = sup[q];
+    const int c = (int)(e / n3);
+    const int pos = (int)(e - c * n3);
+    const int i = pos % n, j = (pos / n) % n, k = pos / (n * n);
+    double t;
+    if (c == 0) t = (flux_z(ac, n, n3, i, j, k) - flux_z(ac, n, n3, i, j - 1, k)) +
+                    (flux_y(ac, n, n3, i, j, k - 1) - flux_y(ac, n, n3, i, j, k));
+    else if (c == 1) t = (flux_z(ac, n, n3, i - 1, j, k) - flux_z(ac, n, n3, i, j, k)) +
+                         (flux_x(ac, n, n3, i, j, k) - flux_x(ac, n, n3, i, j, k - 1));
+    else t = (flux_x(ac, n, n3, i, j - 1, k) - flux_x(ac, n, n3, i, j, k)) +
+             (flux_y(ac, n, n3, i, j, k) - flux_y(ac, n, n3, i - 1, j, k));
+    b[e] = fma(cs, coil_xs(coil, c, i, j, k), -t);
+  }
 }
 
 static int stencil_grid(const Box& box) {
@@ -66,9 +81,10 @@ int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, 
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
-int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, Box box,
-               cudaStream_t st) {
-  rhs_kernel<<<stencil_grid(box), kBlock, 0, st>>>(dg.g, ac_full, b, drive, coil, box);
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, const int* sup,
+               int nsup, cudaStream_t st) {
+  if (nsup <= 0) return MQS_OK;
+  rhs_list_kernel<<<(nsup + 255) / 256, 256, 0, st>>>(dg.g, ac_full, b, drive, coil, sup, nsup);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -47,13 +47,16 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
 int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);
 
-// b = s X_s - L ac on n-edges of `box` with s = scale * i_S(t) (the scaled
-// right-hand side of eq. (mrhs), scale = h/nu0); the coil is the loop
-// (plane_k, i0, j0, i1, j1); amplitude 0 gives b = -L ac.
+// the coil loop (plane_k, i0, j0, i1, j1) and its current: i_S(t) = amplitude sin(2 pi
+// freq t) (waveform 0) or amplitude (1 - exp(-t / tau)) (waveform 1), times scale
 struct CoilGeom { int k, i0, j0, i1, j1; };
 struct CoilDrive { double scale, amplitude, freq, tau, t; int waveform; };
-int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, Box box,
-               cudaStream_t st);
+// b = scale i_S(t) X_s - L ac_full (eq. (mrhs) in scaled units, scale = h/nu0;
+// amplitude 0 gives b = -L ac) at the listed layout indices only: the right-hand side's support (n-edges
+// sharing a face with a c-edge, and the coil); b keeps its values elsewhere (zero for
+// the step's b)
+int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, const int* sup,
+               int nsup, cudaStream_t st);
 
 // Conductor region kernels (eq. (acm)).
 struct CondGeom {

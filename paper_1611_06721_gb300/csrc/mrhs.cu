@@ -359,28 +359,30 @@ __device__ int chol_drop_solve(double* H, double* g, double* y, int m, double dr
   return nk_s;
 }
 
-// chol_drop_solve for m <= M (8 or 16) held in registers: lane r keeps row r of the scaled
-// matrix (compile-time indexed, every loop unrolled), column values travel by
-// shuffles.  Same pivot order, scaling, drop rule and substitutions as
-// chol_drop_solve; on this GPU every dependent FP64 step costs the FP64 unit's issue
-// time, so the register form keeps the serial chain short.  Called by warp 0.
+// chol_drop_solve for m <= M (8 or 16) held in registers, in two halves (the factor
+// needs only H, the substitutions g): lane r keeps row r of the scaled matrix
+// (compile-time indexed, every loop unrolled), column values travel by shuffles.
+// Same pivot order, scaling, drop rule and substitutions as chol_drop_solve; on this
+// GPU every dependent FP64 step costs the FP64 unit's issue time, so the register form
+// keeps the serial chain short.  Called by warp 0.  Factor: h becomes row `lane` of
+// the factor L (scaled units), inv its reciprocal pivot (0 where the column was
+// dropped), sc the row's diagonal scaling; returns the number of kept columns.
 template <int M>
-__device__ int chol_drop_solve_reg(const double* H, const double* g, double* y, int m, double drop2,
-                                   double rel_floor) {
+__device__ int chol_drop_factor_reg(const double* H, int m, double drop2, double rel_floor, double (&h)[M],
+                                    double& inv, double& sc) {
   static_assert(M <= 32, "one row per lane");
   const int lane = threadIdx.x & 31;
   const bool own = lane < m;
-  double h[M];
 #pragma unroll
   for (int c = 0; c < M; ++c) h[c] = (own && c < m) ? H[lane * m + c] : 0.0;
   double d = 0.0;
 #pragma unroll
   for (int c = 0; c < M; ++c) if (c == lane) d = h[c];
-  const double sc = (own && d > 0.0) ? rsqrt(d) : 0.0;
+  sc = (own && d > 0.0) ? rsqrt(d) : 0.0;
   const double hd00 = __shfl_sync(0xffffffffu, d, 0);
 #pragma unroll
   for (int c = 0; c < M; ++c) h[c] *= sc * __shfl_sync(0xffffffffu, sc, c);
-  double inv = 0.0;
+  inv = 0.0;
   int nk = 0;
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -399,7 +401,15 @@ __device__ int chol_drop_solve_reg(const double* H, const double* g, double* y, 
       if (lane >= k) h[k] = fma(-lij, lkj, h[k]);
     }
   }
-  // forward L z = S g
+  return nk;
+}
+
+// Substitutions with the factor of chol_drop_factor_reg: forward L z = S g, backward
+// L^T u = z, y = S u (dropped entries zero).
+template <int M>
+__device__ void chol_solve_reg(const double (&h)[M], double inv, double sc, const double* g, double* y, int m) {
+  const int lane = threadIdx.x & 31;
+  const bool own = lane < m;
   double a = own ? g[lane] * sc : 0.0, z = 0.0;
 #pragma unroll
   for (int t = 0; t < M; ++t) {
@@ -408,7 +418,7 @@ __device__ int chol_drop_solve_reg(const double* H, const double* g, double* y, 
     const double zt = __shfl_sync(0xffffffffu, z, t);
     if (lane > t) a = fma(-h[t], zt, a);
   }
-  // backward L^T u = z: row t's entries go to the lanes of the columns
+  // backward: row t's entries go to the lanes of the columns
   double b = z, u = 0.0;
 #pragma unroll
   for (int t = M - 1; t >= 0; --t) {
@@ -424,7 +434,6 @@ __device__ int chol_drop_solve_reg(const double* H, const double* g, double* y, 
     if (lane < t) b = fma(-lti, ut, b);
   }
   if (own) y[lane] = u * sc;
-  return nk;
 }
 
 // Gram row of a new snapshot: part tiles t = 0..ntile-1 hold (w, Lw) . X_q.
@@ -860,21 +869,28 @@ __global__ void __launch_bounds__(kTS, 1) spe_push_dots_kernel(MutVecSet D, MutV
                         part + (size_t)blockIdx.x * kTileSlots);
 }
 
-// g_q = D_q . b (q < m <= MAXM) over the edges of the positions in box (b is zero
-// elsewhere); float-float partials, kSpeGSlots per block.
+// g_q = D_q . b (q < m <= MAXM) over the listed layout indices (idx != nullptr) or
+// the edges of the positions in box (b is zero elsewhere); float-float partials,
+// kSpeGSlots per block.
 template <int MAXM>
 __global__ void __launch_bounds__(kTS) spe_g_kernel(VecSet D, const double* __restrict__ b, int m, int n, Box box,
-                                                    float2* gpart) {
+                                                    const int* __restrict__ idx, int nidx, float2* gpart) {
   const int bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
   const int npos = bx * by * bz;
   const long long n3 = (long long)n * n * n;
+  const int cnt = idx ? nidx : 3 * npos;
   float S[16], E[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) { S[q] = 0.f; E[q] = 0.f; }
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < 3 * npos; u += gridDim.x * blockDim.x) {
-    const int c = u / npos, r = u - c * npos;
-    const int i = box.lo[0] + r % bx, j = box.lo[1] + (r / bx) % by, k = box.lo[2] + r / (bx * by);
-    const long long e = c * n3 + i + (long long)n * (j + (long long)n * k);
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += gridDim.x * blockDim.x) {
+    long long e;
+    if (idx) {
+      e = idx[u];
+    } else {
+      const int c = u / npos, r = u - c * npos;
+      const int i = box.lo[0] + r % bx, j = box.lo[1] + (r / bx) % by, k = box.lo[2] + r / (bx * by);
+      e = c * n3 + i + (long long)n * (j + (long long)n * k);
+    }
     const double be = b[e];
     if (be != 0.0) {
       const float2 bf = ff_split(be);
@@ -932,36 +948,25 @@ __device__ __forceinline__ ffv sum_parts_ff(const float2* base, int stride, int 
   return s;
 }
 
-// SPE small system: sums the product partials (entries (q, p), q >= p, of
-// H = D^T K D in tiles of 8: tile 0 rows/columns 0-7, tiles 1 and 3 rows 8-11 and
-// 12-15 against columns 0-7, tile 2 rows/columns 8-15) and g = D^T b, then the
-// pivoted Cholesky with the drop rule (register form, warp 0) and coef = y.
-__global__ void __launch_bounds__(512) spe_solve_kernel(const float2* hpart, int nbh, const float2* gpart, int nbg,
-                                                        int m, double drop2, double* coef, SmallOut* out) {
-  __shared__ double H[kMaxSpe * kMaxSpe], g[kMaxSpe], y[kMaxSpe];
-  __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2 + kMaxSpe];
+// SPE small system, first half (needs only the table): sums the product partials
+// (entries (q, p), q >= p, of H = D^T K D in tiles of 8: tile 0 rows/columns 0-7,
+// tiles 1 and 3 rows 8-11 and 12-15 against columns 0-7, tile 2 rows/columns 8-15)
+// and factors H (pivoted Cholesky with the drop rule, register form, warp 0) into fac.
+__global__ void __launch_bounds__(512) spe_factor_kernel(const float2* hpart, int nbh, int m, double drop2,
+                                                         SpeFac* fac) {
+  __shared__ double H[kMaxSpe * kMaxSpe];
+  __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2];
   const int npair = m * (m + 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = wid; t < npair + m; t += nw) {
-    const float2* base;
-    int stride, cnt;
-    if (t < npair) {
-      int qq = 0;
-      while ((qq + 1) * (qq + 2) / 2 <= t) ++qq;
-      const int pp = t - qq * (qq + 1) / 2;
-      int tile, slot;
-      if (qq < 8) { tile = 0; slot = pp * 8 + qq; }
-      else if (pp < 8) { tile = qq < 12 ? 1 : 3; slot = pp * 8 + (qq < 12 ? qq - 8 : qq - 12); }
-      else { tile = 2; slot = (pp - 8) * 8 + (qq - 8); }
-      base = hpart + (size_t)tile * nbh * kTileSlots + slot;
-      stride = kTileSlots;
-      cnt = nbh;
-    } else {
-      base = gpart + (t - npair);
-      stride = kSpeGSlots;
-      cnt = nbg;
-    }
-    const ffv s = sum_parts_ff(base, stride, cnt);
+  for (int t = wid; t < npair; t += nw) {
+    int qq = 0;
+    while ((qq + 1) * (qq + 2) / 2 <= t) ++qq;
+    const int pp = t - qq * (qq + 1) / 2;
+    int tile, slot;
+    if (qq < 8) { tile = 0; slot = pp * 8 + qq; }
+    else if (pp < 8) { tile = qq < 12 ? 1 : 3; slot = pp * 8 + (qq < 12 ? qq - 8 : qq - 12); }
+    else { tile = 2; slot = (pp - 8) * 8 + (qq - 8); }
+    const ffv s = sum_parts_ff(hpart + (size_t)tile * nbh * kTileSlots + slot, kTileSlots, nbh);
     if (lane == 0) vals[t] = ff_to(s);
   }
   __syncthreads();
@@ -970,15 +975,55 @@ __global__ void __launch_bounds__(512) spe_solve_kernel(const float2* hpart, int
     const int pp = p < q ? p : q, qq = p < q ? q : p;
     H[s] = vals[qq * (qq + 1) / 2 + pp];
   }
-  for (int p = threadIdx.x; p < m; p += blockDim.x) g[p] = vals[npair + p];
   __syncthreads();
   if (threadIdx.x < 32) {
-    // unrolled to the table width: every unrolled FP64 step costs its issue time
-    const int nk = (m <= 8) ? chol_drop_solve_reg<8>(H, g, y, m, drop2, 1e-13)
-                            : chol_drop_solve_reg<16>(H, g, y, m, drop2, 1e-13);
+    double inv, sc;
+    int nk;
+    if (m <= 8) {
+      double h[8];
+      nk = chol_drop_factor_reg<8>(H, m, drop2, 1e-13, h, inv, sc);
+      if (lane < m)
+        for (int c = 0; c < 8; ++c) fac->L[lane * kMaxSpe + c] = h[c];
+    } else {
+      double h[16];
+      nk = chol_drop_factor_reg<16>(H, m, drop2, 1e-13, h, inv, sc);
+      if (lane < m)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) fac->L[lane * kMaxSpe + c] = h[c];
+    }
+    if (lane < m) { fac->inv[lane] = inv; fac->sc[lane] = sc; }
+    if (lane == 0) { fac->nk = nk; fac->m = m; }
+  }
+}
+
+// Second half (needs b): sums g = D^T b from its partials, the substitutions with
+// fac, coef = y.
+__global__ void __launch_bounds__(512) spe_solve_kernel(const float2* gpart, int nbg, int m, const SpeFac* fac,
+                                                        double* coef, SmallOut* out) {
+  __shared__ double g[kMaxSpe], y[kMaxSpe];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = wid; t < m; t += nw) {
+    const ffv s = sum_parts_ff(gpart + t, kSpeGSlots, nbg);
+    if (lane == 0) g[t] = ff_to(s);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool own = lane < m;
+    const double inv = own ? fac->inv[lane] : 0.0, sc = own ? fac->sc[lane] : 0.0;
+    if (m <= 8) {
+      double h[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) h[c] = own ? fac->L[lane * kMaxSpe + c] : 0.0;
+      chol_solve_reg<8>(h, inv, sc, g, y, m);
+    } else {
+      double h[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) h[c] = own ? fac->L[lane * kMaxSpe + c] : 0.0;
+      chol_solve_reg<16>(h, inv, sc, g, y, m);
+    }
     __syncwarp();
-    if (threadIdx.x < m) coef[threadIdx.x] = y[threadIdx.x];
-    if (threadIdx.x == 0) { out->rank = nk; out->info = 0.0; }
+    if (own) coef[lane] = y[lane];
+    if (lane == 0) { out->rank = fac->nk; out->info = 0.0; }
   }
 }
 
@@ -1011,12 +1056,19 @@ int spe_hblocks(long long len, int m) {
 }
 int spe_gblocks() { return ts_max_blocks(); }
 
+int spe_factor(const double* hpart, int m, long long len, double eps_lin, SpeFac* fac, cudaStream_t st) {
+  if (m <= 0 || m > kMaxSpe) return MQS_ERR_ARG;
+  spe_factor_kernel<<<1, 512, 0, st>>>(reinterpret_cast<const float2*>(hpart), spe_hblocks(len, m), m,
+                                       eps_lin * eps_lin, fac);
+  return chk();
+}
+
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
-             long long len, double* hpart, cudaStream_t st) {
+             long long len, double* hpart, double eps_lin, SpeFac* fac, cudaStream_t st) {
   float2* hp = reinterpret_cast<float2*>(hpart);
   if (m_new <= 8) {
     spe_push_dots_kernel<<<spe_hblocks(len, m_new), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len, hp);
-    return chk();
+    return spe_factor(hpart, m_new, len, eps_lin, fac, st);
   }
   diff_push_ff_kernel<16><<<ts_blocks(len) * 2, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   // Entry (q, p), q >= p, of the Galerkin matrix is D_q . (K D_p): the
@@ -1039,24 +1091,24 @@ int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const dou
   for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 8]; B2.v[p] = D.v[8 + p < m ? 8 + p : 8]; }
   if (m <= 12) dots_ff_kernel<kTri4><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
   else dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
-  return chk();
+  return spe_factor(hpart, m, len, eps_lin, fac, st);
 }
 
-int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, double* x0, long long len,
-           double eps_lin, const double* hpart, double* gpart, double* coef, SmallOut* out, cudaStream_t st) {
+int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, const int* sup, int nsup, double* x0,
+           long long len, const SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st) {
   if (m <= 0) {
     if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
     return MQS_OK;
   }
   if (m > kMaxSpe) return MQS_ERR_ARG;
   // g: about one edge per thread (most of the region's b vanishes: latency, not bandwidth)
-  const long long edges = 3LL * (bbox.hi[0] - bbox.lo[0]) * (bbox.hi[1] - bbox.lo[1]) * (bbox.hi[2] - bbox.lo[2]);
+  const long long edges =
+      sup ? nsup : 3LL * (bbox.hi[0] - bbox.lo[0]) * (bbox.hi[1] - bbox.lo[1]) * (bbox.hi[2] - bbox.lo[2]);
   const int nbg = (int)std::min<long long>(std::max<long long>((edges + kTS - 1) / kTS, 1), spe_gblocks());
   float2* gp = reinterpret_cast<float2*>(gpart);
-  if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, gp);
-  else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, gp);
-  spe_solve_kernel<<<1, 512, 0, st>>>(reinterpret_cast<const float2*>(hpart), spe_hblocks(len, m), gp, nbg, m,
-                                      eps_lin * eps_lin, coef, out);
+  if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp);
+  else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp);
+  spe_solve_kernel<<<1, 512, 0, st>>>(gp, nbg, m, fac, coef, out);
   const int nl = ts_blocks(len) * 4;
   if (m <= 8) lincomb_ff_kernel<8><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   else if (m <= 12) lincomb_ff_kernel<12><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);

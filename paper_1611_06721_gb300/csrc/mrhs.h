@@ -17,21 +17,33 @@ struct SmallOut { int rank; int pad; double info; };
 int ts_nblk();
 // partial-sum buffer needed: 5 tiles * ts_nblk() * kTileSlots doubles
 constexpr int kSpeGSlots = 16;      // g = D^T b partials per block
+// Factor of the SPE small system (device memory): rows of the scaled Cholesky factor
+// with the drop rule applied, reciprocal pivots (0 = dropped), diagonal scaling
+struct SpeFac {
+  double L[kMaxSpe * kMaxSpe];
+  double inv[kMaxSpe];
+  double sc[kMaxSpe];
+  int nk, m;
+};
 // SPE difference table D_p and images L D_p, stored as float-float pairs (8 bytes per
 // value, the buffers are FP64-sized): push the new solution w (FP64) and its image lw,
-// and form the block partials of the Galerkin products D_q . L D_p (q >= p) of the new
-// table in hpart (4 tiles * ts_nblk() * kTileSlots 8-byte slots, float-float pairs)
+// form the block partials of the Galerkin products D_q . L D_p (q >= p) of the new
+// table in hpart (4 tiles * ts_nblk() * kTileSlots 8-byte slots, float-float pairs) and
+// factor H = D^T K D into fac (drop rule at eps_lin)
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
-             long long len, double* hpart, cudaStream_t st);
+             long long len, double* hpart, double eps_lin, SpeFac* fac, cudaStream_t st);
+// the factor again from the partials in hpart (another eps_lin)
+int spe_factor(const double* hpart, int m, long long len, double eps_lin, SpeFac* fac, cudaStream_t st);
 // blocks of the product partials of a table of m columns (their layout in hpart)
 int spe_hblocks(long long len, int m);
 // gpart needed: spe_gblocks() * kSpeGSlots 8-byte slots
 int spe_gblocks();
-// x0 (FP64) = Galerkin start from the table of m columns, whose products spe_push left
-// in hpart: g = D^T b over the edges of the positions in bbox (b must vanish outside
-// it; n is the grid size), the small solve, x0 = D y
-int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, double* x0, long long len,
-           double eps_lin, const double* hpart, double* gpart, double* coef, SmallOut* out, cudaStream_t st);
+// x0 (FP64) = Galerkin start from the table of m columns factored in fac: g = D^T b
+// over the nsup layout indices sup, or (sup == nullptr) over the edges of the
+// positions in bbox (b must vanish elsewhere; n is the grid size), the
+// substitutions, x0 = D y
+int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, const int* sup, int nsup, double* x0,
+           long long len, const SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st);
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st);
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
