@@ -587,6 +587,7 @@ def run_adjoint(args):
     p = W.config_nonlinear_iron() if args.grid == 64 else W.scaled_nonlinear(args.grid)
     s = pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10))
     lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
+    s_nc = s.n_c
     s.close()
     dt = 0.9 * 2.0 / lam
     stream = torch.cuda.Stream(device=dev)
@@ -618,6 +619,19 @@ def run_adjoint(args):
     sa = fresh(1e-10)
     ms_adj, (J, gs, gI, info) = timed(lambda: sa.adjoint(args.steps))
     sa.close()
+    ck = None
+    if args.checkpoint > 0:
+        sc = fresh(1e-10)
+        ms_ck, (Jc, gsc, gIc, infoc) = timed(lambda: sc.adjoint(args.steps, args.checkpoint))
+        sc.close()
+        gf, gcf = gs.reshape(-1), gsc.reshape(-1)
+        ck = {"every": args.checkpoint, "steps_per_s": args.steps / (ms_ck * 1e-3),
+              "recompute_iterations": int(infoc.recompute_iterations),
+              "adjoint_iterations": int(infoc.adjoint_iterations),
+              "rel_diff_grad_sigma_vs_full": float(np.linalg.norm(gcf - gf) / np.linalg.norm(gf)),
+              "rel_diff_J": abs(Jc - J) / abs(J), "rel_diff_grad_amplitude": abs(gIc - gI) / abs(gI),
+              "trajectory_bytes": 8 * s_nc * ((args.steps + args.checkpoint - 1) // args.checkpoint + 1)
+                                  + 16 * s_nc * args.checkpoint}
     fd_err, cells = {}, []
     if args.fd_params > 0:
         fd_err, cells = adjoint_fd_check(args, p, fresh)
@@ -629,13 +643,16 @@ def run_adjoint(args):
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod") else "")
                                        + " (forward and adjoint solves)", "dt_s": dt,
                        "parameters": f"{int((p.sigma_cell > 0).sum())} cell conductivities + coil amplitude",
-                       "trajectory": "conductor state and rate of every step kept on the device"},
+                       "trajectory": "conductor state and rate of every step kept on the device"
+                                     f" ({16 * s_nc * args.steps} bytes)"},
             "forward_only_steps_per_s": args.steps / (ms_fwd * 1e-3),
             "reverse_cost_vs_forward": (ms_adj - ms_fwd) / ms_fwd,
             "objective_J": J, "grad_amplitude": gI,
             "pcg_iterations": {"forward": int(info.forward_iterations), "adjoint": int(info.adjoint_iterations)},
             "fd_check": {"tol": 1e-12, "cells": len(cells),
                          "cells_from": "random iron cells with |dJ/dsigma| >= 1% of the largest", **fd_err}}
+    if ck:
+        line["checkpointed"] = ck
     print(json.dumps(line), flush=True)
 
 
@@ -674,6 +691,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the adjoint gradient of the eddy-current loss and check it by central differences")
     ap.add_argument("--fd-params", type=int, default=32, help="parameters checked by central differences")
+    ap.add_argument("--checkpoint", type=int, default=25,
+                    help="adjoint mode: also run with checkpoints every this many steps (0: skip)")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

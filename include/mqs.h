@@ -377,8 +377,21 @@ typedef struct {
     double grad_amplitude;   /* dJ / d(coil amplitude)                          */
     long   forward_iterations;   /* PCG iterations of the forward steps         */
     long   adjoint_iterations;   /* PCG iterations of the adjoint solves        */
+    long   recompute_iterations; /* PCG iterations of recomputed forward steps  */
 } mqs_adjoint_info;
 int mqs_adjoint(mqs_handle* h, int nsteps, double* grad_sigma_cell, mqs_adjoint_info* info);
+
+/* mqs_adjoint with checkpoints: the forward sweep keeps a_c at every
+ * checkpoint_every-th step (8 n_c bytes each) and the record of one segment
+ * (16 n_c bytes per step of it) instead of the whole trajectory; the reverse
+ * sweep recomputes each segment's forward steps from its checkpoint, with a
+ * start-vector history that starts empty at each segment, before the segment's
+ * adjoint steps, whose history (with SPE a second table) runs on across
+ * segments.  J is the forward sweep's.  checkpoint_every = 0 (or >= nsteps) is
+ * mqs_adjoint.  The recomputed steps' PCG total goes to
+ * info->recompute_iterations.  Same end state and errors as mqs_adjoint. */
+int mqs_adjoint_ckpt(mqs_handle* h, int nsteps, int checkpoint_every, double* grad_sigma_cell,
+                     mqs_adjoint_info* info);
 
 /* mqs_loss: the forward part of mqs_adjoint alone: nsteps steps from the
  * current state and J over them (*objective, host, nullable); the handle

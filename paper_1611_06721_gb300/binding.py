@@ -30,7 +30,8 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_conductor_rate", "mqs_push_history", "spe_start", "pod_basis", "pod_start", "mqs_set_stream",
            "mqs_timing_enable", "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout",
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
-           "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_loss", "mqs_solve_an")
+           "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
+           "mqs_solve_an")
 
 
 class Grid(C.Structure):
@@ -61,7 +62,8 @@ class LayoutInfo(C.Structure):
 
 class AdjointInfo(C.Structure):
     _fields_ = [("objective", C.c_double), ("grad_amplitude", C.c_double),
-                ("forward_iterations", C.c_long), ("adjoint_iterations", C.c_long)]
+                ("forward_iterations", C.c_long), ("adjoint_iterations", C.c_long),
+                ("recompute_iterations", C.c_long)]
 
 
 class StepStats(C.Structure):
@@ -134,6 +136,7 @@ def load():
         "mqs_batch_tune": ([V, I, P(D)], I),
         "mqs_batch_destroy": ([V], I),
         "mqs_adjoint": ([H, I, P(D), P(AdjointInfo)], I),
+        "mqs_adjoint_ckpt": ([H, I, I, P(D), P(AdjointInfo)], I),
         "mqs_loss": ([H, I, P(D)], I),
         "mqs_solve_an": ([H, P(D), P(PcgInfo)], I),
     }
@@ -298,13 +301,17 @@ class Solver:
             self._check(rc)
         return rc, [st[q] for q in range(nsteps)]
 
-    def adjoint(self, nsteps):
+    def adjoint(self, nsteps, checkpoint_every=0):
         """Gradient of the eddy-current loss J over nsteps steps from the current state
-        (mqs_adjoint): returns (J, dJ/dsigma per cell as an (N, N, N) array indexed
-        [k, j, i], dJ/d amplitude, AdjointInfo)."""
+        (mqs_adjoint, or mqs_adjoint_ckpt with checkpoints every `checkpoint_every` steps
+        and recomputation in between): returns (J, dJ/dsigma per cell as an (N, N, N)
+        array indexed [k, j, i], dJ/d amplitude, AdjointInfo)."""
         g = np.zeros(self.n ** 3)
         info = AdjointInfo()
-        self._check(self.lib.mqs_adjoint(self.h, nsteps, _dp(g), C.byref(info)))
+        if checkpoint_every > 0:
+            self._check(self.lib.mqs_adjoint_ckpt(self.h, nsteps, checkpoint_every, _dp(g), C.byref(info)))
+        else:
+            self._check(self.lib.mqs_adjoint(self.h, nsteps, _dp(g), C.byref(info)))
         return info.objective, g.reshape(self.n, self.n, self.n), info.grad_amplitude, info
 
     def solve_an(self):
@@ -480,12 +487,13 @@ class Batch:
             pass
 
 
-def eddy_loss(sigma_cell, amplitude, problem, options: SolverOptions, nsteps):
+def eddy_loss(sigma_cell, amplitude, problem, options: SolverOptions, nsteps, checkpoint_every=0):
     """The eddy-current loss J over `nsteps` steps from rest as a differentiable torch
     function of the cell conductivities (tensor [N, N, N] indexed [k, j, i]) and the coil
     amplitude (0-d tensor); dt, the edge classes and the waveform come from `problem` /
     `options` and stay fixed.  The forward call runs mqs_adjoint (J and both gradients
-    at once), backward scales the stored gradients."""
+    at once; checkpoints every `checkpoint_every` steps when positive), backward scales
+    the stored gradients."""
     import torch
 
     class _EddyLoss(torch.autograd.Function):
@@ -495,7 +503,7 @@ def eddy_loss(sigma_cell, amplitude, problem, options: SolverOptions, nsteps):
             p = problem.with_(sigma_cell=sg, amplitude=float(amp))
             s = Solver.from_problem(p, options)
             try:
-                J, g, gI, _ = s.adjoint(nsteps)
+                J, g, gI, _ = s.adjoint(nsteps, checkpoint_every)
             finally:
                 s.close()
             ctx.save_for_backward(torch.from_numpy(g).to(sig.device, sig.dtype),

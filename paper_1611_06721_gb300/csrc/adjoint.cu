@@ -179,12 +179,13 @@ __global__ void adj_objective_kernel(CondGeom cg, const double* F, long long tot
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }
 
+// out[0] += scale * sum(part[0..cnt))
 __global__ void adj_sum_kernel(const double* part, int cnt, double scale, double* out) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) s += part[q];
   const double t = block_reduce(s, sh);
-  if (threadIdx.x == 0) out[0] = scale * t;
+  if (threadIdx.x == 0) out[0] += scale * t;
 }
 
 __global__ void adj_qmap_kernel(Geom g, CondGeom cg, int* qmap) {

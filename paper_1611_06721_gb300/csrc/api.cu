@@ -83,6 +83,15 @@ struct mqs_handle {
   long traj_cap = 0;
   AdjBufs adj{};
   double *adjJ = nullptr, *adj_sig = nullptr;
+  double* ckpt = nullptr;                  // checkpointed adjoint: a_c at every segment start + end state
+  long ckpt_cap = 0;
+  // second SPE history: the adjoint solves' own, while forward segments are recomputed
+  double* alt_D[kMaxSpe] = {};
+  double* alt_LD[kMaxSpe] = {};
+  int alt_m = 0, alt_cols = 0;
+  double* alt_hpart = nullptr;
+  SpeFac* alt_fac = nullptr;
+  double alt_eps = -1.0;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -169,11 +178,13 @@ __global__ void power_update_kernel(int n_c, const double* F, const double* isq,
   for (int q = threadIdx.x; q < n_c; q += blockDim.x) v[q] = F[q] * isq[q] / nz;
 }
 
+// The step's statistics; a grid-barrier timeout recorded in *derr since the call
+// began marks the step failed (the timed-out kernel did not write its result).
 __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                              mqs_step_stats* dst) {
+                              const int* derr, mqs_step_stats* dst) {
   mqs_step_stats s;
   s.iterations = pr->iterations;
-  s.status = pr->status;
+  s.status = (*derr != 0) ? *derr : pr->status;
   s.rank = use_small ? so->rank : 0;
   s.refinements = refin ? *refin : 0;
   s.relres = pr->relres;
@@ -805,8 +816,7 @@ int enqueue_step(mqs_handle* H, int s) {
   nl += start_launches(H);
   RK(start_vector(H, H->b, H->x, st, &used_small, &init));
   mark(H);
-  // (a4) PCG
-  CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
+  // (a4) PCG (the error word was cleared when the call began: a timeout stays visible)
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
   H->lx_valid = true;
   nl += 1;
@@ -820,7 +830,7 @@ int enqueue_step(mqs_handle* H, int s) {
   RK(conductor_step(H, H->x, H->dt, st));
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->dstats + s);
+                                 H->derr, H->dstats + s);
   nl += 1;
   mark(H);
   if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
@@ -867,9 +877,12 @@ int ensure_adjoint(mqs_handle* H, int nsteps) {
   return MQS_OK;
 }
 
+// Before the steps of a call: buffers, and (unless steps are already queued) a cleared
+// device error word, so a barrier timeout of any step of the call stays recorded.
 int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
+  if (keep == 0) CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
   return ensure_stats(H, nsteps, keep);
 }
 
@@ -944,6 +957,7 @@ int adjoint_forward(mqs_handle* H, int nsteps, int stats_steps) {
     if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
   }
   H->rec_a = H->rec_F = nullptr;
+  CK(cudaMemsetAsync(H->adjJ, 0, sizeof(double), H->st));
   return launch_adj_objective(H->cg, trajF, nsteps, H->dt, H->adj, H->adjJ, H->st);
 }
 
@@ -963,78 +977,190 @@ int mqs_loss(mqs_handle* H, int nsteps, double* objective) {
   return MQS_OK;
 }
 
-int mqs_adjoint(mqs_handle* H, int nsteps, double* grad_sigma_cell, mqs_adjoint_info* info) {
-  if (!H) return MQS_ERR_ARG;
-  const long m0 = H->m;
-  RK(adjoint_forward(H, nsteps, 2 * nsteps));
+namespace {
+
+// swap the active SPE history with the second one (pointers only; the side stream joins
+// first, so no pending push writes a table after it changed role)
+int swap_spe(mqs_handle* H) {
+  RK(join_side(H));
+  for (int a = 0; a < kMaxSpe; ++a) { std::swap(H->spe_D[a], H->alt_D[a]); std::swap(H->spe_LD[a], H->alt_LD[a]); }
+  std::swap(H->spe_m, H->alt_m);
+  std::swap(H->spe_hpart, H->alt_hpart);
+  std::swap(H->spe_fac, H->alt_fac);
+  std::swap(H->fac_eps, H->alt_eps);
+  return MQS_OK;
+}
+
+int ensure_spe_alt(mqs_handle* H) {
+  const int d = H->opt.spe_depth;
+  if (!H->alt_hpart) {
+    RK(dalloc(H, &H->alt_hpart, (size_t)4 * ts_nblk() * kTileSlots));
+    RK(dalloc(H, &H->alt_fac, 1));
+  }
+  for (int a = H->alt_cols; a < d; ++a) { RK(dalloc(H, &H->alt_D[a], H->len)); RK(dalloc(H, &H->alt_LD[a], H->len)); }
+  H->alt_cols = std::max(H->alt_cols, d);
+  H->alt_m = 0;
+  return MQS_OK;
+}
+
+int ensure_ckpt(mqs_handle* H, long count) {
+  if (H->ckpt_cap >= count) return MQS_OK;
+  if (H->ckpt) { CK(cudaStreamSynchronize(H->st)); dfree(H, H->ckpt); H->ckpt = nullptr; H->ckpt_cap = 0; }
+  RK(dalloc(H, &H->ckpt, (size_t)count * H->n_c));
+  H->ckpt_cap = count;
+  return MQS_OK;
+}
+
+// One step of the reverse sweep: the adjoint of step mabs (absolute) from the forward
+// record a^{m-1} (A) and F_m (F); statistics into slot.
+int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double* F, int slot) {
   cudaStream_t st = H->st;
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  RK(launch_adj_mu(H->cg, F, H->adj, H->dt, st));
+  RK(launch_scatter_c(H->cg, A, H->adj.ap_full, 1.0, st));
+  const double t_src = (H->opt.rhs_time == 0 ? (double)mabs : (double)(mabs - 1)) * H->dt;
+  // b' = -(h/nu0) K_cn^T mu: the right-hand side with the coil switched off
+  const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->sup, H->nsup, st));
+  int used_small = 0, init = 0;
+  RK(start_vector(H, H->b, H->x, st, &used_small, &init));
+  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
+  H->lx_valid = true;
+  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
+                                 H->derr, H->dstats + slot);
+  RK(history_push(H, H->x, H->lx, st));
+  RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
+  RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
+  const CoilDrive unit{1.0, 1.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  RK(launch_adj_coil(H->dg, coil, unit, H->x, H->adj, st));
+  return MQS_OK;
+}
+
+// The discrete adjoint over nsteps steps.  k <= 0 (or k >= nsteps) records the whole
+// trajectory in the forward sweep.  k > 0 keeps a_c every k steps (checkpoints) and
+// one segment's record: the reverse sweep recomputes each segment's forward steps from
+// its checkpoint (on a start-vector history of their own, cold at each segment) before
+// its adjoint steps (whose history runs on across segments).
+int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_adjoint_info* info) {
+  if (!H || nsteps < 1) return MQS_ERR_ARG;
+  if (H->n_c < 1) return fail(H, MQS_ERR_ARG, "no conducting edges");
+  const bool ck = k > 0 && k < nsteps;
+  const long m0 = H->m;
   const long nc = H->n_c;
+  const int seglen = ck ? k : nsteps, nseg = ck ? (nsteps + k - 1) / k : 1;
+  const int nstat = ck ? 3 * nsteps : 2 * nsteps;
+  cudaStream_t st = H->st;
+  RK(prepare_steps(H, nstat));
+  RK(ensure_adjoint(H, seglen));
+  if (ck) RK(ensure_ckpt(H, nseg + 1));
   double* trajA = H->traj;
-  double* trajF = H->traj + (size_t)nsteps * nc;
+  double* trajF = H->traj + (size_t)seglen * nc;
+  // forward sweep: J accumulated per recorded segment
+  CK(cudaMemsetAsync(H->adjJ, 0, sizeof(double), st));
+  for (int s = 0; s < nsteps; ++s) {
+    const int j = s % seglen;
+    if (ck && j == 0) CK(cudaMemcpyAsync(H->ckpt + (size_t)(s / k) * nc, H->ac, sizeof(double) * nc,
+                                         cudaMemcpyDeviceToDevice, st));
+    H->rec_a = trajA + (size_t)j * nc;
+    H->rec_F = trajF + (size_t)j * nc;
+    const int rc = enqueue_step(H, s);
+    if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
+    if (j == seglen - 1 || s == nsteps - 1) RK(launch_adj_objective(H->cg, trajF, j + 1, H->dt, H->adj, H->adjJ, st));
+  }
+  H->rec_a = H->rec_F = nullptr;
+  const long m_end = H->m;
+  if (ck) CK(cudaMemcpyAsync(H->ckpt + (size_t)nseg * nc, H->ac, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
   // reverse sweep; the start-vector history now follows the adjoint solves
+  const bool spe2 = ck && H->opt.start_mode == MQS_START_SPE;
+  if (spe2) { RK(ensure_spe_alt(H)); RK(swap_spe(H)); }
   clear_history(H);
   H->lx_valid = false;
   CK(cudaMemsetAsync(H->adj.lam, 0, sizeof(double) * nc, st));
   CK(cudaMemsetAsync(H->adj.gmc, 0, sizeof(double) * nc, st));
   CK(cudaMemsetAsync(H->adj.gI, 0, sizeof(double), st));
-  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
-  for (int m = nsteps; m >= 1; --m) {
-    const int s = nsteps - m;
-    RK(launch_adj_mu(H->cg, trajF + (size_t)(m - 1) * nc, H->adj, H->dt, st));
-    RK(launch_scatter_c(H->cg, trajA + (size_t)(m - 1) * nc, H->adj.ap_full, 1.0, st));
-    const long mabs = m0 + m;
-    const double t_src = (H->opt.rhs_time == 0 ? (double)mabs : (double)(mabs - 1)) * H->dt;
-    // b' = -(h/nu0) K_cn^T mu: the right-hand side stencil with the coil switched off
-    const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-    RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->sup, H->nsup, st));
-    int used_small = 0, init = 0;
-    RK(start_vector(H, H->b, H->x, st, &used_small, &init));
-    CK(cudaMemsetAsync(H->derr, 0, sizeof(int), st));
-    RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
-    H->lx_valid = true;
-    record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                   H->dstats + nsteps + s);
-    RK(history_push(H, H->x, H->lx, st));
-    RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
-    RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
-    const CoilDrive unit{1.0, 1.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-    RK(launch_adj_coil(H->dg, coil, unit, H->x, H->adj, st));
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int lo = seg * seglen, hi = std::min(lo + seglen, nsteps);
+    if (ck) {
+      // recompute steps lo+1 .. hi from the checkpoint, recording them
+      if (spe2) RK(swap_spe(H));
+      clear_history(H);
+      H->lx_valid = false;
+      CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)seg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
+      RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+      H->m = m0 + lo;
+      H->t = H->m * H->dt;
+      for (int s = lo; s < hi; ++s) {
+        H->rec_a = trajA + (size_t)(s - lo) * nc;
+        H->rec_F = trajF + (size_t)(s - lo) * nc;
+        const int rc = enqueue_step(H, 2 * nsteps + s);
+        if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
+      }
+      H->rec_a = H->rec_F = nullptr;
+      if (spe2) RK(swap_spe(H));
+      else clear_history(H);
+      H->lx_valid = false;
+    }
+    for (int m = hi; m > lo; --m)
+      RK(adjoint_reverse_step(H, m0 + m, trajA + (size_t)(m - 1 - lo) * nc, trajF + (size_t)(m - 1 - lo) * nc,
+                              nsteps + (nsteps - m)));
   }
+  if (ck) {
+    // back to the forward end state
+    CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)nseg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
+    RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+    H->m = m_end;
+    H->t = H->m * H->dt;
+  }
+  if (spe2) { RK(swap_spe(H)); H->alt_m = 0; }
   clear_history(H);            // holds adjoint solutions, not solutions of the time loop
   H->lx_valid = false;
   RK(launch_adj_sigma(H->dg, H->cg, H->condbox, H->adj, H->adj_sig, st));
-  std::vector<mqs_step_stats> hs((size_t)2 * nsteps);
+  std::vector<mqs_step_stats> hs((size_t)nstat);
   std::vector<double> sg(H->ccells);
   double J = 0.0, gI = 0.0;
   int derr = 0;
-  RK(fetch_stats(H, 2 * nsteps, hs.data(), &derr));
+  RK(fetch_stats(H, nstat, hs.data(), &derr));
   CK(cudaMemcpyAsync(&J, H->adjJ, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&gI, H->adj.gI, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(sg.data(), H->adj_sig, sizeof(double) * H->ccells, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  RK(check_stats(H, 2 * nsteps, hs.data(), derr));
+  RK(check_stats(H, nstat, hs.data(), derr));
   if (grad_sigma_cell) {
     const int n = H->n;
     std::fill(grad_sigma_cell, grad_sigma_cell + (size_t)n * n * n, 0.0);
     const int* lo = H->cg.clo;
     const int* hi = H->cg.chi;
-    for (int k = lo[2]; k < hi[2]; ++k)
+    for (int kk = lo[2]; kk < hi[2]; ++kk)
       for (int j = lo[1]; j < hi[1]; ++j)
         for (int i = lo[0]; i < hi[0]; ++i)
-          grad_sigma_cell[i + (size_t)n * (j + (size_t)n * k)] =
-              sg[(i - lo[0]) + (size_t)(hi[0] - lo[0]) * ((j - lo[1]) + (size_t)(hi[1] - lo[1]) * (k - lo[2]))];
+          grad_sigma_cell[i + (size_t)n * (j + (size_t)n * kk)] =
+              sg[(i - lo[0]) + (size_t)(hi[0] - lo[0]) * ((j - lo[1]) + (size_t)(hi[1] - lo[1]) * (kk - lo[2]))];
   }
   if (info) {
     info->objective = J;
     info->grad_amplitude = gI;
     info->forward_iterations = 0;
     info->adjoint_iterations = 0;
+    info->recompute_iterations = 0;
     for (int s = 0; s < nsteps; ++s) {
       info->forward_iterations += hs[s].iterations;
       info->adjoint_iterations += hs[nsteps + s].iterations;
+      if (ck) info->recompute_iterations += hs[2 * nsteps + s].iterations;
     }
   }
   return MQS_OK;
+}
+
+}  // namespace
+
+int mqs_adjoint(mqs_handle* H, int nsteps, double* grad_sigma_cell, mqs_adjoint_info* info) {
+  return adjoint_run(H, nsteps, 0, grad_sigma_cell, info);
+}
+
+int mqs_adjoint_ckpt(mqs_handle* H, int nsteps, int checkpoint_every, double* grad_sigma_cell,
+                     mqs_adjoint_info* info) {
+  if (!H || checkpoint_every < 0) return MQS_ERR_ARG;
+  return adjoint_run(H, nsteps, checkpoint_every, grad_sigma_cell, info);
 }
 
 int mqs_get_state(mqs_handle* H, double* a_c, size_t n_c, double* t, long* m) {

@@ -105,7 +105,7 @@ int launch_adj_lambda(const DevGeom& dg, const CondGeom& cg, const double* x, co
 // gI += -g(t) X_s . x over the coil loop (g: the unit-amplitude waveform of drv at drv.t)
 int launch_adj_coil(const DevGeom& dg, const CoilGeom& coil, const CoilDrive& drv, const double* x,
                     const AdjBufs& ab, cudaStream_t st);
-// J = dt sum over steps and c-edges of F^2 / M_c  ->  *J_dev
+// *J_dev += dt sum over the nsteps recorded steps and c-edges of F^2 / M_c
 int launch_adj_objective(const CondGeom& cg, const double* F_traj, int nsteps, double dt, const AdjBufs& ab,
                          double* J_dev, cudaStream_t st);
 // qmap from the compact c-edge list (node box lo = cg.clo, extent cg.chi - cg.clo + 1 per axis)

@@ -51,6 +51,39 @@ def test_adjoint_matches_the_oracle_with_brauer_active(pkg, mode, precision):
     s.close()
 
 
+@pytest.mark.parametrize("mode", [START_SPE, START_ZERO])
+def test_checkpointed_adjoint_matches_the_full_trajectory(pkg, mode):
+    # checkpoints every 4 steps (segments 4, 4, 4, 3) with recomputation in between
+    p = W.scaled_nonlinear(12, amplitude=2000.0)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    a0 = 3e-7 * W.random_vector(7, d.n_c)
+    steps = 15
+    ref = A.adjoint_gradient(d, dt, steps, a_c0=a0)
+    opts = pkg.SolverOptions(tol=1e-11, start_mode=mode, spe_depth=8, dt=dt)
+    full = pkg.Solver.from_problem(p, opts)
+    full.set_state(a0, 0.0, 0)
+    J0, g0, gI0, i0 = full.adjoint(steps)
+    s = pkg.Solver.from_problem(p, opts)
+    s.set_state(a0, 0.0, 0)
+    J, gs, gI, info = s.adjoint(steps, checkpoint_every=4)
+    assert J == pytest.approx(J0, rel=1e-12)                 # the same forward sweep
+    assert info.forward_iterations == i0.forward_iterations and info.recompute_iterations > 0
+    assert rel(gs.reshape(-1), g0.reshape(-1)) < 1e-8       # recomputed records agree to the solve tolerance
+    assert rel(gs.reshape(-1), ref.grad_sigma) < 1e-7
+    assert gI == pytest.approx(gI0, rel=1e-8)
+    a_c, t, m = s.get_state()
+    b_c, tb, mb = full.get_state()
+    assert m == mb == steps and t == tb and np.array_equal(a_c, b_c)
+    # a second call continues from the end state
+    J2, gs2, gI2, _ = s.adjoint(9, checkpoint_every=5)
+    J2f, gs2f, gI2f, _ = full.adjoint(9)
+    assert J2 == pytest.approx(J2f, rel=1e-12) and gI2 == pytest.approx(gI2f, rel=1e-8)
+    assert rel(gs2.reshape(-1), gs2f.reshape(-1)) < 1e-8
+    s.close()
+    full.close()
+
+
 def test_adjoint_amplitude_gradient_from_rest(pkg):
     p = W.scaled_nonlinear(12, amplitude=3000.0)
     d = O.Discretization(p)
@@ -123,3 +156,8 @@ def test_eddy_loss_autograd_function(pkg):
     assert float(J) == pytest.approx(ref.J, rel=1e-9)
     assert rel(sig.grad.numpy().reshape(-1), 3.0 * ref.grad_sigma) < 1e-7
     assert float(amp.grad) == pytest.approx(3.0 * ref.grad_amplitude, rel=1e-7)
+    sig2 = sig.detach().clone().requires_grad_(True)
+    J2 = pkg.eddy_loss(sig2, amp.detach(), p, opts, 10, checkpoint_every=3)
+    J2.backward()
+    assert float(J2) == pytest.approx(ref.J, rel=1e-9)
+    assert rel(sig2.grad.numpy().reshape(-1), ref.grad_sigma) < 1e-7
