@@ -458,7 +458,8 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
   __shared__ int order[kMaxPod], keep[kMaxPod];
   __shared__ double cs[kMaxPod / 2 + 1], sn[kMaxPod / 2 + 1];
   __shared__ int pp[kMaxPod / 2 + 1], qq[kMaxPod / 2 + 1];
-  __shared__ double offn, totn;
+  __shared__ int rotated;
+  __shared__ double floor_abs;
   __shared__ int kk;
   const int tid = threadIdx.x;
   const int me = (m + 1) & ~1;  // even size for the round-robin ordering (padding index is inert)
@@ -472,20 +473,22 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
     gv[p] = sum_part(part + (size_t)tile * nblk * kTileSlots, nblk, 64 + (p % 8));
   }
   __syncthreads();
-  // parallel-order cyclic Jacobi: me-1 rounds of me/2 disjoint rotations per sweep
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) {
-      double o = 0.0, t = 0.0;
-      for (int p = 0; p < me; ++p)
-        for (int q = 0; q < me; ++q) {
-          const double v = Mt[p * me + q] * Mt[p * me + q];
-          t += v;
-          if (p != q) o += v;
-        }
-      offn = o; totn = t;
-    }
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int p = 0; p < m; ++p) tr += fabs(Mt[p * me + p]);
+    floor_abs = 1e-15 * tr;
+  }
+  __syncthreads();
+  // parallel-order cyclic Jacobi: me-1 rounds of me/2 disjoint rotations per sweep.
+  // Threshold rule: a pair is rotated only while |a_pq| > 1e-15 sqrt(|a_pp a_qq|)
+  // (relative to its own diagonal, so small eigenvalues keep their relative accuracy)
+  // and |a_pq| > 1e-15 trace(G) (the FP64 rounding level of the matrix: eigenvalues
+  // below it are noise, and far below the POD truncation at sigma_i/sigma_1 >= eps_POD);
+  // the sweep that rotates no pair ends the iteration.  (An off-norm test against the
+  // total norm cannot be met below the rounding level and ran every sweep.)
+  for (int sweep = 0; sweep < 40 && me >= 2; ++sweep) {
+    if (tid == 0) rotated = 0;
     __syncthreads();
-    if (!(offn > 1e-32 * totn) || me < 2) break;
     for (int round = 0; round < me - 1; ++round) {
       // pairs of the round-robin schedule: index me-1 fixed, others rotate
       for (int t = tid; t < me / 2; t += blockDim.x) {
@@ -496,11 +499,12 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
         pp[t] = p; qq[t] = q;
         const double apq = Mt[p * me + q];
         double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
+        if (fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(Mt[p * me + p] * Mt[q * me + q]))) {
           const double theta = (Mt[q * me + q] - Mt[p * me + p]) / (2.0 * apq);
           const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
           c = 1.0 / sqrt(tt * tt + 1.0);
           s = tt * c;
+          rotated = 1;
         }
         cs[t] = c; sn[t] = s;
       }
@@ -527,6 +531,11 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
       }
       __syncthreads();
     }
+    // every thread reads the flag before the barrier; thread 0 resets it only after,
+    // so all threads take the same branch
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
   }
   if (tid == 0) {
     for (int p = 0; p < m; ++p) { lam[p] = Mt[p * me + p]; order[p] = p; }
