@@ -13,7 +13,11 @@ By linearity of K_n^+ on consistent right-hand sides this needs one solve per
 step:  w = K_n^+ (j^m - K_cn^T a_c^{m-1})  (which is a_n of eq. (a_n)), then
 K_S a_c + K_cn K_n^+ j = K_c a_c + K_cn w = (K(a) [a_c; w])_c.  The mode
 ``literal=True`` instead solves for j^m and for K_cn^T a_c^{m-1} separately
-(the separate right-hand sides listed after eq. (mrhs)) and subtracts.
+(the separate right-hand sides listed after eq. (mrhs)) and subtracts.  With the
+SPE start each right-hand-side type keeps its own window of past solutions
+(Sec. III: the start vector of K_n a_p = j_p projects onto solutions a_p of the
+same type), so each solve starts from its own Galerkin projection; other start
+modes solve the two types from zero.
 
 Source time level: ``rhs_time = 0`` uses j^m = i(m dt) X_s as printed in
 (acm); ``rhs_time = 1`` uses i((m-1) dt).
@@ -120,6 +124,7 @@ def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
     p = disc.problem
     a_c = np.zeros(disc.n_c) if a_c0 is None else np.array(a_c0, dtype=np.float64)
     hist = history if history is not None else []
+    hist_s, hist_c = [], []            # literal SPE: past solutions per right-hand-side type
     cspe = CspeBasis(cspe_period, spe_depth)
     depth = max(spe_depth if start_mode == START_SPE else pod_snapshots if start_mode == START_POD else 1, 1)
     jn = disc.X_s[disc.n_idx]
@@ -145,9 +150,20 @@ def run_explicit_euler(disc: Discretization, dt, n_steps, start_mode=START_ZERO,
         nb = np.linalg.norm(b)
         r0 = np.linalg.norm(b - disc.K_n @ x0) / nb if nb > 0 else 0.0
         if literal:
-            s1 = pcg_jacobi(disc.K_n, i_t * jn, None, disc.D, tol, maxit)
-            s2 = pcg_jacobi(disc.K_n, disc.K_cn.T @ a_c, None, disc.D, tol, maxit)
+            b1, b2 = i_t * jn, disc.K_cn.T @ a_c
+            x1 = x2 = None
+            rank = 0
+            if start_mode == START_SPE:
+                x1, r1 = spe_start(disc.K_n, hist_s[:spe_depth], b1, eps_lin) if hist_s else (None, 0)
+                x2, r2 = spe_start(disc.K_n, hist_c[:spe_depth], b2, eps_lin) if hist_c else (None, 0)
+                rank = r1 + r2
+            s1 = pcg_jacobi(disc.K_n, b1, x1, disc.D, tol, maxit)
+            s2 = pcg_jacobi(disc.K_n, b2, x2, disc.D, tol, maxit)
             w = s1.x - s2.x
+            if start_mode == START_SPE:
+                hist_s.insert(0, s1.x.copy())
+                hist_c.insert(0, s2.x.copy())
+                del hist_s[spe_depth:], hist_c[spe_depth:]
             rec = StepRecord(s1.iterations + s2.iterations, max(s1.relres, s2.relres), r0, rank,
                              s1.status if s1.status != STATUS_OK else s2.status)
         else:

@@ -322,6 +322,27 @@ def test_start_vectors_do_not_change_the_result():
     assert it[2] < it[0] and it[4] < it[0]
 
 
+def test_literal_spe_keeps_a_history_per_right_hand_side_type():
+    # the separate right-hand sides of eq. (mrhs), each started from the SPE projection on
+    # its own past solutions: the same a_c as the fused solve; the coil term's solutions are
+    # multiples of K_n^+ X_s, so once one is known its start vector is exact (rank 1) and
+    # costs no iteration; and the per-type starts save iterations over zero starts
+    p = W.scaled_nonlinear(8, amplitude=900.0)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 20, start_mode=0, tol=1e-12)
+    lit0 = O.run_explicit_euler(d, dt, 20, start_mode=0, tol=1e-12, literal=True)
+    lit = O.run_explicit_euler(d, dt, 20, start_mode=2, spe_depth=4, tol=1e-12, literal=True)
+    assert rel(lit.a_c, ref.a_c) < 1e-8 and rel(lit0.a_c, ref.a_c) < 1e-8
+    assert lit.iterations.sum() < lit0.iterations.sum()
+    # coil-type solve alone, with its own history, after the first step: exact start
+    jn = d.X_s[d.n_idx]
+    u = O.pcg_jacobi(d.K_n, jn, None, d.D, 1e-13).x
+    from oracle.mrhs import spe_start
+    x0, rank = spe_start(d.K_n, [0.3 * u, -0.7 * u], 2.5 * jn)
+    assert rank == 1 and rel(x0, 2.5 * u) < 1e-10
+
+
 def test_cspe_column_schedule():
     # the live column is the newest solution; the solutions of steps P, 2P, ... are frozen
     # until the basis holds `depth` columns (Sec. III cascaded SPE, Sec. IV growth below 20)
