@@ -225,7 +225,7 @@ def run_ours(args, rank, ws, local, dist):
                              spe_depth=depth if args.start in ("spe", "cspe") else 8,
                              pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
                              cspe_period=args.cspe_period,
-                             precision=args.precision)
+                             precision=args.precision, rhs_split=1 if args.rhs_split else 0)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -324,7 +324,10 @@ def run_ours(args, rank, ws, local, dist):
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
                                        + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
                        "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
-                       "pcg": "two reductions per iteration" if args.pcg_variant == 0 else "one reduction per iteration",
+                       "pcg": "one reduction per iteration" if (args.pcg_variant == 1 or args.precision == 2)
+                              else "two reductions per iteration",
+                       "right_hand_sides": "separate (conductor and coil types, one history each)" if args.rhs_split
+                                           else "fused (one solve per step)",
                        "l2": "flushed between timed steps by a 256 MiB write",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters_per_step": float(its.mean()),
@@ -677,6 +680,9 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0: FP64 PCG (default); 1: FP32 / 2: float-float inner solves in FP64 refinement "
                          "(same tolerance)")
+    ap.add_argument("--rhs-split", action="store_true",
+                    help="solve the conductor-type and coil-type right-hand sides separately, each with its own "
+                         "SPE history (the paper's separate right-hand sides)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
                     help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
     ap.add_argument("--grid", type=int, default=64,

@@ -137,6 +137,15 @@ typedef struct {
                              the newest solution is projected against them every
                              step.  mqs_push_history makes the pushed solution the
                              newest column; columns are frozen only by steps. */
+    int    rhs_split;     /* 1: solve the separate right-hand sides listed after
+                             eq. (mrhs) - the conductor type -K_cn^T a_c^{m-1} and
+                             the coil type j^m_{s,n} - one PCG solve each, each
+                             started from the SPE projection on past solutions of
+                             its own type (two difference tables), w = sum; needs
+                             start_mode ZERO or SPE; the adjoint refuses it.
+                             mqs_push_history / spe_start act on the conductor
+                             type's table.  0 (default): one fused solve (exact
+                             by linearity). */
 } mqs_options;
 
 typedef struct {

@@ -52,7 +52,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("cspe_period", C.c_int)]
+                ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -180,11 +180,12 @@ class SolverOptions:
     precision: int = 0
     inner_tol: float = 0.0
     cspe_period: int = 0
+    rhs_split: int = 0
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
-                       self.inner_tol, self.cspe_period)
+                       self.inner_tol, self.cspe_period, self.rhs_split)
 
 
 class Solver:

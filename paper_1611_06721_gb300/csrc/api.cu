@@ -89,6 +89,8 @@ struct mqs_handle {
   double* alt_D[kMaxSpe] = {};
   double* alt_LD[kMaxSpe] = {};
   int alt_m = 0, alt_cols = 0;
+  // separate right-hand sides (rhs_split): coil-type b, conductor-type solution, zero vector
+  double *bs = nullptr, *xc = nullptr, *zero_full = nullptr;
   double* alt_hpart = nullptr;
   SpeFac* alt_fac = nullptr;
   double alt_eps = -1.0;
@@ -191,6 +193,24 @@ __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_s
   s.start_relres = pr->start_relres;
   s.pod_info = (use_small == 2) ? so->info : 0.0;
   *dst = s;
+}
+
+// Adds a second solve of the same step (separate right-hand sides) to its record.
+__global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
+                                  const int* derr, mqs_step_stats* dst) {
+  mqs_step_stats s = *dst;
+  s.iterations += pr->iterations;
+  if (s.status == MQS_OK) s.status = (*derr != 0) ? *derr : pr->status;
+  s.rank += use_small ? so->rank : 0;
+  s.refinements += refin ? *refin : 0;
+  s.relres = fmax(s.relres, pr->relres);
+  s.start_relres = fmax(s.start_relres, pr->start_relres);
+  *dst = s;
+}
+
+__global__ void add_kernel(double* x, const double* y, long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
+    x[e] += y[e];
 }
 
 int mask_scale(mqs_handle* H, const double* v, double* y, double s, cudaStream_t st) {
@@ -441,6 +461,11 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (o->precision < 0 || o->precision > 2) { why = "precision must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
+  if (o->rhs_split != 0 && o->rhs_split != 1) { why = "rhs_split must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->rhs_split && o->start_mode != MQS_START_ZERO && o->start_mode != MQS_START_SPE) {
+    why = "rhs_split needs the zero or the SPE start";
+    return MQS_ERR_ARG;
+  }
   return MQS_OK;
 }
 
@@ -679,6 +704,7 @@ int ensure_pod(mqs_handle* H) {
 }
 
 void clear_history(mqs_handle* H) {
+  if (H->opt.rhs_split) H->alt_m = 0;    // the coil type's table
   H->spe_m = 0;
   H->pod_m = 0;
   H->pod_next = 0;
@@ -781,7 +807,8 @@ int mqs_set_options(mqs_handle* H, const mqs_options* o) {
   std::string why;
   if (validate_options(o, why) != MQS_OK) return fail(H, MQS_ERR_ARG, why.c_str());
   const bool reset = o->start_mode != H->opt.start_mode || o->spe_depth != H->opt.spe_depth ||
-                     o->pod_snapshots != H->opt.pod_snapshots || o->cspe_period != H->opt.cspe_period;
+                     o->pod_snapshots != H->opt.pod_snapshots || o->cspe_period != H->opt.cspe_period ||
+                     o->rhs_split != H->opt.rhs_split;
   const double dt = H->dt;
   H->opt = *o;
   H->dt = (o->dt > 0.0) ? o->dt : dt;
@@ -797,9 +824,84 @@ int mqs_reset_history(mqs_handle* H) {
 
 namespace {
 
+// swap the active SPE history with the second one (pointers only; the side stream joins
+// first, so no pending push writes a table after it changed role)
+int swap_spe(mqs_handle* H) {
+  RK(join_side(H));
+  for (int a = 0; a < kMaxSpe; ++a) { std::swap(H->spe_D[a], H->alt_D[a]); std::swap(H->spe_LD[a], H->alt_LD[a]); }
+  std::swap(H->spe_m, H->alt_m);
+  std::swap(H->spe_hpart, H->alt_hpart);
+  std::swap(H->spe_fac, H->alt_fac);
+  std::swap(H->fac_eps, H->alt_eps);
+  return MQS_OK;
+}
+
+int ensure_spe_alt(mqs_handle* H) {
+  const int d = H->opt.spe_depth;
+  if (!H->alt_hpart) {
+    RK(dalloc(H, &H->alt_hpart, (size_t)4 * ts_nblk() * kTileSlots));
+    RK(dalloc(H, &H->alt_fac, 1));
+  }
+  for (int a = H->alt_cols; a < d; ++a) { RK(dalloc(H, &H->alt_D[a], H->len)); RK(dalloc(H, &H->alt_LD[a], H->len)); }
+  H->alt_cols = std::max(H->alt_cols, d);
+  return MQS_OK;
+}
+
+// One step with the separate right-hand sides listed after eq. (mrhs): K_n w_c =
+// -(h/nu0) K_cn^T a_c^{m-1} and K_n w_s = (h/nu0) i(t) X_s, each started from the
+// SPE projection on past solutions of its own type (the handle's table holds the
+// conductor type, the second table the coil type), then w = w_c + w_s and the conductor
+// update.  Phase marks: rhs (both), start (conductor type), PCG (conductor type, then
+// the coil type's start vector and solve), history, conductor.
+int enqueue_split_step(mqs_handle* H, int s) {
+  cudaStream_t st = H->st;
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  const long m = H->m + 1;
+  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+  const int refin = H->opt.precision != 0;
+  mark(H);
+  const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  RK(launch_rhs(H->dg, H->ac_full, H->b, none, coil, H->sup, H->nsup, st));     // conductor type
+  RK(launch_rhs(H->dg, H->zero_full, H->bs, drv, coil, H->sup, H->nsup, st));   // coil type
+  mark(H);
+  int used_c = 0, init_c = 0, used_s = 0, init_s = 0;
+  const long nl_start = start_launches(H);
+  RK(start_vector(H, H->b, H->x, st, &used_c, &init_c));
+  mark(H);
+  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c));
+  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats + s);
+  RK(history_push(H, H->x, H->lx, st));
+  CK(cudaMemcpyAsync(H->xc, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
+  RK(swap_spe(H));                                    // the coil type's table (joins the push)
+  const long nl_start_s = start_launches(H);
+  RK(start_vector(H, H->bs, H->x, st, &used_s, &init_s));
+  RK(pcg_launch(H, H->bs, H->x, H->opt.tol, H->opt.maxit, st, init_s));
+  record_add_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_s, refin ? H->refin : nullptr, H->derr,
+                                     H->dstats + s);
+  mark(H);
+  RK(history_push(H, H->x, H->lx, st));
+  const long nl_hist = 2 * history_launches(H);
+  RK(swap_spe(H));                                    // back to the conductor type (joins the push)
+  add_kernel<<<H->nblk * 2, 256, 0, st>>>(H->x, H->xc, H->len);   // w = w_s + w_c
+  H->lx_valid = false;                                // lx holds L w_s only
+  mark(H);
+  RK(conductor_step(H, H->x, H->dt, st));
+  mark(H);
+  if (H->timing) {
+    H->launches += 2 + nl_start + nl_start_s + 2 + 2 + nl_hist + 1 + (H->any_brauer ? 2 : 1);
+    H->pcg_launches += 2;
+    H->tsteps += 1;
+  }
+  H->m = m;
+  H->t = m * H->dt;
+  return MQS_OK;
+}
+
 // Issues the launches of one explicit-Euler step of H on H->st (no host wait);
 // the step's statistics go to H->dstats[s].
 int enqueue_step(mqs_handle* H, int s) {
+  if (H->opt.rhs_split) return enqueue_split_step(H, s);
   cudaStream_t st = H->st;
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   const long m = H->m + 1;
@@ -877,11 +979,21 @@ int ensure_adjoint(mqs_handle* H, int nsteps) {
   return MQS_OK;
 }
 
+// buffers of the separate right-hand sides (rhs_split) and the coil type's table
+int ensure_split(mqs_handle* H) {
+  if (!H->bs) {
+    for (double** v : {&H->bs, &H->xc, &H->zero_full}) RK(dalloc(H, v, H->len));
+    for (double* v : {H->bs, H->zero_full}) CK(cudaMemsetAsync(v, 0, sizeof(double) * H->len, H->st));
+  }
+  return ensure_spe_alt(H);
+}
+
 // Before the steps of a call: buffers, and (unless steps are already queued) a cleared
 // device error word, so a barrier timeout of any step of the call stays recorded.
 int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
+  if (H->opt.rhs_split) RK(ensure_split(H));
   if (keep == 0) CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
   return ensure_stats(H, nsteps, keep);
 }
@@ -979,30 +1091,6 @@ int mqs_loss(mqs_handle* H, int nsteps, double* objective) {
 
 namespace {
 
-// swap the active SPE history with the second one (pointers only; the side stream joins
-// first, so no pending push writes a table after it changed role)
-int swap_spe(mqs_handle* H) {
-  RK(join_side(H));
-  for (int a = 0; a < kMaxSpe; ++a) { std::swap(H->spe_D[a], H->alt_D[a]); std::swap(H->spe_LD[a], H->alt_LD[a]); }
-  std::swap(H->spe_m, H->alt_m);
-  std::swap(H->spe_hpart, H->alt_hpart);
-  std::swap(H->spe_fac, H->alt_fac);
-  std::swap(H->fac_eps, H->alt_eps);
-  return MQS_OK;
-}
-
-int ensure_spe_alt(mqs_handle* H) {
-  const int d = H->opt.spe_depth;
-  if (!H->alt_hpart) {
-    RK(dalloc(H, &H->alt_hpart, (size_t)4 * ts_nblk() * kTileSlots));
-    RK(dalloc(H, &H->alt_fac, 1));
-  }
-  for (int a = H->alt_cols; a < d; ++a) { RK(dalloc(H, &H->alt_D[a], H->len)); RK(dalloc(H, &H->alt_LD[a], H->len)); }
-  H->alt_cols = std::max(H->alt_cols, d);
-  H->alt_m = 0;
-  return MQS_OK;
-}
-
 int ensure_ckpt(mqs_handle* H, long count) {
   if (H->ckpt_cap >= count) return MQS_OK;
   if (H->ckpt) { CK(cudaStreamSynchronize(H->st)); dfree(H, H->ckpt); H->ckpt = nullptr; H->ckpt_cap = 0; }
@@ -1043,6 +1131,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
 // its adjoint steps (whose history runs on across segments).
 int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_adjoint_info* info) {
   if (!H || nsteps < 1) return MQS_ERR_ARG;
+  if (H->opt.rhs_split) return fail(H, MQS_ERR_ARG, "the adjoint runs the fused solve (rhs_split = 0)");
   if (H->n_c < 1) return fail(H, MQS_ERR_ARG, "no conducting edges");
   const bool ck = k > 0 && k < nsteps;
   const long m0 = H->m;
@@ -1072,7 +1161,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
   if (ck) CK(cudaMemcpyAsync(H->ckpt + (size_t)nseg * nc, H->ac, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
   // reverse sweep; the start-vector history now follows the adjoint solves
   const bool spe2 = ck && H->opt.start_mode == MQS_START_SPE;
-  if (spe2) { RK(ensure_spe_alt(H)); RK(swap_spe(H)); }
+  if (spe2) { RK(ensure_spe_alt(H)); H->alt_m = 0; RK(swap_spe(H)); }
   clear_history(H);
   H->lx_valid = false;
   CK(cudaMemsetAsync(H->adj.lam, 0, sizeof(double) * nc, st));

@@ -240,6 +240,39 @@ def test_checkpoint_resume_is_exact(pkg):
     s.close()
 
 
+@pytest.mark.parametrize("mode", [START_SPE, START_ZERO])
+def test_separate_right_hand_sides_match_the_oracle(pkg, mode):
+    # rhs_split: the conductor type and the coil type solved separately, each with its own
+    # SPE table (eq. (mrhs) and the list after it); oracle: literal mode, same histories
+    p = W.scaled_nonlinear(16, amplitude=900.0)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    steps = 25
+    ref = O.run_explicit_euler(d, dt, steps, start_mode=mode, spe_depth=8, tol=1e-10, literal=True)
+    s = make(pkg, p, start_mode=mode, spe_depth=8, dt=dt, tol=1e-10, rhs_split=1)
+    st = s.mqs_step(steps)
+    a_c, t, m = s.get_state()
+    assert m == steps and rel(a_c, ref.a_c) < 1e-8
+    its = np.array([x.iterations for x in st])
+    assert all(x.status == 0 for x in st)
+    assert np.all(np.abs(its - ref.iterations) <= 4), (its, ref.iterations)
+    fused = make(pkg, p, start_mode=mode, spe_depth=8, dt=dt, tol=1e-10)
+    fused.mqs_step(steps)
+    b_c, _, _ = fused.get_state()
+    assert rel(a_c, b_c) < 1e-8
+    if mode == START_SPE:
+        # per-type starts beat zero starts for both types (the coil type's start is exact
+        # once one of its solutions is known)
+        zero = O.run_explicit_euler(d, dt, steps, start_mode=START_ZERO, tol=1e-10, literal=True)
+        assert its[5:].sum() < 0.5 * zero.iterations[5:].sum()
+    with pytest.raises(pkg.MqsError):
+        s.adjoint(3)                                   # the adjoint runs the fused solve
+    s.close()
+    fused.close()
+    with pytest.raises(pkg.MqsError):
+        make(pkg, p, start_mode=START_POD, dt=dt, rhs_split=1)
+
+
 def test_step_enqueue_finish_equals_step(pkg):
     # the two halves of mqs_step (with the SPE table push on the side stream) give the
     # bits of mqs_step, also with several enqueues before one finish; mqs_step while
