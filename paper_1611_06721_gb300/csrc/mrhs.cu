@@ -24,67 +24,24 @@ namespace mqs {
 
 constexpr int kTS = 256;        // threads of the tall-skinny kernels
 
-// ---- difference table push ---------------------------------------------------------
-// All old entries of an element are loaded before any is overwritten (the
-// table columns are distinct arrays, but the compiler cannot know it), two
-// elements per thread per pass as double2.
-template <int MAXD>
-__global__ void __launch_bounds__(kTS) diff_push_kernel(MutVecSet D, MutVecSet LD, const double* __restrict__ w,
-                                                       const double* __restrict__ lw, int m_old, int m_new,
-                                                       long long len) {
-  const long long half = len >> 1;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < half; e += stride) {
-    double2 od[MAXD], ol[MAXD];
-#pragma unroll
-    for (int p = 0; p < MAXD; ++p)
-      if (p < m_old) {
-        od[p] = reinterpret_cast<const double2*>(D.v[p])[e];
-        ol[p] = reinterpret_cast<const double2*>(LD.v[p])[e];
-      }
-    double2 t = reinterpret_cast<const double2*>(w)[e], tl = reinterpret_cast<const double2*>(lw)[e];
-#pragma unroll
-    for (int p = 0; p < MAXD; ++p)
-      if (p < m_new) {
-        reinterpret_cast<double2*>(D.v[p])[e] = t;
-        reinterpret_cast<double2*>(LD.v[p])[e] = tl;
-        if (p < m_old) {
-          t.x -= od[p].x; t.y -= od[p].y;
-          tl.x -= ol[p].x; tl.y -= ol[p].y;
-        }
-      }
-  }
-  if ((len & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const long long e = len - 1;
-    double od[MAXD], ol[MAXD];
-    for (int p = 0; p < m_old && p < MAXD; ++p) { od[p] = D.v[p][e]; ol[p] = LD.v[p][e]; }
-    double t = w[e], tl = lw[e];
-    for (int p = 0; p < m_new && p < MAXD; ++p) {
-      D.v[p][e] = t; LD.v[p][e] = tl;
-      if (p < m_old) { t -= od[p]; tl -= ol[p]; }
-    }
-  }
-}
-
-// ---- tiled dot products ------------------------------------------------------------
-// part[blk * kTileSlots + p*8 + q] = sum_e A_p[e] B_q[e]   (p < ma, q < mb; q >= p if diag)
+// ---- tiled dot products (FP64: POD snapshot rows, CSPE projections) -----------------
+// part[blk * kTileSlots + p*8 + q] = sum_e A_p[e] B_q[e]   (p < ma <= 2, q < mb; kRow2)
 // part[blk * kTileSlots + 64 + q]  = sum_e B_q[e] c[e]     (if c != nullptr)
-// The diagonal tile keeps only the 36 accumulators of its triangle; the c
-// products are skipped where c vanishes (the right-hand side of eq. (mrhs) is
-// zero away from the conductor and the coil).
-enum DotsMode { kTri = 0, kFull = 1, kRow2 = 2, kConly = 3, kRect4 = 4, kTri4 = 5 };
+// The c products are skipped where c vanishes (the right-hand side of eq. (mrhs) is
+// zero away from the conductor and the coil).  The float-float product kernels of the
+// SPE table use the tile modes kTri, kRect4, kTri4 (below).
+enum DotsMode { kTri = 0, kRow2 = 2, kConly = 3, kRect4 = 4, kTri4 = 5 };
 
 // 8x8 slot (p*8 + q) of the t-th upper-triangle product, in the order p, then q >= p
 __constant__ int c_tri_slot[36] = {0,  1,  2,  3,  4,  5,  6,  7,  9,  10, 11, 12, 13, 14, 15, 18, 19, 20,
                                    21, 22, 23, 27, 28, 29, 30, 31, 36, 37, 38, 39, 45, 46, 47, 54, 55, 63};
 
 template <int MODE>
-__global__ void __launch_bounds__(kTS, (MODE == kFull) ? 1 : 2) dots_kernel(VecSet A, VecSet B, const double* c,
-                                                                            int ma, int mb, long long len,
-                                                                            double* part) {
-  constexpr bool DIAG = (MODE == kTri);
-  constexpr int MA = (MODE == kRow2) ? 2 : (MODE == kConly ? 0 : 8);
-  constexpr int NACC = DIAG ? 36 : (MA * 8 > 0 ? MA * 8 : 1);
+__global__ void __launch_bounds__(kTS, 2) dots_kernel(VecSet A, VecSet B, const double* c, int ma, int mb,
+                                                     long long len, double* part) {
+  static_assert(MODE == kRow2 || MODE == kConly, "FP64 tiles: two rows, or the c products alone");
+  constexpr int MA = (MODE == kRow2) ? 2 : 0;
+  constexpr int NACC = MA * 8 > 0 ? MA * 8 : 1;
   double acc[NACC], accc[8];
 #pragma unroll
   for (int t = 0; t < NACC; ++t) acc[t] = 0.0;
@@ -101,7 +58,7 @@ __global__ void __launch_bounds__(kTS, (MODE == kFull) ? 1 : 2) dots_kernel(VecS
 #pragma unroll
     for (int p = 0; p < MA; ++p) {
 #pragma unroll
-      for (int q = (DIAG ? p : 0); q < 8; ++q, ++t)
+      for (int q = 0; q < 8; ++q, ++t)
         if (p < ma && q < mb) acc[t] = fma(a[p], b[q], acc[t]);
     }
     if (c != nullptr) {
@@ -115,64 +72,42 @@ __global__ void __launch_bounds__(kTS, (MODE == kFull) ? 1 : 2) dots_kernel(VecS
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   __shared__ double red[kTS / 32][kTileSlots];
-  if (MODE == kFull) {
-    // rare (more than 8 SPE columns): plain butterfly sums
-    int t = 0;
+  // Warp reduce-scatter over 48 slots (16 products, then the 8 c products): lane
+  // pairs exchange the half they do not keep, four times, then one butterfly step;
+  // 48 additions per lane instead of 5 per slot.
+  double v[48];
 #pragma unroll
-    for (int p = 0; p < 8; ++p)
+  for (int t = 0; t < 48; ++t) v[t] = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q, ++t) {
-        const double x = warp_sum(acc[t]);
-        if (lane == 0) red[wp][p * 8 + q] = x;
-      }
+  for (int t = 0; t < MA * 8; ++t) v[t] = acc[t];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double x = warp_sum(accc[q]);
-      if (lane == 0) red[wp][64 + q] = x;
-    }
-  } else {
-    // Warp reduce-scatter over 48 slots (the products, then the 8 c products):
-    // lane pairs exchange the half they do not keep, four times, then one
-    // butterfly step; 48 additions per lane instead of 5 per slot.
-    double v[48];
+  for (int q = 0; q < 8; ++q) v[36 + q] = accc[q];
 #pragma unroll
-    for (int t = 0; t < 48; ++t) v[t] = 0.0;
-    constexpr int NP = DIAG ? 36 : MA * 8;
+  for (int half = 24, off = 16; off >= 2; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int t = 0; t < NP; ++t) v[t] = acc[t];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[36 + q] = accc[q];
-#pragma unroll
-    for (int half = 24, off = 16; off >= 2; half >>= 1, off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int i = 0; i < half; ++i) {
-        const double keep = up ? v[i + half] : v[i];
-        const double send = up ? v[i] : v[i + half];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
-    if ((lane & 1) == 0) {
-      const int base = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) + 3 * ((lane >> 1) & 1);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int sl = base + i;
-        int dst = -1;
-        if (sl >= 36) dst = (sl < 44) ? 64 + (sl - 36) : -1;
-        else if (DIAG) dst = c_tri_slot[sl];
-        else if (sl < MA * 8) dst = sl;
-        if (dst >= 0) red[wp][dst] = v[i];
-      }
-    }
-    // slots no lane writes (lower triangle, unused rows) are zero
-    for (int t = lane; t < 64; t += 32) {
-      const int p = t / 8, q = t % 8;
-      const bool used = DIAG ? (q >= p) : (p < MA);
-      if (!used) red[wp][t] = 0.0;
+    for (int i = 0; i < half; ++i) {
+      const double keep = up ? v[i + half] : v[i];
+      const double send = up ? v[i] : v[i + half];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
+  if ((lane & 1) == 0) {
+    const int base = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) + 3 * ((lane >> 1) & 1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int sl = base + i;
+      int dst = -1;
+      if (sl >= 36) dst = (sl < 44) ? 64 + (sl - 36) : -1;
+      else if (sl < MA * 8) dst = sl;
+      if (dst >= 0) red[wp][dst] = v[i];
+    }
+  }
+  // slots no lane writes (unused rows) are zero
+  for (int t = lane; t < 64; t += 32)
+    if (t / 8 >= MA) red[wp][t] = 0.0;
   __syncthreads();
   for (int s2 = threadIdx.x; s2 < kTileSlots; s2 += blockDim.x) {
     double t = 0.0;

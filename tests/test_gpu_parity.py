@@ -240,6 +240,32 @@ def test_checkpoint_resume_is_exact(pkg):
     s.close()
 
 
+def test_boundary_touching_coil_and_conductor_match_the_oracle(pkg):
+    # the right-hand side's support list at the domain faces: a conductor slab on the x = 0
+    # face and a coil loop one node inside the y = 0 face; a loop on the face itself (its
+    # edges would be Dirichlet) is refused by both sides
+    N = 12
+    sig = np.zeros((N, N, N))
+    sig[3:7, 3:8, 0:4] = 2e6                       # [k, j, i]: cells with i = 0..3 touch x = 0
+    base = W.scaled_nonlinear(N, amplitude=800.0).with_(sigma_cell=sig, brauer_cell=(sig > 0).astype(np.uint8),
+                                                        coil_k=9, coil_i0=2, coil_i1=9, coil_j1=7)
+    with pytest.raises(ValueError):
+        O.Discretization(base.with_(coil_j0=0))
+    with pytest.raises(pkg.MqsError):
+        make(pkg, base.with_(coil_j0=0), start_mode=START_SPE, dt=1e-7)
+    p = base.with_(coil_j0=1)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 12, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    for split in (0, 1):
+        s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, rhs_split=split)
+        st = s.mqs_step(12)
+        a_c, _, m = s.get_state()
+        assert m == 12 and all(x.status == 0 for x in st)
+        assert rel(a_c, ref.a_c) < 1e-8, (split, rel(a_c, ref.a_c))
+        s.close()
+
+
 @pytest.mark.parametrize("mode", [START_SPE, START_ZERO])
 def test_separate_right_hand_sides_match_the_oracle(pkg, mode):
     # rhs_split: the conductor type and the coil type solved separately, each with its own
@@ -282,6 +308,8 @@ def test_step_enqueue_finish_equals_step(pkg):
     a = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
     b = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt)
     _, sa = a.step(12)
+    with pytest.raises(pkg.MqsError):
+        b.step_enqueue(0)
     for _ in range(2):
         b.step_enqueue(4)
         with pytest.raises(pkg.MqsError):
