@@ -208,6 +208,43 @@ def run_reference(args, rank, ws, dist):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(s, steps, warmup, stream, flush, dev):
+    """Per-step device spans of `steps` queued steps (L2 flushed before each, CUDA events
+    in stream order around each), after `warmup` untimed steps: (ms total, stats)."""
+    import torch
+    with torch.cuda.stream(stream):
+        if warmup:
+            s.step(warmup)
+        torch.cuda.synchronize(dev)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            s.step_enqueue(1)
+            ends[k].record(stream)
+        _, sts = s.step_finish(steps, allow_fail=True)
+        torch.cuda.synchronize(dev)
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), sts
+
+
+def other_arithmetic(args, p, dt, stream, flush, dev):
+    """The same workload and timing on the FP64-refined paths with FP32 and float-float
+    inner solves (same tolerance on the FP64 true residual), each from rest."""
+    import paper_1611_06721_gb300 as pkg
+    out = {}
+    for name, prec, var in (("f32+f64", 1, 1), ("ff+f64", 2, 1)):
+        so = pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8,
+                                                          dt=dt, precision=prec, pcg_variant=var))
+        so.set_stream(stream.cuda_stream)
+        ms, sts = timed_steps(so, args.steps, args.warmup, stream, flush, dev)
+        so.close()
+        out[name] = {"value": args.steps / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms / args.steps,
+                     "iters_per_step": sum(x.iterations for x in sts) / len(sts),
+                     "failed_steps": sum(1 for x in sts if x.status != 0)}
+    return out
+
+
 def run_ours(args, rank, ws, local, dist):
     import numpy as np
     import torch
@@ -342,6 +379,11 @@ def run_ours(args, rank, ws, local, dist):
             "setup": {"power_iterations": pit, "seconds": setup_s}}
     if e2e:
         line["e2e"] = e2e
+    if ws == 1 and args.alt and args.start == "spe" and depth == 8 and args.precision == 0 and not args.rhs_split:
+        line["other_arithmetic"] = {
+            "note": "same workload and timing, FP64-refined PCG with FP32 / float-float inner solves to the same "
+                    "1e-10 FP64 true residual (the headline value stays the FP64 path)",
+            **other_arithmetic(args, p, dt, stream, flush, dev)}
     if rank == 0 and ws == 1 and not args.no_cpu and args.grid == 64:
         try:
             c = run_oracle_subprocess(args.cpu_steps, args.cpu_budget)
@@ -680,6 +722,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0: FP64 PCG (default); 1: FP32 / 2: float-float inner solves in FP64 refinement "
                          "(same tolerance)")
+    ap.add_argument("--no-alt", dest="alt", action="store_false",
+                    help="skip timing the FP32- and float-float-inner paths beside the FP64 line")
     ap.add_argument("--rhs-split", action="store_true",
                     help="solve the conductor-type and coil-type right-hand sides separately, each with its own "
                          "SPE history (the paper's separate right-hand sides)")
