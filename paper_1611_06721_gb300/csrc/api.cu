@@ -54,6 +54,7 @@ struct mqs_handle {
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool side_pending = false;
+  bool in_batch = false;     // in a batch: the instances overlap each other, no side stream
   int enqueued = 0;          // steps issued by mqs_step_enqueue and not yet finished
   double* pod_X[kMaxPod] = {};
   double* pod_LX[kMaxPod] = {};
@@ -308,7 +309,7 @@ int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t 
   if (mode == MQS_START_SPE) {
     const int d = H->opt.spe_depth;
     const int mn = H->spe_m + 1 < d ? H->spe_m + 1 : d;
-    if (st == H->st) {
+    if (st == H->st && !H->in_batch) {
       // fork: the push reads w and lw, which nothing on the main stream writes
       // before the next start vector (which joins first)
       CK(cudaEventRecord(H->ev_fork, st));
@@ -1602,6 +1603,7 @@ void batch_release(mqs_batch* B) {
   for (size_t i = 0; i < B->hs.size(); ++i) {
     B->hs[i]->st = B->saved_st[i];
     B->hs[i]->nblk = B->saved_nblk[i];
+    B->hs[i]->in_batch = false;
   }
   for (cudaStream_t s : B->streams) if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : B->done) if (e) cudaEventDestroy(e);
@@ -1644,6 +1646,7 @@ int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale,
     B->saved_st.push_back(H->st);
     B->saved_nblk.push_back(H->nblk);
     H->st = B->streams[i % ns];
+    H->in_batch = true;
   }
   if (!ok) { batch_release(B); return MQS_ERR_CUDA; }
   const int rc = batch_assign(B);
