@@ -611,7 +611,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
                      &H->ac_full2, &H->r1, &H->w0, &H->w1, &H->s1})
     RK(dalloc(H, v, L));
   for (double** v : {&H->ac, &H->ac2, &H->cvec, &H->cvec2}) RK(dalloc(H, v, std::max<long>(H->n_c, 1)));
-  RK(dalloc(H, &H->part, (size_t)8 * H->nblk));
+  RK(dalloc(H, &H->part, (size_t)16 * H->nblk));    // 2 slots x 4 values x blocks (x2: two blocks per SM)
   RK(dalloc(H, &H->bar, 1));
   RK(dalloc(H, &H->derr, 1));
   RK(dalloc(H, &H->pres, 1));

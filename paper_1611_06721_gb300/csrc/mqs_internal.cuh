@@ -31,6 +31,9 @@ constexpr int kWarps = kGroups * kGroupWarps;
 constexpr int kBlock = 32 * kWarps;     // 320 threads
 constexpr int kMaxSeg = 32;             // planes per segment (x halo: one per lane)
 constexpr int kPcgBlocksPerSM = 1;      // co-resident PCG blocks per SM
+// layout length (3 n^3) from which the FP64 PCG and the FP32-inner refinement run two
+// blocks per SM (n >= 96: their vectors exceed the L2 several times)
+constexpr long long kMixedTwoBlocksLen = 3LL * 96 * 96 * 96;
 
 struct Box { int lo[3]; int hi[3]; };
 

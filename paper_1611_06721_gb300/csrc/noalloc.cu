@@ -99,7 +99,7 @@ extern "C" int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t*
   int nblk = 0;
   rc = pcg_max_blocks(&nblk);
   if (rc != MQS_OK) return rc;
-  if (nblk > kMaxBlocks) nblk = kMaxBlocks;
+  if (nblk > kMaxBlocks / 2) nblk = kMaxBlocks / 2;   // large grids launch two blocks per SM
   uint8_t* flags = reinterpret_cast<uint8_t*>(base + kOffFlags);
   unsigned* bar = reinterpret_cast<unsigned*>(base + kOffTail);
   int* err = reinterpret_cast<int*>(base + kOffTail + 1);

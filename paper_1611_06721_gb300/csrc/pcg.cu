@@ -88,7 +88,12 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
   }
 };
 
-__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_kernel(PcgArgs a) {
+// BPS co-resident blocks per SM: 2 once the vectors are far beyond L2 (there 20 warps
+// per SM hide more of the plane-sync and memory latency than 10; measured 236 -> 191 us
+// per iteration at 128^3), 1 while they stay in L2 (64^3: the extra blocks only add
+// barrier arrivals and partials).
+template <int BPS>
+__global__ void __launch_bounds__(kBlock, BPS) pcg_kernel(PcgArgs a) {
   __shared__ SweepSmem sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -392,7 +397,10 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
   a.init = init;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;
+  cudaError_t e = two ? cudaLaunchCooperativeKernel((const void*)pcg_kernel<2>, dim3(2 * nblk), dim3(kBlock), args,
+                                                    0, st)
+                      : cudaLaunchCooperativeKernel((const void*)pcg_kernel<1>, dim3(nblk), dim3(kBlock), args, 0, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
@@ -406,7 +414,7 @@ int pcg_max_blocks(int* nblk) {
   int dev = 0, nsm = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MQS_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MQS_ERR_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel, kBlock, 0) != cudaSuccess) return MQS_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<1>, kBlock, 0) != cudaSuccess) return MQS_ERR_CUDA;
   if (occ < 1) return MQS_ERR_CUDA;
   *nblk = nsm * (occ < kPcgBlocksPerSM ? occ : kPcgBlocksPerSM);  // persistent, co-resident blocks
   return MQS_OK;

@@ -111,7 +111,11 @@ struct EpiApplyDot32 {  // w = t on n-edges (0 elsewhere, FP32); sums w.r with r
   }
 };
 
-__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_mixed_kernel(MixedArgs a) {
+// BPS co-resident blocks per SM: 2 once the FP32 vectors are far beyond L2 (the inner
+// sweep is then bound by memory latency and plane syncs, and 20 warps per SM hide more
+// of both than 10; the register cap of 96 spills a little, in the FP64 passes), else 1.
+template <int BPS>
+__global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
   __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; FusedSmemBlockT<float> ff; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -437,7 +441,13 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   a.init = (init == 2) ? 2 : 0;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  // 64^3 (FP32 vectors in L2): one block per SM; from 96^3 on, two (28% faster per
+  // inner iteration at 128^3, 83.6 -> 62.8 us)
+  const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;
+  cudaError_t e = two ? cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel<2>, dim3(2 * nblk), dim3(kBlock),
+                                                    args, 0, st)
+                      : cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel<1>, dim3(nblk), dim3(kBlock),
+                                                    args, 0, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
