@@ -262,7 +262,8 @@ def run_ours(args, rank, ws, local, dist):
                              spe_depth=depth if args.start in ("spe", "cspe") else 8,
                              pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
                              cspe_period=args.cspe_period,
-                             precision=args.precision, rhs_split=1 if args.rhs_split else 0)
+                             precision=args.precision, rhs_split=1 if args.rhs_split else 0,
+                             eps_lin=args.eps_lin)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -360,7 +361,7 @@ def run_ours(args, rank, ws, local, dist):
                                      2: "float-float inner CG in FP64 refinement"}[args.precision],
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
                                        + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
-                       "tol": 1e-10, "dt_s": dt, "lambda_max": lam,
+                       "tol": 1e-10, "eps_lin": args.eps_lin, "dt_s": dt, "lambda_max": lam,
                        "pcg": "one reduction per iteration" if (args.pcg_variant == 1 or args.precision == 2)
                               else "two reductions per iteration",
                        "right_hand_sides": "separate (conductor and coil types, one history each)" if args.rhs_split
@@ -722,6 +723,9 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0: FP64 PCG (default); 1: FP32 / 2: float-float inner solves in FP64 refinement "
                          "(same tolerance)")
+    ap.add_argument("--eps-lin", type=float, default=1e-10,
+                    help="SPE drop tolerance: a column is dropped when its K-remainder falls below eps_lin x the "
+                         "newest solution's K-norm")
     ap.add_argument("--no-alt", dest="alt", action="store_false",
                     help="skip timing the FP32- and float-float-inner paths beside the FP64 line")
     ap.add_argument("--rhs-split", action="store_true",
