@@ -56,6 +56,12 @@ struct mqs_handle {
   bool side_pending = false;
   bool in_batch = false;     // in a batch: the instances overlap each other, no side stream
   int enqueued = 0;          // steps issued by mqs_step_enqueue and not yet finished
+  // b is formed at the end of a step for the next one (beside the side stream's push);
+  // it is reused only while its key still holds: the step it was formed for, the state
+  // generation (bumped when a_c changes outside a step), dt and the source time level
+  long b_for_m = -1, ac_gen = 0, b_ac_gen = -1;
+  double b_dt = 0.0;
+  int b_rhs_time = -1;
   double* pod_X[kMaxPod] = {};
   double* pod_LX[kMaxPod] = {};
   double *pod_G = nullptr, *pod_A = nullptr;
@@ -848,6 +854,23 @@ int ensure_spe_alt(mqs_handle* H) {
   return MQS_OK;
 }
 
+bool rhs_ready(const mqs_handle* H, long m) {
+  return H->b_for_m == m && H->b_ac_gen == H->ac_gen && H->b_dt == H->dt && H->b_rhs_time == H->opt.rhs_time;
+}
+
+// b of eq. (mrhs) for step m (scaled by h / nu0) from the current conductor state
+int form_rhs(mqs_handle* H, long m, cudaStream_t st) {
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
+  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->sup, H->nsup, st));
+  H->b_for_m = m;
+  H->b_ac_gen = H->ac_gen;
+  H->b_dt = H->dt;
+  H->b_rhs_time = H->opt.rhs_time;
+  return MQS_OK;
+}
+
 // One step with the separate right-hand sides listed after eq. (mrhs): K_n w_c =
 // -(h/nu0) K_cn^T a_c^{m-1} and K_n w_s = (h/nu0) i(t) X_s, each started from the
 // SPE projection on past solutions of its own type (the handle's table holds the
@@ -864,6 +887,7 @@ int enqueue_split_step(mqs_handle* H, int s) {
   const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
   const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
   RK(launch_rhs(H->dg, H->ac_full, H->b, none, coil, H->sup, H->nsup, st));     // conductor type
+  H->b_for_m = -1;
   RK(launch_rhs(H->dg, H->zero_full, H->bs, drv, coil, H->sup, H->nsup, st));   // coil type
   mark(H);
   int used_c = 0, init_c = 0, used_s = 0, init_s = 0;
@@ -904,15 +928,15 @@ int enqueue_split_step(mqs_handle* H, int s) {
 int enqueue_step(mqs_handle* H, int s) {
   if (H->opt.rhs_split) return enqueue_split_step(H, s);
   cudaStream_t st = H->st;
-  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   const long m = H->m + 1;
-  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
   long nl = 0;
   mark(H);
-  // (a2) right-hand side of eq. (mrhs), scaled by h / nu0
-  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->sup, H->nsup, st));
-  nl += 1;
+  // (a2) right-hand side of eq. (mrhs), scaled by h / nu0 (usually formed by the
+  // previous step already)
+  if (!rhs_ready(H, m)) {
+    RK(form_rhs(H, m, st));
+    nl += 1;
+  }
   mark(H);
   // (a3) start vector
   int used_small = 0, init = 0;
@@ -934,6 +958,10 @@ int enqueue_step(mqs_handle* H, int s) {
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
                                  H->derr, H->dstats + s);
+  nl += 1;
+  // the next step's right-hand side from the new state, beside the side stream's push
+  H->m = m;
+  RK(form_rhs(H, m + 1, st));
   nl += 1;
   mark(H);
   if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
@@ -1111,6 +1139,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
   // b' = -(h/nu0) K_cn^T mu: the right-hand side with the coil switched off
   const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
   RK(launch_rhs(H->dg, H->adj.mu_full, H->b, none, coil, H->sup, H->nsup, st));
+  H->b_for_m = -1;                                      // b now holds an adjoint right-hand side
   int used_small = 0, init = 0;
   RK(start_vector(H, H->b, H->x, st, &used_small, &init));
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
@@ -1177,6 +1206,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
       H->lx_valid = false;
       CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)seg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
       RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+      H->ac_gen += 1;
       H->m = m0 + lo;
       H->t = H->m * H->dt;
       for (int s = lo; s < hi; ++s) {
@@ -1198,6 +1228,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
     // back to the forward end state
     CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)nseg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
     RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+    H->ac_gen += 1;
     H->m = m_end;
     H->t = H->m * H->dt;
   }
@@ -1270,6 +1301,7 @@ int mqs_set_state(mqs_handle* H, const double* a_c, size_t n_c, double t, long m
   if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
   CK(cudaMemcpyAsync(H->ac, a_c, sizeof(double) * n_c, cudaMemcpyHostToDevice, H->st));
   RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  H->ac_gen += 1;
   CK(cudaStreamSynchronize(H->st));
   H->t = t;
   H->m = m;
@@ -1292,6 +1324,7 @@ int mqs_set_state_dev(mqs_handle* H, const double* a_c_dev, size_t n_c, void* st
   if (st != H->st) CK(cudaStreamSynchronize(st));
   CK(cudaMemcpyAsync(H->ac, a_c_dev, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, H->st));
   RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  H->ac_gen += 1;
   if (st != H->st) CK(cudaStreamSynchronize(H->st));
   return MQS_OK;
 }

@@ -240,6 +240,28 @@ def test_checkpoint_resume_is_exact(pkg):
     s.close()
 
 
+def test_dt_and_source_level_changes_between_calls(pkg):
+    # each step forms the next step's right-hand side in advance; a dt or source-level
+    # change between calls must not reuse it (oracle: the same three legs)
+    p = W.scaled_nonlinear(12, amplitude=900.0)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    r1 = O.run_explicit_euler(d, dt, 6, start_mode=START_SPE, spe_depth=8, tol=1e-11)
+    r2 = O.run_explicit_euler(d, 0.5 * dt, 5, start_mode=START_ZERO, tol=1e-11, a_c0=r1.a_c, m0=6)
+    r3 = O.run_explicit_euler(d, 0.5 * dt, 4, start_mode=START_ZERO, tol=1e-11, a_c0=r2.a_c, m0=11, rhs_time=1)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-11)
+    s.mqs_step(6)
+    s.set_dt(0.5 * dt)
+    s.mqs_step(5)
+    a2, _, _ = s.get_state()
+    assert rel(a2, r2.a_c) < 1e-8
+    s.set_options(pkg.SolverOptions(start_mode=START_SPE, spe_depth=8, dt=0.5 * dt, tol=1e-11, rhs_time=1))
+    s.mqs_step(4)
+    a3, _, m = s.get_state()
+    assert m == 15 and rel(a3, r3.a_c) < 1e-8
+    s.close()
+
+
 def test_boundary_touching_coil_and_conductor_match_the_oracle(pkg):
     # the right-hand side's support list at the domain faces: a conductor slab on the x = 0
     # face and a coil loop one node inside the y = 0 face; a loop on the face itself (its
