@@ -85,6 +85,31 @@ def test_batch_equals_separate_runs(pkg):
         s.close()
 
 
+def test_batch_with_a_two_blocks_per_sm_instance(pkg):
+    # a 96^3 instance (its PCG runs two blocks per SM) beside a small one, against the
+    # same problems stepped separately
+    probs = [W.scaled_nonlinear(96, amplitude=600.0), W.scaled_nonlinear(16, amplitude=800.0)]
+    dts = [1.0e-7, 2.0e-7]
+
+    def solvers():
+        return [pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, dt=dt, start_mode=START_SPE, spe_depth=8))
+                for p, dt in zip(probs, dts)]
+    alone = solvers()
+    for s in alone:
+        s.mqs_step(6)
+    sv = solvers()
+    batch = pkg.Batch(sv, blocks_scale=2.0)
+    _, stats = batch.step(6)
+    assert all(x.status == 0 for row in stats for x in row)
+    for a, b in zip(alone, sv):
+        x, _, _ = a.get_state()
+        y, _, m = b.get_state()
+        assert m == 6 and rel(y, x) < 1e-9
+    batch.close()
+    for s in alone + sv:
+        s.close()
+
+
 @pytest.mark.parametrize("nblk", [1, 3, 7])
 def test_pcg_on_few_persistent_blocks(pkg, nblk):
     p = W.scaled_nonlinear(24)

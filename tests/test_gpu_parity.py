@@ -79,6 +79,39 @@ def test_pcg_solve_matches_oracle(pkg, N):
     s.close()
 
 
+_REF96 = {}
+
+
+def _oracle_solve_96():
+    # one oracle solve at 96^3 (2.6 M unknowns), shared by the two precisions below
+    if not _REF96:
+        p = W.scaled_nonlinear(96)
+        d = O.Discretization(p)
+        a_c = W.random_vector(7, d.n_c) * 1e-9
+        b_n = 3.0 * d.X_s[d.n_idx] - d.K_cn.T @ a_c
+        _REF96.update(p=p, d=d, b_n=b_n, ref=O.pcg_jacobi(d.K_n, b_n, None, d.D, tol=1e-10))
+    return _REF96
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_blocks_per_sm_solve_matches_oracle_at_96(pkg, precision):
+    # from 96^3 on the FP64 PCG and the FP32-inner refinement run two blocks per SM
+    # (the kernels' second instantiation); their solve against the oracle's
+    r = _oracle_solve_96()
+    p, d, b_n, ref = r["p"], r["d"], r["b_n"], r["ref"]
+    s = make(pkg, p, precision=precision, pcg_variant=precision)
+    b_o = np.zeros(d.grid.n_edges)
+    b_o[d.n_idx] = b_n
+    x_l, info = s.pcg_solve(oracle_to_layout(96, b_o), tol=1e-10)
+    x_n = layout_to_oracle(96, x_l)[d.n_idx]
+    assert info.status == 0 and info.relres <= 1e-10
+    if precision == 0:
+        assert abs(info.iterations - ref.iterations) <= 3
+    assert rel(d.K_cn @ x_n, d.K_cn @ ref.x) < 1e-9
+    assert np.linalg.norm(b_n - d.K_n @ x_n) <= 1.01e-10 * np.linalg.norm(b_n)
+    s.close()
+
+
 def test_pcg_edge_cases(pkg):
     p = W.config_linear_block()
     d = O.Discretization(p)
