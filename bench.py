@@ -228,6 +228,26 @@ def timed_steps(s, steps, warmup, stream, flush, dev):
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), sts
 
 
+def graph_replay(args, s, stream, flush, dev, iters):
+    """The timed steps once more from the same start (rest, the same warm-up), each
+    steady-state step replayed from a CUDA graph and no event marks inside the steps:
+    the arithmetic is bitwise the same, so the iterations repeat exactly and the
+    difference in time is the cost of issuing the launches."""
+    import numpy as np
+    import torch
+    s.set_state(np.zeros(s.n_c), 0.0, 0)
+    s.reset_history()
+    with torch.cuda.stream(stream):
+        if args.warmup:
+            s.step(args.warmup)
+    g0 = s.graph_steps()
+    ms, sts = timed_steps(s, args.steps, 0, stream, flush, dev)
+    return {"ms": ms, "ms_per_step": ms / args.steps, "unit": "steps/s", "graph_steps": s.graph_steps() - g0,
+            "same_iterations": [x.iterations for x in sts] == list(iters),
+            "note": "the timed steps again from rest after the same warm-up, steady-state SPE steps "
+                    "replayed from CUDA graphs (bitwise the same results)"}
+
+
 def other_arithmetic(args, p, dt, stream, flush, dev):
     """The same workload and timing on the FP64-refined paths with FP32 and float-float
     inner solves (same tolerance on the FP64 true residual), each from rest."""
@@ -235,7 +255,8 @@ def other_arithmetic(args, p, dt, stream, flush, dev):
     out = {}
     for name, prec, var in (("f32+f64", 1, 1), ("ff+f64", 2, 1)):
         so = pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8,
-                                                          dt=dt, precision=prec, pcg_variant=var))
+                                                          dt=dt, precision=prec, pcg_variant=var,
+                                                          graph=args.graph))
         so.set_stream(stream.cuda_stream)
         ms, sts = timed_steps(so, args.steps, args.warmup, stream, flush, dev)
         so.close()
@@ -263,7 +284,7 @@ def run_ours(args, rank, ws, local, dist):
                              pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
                              cspe_period=args.cspe_period,
                              precision=args.precision, rhs_split=1 if args.rhs_split else 0,
-                             eps_lin=args.eps_lin)
+                             eps_lin=args.eps_lin, graph=args.graph)
     s = pkg.Solver.from_problem(p, opts)
     stream = torch.cuda.Stream(device=dev)
     s.set_stream(stream.cuda_stream)
@@ -308,6 +329,10 @@ def run_ours(args, rank, ws, local, dist):
         tm = s.timing_get()
         s.timing_enable(False)
         barrier(dist, dev)
+        graph = graph_replay(args, s, stream, flush, dev, iters) if args.graph and args.start == "spe" \
+            and not args.rhs_split else None
+        if graph:
+            graph["value"] = ws * args.steps / (reduce_max(graph.pop("ms"), dist, dev) * 1e-3)
     ms_max = reduce_max(ms, dist, dev)
     value = ws * args.steps / (ms_max * 1e-3)
     # end to end through the host C ABI: a_c in from pinned memory, step, a_c out
@@ -367,6 +392,7 @@ def run_ours(args, rank, ws, local, dist):
                        "right_hand_sides": "separate (conductor and coil types, one history each)" if args.rhs_split
                                            else "fused (one solve per step)",
                        "l2": "flushed between timed steps by a 256 MiB write",
+                       "step_issue": "launch by launch, event marks between the phases",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters_per_step": float(its.mean()),
             "phases_ms_per_step": {k: tm[k] / args.steps for k in ("ms_rhs", "ms_start", "ms_pcg",
@@ -380,6 +406,8 @@ def run_ours(args, rank, ws, local, dist):
             "setup": {"power_iterations": pit, "seconds": setup_s}}
     if e2e:
         line["e2e"] = e2e
+    if graph:
+        line["graph_replay"] = graph
     if ws == 1 and args.alt and args.start == "spe" and depth == 8 and args.precision == 0 and not args.rhs_split:
         line["other_arithmetic"] = {
             "note": "same workload and timing, FP64-refined PCG with FP32 / float-float inner solves to the same "
@@ -519,7 +547,7 @@ def run_batch(args):
         lam = lam_ref[p.N] * 2.0e6 / sig
         solvers.append(pkg.Solver.from_problem(p, pkg.SolverOptions(
             tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, precision=args.precision,
-            pcg_variant=args.pcg_variant, dt=0.9 * 2.0 / lam)))
+            pcg_variant=args.pcg_variant, dt=0.9 * 2.0 / lam, graph=args.graph)))
     setup_s = time.perf_counter() - t0
     batch = pkg.Batch(solvers)
     best = batch.tune(max(args.warmup // 4, 1))
@@ -529,9 +557,11 @@ def run_batch(args):
     except Exception:
         gpu_id = None
     clocks = ClockSampler(gpu_id)
+    g0 = batch.graph_steps()
     rc, stats = batch.step(args.steps, allow_fail=True)
     clk = clocks.stop()
     ms = batch.last_ms()
+    graph_steps = batch.graph_steps() - g0
     batch.close()
     its = np.array([[x.iterations for x in row] for row in stats], dtype=float)
     failed = int(sum(1 for row in stats for x in row if x.status != 0))
@@ -563,6 +593,7 @@ def run_batch(args):
                        "n_unknowns": int(sum(s.n_n for s in solvers)),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
                        "blocks_scale": best, "l2": "working set larger than L2 (no flush)",
+                       "graph_steps": graph_steps,
                        "parallelism": "1 GPU, instances on 32 streams"},
             "iters_per_step": float(its.mean()), "failed_steps": failed,
             "single_instance": {"value": seq, "unit": "instance-steps/s",
@@ -731,6 +762,8 @@ def main():
     ap.add_argument("--rhs-split", action="store_true",
                     help="solve the conductor-type and coil-type right-hand sides separately, each with its own "
                          "SPE history (the paper's separate right-hand sides)")
+    ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
+                    help="replay steady-state SPE steps from CUDA graphs (1, default) or issue every launch (0)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
                     help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
     ap.add_argument("--grid", type=int, default=64,

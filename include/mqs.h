@@ -146,6 +146,17 @@ typedef struct {
                              mqs_push_history / spe_start act on the conductor
                              type's table.  0 (default): one fused solve (exact
                              by linearity). */
+    int    graph;         /* 1: once the SPE table is full, steps are replayed
+                             from CUDA graphs (one per parity of the conductor
+                             buffers, captured on first use and again whenever
+                             the stream, block count, options, dt or a buffer
+                             the step uses changes): the same launches with the
+                             same arguments, so the results are bitwise those
+                             of 0.  Only SPE starts without rhs_split, timing or
+                             adjoint recording, and a stream that can be
+                             captured (not the legacy default stream); other
+                             steps are issued launch by launch.  0 (default):
+                             every step launch by launch. */
 } mqs_options;
 
 typedef struct {
@@ -302,6 +313,11 @@ int mqs_timing_enable(mqs_handle* h, int on);
 /* Waits for the stream and returns the accumulated times and counts. */
 int mqs_timing_get(mqs_handle* h, mqs_timing* out);
 
+/* mqs_graph_steps: steps of the handle replayed from (or captured into) a CUDA
+ * graph since setup (options.graph); mqs_batch_graph_steps: the same count of
+ * batch steps (each advances every handle of the batch).  *steps (host). */
+int mqs_graph_steps(const mqs_handle* h, long* steps);
+
 /* mqs_selftest_barrier_timeout: launches the persistent kernels' grid
  * barrier with an arrival count that can never be reached and a wait limit
  * of `polls` polls (about 100 ns each), so every block gives up, records
@@ -456,6 +472,7 @@ int mqs_batch_step(mqs_batch* b, int nsteps, mqs_step_stats* per_step);
 int mqs_batch_last_ms(mqs_batch* b, double* ms);
 int mqs_batch_tune(mqs_batch* b, int trial_steps, double* best_scale);
 int mqs_batch_destroy(mqs_batch* b);
+int mqs_batch_graph_steps(const mqs_batch* b, long* steps);
 
 #ifdef __cplusplus
 }

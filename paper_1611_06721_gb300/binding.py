@@ -31,7 +31,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_timing_enable", "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout",
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
-           "mqs_solve_an")
+           "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps")
 
 
 class Grid(C.Structure):
@@ -52,7 +52,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int)]
+                ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int), ("graph", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -139,6 +139,8 @@ def load():
         "mqs_adjoint_ckpt": ([H, I, I, P(D), P(AdjointInfo)], I),
         "mqs_loss": ([H, I, P(D)], I),
         "mqs_solve_an": ([H, P(D), P(PcgInfo)], I),
+        "mqs_graph_steps": ([H, P(C.c_long)], I),
+        "mqs_batch_graph_steps": ([V, P(C.c_long)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -181,11 +183,12 @@ class SolverOptions:
     inner_tol: float = 0.0
     cspe_period: int = 0
     rhs_split: int = 0
+    graph: int = 0
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
-                       self.inner_tol, self.cspe_period, self.rhs_split)
+                       self.inner_tol, self.cspe_period, self.rhs_split, self.graph)
 
 
 class Solver:
@@ -278,6 +281,12 @@ class Solver:
         t = Timing()
         self._check(self.lib.mqs_timing_get(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+    def graph_steps(self):
+        """Steps replayed from (or captured into) a CUDA graph since setup."""
+        v = C.c_long()
+        self._check(self.lib.mqs_graph_steps(self.h, C.byref(v)))
+        return v.value
 
     # -- time stepping -----------------------------------------------------------------
     def step(self, nsteps, allow_fail=False):
@@ -464,6 +473,12 @@ class Batch:
     def last_ms(self):
         v = C.c_double()
         self._check(self.lib.mqs_batch_last_ms(self.b, C.byref(v)))
+        return v.value
+
+    def graph_steps(self):
+        """Batch steps replayed from (or captured into) a CUDA graph."""
+        v = C.c_long()
+        self._check(self.lib.mqs_batch_graph_steps(self.b, C.byref(v)))
         return v.value
 
     def set_scale(self, blocks_scale):

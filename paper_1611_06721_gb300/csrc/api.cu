@@ -12,6 +12,22 @@
 
 using namespace mqs;
 
+namespace {
+// what a captured step depends on besides its own launches: a replay is valid only
+// while all of it is unchanged
+struct GraphKey {
+  cudaStream_t st, st2;
+  int nblk, in_batch;
+  mqs_options opt;
+  double dt;
+  const void *dstats, *ac, *spe0, *hpart, *fac;
+};
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key{};
+};
+}  // namespace
+
 struct mqs_handle {
   int n = 0;
   long long n3 = 0, len = 0;
@@ -56,6 +72,15 @@ struct mqs_handle {
   bool side_pending = false;
   bool in_batch = false;     // in a batch: the instances overlap each other, no side stream
   int enqueued = 0;          // steps issued by mqs_step_enqueue and not yet finished
+  // step counter on the device: [0] the time level of the last step issued, [1] the
+  // statistics slot of the next one; the record kernel advances both and the right-hand
+  // side reads [0], so the launches of one step do not depend on m
+  long long* dctr = nullptr;
+  // CUDA graphs of one steady-state SPE step (two: the conductor buffers alternate)
+  StepGraph graphs[2];
+  int graph_next = 0;        // the entry the next capture replaces
+  bool graph_off = false;    // a capture failed: steps are issued launch by launch
+  long graph_steps = 0;      // steps replayed from (or captured into) a graph
   // b is formed at the end of a step for the next one (beside the side stream's push);
   // it is reused only while its key still holds: the step it was formed for, the state
   // generation (bumped when a_c changes outside a step), dt and the source time level
@@ -188,9 +213,16 @@ __global__ void power_update_kernel(int n_c, const double* F, const double* isq,
 }
 
 // The step's statistics; a grid-barrier timeout recorded in *derr since the call
-// began marks the step failed (the timed-out kernel did not write its result).
+// began marks the step failed (the timed-out kernel did not write its result).  With
+// the step counter ctr the record goes to dst[ctr[1]] and the counter advances one
+// step; without it, to *dst.
 __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                              const int* derr, mqs_step_stats* dst) {
+                              const int* derr, mqs_step_stats* dst, long long* ctr) {
+  if (ctr) {
+    dst += ctr[1];
+    ctr[0] += 1;
+    ctr[1] += 1;
+  }
   mqs_step_stats s;
   s.iterations = pr->iterations;
   s.status = (*derr != 0) ? *derr : pr->status;
@@ -202,9 +234,11 @@ __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_s
   *dst = s;
 }
 
-// Adds a second solve of the same step (separate right-hand sides) to its record.
+// Adds a second solve of the same step (separate right-hand sides) to its record
+// (the one record_kernel wrote last: dst[ctr[1] - 1]).
 __global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                                  const int* derr, mqs_step_stats* dst) {
+                                  const int* derr, mqs_step_stats* dst, const long long* ctr) {
+  dst += ctr[1] - 1;
   mqs_step_stats s = *dst;
   s.iterations += pr->iterations;
   if (s.status == MQS_OK) s.status = (*derr != 0) ? *derr : pr->status;
@@ -213,6 +247,11 @@ __global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int u
   s.relres = fmax(s.relres, pr->relres);
   s.start_relres = fmax(s.start_relres, pr->start_relres);
   *dst = s;
+}
+
+__global__ void set_ctr_kernel(long long* ctr, long long m, long long slot) {
+  ctr[0] = m;
+  ctr[1] = slot;
 }
 
 __global__ void add_kernel(double* x, const double* y, long long len) {
@@ -776,6 +815,8 @@ int mqs_destroy(mqs_handle* H) {
   if (H->st2) cudaStreamDestroy(H->st2);
   if (H->ev_fork) cudaEventDestroy(H->ev_fork);
   if (H->ev_join) cudaEventDestroy(H->ev_join);
+  for (StepGraph& g : H->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   delete H;
   return MQS_OK;
 }
@@ -858,12 +899,21 @@ bool rhs_ready(const mqs_handle* H, long m) {
   return H->b_for_m == m && H->b_ac_gen == H->ac_gen && H->b_dt == H->dt && H->b_rhs_time == H->opt.rhs_time;
 }
 
-// b of eq. (mrhs) for step m (scaled by h / nu0) from the current conductor state
+// the source of the step after the last one issued, at t_m (rhs_time 0) or t_{m-1},
+// with m taken from the device step counter
+CoilDrive step_drive(const mqs_handle* H, double amplitude) {
+  CoilDrive d{H->h / H->nu0, amplitude, H->coil.freq_hz, H->coil.tau, 0.0, H->coil.waveform};
+  d.m_dev = H->dctr;
+  d.level = H->opt.rhs_time == 0 ? 1 : 0;
+  d.dt = H->dt;
+  return d;
+}
+
+// b of eq. (mrhs) for step m = (last step issued) + 1 (scaled by h / nu0) from the
+// current conductor state
 int form_rhs(mqs_handle* H, long m, cudaStream_t st) {
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
-  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
-  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-  RK(launch_rhs(H->dg, H->ac_full, H->b, drv, coil, H->sup, H->nsup, st));
+  RK(launch_rhs(H->dg, H->ac_full, H->b, step_drive(H, H->coil.amplitude), coil, H->sup, H->nsup, st));
   H->b_for_m = m;
   H->b_ac_gen = H->ac_gen;
   H->b_dt = H->dt;
@@ -877,15 +927,14 @@ int form_rhs(mqs_handle* H, long m, cudaStream_t st) {
 // conductor type, the second table the coil type), then w = w_c + w_s and the conductor
 // update.  Phase marks: rhs (both), start (conductor type), PCG (conductor type, then
 // the coil type's start vector and solve), history, conductor.
-int enqueue_split_step(mqs_handle* H, int s) {
+int enqueue_split_step(mqs_handle* H) {
   cudaStream_t st = H->st;
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   const long m = H->m + 1;
-  const double t_src = (H->opt.rhs_time == 0 ? (double)m : (double)(m - 1)) * H->dt;
   const int refin = H->opt.precision != 0;
   mark(H);
-  const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
-  const CoilDrive drv{H->h / H->nu0, H->coil.amplitude, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
+  const CoilDrive none = step_drive(H, 0.0);
+  const CoilDrive drv = step_drive(H, H->coil.amplitude);
   RK(launch_rhs(H->dg, H->ac_full, H->b, none, coil, H->sup, H->nsup, st));     // conductor type
   H->b_for_m = -1;
   RK(launch_rhs(H->dg, H->zero_full, H->bs, drv, coil, H->sup, H->nsup, st));   // coil type
@@ -895,7 +944,8 @@ int enqueue_split_step(mqs_handle* H, int s) {
   RK(start_vector(H, H->b, H->x, st, &used_c, &init_c));
   mark(H);
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c));
-  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats + s);
+  record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats,
+                                 H->dctr);
   RK(history_push(H, H->x, H->lx, st));
   CK(cudaMemcpyAsync(H->xc, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
   RK(swap_spe(H));                                    // the coil type's table (joins the push)
@@ -903,7 +953,7 @@ int enqueue_split_step(mqs_handle* H, int s) {
   RK(start_vector(H, H->bs, H->x, st, &used_s, &init_s));
   RK(pcg_launch(H, H->bs, H->x, H->opt.tol, H->opt.maxit, st, init_s));
   record_add_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_s, refin ? H->refin : nullptr, H->derr,
-                                     H->dstats + s);
+                                     H->dstats, H->dctr);
   mark(H);
   RK(history_push(H, H->x, H->lx, st));
   const long nl_hist = 2 * history_launches(H);
@@ -923,10 +973,10 @@ int enqueue_split_step(mqs_handle* H, int s) {
   return MQS_OK;
 }
 
-// Issues the launches of one explicit-Euler step of H on H->st (no host wait);
-// the step's statistics go to H->dstats[s].
-int enqueue_step(mqs_handle* H, int s) {
-  if (H->opt.rhs_split) return enqueue_split_step(H, s);
+// Issues the launches of one explicit-Euler step of H on H->st (no host wait); the
+// step's statistics go to the slot the device step counter names.
+int enqueue_step(mqs_handle* H) {
+  if (H->opt.rhs_split) return enqueue_split_step(H);
   cudaStream_t st = H->st;
   const long m = H->m + 1;
   long nl = 0;
@@ -957,7 +1007,7 @@ int enqueue_step(mqs_handle* H, int s) {
   RK(conductor_step(H, H->x, H->dt, st));
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats + s);
+                                 H->derr, H->dstats, H->dctr);
   nl += 1;
   // the next step's right-hand side from the new state, beside the side stream's push
   H->m = m;
@@ -967,6 +1017,143 @@ int enqueue_step(mqs_handle* H, int s) {
   if (H->timing) { H->launches += nl; H->pcg_launches += 1; H->tsteps += 1; }
   H->m = m;
   H->t = m * H->dt;
+  return MQS_OK;
+}
+
+// ---- CUDA graphs of the steady-state SPE step ----------------------------------------
+// Once the SPE table is full (and b was formed by the step before), a step issues the
+// same launches with the same arguments every time, except that the conductor buffers
+// alternate: one graph per buffer parity replays them.  The host-side effect of such a
+// step is fixed (after_step), so a replay updates the host state without issuing it.
+
+GraphKey graph_key(const mqs_handle* H) {
+  GraphKey k;
+  memset(&k, 0, sizeof k);
+  k.st = H->st;
+  k.st2 = H->st2;
+  k.nblk = H->nblk;
+  k.in_batch = H->in_batch ? 1 : 0;
+  memcpy(&k.opt, &H->opt, sizeof k.opt);
+  k.dt = H->dt;
+  k.dstats = H->dstats;
+  k.ac = H->ac;
+  k.spe0 = H->spe_D[0];
+  k.hpart = H->spe_hpart;
+  k.fac = H->spe_fac;
+  return k;
+}
+
+bool graph_eligible(const mqs_handle* H) {
+  return H->opt.graph && !H->graph_off && !H->timing && !H->opt.rhs_split && H->opt.start_mode == MQS_START_SPE &&
+         H->spe_m == H->opt.spe_depth && H->fac_eps == H->opt.eps_lin && !H->rec_F && !H->rec_a &&
+         rhs_ready(H, H->m + 1);
+}
+
+// the host fields a step changes
+struct StepHost {
+  long m, b_for_m, b_ac_gen;
+  double t, b_dt, fac_eps;
+  int b_rhs_time, spe_m;
+  bool lx_valid, side_pending;
+  double *ac, *ac2, *ac_full, *ac_full2;
+};
+StepHost save_host(const mqs_handle* H) {
+  return StepHost{H->m,     H->b_for_m, H->b_ac_gen, H->t,   H->b_dt,    H->fac_eps,  H->b_rhs_time,
+                  H->spe_m, H->lx_valid, H->side_pending, H->ac, H->ac2, H->ac_full, H->ac_full2};
+}
+void load_host(mqs_handle* H, const StepHost& s) {
+  H->m = s.m; H->b_for_m = s.b_for_m; H->b_ac_gen = s.b_ac_gen; H->t = s.t; H->b_dt = s.b_dt;
+  H->fac_eps = s.fac_eps; H->b_rhs_time = s.b_rhs_time; H->spe_m = s.spe_m; H->lx_valid = s.lx_valid;
+  H->side_pending = s.side_pending; H->ac = s.ac; H->ac2 = s.ac2; H->ac_full = s.ac_full;
+  H->ac_full2 = s.ac_full2;
+}
+bool same_host(const StepHost& a, const StepHost& b) {
+  return a.m == b.m && a.b_for_m == b.b_for_m && a.b_ac_gen == b.b_ac_gen && a.t == b.t && a.b_dt == b.b_dt &&
+         a.fac_eps == b.fac_eps && a.b_rhs_time == b.b_rhs_time && a.spe_m == b.spe_m &&
+         a.lx_valid == b.lx_valid && a.side_pending == b.side_pending && a.ac == b.ac && a.ac2 == b.ac2 &&
+         a.ac_full == b.ac_full && a.ac_full2 == b.ac_full2;
+}
+// what a steady-state SPE step (its side stream joined) leaves on the host
+StepHost after_step(const mqs_handle* H, const StepHost& s) {
+  StepHost r = s;
+  r.m = s.m + 1;
+  r.t = r.m * H->dt;
+  r.b_for_m = r.m + 1;
+  r.b_ac_gen = H->ac_gen;
+  r.b_dt = H->dt;
+  r.b_rhs_time = H->opt.rhs_time;
+  r.fac_eps = H->opt.eps_lin;
+  r.lx_valid = true;
+  r.side_pending = false;
+  std::swap(r.ac, r.ac2);
+  std::swap(r.ac_full, r.ac_full2);
+  return r;
+}
+
+void drop_graph(StepGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+}
+
+// Captures the launches `issue` makes on `origin` into an executable graph; false (and
+// nothing left captured) when the capture or the instantiation fails.
+extern "C++" template <class F>
+bool capture(cudaStream_t origin, F issue, cudaGraphExec_t* exec) {
+  *exec = nullptr;
+  if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const bool issued = issue();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+  bool ok = issued && ec == cudaSuccess && graph && cudaGraphInstantiate(exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+    cudaGetLastError();
+  }
+  return ok;
+}
+
+// One step of H from a graph when the step is eligible: replayed when a graph with this
+// step's key exists, else captured (launch by launch as enqueue_step issues them, the
+// side stream joined at the end) and launched.  *done is false when the step is to be
+// issued without a graph (not eligible, or the capture failed: graphs then stay off).
+int graph_step(mqs_handle* H, bool* done) {
+  *done = false;
+  if (!graph_eligible(H)) return MQS_OK;
+  RK(join_side(H));
+  const GraphKey k = graph_key(H);
+  const StepHost s0 = save_host(H);
+  for (StepGraph& g : H->graphs)
+    if (g.exec && memcmp(&g.key, &k, sizeof k) == 0) {
+      CK(cudaGraphLaunch(g.exec, H->st));
+      load_host(H, after_step(H, s0));
+      H->graph_steps += 1;
+      *done = true;
+      return MQS_OK;
+    }
+  StepGraph& g = H->graphs[H->graph_next];
+  H->graph_next ^= 1;
+  drop_graph(g);
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = capture(
+      H->st,
+      [&] { return enqueue_step(H) == MQS_OK && join_side(H) == MQS_OK && same_host(save_host(H), after_step(H, s0)); },
+      &exec);
+  if (!ok) {
+    load_host(H, s0);
+    H->graph_off = true;
+    H->err.clear();
+    return MQS_OK;
+  }
+  g.exec = exec;
+  g.key = k;
+  CK(cudaGraphLaunch(exec, H->st));
+  H->graph_steps += 1;
+  *done = true;
   return MQS_OK;
 }
 
@@ -1023,8 +1210,13 @@ int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (H->opt.start_mode == MQS_START_POD || H->opt.start_mode == MQS_START_CSPE) RK(ensure_pod(H));
   if (H->opt.rhs_split) RK(ensure_split(H));
+  if (H->opt.precision != 0) RK(ensure_mixed(H));
+  if (!H->dctr) RK(dalloc(H, &H->dctr, 2));
   if (keep == 0) CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
-  return ensure_stats(H, nsteps, keep);
+  RK(ensure_stats(H, nsteps, keep));
+  set_ctr_kernel<<<1, 1, 0, H->st>>>(H->dctr, H->m, keep);
+  CK(cudaGetLastError());
+  return MQS_OK;
 }
 
 // Copies the step statistics of the last nsteps steps into hs (async on H->st).
@@ -1061,7 +1253,11 @@ int mqs_step_enqueue(mqs_handle* H, int nsteps) {
   if (nsteps > (1 << 30) - H->enqueued) return fail(H, MQS_ERR_ARG, "too many steps enqueued");
   const int base = H->enqueued;
   int rc = prepare_steps(H, base + nsteps, base);
-  for (int s = 0; s < nsteps && rc == MQS_OK; ++s) rc = enqueue_step(H, base + s);
+  for (int s = 0; s < nsteps && rc == MQS_OK; ++s) {
+    bool done = false;
+    rc = graph_step(H, &done);
+    if (rc == MQS_OK && !done) rc = enqueue_step(H);
+  }
   const int rj = join_side(H);          // also after a failed launch: nothing left running beside
   if (rc != MQS_OK) { H->enqueued = 0; return rc; }
   if (rj != MQS_OK) { H->enqueued = 0; return rj; }
@@ -1094,7 +1290,7 @@ int adjoint_forward(mqs_handle* H, int nsteps, int stats_steps) {
   for (int s = 0; s < nsteps; ++s) {
     H->rec_a = trajA + (size_t)s * nc;
     H->rec_F = trajF + (size_t)s * nc;
-    const int rc = enqueue_step(H, s);
+    const int rc = enqueue_step(H);
     if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
   }
   H->rec_a = H->rec_F = nullptr;
@@ -1145,7 +1341,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
   H->lx_valid = true;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats + slot);
+                                 H->derr, H->dstats + slot, nullptr);
   RK(history_push(H, H->x, H->lx, st));
   RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
   RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
@@ -1182,7 +1378,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
                                          cudaMemcpyDeviceToDevice, st));
     H->rec_a = trajA + (size_t)j * nc;
     H->rec_F = trajF + (size_t)j * nc;
-    const int rc = enqueue_step(H, s);
+    const int rc = enqueue_step(H);
     if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
     if (j == seglen - 1 || s == nsteps - 1) RK(launch_adj_objective(H->cg, trajF, j + 1, H->dt, H->adj, H->adjJ, st));
   }
@@ -1209,10 +1405,11 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
       H->ac_gen += 1;
       H->m = m0 + lo;
       H->t = H->m * H->dt;
+      set_ctr_kernel<<<1, 1, 0, st>>>(H->dctr, H->m, 2 * nsteps + lo);
       for (int s = lo; s < hi; ++s) {
         H->rec_a = trajA + (size_t)(s - lo) * nc;
         H->rec_F = trajF + (size_t)(s - lo) * nc;
-        const int rc = enqueue_step(H, 2 * nsteps + s);
+        const int rc = enqueue_step(H);
         if (rc != MQS_OK) { H->rec_a = H->rec_F = nullptr; return rc; }
       }
       H->rec_a = H->rec_F = nullptr;
@@ -1473,6 +1670,12 @@ int mqs_timing_enable(mqs_handle* H, int on) {
   return MQS_OK;
 }
 
+int mqs_graph_steps(const mqs_handle* H, long* steps) {
+  if (!H || !steps) return MQS_ERR_ARG;
+  *steps = H->graph_steps;
+  return MQS_OK;
+}
+
 int mqs_timing_get(mqs_handle* H, mqs_timing* out) {
   if (!H || !out) return MQS_ERR_ARG;
   CK(cudaStreamSynchronize(H->st));
@@ -1603,15 +1806,28 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
 // (CUDA_DEVICE_MAX_CONNECTIONS), so more streams would only alias
 constexpr int kBatchStreams = 32;
 
+// a graph of kBatchGraphSteps steps of every handle of a batch, issued step-major as
+// the launch-by-launch path does (each handle's launches on its own batch stream, so
+// the handles drift apart inside the graph and meet only at its end)
+constexpr int kBatchGraphSteps = 8;
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<GraphKey> keys;
+};
+
 struct mqs_batch {
   std::vector<mqs_handle*> hs;
   std::vector<cudaStream_t> streams, saved_st;
   std::vector<int> saved_nblk;
   std::vector<cudaEvent_t> done;
   cudaStream_t master = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evf = nullptr;
   double scale = 2.0;
   float last_ms = 0.f;
+  BatchGraph graphs[2];
+  int graph_next = 0;
+  bool graph_off = false;
+  long graph_steps = 0;     // batch steps replayed from (or captured into) a graph
 };
 
 namespace {
@@ -1638,12 +1854,93 @@ void batch_release(mqs_batch* B) {
     B->hs[i]->nblk = B->saved_nblk[i];
     B->hs[i]->in_batch = false;
   }
+  if (B->master) cudaStreamSynchronize(B->master);
+  for (BatchGraph& g : B->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (cudaStream_t s : B->streams) if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : B->done) if (e) cudaEventDestroy(e);
   if (B->ev0) cudaEventDestroy(B->ev0);
   if (B->ev1) cudaEventDestroy(B->ev1);
+  if (B->evf) cudaEventDestroy(B->evf);
   if (B->master) cudaStreamDestroy(B->master);
   delete B;
+}
+
+// the batch streams' work so far joins the master stream / the master's joins the streams
+int batch_to_master(mqs_batch* B) {
+  for (size_t i = 0; i < B->streams.size(); ++i) {
+    if (cudaEventRecord(B->done[i], B->streams[i]) != cudaSuccess) return MQS_ERR_CUDA;
+    if (cudaStreamWaitEvent(B->master, B->done[i], 0) != cudaSuccess) return MQS_ERR_CUDA;
+  }
+  return MQS_OK;
+}
+int master_to_batch(mqs_batch* B) {
+  if (cudaEventRecord(B->evf, B->master) != cudaSuccess) return MQS_ERR_CUDA;
+  for (cudaStream_t s : B->streams)
+    if (cudaStreamWaitEvent(s, B->evf, 0) != cudaSuccess) return MQS_ERR_CUDA;
+  return MQS_OK;
+}
+
+// kBatchGraphSteps steps of every handle from a graph on the master stream, when every
+// handle is eligible (see graph_step); *done false otherwise.  *on_master tracks where
+// the batch's latest work is.
+int batch_graph_steps(mqs_batch* B, bool* on_master, bool* done) {
+  *done = false;
+  if (B->graph_off) return MQS_OK;
+  for (mqs_handle* H : B->hs)
+    if (!graph_eligible(H)) return MQS_OK;
+  const size_t cnt = B->hs.size();
+  std::vector<GraphKey> keys(cnt);
+  std::vector<StepHost> s0(cnt), s1(cnt);
+  for (size_t i = 0; i < cnt; ++i) {
+    keys[i] = graph_key(B->hs[i]);
+    s0[i] = save_host(B->hs[i]);
+    s1[i] = s0[i];
+    for (int k = 0; k < kBatchGraphSteps; ++k) s1[i] = after_step(B->hs[i], s1[i]);
+  }
+  if (!*on_master) {
+    const int r = batch_to_master(B);
+    if (r != MQS_OK) return r;
+    *on_master = true;
+  }
+  for (BatchGraph& g : B->graphs)
+    if (g.exec && g.keys.size() == cnt && memcmp(g.keys.data(), keys.data(), sizeof(GraphKey) * cnt) == 0) {
+      if (cudaGraphLaunch(g.exec, B->master) != cudaSuccess) return MQS_ERR_CUDA;
+      for (size_t i = 0; i < cnt; ++i) load_host(B->hs[i], s1[i]);
+      B->graph_steps += kBatchGraphSteps;
+      *done = true;
+      return MQS_OK;
+    }
+  BatchGraph& g = B->graphs[B->graph_next];
+  B->graph_next ^= 1;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = capture(
+      B->master,
+      [&] {
+        if (master_to_batch(B) != MQS_OK) return false;
+        bool good = true;
+        for (int k = 0; k < kBatchGraphSteps && good; ++k)
+          for (size_t i = 0; i < cnt && good; ++i) good = enqueue_step(B->hs[i]) == MQS_OK;
+        for (size_t i = 0; i < cnt; ++i) good = good && same_host(save_host(B->hs[i]), s1[i]);
+        return batch_to_master(B) == MQS_OK && good;   // joined also after a failure
+      },
+      &exec);
+  if (!ok) {
+    for (size_t i = 0; i < cnt; ++i) {
+      load_host(B->hs[i], s0[i]);
+      B->hs[i]->err.clear();
+    }
+    B->graph_off = true;
+    return MQS_OK;
+  }
+  g.exec = exec;
+  g.keys = keys;
+  if (cudaGraphLaunch(exec, B->master) != cudaSuccess) return MQS_ERR_CUDA;
+  B->graph_steps += kBatchGraphSteps;
+  *done = true;
+  return MQS_OK;
 }
 
 }  // namespace
@@ -1661,7 +1958,8 @@ int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale,
   if (!B) return MQS_ERR_OOM;
   B->scale = blocks_scale > 0.0 ? blocks_scale : 2.0;
   bool ok = cudaStreamCreateWithFlags(&B->master, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreate(&B->ev0) == cudaSuccess && cudaEventCreate(&B->ev1) == cudaSuccess;
+            cudaEventCreate(&B->ev0) == cudaSuccess && cudaEventCreate(&B->ev1) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->evf, cudaEventDisableTiming) == cudaSuccess;
   const int ns = std::min(count, kBatchStreams);
   for (int i = 0; ok && i < ns; ++i) {
     cudaStream_t s = nullptr;
@@ -1706,16 +2004,29 @@ int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
   for (cudaStream_t s : B->streams) BCK(cudaStreamWaitEvent(s, B->ev0, 0));
   int rc = MQS_OK;
   // step-major issue order: every problem's step s is queued before any step s+1,
-  // so the streams advance side by side
-  for (int s = 0; s < nsteps && rc == MQS_OK; ++s)
-    for (int i = 0; i < cnt && rc == MQS_OK; ++i) rc = enqueue_step(B->hs[i], s);
+  // so the streams advance side by side; whole chunks of steady-state steps come
+  // from a graph
+  bool on_master = false;
+  for (int s = 0; s < nsteps && rc == MQS_OK;) {
+    bool done = false;
+    if (nsteps - s >= kBatchGraphSteps) rc = batch_graph_steps(B, &on_master, &done);
+    if (rc != MQS_OK) break;
+    if (done) {
+      s += kBatchGraphSteps;
+      continue;
+    }
+    if (on_master) {
+      rc = master_to_batch(B);
+      on_master = false;
+    }
+    for (int i = 0; i < cnt && rc == MQS_OK; ++i) rc = enqueue_step(B->hs[i]);
+    ++s;
+  }
   for (mqs_handle* H : B->hs)
     if (join_side(H) != MQS_OK && rc == MQS_OK) rc = MQS_ERR_CUDA;   // side streams inside the timed span
-  for (size_t i = 0; i < B->streams.size(); ++i) {
-    BCK(cudaEventRecord(B->done[i], B->streams[i]));
-    BCK(cudaStreamWaitEvent(B->master, B->done[i], 0));
-  }
+  if (!on_master) BRK(batch_to_master(B));
   BCK(cudaEventRecord(B->ev1, B->master));
+  BRK(master_to_batch(B));     // the statistics copies below follow every step
   if (rc != MQS_OK) {
     for (cudaStream_t s : B->streams) cudaStreamSynchronize(s);
     return rc;
@@ -1754,6 +2065,12 @@ int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
   }
   BRK(mqs_batch_set_scale(B, best));
   if (best_scale) *best_scale = best;
+  return MQS_OK;
+}
+
+int mqs_batch_graph_steps(const mqs_batch* B, long* steps) {
+  if (!B || !steps) return MQS_ERR_ARG;
+  *steps = B->graph_steps;
   return MQS_OK;
 }
 

@@ -46,8 +46,9 @@ __device__ __forceinline__ double flux_z(const double* a, int n, long long n3, i
 // the same arithmetic and grouping as the sweep's, so b is bitwise the sweep's
 __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac, double* b, CoilDrive drv,
                                                        CoilGeom coil, const int* sup, int nsup) {
-  const double i_t = (drv.waveform == 0) ? drv.amplitude * sin(2.0 * 3.141592653589793 * drv.freq * drv.t)
-                                         : drv.amplitude * (1.0 - exp(-drv.t / drv.tau));
+  const double t = drv.m_dev ? (double)(*drv.m_dev + drv.level) * drv.dt : drv.t;
+  const double i_t = (drv.waveform == 0) ? drv.amplitude * sin(2.0 * 3.141592653589793 * drv.freq * t)
+                                         : drv.amplitude * (1.0 - exp(-t / drv.tau));
   const double cs = drv.scale * i_t;
   const int n = g.n;
   const long long n3 = g.n3;

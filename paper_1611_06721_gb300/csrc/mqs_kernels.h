@@ -50,7 +50,15 @@ int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, 
 // the coil loop (plane_k, i0, j0, i1, j1) and its current: i_S(t) = amplitude sin(2 pi
 // freq t) (waveform 0) or amplitude (1 - exp(-t / tau)) (waveform 1), times scale
 struct CoilGeom { int k, i0, j0, i1, j1; };
-struct CoilDrive { double scale, amplitude, freq, tau, t; int waveform; };
+// i_S at time t, or (m_dev != nullptr) at t = (*m_dev + level) * dt: the step counter on
+// the device, so a captured step's launches do not change from step to step
+struct CoilDrive {
+  double scale, amplitude, freq, tau, t;
+  int waveform;
+  const long long* m_dev = nullptr;
+  long long level = 0;
+  double dt = 0.0;
+};
 // b = scale i_S(t) X_s - L ac_full (eq. (mrhs) in scaled units, scale = h/nu0;
 // amplitude 0 gives b = -L ac) at the listed layout indices only: the right-hand side's support (n-edges
 // sharing a face with a c-edge, and the coil); b keeps its values elsewhere (zero for
