@@ -76,6 +76,7 @@ struct mqs_handle {
   // statistics slot of the next one; the record kernel advances both and the right-hand
   // side reads [0], so the launches of one step do not depend on m
   long long* dctr = nullptr;
+  long long ctr_m = -1, ctr_slot = -1;   // what dctr holds once the issued work ran (-1: unknown)
   // CUDA graphs of one steady-state SPE step (two: the conductor buffers alternate)
   StepGraph graphs[2];
   int graph_next = 0;        // the entry the next capture replaces
@@ -899,6 +900,12 @@ bool rhs_ready(const mqs_handle* H, long m) {
   return H->b_for_m == m && H->b_ac_gen == H->ac_gen && H->b_dt == H->dt && H->b_rhs_time == H->opt.rhs_time;
 }
 
+// the host's copy of the device step counter follows a record_kernel launch
+void advance_ctr(mqs_handle* H) {
+  if (H->ctr_m >= 0) H->ctr_m += 1;
+  if (H->ctr_slot >= 0) H->ctr_slot += 1;
+}
+
 // the source of the step after the last one issued, at t_m (rhs_time 0) or t_{m-1},
 // with m taken from the device step counter
 CoilDrive step_drive(const mqs_handle* H, double amplitude) {
@@ -946,6 +953,7 @@ int enqueue_split_step(mqs_handle* H) {
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c));
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats,
                                  H->dctr);
+  advance_ctr(H);
   RK(history_push(H, H->x, H->lx, st));
   CK(cudaMemcpyAsync(H->xc, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
   RK(swap_spe(H));                                    // the coil type's table (joins the push)
@@ -1008,6 +1016,7 @@ int enqueue_step(mqs_handle* H) {
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
                                  H->derr, H->dstats, H->dctr);
+  advance_ctr(H);
   nl += 1;
   // the next step's right-hand side from the new state, beside the side stream's push
   H->m = m;
@@ -1051,6 +1060,7 @@ bool graph_eligible(const mqs_handle* H) {
 
 // the host fields a step changes
 struct StepHost {
+  long long ctr_m, ctr_slot;
   long m, b_for_m, b_ac_gen;
   double t, b_dt, fac_eps;
   int b_rhs_time, spe_m;
@@ -1058,17 +1068,19 @@ struct StepHost {
   double *ac, *ac2, *ac_full, *ac_full2;
 };
 StepHost save_host(const mqs_handle* H) {
-  return StepHost{H->m,     H->b_for_m, H->b_ac_gen, H->t,   H->b_dt,    H->fac_eps,  H->b_rhs_time,
-                  H->spe_m, H->lx_valid, H->side_pending, H->ac, H->ac2, H->ac_full, H->ac_full2};
+  return StepHost{H->ctr_m, H->ctr_slot,   H->m,     H->b_for_m, H->b_ac_gen, H->t,   H->b_dt,
+                  H->fac_eps, H->b_rhs_time, H->spe_m, H->lx_valid, H->side_pending, H->ac, H->ac2, H->ac_full,
+                  H->ac_full2};
 }
 void load_host(mqs_handle* H, const StepHost& s) {
+  H->ctr_m = s.ctr_m; H->ctr_slot = s.ctr_slot;
   H->m = s.m; H->b_for_m = s.b_for_m; H->b_ac_gen = s.b_ac_gen; H->t = s.t; H->b_dt = s.b_dt;
   H->fac_eps = s.fac_eps; H->b_rhs_time = s.b_rhs_time; H->spe_m = s.spe_m; H->lx_valid = s.lx_valid;
   H->side_pending = s.side_pending; H->ac = s.ac; H->ac2 = s.ac2; H->ac_full = s.ac_full;
   H->ac_full2 = s.ac_full2;
 }
 bool same_host(const StepHost& a, const StepHost& b) {
-  return a.m == b.m && a.b_for_m == b.b_for_m && a.b_ac_gen == b.b_ac_gen && a.t == b.t && a.b_dt == b.b_dt &&
+  return a.ctr_m == b.ctr_m && a.ctr_slot == b.ctr_slot && a.m == b.m && a.b_for_m == b.b_for_m && a.b_ac_gen == b.b_ac_gen && a.t == b.t && a.b_dt == b.b_dt &&
          a.fac_eps == b.fac_eps && a.b_rhs_time == b.b_rhs_time && a.spe_m == b.spe_m &&
          a.lx_valid == b.lx_valid && a.side_pending == b.side_pending && a.ac == b.ac && a.ac2 == b.ac2 &&
          a.ac_full == b.ac_full && a.ac_full2 == b.ac_full2;
@@ -1076,6 +1088,8 @@ bool same_host(const StepHost& a, const StepHost& b) {
 // what a steady-state SPE step (its side stream joined) leaves on the host
 StepHost after_step(const mqs_handle* H, const StepHost& s) {
   StepHost r = s;
+  if (r.ctr_m >= 0) r.ctr_m += 1;
+  if (r.ctr_slot >= 0) r.ctr_slot += 1;
   r.m = s.m + 1;
   r.t = r.m * H->dt;
   r.b_for_m = r.m + 1;
@@ -1204,6 +1218,17 @@ int ensure_split(mqs_handle* H) {
   return ensure_spe_alt(H);
 }
 
+// the device step counter at (H->m, slot); unless forced, launched only when it would hold
+// other values once the issued work ran (steps enqueued behind each other need none)
+int set_ctr(mqs_handle* H, long long slot, bool force) {
+  if (!force && H->ctr_m == H->m && H->ctr_slot == slot) return MQS_OK;
+  set_ctr_kernel<<<1, 1, 0, H->st>>>(H->dctr, H->m, slot);
+  CK(cudaGetLastError());
+  H->ctr_m = H->m;
+  H->ctr_slot = slot;
+  return MQS_OK;
+}
+
 // Before the steps of a call: buffers, and (unless steps are already queued) a cleared
 // device error word, so a barrier timeout of any step of the call stays recorded.
 int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
@@ -1214,9 +1239,7 @@ int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (!H->dctr) RK(dalloc(H, &H->dctr, 2));
   if (keep == 0) CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
   RK(ensure_stats(H, nsteps, keep));
-  set_ctr_kernel<<<1, 1, 0, H->st>>>(H->dctr, H->m, keep);
-  CK(cudaGetLastError());
-  return MQS_OK;
+  return set_ctr(H, keep, keep == 0);
 }
 
 // Copies the step statistics of the last nsteps steps into hs (async on H->st).
@@ -1405,7 +1428,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
       H->ac_gen += 1;
       H->m = m0 + lo;
       H->t = H->m * H->dt;
-      set_ctr_kernel<<<1, 1, 0, st>>>(H->dctr, H->m, 2 * nsteps + lo);
+      RK(set_ctr(H, 2 * nsteps + lo, true));
       for (int s = lo; s < hi; ++s) {
         H->rec_a = trajA + (size_t)(s - lo) * nc;
         H->rec_F = trajF + (size_t)(s - lo) * nc;
