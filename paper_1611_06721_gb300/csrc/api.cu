@@ -463,8 +463,8 @@ int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int
 long start_launches(const mqs_handle* H) {
   switch (H->opt.start_mode) {
     case MQS_START_SPE: {
-      const int m = H->spe_m;  // value before this step's push: g, substitutions, linear combination
-      return m == 0 ? 0 : 3;
+      const int m = H->spe_m;  // value before this step's push: g with the substitutions, linear combination
+      return m == 0 ? 0 : 2;
     }
     case MQS_START_POD:
       return H->pod_m == 0 ? 0 : (H->pod_m + 7) / 8 + 2;
@@ -665,6 +665,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->spe_hpart, (size_t)4 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_gpart, (size_t)spe_gblocks() * kSpeGSlots));
   RK(dalloc(H, &H->spe_fac, 1));
+  CK(cudaMemset(H->spe_fac, 0, sizeof(SpeFac)));     // arrival counters start at zero
   H->nsup = (int)sup.size();
   RK(dalloc(H, &H->sup, std::max<size_t>(sup.size(), 1)));
   if (!sup.empty()) CK(cudaMemcpy(H->sup, sup.data(), sizeof(int) * sup.size(), cudaMemcpyHostToDevice));
@@ -890,6 +891,7 @@ int ensure_spe_alt(mqs_handle* H) {
   if (!H->alt_hpart) {
     RK(dalloc(H, &H->alt_hpart, (size_t)4 * ts_nblk() * kTileSlots));
     RK(dalloc(H, &H->alt_fac, 1));
+    CK(cudaMemsetAsync(H->alt_fac, 0, sizeof(SpeFac), H->st));
   }
   for (int a = H->alt_cols; a < d; ++a) { RK(dalloc(H, &H->alt_D[a], H->len)); RK(dalloc(H, &H->alt_LD[a], H->len)); }
   H->alt_cols = std::max(H->alt_cols, d);

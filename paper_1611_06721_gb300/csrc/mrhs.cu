@@ -759,6 +759,24 @@ __global__ void __launch_bounds__(kTS, 1) dots_ff_kernel(VecSet A, VecSet B, int
 // Galerkin products of the new table (tile 0: D_q . LD_p, p <= q < m_new <= 8):
 // one pass over the table instead of a push and a second pass re-reading it.
 // New table: D_0 = w, D_p = D_{p-1}^new - D_{p-1}^old (and likewise the images).
+__device__ void spe_solve_body(const float2* gpart, int nbg, int m, const SpeFac* fac, double* coef, SmallOut* out);
+
+// True in the block that arrives last at this call (every block calls it once, after its
+// global writes); that block also returns the counter to zero for the next launch.  No
+// block waits for another.
+__device__ __forceinline__ bool last_block(unsigned* ctr) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    if (last) atomicExch(ctr, 0u);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
 __global__ void __launch_bounds__(kTS, 1) spe_push_dots_kernel(MutVecSet D, MutVecSet LD, const double* __restrict__ w,
                                                               const double* __restrict__ lw, int m_old, int m_new,
                                                               long long len, float2* part) {
@@ -815,10 +833,12 @@ __global__ void __launch_bounds__(kTS, 1) spe_push_dots_kernel(MutVecSet D, MutV
 
 // g_q = D_q . b (q < m <= MAXM) over the listed layout indices (idx != nullptr) or
 // the edges of the positions in box (b is zero elsewhere); float-float partials,
-// kSpeGSlots per block.
+// kSpeGSlots per block.  The last block to finish sums them and solves with the
+// factor in fac (spe_solve_body): coef = y.
 template <int MAXM>
 __global__ void __launch_bounds__(kTS) spe_g_kernel(VecSet D, const double* __restrict__ b, int m, int n, Box box,
-                                                    const int* __restrict__ idx, int nidx, float2* gpart) {
+                                                    const int* __restrict__ idx, int nidx, float2* gpart,
+                                                    SpeFac* fac, double* coef, SmallOut* out) {
   const int bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
   const int npos = bx * by * bz;
   const long long n3 = (long long)n * n * n;
@@ -845,6 +865,7 @@ __global__ void __launch_bounds__(kTS) spe_g_kernel(VecSet D, const double* __re
   }
   __shared__ float2 red[kTS / 32][16];
   block_partials_ff<16>(S, E, red, [](int s) { return s; }, gpart + (size_t)blockIdx.x * kSpeGSlots);
+  if (last_block(&fac->g_done)) spe_solve_body(gpart, gridDim.x, m, fac, coef, out);
 }
 
 // x = sum_p coef_p V_p with float-float V and FP64 coefficients
@@ -875,7 +896,7 @@ __device__ __forceinline__ ffv sum_parts_ff(const float2* base, int stride, int 
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int q = lane + 32 * r;
-    const float2 f = (q < cnt) ? base[(size_t)q * stride] : make_float2(0.f, 0.f);
+    const float2 f = (q < cnt) ? __ldcg(base + (size_t)q * stride) : make_float2(0.f, 0.f);
     v[r] = ffv(f.x, f.y);
   }
 #pragma unroll
@@ -884,7 +905,7 @@ __device__ __forceinline__ ffv sum_parts_ff(const float2* base, int stride, int 
     for (int r = 0; r < w2; ++r) v[r] = v[r] + v[r + w2];
   ffv s = v[0];
   for (int q = lane + 512; q < cnt; q += 32) {
-    const float2 f = base[(size_t)q * stride];
+    const float2 f = __ldcg(base + (size_t)q * stride);
     s = s + ffv(f.x, f.y);
   }
 #pragma unroll
@@ -896,8 +917,7 @@ __device__ __forceinline__ ffv sum_parts_ff(const float2* base, int stride, int 
 // (entries (q, p), q >= p, of H = D^T K D in tiles of 8: tile 0 rows/columns 0-7,
 // tiles 1 and 3 rows 8-11 and 12-15 against columns 0-7, tile 2 rows/columns 8-15)
 // and factors H (pivoted Cholesky with the drop rule, register form, warp 0) into fac.
-__global__ void __launch_bounds__(512) spe_factor_kernel(const float2* hpart, int nbh, int m, double drop2,
-                                                         SpeFac* fac) {
+__device__ void spe_factor_body(const float2* hpart, int nbh, int m, double drop2, SpeFac* fac) {
   __shared__ double H[kMaxSpe * kMaxSpe];
   __shared__ double vals[kMaxSpe * (kMaxSpe + 1) / 2];
   const int npair = m * (m + 1) / 2;
@@ -940,10 +960,14 @@ __global__ void __launch_bounds__(512) spe_factor_kernel(const float2* hpart, in
   }
 }
 
+__global__ void __launch_bounds__(512) spe_factor_kernel(const float2* hpart, int nbh, int m, double drop2,
+                                                         SpeFac* fac) {
+  spe_factor_body(hpart, nbh, m, drop2, fac);
+}
+
 // Second half (needs b): sums g = D^T b from its partials, the substitutions with
-// fac, coef = y.
-__global__ void __launch_bounds__(512) spe_solve_kernel(const float2* gpart, int nbg, int m, const SpeFac* fac,
-                                                        double* coef, SmallOut* out) {
+// fac, coef = y.  Any block size that is a multiple of 32.
+__device__ void spe_solve_body(const float2* gpart, int nbg, int m, const SpeFac* fac, double* coef, SmallOut* out) {
   __shared__ double g[kMaxSpe], y[kMaxSpe];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = wid; t < m; t += nw) {
@@ -1039,7 +1063,7 @@ int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const dou
 }
 
 int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, const int* sup, int nsup, double* x0,
-           long long len, const SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st) {
+           long long len, SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st) {
   if (m <= 0) {
     if (cudaMemsetAsync(x0, 0, sizeof(double) * len, st) != cudaSuccess) return MQS_ERR_CUDA;
     return MQS_OK;
@@ -1050,9 +1074,8 @@ int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, cons
       sup ? nsup : 3LL * (bbox.hi[0] - bbox.lo[0]) * (bbox.hi[1] - bbox.lo[1]) * (bbox.hi[2] - bbox.lo[2]);
   const int nbg = (int)std::min<long long>(std::max<long long>((edges + kTS - 1) / kTS, 1), spe_gblocks());
   float2* gp = reinterpret_cast<float2*>(gpart);
-  if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp);
-  else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp);
-  spe_solve_kernel<<<1, 512, 0, st>>>(gp, nbg, m, fac, coef, out);
+  if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp, fac, coef, out);
+  else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp, fac, coef, out);
   const int nl = ts_blocks(len) * 4;
   if (m <= 8) lincomb_ff_kernel<8><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);
   else if (m <= 12) lincomb_ff_kernel<12><<<nl, kTS, 0, st>>>(D, coef, m, len, x0);

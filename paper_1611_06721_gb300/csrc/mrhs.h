@@ -24,6 +24,9 @@ struct SpeFac {
   double inv[kMaxSpe];
   double sc[kMaxSpe];
   int nk, m;
+  // arrival counter of the g kernel (zero between launches): its last block solves the
+  // small system from the partials of all blocks
+  unsigned g_done;
 };
 // SPE difference table D_p and images L D_p, stored as float-float pairs (8 bytes per
 // value, the buffers are FP64-sized): push the new solution w (FP64) and its image lw,
@@ -43,7 +46,7 @@ int spe_gblocks();
 // positions in bbox (b must vanish elsewhere; n is the grid size), the
 // substitutions, x0 = D y
 int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, const int* sup, int nsup, double* x0,
-           long long len, const SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st);
+           long long len, SpeFac* fac, double* gpart, double* coef, SmallOut* out, cudaStream_t st);
 int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot_new, long long len, double* part,
              double* G, double* A, cudaStream_t st);
 int pod_x0(const VecSet& X, int m, const double* G, const double* A, const double* b, double* x0, long long len,
