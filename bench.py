@@ -551,6 +551,10 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     batch = pkg.Batch(solvers)
     best = batch.tune(max(args.warmup // 4, 1))
+    depth_by_n = None
+    if args.tune_depth:
+        chosen = batch.tune_depth(max(args.warmup // 4, 5), depths=(4, 8, 16))
+        depth_by_n = {int(p.N): int(d) for p, d in zip(probs, chosen)}
     batch.step(args.warmup)
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -589,7 +593,9 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"{len(solvers)} instances, N from {set(sizes)} "
                                    f"(count per N {sizes}), sigma U[1e6,5e6] S/m, coil 100-1000 A, "
-                                   f"Brauer iron, SPE 8, seed 1611",
+                                   f"Brauer iron, "
+                                   + (f"SPE depth tuned per N {depth_by_n}" if depth_by_n else "SPE 8")
+                                   + ", seed 1611",
                        "n_unknowns": int(sum(s.n_n for s in solvers)),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
                        "blocks_scale": best, "l2": "working set larger than L2 (no flush)",
@@ -773,6 +779,8 @@ def main():
                     help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
     ap.add_argument("--batch", type=int, default=0,
                     help="advance this many seeded multi-query instances together (batched mode)")
+    ap.add_argument("--tune-depth", action="store_true",
+                    help="batched mode: tune the SPE depth per grid size over {4, 8, 16} after the block scale")
     ap.add_argument("--batch-grid", type=str, default="",
                     help="comma-separated grid sizes the batched instances draw from (default 32,40,48,64)")
     ap.add_argument("--adjoint", action="store_true",

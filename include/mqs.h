@@ -462,7 +462,19 @@ int mqs_loss(mqs_handle* h, int nsteps, double* objective);
  * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8 for trial_steps steps
  * each -- real steps that advance every problem -- and keeps the fastest
  * (returned in *best_scale, nullable).
- * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts. */
+ * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts.
+ *
+ * mqs_batch_tune_depth: the SPE depth per grid size.  The handles with the SPE
+ * start are grouped by n.  Group by group, in increasing n, the depths in
+ * depths[0..ndepths) (each 1..16) are tried in the order d_0 .. d_last, then
+ * d_last .. d_0.  Each trial sets the depth on the group's handles (through
+ * mqs_set_options: a new history), refills the tables with dmax + 1 steps and
+ * times trial_steps steps (mqs_batch_last_ms).  A depth's two trial times are
+ * added, so a linear drift of a transient's iteration counts cancels.  The group
+ * keeps its fastest depth while the next group is searched.  These are real
+ * steps: every problem advances.  chosen (host, nullable) receives the final spe_depth of every
+ * handle, in the batch's order.  Other handles keep their options.  Errors:
+ * MQS_ERR_ARG, or the status of a failing step. */
 int mqs_set_blocks(mqs_handle* h, int nblk);
 typedef struct mqs_batch mqs_batch;
 int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale,
@@ -471,6 +483,8 @@ int mqs_batch_set_scale(mqs_batch* b, double blocks_scale);
 int mqs_batch_step(mqs_batch* b, int nsteps, mqs_step_stats* per_step);
 int mqs_batch_last_ms(mqs_batch* b, double* ms);
 int mqs_batch_tune(mqs_batch* b, int trial_steps, double* best_scale);
+int mqs_batch_tune_depth(mqs_batch* b, int trial_steps, const int* depths, int ndepths,
+                         int* chosen);
 int mqs_batch_destroy(mqs_batch* b);
 int mqs_batch_graph_steps(const mqs_batch* b, long* steps);
 

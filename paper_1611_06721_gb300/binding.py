@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes as C
 import weakref
 import os
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -31,7 +31,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_timing_enable", "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout",
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
-           "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps")
+           "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth")
 
 
 class Grid(C.Structure):
@@ -141,6 +141,7 @@ def load():
         "mqs_solve_an": ([H, P(D), P(PcgInfo)], I),
         "mqs_graph_steps": ([H, P(C.c_long)], I),
         "mqs_batch_graph_steps": ([V, P(C.c_long)], I),
+        "mqs_batch_tune_depth": ([V, I, P(I), I, P(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -488,6 +489,16 @@ class Batch:
         v = C.c_double()
         self._check(self.lib.mqs_batch_tune(self.b, trial_steps, C.byref(v)))
         return v.value
+
+    def tune_depth(self, trial_steps, depths=(4, 8, 16)):
+        """SPE depth per grid size (mqs_batch_tune_depth); returns every solver's depth."""
+        ds = (C.c_int * len(depths))(*depths)
+        out = (C.c_int * len(self.solvers))()
+        self._check(self.lib.mqs_batch_tune_depth(self.b, trial_steps, ds, len(depths), out))
+        for sv, d in zip(self.solvers, out):
+            if sv.options.start_mode == START_SPE:
+                sv.options = replace(sv.options, spe_depth=int(d))
+        return list(out)
 
     def close(self):
         if getattr(self, "b", None):

@@ -2093,6 +2093,52 @@ int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
   return MQS_OK;
 }
 
+int mqs_batch_tune_depth(mqs_batch* B, int trial_steps, const int* depths, int ndepths, int* chosen) {
+  if (!B || trial_steps < 1 || !depths || ndepths < 1) return MQS_ERR_ARG;
+  int dmax = 0;
+  for (int c = 0; c < ndepths; ++c) {
+    if (depths[c] < 1 || depths[c] > kMaxSpe) return MQS_ERR_ARG;
+    dmax = std::max(dmax, depths[c]);
+  }
+  const size_t cnt = B->hs.size();
+  // the SPE handles grouped by grid size, each group's depth searched in turn with the
+  // others held (coordinate search on the batch's device time)
+  std::vector<int> sizes;
+  for (mqs_handle* H : B->hs)
+    if (H->opt.start_mode == MQS_START_SPE && std::find(sizes.begin(), sizes.end(), H->n) == sizes.end())
+      sizes.push_back(H->n);
+  std::sort(sizes.begin(), sizes.end());
+  auto set_group = [&](int n, int d) -> int {
+    for (mqs_handle* H : B->hs)
+      if (H->opt.start_mode == MQS_START_SPE && H->n == n && H->opt.spe_depth != d) {
+        mqs_options o = H->opt;
+        o.spe_depth = d;
+        RK(mqs_set_options(H, &o));   // a new depth starts a new history
+      }
+    return MQS_OK;
+  };
+  // candidates in the order c_0 .. c_{k-1}, c_{k-1} .. c_0 with the two trial times of a
+  // candidate added: the iteration counts of a transient drift from trial to trial, and
+  // the mirrored order cancels a linear drift (one pass in one order favours the last)
+  for (int n : sizes) {
+    std::vector<double> ms(ndepths, 0.0);
+    for (int r = 0; r < 2 * ndepths; ++r) {
+      const int c = r < ndepths ? r : 2 * ndepths - 1 - r;
+      BRK(set_group(n, depths[c]));
+      BRK(mqs_batch_step(B, dmax + 1, nullptr));       // every table full again
+      BRK(mqs_batch_step(B, trial_steps, nullptr));
+      ms[c] += B->last_ms;
+    }
+    int best = 0;
+    for (int c = 1; c < ndepths; ++c)
+      if (ms[c] < ms[best]) best = c;
+    BRK(set_group(n, depths[best]));
+  }
+  if (chosen)
+    for (size_t i = 0; i < cnt; ++i) chosen[i] = B->hs[i]->opt.spe_depth;
+  return MQS_OK;
+}
+
 int mqs_batch_graph_steps(const mqs_batch* B, long* steps) {
   if (!B || !steps) return MQS_ERR_ARG;
   *steps = B->graph_steps;

@@ -142,3 +142,35 @@ def test_batch_tune_and_argument_checks(pkg):
     assert batch.b is None
     for s in sv[1:]:
         s.close()
+
+
+def test_depth_tuner_sets_one_depth_per_grid_size(pkg):
+    # the tuner searches the SPE depth group by group (grid size), sets the winner on every
+    # SPE handle of the group, leaves other start modes alone; the trajectory stays the
+    # oracle's (the start vector decides iteration counts only: a_c within the tolerance floor)
+    probs = [
+        (W.scaled_nonlinear(12, sigma=2.0e6, amplitude=700.0), dict(start_mode=START_SPE, spe_depth=8)),
+        (W.scaled_nonlinear(12, sigma=4.0e6, amplitude=300.0), dict(start_mode=START_SPE, spe_depth=8)),
+        (W.scaled_nonlinear(16, sigma=3.0e6, amplitude=500.0), dict(start_mode=START_SPE, spe_depth=8)),
+        (W.scaled_nonlinear(8, amplitude=500.0), dict(start_mode=1)),
+    ]
+    dts = [O.dt_gershgorin(O.Discretization(p)) for p, _ in probs]
+    sv = [pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, dt=dt, **kw)) for (p, kw), dt in zip(probs, dts)]
+    bt = pkg.Batch(sv)
+    with pytest.raises(pkg.MqsError):
+        bt.tune_depth(3, depths=(0,))
+    with pytest.raises(pkg.MqsError):
+        bt.tune_depth(3, depths=(17,))
+    chosen = bt.tune_depth(3, depths=(4, 8))
+    assert chosen[0] == chosen[1] and chosen[0] in (4, 8) and chosen[2] in (4, 8) and chosen[3] == 8
+    assert [s.options.spe_depth for s in sv] == chosen
+    _, rows = bt.step(10)
+    assert all(x.status == 0 for row in rows for x in row)
+    bt.close()
+    p, _ = probs[2]
+    a_c, _, m = sv[2].get_state()
+    assert m == 2 * 4 * (8 + 1 + 3) + 10         # two groups x four trials x (refill + trial), then 10
+    ref = O.run_explicit_euler(O.Discretization(p), dts[2], m, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    assert rel(a_c, ref.a_c) < 1e-8
+    for s in sv:
+        s.close()
