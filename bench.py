@@ -195,14 +195,16 @@ def run_reference(args, rank, ws, dist):
     s = oracle_sample(total, budget)
     cores = 1
     line = {"impl": "reference", "metric": METRIC, "value": s["steps_per_s"], "unit": "steps/s",
-            "n_gpus": args.gpus, "steps": s["steps"], "warmup": 0, "ms_per_step": 1e3 / s["steps_per_s"],
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / s["steps_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "grid": 64, "start_vector": "spe8", "tol": 1e-10},
             "iters_per_step": s["iters_per_step"],
             "cpu_baseline": {"value": s["steps_per_s"], "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {s['steps']} explicit Euler steps of the workload "
-                                       f"(of {total} requested, {budget:.0f} s budget), single thread, "
-                                       f"setup {s['setup_s']:.1f} s excluded"},
+                             "sample": f"first {s['steps']} explicit Euler steps of the workload timed "
+                                       f"(of the {total} = warm-up + steps requested, {budget:.0f} s budget), "
+                                       f"single thread, setup {s['setup_s']:.1f} s excluded; these early "
+                                       f"steps take {s['iters_per_step']:.1f} PCG iterations per step while "
+                                       f"the SPE history fills"},
             "e2e": {"value": s["steps_per_s"], "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

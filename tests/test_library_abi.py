@@ -54,3 +54,37 @@ def test_layout_mapping_round_trip():
         assert np.all(d[m < 0])                     # unstored edges are Dirichlet
         v = np.random.default_rng(0).standard_normal(g.n_edges) * (m >= 0)
         assert np.array_equal(layout_to_oracle(N, oracle_to_layout(N, v)), v)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # every ctypes mirror of a header struct has the C compiler's size and field offsets
+    # (a field added to the header but not to the binding would shift the ones after it)
+    import ctypes
+    import shutil
+    import subprocess
+    import paper_1611_06721_gb300.binding as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"mqs_grid": b.Grid, "mqs_materials": b.Materials, "mqs_coil": b.Coil, "mqs_options": b.Options,
+             "mqs_layout_info": b.LayoutInfo, "mqs_adjoint_info": b.AdjointInfo, "mqs_step_stats": b.StepStats,
+             "mqs_timing": b.Timing, "mqs_pcg_info": b.PcgInfo}
+    lines = ['#include <stdio.h>', '#include "mqs.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
