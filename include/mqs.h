@@ -155,8 +155,10 @@ typedef struct {
                              of 0.  Only SPE starts without rhs_split, timing or
                              adjoint recording, and a stream that can be
                              captured (not the legacy default stream); other
-                             steps are issued launch by launch.  0 (default):
-                             every step launch by launch. */
+                             steps are issued launch by launch.  0 (the C
+                             default of a zeroed struct; the Python binding's
+                             SolverOptions defaults to 1): every step launch
+                             by launch. */
 } mqs_options;
 
 typedef struct {

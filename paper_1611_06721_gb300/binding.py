@@ -184,7 +184,7 @@ class SolverOptions:
     inner_tol: float = 0.0
     cspe_period: int = 0
     rhs_split: int = 0
-    graph: int = 0
+    graph: int = 1          # steady-state SPE steps from CUDA graphs (bitwise the same results)
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
