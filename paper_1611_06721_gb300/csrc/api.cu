@@ -1157,7 +1157,11 @@ int graph_step(mqs_handle* H, bool* done) {
   cudaGraphExec_t exec = nullptr;
   const bool ok = capture(
       H->st,
-      [&] { return enqueue_step(H) == MQS_OK && join_side(H) == MQS_OK && same_host(save_host(H), after_step(H, s0)); },
+      [&] {
+        const bool issued = enqueue_step(H) == MQS_OK;
+        const bool joined = join_side(H) == MQS_OK;     // also after a failure: no fork left open
+        return issued && joined && same_host(save_host(H), after_step(H, s0));
+      },
       &exec);
   if (!ok) {
     load_host(H, s0);
