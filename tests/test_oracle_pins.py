@@ -284,6 +284,71 @@ def test_spe_start_galerkin_and_exact_recovery():
         assert e1 @ (d.K_n @ e1) > e0 @ (d.K_n @ e0)
 
 
+class _CountEigh:
+    """Counts calls of numpy.linalg.eigh (the small solve's fallback branch)."""
+
+    def __init__(self, monkeypatch):
+        self.calls = 0
+        real = np.linalg.eigh
+
+        def wrapped(*a, **k):
+            self.calls += 1
+            return real(*a, **k)
+        monkeypatch.setattr(np.linalg, "eigh", wrapped)
+
+
+def test_small_solve_fallback_on_a_singular_system(monkeypatch):
+    # Cholesky fails on a singular H; the fallback keeps the eigenspace above
+    # 1e-14 lambda_max and returns the minimum-norm least-squares solution there
+    from oracle.mrhs import solve_small_spd
+    rng = np.random.default_rng(7)
+    V, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    lam = np.array([5.0, 2.0, 0.5, 1e-3, 0.0, 0.0])
+    H = (V * lam) @ V.T
+    H[1, 0] += 1e-17                                     # asymmetric by rounding: symmetrised first
+    g = rng.standard_normal(6)
+    count = _CountEigh(monkeypatch)
+    y = solve_small_spd(H, g)
+    assert count.calls == 1                              # the fallback branch ran
+    # the minimum-norm least-squares solution by an SVD-based pseudo-inverse (a different routine)
+    Hs = 0.5 * (H + H.T)
+    y_pinv = np.linalg.pinv(Hs, rcond=1e-12) @ g
+    y_lstsq = np.linalg.lstsq(Hs, g, rcond=1e-12)[0]
+    assert rel(y, y_pinv) < 1e-10 and rel(y, y_lstsq) < 1e-10
+    # Galerkin orthogonality on the kept eigenspace, nothing in the dropped one
+    Vk, V0 = V[:, :4], V[:, 4:]
+    assert np.abs(Vk.T @ (g - Hs @ y)).max() <= 1e-12 * np.linalg.norm(g)
+    assert np.abs(V0.T @ y).max() <= 1e-12 * np.linalg.norm(y)
+    # a wrong truncation (dropping the 1e-3 eigenvalue) would change y by its component
+    assert abs(Vk[:, 3] @ y - (Vk[:, 3] @ g) / 1e-3) <= 1e-8 * abs((Vk[:, 3] @ g) / 1e-3)
+
+
+def test_galerkin_start_fallback_agrees_with_cholesky(monkeypatch):
+    # (a) on a nonsingular SPE Galerkin system the eigen-solve branch must give the
+    # Cholesky solution: Cholesky is made to fail on purpose
+    p = W.config_linear_block(N=6)
+    d = O.Discretization(p)
+    Q = O.mgs_orthonormal_basis(_smooth_window(d, 3, 21))
+    b = d.K_n @ W.random_vector(98, d.n_n)
+    x_chol = galerkin_start(d.K_n, Q, b)
+    count = _CountEigh(monkeypatch)
+
+    def no_cholesky(*a, **k):
+        raise np.linalg.LinAlgError("forced")
+    with monkeypatch.context() as m:
+        m.setattr(np.linalg, "cholesky", no_cholesky)
+        x_eig = galerkin_start(d.K_n, Q, b)
+    assert count.calls == 1
+    assert rel(x_eig, x_chol) < 1e-10
+    # (b) a basis column that K_n annihilates exactly (here: zero) makes U^T K_n U
+    # singular, Cholesky fails by itself, and the fallback projects on the other columns
+    U = np.column_stack([Q, np.zeros(d.n_n)])
+    x0 = galerkin_start(d.K_n, U, b)
+    assert count.calls == 2
+    assert rel(d.K_n @ x0, d.K_n @ x_chol) < 1e-10
+    assert np.abs(U.T @ (b - d.K_n @ x0)).max() <= 1e-10 * np.linalg.norm(b)
+
+
 def test_pod_recovers_constructed_singular_values():
     rng = np.random.default_rng(5)
     n, m = 400, 8
