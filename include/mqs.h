@@ -360,11 +360,14 @@ int pod_start(mqs_handle* h, const double* b, double* x0, int* k);
  * are set to zero; 16-byte aligned, as cudaMalloc returns).  n, h, nu0: grid cells per axis, spacing, reluctivity.
  * Scratch: one file-scope device array sized for n <= MQS_NOALLOC_MAX_N
  * (about 13.4 MB), held by every GPU that loads the library until the
- * process exits.  Larger n returns MQS_ERR_ARG (message on stderr).  The
- * first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (other streams, other host threads) race; serialise them.
+ * process exits.  Larger n returns MQS_ERR_ARG (message on stderr).  Set-up:
+ * the first call in a CUDA context (per device, and again after a device
+ * reset, which makes a new context) looks the array's address up
+ * (cudaGetSymbolAddress) with that device current, under a lock, and keeps it
+ * for later calls in that context; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other host threads) race; serialise them.  Every call starts its
+ * own scratch state afresh (the barrier counter and error word are cleared).
  * Blocks the host until the solve finishes; info (host) may be NULL.
  * Returns MQS_OK or the PCG status (MQS_ERR_NOT_CONVERGED, _BREAKDOWN,
  * _NAN, _TIMEOUT), MQS_ERR_ARG or MQS_ERR_CUDA. */

@@ -155,6 +155,37 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _dev_ptrs(*specs):
+    """Device pointers of torch tensors, after checking that each is what the library
+    reads or writes there.  specs: (tensor, name, dtype, numel[, align]) tuples.  First
+    every tensor's dtype, element count and layout, then that each is a CUDA tensor on
+    the current device and aligned: ValueError on the first mismatch, before any launch."""
+    import torch
+    for sp in specs:
+        t, name, dtype, numel = sp[:4]
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor, got {type(t).__name__}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{name} must hold {numel} values, got {t.numel()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    out = []
+    for sp in specs:
+        t, name = sp[0], sp[1]
+        align = sp[4] if len(sp) > 4 else 8
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
+        if t.data_ptr() % align:
+            raise ValueError(f"{name} must be {align}-byte aligned")
+        out.append(C.c_void_p(t.data_ptr()))
+    return out if len(out) > 1 else out[0]
+
+
 def _f64(a, n=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     if n is not None and a.size != n:
@@ -353,11 +384,16 @@ class Solver:
         self._check(self.lib.mqs_set_state(self.h, _dp(a), a.size, t, m))
 
     def get_state_dev(self, out, stream=0):
-        self._check(self.lib.mqs_get_state_dev(self.h, C.c_void_p(out.data_ptr()), self.n_c,
-                                               C.c_void_p(stream)))
+        """a_c into the float64 CUDA tensor `out` (n_c values)."""
+        import torch
+        ptr = _dev_ptrs((out, "out", torch.float64, self.n_c))
+        self._check(self.lib.mqs_get_state_dev(self.h, ptr, self.n_c, C.c_void_p(stream)))
 
     def set_state_dev(self, a, stream=0):
-        self._check(self.lib.mqs_set_state_dev(self.h, C.c_void_p(a.data_ptr()), self.n_c, C.c_void_p(stream)))
+        """a_c from the float64 CUDA tensor `a` (n_c values)."""
+        import torch
+        ptr = _dev_ptrs((a, "a", torch.float64, self.n_c))
+        self._check(self.lib.mqs_set_state_dev(self.h, ptr, self.n_c, C.c_void_p(stream)))
 
     def get_solution(self):
         w = np.empty(self.n_layout)
@@ -375,9 +411,11 @@ class Solver:
         return x, info
 
     def pcg_solve_dev(self, b, x, tol=1e-10, maxit=100000, stream=0, allow_fail=False):
+        """pcg_solve_dev on float64 CUDA tensors of n_layout values (x: start in, solution out)."""
+        import torch
+        pb, px = _dev_ptrs((b, "b", torch.float64, self.n_layout), (x, "x", torch.float64, self.n_layout))
         info = PcgInfo()
-        rc = self.lib.pcg_solve_dev(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), tol, maxit,
-                                    C.byref(info), C.c_void_p(stream))
+        rc = self.lib.pcg_solve_dev(self.h, pb, px, tol, maxit, C.byref(info), C.c_void_p(stream))
         if not allow_fail:
             self._check(rc)
         return info
@@ -389,8 +427,10 @@ class Solver:
         return y
 
     def apply_kn_dev(self, x, y, stream=0):
-        self._check(self.lib.mqs_apply_kn_dev(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
-                                              C.c_void_p(stream)))
+        """y = K_n x on float64 CUDA tensors of n_layout values."""
+        import torch
+        px, py = _dev_ptrs((x, "x", torch.float64, self.n_layout), (y, "y", torch.float64, self.n_layout))
+        self._check(self.lib.mqs_apply_kn_dev(self.h, px, py, C.c_void_p(stream)))
 
     def conductor_rate(self, a_c, w):
         a = _f64(a_c, self.n_c)
@@ -426,11 +466,15 @@ class Solver:
 
 def pcg_solve_noalloc(n, h, nu0, cell_mask, b, x, tol=1e-10, maxit=100000, stream=0):
     """mqs_pcg_solve_noalloc on torch CUDA tensors (cell_mask uint8 n^3, b and
-    x float64 layout vectors); x is overwritten.  Returns (status, PcgInfo)."""
+    x float64 layout vectors of 3 n^3 values, x 16-byte aligned); x is overwritten.
+    Returns (status, PcgInfo).  The tensors are checked before the call."""
+    import torch
+    n3 = int(n) ** 3
+    pm, pb, px = _dev_ptrs((cell_mask, "cell_mask", torch.uint8, n3, 1), (b, "b", torch.float64, 3 * n3),
+                           (x, "x", torch.float64, 3 * n3, 16))
     lib = load()
     info = PcgInfo()
-    rc = lib.mqs_pcg_solve_noalloc(n, h, nu0, C.c_void_p(cell_mask.data_ptr()), C.c_void_p(b.data_ptr()),
-                                   C.c_void_p(x.data_ptr()), tol, maxit, C.byref(info), C.c_void_p(stream))
+    rc = lib.mqs_pcg_solve_noalloc(n, h, nu0, pm, pb, px, tol, maxit, C.byref(info), C.c_void_p(stream))
     return rc, info
 
 
@@ -520,15 +564,20 @@ def eddy_loss(sigma_cell, amplitude, problem, options: SolverOptions, nsteps, ch
     amplitude (0-d tensor); dt, the edge classes and the waveform come from `problem` /
     `options` and stay fixed.  The forward call runs mqs_adjoint (J and both gradients
     at once; checkpoints every `checkpoint_every` steps when positive), backward scales
-    the stored gradients."""
+    the stored gradients.  The conducting region (and so the edge classes) is the one of
+    `problem` (its cells with sigma > 0); a conductivity that reaches 0 or below inside
+    it raises MqsError."""
     import torch
+    cmask = (np.asarray(problem.sigma_cell) > 0).astype(np.uint8)
 
     class _EddyLoss(torch.autograd.Function):
         @staticmethod
         def forward(ctx, sig, amp):
             sg = sig.detach().to("cpu", torch.float64).numpy()
             p = problem.with_(sigma_cell=sg, amplitude=float(amp))
-            s = Solver.from_problem(p, options)
+            # the conducting region stays the problem's own: a conductivity driven to 0
+            # inside it is refused by mqs_setup instead of silently changing the edge classes
+            s = Solver.from_problem(p, options, conductor_mask=cmask)
             try:
                 J, g, gI, _ = s.adjoint(nsteps, checkpoint_every)
             finally:

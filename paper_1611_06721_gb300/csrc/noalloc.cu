@@ -6,8 +6,10 @@
 // point serves them: the caller passes inputs and outputs, and every scratch
 // vector lives in one file-scope device array of fixed size, reserved by every
 // GPU that loads the library until the process exits.
+#include <cuda.h>   // driver types only: the two driver calls below are looked up at run time
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include "mqs_kernels.h"
 
 using namespace mqs;
@@ -27,9 +29,24 @@ constexpr long long kScratchDoubles = kOffTail + 8;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-// scratch address per device, filled once with that device current
-constexpr int kMaxDevices = 64;
-static double* s_addr[kMaxDevices] = {};
+// The scratch array's device address, looked up once per CUDA context (the set-up of
+// this entry point) with that context's device current.  Keyed by the driver's
+// context ID, which is unique for the life of the process: after a device reset
+// the primary context is a new one, so the address is looked up again instead of
+// reusing one that may have moved.  The table is guarded by a mutex (host threads
+// may make their first calls at the same time).
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  double* addr;
+};
+constexpr int kMaxContexts = 64;
+std::mutex s_mu;
+ScratchSlot s_slots[kMaxContexts];
+int s_used = 0, s_next = 0;
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn s_get_current = nullptr;
+CtxGetIdFn s_get_id = nullptr;
 
 // bit c of flags[pos] set iff edge (c; pos) touches a conducting cell
 __global__ void cell_flags_kernel(int n, const uint8_t* cell, uint8_t* flags) {
@@ -61,20 +78,53 @@ __global__ void prepare_kernel(Geom g, const double* b, double* bs, double* x, d
   }
 }
 
-int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return MQS_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return MQS_ERR_ARG;
-  if (!s_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      fprintf(stderr, "mqs_pcg_solve_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+// ID of the calling thread's current context; the runtime creates the device's
+// primary context first if there is none yet.
+int current_context(unsigned long long* id) {
+  if (!s_get_current || !s_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1{}, q2{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      fprintf(stderr, "mqs_pcg_solve_noalloc: the driver does not provide cuCtxGetCurrent / cuCtxGetId\n");
       return MQS_ERR_CUDA;
     }
-    s_addr[dev] = static_cast<double*>(p);
+    s_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    s_get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = s_addr[dev];
+  CUcontext ctx = nullptr;
+  if (s_get_current(&ctx) != CUDA_SUCCESS) return MQS_ERR_CUDA;
+  if (!ctx) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return MQS_ERR_CUDA;
+    if (s_get_current(&ctx) != CUDA_SUCCESS || !ctx) return MQS_ERR_CUDA;
+  }
+  return s_get_id(ctx, id) == CUDA_SUCCESS ? MQS_OK : MQS_ERR_CUDA;
+}
+
+// The scratch address in the current context (set-up on the first call in it).
+int scratch_address(double** out) {
+  std::lock_guard<std::mutex> lock(s_mu);
+  unsigned long long id = 0;
+  const int rc = current_context(&id);
+  if (rc != MQS_OK) return rc;
+  for (int q = 0; q < s_used; ++q)
+    if (s_slots[q].ctx_id == id) {
+      *out = s_slots[q].addr;
+      return MQS_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    fprintf(stderr, "mqs_pcg_solve_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+    return MQS_ERR_CUDA;
+  }
+  ScratchSlot& slot = s_used < kMaxContexts ? s_slots[s_used++] : s_slots[s_next++ % kMaxContexts];
+  slot.ctx_id = id;
+  slot.addr = static_cast<double*>(p);
+  *out = slot.addr;
   return MQS_OK;
 }
 
@@ -109,7 +159,11 @@ extern "C" int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t*
   dg.g.n3 = (long long)n * n * n;
   for (int a = 0; a < 3; ++a) { dg.g.cb_lo[a] = 0; dg.g.cb_hi[a] = n; }
   dg.g.cflags = flags;
-  const int eb = 2 * 152;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MQS_ERR_CUDA;
+  const int eb = 2 * nsm;   // element-wise helpers: two blocks per SM
   cell_flags_kernel<<<eb, 256, 0, st>>>(n, cell_mask_dev, flags);
   prepare_kernel<<<eb, 256, 0, st>>>(dg.g, b_dev, base + kOffB, x_dev, h / nu0);
   if (cudaGetLastError() != cudaSuccess) return MQS_ERR_CUDA;

@@ -48,8 +48,13 @@ def test_noalloc_matches_pcg_solve_twice(env, N):
         x_ref, info_ref = s.pcg_solve(b_l, tol=1e-10)
         b = torch.tensor(b_l, device="cuda")
         x = torch.zeros(3 * N ** 3, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         rc, info = noalloc(N, p.h, p.nu0, mask, b, x, tol=1e-10)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call (which loaded the module), a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
         assert rc == 0 and info.status == 0 and info.relres <= 1e-10, (call, rc, info.status)
         assert abs(info.iterations - info_ref.iterations) <= 3
         xg = x.cpu().numpy()
