@@ -48,7 +48,15 @@ def workload_name(p):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FLOPS_PER_ITER = 16                                   # stencil 6 adds + 5 FMAs, per unknown
 FLOPS_PER_RESIDUAL = 9                                # stencil 6 + subtract 1 + FMA 2, per unknown
-BYTES_PER_ITER = 48                                   # x, r, p read and written once, per unknown
+# algorithmic bytes per unknown and PCG iteration: x, r, p read and written once, at the
+# value size of the iteration's vectors (FP64 and float-float: 8 B; FP32 inner CG: 4 B)
+BYTES_PER_ITER = {0: 48, 1: 24, 2: 48}
+PRECISION_NAMES = {
+    0: "FP64 (PCG, stencil, conductor update, residuals); SPE difference table, its Galerkin products and "
+       "x0 = D y in float-float (FP32 pairs, about 48 bits)",
+    1: "FP32 inner CG in FP64 refinement (FP64 residual, update and stopping test); SPE table in float-float",
+    2: "float-float inner CG in FP64 refinement (FP64 residual, update and stopping test); SPE table in "
+       "float-float"}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2070 MHz
 # DRAM bytes (read + write) per launch of the PCG kernel on the 64^3 iron workload, from one
 # ncu capture of the current kernel build; keyed by (precision, pcg_variant).  The carried
@@ -65,20 +73,24 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------------------
-def oracle_sample(steps: int, budget_s: float):
-    """Time the FP64 oracle on the same workload (first `steps` steps, SPE
-    depth 8, tol 1e-10), stopping early once `budget_s` seconds are used."""
+def oracle_sample(warmup: int, steps: int, budget_s: float, dt: float):
+    """Time the FP64 oracle on the workload: `warmup` untimed explicit Euler steps from
+    rest, then up to `steps` timed ones (SPE depth 8, tol 1e-10, step dt), stopping early
+    once `budget_s` seconds of timed steps are used: the steps the GPU arm times."""
     import numpy as np
     import oracle as O
     import workloads as W
     p = W.config_nonlinear_iron()
     t0 = time.perf_counter()
     d = O.Discretization(p)
-    dt = O.dt_gershgorin(d)
     setup = time.perf_counter() - t0
     hist, a_c, its, done = [], None, [], 0
+    for m in range(warmup):
+        r = O.run_explicit_euler(d, dt, 1, start_mode=O.stepper.START_SPE, spe_depth=8, tol=1e-10,
+                                 a_c0=a_c, m0=m, history=hist)
+        a_c = r.a_c
     t1 = time.perf_counter()
-    for m in range(steps):
+    for m in range(warmup, warmup + steps):
         r = O.run_explicit_euler(d, dt, 1, start_mode=O.stepper.START_SPE, spe_depth=8, tol=1e-10,
                                  a_c0=a_c, m0=m, history=hist)
         a_c = r.a_c
@@ -87,18 +99,58 @@ def oracle_sample(steps: int, budget_s: float):
         if time.perf_counter() - t1 > budget_s:
             break
     el = time.perf_counter() - t1
-    return {"steps_per_s": done / el, "steps": done, "seconds": el, "setup_s": setup,
-            "iters_per_step": float(np.mean(its)), "threads": 1}
+    return {"steps_per_s": done / el, "steps": done, "first_step": warmup + 1, "seconds": el, "setup_s": setup,
+            "iters_per_step": float(np.mean(its)), "threads": 1, "dt": dt}
 
 
-def run_oracle_subprocess(steps, budget_s):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(steps),
-                          "--oracle-budget", str(budget_s)], capture_output=True, text=True, env=env,
+def oracle_cmd(warmup, steps, budget_s, dt):
+    return [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(steps), "--oracle-warmup",
+            str(warmup), "--oracle-budget", str(budget_s), "--oracle-dt", repr(dt)]
+
+
+ORACLE_ENV = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def run_oracle_subprocess(warmup, steps, budget_s, dt):
+    """One single-thread oracle sample in a fresh interpreter (nothing forked from a
+    process that holds a CUDA context)."""
+    res = subprocess.run(oracle_cmd(warmup, steps, budget_s, dt), capture_output=True, text=True, env=ORACLE_ENV,
                          cwd=ROOT)
     if res.returncode != 0:
         raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
     return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_all_cores(warmup, steps, budget_s, dt):
+    """The same single-thread oracle sample in one fresh interpreter per host core, all at
+    once: the host's aggregate oracle throughput (independent trajectories; the oracle's
+    sparse products do not scale over threads within one trajectory)."""
+    cores = host_cores()
+    procs = [subprocess.Popen(oracle_cmd(warmup, steps, budget_s, dt), stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=ORACLE_ENV, cwd=ROOT) for _ in range(cores)]
+    outs = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    return {"value": sum(o["steps_per_s"] for o in outs), "cores": cores, "processes": cores,
+            "per_process_steps_per_s": [o["steps_per_s"] for o in outs], "steps_each": outs[0]["steps"]}
+
+
+def reference_dt():
+    """The workload's step 0.9 * 2 / lambda_max with lambda_max from the oracle's power
+    method (stored by tests/golden/make_golden.py --iron64)."""
+    with open(os.path.join(ROOT, "tests", "golden", "nonlinear_iron_64.json")) as f:
+        g = json.load(f)
+    return g["dt"], g["lambda_max"]
 
 
 # ----------------------------------------------------------------------------------------
@@ -188,23 +240,29 @@ def barrier(dist, device=None):
 
 # ----------------------------------------------------------------------------------------
 def run_reference(args, rank, ws, dist):
+    """The FP64 oracle on the host cores, on the GPU arm's workload, step and step range:
+    warm-up steps untimed, then the timed steps (bounded by --reference-budget seconds),
+    one thread; the line's `value` is that single-trajectory rate."""
     if rank != 0:
         return
-    total = args.warmup + args.steps
+    dt, lam = reference_dt()
     budget = float(args.reference_budget)
-    s = oracle_sample(total, budget)
-    cores = 1
+    s = run_oracle_subprocess(args.warmup, args.steps, budget, dt)
+    sample = (f"explicit Euler steps {s['first_step']}..{s['first_step'] + s['steps'] - 1} of the workload from "
+              f"rest (the steps the GPU arm times; {args.warmup} untimed warm-up steps before them), "
+              f"dt {dt:.6e} s, SPE 8, tol 1e-10, one host thread, setup {s['setup_s']:.1f} s excluded"
+              + ("" if s["steps"] == args.steps else f"; stopped after {s['steps']} of {args.steps} steps "
+                 f"at the {budget:.0f} s budget"))
     line = {"impl": "reference", "metric": METRIC, "value": s["steps_per_s"], "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / s["steps_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": 64, "start_vector": "spe8", "tol": 1e-10},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": 64, "start_vector": "spe8", "tol": 1e-10, "dt_s": dt,
+                       "lambda_max": lam, "dt_from": "0.9 * 2 / lambda_max, oracle power method",
+                       "steps_timed": s["steps"], "first_step": s["first_step"]},
             "iters_per_step": s["iters_per_step"],
-            "cpu_baseline": {"value": s["steps_per_s"], "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {s['steps']} explicit Euler steps of the workload timed "
-                                       f"(of the {total} = warm-up + steps requested, {budget:.0f} s budget), "
-                                       f"single thread, setup {s['setup_s']:.1f} s excluded; these early "
-                                       f"steps take {s['iters_per_step']:.1f} PCG iterations per step while "
-                                       f"the SPE history fills"},
+            "cpu_baseline": {"value": s["steps_per_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": s["steps_per_s"], "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -269,6 +327,10 @@ def other_arithmetic(args, p, dt, stream, flush, dev):
 
 
 def run_ours(args, rank, ws, local, dist):
+    # the batched measurement spreads its problems over 32 streams; CUDA maps streams onto
+    # this many hardware queues (read when the context is created)
+    if args.batch_sub > 0:
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import numpy as np
     import torch
     import __graft_entry__ as g
@@ -337,24 +399,40 @@ def run_ours(args, rank, ws, local, dist):
             graph["value"] = ws * args.steps / (reduce_max(graph.pop("ms"), dist, dev) * 1e-3)
     ms_max = reduce_max(ms, dist, dev)
     value = ws * args.steps / (ms_max * 1e-3)
-    # end to end through the host C ABI: a_c in from pinned memory, step, a_c out
+    # end to end through the host C ABI over the same steps: from rest, the same warm-up,
+    # then each timed step with its state in from pinned host memory and out again, L2
+    # flushed before each (outside its host-timed span)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e:
         a_host = torch.empty(s.n_c, dtype=torch.float64, pin_memory=True).numpy()
-        a_cur, t_cur, m_cur = s.get_state()
-        a_host[:] = a_cur
-        torch.cuda.synchronize(dev)
-        barrier(dist, dev)
-        t1 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            s.set_state(a_host, t_cur, m_cur)
-            s.step(1, allow_fail=True)
-            a_new, t_cur, m_cur = s.get_state()
-            a_host[:] = a_new
-        el = time.perf_counter() - t1
+        s.set_state(np.zeros(s.n_c), 0.0, 0)
+        s.reset_history()
+        with torch.cuda.stream(stream):
+            if args.warmup:
+                s.step(args.warmup)
+            a_cur, t_cur, m_cur = s.get_state()
+            a_host[:] = a_cur
+            torch.cuda.synchronize(dev)
+            barrier(dist, dev)
+            el, e2e_its = 0.0, []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t1 = time.perf_counter()
+                s.set_state(a_host, t_cur, m_cur)
+                _, st1 = s.step(1, allow_fail=True)
+                a_new, t_cur, m_cur = s.get_state()
+                a_host[:] = a_new
+                el += time.perf_counter() - t1
+                e2e_its.append(st1[0].iterations)
         el_max = reduce_max(el, dist, dev)
-        e2e = {"value": ws * args.e2e_steps / el_max, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.n_c,
-               "d2h_bytes_per_step": 8 * s.n_c + 48, "steps": args.e2e_steps}
+        e2e = {"value": ws * args.steps / el_max, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.n_c,
+               "d2h_bytes_per_step": 8 * s.n_c + 48, "steps": args.steps,
+               "iters_per_step": float(np.mean(e2e_its)),
+               "same_iterations": e2e_its == list(iters),
+               "note": "the timed steps again from rest after the same warm-up, each through the host C ABI "
+                       "(mqs_set_state from pinned memory, mqs_step, mqs_get_state), host wall clock per step, "
+                       "L2 flushed before each step outside its span"}
     n_n = s.n_n
     its = np.array(iters)
     flops = n_n * (FLOPS_PER_ITER * its.sum() + 2 * FLOPS_PER_RESIDUAL * len(its))
@@ -377,15 +455,14 @@ def run_ours(args, rank, ws, local, dist):
                 "traffic": traffic,
                 "note": "inner iterations (FP32 or float-float) against the FP32 issue peak (152 SM x 128 FMA/clk"
                         " x 2 x 2070 MHz); the inner iteration is latency and grid-barrier bound"}
-    hbm = n_n * BYTES_PER_ITER * its.sum() / (tm["ms_pcg"] * 1e-3) / 1e9
+    hbm = n_n * BYTES_PER_ITER[args.precision] * its.sum() / (tm["ms_pcg"] * 1e-3) / 1e9
     peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f32+f64", 2: "ff+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_name(p), "grid": p.N, "n_unknowns": int(n_n), "n_conducting": int(s.n_c),
-                       "precision": {0: "FP64", 1: "FP32 inner CG in FP64 refinement",
-                                     2: "float-float inner CG in FP64 refinement"}[args.precision],
+                       "precision": PRECISION_NAMES[args.precision],
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
                                        + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
                        "tol": 1e-10, "eps_lin": args.eps_lin, "dt_s": dt, "lambda_max": lam,
@@ -402,7 +479,9 @@ def run_ours(args, rank, ws, local, dist):
             "roofline": roof,
             "stencil_hbm_view": {"algorithmic_GBps": hbm, "peak_GBps": peaks.get("hbm_gbs"),
                                  "frac": hbm / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                                 "note": "48 B/unknown/iteration; the 64^3 PCG working set is L2-resident"},
+                                 "note": f"{BYTES_PER_ITER[args.precision]} B/unknown/iteration (x, r, p read "
+                                         "and written once)" + ("; the 64^3 PCG working set is L2-resident"
+                                                                if p.N <= 64 else "")},
             "clocks": clk, "gpu_launches": int(tm["launches"]), "pcg_launches": int(tm["pcg_launches"]),
             "failed_steps": int(sum(1 for x in statuses if x != 0)),
             "setup": {"power_iterations": pit, "seconds": setup_s}}
@@ -417,17 +496,32 @@ def run_ours(args, rank, ws, local, dist):
             **other_arithmetic(args, p, dt, stream, flush, dev)}
     if rank == 0 and ws == 1 and not args.no_cpu and args.grid == 64:
         try:
-            c = run_oracle_subprocess(args.cpu_steps, args.cpu_budget)
-            line["cpu_baseline"] = {"value": c["steps_per_s"], "unit": "steps/s", "cores": c["threads"],
-                                    "kind": "oracle",
-                                    "sample": f"first {c['steps']} explicit Euler steps of the same workload "
-                                              f"(SPE 8, tol 1e-10) on one host thread, setup excluded"}
+            c = run_oracle_subprocess(args.warmup, args.steps, args.cpu_budget, dt)
+            line["cpu_baseline"] = {
+                "value": c["steps_per_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                "dt_s": dt, "iters_per_step": c["iters_per_step"],
+                "sample": f"explicit Euler steps {c['first_step']}..{c['first_step'] + c['steps'] - 1} of the same "
+                          f"workload (the steps timed above, {args.warmup} untimed warm-up steps before them), "
+                          f"this line's dt, SPE 8, tol 1e-10, one host thread, setup excluded"}
+            if args.cpu_all_cores:
+                allc = run_oracle_all_cores(args.warmup, min(args.steps, 4), args.cpu_budget, dt)
+                line["cpu_baseline"]["all_cores"] = {
+                    "value": allc["value"], "unit": "steps/s", "cores": allc["cores"],
+                    "sample": f"one single-thread oracle process per host core ({allc['processes']}), each "
+                              f"stepping the same workload from rest and timing steps {args.warmup + 1}.."
+                              f"{args.warmup + allc['steps_each']}: the host's aggregate throughput over "
+                              f"independent trajectories"}
         except Exception as e:  # the GPU line is still valid without it
             line["cpu_baseline"] = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {e}"[:200]}
+    s.close()
+    if ws == 1 and args.batch_sub > 0:
+        try:
+            line["batch"] = batch_sub(args, dev)
+        except Exception as e:  # the headline stays valid without it
+            line["batch"] = {"failed": f"{e}"[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
 
 
 def coil_rhs(p, amp=100.0):
@@ -613,6 +707,78 @@ def run_batch(args):
         s.close()
 
 
+def batch_sub(args, dev):
+    """Batched multi-query beside the headline (the workload of the batched configuration,
+    shortened): `args.batch_sub` seeded instances (N from {32, 40, 48, 64}, sigma ~
+    U[1e6, 5e6] S/m, 100-1000 A, Brauer iron, SPE 8) advanced together with FP32 inner
+    solves in FP64 refinement (every solve to the FP64 true residual 1e-10), the block
+    scale tuned during the warm-up, then `args.batch_sub_steps` timed batch steps (device
+    time from the fork of the batch streams to their join).  Beside it, the same instances
+    in the plain single-instance FP64 form: each alone on the whole GPU, from rest, the
+    same warm-up and the same timed steps (device time of each)."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    probs = W.batched_instances(args.batch_sub, sizes=(32, 40, 48, 64))
+    t0 = time.perf_counter()
+    lam_ref = {}
+    for n in sorted({p.N for p in probs}):
+        s = pkg.Solver.from_problem(W.scaled_nonlinear(n), pkg.SolverOptions(tol=1e-10))
+        lam_ref[n], _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=args.power_maxit)
+        s.close()
+    opts, solvers = [], []
+    for p in probs:
+        lam = lam_ref[p.N] * 2.0e6 / float(p.sigma_cell.max())       # M_c scales with sigma
+        o = pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8, precision=1, pcg_variant=1,
+                              dt=0.9 * 2.0 / lam, graph=1)
+        opts.append(o)
+        solvers.append(pkg.Solver.from_problem(p, o))
+    setup_s = time.perf_counter() - t0
+    trial = 2
+    batch = pkg.Batch(solvers)
+    scale = batch.tune(trial)                       # 4 x trial warm-up steps
+    extra = max(args.batch_sub_warmup - 4 * trial, 0)
+    if extra:
+        batch.step(extra)
+    warm = 4 * trial + extra
+    rc, stats = batch.step(args.batch_sub_steps, allow_fail=True)
+    ms = batch.last_ms()
+    batch.close()
+    its = np.array([[x.iterations for x in row] for row in stats], dtype=float)
+    failed = int(sum(1 for row in stats for x in row if x.status != 0))
+    value = len(solvers) * args.batch_sub_steps / (ms * 1e-3)
+    stream = torch.cuda.Stream(device=dev)
+    per_ms, its64 = [], []
+    for sv, o in zip(solvers, opts):
+        sv.set_options(dataclasses.replace(o, precision=0, pcg_variant=0))
+        sv.set_state(np.zeros(sv.n_c), 0.0, 0)
+        sv.reset_history()
+        sv.set_stream(stream.cuda_stream)
+        sv.step(warm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st64 = sv.step(args.batch_sub_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        per_ms.append(e0.elapsed_time(e1))
+        its64.extend(x.iterations for x in st64)
+        sv.set_stream(0)
+        sv.close()
+    single = len(solvers) * args.batch_sub_steps / (sum(per_ms) * 1e-3)
+    sizes = {n: sum(1 for p in probs if p.N == n) for n in sorted({p.N for p in probs})}
+    return {"value": value, "unit": "instance-steps/s", "instances": len(solvers), "count_per_N": sizes,
+            "n_unknowns": int(sum(p_n for p_n in (sv.n_n for sv in solvers))),
+            "steps": args.batch_sub_steps, "first_step": warm + 1, "ms": ms,
+            "precision": "FP32 inner CG in FP64 refinement (FP64 true residual 1e-10 per solve)",
+            "blocks_scale": scale, "inner_iters_per_step": float(its.mean()), "failed_steps": failed,
+            "single_instance_fp64": {"value": single, "unit": "instance-steps/s",
+                                     "iters_per_step": float(np.mean(its64)),
+                                     "note": "each instance alone on the whole GPU, FP64 PCG, the same steps"},
+            "speedup_vs_single_instance_fp64": value / single, "setup_s": setup_s}
+
+
 def adjoint_fd_check(args, p, fresh):
     """Central differences of J (solves at tol 1e-12) against the adjoint gradient:
     random iron cells with a gradient of at least 1% of the largest, and the coil
@@ -747,11 +913,13 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false",
+                    help="skip the end-to-end host C ABI timing of the same steps")
     ap.add_argument("--power-maxit", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=4)
-    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--cpu-budget", type=float, default=40.0, help="seconds of timed oracle steps at most")
+    ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
+                    help="skip the all-core oracle throughput")
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per PCG launch, if measured")
     ap.add_argument("--start", choices=["zero", "prev", "spe", "pod", "cspe"], default="spe",
@@ -779,6 +947,10 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
     ap.add_argument("--sweep", type=str, default="",
                     help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
+    ap.add_argument("--batch-sub", type=int, default=64,
+                    help="instances of the short batched measurement added to the line (0: skip)")
+    ap.add_argument("--batch-sub-steps", type=int, default=20, help="timed steps of that batch")
+    ap.add_argument("--batch-sub-warmup", type=int, default=10, help="its warm-up steps (tuning included)")
     ap.add_argument("--batch", type=int, default=0,
                     help="advance this many seeded multi-query instances together (batched mode)")
     ap.add_argument("--tune-depth", action="store_true",
@@ -794,9 +966,12 @@ def main():
                     help="run one zero-start PCG solve of the workload twice (profiling)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=25.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-warmup", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-dt", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.oracle_sample, args.oracle_budget)), flush=True)
+        print(json.dumps(oracle_sample(args.oracle_warmup, args.oracle_sample, args.oracle_budget, args.oracle_dt)),
+              flush=True)
         return
     if args.single_solve:
         single_solve()

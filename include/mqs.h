@@ -60,6 +60,8 @@ extern "C" {
 #define MQS_ERR_UNSTABLE       -7   /* explicit Euler state blew up        */
 #define MQS_ERR_TIMEOUT        -8   /* a bounded device wait gave up       */
 #define MQS_ERR_UNIMPLEMENTED  -9
+#define MQS_ERR_HALTED        -10   /* step not run: an earlier step of the
+                                       same call failed                    */
 
 #define MQS_START_ZERO 0            /* x0 = 0                              */
 #define MQS_START_PREV 1            /* x0 = solution of the previous step  */
@@ -70,8 +72,10 @@ extern "C" {
 
 typedef struct mqs_handle mqs_handle;
 
-/* Grid: n cells per axis (2 <= n <= 800), spacing h metres. */
-typedef struct { int n; double h; } mqs_grid;
+/* Grid: nx x ny x nz cells of spacing h metres.  This build runs cubic grids,
+ * nx = ny = nz = n with 2 <= n <= 800 (every kernel indexes one n for all three
+ * axes); other shapes return MQS_ERR_UNIMPLEMENTED from mqs_setup. */
+typedef struct { int nx, ny, nz; double h; } mqs_grid;
 
 /* Materials.  sigma_cell: n^3 conductivities (S/m, >= 0).  brauer_cell:
  * n^3 flags (1 = reluctivity nu(B) = k1 exp(k2 B^2) + k3, else nu0), or
@@ -98,7 +102,8 @@ typedef struct {
  * residual).  maxit: PCG iteration cap.  start_mode: MQS_START_*.
  * spe_depth (1..16; CSPE 1..19), pod_snapshots (1..40), eps_pod (POD truncation
  * sigma_i/sigma_1 >= eps_pod, eq. (relSV2)), eps_lin (SPE drop tolerance).
- * dt: explicit Euler step (s); may be set later with mqs_set_dt.
+ * dt: explicit Euler step (s); may be set later with mqs_set_dt.  With dt <= 0
+ * and cfl_factor > 0, mqs_setup sets it from eq. (CFL) (see cfl_factor).
  * rhs_time: 0 = source at t_m (as printed in eq. (acm)), 1 = at t_{m-1}.
  * pcg_variant: see the field. */
 typedef struct {
@@ -159,6 +164,27 @@ typedef struct {
                              default of a zeroed struct; the Python binding's
                              SolverOptions defaults to 1): every step launch
                              by launch. */
+    double cfl_factor;    /* eq. (CFL): with dt <= 0 and cfl_factor > 0, mqs_setup
+                             runs the power method of mqs_lambda_max (PCG tol 1e-12,
+                             stop at |dlambda| < 1e-8 lambda or 2000 iterations; its
+                             start vector is the library's own: uniform numbers in
+                             [-1, 1) from the SplitMix64 generator, seed 1611) and
+                             sets dt = cfl_factor * 2 / lambda_max (0.9 in the
+                             paper's setting); mqs_get_dt returns lambda_max.  0
+                             (a zeroed struct): dt stays unset until mqs_set_dt. */
+    int    monitor_steps; /* instability monitor of the explicit Euler update
+                             (eq. (CFL) violated): a step fails with
+                             MQS_ERR_UNSTABLE once the M_c-energy of the state
+                             increment a^m - a^{m-1} has grown, with the sign of
+                             the increment alternating (M_c-inner product of
+                             successive increments < 0), over monitor_steps
+                             consecutive steps (above 1e-20 of the largest
+                             increment energy seen), or when the state is not
+                             finite.  That is the signature of the explicit Euler
+                             factor 1 - dt lambda < -1 of the top mode; stable
+                             steps (|1 - dt lambda| <= 1 for every mode) shrink the
+                             alternating part instead.  0: 8 steps; < 0: off (the
+                             non-finite test stays). */
 } mqs_options;
 
 typedef struct {
@@ -210,9 +236,12 @@ int mqs_last_error(const mqs_handle* h, char* buf, size_t len);
 
 int mqs_layout(const mqs_handle* h, mqs_layout_info* info);
 
-/* mqs_set_dt / mqs_get_dt: the explicit Euler step (eq. (acm)). */
+/* mqs_set_dt / mqs_get_dt: the explicit Euler step (eq. (acm)).  mqs_get_dt
+ * also returns (lambda_max, nullable) the largest eigenvalue of M_c^-1 K_S(0)
+ * of eq. (CFL) found on this handle (by mqs_setup with cfl_factor, or the last
+ * mqs_lambda_max), 0 if none was computed.  dt (nullable) is 0 while unset. */
 int mqs_set_dt(mqs_handle* h, double dt);
-int mqs_get_dt(const mqs_handle* h, double* dt);
+int mqs_get_dt(const mqs_handle* h, double* dt, double* lambda_max);
 
 /* mqs_set_options: replaces tol, maxit, start_mode, spe_depth,
  * pod_snapshots, eps_pod, eps_lin, rhs_time (dt is kept unless > 0).
@@ -234,8 +263,14 @@ int mqs_lambda_max(mqs_handle* h, const double* v0, double pcg_tol,
  *   w   = PCG(K_n, b, x0)                    (= a_n, eq. (a_n))
  *   a_c = a_c - dt M_c^-1 (K(a)[a_c; w])_c   (Brauer nu re-evaluated per cell)
  * then w and K_n w join the start-vector history.  per_step: host array of
- * nsteps records or NULL.  Returns the first non-OK step status (the step
- * loop still completes), MQS_ERR_ARG if dt is unset. */
+ * nsteps records or NULL.  The loop stops at the first failing step (a PCG
+ * status other than MQS_OK, a timed-out device wait, or MQS_ERR_UNSTABLE from
+ * the instability monitor, see mqs_options.monitor_steps): on the device, every
+ * later step of the call skips its solve and its conductor update, and its
+ * record carries MQS_ERR_HALTED.  The handle is then left at the last step that
+ * succeeded: a_c, t and m as after that step (the failing step's update is
+ * discarded), with an empty start-vector history.  Returns the failing step's
+ * status (MQS_OK if none), MQS_ERR_ARG if dt is unset. */
 int mqs_step(mqs_handle* h, int nsteps, mqs_step_stats* per_step);
 
 /* mqs_step in two halves.  mqs_step_enqueue issues the launches of nsteps

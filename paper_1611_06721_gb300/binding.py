@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmqs.so")
 MQS_OK = 0
 ERRORS = {-1: "MQS_ERR_ARG", -2: "MQS_ERR_CUDA", -3: "MQS_ERR_OOM", -4: "MQS_ERR_NOT_CONVERGED",
           -5: "MQS_ERR_BREAKDOWN", -6: "MQS_ERR_NAN", -7: "MQS_ERR_UNSTABLE", -8: "MQS_ERR_TIMEOUT",
-          -9: "MQS_ERR_UNIMPLEMENTED"}
+          -9: "MQS_ERR_UNIMPLEMENTED", -10: "MQS_ERR_HALTED"}
 START_ZERO, START_PREV, START_SPE, START_POD, START_CSPE = 0, 1, 2, 3, 4
 
 EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_dt", "mqs_get_dt",
@@ -35,7 +35,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
 
 
 class Grid(C.Structure):
-    _fields_ = [("n", C.c_int), ("h", C.c_double)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double)]
 
 
 class Materials(C.Structure):
@@ -52,7 +52,8 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("start_mode", C.c_int), ("spe_depth", C.c_int),
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int), ("graph", C.c_int)]
+                ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int), ("graph", C.c_int),
+                ("cfl_factor", C.c_double), ("monitor_steps", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -102,7 +103,7 @@ def load():
         "mqs_last_error": ([H, C.c_char_p, C.c_size_t], I),
         "mqs_layout": ([H, P(LayoutInfo)], I),
         "mqs_set_dt": ([H, D], I),
-        "mqs_get_dt": ([H, P(D)], I),
+        "mqs_get_dt": ([H, P(D), P(D)], I),
         "mqs_set_options": ([H, P(Options)], I),
         "mqs_lambda_max": ([H, P(D), D, D, I, P(D), P(I)], I),
         "mqs_step": ([H, I, P(StepStats)], I),
@@ -216,11 +217,14 @@ class SolverOptions:
     cspe_period: int = 0
     rhs_split: int = 0
     graph: int = 1          # steady-state SPE steps from CUDA graphs (bitwise the same results)
+    cfl_factor: float = 0.0  # > 0 with dt <= 0: setup sets dt = cfl_factor * 2 / lambda_max (eq. (CFL))
+    monitor_steps: int = 0   # instability monitor window (0: 8 steps; < 0: finiteness test only)
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
-                       self.inner_tol, self.cspe_period, self.rhs_split, self.graph)
+                       self.inner_tol, self.cspe_period, self.rhs_split, self.graph, self.cfl_factor,
+                       self.monitor_steps)
 
 
 class Solver:
@@ -240,7 +244,7 @@ class Solver:
             mask = self._mask.ctypes.data_as(C.POINTER(C.c_uint8))
         self.options = options
         h_ = C.c_void_p()
-        rc = self.lib.mqs_setup(C.byref(Grid(n, h)), C.byref(mat), mask, C.byref(Coil(*coil)),
+        rc = self.lib.mqs_setup(C.byref(Grid(n, n, n, h)), C.byref(mat), mask, C.byref(Coil(*coil)),
                                 C.byref(options.c()), C.byref(h_))
         if rc != MQS_OK:
             raise MqsError(rc, "mqs_setup failed (see stderr)")
@@ -285,9 +289,13 @@ class Solver:
         self._check(self.lib.mqs_set_dt(self.h, dt))
 
     def get_dt(self):
-        d = C.c_double()
-        self._check(self.lib.mqs_get_dt(self.h, C.byref(d)))
-        return d.value
+        return self.dt_lambda()[0]
+
+    def dt_lambda(self):
+        """(dt, lambda_max of eq. (CFL) found on this handle, 0 if none) (mqs_get_dt)."""
+        d, lam = C.c_double(), C.c_double()
+        self._check(self.lib.mqs_get_dt(self.h, C.byref(d), C.byref(lam)))
+        return d.value, lam.value
 
     def set_options(self, options: SolverOptions):
         self._check(self.lib.mqs_set_options(self.h, C.byref(options.c())))

@@ -2,6 +2,8 @@
 // the stand-alone entry points declared in include/mqs.h.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <cstdint>
 #include <new>
 #include <cstdio>
 #include <cstring>
@@ -59,6 +61,12 @@ struct mqs_handle {
   unsigned* bar = nullptr;
   int* derr = nullptr;
   PcgResult* pres = nullptr;
+  // halt flag and instability monitor of stepping calls; where the current call began
+  StepGuard* guard = nullptr;
+  double* mon_part = nullptr;
+  long call_m0 = 0;
+  double *call_ac0 = nullptr, *call_full0 = nullptr;
+  double lambda = 0.0;       // lambda_max of eq. (CFL) found on this handle (0: none)
   double* spe_D[kMaxSpe] = {};
   double* spe_LD[kMaxSpe] = {};
   int spe_m = 0;
@@ -217,16 +225,27 @@ __global__ void power_update_kernel(int n_c, const double* F, const double* isq,
 // began marks the step failed (the timed-out kernel did not write its result).  With
 // the step counter ctr the record goes to dst[ctr[1]] and the counter advances one
 // step; without it, to *dst.
+// With the step guard gd: a step of a halted call is recorded as MQS_ERR_HALTED; a
+// step whose solve succeeded takes the instability monitor's verdict; a failing step
+// halts the call.
 __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                              const int* derr, mqs_step_stats* dst, long long* ctr) {
+                              const int* derr, mqs_step_stats* dst, long long* ctr, StepGuard* gd) {
   if (ctr) {
     dst += ctr[1];
     ctr[0] += 1;
     ctr[1] += 1;
   }
   mqs_step_stats s;
+  if (gd && gd->halt) {
+    *dst = mqs_step_stats{0, MQS_ERR_HALTED, 0, 0, 0.0, 0.0, 0.0};
+    return;
+  }
   s.iterations = pr->iterations;
   s.status = (*derr != 0) ? *derr : pr->status;
+  if (gd) {
+    if (s.status == MQS_OK) s.status = gd->status;
+    if (s.status != MQS_OK) gd->halt = 1;
+  }
   s.rank = use_small ? so->rank : 0;
   s.refinements = refin ? *refin : 0;
   s.relres = pr->relres;
@@ -238,16 +257,28 @@ __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_s
 // Adds a second solve of the same step (separate right-hand sides) to its record
 // (the one record_kernel wrote last: dst[ctr[1] - 1]).
 __global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                                  const int* derr, mqs_step_stats* dst, const long long* ctr) {
+                                  const int* derr, mqs_step_stats* dst, const long long* ctr, StepGuard* gd) {
   dst += ctr[1] - 1;
   mqs_step_stats s = *dst;
+  if (s.status == MQS_ERR_HALTED) return;
   s.iterations += pr->iterations;
   if (s.status == MQS_OK) s.status = (*derr != 0) ? *derr : pr->status;
+  if (s.status != MQS_OK) gd->halt = 1;
   s.rank += use_small ? so->rank : 0;
   s.refinements += refin ? *refin : 0;
   s.relres = fmax(s.relres, pr->relres);
   s.start_relres = fmax(s.start_relres, pr->start_relres);
   *dst = s;
+}
+
+// Separate right-hand sides record their solves before the conductor update: its
+// monitor verdict joins the step's record afterwards.
+__global__ void record_mon_kernel(StepGuard* gd, mqs_step_stats* dst, const long long* ctr) {
+  dst += ctr[1] - 1;
+  if (dst->status == MQS_OK && gd->status != MQS_OK) {
+    dst->status = gd->status;
+    gd->halt = 1;
+  }
 }
 
 __global__ void set_ctr_kernel(long long* ctr, long long m, long long slot) {
@@ -275,28 +306,29 @@ int ensure_mixed(mqs_handle* H) {
 }
 
 // the PCG kernel selected by opt.precision and opt.pcg_variant
-int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init) {
+int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init,
+               const int* halt = nullptr) {
   if (H->opt.precision == 2) {
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-12;
     return launch_pcg_ff(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                         maxit, H->nblk, st, init);
+                         maxit, H->nblk, st, init, halt);
   }
   if (H->opt.precision == 1) {
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-5;
     return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                            maxit, H->nblk, st, init, H->opt.pcg_variant);
+                            maxit, H->nblk, st, init, H->opt.pcg_variant, halt);
   }
   if (H->opt.pcg_variant == 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
-                            H->nblk, st, init);
+                            H->nblk, st, init, halt);
   }
   return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
-                    st, init);
+                    st, init, halt);
 }
 
 int run_pcg(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st) {
@@ -509,6 +541,7 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
   if (o->rhs_split != 0 && o->rhs_split != 1) { why = "rhs_split must be 0 or 1"; return MQS_ERR_ARG; }
+  if (!std::isfinite(o->cfl_factor) || o->cfl_factor < 0.0) { why = "cfl_factor must be >= 0"; return MQS_ERR_ARG; }
   if (o->rhs_split && o->start_mode != MQS_START_ZERO && o->start_mode != MQS_START_SPE) {
     why = "rhs_split needs the zero or the SPE start";
     return MQS_ERR_ARG;
@@ -518,7 +551,9 @@ int validate_options(const mqs_options* o, std::string& why) {
 
 int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, const uint8_t* cmask,
              const mqs_coil* coil, const mqs_options* opts) {
-  const int n = grid->n;
+  if (grid->nx != grid->ny || grid->nx != grid->nz)
+    return fail(H, MQS_ERR_UNIMPLEMENTED, "only cubic grids (nx = ny = nz) are implemented");
+  const int n = grid->nx;
   if (n < 2 || n > 800) return fail(H, MQS_ERR_ARG, "grid n must be in [2, 800]");
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return fail(H, MQS_ERR_ARG, "grid spacing must be positive");
   if (!mat->sigma_cell) return fail(H, MQS_ERR_ARG, "sigma_cell is NULL");
@@ -661,6 +696,9 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->bar, 1));
   RK(dalloc(H, &H->derr, 1));
   RK(dalloc(H, &H->pres, 1));
+  RK(dalloc(H, &H->guard, 1));
+  RK(dalloc(H, &H->mon_part, 2 * kMonBlocks));
+  CK(cudaMemset(H->guard, 0, sizeof(StepGuard)));
   RK(dalloc(H, &H->tspart, (size_t)5 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_hpart, (size_t)4 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_gpart, (size_t)spe_gblocks() * kSpeGSlots));
@@ -777,11 +815,105 @@ int ensure_stats(mqs_handle* H, int nsteps, int keep = 0) {
 
 // conductor update for the state currently in H->ac / H->ac_full with w = x;
 // the new state goes to the other compact and layout buffers, then they swap
+// device address of the guard's halt flag (no host dereference of the device pointer)
+const int* halt_flag(const mqs_handle* H) {
+  return reinterpret_cast<const int*>(reinterpret_cast<const char*>(H->guard) + offsetof(StepGuard, halt));
+}
+
+// The instability monitor forgets its history (the other conductor buffer no longer
+// holds the state before the current one).
+int reset_monitor(mqs_handle* H) {
+  const size_t off = offsetof(StepGuard, count);
+  CK(cudaMemsetAsync(reinterpret_cast<char*>(H->guard) + off, 0, sizeof(StepGuard) - off, H->st));
+  return MQS_OK;
+}
+
+// a_c changed outside a step: b must be formed again and the monitor starts afresh
+int state_changed(mqs_handle* H) {
+  H->ac_gen += 1;
+  return reset_monitor(H);
+}
+
 int conductor_step(mqs_handle* H, const double* w, double dt, cudaStream_t st) {
-  if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st));
-  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st, H->ac_full2, H->rec_F, H->rec_a));
+  const int window = H->opt.monitor_steps == 0 ? 8 : H->opt.monitor_steps;
+  const GuardView gv{H->guard, H->mon_part, H->pres, H->derr, window};
+  if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st, halt_flag(H)));
+  RK(launch_cond_update(H->dg, H->cg, H->ac_full, w, 1.0, H->ac, H->ac2, dt, st, H->ac_full2, H->rec_F, H->rec_a,
+                        &gv));
   std::swap(H->ac, H->ac2);
   std::swap(H->ac_full, H->ac_full2);
+  return MQS_OK;
+}
+
+// eq. (CFL): power method on M_c^-1/2 K_S(0) M_c^-1/2 from v0 (n_c values, host),
+// Rayleigh quotient; every application of K_S takes one PCG solve of K_n.
+int power_method(mqs_handle* H, const double* v0, double pcg_tol, double rtol, int maxit, double* lambda_max,
+                 int* iters) {
+  if (!(pcg_tol > 0.0) || !(rtol > 0.0) || maxit < 1) return fail(H, MQS_ERR_ARG, "bad power-method settings");
+  cudaStream_t st = H->st;
+  double nv = 0.0;
+  for (long q = 0; q < H->n_c; ++q) nv += v0[q] * v0[q];
+  if (!(nv > 0.0)) return fail(H, MQS_ERR_ARG, "v0 must be nonzero");
+  std::vector<double> vn(v0, v0 + H->n_c);
+  for (double& v : vn) v /= std::sqrt(nv);
+  CK(cudaMemcpyAsync(H->cvec, vn.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->tmp, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
+  const CoilDrive nodrv{H->h / H->nu0, 0.0, 0.0, 1.0, 0.0, 0};
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  double lam = 0.0, lam_old = 0.0;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
+    power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
+    RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
+    RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->sup, H->nsup, st));
+    RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
+    // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
+    RK(launch_cell_nu(H->dg, H->cg, H->tmp, H->xu, true, st));
+    RK(launch_cond_update(H->dg, H->cg, H->tmp, H->xu, 1.0, H->cvec2, H->ac2, 0.0, st));
+    power_update_kernel<<<1, 1024, 0, st>>>((int)H->n_c, H->ac2, H->isqmc, H->cvec, H->scal + 1);
+    PcgResult pr{};
+    CK(cudaMemcpyAsync(&lam, H->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&pr, H->pres, sizeof(pr), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (pr.status != MQS_OK) return fail(H, pr.status, "PCG failed inside the power method");
+    if (it > 1 && std::fabs(lam - lam_old) < rtol * std::fabs(lam)) break;
+    lam_old = lam;
+  }
+  // the scratch a_c buffer ac2 was used (ac holds the state): the monitor's history is gone
+  RK(reset_monitor(H));
+  H->lambda = lam;
+  *lambda_max = lam;
+  if (iters) *iters = it > maxit ? maxit : it;
+  return MQS_OK;
+}
+
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014): the state advances by the golden-ratio increment and each output is a
+// mix of it by two xor-shift-multiply rounds.  Used for the library's own start vector
+// of the power method (uniform in [-1, 1)).
+uint64_t splitmix64(uint64_t& state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// dt = cfl_factor * 2 / lambda_max (eq. (CFL)) by the power method from the library's
+// own start vector, at the settings of the oracle's power method
+int setup_dt(mqs_handle* H, double cfl) {
+  std::vector<double> v0(H->n_c);
+  uint64_t state = 1611;
+  for (double& v : v0) v = 2.0 * ((double)(splitmix64(state) >> 11) * 0x1.0p-53) - 1.0;
+  double lam = 0.0;
+  int it = 0;
+  RK(power_method(H, v0.data(), 1e-12, 1e-8, 2000, &lam, &it));
+  if (!(lam > 0.0) || !std::isfinite(lam)) return fail(H, MQS_ERR_NAN, "the power method gave no positive lambda_max");
+  H->dt = cfl * 2.0 / lam;
+  CK(cudaStreamSynchronize(H->st));
   return MQS_OK;
 }
 
@@ -798,6 +930,7 @@ int mqs_setup(const mqs_grid* grid, const mqs_materials* mat, const uint8_t* con
   mqs_handle* H = new (std::nothrow) mqs_handle();
   if (!H) return MQS_ERR_OOM;
   int rc = do_setup(H, grid, mat, conductor_mask, coil, opts);
+  if (rc == MQS_OK && !(opts->dt > 0.0) && opts->cfl_factor > 0.0) rc = setup_dt(H, opts->cfl_factor);
   if (rc != MQS_OK) {
     fprintf(stderr, "mqs_setup: %s\n", H->err.c_str());
     mqs_destroy(H);
@@ -846,9 +979,10 @@ int mqs_set_dt(mqs_handle* H, double dt) {
   return MQS_OK;
 }
 
-int mqs_get_dt(const mqs_handle* H, double* dt) {
-  if (!H || !dt) return MQS_ERR_ARG;
-  *dt = H->dt;
+int mqs_get_dt(const mqs_handle* H, double* dt, double* lambda_max) {
+  if (!H) return MQS_ERR_ARG;
+  if (dt) *dt = H->dt;
+  if (lambda_max) *lambda_max = H->lambda;
   return MQS_OK;
 }
 
@@ -952,18 +1086,18 @@ int enqueue_split_step(mqs_handle* H) {
   const long nl_start = start_launches(H);
   RK(start_vector(H, H->b, H->x, st, &used_c, &init_c));
   mark(H);
-  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c));
+  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c, halt_flag(H)));
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats,
-                                 H->dctr);
+                                 H->dctr, H->guard);
   advance_ctr(H);
   RK(history_push(H, H->x, H->lx, st));
   CK(cudaMemcpyAsync(H->xc, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
   RK(swap_spe(H));                                    // the coil type's table (joins the push)
   const long nl_start_s = start_launches(H);
   RK(start_vector(H, H->bs, H->x, st, &used_s, &init_s));
-  RK(pcg_launch(H, H->bs, H->x, H->opt.tol, H->opt.maxit, st, init_s));
+  RK(pcg_launch(H, H->bs, H->x, H->opt.tol, H->opt.maxit, st, init_s, halt_flag(H)));
   record_add_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_s, refin ? H->refin : nullptr, H->derr,
-                                     H->dstats, H->dctr);
+                                     H->dstats, H->dctr, H->guard);
   mark(H);
   RK(history_push(H, H->x, H->lx, st));
   const long nl_hist = 2 * history_launches(H);
@@ -972,9 +1106,10 @@ int enqueue_split_step(mqs_handle* H) {
   H->lx_valid = false;                                // lx holds L w_s only
   mark(H);
   RK(conductor_step(H, H->x, H->dt, st));
+  record_mon_kernel<<<1, 1, 0, st>>>(H->guard, H->dstats, H->dctr);
   mark(H);
   if (H->timing) {
-    H->launches += 2 + nl_start + nl_start_s + 2 + 2 + nl_hist + 1 + (H->any_brauer ? 2 : 1);
+    H->launches += 2 + nl_start + nl_start_s + 2 + 2 + nl_hist + 1 + (H->any_brauer ? 2 : 1) + 1;
     H->pcg_launches += 2;
     H->tsteps += 1;
   }
@@ -1004,7 +1139,7 @@ int enqueue_step(mqs_handle* H) {
   RK(start_vector(H, H->b, H->x, st, &used_small, &init));
   mark(H);
   // (a4) PCG (the error word was cleared when the call began: a timeout stays visible)
-  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
+  RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init, halt_flag(H)));
   H->lx_valid = true;
   nl += 1;
   mark(H);
@@ -1017,7 +1152,7 @@ int enqueue_step(mqs_handle* H) {
   RK(conductor_step(H, H->x, H->dt, st));
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats, H->dctr);
+                                 H->derr, H->dstats, H->dctr, H->guard);
   advance_ctr(H);
   nl += 1;
   // the next step's right-hand side from the new state, beside the side stream's push
@@ -1243,9 +1378,56 @@ int prepare_steps(mqs_handle* H, int nsteps, int keep = 0) {
   if (H->opt.rhs_split) RK(ensure_split(H));
   if (H->opt.precision != 0) RK(ensure_mixed(H));
   if (!H->dctr) RK(dalloc(H, &H->dctr, 2));
-  if (keep == 0) CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
+  if (keep == 0) {
+    CK(cudaMemsetAsync(H->derr, 0, sizeof(int), H->st));
+    CK(cudaMemsetAsync(const_cast<int*>(halt_flag(H)), 0, sizeof(int), H->st));   // a new call runs
+    H->call_m0 = H->m;
+    H->call_ac0 = H->ac;
+    H->call_full0 = H->ac_full;
+  }
   RK(ensure_stats(H, nsteps, keep));
   return set_ctr(H, keep, keep == 0);
+}
+
+// After the first failing step of a call (index f among its steps, which the device
+// halted after it): the handle goes back to the state after the call's first f steps.
+// The conductor buffer pair alternates once per issued step, and the failing step and
+// the halted ones wrote nothing but the failing step's discarded update into the
+// other buffer, so the state after f steps is the buffer of parity f.  Its start-vector
+// history and b are dropped (halted steps pushed start vectors, not solutions).
+int roll_back(mqs_handle* H, int f) {
+  double* a0 = H->call_ac0;
+  double* a1 = (H->ac == a0) ? H->ac2 : H->ac;
+  double* f0 = H->call_full0;
+  double* f1 = (H->ac_full == f0) ? H->ac_full2 : H->ac_full;
+  H->ac = (f % 2 == 0) ? a0 : a1;
+  H->ac2 = (f % 2 == 0) ? a1 : a0;
+  H->ac_full = (f % 2 == 0) ? f0 : f1;
+  H->ac_full2 = (f % 2 == 0) ? f1 : f0;
+  H->m = H->call_m0 + f;
+  H->t = H->m * H->dt;
+  H->ctr_m = H->ctr_slot = -1;       // the device counter ran on through the halted steps
+  H->b_for_m = -1;
+  H->lx_valid = false;
+  clear_history(H);
+  return state_changed(H);
+}
+
+// The statistics of a finished stepping call: OK, or the first failing step's status
+// with the handle rolled back to the step before it.
+int finish_call(mqs_handle* H, int nsteps, const mqs_step_stats* hs, int derr) {
+  for (int s = 0; s < nsteps; ++s)
+    if (hs[s].status != MQS_OK) {
+      const int code = hs[s].status;
+      RK(roll_back(H, s));
+      char buf[160];
+      snprintf(buf, sizeof buf, "step %d of the call failed (status %d); the handle is at the step before it",
+               s + 1, code);
+      H->err = buf;
+      return code;
+    }
+  if (derr != 0) return fail(H, derr, "a bounded grid barrier wait timed out");
+  return MQS_OK;
 }
 
 // Copies the step statistics of the last nsteps steps into hs (async on H->st).
@@ -1302,7 +1484,7 @@ int mqs_step_finish(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
   RK(fetch_stats(H, nsteps, hs.data(), &derr));
   CK(cudaStreamSynchronize(H->st));
   if (per_step) memcpy(per_step, hs.data(), sizeof(mqs_step_stats) * nsteps);
-  return check_stats(H, nsteps, hs.data(), derr);
+  return finish_call(H, nsteps, hs.data(), derr);
 }
 
 namespace {
@@ -1370,7 +1552,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
   H->lx_valid = true;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats + slot, nullptr);
+                                 H->derr, H->dstats + slot, nullptr, nullptr);
   RK(history_push(H, H->x, H->lx, st));
   RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
   RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
@@ -1431,7 +1613,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
       H->lx_valid = false;
       CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)seg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
       RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
-      H->ac_gen += 1;
+      RK(state_changed(H));
       H->m = m0 + lo;
       H->t = H->m * H->dt;
       RK(set_ctr(H, 2 * nsteps + lo, true));
@@ -1454,7 +1636,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
     // back to the forward end state
     CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)nseg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
     RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
-    H->ac_gen += 1;
+    RK(state_changed(H));
     H->m = m_end;
     H->t = H->m * H->dt;
   }
@@ -1527,7 +1709,7 @@ int mqs_set_state(mqs_handle* H, const double* a_c, size_t n_c, double t, long m
   if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
   CK(cudaMemcpyAsync(H->ac, a_c, sizeof(double) * n_c, cudaMemcpyHostToDevice, H->st));
   RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
-  H->ac_gen += 1;
+  RK(state_changed(H));
   CK(cudaStreamSynchronize(H->st));
   H->t = t;
   H->m = m;
@@ -1550,7 +1732,7 @@ int mqs_set_state_dev(mqs_handle* H, const double* a_c_dev, size_t n_c, void* st
   if (st != H->st) CK(cudaStreamSynchronize(st));
   CK(cudaMemcpyAsync(H->ac, a_c_dev, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, H->st));
   RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
-  H->ac_gen += 1;
+  RK(state_changed(H));
   if (st != H->st) CK(cudaStreamSynchronize(H->st));
   return MQS_OK;
 }
@@ -1642,43 +1824,7 @@ int mqs_conductor_rate(mqs_handle* H, const double* a_c, const double* w, double
 int mqs_lambda_max(mqs_handle* H, const double* v0, double pcg_tol, double rtol, int maxit, double* lambda_max,
                    int* iters) {
   if (!H || !v0 || !lambda_max) return MQS_ERR_ARG;
-  if (!(pcg_tol > 0.0) || !(rtol > 0.0) || maxit < 1) return fail(H, MQS_ERR_ARG, "bad power-method settings");
-  cudaStream_t st = H->st;
-  double nv = 0.0;
-  for (long q = 0; q < H->n_c; ++q) nv += v0[q] * v0[q];
-  if (!(nv > 0.0)) return fail(H, MQS_ERR_ARG, "v0 must be nonzero");
-  std::vector<double> vn(v0, v0 + H->n_c);
-  for (double& v : vn) v /= std::sqrt(nv);
-  CK(cudaMemcpyAsync(H->cvec, vn.data(), sizeof(double) * H->n_c, cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
-  CK(cudaMemsetAsync(H->tmp, 0, sizeof(double) * H->len, st));
-  CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
-  const CoilDrive nodrv{H->h / H->nu0, 0.0, 0.0, 1.0, 0.0, 0};
-  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
-  double lam = 0.0, lam_old = 0.0;
-  int it = 0;
-  for (it = 1; it <= maxit; ++it) {
-    // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
-    power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
-    RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
-    RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->sup, H->nsup, st));
-    RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
-    // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
-    RK(launch_cell_nu(H->dg, H->cg, H->tmp, H->xu, true, st));
-    RK(launch_cond_update(H->dg, H->cg, H->tmp, H->xu, 1.0, H->cvec2, H->ac2, 0.0, st));
-    power_update_kernel<<<1, 1024, 0, st>>>((int)H->n_c, H->ac2, H->isqmc, H->cvec, H->scal + 1);
-    PcgResult pr{};
-    CK(cudaMemcpyAsync(&lam, H->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&pr, H->pres, sizeof(pr), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (pr.status != MQS_OK) return fail(H, pr.status, "PCG failed inside the power method");
-    if (it > 1 && std::fabs(lam - lam_old) < rtol * std::fabs(lam)) break;
-    lam_old = lam;
-  }
-  // the scratch a_c buffer ac2 was used; restore nothing (ac holds the state)
-  *lambda_max = lam;
-  if (iters) *iters = it > maxit ? maxit : it;
-  return MQS_OK;
+  return power_method(H, v0, pcg_tol, rtol, maxit, lambda_max, iters);
 }
 
 int mqs_set_stream(mqs_handle* H, void* stream) {
@@ -2070,7 +2216,7 @@ int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
     for (int s = 0; s < nsteps; ++s)
       for (int i = 0; i < cnt; ++i) per_step[(size_t)s * cnt + i] = hs[(size_t)i * nsteps + s];
   for (int i = 0; i < cnt; ++i) {
-    const int r = check_stats(B->hs[i], nsteps, hs.data() + (size_t)i * nsteps, derr[i]);
+    const int r = finish_call(B->hs[i], nsteps, hs.data() + (size_t)i * nsteps, derr[i]);
     if (r != MQS_OK && rc == MQS_OK) rc = r;
   }
   return rc;

@@ -90,7 +90,9 @@ int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive dr
 }
 
 // ---- conducting region ------------------------------------------------------------
-__global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const double* w, int at_zero) {
+__global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const double* w, int at_zero,
+                               const int* halt) {
+  if (halt && *halt) return;
   const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1], wz = cg.chi[2] - cg.clo[2];
   const long long ncell = (long long)wx * wy * wz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
@@ -112,11 +114,67 @@ __global__ void cell_nu_kernel(Geom g, CondGeom cg, const double* ac, const doub
   }
 }
 
+// The instability monitor's step (last block of a guarded conductor update): with
+// e = M_c-energy of the increment d_m = a^m - a^{m-1} and s = d_m^T M_c d_{m-1}, a step
+// whose increment grew (e > e_prev) while changing sign (s < 0), above 1e-20 of the
+// largest increment energy seen, extends a run of such steps; `window` of them in a
+// row, or a non-finite increment, is the explicit Euler instability of a mode with
+// 1 - dt lambda < -1 (eq. (CFL) violated).  Each block's partials (e, s) are summed in a
+// fixed order, so the verdict does not depend on scheduling.
+__device__ void monitor_finish(const GuardView& gv, double e, double s) {
+  __shared__ double red[2][32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  e = warp_sum(e);
+  s = warp_sum(s);
+  if (lane == 0) { red[0][w] = e; red[1][w] = s; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double be = 0.0, bs = 0.0;
+    for (int q = 0; q < nw; ++q) { be += red[0][q]; bs += red[1][q]; }
+    gv.part[2 * blockIdx.x] = be;
+    gv.part[2 * blockIdx.x + 1] = bs;
+    __threadfence();
+    last = atomicAdd(&gv.gd->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || w != 0) return;
+  __threadfence();
+  const volatile double* pv = gv.part;
+  double E = 0.0, S = 0.0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) { E += pv[2 * b]; S += pv[2 * b + 1]; }
+  E = warp_sum(E);
+  S = warp_sum(S);
+  if (lane != 0) return;
+  StepGuard* gd = gv.gd;
+  int status = MQS_OK;
+  if (!isfinite(E) || (gd->valid && !isfinite(S))) {
+    status = MQS_ERR_UNSTABLE;
+  } else {
+    const bool grow = gd->valid && E > gd->e_prev && S < 0.0 && E > 1e-20 * gd->e_max;
+    gd->count = grow ? gd->count + 1 : 0;
+    if (gv.window > 0 && gd->count >= gv.window) status = MQS_ERR_UNSTABLE;
+    gd->e_max = fmax(gd->e_max, E);
+    gd->e_prev = E;
+    gd->valid = 1;
+  }
+  gd->status = status;
+  gd->arrive = 0u;
+}
+
 // F_e = sum over the four faces f of e of C_fe M_nu[f] (C a)_f with
 // M_nu[f] = (nu of the two cells of f) / (2h); a_c update of eq. (acm).
 __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const double* w, double sw,
                                    const double* a_in, double* a_out, double dt, double* ac_out, double* F_out,
-                                   double* a_prev_out) {
+                                   double* a_prev_out, GuardView gv) {
+  if (gv.gd) {
+    // a halted call, a failed solve or a timed-out wait: this step writes nothing
+    if (*(volatile const int*)&gv.gd->halt || (gv.pres && gv.pres->status != MQS_OK) || (gv.derr && *gv.derr != 0))
+      return;
+  }
+  const bool mon = gv.gd != nullptr && dt != 0.0;
+  const bool prev = mon && gv.gd->valid;     // a_out holds a^{m-2}: the previous increment is known
+  double en = 0.0, sx = 0.0;
   const int n = g.n;
   const long long n3 = g.n3;
   const double ih2 = 0.5 / cg.h;
@@ -150,11 +208,17 @@ __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const 
     }
     const double a0 = a_in[q];
     const double v = (dt != 0.0) ? fma(-dt * cg.inv_mc[q], F, a0) : F;
+    if (mon) {
+      const double md = -dt * F;                  // M_c (a^m - a^{m-1})
+      en = fma(md * md, cg.inv_mc[q], en);        // M_c |a^m - a^{m-1}|^2
+      if (prev) sx = fma(md, a0 - a_out[q], sx);  // with a^{m-1} - a^{m-2} (a_out read before written)
+    }
     if (F_out) F_out[q] = F;            // recorded trajectory (adjoint)
     if (a_prev_out) a_prev_out[q] = a0;
     a_out[q] = v;
     if (ac_out) ac_out[e] = v;      // the other layout buffer (read and written buffers differ)
   }
+  if (mon) monitor_finish(gv, en, sx);
 }
 
 __global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, double* ac_full, double scale) {
@@ -163,23 +227,24 @@ __global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, d
 }
 
 int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
-                   cudaStream_t st) {
+                   cudaStream_t st, const int* halt) {
   const long long ncell = (long long)(cg.chi[0] - cg.clo[0]) * (cg.chi[1] - cg.clo[1]) * (cg.chi[2] - cg.clo[2]);
   int blocks = (int)((ncell + 255) / 256);
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  cell_nu_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, at_zero ? 1 : 0);
+  cell_nu_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, at_zero ? 1 : 0, halt);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
                        double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
-                       double* ac_full_out, double* F_out, double* a_prev_out) {
+                       double* ac_full_out, double* F_out, double* a_prev_out, const GuardView* guard) {
   int blocks = (cg.n_c + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
+  if (blocks > kMonBlocks) blocks = kMonBlocks;
   if (blocks < 1) blocks = 1;
+  const GuardView gv = guard ? *guard : GuardView{nullptr, nullptr, nullptr, nullptr, 0};
   cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out, F_out,
-                                             a_prev_out);
+                                             a_prev_out, gv);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

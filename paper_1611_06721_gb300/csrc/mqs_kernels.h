@@ -16,11 +16,38 @@ struct DevGeom {
   Geom g;                 // device view (cflags points to device memory)
 };
 
+// Device state of a stepping call (one per handle): the halt flag that makes every
+// step after a failing one skip its solve and its conductor update, and the
+// instability monitor of the explicit Euler update (mqs_options.monitor_steps).
+struct StepGuard {
+  int halt;               // 1 once a step of the current call failed (set by the record kernels)
+  int status;             // the monitor's verdict on the last conductor update it checked
+  unsigned arrive;        // blocks of the running conductor update that wrote their partials
+  int pad;
+  // from here on: the monitor's history, cleared whenever the state changes outside a step
+  int count;              // consecutive steps with growing, sign-alternating increments
+  int valid;              // the other conductor buffer holds the state before the current one
+  double e_prev;          // M_c-energy of the last increment
+  double e_max;           // largest increment energy since the last clear
+};
+constexpr int kMonBlocks = 1024;          // most blocks of a conductor update (2 partials each)
+// what a guarded conductor update reads besides its operands: the guard and its partials,
+// the solve it follows (its result and the call's error word) and the monitor window
+struct GuardView {
+  StepGuard* gd;
+  double* part;
+  const PcgResult* pres;
+  const int* derr;
+  int window;             // > 0: consecutive steps that flag an instability; <= 0: finiteness only
+};
+
 // init: 0 = the kernel forms r = b - L x; 1 = r holds b - L x already;
 // 2 = zero start (the kernel sets x = 0, r = b).
+// halt (nullable): a solve issued inside a stepping call returns at once, writing a
+// zero-iteration MQS_OK result, when *halt != 0 (an earlier step of the call failed).
 int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
                double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
-               cudaStream_t st, int init = 0);
+               cudaStream_t st, int init = 0, const int* halt = nullptr);
 int pcg_max_blocks(int* nblk);
 
 // mixed precision: FP64 iterative refinement around FP32 CG inner solves
@@ -30,19 +57,21 @@ struct MixedBufs {
 };
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0, int variant = 0);
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0, int variant = 0,
+                     const int* halt = nullptr);
 // precision 2: the same refinement with float-float one-reduction inner solves
 // (MixedBufs sized for 8 bytes per value, all nine buffers)
 int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                   double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0);
+                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0,
+                  const int* halt = nullptr);
 
 // one-reduction PCG (one fused stencil pass and one grid reduction per
 // iteration); needs five more layout vectors
 struct PcgExtra { double* r1; double* w0; double* w1; double* s0; double* s1; };
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
-                     int nblk, cudaStream_t st, int init = 0);
+                     int nblk, cudaStream_t st, int init = 0, const int* halt = nullptr);
 
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
 int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);
@@ -77,17 +106,23 @@ struct CondGeom {
   double nu0, k1, k2, k3, h;
 };
 // nu per cell of the cell box from a = ac_full + w (nonlinear cells); if
-// `at_zero` the Brauer law is evaluated at B = 0.
+// `at_zero` the Brauer law is evaluated at B = 0.  halt (nullable): nothing is done
+// when *halt != 0.
 int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
-                   cudaStream_t st);
+                   cudaStream_t st, const int* halt = nullptr);
 // F = (K(a) a)_c at every c-edge (a = ac_full + sign_w * w).  If dt != 0:
 // a_c_out = a_c_in - dt F / M_c, else F is written to a_c_out.  If
 // ac_full_out is given (a layout buffer other than ac_full), the result is
 // also written there at the c-edges.  F_out / a_prev_out (nullable) receive
 // F and a_c_in per c-edge (the recorded trajectory of the adjoint).
+// guard (nullable; steps only): the update writes nothing when the call is halted, the
+// solve it follows failed or a device wait timed out; otherwise (dt != 0) it also runs
+// the instability monitor, whose verdict goes to guard->gd->status.  a_c_out must then
+// hold the state before a_c_in (the buffer pair alternates), read before it is written.
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
                        double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
-                       double* ac_full_out = nullptr, double* F_out = nullptr, double* a_prev_out = nullptr);
+                       double* ac_full_out = nullptr, double* F_out = nullptr, double* a_prev_out = nullptr,
+                       const GuardView* guard = nullptr);
 // scatter compact a_c into the layout vector ac_full (c-edges only)
 int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st);
 

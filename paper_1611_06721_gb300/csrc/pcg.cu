@@ -35,7 +35,16 @@ struct PcgArgs {
   int maxit;
   long long spin;
   int init;           // 0: r = b - L x (stencil); 1: r given (start vector's image known); 2: x = 0, r = b
+  const int* halt;    // nullable: nonzero = an earlier step of the stepping call failed, skip the solve
 };
+
+// A solve inside a halted stepping call returns at once (every block reads the same
+// word before any grid barrier) with a zero-iteration result the record kernel ignores.
+__device__ __forceinline__ bool pcg_halted(const int* halt, PcgResult* out) {
+  if (!halt || *(volatile const int*)halt == 0) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out = PcgResult{0, MQS_OK, 0.0, 0.0};
+  return true;
+}
 
 struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
   const double* b; double* r; double* lx; long long n3;
@@ -94,6 +103,7 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
 // barrier arrivals and partials).
 template <int BPS>
 __global__ void __launch_bounds__(kBlock, BPS) pcg_kernel(PcgArgs a) {
+  if (pcg_halted(a.halt, a.out)) return;
   __shared__ SweepSmem sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -255,6 +265,7 @@ struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; }
 // (gamma, delta).  Same iterates as the two-reduction kernel in exact
 // arithmetic; convergence is confirmed on the true residual as there.
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
+  if (pcg_halted(a.halt, a.out)) return;
   __shared__ union { SweepSmem s; FusedSmemBlock f; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgA
 
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
-                     int nblk, cudaStream_t st, int init) {
+                     int nblk, cudaStream_t st, int init, const int* halt) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -377,6 +388,7 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
   a.tol2 = tol * tol; a.maxit = maxit;
   a.spin = 1ll << 21;
   a.init = init;
+  a.halt = halt;
   FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1};
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a, &fb};
@@ -386,7 +398,7 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
 
 int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* q, double* lx,
                double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit, int nblk,
-               cudaStream_t st, int init) {
+               cudaStream_t st, int init, const int* halt) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -395,6 +407,7 @@ int launch_pcg(const DevGeom& dg, const double* b, double* x, double* r, double*
   a.tol2 = tol * tol; a.maxit = maxit;
   a.spin = 1ll << 21;   // about a second of polling before a barrier gives up
   a.init = init;
+  a.halt = halt;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
   const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;

@@ -44,7 +44,15 @@ struct MixedArgs {
   int maxit;            // cap on the total inner iterations
   long long spin;
   int init;             // as in the FP64 kernel: 0 stencil, 2 zero start
+  const int* halt;      // nullable: nonzero = an earlier step of the stepping call failed, skip the solve
 };
+
+// as in the FP64 kernel: a halted stepping call skips the solve (zero iterations)
+__device__ __forceinline__ bool mixed_halted(const MixedArgs& a) {
+  if (!a.halt || *(volatile const int*)a.halt == 0) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) { *a.out = PcgResult{0, MQS_OK, 0.0, 0.0}; *a.refinements = 0; }
+  return true;
+}
 
 struct EpiResidualM {   // r = b - t, lx = t on n-edges; sums r.r and b.b (FP64)
   const double* b; double* r; double* lx; long long n3;
@@ -116,6 +124,7 @@ struct EpiApplyDot32 {  // w = t on n-edges (0 elsewhere, FP32); sums w.r with r
 // of both than 10; the register cap of 96 spills a little, in the FP64 passes), else 1.
 template <int BPS>
 __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
+  if (mixed_halted(a)) return;
   __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; FusedSmemBlockT<float> ff; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -293,6 +302,7 @@ struct EpiApplyDotFF {  // w = t on n-edges (0 elsewhere); sums w.r with r the s
 };
 
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedArgs a) {
+  if (mixed_halted(a)) return;
   __shared__ union { SweepSmemT<double> d; SweepSmemT<ffv> f; FusedSmemBlockT<ffv> ff; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedAr
 
 int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                   double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init) {
+                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init, const int* halt) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -418,6 +428,7 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
   a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
   a.spin = 1ll << 21;
   a.init = (init == 2) ? 2 : 0;
+  a.halt = halt;
   if (!mb.r32b || !mb.w32a || !mb.w32b || !mb.s32a || !mb.s32b) return MQS_ERR_ARG;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
@@ -427,7 +438,8 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
 
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant) {
+                     double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant,
+                     const int* halt) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -439,6 +451,7 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
   a.spin = 1ll << 21;
   a.init = (init == 2) ? 2 : 0;
+  a.halt = halt;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a};
   // 64^3 (FP32 vectors in L2): one block per SM; from 96^3 on, two (28% faster per

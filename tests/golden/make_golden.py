@@ -6,7 +6,12 @@ lambda_max of M_c^-1 K_S by the power method (eq. (CFL)), dt = 0.9 * 2 /
 lambda_max, and 200 explicit-Euler steps (eq. (acm)) for every start vector
 (zero, previous, SPE with 8 columns, POD with 20 snapshots; Sec. III).
 
-Run:  python tests/golden/make_golden.py
+With --iron64: lambda_max and dt = 0.9 * 2 / lambda_max of the 64^3 nonlinear
+iron workload (24x24x16 Brauer iron, sigma 2e6 S/m, 40x40 coil, 500 A at 50 Hz)
+by the same power method (PCG tol 1e-12, stop at |dlambda| < 1e-8 lambda), for
+the parity test that runs both sides on that workload with this step.
+
+Run:  python tests/golden/make_golden.py [--iron64]
 """
 import json
 import os
@@ -38,5 +43,19 @@ def main():
         json.dump(out, f, indent=0)
 
 
+def iron64():
+    p = W.config_nonlinear_iron()
+    d = O.Discretization(p)
+    lam, it = O.lambda_max_power(d, W.power_start_vector(d.n_c))
+    out = {"problem": "nonlinear iron 64^3", "N": p.N, "n_c": int(d.n_c), "n_n": int(d.n_n),
+           "lambda_max": lam, "power_iterations": it, "cfl_factor": 0.9, "dt": O.dt_from_lambda(lam)}
+    print(out)
+    with open(os.path.join(HERE, "nonlinear_iron_64.json"), "w") as f:
+        json.dump(out, f, indent=0)
+
+
 if __name__ == "__main__":
-    main()
+    if "--iron64" in sys.argv:
+        iron64()
+    else:
+        main()

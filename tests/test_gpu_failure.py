@@ -1,6 +1,8 @@
 """Failure paths on the GPU, produced without faulting it: a grid barrier that
 can never complete gives up after its poll limit and reports MQS_ERR_TIMEOUT,
-and the context stays usable; bad inputs come back as error codes."""
+and the context stays usable; bad inputs come back as error codes; a step
+above the stability bound of eq. (CFL) is caught by the instability monitor,
+and a failing step stops the rest of its call."""
 import numpy as np
 import pytest
 
@@ -57,12 +59,62 @@ def test_setup_rejects_bad_inputs(pkg):
     s.close()
 
 
-def test_unstable_step_is_reported(pkg):
-    # far above the CFL bound the explicit update blows up; the PCG reports NaN
-    # or non-convergence instead of hanging
+@pytest.mark.parametrize("factor", [10.0, 100.0])
+def test_unstable_step_is_reported(pkg, factor):
+    # dt at 10x / 100x the stability bound 2 / lambda_max (setup computes lambda_max and
+    # scales by cfl_factor): the instability monitor fails the step once the increments
+    # have grown with alternating sign over 8 steps in a row, the loop stops there, and
+    # the handle stays at the step before it
     p = W.config_linear_block()
-    s = pkg.Solver.from_problem(p, pkg.SolverOptions(dt=1e-3, maxit=2000))
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(cfl_factor=factor, start_mode=pkg.START_SPE))
+    dt, lam = s.dt_lambda()
+    assert lam > 0 and dt == pytest.approx(factor * 2.0 / lam, rel=1e-15)
     rc, stats = s.step(60, allow_fail=True)
-    assert rc != 0
-    assert any(st.status in (-4, -5, -6) for st in stats)
+    assert rc == -7                                                  # MQS_ERR_UNSTABLE
+    codes = [st.status for st in stats]
+    f = codes.index(-7)
+    assert all(c == 0 for c in codes[:f]) and all(c == -10 for c in codes[f + 1:])   # MQS_ERR_HALTED
+    assert 8 <= f <= 30
+    assert all(st.iterations == 0 for st in stats[f + 1:])
+    a_c, t, m = s.get_state()
+    assert m == f and t == pytest.approx(f * dt, rel=1e-15)
+    # the same f steps on a fresh handle: bitwise the state the failed call left
+    r = pkg.Solver.from_problem(p, pkg.SolverOptions(dt=dt, start_mode=pkg.START_SPE))
+    r.step(f)
+    a_r, _, _ = r.get_state()
+    assert np.array_equal(a_c, a_r)
+    r.close()
+    # the handle goes on from there at a stable step
+    s.set_dt(0.9 * 2.0 / lam)
+    rc, stats = s.step(5)
+    assert rc == 0 and s.get_state()[2] == f + 5
+    s.close()
+
+
+def test_failed_solve_halts_the_rest_of_the_call(pkg):
+    # a solve that stops at maxit fails its step; the later steps of the call do not run
+    # and the handle keeps the state of the last good step
+    p = W.config_linear_block()
+    dt = O.dt_gershgorin(O.Discretization(p))
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(dt=dt, start_mode=pkg.START_ZERO))
+    s.step(3)
+    a3, _, _ = s.get_state()
+    s.set_options(pkg.SolverOptions(dt=dt, start_mode=pkg.START_ZERO, maxit=2))
+    rc, stats = s.step(6, allow_fail=True)
+    assert rc == -4 and stats[0].status == -4                        # MQS_ERR_NOT_CONVERGED
+    assert [st.status for st in stats[1:]] == [-10] * 5
+    a_c, _, m = s.get_state()
+    assert m == 3 and np.array_equal(a_c, a3)
+    s.set_options(pkg.SolverOptions(dt=dt, start_mode=pkg.START_ZERO))
+    rc, _ = s.step(2)
+    assert rc == 0 and s.get_state()[2] == 5
+    s.close()
+
+
+def test_monitor_is_quiet_at_the_stability_bound(pkg):
+    # at 0.99 of the bound (top-mode factor -0.98: alternating, decaying) nothing is flagged
+    p = W.config_linear_block()
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(cfl_factor=0.99, start_mode=pkg.START_SPE))
+    rc, stats = s.step(200)
+    assert rc == 0 and all(st.status == 0 for st in stats)
     s.close()

@@ -164,6 +164,20 @@ def test_lambda_max_matches_oracle(pkg):
     s.close()
 
 
+def test_setup_sets_dt_from_the_cfl_factor(pkg):
+    # mqs_setup with dt <= 0 and cfl_factor > 0 runs the power method itself (its own
+    # start vector): lambda_max as the oracle's, dt = cfl_factor 2 / lambda_max
+    g = golden()
+    s = make(pkg, W.config_linear_block(), cfl_factor=0.9)
+    dt, lam = s.dt_lambda()
+    assert lam == pytest.approx(g["lambda_max"], rel=1e-6)
+    assert dt == 0.9 * 2.0 / lam
+    s.close()
+    s = make(pkg, W.config_linear_block(), dt=1e-7, cfl_factor=0.9)     # an explicit dt wins
+    assert s.dt_lambda() == (1e-7, 0.0)
+    s.close()
+
+
 # ---- full steps (a2-a6), 16^3 linear block, 200 steps, every start vector ---------------------
 @pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_PREV, "prev"), (START_SPE, "spe8"),
                                        (START_POD, "pod20")])
@@ -406,6 +420,37 @@ def test_full_size_nonlinear_first_steps(pkg):
     assert np.mean([x.iterations for x in st_spe[-8:]]) < 0.5 * np.mean([x.iterations for x in st_zero[-8:]])
     s.close()
     s2.close()
+
+
+def test_bench_configuration_against_the_oracle(pkg):
+    # the timed workload itself: 64^3 Brauer iron, SPE 8 (float-float table full after
+    # 8 steps), tol 1e-10, one block per SM, steps issued one at a time as the benchmark
+    # issues them, at the step of eq. (CFL) (0.9 * 2 / lambda_max) that the oracle's power
+    # method gives (stored by tests/golden/make_golden.py --iron64), given to both sides
+    with open(os.path.join(HERE, "golden", "nonlinear_iron_64.json")) as f:
+        g64 = json.load(f)
+    p = W.config_nonlinear_iron()
+    d = O.Discretization(p)
+    dt = g64["dt"]
+    steps = 30
+    ref = O.run_explicit_euler(d, dt, steps, start_mode=START_SPE, spe_depth=8, tol=1e-10, eps_lin=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, eps_lin=1e-10)
+    # the benchmark's own step comes from the GPU power method: the same lambda_max
+    lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=2000)
+    assert lam == pytest.approx(g64["lambda_max"], rel=1e-6)
+    s.set_dt(dt)
+    for _ in range(steps):
+        s.step_enqueue(1)
+    rc, stats = s.step_finish(steps)
+    assert rc == 0
+    a_c, _, m = s.get_state()
+    assert m == steps
+    assert rel(a_c, ref.a_c) < 1e-8
+    w = layout_to_oracle(p.N, s.get_solution())[d.n_idx]
+    assert rel(d.K_cn @ w, d.K_cn @ ref.w) < 1e-8
+    its = np.array([st.iterations for st in stats])
+    assert np.abs(its - ref.iterations).max() <= 3, (its.tolist(), ref.iterations.tolist())
+    s.close()
 
 
 # ---- other readings of the step and the paper-sized grid ---------------------------------------
