@@ -58,10 +58,12 @@ PRECISION_NAMES = {
     2: "float-float inner CG in FP64 refinement (FP64 residual, update and stopping test); SPE table in "
        "float-float"}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2070 MHz
-# DRAM bytes (read + write) per launch of the PCG kernel on the 64^3 iron workload, from one
-# ncu capture of the current kernel build; keyed by (precision, pcg_variant).  The carried
-# vectors stay in L2, so the figure does not depend on the iteration count of the launch.
-PCG_TRAFFIC = {(0, 0): 12.723456e6 + 1.524480e6}
+# DRAM bytes of the PCG kernel on the 64^3 iron workload from one ncu capture of the current
+# kernel build (a zero-start solve of 221 iterations, profiles/pcg_fused_kernel_...): bytes
+# read per launch (the carried vectors stay in L2) and bytes written per iteration (L2
+# write-back of the ping-pong vectors, which grows with the iterations); keyed by
+# (precision, pcg_variant).  A launch of the benchmark is scaled by its iteration count.
+PCG_TRAFFIC = {(0, 1): (12.952320e6, 228.410112e6 / 221)}
 
 
 def measured_peaks():
@@ -441,8 +443,9 @@ def run_ours(args, rank, ws, local, dist):
         flops = n_n * (FLOPS_PER_ITER * its.sum() + FLOPS_PER_RESIDUAL * (len(its) + sum(refs)))
     achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
     traffic = args.traffic
-    if traffic is None and args.start == "spe" and depth == 8:
-        traffic = PCG_TRAFFIC.get((args.precision, args.pcg_variant))
+    if traffic is None and args.start == "spe" and depth == 8 and (args.precision, args.pcg_variant) in PCG_TRAFFIC:
+        rd, wr_it = PCG_TRAFFIC[(args.precision, args.pcg_variant)]
+        traffic = rd + wr_it * float(its.mean())
     if args.precision == 0:
         roof = {"bound": "alu", "kernel": "pcg_kernel" if args.pcg_variant == 0 else "pcg_fused_kernel",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -539,14 +542,14 @@ def coil_rhs(p, amp=100.0):
     return b
 
 
-def single_solve():
+def single_solve(variant=1):
     """One zero-start PCG solve of K_n w = 100 X_s on the workload (twice)."""
     import __graft_entry__ as g
     g.build()
     import paper_1611_06721_gb300 as pkg
     import workloads as W
     p = W.config_nonlinear_iron()
-    s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7))
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, pcg_variant=variant))
     b = coil_rhs(p)
     for _ in range(2):
         x, info = s.pcg_solve(b, tol=1e-10)
@@ -940,8 +943,8 @@ def main():
                          "SPE history (the paper's separate right-hand sides)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="replay steady-state SPE steps from CUDA graphs (1, default) or issue every launch (0)")
-    ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1],
-                    help="0: two grid reductions per PCG iteration (default), 1: one (fused pass)")
+    ap.add_argument("--pcg-variant", type=int, default=1, choices=[0, 1],
+                    help="0: two grid reductions per PCG iteration, 1: one (fused pass; default)")
     ap.add_argument("--grid", type=int, default=64,
                     help="cells per axis of the iron workload (64: the benchmark; others scale it)")
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
@@ -974,7 +977,7 @@ def main():
               flush=True)
         return
     if args.single_solve:
-        single_solve()
+        single_solve(args.pcg_variant)
         return
     if args.sweep:
         size_sweep([int(v) for v in args.sweep.split(",") if v])

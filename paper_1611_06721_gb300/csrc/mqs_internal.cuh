@@ -70,6 +70,89 @@ __device__ __forceinline__ double ld(const double* __restrict__ v, int n, long l
   return v[c * n3 + pidx(n, i, j, k)];
 }
 
+// identity load conversion of sweep_L
+struct LoadAs {
+  template <class V>
+  __device__ __forceinline__ V operator()(V v) const { return v; }
+};
+
+// ---- 64-bit fixed point for the integer stencil ----------------------------------
+// On this GPU an FP64 addition issues at about 1.6 lanes per clock and SM, a 64-bit
+// integer addition at about 32, and the hardware FP64 <-> int64 conversions at 2 (on
+// the FP64 unit).  L has integer coefficients, so a sweep can convert its FP64 source
+// v (all |v_i| < 2^(E-1)) to the integers V_i = round(v_i 2^(58-E)) (|V_i| < 2^58), form
+// L V exactly in 64-bit integer arithmetic (every flux sums 4 values, every output 4
+// fluxes: |L V| < 2^62), and convert back with one rounding, t = (L V) 2^(E-58).  Both
+// conversions are bit manipulations on the integer pipes.
+
+// round(v 2^sh) as a 64-bit integer (nearest, ties away from zero), for |v 2^sh| < 2^58;
+// zero and subnormal v give 0 (they lie far below the resolution 2^-sh).
+__host__ __device__ __forceinline__ long long fx_from_double(double v, int sh) {
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(v);
+#else
+  long long b;
+  __builtin_memcpy(&b, &v, sizeof b);
+#endif
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int s = e - 1075 + sh;                                   // |v| 2^sh = m 2^s
+  const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+  const int rs = -s;
+  long long r = 0;
+  if (s >= 0) r = m << s;
+  else if (rs < 54) r = (m + (1LL << (rs - 1))) >> rs;
+  if (e == 0) r = 0;
+  return b < 0 ? -r : r;
+}
+
+// t 2^sh as the nearest double (ties to even), for |t| < 2^63 and a normal result.
+__host__ __device__ __forceinline__ double fx_to_double(long long t, int sh) {
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = t < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+#ifdef __CUDA_ARCH__
+  const int lz = __clzll((long long)a);
+#else
+  const int lz = __builtin_clzll(a);
+#endif
+  a <<= lz;                                                      // leading one at bit 63
+  unsigned long long mant = a >> 11;                             // 53 bits, leading one at bit 52
+  const unsigned rem = (unsigned)(a & 0x7FFull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const long long eb = 1023 + 63 - lz + sh;                      // biased exponent of the leading one
+  // (eb - 1) 2^52 + mant: the implicit bit of mant completes the exponent, and a
+  // rounding carry to 2^53 moves it up by one with a zero fraction
+  const unsigned long long bits = ((unsigned long long)(eb - 1) << 52) + mant;
+  const unsigned long long out = bits | sgn;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)out);
+#else
+  double d;
+  __builtin_memcpy(&d, &out, sizeof d);
+  return d;
+#endif
+}
+
+// E for a vector of squared norm ss (> 0, finite): every component lies below 2^(E-1)
+// (|v_i| <= sqrt(ss) < 2^(floor(ilogb(ss) / 2) + 1)), with a factor 2 to spare
+__host__ __device__ __forceinline__ int fx_exponent(double ss) {
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(ss);
+#else
+  long long b;
+  __builtin_memcpy(&b, &ss, sizeof b);
+#endif
+  const int e2 = (int)((b >> 52) & 0x7FF) - 1023;
+  return (e2 >> 1) + 2;
+}
+
+// load conversion of sweep_L: FP64 source to the fixed point of scale 2^sh (sh = 58 - E)
+struct LoadFx {
+  int sh;
+  __device__ __forceinline__ long long operator()(double v) const { return fx_from_double(v, sh); }
+};
+__device__ __forceinline__ long long shfl_up1(long long v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
 template <class T>
 struct SweepGroupSmemT {
   T fz[2][kGroupWarps][32];
@@ -101,10 +184,13 @@ __device__ __forceinline__ void group_sync(int grp) {
 // n <= 800); bounds tests are hoisted out of the plane loop.
 // Templated on the value type T (double for the FP64 path, float or the
 // float-float ffv for the inner solves of the refined paths); arithmetic is in T.
+// Values are loaded as M (= T by default) and turned into T by cv (the identity by
+// default; the FP64 PCG's direction sweep loads FP64 and runs the stencil in 64-bit
+// fixed point, exactly, on the integer pipes).
 // Must be called by all kBlock threads of the block.
-template <class T, class Epi>
-__device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, int part, int nparts,
-                        SweepSmemT<T>& sm, Epi& epi) {
+template <class T, class Epi, class M, class Cv = LoadAs>
+__device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, int part, int nparts,
+                        SweepSmemT<T>& sm, Epi& epi, Cv cv = Cv()) {
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
@@ -139,23 +225,23 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
       const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
       const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
       const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
-      const T* __restrict__ sx_ = s;
-      const T* __restrict__ sy_ = s + n3;
-      const T* __restrict__ sz_ = s + 2 * n3;
+      const M* __restrict__ sx_ = s;
+      const M* __restrict__ sy_ = s + n3;
+      const M* __restrict__ sz_ = s + 2 * n3;
       int o = col ? i + n * (j + n * ks) : 0;     // position of plane ks
       // all loads of the segment start issued together: warm-up plane ks - 1,
       // plane ks (own, x+1 and y+1 neighbours) and own values of plane ks + 1
       const bool wu = (ks >= 1) && col;
       const int om = o - n2;
-      const T xm = wu ? sx_[om] : T(0), ym = wu ? sy_[om] : T(0), zm = wu ? sz_[om] : T(0);
-      const T zim = (wu && vi1) ? sz_[om + 1] : T(0), zjm = (wu && vj1) ? sz_[om + n] : T(0);
+      const T xm = wu ? cv(sx_[om]) : T(0), ym = wu ? cv(sy_[om]) : T(0), zm = wu ? cv(sz_[om]) : T(0);
+      const T zim = (wu && vi1) ? cv(sz_[om + 1]) : T(0), zjm = (wu && vj1) ? cv(sz_[om + n]) : T(0);
       T x0 = 0, y0 = 0, z0 = 0;
       T yi = 0, zi = 0, xj = 0, zj = 0, xk = 0, yk = 0, zk = 0;
       if (col) {
-        x0 = sx_[o]; y0 = sy_[o]; z0 = sz_[o];
-        if (vi1) { yi = sy_[o + 1]; zi = sz_[o + 1]; }
-        if (vj1) { xj = sx_[o + n]; zj = sz_[o + n]; }
-        if (ks + 1 < n) { xk = sx_[o + n2]; yk = sy_[o + n2]; zk = sz_[o + n2]; }
+        x0 = cv(sx_[o]); y0 = cv(sy_[o]); z0 = cv(sz_[o]);
+        if (vi1) { yi = cv(sy_[o + 1]); zi = cv(sz_[o + 1]); }
+        if (vj1) { xj = cv(sx_[o + n]); zj = cv(sz_[o + n]); }
+        if (ks + 1 < n) { xk = cv(sx_[o + n2]); yk = cv(sy_[o + n2]); zk = cv(sz_[o + n2]); }
       }
       if (act) epi.prefetch(o);
       // warm-up fluxes bx, by at plane ks - 1 (zero when ks = 0: unused there)
@@ -166,8 +252,9 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
       }
       int buf = 0;
       for (int k = ks; k < ke; ++k, o += n2) {
-        // issue the next plane's loads first
-        T nyi = 0, nzi = 0, nxj = 0, nzj = 0, nxk = 0, nyk = 0, nzk = 0;
+        // issue the next plane's loads first; they are converted only when they become
+        // the current plane's values, so the plane step never waits on them
+        M nyi = M(0), nzi = M(0), nxj = M(0), nzj = M(0), nxk = M(0), nyk = M(0), nzk = M(0);
         const int o1 = o + n2;
         if (col && k + 1 < ke) {
           if (vi1) { nyi = sy_[o1 + 1]; nzi = sz_[o1 + 1]; }
@@ -197,7 +284,7 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
         }
         bxm = bx; bym = by;
         x0 = xk; y0 = yk; z0 = zk;
-        yi = nyi; zi = nzi; xj = nxj; zj = nzj; xk = nxk; yk = nyk; zk = nzk;
+        yi = cv(nyi); zi = cv(nzi); xj = cv(nxj); zj = cv(nzj); xk = cv(nxk); yk = cv(nyk); zk = cv(nzk);
         buf ^= 1;
       }
     } else {
@@ -209,39 +296,47 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
       const int jr = j0 + lane;
       const bool hcol = (i0 >= 1) && (lane < kTY) && (jr < n);
       const bool hi1 = hrow && (i + 1 < n), hj1 = hcol && (jr + 1 < n);
-      const T* __restrict__ sx_ = s;
-      const T* __restrict__ sy_ = s + n3;
-      const T* __restrict__ sz_ = s + 2 * n3;
+      const M* __restrict__ sx_ = s;
+      const M* __restrict__ sy_ = s + n3;
+      const M* __restrict__ sz_ = s + 2 * n3;
       int oh = hrow ? i + n * (jh + n * ks) : 0;          // halo row position, plane ks
       int oc = hcol ? (i0 - 1) + n * (jr + n * ks) : 0;   // halo column position, plane ks
       T a[7], c[8];
-      auto load_row = [&](int k, int o, T* v) {
+      // raw loads (converted when used, as in the row warps)
+      auto load_row = [&](int k, int o, M* v) {
         v[0] = sx_[o]; v[1] = sy_[o]; v[2] = sz_[o];
-        v[3] = hi1 ? sy_[o + 1] : T(0);
+        v[3] = hi1 ? sy_[o + 1] : M(0);
         v[4] = sx_[o + n]; v[5] = sz_[o + n];
-        v[6] = (k + 1 < n) ? sy_[o + n2] : T(0);
+        v[6] = (k + 1 < n) ? sy_[o + n2] : M(0);
       };
-      auto load_col = [&](int k, int o, T* v) {
+      auto load_col = [&](int k, int o, M* v) {
         v[0] = sx_[o]; v[1] = sy_[o + 1];
-        v[2] = hj1 ? sx_[o + n] : T(0);
+        v[2] = hj1 ? sx_[o + n] : M(0);
         v[3] = sy_[o]; v[4] = sz_[o];
-        v[5] = (k + 1 < n) ? sx_[o + n2] : T(0);
+        v[5] = (k + 1 < n) ? sx_[o + n2] : M(0);
         v[6] = sz_[o + 1];
-        v[7] = T(0);
+        v[7] = M(0);
       };
+      {
+        M ra[7], rc[8];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) a[q] = T(0);
+        for (int q = 0; q < 7; ++q) ra[q] = M(0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) c[q] = T(0);
-      if (hrow) load_row(ks, oh, a);
-      if (hcol) load_col(ks, oc, c);
+        for (int q = 0; q < 8; ++q) rc[q] = M(0);
+        if (hrow) load_row(ks, oh, ra);
+        if (hcol) load_col(ks, oc, rc);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) a[q] = cv(ra[q]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c[q] = cv(rc[q]);
+      }
       int buf = 0;
       for (int k = ks; k < ke; ++k) {
-        T na[7], nc[8];
+        M na[7], nc[8];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) na[q] = T(0);
+        for (int q = 0; q < 7; ++q) na[q] = M(0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) nc[q] = T(0);
+        for (int q = 0; q < 8; ++q) nc[q] = M(0);
         if (k + 1 < ke) {
           if (hrow) load_row(k + 1, oh + n2, na);
           if (hcol) load_col(k + 1, oc + n2, nc);
@@ -258,9 +353,9 @@ __device__ void sweep_L(const Geom& g, const T* __restrict__ s, const Box& box, 
         }
         group_sync(grp);
 #pragma unroll
-        for (int q = 0; q < 7; ++q) a[q] = na[q];
+        for (int q = 0; q < 7; ++q) a[q] = cv(na[q]);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) c[q] = nc[q];
+        for (int q = 0; q < 8; ++q) c[q] = cv(nc[q]);
         buf ^= 1;
       }
     }
@@ -400,6 +495,55 @@ __device__ __forceinline__ bool grid_sum2(T v0, T v1, T& s0, T& s1, void* part, 
   }
   __syncthreads();
   s0 = gs[0]; s1 = gs[1];
+  slot ^= 1;
+  return true;
+}
+
+// grid_sum2 of (v0, v1) together with the grid-wide maxima of three ints m0..m2 in
+// [0, 2^16) (biased exponents), packed into the third partial slot of each block:
+// one grid barrier for all five.  The maxima take one warp instruction per warp
+// (redux.sync) and one more warp after the barrier.  gm: 3 ints of shared memory.
+__device__ __forceinline__ bool grid_sum2_max3(double v0, double v1, int m0, int m1, int m2, double& s0, double& s1,
+                                               int& x0, int& x1, int& x2, void* part, int& slot, unsigned& nbar,
+                                               unsigned* bar, long long spin, int* err, double* red, double* gs,
+                                               int* gm) {
+  __shared__ int wm[3][32];
+  const int nb = gridDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* p0 = reinterpret_cast<double*>(part) + (size_t)slot * 4 * nb;
+  double* p1 = p0 + nb;
+  long long* p2 = reinterpret_cast<long long*>(p0 + 2 * nb);
+  const int a0 = __reduce_max_sync(0xffffffffu, m0), a1 = __reduce_max_sync(0xffffffffu, m1);
+  const int a2 = __reduce_max_sync(0xffffffffu, m2);
+  if (lane == 0) { wm[0][w] = a0; wm[1][w] = a1; wm[2][w] = a2; }
+  double t0, t1;
+  block_sum2(v0, v1, red, t0, t1);                    // its block barrier also publishes wm
+  if (threadIdx.x == 0) {
+    int b0 = 0, b1 = 0, b2 = 0;
+    for (int q = 0; q < nw; ++q) { b0 = max(b0, wm[0][q]); b1 = max(b1, wm[1][q]); b2 = max(b2, wm[2][q]); }
+    p0[blockIdx.x] = t0;
+    p1[blockIdx.x] = t1;
+    p2[blockIdx.x] = (long long)b0 | ((long long)b1 << 16) | ((long long)b2 << 32);
+  }
+  if (!grid_barrier(bar, nb * (++nbar), spin, err)) return false;
+  if (w < 2) {
+    const double t = warp_fixed_sum(w ? p1 : p0, nb);
+    if (lane == 0) gs[w] = t;
+  } else if (w == 2) {
+    int c0 = 0, c1 = 0, c2 = 0;
+    for (int q = lane; q < nb; q += 32) {
+      const long long pk = p2[q];
+      c0 = max(c0, (int)(pk & 0xFFFF));
+      c1 = max(c1, (int)((pk >> 16) & 0xFFFF));
+      c2 = max(c2, (int)((pk >> 32) & 0xFFFF));
+    }
+    c0 = __reduce_max_sync(0xffffffffu, c0);
+    c1 = __reduce_max_sync(0xffffffffu, c1);
+    c2 = __reduce_max_sync(0xffffffffu, c2);
+    if (lane == 0) { gm[0] = c0; gm[1] = c1; gm[2] = c2; }
+  }
+  __syncthreads();
+  s0 = gs[0]; s1 = gs[1];
+  x0 = gm[0]; x1 = gm[1]; x2 = gm[2];
   slot ^= 1;
   return true;
 }

@@ -7,7 +7,10 @@
 // stencil scaling).  Per iteration, with one grid barrier after each of the
 // two reductions of the Hestenes-Stiefel recurrences:
 //   phase A  t = L r;  q = t + beta q;  p = r + beta p;  pq = p.q
-//            (q = L p by linearity, so the stencil reads r, which is final)
+//            (q = L p by linearity, so the stencil reads r, which is final;
+//            t is formed exactly in 64-bit fixed point on the integer pipes,
+//            with r rounded once to 2^(E-58), |r_i| < 2^(E-1), and t rounded
+//            once back to FP64: see fx_from_double in mqs_internal.cuh)
 //   phase B  x += alpha p;  r -= alpha q;  rr = r.r
 // Convergence ||r|| <= tol ||b|| is confirmed on the true residual b - L x,
 // whose stencil output L x is kept for the start-vector history.
@@ -71,25 +74,33 @@ struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
   }
 };
 
-struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
-  double* p; double* q; long long n3; double beta; bool first;
+// The direction sweep of the FP64 kernel: t = L r formed exactly in 64-bit fixed point
+// (sweep_L with LoadFx: r_i -> round(r_i 2^(58-E)), E from ||r||^2, see fx_exponent),
+// converted back once (t 2^(E-58)); then q = t + beta q, p = r + beta p on n-edges and
+// p.q, in FP64.  The FP64 r for p is loaded here (the sweep's source values are the
+// fixed-point ones).
+struct EpiDirectionFx {
+  double* p; double* q; const double* r; long long n3; double beta; bool first; int sh;
   double pq = 0.0;
-  double pp[3], qp[3];
+  double pp[3], qp[3], rp[3];
   __device__ void prefetch(long long e) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rp[c] = r[e + c * n3];
     if (first) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c) { pp[c] = p[e + c * n3]; qp[c] = q[e + c * n3]; }
   }
-  __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double sx, double sy,
-                             double sz) {
-    const double t[3] = {tx, ty, tz}, s[3] = {sx, sy, sz};
+  __device__ void operator()(long long e, unsigned m, long long tx, long long ty, long long tz, long long,
+                             long long, long long) {
+    const long long t[3] = {tx, ty, tz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long idx = e + c * n3;
       double qn = 0.0, pn = 0.0;
       if (m >> c & 1u) {
-        qn = first ? t[c] : fma(beta, qp[c], t[c]);
-        pn = first ? s[c] : fma(beta, pp[c], s[c]);
+        const double tc = fx_to_double(t[c], sh);
+        qn = first ? tc : fma(beta, qp[c], tc);
+        pn = first ? rp[c] : fma(beta, pp[c], rp[c]);
         pq = fma(pn, qn, pq);
       }
       q[idx] = qn; p[idx] = pn;
@@ -104,7 +115,11 @@ struct EpiDirection {  // q = t + beta q, p = r + beta p on n-edges; sums p.q
 template <int BPS>
 __global__ void __launch_bounds__(kBlock, BPS) pcg_kernel(PcgArgs a) {
   if (pcg_halted(a.halt, a.out)) return;
-  __shared__ SweepSmem sm;
+  __shared__ union {
+    SweepSmem d;                      // FP64 sweeps (residuals)
+    SweepSmemT<long long> fx;         // the fixed-point direction sweep
+  } smu;
+  SweepSmem& sm = smu.d;
   __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
@@ -165,8 +180,10 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_kernel(PcgArgs a) {
     for (;;) {
       double pq = 0.0, dummy;
       {
-        EpiDirection ep{a.p, a.q, a.g.n3, beta, first};
-        sweep_L(a.g, a.r, a.full, bid, nb, sm, ep);
+        // every |r_i| <= ||r||_2 < 2^(E-1): the stencil runs exactly in 64-bit integers
+        const int E = fx_exponent(rr);
+        EpiDirectionFx ep{a.p, a.q, a.r, a.g.n3, beta, first, E - 58};
+        sweep_L(a.g, a.r, a.full, bid, nb, smu.fx, ep, LoadFx{58 - E});
         if (!reduce2(ep.pq, 0.0, pq, dummy)) return;
       }
       ++it;
@@ -264,11 +281,28 @@ struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; }
 // iteration is one fused pass (sweep_fused) and one grid reduction of
 // (gamma, delta).  Same iterates as the two-reduction kernel in exact
 // arithmetic; convergence is confirmed on the true residual as there.
+// Scale of the fixed-point pass: E with bound < 2^(E-1) (bound >= every |r_{i+1}|); the
+// pass converts with 2^(58-E) (|R| < 2^57, |L R| < 2^61).
+__device__ __forceinline__ int fx_exponent_of_bound(double bound) {
+  const int eb = (int)((__double_as_longlong(bound) >> 52) & 0x7FF);
+  return (eb == 0 ? -1022 : eb - 1023) + 2;
+}
+// an upper bound of |v| for every v whose biased exponent is at most e (e > 0), 2^(e - 1022)
+__device__ __forceinline__ double fx_below(int e) { return e == 0 ? 0x1.0p-1022 : ldexp(1.0, e - 1022); }
+
+// The one-reduction form: after the initial residual r and w = L r, every
+// iteration is one fused pass (sweep_fused_fx: the stencil in 64-bit fixed point) and
+// one grid reduction of (gamma, delta) with the exponent maxima that bound the next
+// pass's r_{i+2} = r_{i+1} - alpha' (w_{i+1} + beta' s_i):
+//   max |r_{i+2}| <= max |r_{i+1}| + |alpha'| (max |w_{i+1}| + |beta'| max |s_i|).
+// Same iterates as the two-reduction kernel in exact arithmetic; convergence is
+// confirmed on the true residual as there.
 __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
   if (pcg_halted(a.halt, a.out)) return;
-  __shared__ union { SweepSmem s; FusedSmemBlock f; } sm;
+  __shared__ union { SweepSmem s; FusedFxSmemBlock f; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
+  __shared__ int gm[3];
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
@@ -319,6 +353,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgA
     status = MQS_ERR_NAN;
   } else if (rr > a.tol2 * bb) {
     double gamma = rr, alpha = 0.0, beta = 0.0;
+    double mr = 0.0, mw = 0.0, ms = 0.0;   // upper bounds of max |r|, max |w| of the current r, w; of max |s|
     bool first = true;
     int restarts = 0;
     bool restart_w = true;     // w = L r must be formed for the current r
@@ -333,12 +368,26 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgA
         beta = 0.0;
         first = true;
         restart_w = false;
+        // max |r| <= ||r||_2 < 2^(E-1) and |(L r)_e| <= 16 max |r| (the absolute row sum of L)
+        mr = ldexp(1.0, fx_exponent(gamma) - 1);
+        mw = 16.0 * mr;
+        ms = 0.0;
       }
-      FusedVecs v{a.x, a.p, rb(cur), wb(cur), sb(cur), rb(cur ^ 1), wb(cur ^ 1), sb(cur ^ 1), alpha, beta, first};
+      const double bound = mr + fabs(alpha) * (mw + (first ? 0.0 : fabs(beta) * ms));
+      const int E = fx_exponent_of_bound(bound);
+      FusedFxVecs v{FusedVecs{a.x, a.p, rb(cur), wb(cur), sb(cur), rb(cur ^ 1), wb(cur ^ 1), sb(cur ^ 1), alpha, beta,
+                              first},
+                    58 - E, E - 58};
       double g1 = 0.0, d1 = 0.0;
-      sweep_fused(a.g, v, a.full, bid, nb, sm.f, g1, d1);
+      int er = 0, ew = 0, es = 0;
+      sweep_fused_fx(a.g, v, a.full, bid, nb, sm.f, g1, d1, er, ew, es);
       double gn, dn;
-      if (!reduce2(g1, d1, gn, dn)) return;
+      if (!grid_sum2_max3(g1, d1, er, ew, es, gn, dn, er, ew, es, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs,
+                          gm))
+        return;
+      mr = fx_below(er);
+      mw = fx_below(ew);
+      ms = fx_below(es);
       ++it;
       cur ^= 1;
       if (!isfinite(gn) || !isfinite(dn)) { status = MQS_ERR_NAN; need_true = true; break; }

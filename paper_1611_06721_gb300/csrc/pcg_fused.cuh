@@ -296,4 +296,245 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
   }
 }
 
+// ---- the FP64 one-reduction pass with the stencil in 64-bit fixed point ------------
+// As sweep_fused for T = double, but the shared stencil sources are the integers
+// R = round(r_{i+1} 2^sh_in) (fx_from_double; every |r_{i+1}| < 2^(58 - sh_in - 1) by the
+// bound the kernel derives from the previous reduction), the face fluxes and L R are
+// exact 64-bit integer sums, and w_{i+1} = (L R) 2^sh_out is rounded once (sh_out =
+// -sh_in).  r_{i+1} is formed in FP64 (the FMAs of fused_apply / fused_src) by its owner,
+// and by the halo warp for the tile halo, bitwise the same in both; gamma and delta
+// are FP64 sums of the FP64 r_{i+1} and w_{i+1}.  Besides them the pass returns the
+// largest biased FP64 exponents over the owned values of r_{i+1}, w_{i+1} and s_i, from
+// which the next pass's scale is bounded.
+struct FusedFxVecs {
+  FusedVecs v;
+  int sh_in, sh_out;
+};
+struct FusedFxSmem {
+  long long src[2][3][kTY + 2][34];
+  long long fz[2][kTY + 1][32];
+  long long fx[2][kTY + 1][32];
+  long long hz[2][kTY];
+  long long hy[2][kTY];
+};
+struct FusedFxSmemBlock { FusedFxSmem g[kGroups]; };
+
+// biased FP64 exponent field of v (|v| < 2^(e - 1022) for e > 0; 0 for zero and subnormals)
+__device__ __forceinline__ int fx_expo(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
+__device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, const Box& box, int part, int nparts,
+                               FusedFxSmemBlock& smb, double& gamma, double& delta, int& mer, int& mew,
+                               int& mes) {
+  const FusedVecs& v = fv.v;
+  const int shi = fv.sh_in, sho = fv.sh_out;
+  const int n = g.n;
+  const int n2 = n * n;
+  const int n3 = (int)g.n3;
+  const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
+  FusedFxSmem& sg = smb.g[grp];
+  const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
+  if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
+  const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
+  const long long ntiles = (long long)ntx * nty * nz;
+  const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
+  long long u = ntiles * gp / gn;
+  const long long u1 = ntiles * (gp + 1) / gn;
+  const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
+  // owned position: the FP64 update of fused_apply, the exponents of r_{i+1} and s_i
+  auto own_apply = [&](int o, const FusedLoadT<double>& L, double* rn) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double sv = v.first ? L.w[c] : fma(v.beta, L.s[c], L.w[c]);
+      const double r1 = fma(-v.alpha, sv, L.r[c]);
+      const int e = o + c * n3;
+      const double pv = v.first ? L.r[c] : fma(v.beta, L.p[c], L.r[c]);
+      v.s_out[e] = sv;
+      v.p[e] = pv;
+      v.x[e] = fma(v.alpha, pv, L.x[c]);
+      v.r_out[e] = r1;
+      rn[c] = r1;
+      mes = max(mes, fx_expo(sv));
+      mer = max(mer, fx_expo(r1));
+    }
+  };
+  // r_{i+1} of a position this group does not own (no writes)
+  auto other_apply = [&](const FusedLoadT<double>& L, double* rn) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double sv = v.first ? L.w[c] : fma(v.beta, L.s[c], L.w[c]);
+      rn[c] = fma(-v.alpha, sv, L.r[c]);
+    }
+  };
+  while (u < u1) {
+    const long long tc = u / nz;
+    const int ka = (int)(u % nz);
+    int len = nz - ka;
+    if ((long long)len > u1 - u) len = (int)(u1 - u);
+    if (len > kMaxSeg) len = kMaxSeg;
+    u += len;
+    const int i0 = box.lo[0] + (int)(tc % ntx) * 32;
+    const int j0 = box.lo[1] + (int)(tc / ntx) * kTY;
+    const int ks = box.lo[2] + ka, ke = ks + len;
+    const int i = i0 + lane;
+    group_sync(grp);  // smem reuse across segments
+    if (w < kTY) {
+      const int j = j0 + w;
+      const bool act = (i < box.hi[0]) && (j < box.hi[1]);   // owned position
+      const bool col = (i < n) && (j < n);
+      const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
+      const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
+      const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
+      int o = col ? i + n * (j + n * ks) : 0;
+      // prologue: plane ks (owned: updated), warm-up fluxes at ks - 1 from recomputed sources
+      double skd[3] = {0.0, 0.0, 0.0};
+      long long sk[3] = {0, 0, 0};
+      if (col) {
+        FusedLoadT<double> L0;
+        fused_load(v, o, n3, act, L0);
+        if (act) own_apply(o, L0, skd);
+        else other_apply(L0, skd);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sk[c] = fx_from_double(skd[c], shi);
+        sg.src[ks & 1][c][w + 1][lane + 1] = sk[c];
+      }
+      long long bxm = 0, bym = 0;
+      if (ks >= 1 && col) {
+        const int om = o - n2;
+        const long long xm = fx_from_double(fused_src(v, om), shi), ym = fx_from_double(fused_src(v, om + n3), shi);
+        const long long zm = fx_from_double(fused_src(v, om + 2 * n3), shi);
+        const long long zim = (i + 1 < n) ? fx_from_double(fused_src(v, om + 1 + 2 * n3), shi) : 0;
+        const long long zjm = (j + 1 < n) ? fx_from_double(fused_src(v, om + n + 2 * n3), shi) : 0;
+        bxm = (ym - zm) + (zjm - sk[1]);
+        bym = (zm - xm) + (sk[0] - zim);
+      }
+      group_sync(grp);
+      FusedLoadT<double> ld1;
+      if (col && ks + 1 < n) fused_load(v, o + n2, n3, act && ks + 1 < ke, ld1);
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k, o += n2) {
+        const int nb = buf ^ 1;
+        // own r_{i+1} of plane k+1 from the inputs loaded during the previous step
+        double sk1d[3] = {0.0, 0.0, 0.0};
+        if (col && k + 1 < n) {
+          if (act && k + 1 < ke) own_apply(o + n2, ld1, sk1d);
+          else other_apply(ld1, sk1d);
+        }
+        long long sk1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sk1[c] = fx_from_double(sk1d[c], shi);
+          sg.src[nb][c][w + 1][lane + 1] = sk1[c];
+        }
+        // then issue the loads of plane k+2
+        if (col && k + 2 < n && k + 1 < ke) fused_load(v, o + 2 * n2, n3, act && k + 2 < ke, ld1);
+        const long long yi = sg.src[buf][1][w + 1][lane + 2], zi = sg.src[buf][2][w + 1][lane + 2];
+        const long long xj = sg.src[buf][0][w + 2][lane + 1], zj = sg.src[buf][2][w + 2][lane + 1];
+        const long long bx = (sk[1] - sk[2]) + (zj - sk1[1]);
+        const long long by = (sk[2] - sk[0]) + (sk1[0] - zi);
+        const long long bz = (sk[0] - sk[1]) + (yi - xj);
+        sg.fz[buf][w + 1][lane] = bz;
+        sg.fx[buf][w + 1][lane] = bx;
+        group_sync(grp);
+        long long bzi = shfl_up1(bz), byi = shfl_up1(by);
+        if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
+        const long long bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
+        if (act) {
+          const long long t[3] = {(bz - bzj) + (bym - by), (bzi - bz) + (bx - bxm), (bxj - bx) + (by - byi)};
+          unsigned m = mcol & (k > 0 ? 7u : 4u);
+          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double wv = (m >> c & 1u) ? fx_to_double(t[c], sho) : 0.0;
+            v.w_out[o + c * n3] = wv;
+            gamma = fma(skd[c], skd[c], gamma);
+            delta = fma(wv, skd[c], delta);
+            mew = max(mew, fx_expo(wv));
+          }
+        }
+        bxm = bx; bym = by;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { sk[c] = sk1[c]; skd[c] = sk1d[c]; }
+        buf = nb;
+      }
+    } else {
+      // halo warp, as in sweep_fused: r_{i+1} on the tile halo of plane k+1 (converted to
+      // the fixed point), then the halo fluxes of plane k
+      constexpr int kSlots = 2 * 34 + 2 * kTY;
+      auto slot_pos = [&](int sl, int& hi, int& hj, int& row, int& cl) {
+        if (sl < 34) { hi = i0 - 1 + sl; hj = j0 - 1; row = 0; cl = sl; }
+        else if (sl < 68) { hi = i0 - 1 + (sl - 34); hj = j0 + kTY; row = kTY + 1; cl = sl - 34; }
+        else if (sl < 68 + kTY) { hi = i0 - 1; hj = j0 + (sl - 68); row = sl - 68 + 1; cl = 0; }
+        else { hi = i0 + 32; hj = j0 + (sl - 68 - kTY); row = sl - 68 - kTY + 1; cl = 33; }
+      };
+      constexpr int kHS = (kSlots + 31) / 32;
+      struct HaloIn { double r[3], w[3], s[3]; };
+      auto halo_load = [&](int kk, HaloIn* hin) {
+#pragma unroll
+        for (int q = 0; q < kHS; ++q) {
+          const int sl = lane + 32 * q;
+          int hi = -1, hj = -1, row = 0, cl = 0;
+          if (sl < kSlots) slot_pos(sl, hi, hj, row, cl);
+          const bool ok = sl < kSlots && hi >= 0 && hj >= 0 && hi < n && hj < n && kk >= 0 && kk < n;
+          const int oo = ok ? hi + n * (hj + n * kk) : 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : 0.0;
+            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : 0.0;
+            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : 0.0;
+          }
+        }
+      };
+      auto halo_store = [&](const HaloIn* hin, int bufw) {
+#pragma unroll
+        for (int q = 0; q < kHS; ++q) {
+          const int sl = lane + 32 * q;
+          if (sl >= kSlots) continue;
+          int hi, hj, row, cl;
+          slot_pos(sl, hi, hj, row, cl);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double sv = v.first ? hin[q].w[c] : fma(v.beta, hin[q].s[c], hin[q].w[c]);
+            sg.src[bufw][c][row][cl] = fx_from_double(fma(-v.alpha, sv, hin[q].r[c]), shi);
+          }
+        }
+      };
+      HaloIn h[kHS];
+      halo_load(ks, h);
+      halo_store(h, ks & 1);
+      halo_load(ks + 1, h);
+      group_sync(grp);
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k) {
+        const int nb = buf ^ 1;
+        halo_store(h, nb);                     // plane k+1, loaded during the previous step
+        if (k + 2 <= ke) halo_load(k + 2, h);  // in flight until the next step
+        __syncwarp();
+        {
+          const long long x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
+          const long long z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
+          const long long xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
+          const long long yk = sg.src[nb][1][0][lane + 1];
+          const bool hrow = (j0 >= 1) && (i < n);
+          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : 0;
+          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : 0;
+        }
+        if (lane < kTY) {
+          const int r = lane + 1;
+          const long long x0 = sg.src[buf][0][r][0], y0 = sg.src[buf][1][r][0], z0 = sg.src[buf][2][r][0];
+          const long long yi = sg.src[buf][1][r][1], zi = sg.src[buf][2][r][1];
+          const long long xj = sg.src[buf][0][r + 1][0];
+          const long long xk = sg.src[nb][0][r][0];
+          const bool hcol = (i0 >= 1) && (j0 + lane < n);
+          sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : 0;
+          sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : 0;
+        }
+        group_sync(grp);
+        buf = nb;
+      }
+    }
+  }
+}
+
 }  // namespace mqs
