@@ -575,9 +575,9 @@ def size_sweep(sizes):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for n in sizes:
         p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
-        for prec in (0, 1):
+        for prec, var in ((0, 1), (1, 1), (1, 2)):
             s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
-                                                             pcg_variant=prec))
+                                                             pcg_variant=var))
             stream = torch.cuda.Stream(device=dev)
             s.set_stream(stream.cuda_stream)
             with torch.cuda.stream(stream):
@@ -598,9 +598,10 @@ def size_sweep(sizes):
                     its = info.iterations
             ms = statistics.median(times)
             us_it = 1e3 * ms / max(its, 1)
-            gbs = (48 if prec == 0 else 24) * s.n_n / (us_it * 1e-6) / 1e9
+            gbs = BYTES_PER_ITER[prec] * s.n_n / (us_it * 1e-6) / 1e9
             print(json.dumps({"sweep": "zero-start solve", "workload": workload_name(p), "grid": n,
                               "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
+                              "pcg_variant": var,
                               "n_unknowns": int(s.n_n), "iterations": int(its), "relres": info.relres,
                               "status": int(info.status), "ms_per_solve": ms, "us_per_iteration": us_it,
                               "algorithmic_GBps": gbs, "hbm_peak_GBps": peaks.get("hbm_gbs"),
@@ -943,8 +944,9 @@ def main():
                          "SPE history (the paper's separate right-hand sides)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="replay steady-state SPE steps from CUDA graphs (1, default) or issue every launch (0)")
-    ap.add_argument("--pcg-variant", type=int, default=1, choices=[0, 1],
-                    help="0: two grid reductions per PCG iteration, 1: one (fused pass; default)")
+    ap.add_argument("--pcg-variant", type=int, default=1, choices=[0, 1, 2],
+                    help="0: two grid reductions per PCG iteration, 1: one (fused pass; default), 2: with "
+                         "--precision 1, the inner pass carrying x, r, p only (24 B per unknown)")
     ap.add_argument("--grid", type=int, default=64,
                     help="cells per axis of the iron workload (64: the benchmark; others scale it)")
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")

@@ -121,7 +121,11 @@ typedef struct {
                              Gear recurrences, one fused stencil pass per
                              iteration). Same iterates in exact arithmetic.
                              With precision 1 it selects the form of the FP32
-                             inner CG the same way. */
+                             inner CG the same way.  2: with precision 1, the
+                             one-reduction inner CG whose pass carries x, r and p
+                             only (s = L p and w = L r formed in the pass: 24 bytes
+                             per unknown and iteration instead of 40); with
+                             precision 0 the same as 1. */
     int    precision;     /* 0: FP64 PCG (default); 1: FP64 iterative refinement
                              around FP32 CG inner solves (stencil, vectors and
                              products in FP32; residual, norms, convergence test

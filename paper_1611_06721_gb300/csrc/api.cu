@@ -300,7 +300,7 @@ int ensure_mixed(mqs_handle* H) {
   // 8 bytes per value: float-float inner vectors (precision 2); FP32 uses the first half
   if (!H->r32)
     for (float** v : {&H->r32, &H->p32, &H->q32, &H->d32}) RK(dalloc(H, v, 2 * H->len));
-  if ((H->opt.pcg_variant == 1 || H->opt.precision == 2) && !H->r32b)
+  if ((H->opt.pcg_variant >= 1 || H->opt.precision == 2) && !H->r32b)
     for (float** v : {&H->r32b, &H->w32a, &H->w32b, &H->s32a, &H->s32b}) RK(dalloc(H, v, 2 * H->len));
   return MQS_OK;
 }
@@ -322,7 +322,7 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
     return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
                             maxit, H->nblk, st, init, H->opt.pcg_variant, halt);
   }
-  if (H->opt.pcg_variant == 1) {
+  if (H->opt.pcg_variant >= 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
                             H->nblk, st, init, halt);
@@ -536,7 +536,7 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (o->pod_snapshots < 1 || o->pod_snapshots > kMaxPod) { why = "pod_snapshots must be in [1, 40]"; return MQS_ERR_ARG; }
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
-  if (o->pcg_variant != 0 && o->pcg_variant != 1) { why = "pcg_variant must be 0 or 1"; return MQS_ERR_ARG; }
+  if (o->pcg_variant < 0 || o->pcg_variant > 2) { why = "pcg_variant must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (o->precision < 0 || o->precision > 2) { why = "precision must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }

@@ -119,13 +119,249 @@ struct EpiApplyDot32 {  // w = t on n-edges (0 elsewhere, FP32); sums w.r with r
   }
 };
 
+// ---- the FP32 inner pass that carries x, r and p only (pcg_variant 2) -------------
+// Chronopoulos-Gear CG with s = L p and w = L r formed in the pass instead of stored:
+//   p_i = r_i + beta p_{i-1},  s_i = L p_i,  x += alpha p_i,  r_{i+1} = r_i - alpha s_i,
+//   w_{i+1} = L r_{i+1},  gamma = r_{i+1}.r_{i+1},  delta = r_{i+1}.w_{i+1}
+// (s_i = w_i + beta s_{i-1} = L p_i by linearity: the same iterates in exact arithmetic as
+// the fused pass).  A pass reads r_i and p_{i-1} (with a two-deep halo) and x, and writes
+// p_i, r_{i+1} and x: 24 B per unknown in FP32, the three carried vectors once each way,
+// against 40 B when s and w are stored.  A block (kWarps warps) owns a tile of kCgTX x
+// kCgTY positions and covers the 32 x kWarps region around it: warp w is region row
+// j0 - 2 + w, lane l region column i0 - 2 + l.  Marching along z, step k forms p(k+1)
+// (whole region), the fluxes of p at plane k, s(k) and r_{i+1}(k) (one-deep region), the
+// fluxes of r_{i+1} at plane k-1 and w(k-1) (owned tile), and writes the owned outputs of
+// plane k-1.  Each thread stages its own column's r and p_{i-1} kCgAhead planes ahead with
+// cp.async (zero-filled outside the grid; only the thread reads them back, so the ring
+// needs no barrier); rows are exchanged through double-buffered shared memory with two
+// block barriers per step.  A segment starts 2 planes early: the owned output of plane m
+// needs r_{i+1} at m-1..m+1, hence s there, hence the fluxes of p from plane m-2 on.
+constexpr int kCgTX = 28, kCgTY = kWarps - 4;
+constexpr int kCgAhead = 6, kCgRing = kCgAhead + 1;
+struct Cg24Smem {
+  float stage[kCgRing][6][kBlock];          // per thread, per plane slot: r (3 comps), p_{i-1} (3)
+  // row exchange, [parity][comp][row + 1][lane]: rows -1 and kWarps stay zero (pads)
+  float p[2][2][kWarps + 2][32];            // p x, z comps by row (read by the row below)
+  float pf[2][2][kWarps + 2][32];           // p fluxes bz, bx by row (read by the row above)
+  float r1[2][2][kWarps + 2][32];           // r_{i+1} x, z comps
+  float rf[2][2][kWarps + 2][32];           // r_{i+1} fluxes bz, bx
+};
+static_assert(sizeof(Cg24Smem) == sizeof(float) * (kCgRing * 6 * kBlock + 4 * 2 * 2 * (kWarps + 2) * 32),
+              "the exchange buffers are contiguous (zeroed as one range)");
+struct Cg24Vecs {
+  const float* r_in;
+  const float* p_in;
+  float* r_out;
+  float* p_out;
+  float* x;
+  float alpha, beta;
+  bool first;
+};
+
+__device__ __forceinline__ void cp_async4(unsigned sdst, const float* gsrc, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sdst), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ float shfl_dn1f(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_up1f(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+__device__ void sweep_cg24(const Geom& g, const Cg24Vecs& v, const Box& box, int part, int nparts, Cg24Smem& sm,
+                           float& gamma, float& delta) {
+  const int n = g.n, n2 = n * n, n3 = (int)g.n3;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
+  const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
+  if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
+  const int ntx = (bx0 + kCgTX - 1) / kCgTX, nty = (by0 + kCgTY - 1) / kCgTY;
+  const long long ntiles = (long long)ntx * nty * nz;
+  long long u = ntiles * part / nparts;
+  const long long u1 = ntiles * (part + 1) / nparts;
+  const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
+  const float al = v.alpha, be = v.beta;
+  constexpr int kComp = (kWarps + 2) * 32;                // component stride of an exchange buffer
+  constexpr int kPar = 2 * kComp;                         // parity stride
+  // this thread's exchange addresses (parity 0; parity 1 at + kPar): own row, the row below
+  // (j + 1) and the row above (j - 1)
+  const int ow = (w + 1) * 32 + lane;
+  float* const xp = &sm.p[0][0][0][0] + ow;
+  float* const xpf = &sm.pf[0][0][0][0] + ow;
+  float* const xr1 = &sm.r1[0][0][0][0] + ow;
+  float* const xrf = &sm.rf[0][0][0][0] + ow;
+  const unsigned stage0 = (unsigned)__cvta_generic_to_shared(&sm.stage[0][0][t]);
+  constexpr unsigned kSlotBytes = 6u * kBlock * 4u, kCompBytes = kBlock * 4u;
+  while (u < u1) {
+    const long long tc = u / nz;
+    const int ka = (int)(u % nz);
+    int len = nz - ka;
+    if ((long long)len > u1 - u) len = (int)(u1 - u);
+    u += len;
+    const int i0 = box.lo[0] + (int)(tc % ntx) * kCgTX;
+    const int j0 = box.lo[1] + (int)(tc / ntx) * kCgTY;
+    const int ks = box.lo[2] + ka, ke = ks + len;
+    const int i = i0 - 2 + lane, j = j0 - 2 + w;        // this thread's region column
+    const bool col = i >= 0 && i < n && j >= 0 && j < n;
+    const int oc = col ? i + n * j : 0;                   // in-plane offset
+    const bool own = lane >= 2 && lane < 2 + kCgTX && w >= 2 && w < 2 + kCgTY && i < box.hi[0] && j < box.hi[1];
+    const unsigned mcol = (j > 0 ? 1u : 0u) | (i > 0 ? 2u : 0u) | ((i > 0 && j > 0) ? 4u : 0u);
+    const bool incb = col && i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
+    const uint8_t* const cfcol = incb ? g.cflags + (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : g.cflags;
+    // conductor flags of plane k (c-edges are not n-edges)
+    auto cflag = [&](int k) -> unsigned {
+      return (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) ? (unsigned)cfcol[cw01 * (k - g.cb_lo[2])] : 0u;
+    };
+    const int kb = ks - 2;                               // first step (warm-up of the lag)
+    // the staging ring: plane sm_ of slot ss_ is the next to issue
+    int st_m = kb, st_slot = 0;
+    auto stage_next = [&]() {
+      const bool ok = col && st_m >= 0 && st_m < n && st_m <= ke + 1;
+      const bool okp = ok && !v.first;
+      const int off = ok ? oc + n2 * st_m : 0;
+      const unsigned sa = stage0 + (unsigned)st_slot * kSlotBytes;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cp_async4(sa + c * kCompBytes, v.r_in + (ok ? off + c * n3 : 0), ok ? 4 : 0);
+        cp_async4(sa + (3 + c) * kCompBytes, v.p_in + (okp ? off + c * n3 : 0), okp ? 4 : 0);
+      }
+      cp_async_commit();
+      ++st_m;
+      st_slot = (st_slot + 1 == kCgRing) ? 0 : st_slot + 1;
+    };
+    __syncthreads();                                     // shared memory reuse across segments
+    {
+      // the row exchange buffers (and their pad rows) start at zero
+      float* ex = &sm.p[0][0][0][0];
+      constexpr int kEx = 4 * 2 * 2 * (kWarps + 2) * 32;
+      for (int q = t; q < kEx; q += kBlock) ex[q] = 0.f;
+    }
+    for (int q = 0; q <= kCgAhead; ++q) stage_next();   // planes kb .. kb + kCgAhead
+    cp_async_wait<kCgAhead>();                           // plane kb
+    __syncthreads();
+    int rd_slot = 0;                                     // slot of the next plane to read
+    float rk[3], pk[3];
+    {
+      const float* st = &sm.stage[rd_slot][0][t];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rk[c] = st[c * kBlock];
+        pk[c] = v.first ? rk[c] : fmaf(be, st[(3 + c) * kBlock], rk[c]);
+      }
+      rd_slot = (rd_slot + 1 == kCgRing) ? 0 : rd_slot + 1;
+    }
+    {
+      const int par = kb & 1;
+      xp[par * kPar] = pk[0];
+      xp[par * kPar + kComp] = pk[2];
+    }
+    float pm1[3] = {0.f, 0.f, 0.f}, r1m1[3] = {0.f, 0.f, 0.f};
+    float pbx_m1 = 0.f, pby_m1 = 0.f, rbx_m2 = 0.f, rby_m2 = 0.f;
+    float xk[3] = {0.f, 0.f, 0.f};       // x of the plane the next output needs (loaded a step ahead)
+    unsigned cf_k = cflag(kb);
+    int ok_off = oc + n2 * kb;           // in-layout offset of plane k of this column
+    __syncthreads();
+    for (int k = kb; k <= ke; ++k, ok_off += n2) {
+      const int par = k & 1, nq = par ^ 1;
+      // plane k+1 staged; its slot is then free for plane k + 1 + kCgAhead
+      cp_async_wait<kCgAhead - 1>();
+      float rk1[3], pk1[3];
+      {
+        const float* st = &sm.stage[rd_slot][0][t];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          rk1[c] = st[c * kBlock];
+          pk1[c] = v.first ? rk1[c] : fmaf(be, st[(3 + c) * kBlock], rk1[c]);
+        }
+        rd_slot = (rd_slot + 1 == kCgRing) ? 0 : rd_slot + 1;
+      }
+      stage_next();
+      const unsigned cf_k1 = cflag(k + 1);               // for the next step
+      float xn[3] = {0.f, 0.f, 0.f};                     // x of plane k (the next step's output)
+      if (own && k >= ks && k < ke) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xn[c] = v.x[ok_off + c * n3];
+      }
+      // p(k+1) rows for the next step; fluxes of p at plane k
+      xp[nq * kPar] = pk1[0];
+      xp[nq * kPar + kComp] = pk1[2];
+      const float pxj = xp[par * kPar + 32], pzj = xp[par * kPar + kComp + 32];
+      const float pyi = shfl_dn1f(pk[1]), pzi = shfl_dn1f(pk[2]);
+      const float bx = (pk[1] - pk[2]) + (pzj - pk1[1]);
+      const float by = (pk[2] - pk[0]) + (pk1[0] - pzi);
+      const float bz = (pk[0] - pk[1]) + (pyi - pxj);
+      xpf[par * kPar] = bz;
+      xpf[par * kPar + kComp] = bx;
+      __syncthreads();
+      // s(k) = L p and r_{i+1}(k) = r(k) - alpha s(k) on n-edges
+      float r1k[3];
+      {
+        const float bzj = xpf[par * kPar - 32], bxj = xpf[par * kPar + kComp - 32];
+        const float bzi = shfl_up1f(bz), byi = shfl_up1f(by);
+        const float sx = (bz - bzj) + (pby_m1 - by);
+        const float sy = (bzi - bz) + (bx - pbx_m1);
+        const float sz = (bxj - bx) + (by - byi);
+        pbx_m1 = bx; pby_m1 = by;
+        const unsigned m = (col && k >= 0 && k < n) ? (mcol & (k > 0 ? 7u : 4u) & ~cf_k) : 0u;
+        r1k[0] = (m & 1u) ? fmaf(-al, sx, rk[0]) : 0.f;
+        r1k[1] = (m & 2u) ? fmaf(-al, sy, rk[1]) : 0.f;
+        r1k[2] = (m & 4u) ? fmaf(-al, sz, rk[2]) : 0.f;
+      }
+      xr1[par * kPar] = r1k[0];
+      xr1[par * kPar + kComp] = r1k[2];
+      // fluxes of r_{i+1} at plane k-1 (its rows of the row below were written last step)
+      const float rxj = xr1[nq * kPar + 32], rzj = xr1[nq * kPar + kComp + 32];
+      const float ryi = shfl_dn1f(r1m1[1]), rzi = shfl_dn1f(r1m1[2]);
+      const float cx = (r1m1[1] - r1m1[2]) + (rzj - r1k[1]);
+      const float cy = (r1m1[2] - r1m1[0]) + (r1k[0] - rzi);
+      const float cz = (r1m1[0] - r1m1[1]) + (ryi - rxj);
+      xrf[par * kPar] = cz;
+      xrf[par * kPar + kComp] = cx;
+      __syncthreads();
+      // w(k-1) = L r_{i+1} and the owned outputs of plane k-1
+      {
+        const float czj = xrf[par * kPar - 32], cxj = xrf[par * kPar + kComp - 32];
+        const float czi = shfl_up1f(cz), cyi = shfl_up1f(cy);
+        const float wv[3] = {(cz - czj) + (rby_m2 - cy), (czi - cz) + (cx - rbx_m2), (cxj - cx) + (cy - cyi)};
+        rbx_m2 = cx; rby_m2 = cy;
+        if (own && k - 1 >= ks && k - 1 < ke) {
+          const int o = ok_off - n2;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            v.p_out[o + c * n3] = pm1[c];
+            v.r_out[o + c * n3] = r1m1[c];
+            v.x[o + c * n3] = fmaf(al, pm1[c], xk[c]);
+            gamma = fmaf(r1m1[c], r1m1[c], gamma);
+            delta = fmaf(r1m1[c], wv[c], delta);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pm1[c] = pk[c]; pk[c] = pk1[c]; rk[c] = rk1[c]; r1m1[c] = r1k[c];
+        xk[c] = xn[c];
+      }
+      cf_k = cf_k1;
+    }
+    cp_async_wait<0>();
+  }
+}
+
+// shared memory of pcg_mixed_kernel, dynamic (the staging ring of sweep_cg24 exceeds the
+// 48 KB of static shared memory)
+union MixedSmem {
+  SweepSmemT<double> d;
+  SweepSmemT<float> f;
+  FusedSmemBlockT<float> ff;
+  Cg24Smem cg;
+};
+
 // BPS co-resident blocks per SM: 2 once the FP32 vectors are far beyond L2 (the inner
 // sweep is then bound by memory latency and plane syncs, and 20 warps per SM hide more
 // of both than 10; the register cap of 96 spills a little, in the FP64 passes), else 1.
 template <int BPS>
 __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
   if (mixed_halted(a)) return;
-  __shared__ union { SweepSmemT<double> d; SweepSmemT<float> f; FusedSmemBlockT<float> ff; } sm;
+  extern __shared__ __align__(16) unsigned char mixed_dyn[];
+  MixedSmem& sm = *reinterpret_cast<MixedSmem*>(mixed_dyn);
   __shared__ double red[32];
   __shared__ double gs[2];
   const int nb = gridDim.x, bid = blockIdx.x;
@@ -210,6 +446,38 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
                             sbuf(cur ^ 1), alpha.hi, bet.hi, first};
         float g1 = 0.f, d1 = 0.f;
         sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
+        ffv gn, dn;
+        if (!reduceF(ffv(g1, 0.f), ffv(d1, 0.f), gn, dn)) return;
+        ++it_in; ++inner_total;
+        cur ^= 1;
+        if (!isfinite(gn.hi) || !isfinite(dn.hi)) break;
+        if (ff_le(gn, stop2) || it_in >= 400) break;
+        const ffv bnew = ff_div(gn, gamma);
+        const ffv den = dn - ff_div(ff_mul(bnew, gn), alpha);
+        if (!(den.hi > 0.f)) break;               // FP32 breakdown / stagnation: refine from here
+        bet = bnew; alpha = ff_div(gn, den); gamma = gn;
+        first = false;
+      }
+    }
+    if (a.variant == 2) {
+      // one reduction per inner iteration, x, r and p carried (r, p double-buffered);
+      // delta = r.L r once for the first alpha (w into w32a, scratch)
+      auto rbuf = [&](int c) { return c ? a.r32b : a.r32; };
+      auto pbuf = [&](int c) { return c ? a.s32a : a.p32; };
+      int cur = 0;
+      ffv delta, dummy;
+      {
+        EpiApplyDot32 ep{a.w32a, a.g.n3};
+        sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
+        if (!reduceF(ffv(ep.wr, 0.f), ffv(0), delta, dummy)) return;
+      }
+      ffv gamma = rho;
+      bool ok = delta.hi > 0.f;
+      ffv alpha = ok ? ff_div(gamma, delta) : ffv(0), bet = ffv(0);
+      while (ok && inner_total < a.maxit) {
+        const Cg24Vecs v{rbuf(cur), pbuf(cur), rbuf(cur ^ 1), pbuf(cur ^ 1), a.d32, alpha.hi, bet.hi, first};
+        float g1 = 0.f, d1 = 0.f;
+        sweep_cg24(a.g, v, a.full, bid, nb, sm.cg, g1, d1);
         ffv gn, dn;
         if (!reduceF(ffv(g1, 0.f), ffv(d1, 0.f), gn, dn)) return;
         ++it_in; ++inner_total;
@@ -446,7 +714,8 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   a.b = b; a.x = x; a.r = r; a.lx = lx;
   a.r32 = mb.r32; a.p32 = mb.p32; a.q32 = mb.q32; a.d32 = mb.d32;
   a.r32b = mb.r32b; a.w32a = mb.w32a; a.w32b = mb.w32b; a.s32a = mb.s32a; a.s32b = mb.s32b;
-  a.variant = (variant == 1 && mb.r32b && mb.w32a && mb.w32b && mb.s32a && mb.s32b) ? 1 : 0;
+  const bool bufs = mb.r32b && mb.w32a && mb.w32b && mb.s32a && mb.s32b;
+  a.variant = (variant >= 1 && bufs) ? variant : 0;
   a.part = part; a.bar = bar; a.err = err; a.out = out; a.refinements = refinements;
   a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
   a.spin = 1ll << 21;
@@ -457,10 +726,10 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   // 64^3 (FP32 vectors in L2): one block per SM; from 96^3 on, two (28% faster per
   // inner iteration at 128^3, 83.6 -> 62.8 us)
   const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;
-  cudaError_t e = two ? cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel<2>, dim3(2 * nblk), dim3(kBlock),
-                                                    args, 0, st)
-                      : cudaLaunchCooperativeKernel((const void*)pcg_mixed_kernel<1>, dim3(nblk), dim3(kBlock),
-                                                    args, 0, st);
+  const void* fn = two ? (const void*)pcg_mixed_kernel<2> : (const void*)pcg_mixed_kernel<1>;
+  const int smem = (int)sizeof(MixedSmem);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return MQS_ERR_CUDA;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(two ? 2 * nblk : nblk), dim3(kBlock), args, (size_t)smem, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

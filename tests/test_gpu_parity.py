@@ -93,13 +93,13 @@ def _oracle_solve_96():
     return _REF96
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_two_blocks_per_sm_solve_matches_oracle_at_96(pkg, precision):
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (1, 1), (1, 2)])
+def test_two_blocks_per_sm_solve_matches_oracle_at_96(pkg, precision, variant):
     # from 96^3 on the FP64 PCG and the FP32-inner refinement run two blocks per SM
     # (the kernels' second instantiation); their solve against the oracle's
     r = _oracle_solve_96()
     p, d, b_n, ref = r["p"], r["d"], r["b_n"], r["ref"]
-    s = make(pkg, p, precision=precision, pcg_variant=precision)
+    s = make(pkg, p, precision=precision, pcg_variant=variant)
     b_o = np.zeros(d.grid.n_edges)
     b_o[d.n_idx] = b_n
     x_l, info = s.pcg_solve(oracle_to_layout(96, b_o), tol=1e-10)
@@ -517,7 +517,7 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant):
 
 
 # ---- mixed precision: FP32 inner solves inside FP64 refinement (same FP64 residual test) ----------
-@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (1, 2), (2, 1)])
 def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, precision, variant):
     p = W.scaled_nonlinear(35)
     d = O.Discretization(p)
@@ -534,7 +534,7 @@ def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, precision, variant)
     s.close()
 
 
-@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (1, 2), (2, 1)])
 @pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_SPE, "spe8")])
 def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, precision, variant):
     g = golden()
@@ -553,7 +553,7 @@ def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, precision, vari
     s.close()
 
 
-@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (1, 2), (2, 1)])
 def test_mixed_precision_full_size_agrees_with_fp64(pkg, precision, variant):
     p = W.config_nonlinear_iron()
     d = O.Discretization(p)
