@@ -532,6 +532,35 @@ int mqs_batch_tune_depth(mqs_batch* b, int trial_steps, const int* depths, int n
 int mqs_batch_destroy(mqs_batch* b);
 int mqs_batch_graph_steps(const mqs_batch* b, long* steps);
 
+/* ---- debug build checks --------------------------------------------------
+ * The library is also built as a debug variant (compiled with
+ * MQS_DEBUG_CHECKS) in which every index a hot kernel computes -- the
+ * stencil sweeps and fused passes, the FP32 inner pass, the conductor,
+ * right-hand-side, SPE and adjoint kernels, the step records -- is tested
+ * against the length of the array it addresses.  An access out of range is
+ * skipped (a load reads 0) and the first one per translation unit is kept
+ * with its site number and index: nothing traps.  Every device buffer a
+ * handle allocates is followed by 256 guard bytes of a fixed pattern.
+ *
+ * mqs_debug_check(h, report): synchronizes the device, reads and clears the
+ * recorded index faults of all translation units, and (h non-NULL) compares
+ * the guard bytes of every buffer of h with the pattern.
+ *   report (host, non-NULL): receives enabled = 1 in the debug variant and 0
+ *     in the release library (where everything else reads 0);
+ *   site / index: the first fault found (site 0: none); faults: how many
+ *     translation units recorded one; canaries_bad: buffers of h whose guard
+ *     bytes changed (buffers: how many were checked).
+ * Returns MQS_OK, MQS_ERR_ARG (report NULL) or MQS_ERR_CUDA. */
+typedef struct {
+  int enabled;
+  int site;
+  long long index;
+  int faults;
+  int canaries_bad;
+  int buffers;
+} mqs_debug_report;
+int mqs_debug_check(mqs_handle* h, mqs_debug_report* report);
+
 #ifdef __cplusplus
 }
 #endif

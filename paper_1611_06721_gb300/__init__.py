@@ -5,6 +5,6 @@ The compute lives in ``_lib/libmqs.so`` (hand-written CUDA, C ABI in
 ``include/mqs.h``); :mod:`.binding` marshals arguments to it.
 """
 from .binding import (  # noqa: F401
-    EXPORTS, LIB_PATH, START_CSPE, START_POD, START_PREV, START_SPE, START_ZERO, Batch, MqsError, Solver, SolverOptions, eddy_loss,
-    load,
+    DEBUG, EXPORTS, LIB_PATH, START_CSPE, START_POD, START_PREV, START_SPE, START_ZERO, Batch, MqsError, Solver,
+    SolverOptions, debug_check, eddy_loss, load,
 )

@@ -15,7 +15,10 @@ from dataclasses import dataclass, replace
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libmqs.so")
+# MQS_DEBUG=1 loads the debug variant (bounds-checked kernel indices, guard bytes
+# after every device buffer; build it with build.build(debug=True))
+DEBUG = os.environ.get("MQS_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "_lib_debug" if DEBUG else "_lib", "libmqs.so")
 
 MQS_OK = 0
 ERRORS = {-1: "MQS_ERR_ARG", -2: "MQS_ERR_CUDA", -3: "MQS_ERR_OOM", -4: "MQS_ERR_NOT_CONVERGED",
@@ -31,7 +34,8 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_timing_enable", "mqs_timing_get", "mqs_pcg_solve_noalloc", "mqs_selftest_barrier_timeout",
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
-           "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth")
+           "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth",
+           "mqs_debug_check")
 
 
 class Grid(C.Structure):
@@ -78,12 +82,18 @@ class Timing(C.Structure):
                 ("pcg_launches", C.c_long), ("steps", C.c_long)]
 
 
+class DebugReport(C.Structure):
+    _fields_ = [("enabled", C.c_int), ("site", C.c_int), ("index", C.c_longlong), ("faults", C.c_int),
+                ("canaries_bad", C.c_int), ("buffers", C.c_int)]
+
+
 class PcgInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double),
                 ("start_relres", C.c_double)]
 
 
 _lib = None
+_live = weakref.WeakSet()     # open solvers (the debug check visits their buffers)
 
 
 def load():
@@ -92,8 +102,8 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1611_06721_gb300.build.build() "
-                           "(the library has no CPU fallback)")
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1611_06721_gb300.build.build("
+                           f"{'debug=True' if DEBUG else ''}) (the library has no CPU fallback)")
     lib = C.CDLL(LIB_PATH)
     P, D, I, L, V = C.POINTER, C.c_double, C.c_int, C.c_long, C.c_void_p
     H = V
@@ -143,6 +153,7 @@ def load():
         "mqs_graph_steps": ([H, P(C.c_long)], I),
         "mqs_batch_graph_steps": ([V, P(C.c_long)], I),
         "mqs_batch_tune_depth": ([V, I, P(I), I, P(I)], I),
+        "mqs_debug_check": ([H, P(DebugReport)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -249,6 +260,7 @@ class Solver:
         if rc != MQS_OK:
             raise MqsError(rc, "mqs_setup failed (see stderr)")
         self.h = h_
+        _live.add(self)
         info = LayoutInfo()
         self._check(self.lib.mqs_layout(self.h, C.byref(info)))
         self.n = info.n
@@ -470,6 +482,33 @@ class Solver:
         k = C.c_int()
         self._check(self.lib.pod_start(self.h, _dp(b), _dp(x0), C.byref(k)))
         return x0, k.value
+
+
+def debug_check(solvers=None):
+    """mqs_debug_check over the recorded index faults and the guard bytes of every
+    open solver's buffers (or of `solvers`).  Returns a dict: enabled (0 in the
+    release library), site and index of the first fault (site 0: none), faults,
+    canaries_bad and buffers summed over the solvers."""
+    lib = load()
+    rep = DebugReport()
+    rc = lib.mqs_debug_check(None, C.byref(rep))
+    if rc != MQS_OK:
+        raise MqsError(rc, "mqs_debug_check failed")
+    out = {"enabled": rep.enabled, "site": rep.site, "index": rep.index, "faults": rep.faults,
+           "canaries_bad": 0, "buffers": 0}
+    for sv in list(_live if solvers is None else solvers):
+        if not getattr(sv, "h", None):
+            continue
+        r = DebugReport()
+        rc = lib.mqs_debug_check(sv.h, C.byref(r))
+        if rc != MQS_OK:
+            raise MqsError(rc, "mqs_debug_check failed")
+        out["canaries_bad"] += r.canaries_bad
+        out["buffers"] += r.buffers
+        if r.faults and not out["faults"]:
+            out.update(site=r.site, index=r.index)
+        out["faults"] += r.faults
+    return out
 
 
 def pcg_solve_noalloc(n, h, nu0, cell_mask, b, x, tol=1e-10, maxit=100000, stream=0):

@@ -37,7 +37,7 @@ __device__ __forceinline__ long long box_cells(const CondGeom& cg) {
 // t_c S_{c,d} of cell (i, j, k), zero outside the box and in linear cells
 __device__ __forceinline__ double tsd(const CondGeom& cg, const double* tS, int d, int i, int j, int k) {
   const long long q = box_cell(cg, i, j, k);
-  return q < 0 ? 0.0 : tS[d * box_cells(cg) + q];
+  return q < 0 ? 0.0 : MQS_LDC(tS, d * box_cells(cg) + q, 3 * box_cells(cg), 501);
 }
 
 __device__ __forceinline__ double block_reduce(double v, double* sh) {
@@ -55,7 +55,7 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
 __global__ void adj_mu_kernel(CondGeom cg, const double* F, AdjBufs ab, double dt) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cg.n_c; q += gridDim.x * blockDim.x) {
     const double f = F[q], l = ab.lam[q], im = cg.inv_mc[q];
-    ab.mu_full[cg.c_idx[q]] = dt * im * fma(2.0, f, -l);
+    MQS_STC(ab.mu_full, cg.c_idx[q], 3 * cg.n3, 502, dt * im * fma(2.0, f, -l));
     ab.gmc[q] += dt * f * (l - f) * im * im;
   }
 }
@@ -154,10 +154,10 @@ __global__ void adj_coil_kernel(Geom g, CoilGeom coil, CoilDrive drv, const doub
   const int L1 = coil.i1 - coil.i0, L2 = coil.j1 - coil.j0, tot = 2 * L1 + 2 * L2;
   double s = 0.0;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    if (t < L1) s += x[pidx(n, coil.i0 + t, coil.j0, coil.k)];
-    else if (t < 2 * L1) s -= x[pidx(n, coil.i0 + t - L1, coil.j1, coil.k)];
-    else if (t < 2 * L1 + L2) s += x[n3 + pidx(n, coil.i1, coil.j0 + t - 2 * L1, coil.k)];
-    else s -= x[n3 + pidx(n, coil.i0, coil.j0 + t - 2 * L1 - L2, coil.k)];
+    if (t < L1) s += MQS_LDC(x, pidx(n, coil.i0 + t, coil.j0, coil.k), 3 * n3, 503);
+    else if (t < 2 * L1) s -= MQS_LDC(x, pidx(n, coil.i0 + t - L1, coil.j1, coil.k), 3 * n3, 504);
+    else if (t < 2 * L1 + L2) s += MQS_LDC(x, n3 + pidx(n, coil.i1, coil.j0 + t - 2 * L1, coil.k), 3 * n3, 505);
+    else s -= MQS_LDC(x, n3 + pidx(n, coil.i0, coil.j0 + t - 2 * L1 - L2, coil.k), 3 * n3, 506);
   }
   const double tot_s = block_reduce(s, sh);
   if (threadIdx.x == 0) {
@@ -197,7 +197,8 @@ __global__ void adj_qmap_kernel(Geom g, CondGeom cg, int* qmap) {
     const long long pos = e - c * g.n3;
     const int i = (int)(pos % g.n) - cg.clo[0], j = (int)((pos / g.n) % g.n) - cg.clo[1],
               k = (int)(pos / ((long long)g.n * g.n)) - cg.clo[2];
-    if (i >= 0 && j >= 0 && k >= 0 && i < ex && j < ey && k < ez) qmap[c * nn + i + (long long)ex * (j + (long long)ey * k)] = q;
+    if (i >= 0 && j >= 0 && k >= 0 && i < ex && j < ey && k < ez)
+      MQS_STC(qmap, c * nn + i + (long long)ex * (j + (long long)ey * k), 3 * nn, 507, q);
   }
 }
 
@@ -206,7 +207,9 @@ __global__ void adj_sigma_kernel(CondGeom cg, const uint8_t* cond, AdjBufs ab, d
   const long long nb = box_cells(cg);
   const int ex = wx + 1, ey = wy + 1, ez = cg.chi[2] - cg.clo[2] + 1;
   const long long nn = (long long)ex * ey * ez;
-  auto qm = [&](int c, int i, int j, int k) { return ab.qmap[c * nn + i + (long long)ex * (j + (long long)ey * k)]; };
+  auto qm = [&](int c, int i, int j, int k) {
+    return MQS_LDC(ab.qmap, c * nn + i + (long long)ex * (j + (long long)ey * k), 3 * nn, 508);
+  };
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nb; q += (long long)gridDim.x * blockDim.x) {
     if (!cond[q]) { out[q] = 0.0; continue; }
     const int i = (int)(q % wx), j = (int)((q / wx) % wy), k = (int)(q / ((long long)wx * wy));   // box-relative
@@ -214,9 +217,9 @@ __global__ void adj_sigma_kernel(CondGeom cg, const uint8_t* cond, AdjBufs ab, d
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b) {
         const int qx = qm(0, i, j + a, k + b), qy = qm(1, i + a, j, k + b), qz = qm(2, i + a, j + b, k);
-        if (qx >= 0) s += ab.gmc[qx];
-        if (qy >= 0) s += ab.gmc[qy];
-        if (qz >= 0) s += ab.gmc[qz];
+        if (qx >= 0) s += MQS_LDC(ab.gmc, qx, cg.n_c, 509);
+        if (qy >= 0) s += MQS_LDC(ab.gmc, qy, cg.n_c, 510);
+        if (qz >= 0) s += MQS_LDC(ab.gmc, qz, cg.n_c, 511);
       }
     out[q] = 0.25 * cg.h * s;          // M_kappa = h * mean sigma of the four cells of an edge
   }
@@ -274,5 +277,7 @@ int launch_adj_sigma(const DevGeom& dg, const CondGeom& cg, const uint8_t* cond,
   adj_sigma_kernel<<<blocks_for(cell_count(cg)), 256, 0, st>>>(cg, cond, ab, out);
   return ok();
 }
+
+MQS_DEBUG_TAKE(adjoint)
 
 }  // namespace mqs

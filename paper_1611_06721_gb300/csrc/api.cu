@@ -9,10 +9,22 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #include "mqs_kernels.h"
 #include "mrhs.h"
 
 using namespace mqs;
+
+namespace {
+// NVTX range over the host's issue of one phase (a profiler shows the kernels each
+// range launched); free when no tool is attached
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 namespace {
 // what a captured step depends on besides its own launches: a replay is valid only
@@ -48,6 +60,7 @@ struct mqs_handle {
   int nblk = 0;
   std::string err;
   std::vector<void*> allocs;
+  std::vector<size_t> guard_at;   // debug builds: offset of each buffer's guard bytes
   // device buffers
   uint8_t* cflags = nullptr;
   int* cidx = nullptr;
@@ -168,15 +181,33 @@ int fail(mqs_handle* H, int code, const char* msg) {
     }                                                                              \
   } while (0)
 
+// Debug builds follow every device buffer with kGuardBytes of kGuardByte (after the
+// buffer's 64 bytes of slack, rounded up to kGuardBytes); mqs_debug_check compares them.
+#ifdef MQS_DEBUG_CHECKS
+constexpr bool kDebugBuild = true;
+#else
+constexpr bool kDebugBuild = false;
+#endif
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 template <class T>
 int dalloc(mqs_handle* H, T** ptr, size_t count) {
   void* v = nullptr;
-  if (cudaMalloc(&v, count * sizeof(T) + 64) != cudaSuccess) {
+  const size_t body = count * sizeof(T) + 64;
+  const size_t guard = (body + kGuardBytes - 1) / kGuardBytes * kGuardBytes;
+  if (cudaMalloc(&v, kDebugBuild ? guard + kGuardBytes : body) != cudaSuccess) {
     cudaGetLastError();
     H->err = "device allocation failed";
     return MQS_ERR_OOM;
   }
+  if (kDebugBuild && cudaMemset(static_cast<char*>(v) + guard, kGuardByte, kGuardBytes) != cudaSuccess) {
+    cudaFree(v);
+    H->err = "guard bytes not written";
+    return MQS_ERR_CUDA;
+  }
   H->allocs.push_back(v);
+  H->guard_at.push_back(kDebugBuild ? guard : 0);
   *ptr = static_cast<T*>(v);
   return MQS_OK;
 }
@@ -229,8 +260,9 @@ __global__ void power_update_kernel(int n_c, const double* F, const double* isq,
 // step whose solve succeeded takes the instability monitor's verdict; a failing step
 // halts the call.
 __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                              const int* derr, mqs_step_stats* dst, long long* ctr, StepGuard* gd) {
+                              const int* derr, mqs_step_stats* dst, long long* ctr, StepGuard* gd, int cap) {
   if (ctr) {
+    if (!MQS_IDX_OK(ctr[1], cap, 701)) return;
     dst += ctr[1];
     ctr[0] += 1;
     ctr[1] += 1;
@@ -257,7 +289,8 @@ __global__ void record_kernel(const PcgResult* pr, const SmallOut* so, int use_s
 // Adds a second solve of the same step (separate right-hand sides) to its record
 // (the one record_kernel wrote last: dst[ctr[1] - 1]).
 __global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int use_small, const int* refin,
-                                  const int* derr, mqs_step_stats* dst, const long long* ctr, StepGuard* gd) {
+                                  const int* derr, mqs_step_stats* dst, const long long* ctr, StepGuard* gd, int cap) {
+  if (!MQS_IDX_OK(ctr[1] - 1, cap, 702)) return;
   dst += ctr[1] - 1;
   mqs_step_stats s = *dst;
   if (s.status == MQS_ERR_HALTED) return;
@@ -273,7 +306,8 @@ __global__ void record_add_kernel(const PcgResult* pr, const SmallOut* so, int u
 
 // Separate right-hand sides record their solves before the conductor update: its
 // monitor verdict joins the step's record afterwards.
-__global__ void record_mon_kernel(StepGuard* gd, mqs_step_stats* dst, const long long* ctr) {
+__global__ void record_mon_kernel(StepGuard* gd, mqs_step_stats* dst, const long long* ctr, int cap) {
+  if (!MQS_IDX_OK(ctr[1] - 1, cap, 703)) return;
   dst += ctr[1] - 1;
   if (dst->status == MQS_OK && gd->status != MQS_OK) {
     dst->status = gd->status;
@@ -308,6 +342,7 @@ int ensure_mixed(mqs_handle* H) {
 // the PCG kernel selected by opt.precision and opt.pcg_variant
 int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit, cudaStream_t st, int init,
                const int* halt = nullptr) {
+  const Range range_("mqs pcg");
   if (H->opt.precision == 2) {
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
@@ -383,6 +418,7 @@ int refactor_spe(mqs_handle* H, cudaStream_t st) {
 }
 
 int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t st) {
+  const Range range_("mqs history push");
   const int mode = H->opt.start_mode;
   if (mode == MQS_START_SPE) {
     const int d = H->opt.spe_depth;
@@ -442,6 +478,7 @@ __global__ void sub_kernel(const double* b, const double* lx, double* r, long lo
 }
 
 int start_vector(mqs_handle* H, const double* b, double* x, cudaStream_t st, int* used_small, int* init) {
+  const Range range_("mqs start vector");
   *used_small = 0;
   *init = 0;
   RK(join_side(H));
@@ -761,6 +798,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   H->cg.brauer = H->brauer;
   H->cg.nu = H->nu;
   H->cg.nu0 = H->nu0; H->cg.k1 = H->k1; H->cg.k2 = H->k2; H->cg.k3 = H->k3; H->cg.h = H->h;
+  H->cg.n3 = n3;
   CK(cudaDeviceSynchronize());
   return MQS_OK;
 }
@@ -835,6 +873,7 @@ int state_changed(mqs_handle* H) {
 }
 
 int conductor_step(mqs_handle* H, const double* w, double dt, cudaStream_t st) {
+  const Range range_("mqs conductor update");
   const int window = H->opt.monitor_steps == 0 ? 8 : H->opt.monitor_steps;
   const GuardView gv{H->guard, H->mon_part, H->pres, H->derr, window};
   if (H->any_brauer) RK(launch_cell_nu(H->dg, H->cg, H->ac_full, w, false, st, halt_flag(H)));
@@ -905,6 +944,7 @@ uint64_t splitmix64(uint64_t& state) {
 // dt = cfl_factor * 2 / lambda_max (eq. (CFL)) by the power method from the library's
 // own start vector, at the settings of the oracle's power method
 int setup_dt(mqs_handle* H, double cfl) {
+  const Range range_("mqs setup dt");
   std::vector<double> v0(H->n_c);
   uint64_t state = 1611;
   for (double& v : v0) v = 2.0 * ((double)(splitmix64(state) >> 11) * 0x1.0p-53) - 1.0;
@@ -924,6 +964,7 @@ extern "C" {
 
 int mqs_setup(const mqs_grid* grid, const mqs_materials* mat, const uint8_t* conductor_mask, const mqs_coil* coil,
               const mqs_options* opts, mqs_handle** out) {
+  const Range range_("mqs_setup");
   if (!out) return MQS_ERR_ARG;
   *out = nullptr;
   if (!grid || !mat || !coil || !opts) return MQS_ERR_ARG;
@@ -1071,6 +1112,7 @@ int form_rhs(mqs_handle* H, long m, cudaStream_t st) {
 // update.  Phase marks: rhs (both), start (conductor type), PCG (conductor type, then
 // the coil type's start vector and solve), history, conductor.
 int enqueue_split_step(mqs_handle* H) {
+  const Range range_("mqs step");
   cudaStream_t st = H->st;
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   const long m = H->m + 1;
@@ -1088,7 +1130,7 @@ int enqueue_split_step(mqs_handle* H) {
   mark(H);
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init_c, halt_flag(H)));
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_c, refin ? H->refin : nullptr, H->derr, H->dstats,
-                                 H->dctr, H->guard);
+                                 H->dctr, H->guard, H->dstats_cap);
   advance_ctr(H);
   RK(history_push(H, H->x, H->lx, st));
   CK(cudaMemcpyAsync(H->xc, H->x, sizeof(double) * H->len, cudaMemcpyDeviceToDevice, st));
@@ -1097,7 +1139,7 @@ int enqueue_split_step(mqs_handle* H) {
   RK(start_vector(H, H->bs, H->x, st, &used_s, &init_s));
   RK(pcg_launch(H, H->bs, H->x, H->opt.tol, H->opt.maxit, st, init_s, halt_flag(H)));
   record_add_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_s, refin ? H->refin : nullptr, H->derr,
-                                     H->dstats, H->dctr, H->guard);
+                                     H->dstats, H->dctr, H->guard, H->dstats_cap);
   mark(H);
   RK(history_push(H, H->x, H->lx, st));
   const long nl_hist = 2 * history_launches(H);
@@ -1106,7 +1148,7 @@ int enqueue_split_step(mqs_handle* H) {
   H->lx_valid = false;                                // lx holds L w_s only
   mark(H);
   RK(conductor_step(H, H->x, H->dt, st));
-  record_mon_kernel<<<1, 1, 0, st>>>(H->guard, H->dstats, H->dctr);
+  record_mon_kernel<<<1, 1, 0, st>>>(H->guard, H->dstats, H->dctr, H->dstats_cap);
   mark(H);
   if (H->timing) {
     H->launches += 2 + nl_start + nl_start_s + 2 + 2 + nl_hist + 1 + (H->any_brauer ? 2 : 1) + 1;
@@ -1121,6 +1163,7 @@ int enqueue_split_step(mqs_handle* H) {
 // Issues the launches of one explicit-Euler step of H on H->st (no host wait); the
 // step's statistics go to the slot the device step counter names.
 int enqueue_step(mqs_handle* H) {
+  const Range range_("mqs step");
   if (H->opt.rhs_split) return enqueue_split_step(H);
   cudaStream_t st = H->st;
   const long m = H->m + 1;
@@ -1152,7 +1195,7 @@ int enqueue_step(mqs_handle* H) {
   RK(conductor_step(H, H->x, H->dt, st));
   nl += H->any_brauer ? 2 : 1;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats, H->dctr, H->guard);
+                                 H->derr, H->dstats, H->dctr, H->guard, H->dstats_cap);
   advance_ctr(H);
   nl += 1;
   // the next step's right-hand side from the new state, beside the side stream's push
@@ -1273,6 +1316,7 @@ bool capture(cudaStream_t origin, F issue, cudaGraphExec_t* exec) {
 // side stream joined at the end) and launched.  *done is false when the step is to be
 // issued without a graph (not eligible, or the capture failed: graphs then stay off).
 int graph_step(mqs_handle* H, bool* done) {
+  const Range range_("mqs step graph");
   *done = false;
   if (!graph_eligible(H)) return MQS_OK;
   RK(join_side(H));
@@ -1317,6 +1361,7 @@ void dfree(mqs_handle* H, void* p) {
     if (H->allocs[i] == p) {
       cudaFree(p);
       H->allocs.erase(H->allocs.begin() + (long)i);
+      H->guard_at.erase(H->guard_at.begin() + (long)i);
       return;
     }
 }
@@ -1451,6 +1496,7 @@ int check_stats(mqs_handle* H, int nsteps, const mqs_step_stats* hs, int derr) {
 }  // namespace
 
 int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
+  const Range range_("mqs_step");
   if (!H || nsteps < 0) return MQS_ERR_ARG;
   if (H->enqueued) return fail(H, MQS_ERR_ARG, "steps are enqueued: call mqs_step_finish first");
   if (nsteps == 0) return (H->dt > 0.0) ? MQS_OK : fail(H, MQS_ERR_ARG, "dt is not set");
@@ -1459,6 +1505,7 @@ int mqs_step(mqs_handle* H, int nsteps, mqs_step_stats* per_step) {
 }
 
 int mqs_step_enqueue(mqs_handle* H, int nsteps) {
+  const Range range_("mqs_step_enqueue");
   if (!H || nsteps < 1) return MQS_ERR_ARG;
   if (!(H->dt > 0.0)) return fail(H, MQS_ERR_ARG, "dt is not set");
   if (nsteps > (1 << 30) - H->enqueued) return fail(H, MQS_ERR_ARG, "too many steps enqueued");
@@ -1552,7 +1599,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
   RK(pcg_launch(H, H->b, H->x, H->opt.tol, H->opt.maxit, st, init));
   H->lx_valid = true;
   record_kernel<<<1, 1, 0, st>>>(H->pres, H->small, used_small, H->opt.precision != 0 ? H->refin : nullptr,
-                                 H->derr, H->dstats + slot, nullptr, nullptr);
+                                 H->derr, H->dstats + slot, nullptr, nullptr, 1);
   RK(history_push(H, H->x, H->lx, st));
   RK(launch_adj_cell(H->dg, H->cg, H->x, H->adj, st));
   RK(launch_adj_lambda(H->dg, H->cg, H->x, H->adj, st));
@@ -1567,6 +1614,7 @@ int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double
 // its checkpoint (on a start-vector history of their own, cold at each segment) before
 // its adjoint steps (whose history runs on across segments).
 int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_adjoint_info* info) {
+  const Range range_("mqs_adjoint");
   if (!H || nsteps < 1) return MQS_ERR_ARG;
   if (H->opt.rhs_split) return fail(H, MQS_ERR_ARG, "the adjoint runs the fused solve (rhs_split = 0)");
   if (H->n_c < 1) return fail(H, MQS_ERR_ARG, "no conducting edges");
@@ -1952,7 +2000,45 @@ int pod_start(mqs_handle* H, const double* b, double* x0, int* k) {
   return MQS_OK;
 }
 
+int mqs_debug_check(mqs_handle* H, mqs_debug_report* rep) {
+  if (!rep) return MQS_ERR_ARG;
+  *rep = mqs_debug_report{};
+  if (!kDebugBuild) return MQS_OK;
+  rep->enabled = 1;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    if (H) H->err = "mqs_debug_check: device synchronization failed";
+    return MQS_ERR_CUDA;
+  }
+  int (*const take[])(unsigned long long*) = {dbg_take_pcg,  dbg_take_mixed, dbg_take_conductor, dbg_take_mrhs,
+                                              dbg_take_adjoint, dbg_take_api, dbg_take_noalloc};
+  for (auto f : take) {
+    unsigned long long w = 0;
+    if (f(&w) != 0) return MQS_ERR_CUDA;
+    if (!(w >> 63)) continue;
+    if (rep->faults++ == 0) {
+      rep->site = (int)((w >> 48) & 0x7FFF);
+      rep->index = (long long)((w & 0xFFFFFFFFFFFFull) << 16) >> 16;   // 48-bit two's complement
+    }
+  }
+  if (H) {
+    unsigned char buf[kGuardBytes];
+    for (size_t i = 0; i < H->allocs.size(); ++i) {
+      if (cudaMemcpy(buf, static_cast<char*>(H->allocs[i]) + H->guard_at[i], kGuardBytes, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        return MQS_ERR_CUDA;
+      ++rep->buffers;
+      for (size_t q = 0; q < kGuardBytes; ++q)
+        if (buf[q] != kGuardByte) { ++rep->canaries_bad; break; }
+    }
+  }
+  return MQS_OK;
+}
+
 }  // extern "C"
+
+namespace mqs {
+MQS_DEBUG_TAKE(api)
+}  // namespace mqs
 
 // ---- batched multi-query ---------------------------------------------------------------
 
@@ -2169,6 +2255,7 @@ int mqs_batch_set_scale(mqs_batch* B, double blocks_scale) {
 }
 
 int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
+  const Range range_("mqs_batch_step");
   if (!B || nsteps < 0) return MQS_ERR_ARG;
   const int cnt = (int)B->hs.size();
   for (mqs_handle* H : B->hs)

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac,
   const long long n3 = g.n3;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsup; q += gridDim.x * blockDim.x) {
     const int e = sup[q];
-    const int c = (int)(e / n3);
+    const int c = (int)(e / n3);   // e < 3 n^3: checked at the store
     const int pos = (int)(e - c * n3);
     const int i = pos % n, j = (pos / n) % n, k = pos / (n * n);
     double t;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac,
                          (flux_x(ac, n, n3, i, j, k) - flux_x(ac, n, n3, i, j, k - 1));
     else t = (flux_x(ac, n, n3, i, j - 1, k) - flux_x(ac, n, n3, i, j, k)) +
              (flux_y(ac, n, n3, i, j, k) - flux_y(ac, n, n3, i - 1, j, k));
-    b[e] = fma(cs, coil_xs(coil, c, i, j, k), -t);
+    MQS_STC(b, e, 3 * n3, 402, fma(cs, coil_xs(coil, c, i, j, k), -t));
   }
 }
 
@@ -216,14 +216,15 @@ __global__ void cond_update_kernel(Geom g, CondGeom cg, const double* ac, const 
     if (F_out) F_out[q] = F;            // recorded trajectory (adjoint)
     if (a_prev_out) a_prev_out[q] = a0;
     a_out[q] = v;
-    if (ac_out) ac_out[e] = v;      // the other layout buffer (read and written buffers differ)
+    if (ac_out) MQS_STC(ac_out, e, 3 * n3, 403, v);   // the other layout buffer (read and written buffers differ)
   }
   if (mon) monitor_finish(gv, en, sx);
 }
 
-__global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, double* ac_full, double scale) {
+__global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, double* ac_full, double scale,
+                                 long long n3) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_c; q += gridDim.x * blockDim.x)
-    ac_full[c_idx[q]] = scale * a_c[q];
+    MQS_STC(ac_full, c_idx[q], 3 * n3, 404, scale * a_c[q]);
 }
 
 int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
@@ -252,8 +253,10 @@ int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, dou
   int blocks = (cg.n_c + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  scatter_c_kernel<<<blocks, 256, 0, st>>>(cg.n_c, cg.c_idx, a_c, ac_full, scale);
+  scatter_c_kernel<<<blocks, 256, 0, st>>>(cg.n_c, cg.c_idx, a_c, ac_full, scale, cg.n3);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
+
+MQS_DEBUG_TAKE(conductor)
 
 }  // namespace mqs

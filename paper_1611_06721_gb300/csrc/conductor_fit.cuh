@@ -32,7 +32,8 @@ __device__ __forceinline__ double cell_nu(const CondGeom& cg, int i, int j, int 
   if (i < cg.clo[0] || j < cg.clo[1] || k < cg.clo[2] || i >= cg.chi[0] || j >= cg.chi[1] || k >= cg.chi[2])
     return cg.nu0;
   const int wx = cg.chi[0] - cg.clo[0], wy = cg.chi[1] - cg.clo[1];
-  return cg.nu[(i - cg.clo[0]) + wx * ((j - cg.clo[1]) + (long long)wy * (k - cg.clo[2]))];
+  return MQS_LDC(cg.nu, (i - cg.clo[0]) + wx * ((j - cg.clo[1]) + (long long)wy * (k - cg.clo[2])),
+                 (long long)wx * wy * (cg.chi[2] - cg.clo[2]), 401);
 }
 
 }  // namespace mqs

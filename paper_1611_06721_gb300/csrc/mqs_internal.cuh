@@ -18,11 +18,55 @@
 // i.e. 6 FP64 additions per edge when every face flux is formed once.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include "../../include/mqs.h"
 #include "ff.cuh"
 
 namespace mqs {
+
+// ---- debug build: checked global accesses ------------------------------------------
+// The library's debug variant (compiled with -DMQS_DEBUG_CHECKS) tests every index that a
+// hot kernel computes (stencil sweeps, fused passes, conductor, right-hand side and
+// support-list kernels) against the length of the array it addresses.  An index outside
+// records its site and value in the translation unit's debug word (the first one wins)
+// and the access is skipped (a load gives 0): nothing traps.  mqs_debug_check reads the
+// words.  Release builds compile the checks out.  Loops whose index is the loop bound
+// itself (grid-stride element loops) need no check.
+#ifdef MQS_DEBUG_CHECKS
+static __device__ unsigned long long g_dbg_word;   // per translation unit
+__device__ __forceinline__ bool dbg_ok(long long idx, long long len, int site) {
+  if (idx >= 0 && idx < len) return true;
+  atomicCAS(&g_dbg_word, 0ull,
+            (1ull << 63) | ((unsigned long long)(site & 0x7FFF) << 48) | ((unsigned long long)idx & 0xFFFFFFFFFFFFull));
+  return false;
+}
+#define MQS_LDC(arr, idx, len, site)                                          \
+  (::mqs::dbg_ok((long long)(idx), (long long)(len), (site))                  \
+       ? (arr)[(idx)]                                                         \
+       : std::remove_cv_t<std::remove_reference_t<decltype((arr)[0])>>{})
+#define MQS_STC(arr, idx, len, site, val)                                             \
+  do {                                                                                \
+    if (::mqs::dbg_ok((long long)(idx), (long long)(len), (site))) (arr)[(idx)] = (val); \
+  } while (0)
+// host: the word of this translation unit, cleared after reading
+#define MQS_IDX_OK(idx, len, site) (::mqs::dbg_ok((long long)(idx), (long long)(len), (site)))
+#define MQS_DEBUG_TAKE(name)                                                          \
+  int dbg_take_##name(unsigned long long* out) {                                      \
+    const unsigned long long zero = 0;                                                \
+    if (cudaMemcpyFromSymbol(out, g_dbg_word, sizeof zero) != cudaSuccess) return -2; \
+    return cudaMemcpyToSymbol(g_dbg_word, &zero, sizeof zero) == cudaSuccess ? 0 : -2; \
+  }
+#else
+#define MQS_LDC(arr, idx, len, site) ((arr)[(idx)])
+#define MQS_STC(arr, idx, len, site, val) ((arr)[(idx)] = (val))
+#define MQS_IDX_OK(idx, len, site) true
+#define MQS_DEBUG_TAKE(name)                       \
+  int dbg_take_##name(unsigned long long* out) { \
+    *out = 0;                                    \
+    return 0;                                    \
+  }
+#endif
 
 constexpr int kTY = 4;                  // row warps per stencil group (tile 32 x kTY)
 constexpr int kGroupWarps = kTY + 1;    // + one warp for the j0-1 halo row
@@ -57,7 +101,8 @@ __device__ __forceinline__ unsigned nmask(const Geom& g, int i, int j, int k) {
   if (i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1] &&
       k >= g.cb_lo[2] && k < g.cb_hi[2]) {
     int w0 = g.cb_hi[0] - g.cb_lo[0], w1 = g.cb_hi[1] - g.cb_lo[1];
-    unsigned cf = g.cflags[(i - g.cb_lo[0]) + w0 * ((j - g.cb_lo[1]) + w1 * (k - g.cb_lo[2]))];
+    unsigned cf = MQS_LDC(g.cflags, (i - g.cb_lo[0]) + w0 * ((j - g.cb_lo[1]) + w1 * (k - g.cb_lo[2])),
+                          w0 * w1 * (g.cb_hi[2] - g.cb_lo[2]), 151);
     m &= ~cf;
   }
   return m;
@@ -67,7 +112,7 @@ __device__ __forceinline__ unsigned nmask(const Geom& g, int i, int j, int k) {
 __device__ __forceinline__ double ld(const double* __restrict__ v, int n, long long n3, int c,
                                      int i, int j, int k) {
   if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) return 0.0;
-  return v[c * n3 + pidx(n, i, j, k)];
+  return MQS_LDC(v, c * n3 + pidx(n, i, j, k), 3 * n3, 152);
 }
 
 // identity load conversion of sweep_L
@@ -233,15 +278,15 @@ __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, 
       // plane ks (own, x+1 and y+1 neighbours) and own values of plane ks + 1
       const bool wu = (ks >= 1) && col;
       const int om = o - n2;
-      const T xm = wu ? cv(sx_[om]) : T(0), ym = wu ? cv(sy_[om]) : T(0), zm = wu ? cv(sz_[om]) : T(0);
-      const T zim = (wu && vi1) ? cv(sz_[om + 1]) : T(0), zjm = (wu && vj1) ? cv(sz_[om + n]) : T(0);
+      const T xm = wu ? cv(MQS_LDC(sx_, om, n3, 101)) : T(0), ym = wu ? cv(MQS_LDC(sy_, om, n3, 102)) : T(0), zm = wu ? cv(MQS_LDC(sz_, om, n3, 103)) : T(0);
+      const T zim = (wu && vi1) ? cv(MQS_LDC(sz_, om + 1, n3, 104)) : T(0), zjm = (wu && vj1) ? cv(MQS_LDC(sz_, om + n, n3, 105)) : T(0);
       T x0 = 0, y0 = 0, z0 = 0;
       T yi = 0, zi = 0, xj = 0, zj = 0, xk = 0, yk = 0, zk = 0;
       if (col) {
-        x0 = cv(sx_[o]); y0 = cv(sy_[o]); z0 = cv(sz_[o]);
-        if (vi1) { yi = cv(sy_[o + 1]); zi = cv(sz_[o + 1]); }
-        if (vj1) { xj = cv(sx_[o + n]); zj = cv(sz_[o + n]); }
-        if (ks + 1 < n) { xk = cv(sx_[o + n2]); yk = cv(sy_[o + n2]); zk = cv(sz_[o + n2]); }
+        x0 = cv(MQS_LDC(sx_, o, n3, 106)); y0 = cv(MQS_LDC(sy_, o, n3, 107)); z0 = cv(MQS_LDC(sz_, o, n3, 108));
+        if (vi1) { yi = cv(MQS_LDC(sy_, o + 1, n3, 109)); zi = cv(MQS_LDC(sz_, o + 1, n3, 110)); }
+        if (vj1) { xj = cv(MQS_LDC(sx_, o + n, n3, 111)); zj = cv(MQS_LDC(sz_, o + n, n3, 112)); }
+        if (ks + 1 < n) { xk = cv(MQS_LDC(sx_, o + n2, n3, 113)); yk = cv(MQS_LDC(sy_, o + n2, n3, 114)); zk = cv(MQS_LDC(sz_, o + n2, n3, 115)); }
       }
       if (act) epi.prefetch(o);
       // warm-up fluxes bx, by at plane ks - 1 (zero when ks = 0: unused there)
@@ -257,9 +302,9 @@ __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, 
         M nyi = M(0), nzi = M(0), nxj = M(0), nzj = M(0), nxk = M(0), nyk = M(0), nzk = M(0);
         const int o1 = o + n2;
         if (col && k + 1 < ke) {
-          if (vi1) { nyi = sy_[o1 + 1]; nzi = sz_[o1 + 1]; }
-          if (vj1) { nxj = sx_[o1 + n]; nzj = sz_[o1 + n]; }
-          if (k + 2 < n) { nxk = sx_[o1 + n2]; nyk = sy_[o1 + n2]; nzk = sz_[o1 + n2]; }
+          if (vi1) { nyi = MQS_LDC(sy_, o1 + 1, n3, 116); nzi = MQS_LDC(sz_, o1 + 1, n3, 117); }
+          if (vj1) { nxj = MQS_LDC(sx_, o1 + n, n3, 118); nzj = MQS_LDC(sz_, o1 + n, n3, 119); }
+          if (k + 2 < n) { nxk = MQS_LDC(sx_, o1 + n2, n3, 120); nyk = MQS_LDC(sy_, o1 + n2, n3, 121); nzk = MQS_LDC(sz_, o1 + n2, n3, 122); }
         }
         T bx = 0, by = 0, bz = 0;
         if (col) {
@@ -278,7 +323,7 @@ __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, 
           const T ty = (bzi - bz) + (bx - bxm);
           const T tz = (bxj - bx) + (by - byi);
           unsigned m = mcol & (k > 0 ? 7u : 4u);
-          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
+          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)MQS_LDC(g.cflags, cfc + cw01 * (k - g.cb_lo[2]), cw01 * (g.cb_hi[2] - g.cb_lo[2]), 150);
           epi(o, m, tx, ty, tz, x0, y0, z0);
           if (k + 1 < ke) epi.prefetch(o1);
         }
@@ -304,17 +349,17 @@ __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, 
       T a[7], c[8];
       // raw loads (converted when used, as in the row warps)
       auto load_row = [&](int k, int o, M* v) {
-        v[0] = sx_[o]; v[1] = sy_[o]; v[2] = sz_[o];
-        v[3] = hi1 ? sy_[o + 1] : M(0);
-        v[4] = sx_[o + n]; v[5] = sz_[o + n];
-        v[6] = (k + 1 < n) ? sy_[o + n2] : M(0);
+        v[0] = MQS_LDC(sx_, o, n3, 123); v[1] = MQS_LDC(sy_, o, n3, 124); v[2] = MQS_LDC(sz_, o, n3, 125);
+        v[3] = hi1 ? MQS_LDC(sy_, o + 1, n3, 126) : M(0);
+        v[4] = MQS_LDC(sx_, o + n, n3, 127); v[5] = MQS_LDC(sz_, o + n, n3, 128);
+        v[6] = (k + 1 < n) ? MQS_LDC(sy_, o + n2, n3, 129) : M(0);
       };
       auto load_col = [&](int k, int o, M* v) {
-        v[0] = sx_[o]; v[1] = sy_[o + 1];
-        v[2] = hj1 ? sx_[o + n] : M(0);
-        v[3] = sy_[o]; v[4] = sz_[o];
-        v[5] = (k + 1 < n) ? sx_[o + n2] : M(0);
-        v[6] = sz_[o + 1];
+        v[0] = MQS_LDC(sx_, o, n3, 130); v[1] = MQS_LDC(sy_, o + 1, n3, 131);
+        v[2] = hj1 ? MQS_LDC(sx_, o + n, n3, 132) : M(0);
+        v[3] = MQS_LDC(sy_, o, n3, 133); v[4] = MQS_LDC(sz_, o, n3, 134);
+        v[5] = (k + 1 < n) ? MQS_LDC(sx_, o + n2, n3, 135) : M(0);
+        v[6] = MQS_LDC(sz_, o + 1, n3, 136);
         v[7] = M(0);
       };
       {

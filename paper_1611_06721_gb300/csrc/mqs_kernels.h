@@ -104,6 +104,7 @@ struct CondGeom {
   const uint8_t* brauer;  // flags over the cell box (1 = Brauer)
   double* nu;             // reluctivity over the cell box
   double nu0, k1, k2, k3, h;
+  long long n3;           // n^3 of the grid (layout vectors hold 3 n^3 values)
 };
 // nu per cell of the cell box from a = ac_full + w (nonlinear cells); if
 // `at_zero` the Brauer law is evaluated at B = 0.  halt (nullable): nothing is done
@@ -157,5 +158,16 @@ int launch_adj_qmap(const DevGeom& dg, const CondGeom& cg, const AdjBufs& ab, cu
 // cond[cell] != 0, else 0
 int launch_adj_sigma(const DevGeom& dg, const CondGeom& cg, const uint8_t* cond, const AdjBufs& ab, double* out,
                      cudaStream_t st);
+
+// debug builds (MQS_DEBUG_CHECKS): the first out-of-range index a translation unit's
+// kernels met, as (1 << 63) | site << 48 | index (0: none), cleared by the read.
+// Release builds report 0.  Returns 0 or -2 (CUDA error).
+int dbg_take_pcg(unsigned long long* out);
+int dbg_take_mixed(unsigned long long* out);
+int dbg_take_conductor(unsigned long long* out);
+int dbg_take_mrhs(unsigned long long* out);
+int dbg_take_adjoint(unsigned long long* out);
+int dbg_take_api(unsigned long long* out);
+int dbg_take_noalloc(unsigned long long* out);
 
 }  // namespace mqs

@@ -855,12 +855,12 @@ __global__ void __launch_bounds__(kTS) spe_g_kernel(VecSet D, const double* __re
       const int i = box.lo[0] + r % bx, j = box.lo[1] + (r / bx) % by, k = box.lo[2] + r / (bx * by);
       e = c * n3 + i + (long long)n * (j + (long long)n * k);
     }
-    const double be = b[e];
+    const double be = MQS_LDC(b, e, 3 * n3, 601);
     if (be != 0.0) {
       const float2 bf = ff_split(be);
 #pragma unroll
       for (int q = 0; q < MAXM; ++q)
-        if (q < m) ff_mac(reinterpret_cast<const float2*>(D.v[q])[e], bf, S[q], E[q]);
+        if (q < m) ff_mac(MQS_LDC(reinterpret_cast<const float2*>(D.v[q]), e, 3 * n3, 602), bf, S[q], E[q]);
     }
   }
   __shared__ float2 red[kTS / 32][16];
@@ -1178,5 +1178,7 @@ int cspe_freeze(const CspeBufs& cb, int k, long long len, cudaStream_t st) {
   cspe_freeze_kernel<<<ts_blocks(len) * 2, kTS, 0, st>>>(z, lz, cb.Q[k], cb.P[k], len, cb.scal);
   return chk();
 }
+
+MQS_DEBUG_TAKE(mrhs)
 
 }  // namespace mqs

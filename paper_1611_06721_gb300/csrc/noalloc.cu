@@ -55,7 +55,7 @@ __global__ void cell_flags_kernel(int n, const uint8_t* cell, uint8_t* flags) {
     const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((long long)n * n));
     auto c = [&](int a, int b, int d) -> unsigned {
       if (a < 0 || b < 0 || d < 0 || a >= n || b >= n || d >= n) return 0u;
-      return cell[a + (long long)n * (b + (long long)n * d)] ? 1u : 0u;
+      return MQS_LDC(cell, a + (long long)n * (b + (long long)n * d), n3, 901) ? 1u : 0u;
     };
     unsigned f = 0u;
     if (c(i, j - 1, k - 1) | c(i, j, k - 1) | c(i, j - 1, k) | c(i, j, k)) f |= 1u;
@@ -185,3 +185,7 @@ extern "C" int mqs_pcg_solve_noalloc(int n, double h, double nu0, const uint8_t*
   if (derr != 0) return derr;
   return pr.status;
 }
+
+namespace mqs {
+MQS_DEBUG_TAKE(noalloc)
+}  // namespace mqs

@@ -55,7 +55,7 @@ struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
   double bp[3];
   __device__ void prefetch(long long e) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) bp[c] = b[e + c * n3];
+    for (int c = 0; c < 3; ++c) bp[c] = MQS_LDC(b, e + c * n3, 3 * n3, 201);
   }
   __device__ void operator()(long long e, unsigned m, double tx, double ty, double tz, double, double, double) {
     const double t[3] = {tx, ty, tz};
@@ -65,10 +65,10 @@ struct EpiResidual {  // r = b - t, lx = t on n-edges; sums r.r and b.b
       if (m >> c & 1u) {
         const double bv = bp[c];
         const double rv = bv - t[c];
-        r[idx] = rv; lx[idx] = t[c];
+        MQS_STC(r, idx, 3 * n3, 202, rv); MQS_STC(lx, idx, 3 * n3, 203, t[c]);
         rr = fma(rv, rv, rr); bb = fma(bv, bv, bb);
       } else {
-        r[idx] = 0.0; lx[idx] = 0.0;
+        MQS_STC(r, idx, 3 * n3, 204, 0.0); MQS_STC(lx, idx, 3 * n3, 205, 0.0);
       }
     }
   }
@@ -85,10 +85,13 @@ struct EpiDirectionFx {
   double pp[3], qp[3], rp[3];
   __device__ void prefetch(long long e) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rp[c] = r[e + c * n3];
+    for (int c = 0; c < 3; ++c) rp[c] = MQS_LDC(r, e + c * n3, 3 * n3, 206);
     if (first) return;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { pp[c] = p[e + c * n3]; qp[c] = q[e + c * n3]; }
+    for (int c = 0; c < 3; ++c) {
+      pp[c] = MQS_LDC(p, e + c * n3, 3 * n3, 207);
+      qp[c] = MQS_LDC(q, e + c * n3, 3 * n3, 208);
+    }
   }
   __device__ void operator()(long long e, unsigned m, long long tx, long long ty, long long tz, long long,
                              long long, long long) {
@@ -103,7 +106,7 @@ struct EpiDirectionFx {
         pn = first ? rp[c] : fma(beta, pp[c], rp[c]);
         pq = fma(pn, qn, pq);
       }
-      q[idx] = qn; p[idx] = pn;
+      MQS_STC(q, idx, 3 * n3, 209, qn); MQS_STC(p, idx, 3 * n3, 210, pn);
     }
   }
 };
@@ -269,7 +272,7 @@ struct EpiApplyDot {  // w = t on n-edges (0 elsewhere); sums w.r with r the sou
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double wv = (m >> c & 1u) ? t[c] : 0.0;
-      w[e + c * n3] = wv;
+      MQS_STC(w, e + c * n3, 3 * n3, 211, wv);
       wr = fma(wv, s[c], wr);
     }
   }
@@ -481,6 +484,8 @@ int pcg_max_blocks(int* nblk) {
   *nblk = nsm * (occ < kPcgBlocksPerSM ? occ : kPcgBlocksPerSM);  // persistent, co-resident blocks
   return MQS_OK;
 }
+
+MQS_DEBUG_TAKE(pcg)
 
 }  // namespace mqs
 

@@ -48,9 +48,10 @@ using FusedSmemBlock = FusedSmemBlockT<double>;
 
 // r_{i+1} at one component position from the input buffers (no writes)
 template <class T>
-__device__ __forceinline__ T fused_src(const FusedVecsT<T>& v, int off) {
-  const T sv = v.first ? v.w_in[off] : fmaT(v.beta, v.s_in[off], v.w_in[off]);
-  return fmaT(-v.alpha, sv, v.r_in[off]);
+__device__ __forceinline__ T fused_src(const FusedVecsT<T>& v, int off, int n3) {
+  const T w = MQS_LDC(v.w_in, off, 3 * n3, 331);
+  const T sv = v.first ? w : fmaT(v.beta, MQS_LDC(v.s_in, off, 3 * n3, 332), w);
+  return fmaT(-v.alpha, sv, MQS_LDC(v.r_in, off, 3 * n3, 333));
 }
 
 // Update of one owned position (3 components): writes p, x, s_out, r_out and
@@ -60,15 +61,15 @@ __device__ __forceinline__ void fused_update(const FusedVecsT<T>& v, int o, int 
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int e = o + c * n3;
-    const T r = v.r_in[e], w = v.w_in[e];
-    const T s = v.first ? w : fmaT(v.beta, v.s_in[e], w);
-    const T p = v.first ? r : fmaT(v.beta, v.p[e], r);
-    const T x = v.x[e];
-    v.s_out[e] = s;
-    v.p[e] = p;
-    v.x[e] = fmaT(v.alpha, p, x);
+    const T r = MQS_LDC(v.r_in, e, 3 * n3, 301), w = MQS_LDC(v.w_in, e, 3 * n3, 302);
+    const T s = v.first ? w : fmaT(v.beta, MQS_LDC(v.s_in, e, 3 * n3, 303), w);
+    const T p = v.first ? r : fmaT(v.beta, MQS_LDC(v.p, e, 3 * n3, 304), r);
+    const T x = MQS_LDC(v.x, e, 3 * n3, 305);
+    MQS_STC(v.s_out, e, 3 * n3, 306, s);
+    MQS_STC(v.p, e, 3 * n3, 307, p);
+    MQS_STC(v.x, e, 3 * n3, 308, fmaT(v.alpha, p, x));
     const T rn = fmaT(-v.alpha, s, r);
-    v.r_out[e] = rn;
+    MQS_STC(v.r_out, e, 3 * n3, 309, rn);
     src[c] = rn;
   }
 }
@@ -84,11 +85,11 @@ __device__ __forceinline__ void fused_load(const FusedVecsT<T>& v, int o, int n3
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int e = o + c * n3;
-    L.r[c] = v.r_in[e];
-    L.w[c] = v.w_in[e];
-    L.s[c] = v.first ? T(0) : v.s_in[e];
-    L.p[c] = (owned && !v.first) ? v.p[e] : T(0);
-    L.x[c] = owned ? v.x[e] : T(0);
+    L.r[c] = MQS_LDC(v.r_in, e, 3 * n3, 310);
+    L.w[c] = MQS_LDC(v.w_in, e, 3 * n3, 311);
+    L.s[c] = v.first ? T(0) : MQS_LDC(v.s_in, e, 3 * n3, 312);
+    L.p[c] = (owned && !v.first) ? MQS_LDC(v.p, e, 3 * n3, 313) : T(0);
+    L.x[c] = owned ? MQS_LDC(v.x, e, 3 * n3, 314) : T(0);
   }
 }
 
@@ -104,10 +105,10 @@ __device__ __forceinline__ void fused_apply(const FusedVecsT<T>& v, int o, int n
     if (owned) {
       const int e = o + c * n3;
       const T pv = v.first ? L.r[c] : fmaT(v.beta, L.p[c], L.r[c]);
-      v.s_out[e] = sv;
-      v.p[e] = pv;
-      v.x[e] = fmaT(v.alpha, pv, L.x[c]);
-      v.r_out[e] = rn;
+      MQS_STC(v.s_out, e, 3 * n3, 315, sv);
+      MQS_STC(v.p, e, 3 * n3, 316, pv);
+      MQS_STC(v.x, e, 3 * n3, 317, fmaT(v.alpha, pv, L.x[c]));
+      MQS_STC(v.r_out, e, 3 * n3, 318, rn);
     }
   }
 }
@@ -153,15 +154,15 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
       // prologue: plane ks is owned -> update it; warm-up fluxes at ks - 1 from recomputed sources
       T sk[3] = {T(0), T(0), T(0)};
       if (act) fused_update(v, o, n3, sk);
-      else if (col) { sk[0] = fused_src(v, o); sk[1] = fused_src(v, o + n3); sk[2] = fused_src(v, o + 2 * n3); }
+      else if (col) { sk[0] = fused_src(v, o, n3); sk[1] = fused_src(v, o + n3, n3); sk[2] = fused_src(v, o + 2 * n3, n3); }
 #pragma unroll
       for (int c = 0; c < 3; ++c) sg.src[ks & 1][c][w + 1][lane + 1] = sk[c];
       T bxm = T(0), bym = T(0);
       if (ks >= 1 && col) {
         const int om = o - n2;
-        const T xm = fused_src(v, om), ym = fused_src(v, om + n3), zm = fused_src(v, om + 2 * n3);
-        const T zim = (i + 1 < n) ? fused_src(v, om + 1 + 2 * n3) : T(0);
-        const T zjm = (j + 1 < n) ? fused_src(v, om + n + 2 * n3) : T(0);
+        const T xm = fused_src(v, om, n3), ym = fused_src(v, om + n3, n3), zm = fused_src(v, om + 2 * n3, n3);
+        const T zim = (i + 1 < n) ? fused_src(v, om + 1 + 2 * n3, n3) : T(0);
+        const T zjm = (j + 1 < n) ? fused_src(v, om + n + 2 * n3, n3) : T(0);
         bxm = (ym - zm) + (zjm - sk[1]);
         bym = (zm - xm) + (sk[0] - zim);
       }
@@ -201,7 +202,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const T wv = (m >> c & 1u) ? t[c] : T(0);
-            v.w_out[o + c * n3] = wv;
+            MQS_STC(v.w_out, o + c * n3, 3 * n3, 319, wv);
             gamma = fmaT(sk[c], sk[c], gamma);
             delta = fmaT(wv, sk[c], delta);
           }
@@ -236,9 +237,9 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
           const int oo = ok ? hi + n * (hj + n * kk) : 0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : T(0);
-            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : T(0);
-            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : T(0);
+            hin[q].r[c] = ok ? MQS_LDC(v.r_in, oo + c * n3, 3 * n3, 325) : T(0);
+            hin[q].w[c] = ok ? MQS_LDC(v.w_in, oo + c * n3, 3 * n3, 326) : T(0);
+            hin[q].s[c] = (ok && !v.first) ? MQS_LDC(v.s_in, oo + c * n3, 3 * n3, 327) : T(0);
           }
         }
       };
@@ -348,10 +349,10 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
       const double r1 = fma(-v.alpha, sv, L.r[c]);
       const int e = o + c * n3;
       const double pv = v.first ? L.r[c] : fma(v.beta, L.p[c], L.r[c]);
-      v.s_out[e] = sv;
-      v.p[e] = pv;
-      v.x[e] = fma(v.alpha, pv, L.x[c]);
-      v.r_out[e] = r1;
+      MQS_STC(v.s_out, e, 3 * n3, 321, sv);
+      MQS_STC(v.p, e, 3 * n3, 322, pv);
+      MQS_STC(v.x, e, 3 * n3, 323, fma(v.alpha, pv, L.x[c]));
+      MQS_STC(v.r_out, e, 3 * n3, 324, r1);
       rn[c] = r1;
       mes = max(mes, fx_expo(sv));
       mer = max(mer, fx_expo(r1));
@@ -402,10 +403,10 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
       long long bxm = 0, bym = 0;
       if (ks >= 1 && col) {
         const int om = o - n2;
-        const long long xm = fx_from_double(fused_src(v, om), shi), ym = fx_from_double(fused_src(v, om + n3), shi);
-        const long long zm = fx_from_double(fused_src(v, om + 2 * n3), shi);
-        const long long zim = (i + 1 < n) ? fx_from_double(fused_src(v, om + 1 + 2 * n3), shi) : 0;
-        const long long zjm = (j + 1 < n) ? fx_from_double(fused_src(v, om + n + 2 * n3), shi) : 0;
+        const long long xm = fx_from_double(fused_src(v, om, n3), shi), ym = fx_from_double(fused_src(v, om + n3, n3), shi);
+        const long long zm = fx_from_double(fused_src(v, om + 2 * n3, n3), shi);
+        const long long zim = (i + 1 < n) ? fx_from_double(fused_src(v, om + 1 + 2 * n3, n3), shi) : 0;
+        const long long zjm = (j + 1 < n) ? fx_from_double(fused_src(v, om + n + 2 * n3, n3), shi) : 0;
         bxm = (ym - zm) + (zjm - sk[1]);
         bym = (zm - xm) + (sk[0] - zim);
       }
@@ -447,7 +448,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const double wv = (m >> c & 1u) ? fx_to_double(t[c], sho) : 0.0;
-            v.w_out[o + c * n3] = wv;
+            MQS_STC(v.w_out, o + c * n3, 3 * n3, 320, wv);
             gamma = fma(skd[c], skd[c], gamma);
             delta = fma(wv, skd[c], delta);
             mew = max(mew, fx_expo(wv));
@@ -480,9 +481,9 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
           const int oo = ok ? hi + n * (hj + n * kk) : 0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            hin[q].r[c] = ok ? v.r_in[oo + c * n3] : 0.0;
-            hin[q].w[c] = ok ? v.w_in[oo + c * n3] : 0.0;
-            hin[q].s[c] = (ok && !v.first) ? v.s_in[oo + c * n3] : 0.0;
+            hin[q].r[c] = ok ? MQS_LDC(v.r_in, oo + c * n3, 3 * n3, 328) : 0.0;
+            hin[q].w[c] = ok ? MQS_LDC(v.w_in, oo + c * n3, 3 * n3, 329) : 0.0;
+            hin[q].s[c] = (ok && !v.first) ? MQS_LDC(v.s_in, oo + c * n3, 3 * n3, 330) : 0.0;
           }
         }
       };

@@ -208,7 +208,10 @@ __device__ void sweep_cg24(const Geom& g, const Cg24Vecs& v, const Box& box, int
     const uint8_t* const cfcol = incb ? g.cflags + (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : g.cflags;
     // conductor flags of plane k (c-edges are not n-edges)
     auto cflag = [&](int k) -> unsigned {
-      return (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) ? (unsigned)cfcol[cw01 * (k - g.cb_lo[2])] : 0u;
+      return (incb && k >= g.cb_lo[2] && k < g.cb_hi[2])
+                 ? (unsigned)MQS_LDC(cfcol, cw01 * (k - g.cb_lo[2]),
+                                     (long long)cw01 * (g.cb_hi[2] - g.cb_lo[2]) - (cfcol - g.cflags), 801)
+                 : 0u;
     };
     const int kb = ks - 2;                               // first step (warm-up of the lag)
     // the staging ring: plane sm_ of slot ss_ is the next to issue
@@ -220,8 +223,9 @@ __device__ void sweep_cg24(const Geom& g, const Cg24Vecs& v, const Box& box, int
       const unsigned sa = stage0 + (unsigned)st_slot * kSlotBytes;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        cp_async4(sa + c * kCompBytes, v.r_in + (ok ? off + c * n3 : 0), ok ? 4 : 0);
-        cp_async4(sa + (3 + c) * kCompBytes, v.p_in + (okp ? off + c * n3 : 0), okp ? 4 : 0);
+        const bool okc = ok && MQS_IDX_OK(off + c * n3, 3 * n3, 802);   // zero-fill when out of range
+        cp_async4(sa + c * kCompBytes, v.r_in + (okc ? off + c * n3 : 0), okc ? 4 : 0);
+        cp_async4(sa + (3 + c) * kCompBytes, v.p_in + (okp && okc ? off + c * n3 : 0), okp && okc ? 4 : 0);
       }
       cp_async_commit();
       ++st_m;
@@ -278,7 +282,7 @@ __device__ void sweep_cg24(const Geom& g, const Cg24Vecs& v, const Box& box, int
       float xn[3] = {0.f, 0.f, 0.f};                     // x of plane k (the next step's output)
       if (own && k >= ks && k < ke) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xn[c] = v.x[ok_off + c * n3];
+        for (int c = 0; c < 3; ++c) xn[c] = MQS_LDC(v.x, ok_off + c * n3, 3 * n3, 803);
       }
       // p(k+1) rows for the next step; fluxes of p at plane k
       xp[nq * kPar] = pk1[0];
@@ -326,9 +330,9 @@ __device__ void sweep_cg24(const Geom& g, const Cg24Vecs& v, const Box& box, int
           const int o = ok_off - n2;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            v.p_out[o + c * n3] = pm1[c];
-            v.r_out[o + c * n3] = r1m1[c];
-            v.x[o + c * n3] = fmaf(al, pm1[c], xk[c]);
+            MQS_STC(v.p_out, o + c * n3, 3 * n3, 804, pm1[c]);
+            MQS_STC(v.r_out, o + c * n3, 3 * n3, 805, r1m1[c]);
+            MQS_STC(v.x, o + c * n3, 3 * n3, 806, fmaf(al, pm1[c], xk[c]));
             gamma = fmaf(r1m1[c], r1m1[c], gamma);
             delta = fmaf(r1m1[c], wv[c], delta);
           }
@@ -732,5 +736,7 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(two ? 2 * nblk : nblk), dim3(kBlock), args, (size_t)smem, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
+
+MQS_DEBUG_TAKE(mixed)
 
 }  // namespace mqs

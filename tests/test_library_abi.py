@@ -68,7 +68,7 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         pytest.skip("no C compiler")
     pairs = {"mqs_grid": b.Grid, "mqs_materials": b.Materials, "mqs_coil": b.Coil, "mqs_options": b.Options,
              "mqs_layout_info": b.LayoutInfo, "mqs_adjoint_info": b.AdjointInfo, "mqs_step_stats": b.StepStats,
-             "mqs_timing": b.Timing, "mqs_pcg_info": b.PcgInfo}
+             "mqs_timing": b.Timing, "mqs_pcg_info": b.PcgInfo, "mqs_debug_report": b.DebugReport}
     lines = ['#include <stdio.h>', '#include "mqs.h"', "int main(void) {"]
     for cname, py in pairs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -88,3 +88,23 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
+
+
+def test_release_debug_check_reports_disabled(lib):
+    # the release library answers without touching the device
+    import ctypes
+    import paper_1611_06721_gb300.binding as b
+    rep = b.DebugReport(7, 7, 7, 7, 7, 7)
+    assert lib.mqs_debug_check(None, ctypes.byref(rep)) == 0
+    assert (rep.enabled, rep.site, rep.index, rep.faults, rep.canaries_bad, rep.buffers) == (0, 0, 0, 0, 0, 0)
+    assert lib.mqs_debug_check(None, None) == -1
+
+
+def test_debug_variant_builds_and_exports_the_header(tmp_path):
+    import ctypes
+    from paper_1611_06721_gb300 import build as bld
+    path = bld.build(debug=True)
+    assert path.endswith(os.path.join("_lib_debug", "libmqs.so"))
+    dbg = ctypes.CDLL(path)
+    missing = [n for n in declared_entry_points() if not hasattr(dbg, n)]
+    assert not missing, missing
