@@ -557,6 +557,71 @@ def single_solve(variant=1):
     s.close()
 
 
+def block_sweep(sizes):
+    """What the batched mode can gain, per grid size: one zero-start solve of K_n w = 100 X_s
+    on the scaled iron workload with the persistent PCG kernel on b blocks (b from 2 to one
+    per SM), FP64 and FP32-inner (pcg_variant 1), CUDA-event time per iteration and its
+    block-microseconds (b x time per iteration: constant where each block's share of the
+    sweep sets the pace, rising where the grid reductions do); then 8 copies of the problem
+    solved at once on 8 streams with 19 blocks each against the same 8 solves one after
+    another on every SM.  One JSON line per (size, precision)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1611_06721_gb300 as pkg
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    for n in sizes:
+        p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
+        for prec in (0, 1):
+            opts = pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec, pcg_variant=1)
+            solvers = [pkg.Solver.from_problem(p, opts) for _ in range(8)]
+            streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
+            for sv, st in zip(solvers, streams):
+                sv.set_stream(st.cuda_stream)
+            b = torch.from_numpy(coil_rhs(p)).to(dev)
+            xs = [torch.zeros_like(b) for _ in range(8)]
+            torch.cuda.synchronize(dev)
+
+            def solve(k, nblk):
+                solvers[k].set_blocks(nblk)
+                xs[k].zero_()
+                return solvers[k].pcg_solve_dev(b, xs[k], tol=1e-10, stream=streams[k].cuda_stream)
+
+            def timed(fn):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record()
+                out = fn()
+                for st in streams:
+                    torch.cuda.current_stream(dev).wait_stream(st)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                return e0.elapsed_time(e1), out
+
+            rows = []
+            for nblk in (2, 4, 8, 16, 19, 38, 76, nsm):
+                solve(0, nblk)                                   # warm-up
+                ms, info = timed(lambda: solve(0, nblk))
+                its = max(info.iterations, 1)
+                rows.append({"blocks": nblk, "iterations": info.iterations, "us_per_iter": 1e3 * ms / its,
+                             "block_us_per_iter": nblk * 1e3 * ms / its})
+            for k in range(8):
+                solve(k, 19)
+            ms_conc, _ = timed(lambda: [solve(k, 19) for k in range(8)])
+            ms_seq, _ = timed(lambda: [solve(k, nsm) for k in range(8)])
+            print(json.dumps({"sweep": "blocks per solve", "workload": workload_name(p), "grid": n,
+                              "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
+                              "n_unknowns": int(solvers[0].n_n), "rows": rows,
+                              "eight_concurrent_19_blocks_ms": ms_conc, "eight_sequential_all_sms_ms": ms_seq,
+                              "concurrent_speedup": ms_seq / ms_conc}), flush=True)
+            for sv in solvers:
+                sv.close()
+
+
 def size_sweep(sizes):
     """Zero-start solves of K_n w = 100 X_s on the scaled iron workload at each grid
     size, FP64 and mixed precision (one-reduction FP32 inner CG): time per PCG
@@ -952,6 +1017,8 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
     ap.add_argument("--sweep", type=str, default="",
                     help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
+    ap.add_argument("--block-sweep", type=str, default="",
+                    help="comma-separated grid sizes: PCG time per iteration against the block count")
     ap.add_argument("--batch-sub", type=int, default=64,
                     help="instances of the short batched measurement added to the line (0: skip)")
     ap.add_argument("--batch-sub-steps", type=int, default=20, help="timed steps of that batch")
@@ -983,6 +1050,9 @@ def main():
         return
     if args.sweep:
         size_sweep([int(v) for v in args.sweep.split(",") if v])
+        return
+    if args.block_sweep:
+        block_sweep([int(v) for v in args.block_sweep.split(",") if v])
         return
     if args.batch:
         run_batch(args)

@@ -68,6 +68,11 @@ __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac,
   }
 }
 
+// The per-edge and per-cell kernels of the step are FP64-bound on the SMs they occupy and
+// their work is small (tens of thousands of edges): 64-thread blocks spread it over every
+// SM instead of a few dozen (ncu: 256-thread blocks filled 35-119 of 152 SMs).
+constexpr int kSmallBlock = 64;
+
 static int stencil_grid(const Box& box) {
   long long ntx = (box.hi[0] - box.lo[0] + 31) / 32, nty = (box.hi[1] - box.lo[1] + kTY - 1) / kTY;
   long long T = ntx * nty * (box.hi[2] - box.lo[2]);
@@ -85,7 +90,8 @@ int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, 
 int launch_rhs(const DevGeom& dg, const double* ac_full, double* b, CoilDrive drive, CoilGeom coil, const int* sup,
                int nsup, cudaStream_t st) {
   if (nsup <= 0) return MQS_OK;
-  rhs_list_kernel<<<(nsup + 255) / 256, 256, 0, st>>>(dg.g, ac_full, b, drive, coil, sup, nsup);
+  rhs_list_kernel<<<(nsup + kSmallBlock - 1) / kSmallBlock, kSmallBlock, 0, st>>>(dg.g, ac_full, b, drive, coil,
+                                                                                   sup, nsup);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
@@ -230,21 +236,21 @@ __global__ void scatter_c_kernel(int n_c, const int* c_idx, const double* a_c, d
 int launch_cell_nu(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w, bool at_zero,
                    cudaStream_t st, const int* halt) {
   const long long ncell = (long long)(cg.chi[0] - cg.clo[0]) * (cg.chi[1] - cg.clo[1]) * (cg.chi[2] - cg.clo[2]);
-  int blocks = (int)((ncell + 255) / 256);
-  if (blocks > 1024) blocks = 1024;
+  int blocks = (int)((ncell + kSmallBlock - 1) / kSmallBlock);
+  if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  cell_nu_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, at_zero ? 1 : 0, halt);
+  cell_nu_kernel<<<blocks, kSmallBlock, 0, st>>>(dg.g, cg, ac_full, w, at_zero ? 1 : 0, halt);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
 int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_full, const double* w,
                        double sign_w, const double* a_c_in, double* a_c_out, double dt, cudaStream_t st,
                        double* ac_full_out, double* F_out, double* a_prev_out, const GuardView* guard) {
-  int blocks = (cg.n_c + 255) / 256;
+  int blocks = (cg.n_c + kSmallBlock - 1) / kSmallBlock;
   if (blocks > kMonBlocks) blocks = kMonBlocks;
   if (blocks < 1) blocks = 1;
   const GuardView gv = guard ? *guard : GuardView{nullptr, nullptr, nullptr, nullptr, 0};
-  cond_update_kernel<<<blocks, 256, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out, F_out,
+  cond_update_kernel<<<blocks, kSmallBlock, 0, st>>>(dg.g, cg, ac_full, w, sign_w, a_c_in, a_c_out, dt, ac_full_out, F_out,
                                              a_prev_out, gv);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }

@@ -192,10 +192,27 @@ static void launch_lincomb(const VecSet& V, const double* coef, int m, long long
 
 // ---- small dense kernels (one block) ----------------------------------------------------
 // fixed-order sum over blocks of one partial slot (serial; small callers)
+// Sum over the nblk block partials of one product slot by one warp (every lane calls
+// it; the total comes back in every lane): each lane adds its blocks lane, lane + 32, ...
+// with the loads issued ahead, then a fixed shuffle tree and lane 0's value broadcast,
+// so the result does not depend on scheduling.  (A single thread walking the blocks in
+// order waits one L2 round trip per block: ~47 us for 304 blocks.)
 __device__ double sum_part(const double* part, int nblk, int slot) {
-  double s = 0.0;
-  for (int q = 0; q < nblk; ++q) s += part[(size_t)q * kTileSlots + slot];
-  return s;
+  const int lane = threadIdx.x & 31;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  int q = lane;
+  for (; q + 96 < nblk; q += 128) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] += __ldcg(part + (size_t)(q + 32 * r) * kTileSlots + slot);
+  }
+  // at most three blocks are left: q, q + 32, q + 64
+  if (q < nblk) a[0] += __ldcg(part + (size_t)q * kTileSlots + slot);
+  if (q + 32 < nblk) a[1] += __ldcg(part + (size_t)(q + 32) * kTileSlots + slot);
+  if (q + 64 < nblk) a[2] += __ldcg(part + (size_t)(q + 64) * kTileSlots + slot);
+  double s = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
 }
 
 // Pivoted (in order) Cholesky of the symmetric m x m matrix H (row-major in
@@ -372,14 +389,50 @@ __device__ void chol_solve_reg(const double (&h)[M], double inv, double sc, cons
 }
 
 // Gram row of a new snapshot: part tiles t = 0..ntile-1 hold (w, Lw) . X_q.
+// (one warp per entry)
 __global__ void pod_row_kernel(const double* part, int nblk, int m, int slot_new, double* G, double* A) {
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = wid; q < m; q += nw) {
     const int tile = q / 8, qq = q % 8;
     const double* pt = part + (size_t)tile * nblk * kTileSlots;
     const double gw = sum_part(pt, nblk, 0 * 8 + qq), aw = sum_part(pt, nblk, 1 * 8 + qq);
-    G[slot_new * kMaxPod + q] = gw; G[q * kMaxPod + slot_new] = gw;
-    A[slot_new * kMaxPod + q] = aw; A[q * kMaxPod + slot_new] = aw;
+    if (lane == 0) {
+      G[slot_new * kMaxPod + q] = gw; G[q * kMaxPod + slot_new] = gw;
+      A[slot_new * kMaxPod + q] = aw; A[q * kMaxPod + slot_new] = aw;
+    }
   }
+}
+
+// Jacobi rotation (c, s) annihilating a_pq of the symmetric block [[a_pp, a_pq], [a_pq, a_qq]]
+// (the classical choice, Golub & Van Loan, "Matrix Computations", Sec. 8.5:
+// tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = (1 + t^2)^(-1/2),
+// s = t c).  t is formed in FP32: every t gives a rotation that is orthogonal to FP64 rounding
+// once c and s are formed from it in FP64, and an FP32 t leaves |a_pq'| ~ 1e-7 |a_pq| for the
+// next sweep to remove (the sweep and rotation counts of the FP64 form, emulated on the
+// snapshot matrices of the stepping workloads).  c = (1 + t^2)^(-1/2) in FP64 from the FP32
+// reciprocal square root by two Newton steps y <- y (3 - x y^2) / 2 (quadratic convergence:
+// 1e-7 -> 1e-14 -> rounding).  Ratios outside FP32's range take the FP64 form (rare).
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& c, double& s) {
+  const double d = aqq - app;
+  const float a32 = (float)(2.0 * apq), d32 = (float)d;
+  const float th = d32 / a32;
+  double t;
+  if (!(fabsf(a32) >= 0x1p-120f && fabsf(a32) <= 0x1p120f && fabsf(th) <= 0x1p60f)) {
+    const double th64 = d / (2.0 * apq);
+    const double at = fabs(th64);
+    t = (at > 1e150) ? 0.5 / th64 : copysign(1.0 / (at + sqrt(fma(th64, th64, 1.0))), th64);
+  } else if (fabsf(th) > 0x1p20f) {
+    t = (double)(0.5f / th);                       // 1/(2 tau): relative error tau^-2 < 2^-40
+  } else {
+    const float t32 = 1.0f / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+    t = (double)(th >= 0.f ? t32 : -t32);
+  }
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  c = y;
+  s = t * y;
 }
 
 // POD solve: Jacobi eigen-decomposition of G (m x m), truncation, reduced
@@ -392,20 +445,22 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
   __shared__ double lam[kMaxPod], gv[kMaxPod], rhs[kMaxPod], y[kMaxPod];
   __shared__ int order[kMaxPod], keep[kMaxPod];
   __shared__ double cs[kMaxPod / 2 + 1], sn[kMaxPod / 2 + 1];
-  __shared__ int pp[kMaxPod / 2 + 1], qq[kMaxPod / 2 + 1];
+  __shared__ int pp[kMaxPod / 2 + 1], qq[kMaxPod / 2 + 1], rot[kMaxPod / 2 + 1];
   __shared__ int rotated;
   __shared__ double floor_abs;
   __shared__ int kk;
   const int tid = threadIdx.x;
   const int me = (m + 1) & ~1;  // even size for the round-robin ordering (padding index is inert)
+  const int np = me / 2;
   for (int s = tid; s < me * me; s += blockDim.x) {
     const int p = s / me, q = s % me;
     Mt[s] = (p < m && q < m) ? Gg[p * kMaxPod + q] : 0.0;
     V[s] = (p == q) ? 1.0 : 0.0;
   }
-  for (int p = tid; p < m; p += blockDim.x) {
+  for (int p = tid >> 5; p < m; p += blockDim.x >> 5) {
     const int tile = p / 8;
-    gv[p] = sum_part(part + (size_t)tile * nblk * kTileSlots, nblk, 64 + (p % 8));
+    const double v = sum_part(part + (size_t)tile * nblk * kTileSlots, nblk, 64 + (p % 8));
+    if ((tid & 31) == 0) gv[p] = v;
   }
   __syncthreads();
   if (tid == 0) {
@@ -421,50 +476,71 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
   // below it are noise, and far below the POD truncation at sigma_i/sigma_1 >= eps_POD);
   // the sweep that rotates no pair ends the iteration.  (An off-norm test against the
   // total norm cannot be met below the rounding level and ran every sweep.)
+  // A round applies J^T M J (J: the round's rotations, block diagonal over its pairs) in one
+  // pass over the 2 x 2 blocks of M on and above the block diagonal, from one buffer into the
+  // other (Mt / Hs; Hs is free until the Galerkin system), and V <- V J on the rotated pairs'
+  // columns: two barriers per round.  Pairs left alone cost no arithmetic.
+  double* cur = Mt;
+  double* nxt = Hs;
   for (int sweep = 0; sweep < 40 && me >= 2; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < me - 1; ++round) {
-      // pairs of the round-robin schedule: index me-1 fixed, others rotate
-      for (int t = tid; t < me / 2; t += blockDim.x) {
+      for (int t = tid; t < np; t += blockDim.x) {
         // circle method: index me-1 meets `round`, the others pair symmetrically
         const int a = (t == 0) ? me - 1 : (round + t) % (me - 1);
         const int b = (t == 0) ? round : (round - t + me - 1) % (me - 1);
         const int p = a < b ? a : b, q = a < b ? b : a;
         pp[t] = p; qq[t] = q;
-        const double apq = Mt[p * me + q];
+        const double apq = cur[p * me + q], app = cur[p * me + p], aqq = cur[q * me + q];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(Mt[p * me + p] * Mt[q * me + q]))) {
-          const double theta = (Mt[q * me + q] - Mt[p * me + p]) / (2.0 * apq);
-          const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(tt * tt + 1.0);
-          s = tt * c;
+        const int r = fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq));
+        if (r) {
+          jacobi_rotation(app, aqq, apq, c, s);
           rotated = 1;
         }
-        cs[t] = c; sn[t] = s;
+        cs[t] = c; sn[t] = s; rot[t] = r;
       }
       __syncthreads();
-      // rows: M <- J^T M
-      for (int w = tid; w < (me / 2) * me; w += blockDim.x) {
-        const int t = w / me, col = w % me, p = pp[t], q = qq[t];
-        const double c = cs[t], s = sn[t];
-        const double mp = Mt[p * me + col], mq = Mt[q * me + col];
-        Mt[p * me + col] = c * mp - s * mq;
-        Mt[q * me + col] = s * mp + c * mq;
+      // M' = J^T M J by 2 x 2 blocks (pair i rows, pair j columns, i <= j), mirrored below
+      for (int w = tid; w < np * np; w += blockDim.x) {
+        const int i = w / np, j = w % np;
+        if (i > j) continue;
+        const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
+        double b00 = cur[pi * me + pj], b01 = cur[pi * me + qj], b10 = cur[qi * me + pj], b11 = cur[qi * me + qj];
+        if (rot[j]) {
+          const double c = cs[j], s = sn[j];
+          const double n00 = fma(c, b00, -s * b01), n01 = fma(s, b00, c * b01);
+          const double n10 = fma(c, b10, -s * b11), n11 = fma(s, b10, c * b11);
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (rot[i]) {
+          const double c = cs[i], s = sn[i];
+          const double n00 = fma(c, b00, -s * b10), n10 = fma(s, b00, c * b10);
+          const double n01 = fma(c, b01, -s * b11), n11 = fma(s, b01, c * b11);
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (i == j) {
+          const double o = 0.5 * (b01 + b10);
+          b01 = o; b10 = o;
+        }
+        nxt[pi * me + pj] = b00; nxt[pi * me + qj] = b01; nxt[qi * me + pj] = b10; nxt[qi * me + qj] = b11;
+        if (i != j) {
+          nxt[pj * me + pi] = b00; nxt[qj * me + pi] = b01; nxt[pj * me + qi] = b10; nxt[qj * me + qi] = b11;
+        }
       }
-      __syncthreads();
-      // columns: M <- M J ; V <- V J
-      for (int w = tid; w < (me / 2) * me; w += blockDim.x) {
-        const int t = w / me, row = w % me, p = pp[t], q = qq[t];
+      // V <- V J on the rotated pairs
+      for (int w = tid; w < me * np; w += blockDim.x) {
+        const int row = w / np, t = w % np;
+        if (!rot[t]) continue;
+        const int p = pp[t], q = qq[t];
         const double c = cs[t], s = sn[t];
-        const double mp = Mt[row * me + p], mq = Mt[row * me + q];
-        Mt[row * me + p] = c * mp - s * mq;
-        Mt[row * me + q] = s * mp + c * mq;
         const double vp = V[row * me + p], vq = V[row * me + q];
-        V[row * me + p] = c * vp - s * vq;
-        V[row * me + q] = s * vp + c * vq;
+        V[row * me + p] = fma(c, vp, -s * vq);
+        V[row * me + q] = fma(s, vp, c * vq);
       }
       __syncthreads();
+      double* sw_ = cur; cur = nxt; nxt = sw_;
     }
     // every thread reads the flag before the barrier; thread 0 resets it only after,
     // so all threads take the same branch
@@ -473,7 +549,7 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
     if (!any) break;
   }
   if (tid == 0) {
-    for (int p = 0; p < m; ++p) { lam[p] = Mt[p * me + p]; order[p] = p; }
+    for (int p = 0; p < m; ++p) { lam[p] = cur[p * me + p]; order[p] = p; }
     for (int a = 0; a < m; ++a)            // selection sort, descending
       for (int b = a + 1; b < m; ++b)
         if (lam[order[b]] > lam[order[a]]) { const int t = order[a]; order[a] = order[b]; order[b] = t; }
@@ -543,17 +619,35 @@ __device__ __forceinline__ double tile_dot(const double* part, int nblk, int q) 
 }
 
 // coef = [1, -h_1 .. -h_k] with h_i = product i; scal[0] = product k (x.Lx) when with_norm
+// (one warp per value)
 __global__ void cspe_proj_kernel(const double* part, int nblk, int k, int with_norm, double* coef, double* scal) {
-  for (int q = threadIdx.x; q <= k; q += blockDim.x) coef[q] = (q == 0) ? 1.0 : -tile_dot(part, nblk, q - 1);
-  if (with_norm && threadIdx.x == 0) scal[0] = tile_dot(part, nblk, k);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) coef[0] = 1.0;
+  for (int q = wid; q < k + (with_norm ? 1 : 0); q += nw) {
+    const double v = tile_dot(part, nblk, q);
+    if (lane == 0) {
+      if (q < k) coef[q + 1] = -v;
+      else scal[0] = v;
+    }
+  }
 }
 
 // x0 coefficients [Q^T b, (z.b)/zeta] from partC (Q_i.b, then z.b) and partD (z.Lz)
+// (one warp per product)
 __global__ void cspe_coef_kernel(const double* partC, const double* partD, int nblk, int k, double drop2,
                                  double* coef, double* scal, SmallOut* out) {
-  for (int q = threadIdx.x; q < k; q += blockDim.x) coef[q] = tile_dot(partC, nblk, q);
+  __shared__ double zz[2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = wid; q < k + 2; q += nw) {
+    const double v = (q <= k) ? tile_dot(partC, nblk, q) : tile_dot(partD, nblk, 0);
+    if (lane == 0) {
+      if (q < k) coef[q] = v;
+      else zz[q - k] = v;              // zz[0] = z.b, zz[1] = z.Lz
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double zeta = tile_dot(partD, nblk, 0), zb = tile_dot(partC, nblk, k);
+    const double zeta = zz[1], zb = zz[0];
     const bool keep = zeta > 0.0 && zeta > drop2 * scal[0];
     coef[k] = keep ? zb / zeta : 0.0;
     scal[1] = keep ? rsqrt(zeta) : 0.0;
@@ -1094,7 +1188,7 @@ int pod_push(const VecSet& X, const double* w, const double* lw, int m, int slot
     for (int q = 0; q < 8; ++q) Bx.v[q] = X.v[8 * t + (q < mb ? q : 0)];
     dots_kernel<kRow2><<<nb, kTS, 0, st>>>(Aw, Bx, nullptr, 2, mb, len, part + (size_t)t * nb * kTileSlots);
   }
-  pod_row_kernel<<<1, 64, 0, st>>>(part, nb, m, slot_new, G, A);
+  pod_row_kernel<<<1, 256, 0, st>>>(part, nb, m, slot_new, G, A);
   return chk();
 }
 
@@ -1141,7 +1235,7 @@ int cspe_x0(const CspeBufs& cb, int k, const double* x, const double* lx, const 
   PX.v[k] = lx;
   // pass 1: h = P^T x (= Q^T L x) and x.Lx; z = x - Q h, Lz = Lx - P h
   dots_against(PX, k + 1, x, len, part, nb, st);
-  cspe_proj_kernel<<<1, 32, 0, st>>>(part, nb, k, 1, coef, cb.scal);
+  cspe_proj_kernel<<<1, 256, 0, st>>>(part, nb, k, 1, coef, cb.scal);
   V.v[0] = x;
   W.v[0] = lx;
   for (int i = 0; i < k; ++i) { V.v[1 + i] = cb.Q[i]; W.v[1 + i] = cb.P[i]; }
@@ -1152,7 +1246,7 @@ int cspe_x0(const CspeBufs& cb, int k, const double* x, const double* lx, const 
   if (k > 0) {
     // pass 2 (re-orthogonalisation against the rounding of pass 1)
     dots_against(PX, k, cb.z, len, part, nb, st);
-    cspe_proj_kernel<<<1, 32, 0, st>>>(part, nb, k, 0, coef, cb.scal);
+    cspe_proj_kernel<<<1, 256, 0, st>>>(part, nb, k, 0, coef, cb.scal);
     V.v[0] = cb.z;
     W.v[0] = cb.lz;
     launch_lincomb(V, coef, k + 1, len, cb.z2, nb, st);
@@ -1167,7 +1261,7 @@ int cspe_x0(const CspeBufs& cb, int k, const double* x, const double* lx, const 
   ZX.v[0] = zf;
   dots_against(QX, k + 1, b, len, partC, nb, st);
   dots_against(ZX, 1, lzf, len, partD, nb, st);
-  cspe_coef_kernel<<<1, 32, 0, st>>>(partC, partD, nb, k, eps_lin * eps_lin, coef, cb.scal, out);
+  cspe_coef_kernel<<<1, 256, 0, st>>>(partC, partD, nb, k, eps_lin * eps_lin, coef, cb.scal, out);
   launch_lincomb(QX, coef, k + 1, len, x0, nb, st);
   return chk();
 }
