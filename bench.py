@@ -562,9 +562,10 @@ def block_sweep(sizes):
     on the scaled iron workload with the persistent PCG kernel on b blocks (b from 2 to one
     per SM), FP64 and FP32-inner (pcg_variant 1), CUDA-event time per iteration and its
     block-microseconds (b x time per iteration: constant where each block's share of the
-    sweep sets the pace, rising where the grid reductions do); then 8 copies of the problem
-    solved at once on 8 streams with 19 blocks each against the same 8 solves one after
-    another on every SM.  One JSON line per (size, precision)."""
+    sweep sets the pace, rising where the grid reductions and barriers do).  A batch that
+    runs its problems side by side on b_i blocks each can gain at most the ratio of the
+    block-microseconds at one block per SM to those at b_i.  One JSON line per (size,
+    precision)."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -576,50 +577,33 @@ def block_sweep(sizes):
     for n in sizes:
         p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
         for prec in (0, 1):
-            opts = pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec, pcg_variant=1)
-            solvers = [pkg.Solver.from_problem(p, opts) for _ in range(8)]
-            streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
-            for sv, st in zip(solvers, streams):
-                sv.set_stream(st.cuda_stream)
+            s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
+                                                             pcg_variant=1))
+            stream = torch.cuda.Stream(device=dev)
+            s.set_stream(stream.cuda_stream)
             b = torch.from_numpy(coil_rhs(p)).to(dev)
-            xs = [torch.zeros_like(b) for _ in range(8)]
-            torch.cuda.synchronize(dev)
-
-            def solve(k, nblk):
-                solvers[k].set_blocks(nblk)
-                xs[k].zero_()
-                return solvers[k].pcg_solve_dev(b, xs[k], tol=1e-10, stream=streams[k].cuda_stream)
-
-            def timed(fn):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(dev)
-                e0.record()
-                out = fn()
-                for st in streams:
-                    torch.cuda.current_stream(dev).wait_stream(st)
-                e1.record()
-                torch.cuda.synchronize(dev)
-                return e0.elapsed_time(e1), out
-
+            x = torch.zeros_like(b)
             rows = []
             for nblk in (2, 4, 8, 16, 19, 38, 76, nsm):
-                solve(0, nblk)                                   # warm-up
-                ms, info = timed(lambda: solve(0, nblk))
+                s.set_blocks(nblk)
+                times = []
+                for rep in range(2):                                 # the first is a warm-up
+                    x.zero_()
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    info = s.pcg_solve_dev(b, x, tol=1e-10, stream=stream.cuda_stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    times.append(e0.elapsed_time(e1))
                 its = max(info.iterations, 1)
-                rows.append({"blocks": nblk, "iterations": info.iterations, "us_per_iter": 1e3 * ms / its,
-                             "block_us_per_iter": nblk * 1e3 * ms / its})
-            for k in range(8):
-                solve(k, 19)
-            ms_conc, _ = timed(lambda: [solve(k, 19) for k in range(8)])
-            ms_seq, _ = timed(lambda: [solve(k, nsm) for k in range(8)])
+                rows.append({"blocks": nblk, "iterations": info.iterations, "us_per_iter": 1e3 * times[-1] / its,
+                             "block_us_per_iter": nblk * 1e3 * times[-1] / its})
             print(json.dumps({"sweep": "blocks per solve", "workload": workload_name(p), "grid": n,
                               "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
-                              "n_unknowns": int(solvers[0].n_n), "rows": rows,
-                              "eight_concurrent_19_blocks_ms": ms_conc, "eight_sequential_all_sms_ms": ms_seq,
-                              "concurrent_speedup": ms_seq / ms_conc}), flush=True)
-            for sv in solvers:
-                sv.close()
+                              "n_unknowns": int(s.n_n), "rows": rows}), flush=True)
+            s.close()
 
 
 def size_sweep(sizes):
@@ -715,7 +699,8 @@ def run_batch(args):
             pcg_variant=args.pcg_variant, dt=0.9 * 2.0 / lam, graph=args.graph)))
     setup_s = time.perf_counter() - t0
     batch = pkg.Batch(solvers)
-    best = batch.tune(max(args.warmup // 4, 1))
+    best = batch.tune(max(args.warmup // 16, 1))     # 16 trials (8 candidates, twice)
+    by_work = batch.weighting()
     depth_by_n = None
     if args.tune_depth:
         chosen = batch.tune_depth(max(args.warmup // 4, 5), depths=(4, 8, 16))
@@ -763,7 +748,8 @@ def run_batch(args):
                                    + ", seed 1611",
                        "n_unknowns": int(sum(s.n_n for s in solvers)),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
-                       "blocks_scale": best, "l2": "working set larger than L2 (no flush)",
+                       "blocks_scale": best, "block_shares": "unknowns x iterations" if by_work else "unknowns",
+                       "l2": "working set larger than L2 (no flush)",
                        "graph_steps": graph_steps,
                        "parallelism": "1 GPU, instances on 32 streams"},
             "iters_per_step": float(its.mean()), "failed_steps": failed,
@@ -805,13 +791,14 @@ def batch_sub(args, dev):
         opts.append(o)
         solvers.append(pkg.Solver.from_problem(p, o))
     setup_s = time.perf_counter() - t0
-    trial = 2
+    trial = 1
     batch = pkg.Batch(solvers)
-    scale = batch.tune(trial)                       # 4 x trial warm-up steps
-    extra = max(args.batch_sub_warmup - 4 * trial, 0)
+    scale = batch.tune(trial)                       # 16 x trial warm-up steps (8 candidates, twice)
+    by_work = batch.weighting()
+    extra = max(args.batch_sub_warmup - 16 * trial, 0)
     if extra:
         batch.step(extra)
-    warm = 4 * trial + extra
+    warm = 16 * trial + extra
     rc, stats = batch.step(args.batch_sub_steps, allow_fail=True)
     ms = batch.last_ms()
     batch.close()
@@ -841,7 +828,8 @@ def batch_sub(args, dev):
             "n_unknowns": int(sum(p_n for p_n in (sv.n_n for sv in solvers))),
             "steps": args.batch_sub_steps, "first_step": warm + 1, "ms": ms,
             "precision": "FP32 inner CG in FP64 refinement (FP64 true residual 1e-10 per solve)",
-            "blocks_scale": scale, "inner_iters_per_step": float(its.mean()), "failed_steps": failed,
+            "blocks_scale": scale, "block_shares": "unknowns x iterations" if by_work else "unknowns",
+            "inner_iters_per_step": float(its.mean()), "failed_steps": failed,
             "single_instance_fp64": {"value": single, "unit": "instance-steps/s",
                                      "iters_per_step": float(np.mean(its64)),
                                      "note": "each instance alone on the whole GPU, FP64 PCG, the same steps"},
@@ -1022,7 +1010,7 @@ def main():
     ap.add_argument("--batch-sub", type=int, default=64,
                     help="instances of the short batched measurement added to the line (0: skip)")
     ap.add_argument("--batch-sub-steps", type=int, default=20, help="timed steps of that batch")
-    ap.add_argument("--batch-sub-warmup", type=int, default=10, help="its warm-up steps (tuning included)")
+    ap.add_argument("--batch-sub-warmup", type=int, default=16, help="its warm-up steps (tuning included)")
     ap.add_argument("--batch", type=int, default=0,
                     help="advance this many seeded multi-query instances together (batched mode)")
     ap.add_argument("--tune-depth", action="store_true",

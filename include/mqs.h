@@ -503,10 +503,19 @@ int mqs_loss(mqs_handle* h, int nsteps, double* objective);
  * mqs_batch_last_ms: device time of the last mqs_batch_step (CUDA events from
  * the fork of the streams to their join).
  *
- * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8 for trial_steps steps
- * each -- real steps that advance every problem -- and keeps the fastest
- * (returned in *best_scale, nullable).
+ * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8, each with block counts
+ * proportional to the unknowns and proportional to the unknowns times the
+ * PCG iterations per step of the previous call (the work weighting), for
+ * trial_steps steps each -- real steps that advance every problem -- once in
+ * that order and once in reverse.  A candidate's score is its device time per
+ * unit of PCG work (unknowns x iterations) summed over its two trials, so the
+ * falling iteration counts of a starting transient favour no candidate.  It
+ * keeps the best (its scale in *best_scale, nullable; the weighting through
+ * mqs_batch_get_weighting).
  * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts.
+ * mqs_batch_set_weighting: by_work 0 (shares by unknowns, the default) or 1
+ * (by unknowns x the last call's iterations per step) and reassigns the
+ * counts; mqs_batch_get_weighting reads it back.  MQS_ERR_ARG otherwise.
  *
  * mqs_batch_tune_depth: the SPE depth per grid size.  The handles with the SPE
  * start are grouped by n.  Group by group, in increasing n, the depths in
@@ -527,6 +536,8 @@ int mqs_batch_set_scale(mqs_batch* b, double blocks_scale);
 int mqs_batch_step(mqs_batch* b, int nsteps, mqs_step_stats* per_step);
 int mqs_batch_last_ms(mqs_batch* b, double* ms);
 int mqs_batch_tune(mqs_batch* b, int trial_steps, double* best_scale);
+int mqs_batch_set_weighting(mqs_batch* b, int by_work);
+int mqs_batch_get_weighting(const mqs_batch* b, int* by_work);
 int mqs_batch_tune_depth(mqs_batch* b, int trial_steps, const int* depths, int ndepths,
                          int* chosen);
 int mqs_batch_destroy(mqs_batch* b);

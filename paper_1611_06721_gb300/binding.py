@@ -35,7 +35,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
            "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth",
-           "mqs_debug_check")
+           "mqs_debug_check", "mqs_batch_set_weighting", "mqs_batch_get_weighting")
 
 
 class Grid(C.Structure):
@@ -154,6 +154,8 @@ def load():
         "mqs_batch_graph_steps": ([V, P(C.c_long)], I),
         "mqs_batch_tune_depth": ([V, I, P(I), I, P(I)], I),
         "mqs_debug_check": ([H, P(DebugReport)], I),
+        "mqs_batch_set_weighting": ([V, I], I),
+        "mqs_batch_get_weighting": ([V, P(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -580,6 +582,15 @@ class Batch:
         v = C.c_double()
         self._check(self.lib.mqs_batch_tune(self.b, trial_steps, C.byref(v)))
         return v.value
+
+    def set_weighting(self, by_work):
+        """Block shares by unknowns (False) or unknowns x last iterations (True)."""
+        self._check(self.lib.mqs_batch_set_weighting(self.b, int(by_work)))
+
+    def weighting(self):
+        v = C.c_int()
+        self._check(self.lib.mqs_batch_get_weighting(self.b, C.byref(v)))
+        return bool(v.value)
 
     def tune_depth(self, trial_steps, depths=(4, 8, 16)):
         """SPE depth per grid size (mqs_batch_tune_depth); returns every solver's depth."""

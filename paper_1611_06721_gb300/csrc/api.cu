@@ -16,6 +16,14 @@
 using namespace mqs;
 
 namespace {
+// The calling thread's tall-skinny launch cap for the duration of a scope
+struct LaunchCap {
+  int saved;
+  explicit LaunchCap(int cap) : saved(launch_cap()) { set_launch_cap(cap); }
+  ~LaunchCap() { set_launch_cap(saved); }
+  LaunchCap(const LaunchCap&) = delete;
+  LaunchCap& operator=(const LaunchCap&) = delete;
+};
 // NVTX range over the host's issue of one phase (a profiler shows the kernels each
 // range launched); free when no tool is attached
 struct Range {
@@ -86,6 +94,8 @@ struct mqs_handle {
   double *spe_hpart = nullptr, *spe_gpart = nullptr;   // Galerkin product partials of the table, g partials
   SpeFac* spe_fac = nullptr;     // factor of the table's small system (drop rule at fac_eps)
   double fac_eps = -1.0;
+  int spe_nbh = 0;               // block partials the last push wrote (the factor's layout)
+  int ts_cap = 0;                // tall-skinny launch cap while in a batch (0: none)
   // side stream: the SPE table push (with its products) runs beside the conductor
   // update and the next right-hand side; the main stream joins before the table is read
   cudaStream_t st2 = nullptr;
@@ -148,6 +158,7 @@ struct mqs_handle {
   double* alt_hpart = nullptr;
   SpeFac* alt_fac = nullptr;
   double alt_eps = -1.0;
+  int alt_nbh = 0;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -412,7 +423,7 @@ int join_side(mqs_handle* H) {
 // the table's factor again when eps_lin changed since the push (the products stay valid)
 int refactor_spe(mqs_handle* H, cudaStream_t st) {
   if (H->fac_eps == H->opt.eps_lin) return MQS_OK;
-  RK(spe_factor(H->spe_hpart, H->spe_m, H->len, H->opt.eps_lin, H->spe_fac, st));
+  RK(spe_factor(H->spe_hpart, H->spe_m, H->spe_nbh, H->opt.eps_lin, H->spe_fac, st));
   H->fac_eps = H->opt.eps_lin;
   return MQS_OK;
 }
@@ -437,6 +448,7 @@ int history_push(mqs_handle* H, const double* w, const double* lw, cudaStream_t 
                   H->spe_fac, st));
     }
     H->spe_m = mn;
+    H->spe_nbh = spe_hblocks(H->len, mn);      // under the same launch cap as the push
     H->fac_eps = H->opt.eps_lin;
   } else if (mode == MQS_START_POD) {
     const int np = H->opt.pod_snapshots;
@@ -1058,6 +1070,7 @@ int swap_spe(mqs_handle* H) {
   std::swap(H->spe_hpart, H->alt_hpart);
   std::swap(H->spe_fac, H->alt_fac);
   std::swap(H->fac_eps, H->alt_eps);
+  std::swap(H->spe_nbh, H->alt_nbh);
   return MQS_OK;
 }
 
@@ -1113,6 +1126,7 @@ int form_rhs(mqs_handle* H, long m, cudaStream_t st) {
 // the coil type's start vector and solve), history, conductor.
 int enqueue_split_step(mqs_handle* H) {
   const Range range_("mqs step");
+  const LaunchCap cap_(H->ts_cap);
   cudaStream_t st = H->st;
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
   const long m = H->m + 1;
@@ -1164,6 +1178,7 @@ int enqueue_split_step(mqs_handle* H) {
 // step's statistics go to the slot the device step counter names.
 int enqueue_step(mqs_handle* H) {
   const Range range_("mqs step");
+  const LaunchCap cap_(H->ts_cap);
   if (H->opt.rhs_split) return enqueue_split_step(H);
   cudaStream_t st = H->st;
   const long m = H->m + 1;
@@ -2089,20 +2104,35 @@ struct mqs_batch {
   int graph_next = 0;
   bool graph_off = false;
   long graph_steps = 0;     // batch steps replayed from (or captured into) a graph
+  // block shares by unknowns (false) or by unknowns x PCG iterations per step (true)
+  bool by_work = false;
+  std::vector<double> its_avg;   // per handle: mean PCG iterations per step of the last call
+  double last_work = 0.0;        // sum over handles and steps of the last call: unknowns x iterations
 };
 
 namespace {
 
-// block counts proportional to the unknowns, scaled so that they add up to
-// about `scale` blocks per SM
+// block counts proportional to each problem's share of the work, scaled so that they add
+// up to about `scale` blocks per SM.  The share is its unknowns, or (by_work) its unknowns
+// times its PCG iterations per step in the last call: the problems' solves then take
+// about the same time on their blocks, and the batch step is not paced by the problems
+// whose iteration counts are highest.
 int batch_assign(mqs_batch* B) {
   int mx = 0;
   BRK(pcg_max_blocks(&mx));
+  const size_t cnt = B->hs.size();
+  std::vector<double> w(cnt);
   double wsum = 0.0;
-  for (mqs_handle* H : B->hs) wsum += (double)H->n_n;
-  for (mqs_handle* H : B->hs) {
-    long nb = std::lround(B->scale * mx * (double)H->n_n / std::max(wsum, 1.0));
+  for (size_t i = 0; i < cnt; ++i) {
+    const double its = (B->by_work && i < B->its_avg.size() && B->its_avg[i] > 0.0) ? B->its_avg[i] : 1.0;
+    w[i] = (double)B->hs[i]->n_n * its;
+    wsum += w[i];
+  }
+  for (size_t i = 0; i < cnt; ++i) {
+    mqs_handle* H = B->hs[i];
+    long nb = std::lround(B->scale * mx * w[i] / std::max(wsum, 1.0));
     H->nblk = (int)std::min<long>(std::max<long>(nb, 1), mx);
+    H->ts_cap = std::max(2 * H->nblk, 4);    // its tall-skinny kernels: about its share of the SMs
   }
   return MQS_OK;
 }
@@ -2113,6 +2143,7 @@ void batch_release(mqs_batch* B) {
   for (size_t i = 0; i < B->hs.size(); ++i) {
     B->hs[i]->st = B->saved_st[i];
     B->hs[i]->nblk = B->saved_nblk[i];
+    B->hs[i]->ts_cap = 0;
     B->hs[i]->in_batch = false;
   }
   if (B->master) cudaStreamSynchronize(B->master);
@@ -2299,6 +2330,14 @@ int mqs_batch_step(mqs_batch* B, int nsteps, mqs_step_stats* per_step) {
   for (cudaStream_t s : B->streams) BCK(cudaStreamSynchronize(s));
   BCK(cudaEventSynchronize(B->ev1));
   BCK(cudaEventElapsedTime(&B->last_ms, B->ev0, B->ev1));
+  B->its_avg.assign(cnt, 0.0);
+  B->last_work = 0.0;
+  for (int i = 0; i < cnt; ++i) {
+    double its = 0.0;
+    for (int s = 0; s < nsteps; ++s) its += hs[(size_t)i * nsteps + s].iterations;
+    B->its_avg[i] = its / nsteps;
+    B->last_work += its * (double)B->hs[i]->n_n;
+  }
   if (per_step)
     for (int s = 0; s < nsteps; ++s)
       for (int i = 0; i < cnt; ++i) per_step[(size_t)s * cnt + i] = hs[(size_t)i * nsteps + s];
@@ -2317,16 +2356,41 @@ int mqs_batch_last_ms(mqs_batch* B, double* ms) {
 
 int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
   if (!B || trial_steps < 1) return MQS_ERR_ARG;
-  static const double cand[] = {1.0, 2.0, 4.0, 8.0};
-  double best = B->scale, best_ms = 0.0;
-  bool have = false;
-  for (double c : cand) {
-    BRK(mqs_batch_set_scale(B, c));
+  // candidates: scale x (shares by unknowns, by work); each is scored by device time per
+  // unit of PCG work (unknowns x iterations) of its trial, so that the falling iteration
+  // counts of a starting transient do not favour the candidates tried last, and the
+  // candidates run in the order c_0 .. c_7, then c_7 .. c_0 with both scores added
+  struct Cand { double scale; bool by_work; };
+  static const Cand cand[] = {{1.0, false}, {2.0, false}, {4.0, false}, {8.0, false},
+                              {1.0, true},  {2.0, true},  {4.0, true},  {8.0, true}};
+  constexpr int kc = 8;
+  double score[kc] = {};
+  for (int r = 0; r < 2 * kc; ++r) {
+    const Cand& c = cand[r < kc ? r : 2 * kc - 1 - r];
+    B->by_work = c.by_work;
+    BRK(mqs_batch_set_scale(B, c.scale));
     BRK(mqs_batch_step(B, trial_steps, nullptr));
-    if (!have || B->last_ms < best_ms) { best = c; best_ms = B->last_ms; have = true; }
+    score[r < kc ? r : 2 * kc - 1 - r] += B->last_ms / std::max(B->last_work, 1.0);
   }
-  BRK(mqs_batch_set_scale(B, best));
-  if (best_scale) *best_scale = best;
+  int best = 0;
+  for (int c = 1; c < kc; ++c)
+    if (score[c] < score[best]) best = c;
+  B->by_work = cand[best].by_work;
+  BRK(mqs_batch_set_scale(B, cand[best].scale));
+  if (best_scale) *best_scale = cand[best].scale;
+  return MQS_OK;
+}
+
+int mqs_batch_set_weighting(mqs_batch* B, int by_work) {
+  if (!B || by_work < 0 || by_work > 1) return MQS_ERR_ARG;
+  for (cudaStream_t s : B->streams) BCK(cudaStreamSynchronize(s));
+  B->by_work = by_work != 0;
+  return batch_assign(B);
+}
+
+int mqs_batch_get_weighting(const mqs_batch* B, int* by_work) {
+  if (!B || !by_work) return MQS_ERR_ARG;
+  *by_work = B->by_work ? 1 : 0;
   return MQS_OK;
 }
 

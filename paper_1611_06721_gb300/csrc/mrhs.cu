@@ -437,7 +437,9 @@ __device__ __forceinline__ void jacobi_rotation(double app, double aqq, double a
 
 // POD solve: Jacobi eigen-decomposition of G (m x m), truncation, reduced
 // Galerkin system, coefficients z with x0 = X z.
-__global__ void pod_solve_kernel(const double* Gg, const double* Ag, const double* part, int nblk, int m,
+constexpr int kPodThreads = 256;   // pod_solve_kernel's block (its fixed share of the rotation work)
+__global__ void __launch_bounds__(kPodThreads) pod_solve_kernel(const double* Gg, const double* Ag, const double* part,
+                                                               int nblk, int m,
                                  double eps_pod, double* coef, double* sigma_out, SmallOut* out) {
   __shared__ double Mt[kMaxPod * kMaxPod], V[kMaxPod * kMaxPod], Hs[kMaxPod * kMaxPod];
   double* W = Mt;   // Mt is free once the eigenvalues are read; W, then L, reuse it
@@ -480,18 +482,45 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
   // pass over the 2 x 2 blocks of M on and above the block diagonal, from one buffer into the
   // other (Mt / Hs; Hs is free until the Galerkin system), and V <- V J on the rotated pairs'
   // columns: two barriers per round.  Pairs left alone cost no arithmetic.
+  // the round-robin schedule of every round (pair t of round r at sched[r * np + t],
+  // packed p | q << 8, p < q) and this thread's fixed share of the block and V updates,
+  // formed once: the rounds then do no integer division
+  __shared__ unsigned short sched[(kMaxPod - 1) * (kMaxPod / 2)];
+  for (int w = tid; w < (me - 1) * np; w += blockDim.x) {
+    const int round = w / np, t = w - round * np;
+    // circle method: index me-1 meets `round`, the others pair symmetrically
+    const int a = (t == 0) ? me - 1 : (round + t) % (me - 1);
+    const int b = (t == 0) ? round : (round - t + me - 1) % (me - 1);
+    sched[w] = (unsigned short)((a < b ? a : b) | ((a < b ? b : a) << 8));
+  }
+  constexpr int kMItems = (kMaxPod / 2) * (kMaxPod / 2) / kPodThreads + 1;   // blocks (i, j) per thread
+  constexpr int kVItems = kMaxPod * (kMaxPod / 2) / kPodThreads + 1;         // (row, pair) V items per thread
+  int mi[kMItems], mj[kMItems], vr[kVItems], vt[kVItems];
+#pragma unroll
+  for (int u = 0; u < kMItems; ++u) {
+    const int w = tid + kPodThreads * u;
+    const int i = w / np, j = w - (w / np) * np;
+    const bool ok = w < np * np && i <= j;
+    mi[u] = ok ? i : -1;
+    mj[u] = j;
+  }
+#pragma unroll
+  for (int u = 0; u < kVItems; ++u) {
+    const int w = tid + kPodThreads * u;
+    vr[u] = (w < me * np) ? w / np : -1;
+    vt[u] = w - (w / np) * np;
+  }
+  __syncthreads();
   double* cur = Mt;
   double* nxt = Hs;
   for (int sweep = 0; sweep < 40 && me >= 2; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < me - 1; ++round) {
-      for (int t = tid; t < np; t += blockDim.x) {
-        // circle method: index me-1 meets `round`, the others pair symmetrically
-        const int a = (t == 0) ? me - 1 : (round + t) % (me - 1);
-        const int b = (t == 0) ? round : (round - t + me - 1) % (me - 1);
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        pp[t] = p; qq[t] = q;
+      if (tid < np) {
+        const int pq = sched[round * np + tid];
+        const int p = pq & 0xFF, q = pq >> 8;
+        pp[tid] = p; qq[tid] = q;
         const double apq = cur[p * me + q], app = cur[p * me + p], aqq = cur[q * me + q];
         double c = 1.0, s = 0.0;
         const int r = fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq));
@@ -499,13 +528,14 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
           jacobi_rotation(app, aqq, apq, c, s);
           rotated = 1;
         }
-        cs[t] = c; sn[t] = s; rot[t] = r;
+        cs[tid] = c; sn[tid] = s; rot[tid] = r;
       }
       __syncthreads();
       // M' = J^T M J by 2 x 2 blocks (pair i rows, pair j columns, i <= j), mirrored below
-      for (int w = tid; w < np * np; w += blockDim.x) {
-        const int i = w / np, j = w % np;
-        if (i > j) continue;
+#pragma unroll
+      for (int u = 0; u < kMItems; ++u) {
+        const int i = mi[u], j = mj[u];
+        if (i < 0) continue;
         const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
         double b00 = cur[pi * me + pj], b01 = cur[pi * me + qj], b10 = cur[qi * me + pj], b11 = cur[qi * me + qj];
         if (rot[j]) {
@@ -530,9 +560,10 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
         }
       }
       // V <- V J on the rotated pairs
-      for (int w = tid; w < me * np; w += blockDim.x) {
-        const int row = w / np, t = w % np;
-        if (!rot[t]) continue;
+#pragma unroll
+      for (int u = 0; u < kVItems; ++u) {
+        const int row = vr[u], t = vt[u];
+        if (row < 0 || !rot[t]) continue;
         const int p = pp[t], q = qq[t];
         const double c = cs[t], s = sn[t];
         const double vp = V[row * me + p], vq = V[row * me + q];
@@ -548,16 +579,28 @@ __global__ void pod_solve_kernel(const double* Gg, const double* Ag, const doubl
     __syncthreads();
     if (!any) break;
   }
+  // eigenvalues in descending order (ties by index): each thread places one by its rank
+  for (int p = tid; p < m; p += blockDim.x) {
+    const double lp = cur[p * me + p];
+    const double kp = (lp == lp) ? lp : -INFINITY;       // a NaN ranks last: the ranks stay a permutation
+    int rank = 0;
+    for (int q = 0; q < m; ++q) {
+      const double lq = cur[q * me + q];
+      const double kq = (lq == lq) ? lq : -INFINITY;
+      rank += (kq > kp || (kq == kp && q < p)) ? 1 : 0;
+    }
+    lam[p] = lp;
+    order[rank] = p;
+  }
+  __syncthreads();
+  for (int a = tid; a < m; a += blockDim.x) y[a] = sqrt(fmax(lam[order[a]], 0.0));   // sigma_a (y is free here)
+  __syncthreads();
   if (tid == 0) {
-    for (int p = 0; p < m; ++p) { lam[p] = cur[p * me + p]; order[p] = p; }
-    for (int a = 0; a < m; ++a)            // selection sort, descending
-      for (int b = a + 1; b < m; ++b)
-        if (lam[order[b]] > lam[order[a]]) { const int t = order[a]; order[a] = order[b]; order[b] = t; }
-    const double s1 = sqrt(fmax(lam[order[0]], 0.0));
+    const double s1 = y[0];
     int k = 0;
     double sk = 0.0, sall = 0.0;
     for (int a = 0; a < m; ++a) {
-      const double sa = sqrt(fmax(lam[order[a]], 0.0));
+      const double sa = y[a];
       sall += sa;
       if (s1 > 0.0 && sa / s1 >= eps_pod) { ++k; sk += sa; }
       if (sigma_out) sigma_out[a] = sa;
@@ -1101,11 +1144,17 @@ static int ts_max_blocks() {
   return nb;
 }
 
+thread_local int t_launch_cap = 0;
+void set_launch_cap(int cap) { t_launch_cap = cap > 0 ? cap : 0; }
+int launch_cap() { return t_launch_cap; }
+static int capped(int nb) { return (t_launch_cap > 0 && nb > t_launch_cap) ? t_launch_cap : nb; }
+
 // blocks of a tall-skinny pass over len values: at least 8 values per thread, at
-// most two blocks per SM (small problems do not flood the GPU with empty blocks)
+// most two blocks per SM (small problems do not flood the GPU with empty blocks), at
+// most the launch cap
 static int ts_blocks(long long len) {
   const long long want = (len + (long long)kTS * 8 - 1) / ((long long)kTS * 8);
-  return (int)std::min<long long>(std::max<long long>(want, 8), ts_max_blocks());
+  return capped((int)std::min<long long>(std::max<long long>(want, 8), ts_max_blocks()));
 }
 int ts_nblk() { return ts_max_blocks(); }
 
@@ -1118,10 +1167,9 @@ int spe_hblocks(long long len, int m) {
 }
 int spe_gblocks() { return ts_max_blocks(); }
 
-int spe_factor(const double* hpart, int m, long long len, double eps_lin, SpeFac* fac, cudaStream_t st) {
-  if (m <= 0 || m > kMaxSpe) return MQS_ERR_ARG;
-  spe_factor_kernel<<<1, 512, 0, st>>>(reinterpret_cast<const float2*>(hpart), spe_hblocks(len, m), m,
-                                       eps_lin * eps_lin, fac);
+int spe_factor(const double* hpart, int m, int nbh, double eps_lin, SpeFac* fac, cudaStream_t st) {
+  if (m <= 0 || m > kMaxSpe || nbh <= 0) return MQS_ERR_ARG;
+  spe_factor_kernel<<<1, 512, 0, st>>>(reinterpret_cast<const float2*>(hpart), nbh, m, eps_lin * eps_lin, fac);
   return chk();
 }
 
@@ -1130,7 +1178,7 @@ int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const dou
   float2* hp = reinterpret_cast<float2*>(hpart);
   if (m_new <= 8) {
     spe_push_dots_kernel<<<spe_hblocks(len, m_new), kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len, hp);
-    return spe_factor(hpart, m_new, len, eps_lin, fac, st);
+    return spe_factor(hpart, m_new, spe_hblocks(len, m_new), eps_lin, fac, st);
   }
   diff_push_ff_kernel<16><<<ts_blocks(len) * 2, kTS, 0, st>>>(D, LD, w, lw, m_old, m_new, len);
   // Entry (q, p), q >= p, of the Galerkin matrix is D_q . (K D_p): the
@@ -1153,7 +1201,7 @@ int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const dou
   for (int p = 0; p < 8; ++p) { A2.v[p] = LD.v[8 + p < m ? 8 + p : 8]; B2.v[p] = D.v[8 + p < m ? 8 + p : 8]; }
   if (m <= 12) dots_ff_kernel<kTri4><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
   else dots_ff_kernel<kTri><<<nb, kTS, 0, st>>>(A2, B2, m - 8, m - 8, len, hp + (size_t)2 * nb * kTileSlots);
-  return spe_factor(hpart, m, len, eps_lin, fac, st);
+  return spe_factor(hpart, m, nb, eps_lin, fac, st);
 }
 
 int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, const int* sup, int nsup, double* x0,
@@ -1166,7 +1214,7 @@ int spe_x0(const VecSet& D, int m, const double* b, int n, const Box& bbox, cons
   // g: about one edge per thread (most of the region's b vanishes: latency, not bandwidth)
   const long long edges =
       sup ? nsup : 3LL * (bbox.hi[0] - bbox.lo[0]) * (bbox.hi[1] - bbox.lo[1]) * (bbox.hi[2] - bbox.lo[2]);
-  const int nbg = (int)std::min<long long>(std::max<long long>((edges + kTS - 1) / kTS, 1), spe_gblocks());
+  const int nbg = capped((int)std::min<long long>(std::max<long long>((edges + kTS - 1) / kTS, 1), spe_gblocks()));
   float2* gp = reinterpret_cast<float2*>(gpart);
   if (m <= 8) spe_g_kernel<8><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp, fac, coef, out);
   else spe_g_kernel<16><<<nbg, kTS, 0, st>>>(D, b, m, n, bbox, sup, nsup, gp, fac, coef, out);
@@ -1207,7 +1255,7 @@ int pod_x0(const VecSet& X, int m, const double* G, const double* A, const doubl
     for (int q = 0; q < 8; ++q) Ax.v[q] = X.v[8 * t + (q < mb ? q : 0)];
     dots_kernel<kConly><<<nb, kTS, 0, st>>>(Ax, Ax, b, 0, mb, len, part + (size_t)t * nb * kTileSlots);
   }
-  pod_solve_kernel<<<1, 256, 0, st>>>(G, A, part, nb, m, eps_pod, coef, sigma, out);
+  pod_solve_kernel<<<1, kPodThreads, 0, st>>>(G, A, part, nb, m, eps_pod, coef, sigma, out);
   if (x0 && r0 && LX) launch_lincomb_res(X, *LX, coef, m, b, len, x0, r0, nb, st);
   else if (x0) launch_lincomb(X, coef, m, len, x0, nb, st);
   return chk();

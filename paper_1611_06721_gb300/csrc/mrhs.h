@@ -15,6 +15,11 @@ struct MutVecSet { double* v[kMaxVec]; };
 struct SmallOut { int rank; int pad; double info; };
 
 int ts_nblk();
+// Most blocks a tall-skinny launch of the calling host thread may use (0: no limit, up
+// to two per SM): a batch sets each problem's share around its launches so that the
+// problems' start-vector and history kernels run side by side, as their PCG kernels do.
+void set_launch_cap(int cap);
+int launch_cap();
 // partial-sum buffer needed: 5 tiles * ts_nblk() * kTileSlots doubles
 constexpr int kSpeGSlots = 16;      // g = D^T b partials per block
 // Factor of the SPE small system (device memory): rows of the scaled Cholesky factor
@@ -35,9 +40,11 @@ struct SpeFac {
 // factor H = D^T K D into fac (drop rule at eps_lin)
 int spe_push(const MutVecSet& D, const MutVecSet& LD, const double* w, const double* lw, int m_old, int m_new,
              long long len, double* hpart, double eps_lin, SpeFac* fac, cudaStream_t st);
-// the factor again from the partials in hpart (another eps_lin)
-int spe_factor(const double* hpart, int m, long long len, double eps_lin, SpeFac* fac, cudaStream_t st);
-// blocks of the product partials of a table of m columns (their layout in hpart)
+// the factor again from the partials in hpart (another eps_lin); nbh: the block count
+// of the push that wrote them (spe_hblocks at that time)
+int spe_factor(const double* hpart, int m, int nbh, double eps_lin, SpeFac* fac, cudaStream_t st);
+// blocks of the product partials of a table of m columns (their layout in hpart), under
+// the calling thread's launch cap
 int spe_hblocks(long long len, int m);
 // gpart needed: spe_gblocks() * kSpeGSlots 8-byte slots
 int spe_gblocks();

@@ -75,7 +75,10 @@ def test_batch_equals_separate_runs(pkg):
     batch = pkg.Batch(sv, blocks_scale=1.0)
     batch.step(10)
     batch.set_scale(4.0)                         # block counts may change between calls
-    batch.step(steps - 10)
+    batch.step(5)
+    batch.set_weighting(True)                    # shares by unknowns x the last call's iterations
+    assert batch.weighting()
+    batch.step(steps - 15)
     for a, b in zip(alone, sv):
         x, _, _ = a.get_state()
         y, _, _ = b.get_state()
@@ -134,8 +137,10 @@ def test_batch_tune_and_argument_checks(pkg):
     with pytest.raises(pkg.MqsError):
         sv[1].set_blocks(100000)                 # more blocks than SMs
     batch = pkg.Batch(sv)
-    best = batch.tune(2)
-    assert best in (1.0, 2.0, 4.0, 8.0)
+    with pytest.raises(pkg.MqsError):
+        batch.set_weighting(2)
+    best = batch.tune(1)
+    assert best in (1.0, 2.0, 4.0, 8.0) and batch.weighting() in (False, True)
     _, stats = batch.step(3)
     assert all(x.status == 0 for row in stats for x in row)
     sv[0].close()                                # closes the batch first
