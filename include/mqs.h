@@ -403,8 +403,7 @@ int pod_start(mqs_handle* h, const double* b, double* x0, int* k);
  * the first call in a CUDA context (per device, and again after a device
  * reset, which makes a new context) looks the array's address up
  * (cudaGetSymbolAddress) with that device current, under a lock, and keeps it
- * for later calls in that context; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
+ * for later calls in that context.  All calls share the array: calls that overlap on the GPU (other
  * streams, other host threads) race; serialise them.  Every call starts its
  * own scratch state afresh (the barrier counter and error word are cleared).
  * Blocks the host until the solve finishes; info (host) may be NULL.

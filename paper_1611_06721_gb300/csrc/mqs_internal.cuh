@@ -574,12 +574,22 @@ __device__ __forceinline__ bool grid_sum2_max3(double v0, double v1, int m0, int
     const double t = warp_fixed_sum(w ? p1 : p0, nb);
     if (lane == 0) gs[w] = t;
   } else if (w == 2) {
+    // the loads issued together (as in warp_fixed_sum), not one L2 round trip per 32 blocks
     int c0 = 0, c1 = 0, c2 = 0;
-    for (int q = lane; q < nb; q += 32) {
-      const long long pk = p2[q];
-      c0 = max(c0, (int)(pk & 0xFFFF));
-      c1 = max(c1, (int)((pk >> 16) & 0xFFFF));
-      c2 = max(c2, (int)((pk >> 32) & 0xFFFF));
+    long long pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pk[q] = (lane + 32 * q < nb) ? p2[lane + 32 * q] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      c0 = max(c0, (int)(pk[q] & 0xFFFF));
+      c1 = max(c1, (int)((pk[q] >> 16) & 0xFFFF));
+      c2 = max(c2, (int)((pk[q] >> 32) & 0xFFFF));
+    }
+    for (int q = lane + 256; q < nb; q += 32) {
+      const long long v = p2[q];
+      c0 = max(c0, (int)(v & 0xFFFF));
+      c1 = max(c1, (int)((v >> 16) & 0xFFFF));
+      c2 = max(c2, (int)((v >> 32) & 0xFFFF));
     }
     c0 = __reduce_max_sync(0xffffffffu, c0);
     c1 = __reduce_max_sync(0xffffffffu, c1);

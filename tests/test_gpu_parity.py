@@ -434,23 +434,25 @@ def test_bench_configuration_against_the_oracle(pkg):
     dt = g64["dt"]
     steps = 30
     ref = O.run_explicit_euler(d, dt, steps, start_mode=START_SPE, spe_depth=8, tol=1e-10, eps_lin=1e-10)
-    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, eps_lin=1e-10)
-    # the benchmark's own step comes from the GPU power method: the same lambda_max
-    lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=2000)
-    assert lam == pytest.approx(g64["lambda_max"], rel=1e-6)
-    s.set_dt(dt)
-    for _ in range(steps):
-        s.step_enqueue(1)
-    rc, stats = s.step_finish(steps)
-    assert rc == 0
-    a_c, _, m = s.get_state()
-    assert m == steps
-    assert rel(a_c, ref.a_c) < 1e-8
-    w = layout_to_oracle(p.N, s.get_solution())[d.n_idx]
-    assert rel(d.K_cn @ w, d.K_cn @ ref.w) < 1e-8
-    its = np.array([st.iterations for st in stats])
-    assert np.abs(its - ref.iterations).max() <= 3, (its.tolist(), ref.iterations.tolist())
-    s.close()
+    # pcg_variant 1 (one reduction per iteration, the benchmark's kernel) and 0
+    for variant in (1, 0):
+        s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, eps_lin=1e-10, pcg_variant=variant)
+        # the benchmark's own step comes from the GPU power method: the same lambda_max
+        lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=2000)
+        assert lam == pytest.approx(g64["lambda_max"], rel=1e-6)
+        s.set_dt(dt)
+        for _ in range(steps):
+            s.step_enqueue(1)
+        rc, stats = s.step_finish(steps)
+        assert rc == 0
+        a_c, _, m = s.get_state()
+        assert m == steps
+        assert rel(a_c, ref.a_c) < 1e-8, variant
+        w = layout_to_oracle(p.N, s.get_solution())[d.n_idx]
+        assert rel(d.K_cn @ w, d.K_cn @ ref.w) < 1e-8, variant
+        its = np.array([st.iterations for st in stats])
+        assert np.abs(its - ref.iterations).max() <= 3, (variant, its.tolist(), ref.iterations.tolist())
+        s.close()
 
 
 # ---- other readings of the step and the paper-sized grid ---------------------------------------
