@@ -624,9 +624,9 @@ def size_sweep(sizes):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for n in sizes:
         p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
-        for prec, var in ((0, 1), (1, 1), (1, 2)):
+        for prec, var, groups in ((0, 1, 0), (0, 1, 3), (1, 1, 0), (1, 2, 0)):
             s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
-                                                             pcg_variant=var))
+                                                             pcg_variant=var, tile_groups=groups))
             stream = torch.cuda.Stream(device=dev)
             s.set_stream(stream.cuda_stream)
             with torch.cuda.stream(stream):
@@ -650,7 +650,7 @@ def size_sweep(sizes):
             gbs = BYTES_PER_ITER[prec] * s.n_n / (us_it * 1e-6) / 1e9
             print(json.dumps({"sweep": "zero-start solve", "workload": workload_name(p), "grid": n,
                               "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
-                              "pcg_variant": var,
+                              "pcg_variant": var, "tile_groups": groups or 2,
                               "n_unknowns": int(s.n_n), "iterations": int(its), "relres": info.relres,
                               "status": int(info.status), "ms_per_solve": ms, "us_per_iteration": us_it,
                               "algorithmic_GBps": gbs, "hbm_peak_GBps": peaks.get("hbm_gbs"),
@@ -701,6 +701,9 @@ def run_batch(args):
     batch = pkg.Batch(solvers)
     best = batch.tune(max(args.warmup // 16, 1))     # 16 trials (8 candidates, twice)
     by_work = batch.weighting()
+    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
+                                                      for s_ in solvers]   # PCG kernel form per grid size
+    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1])} for p, v in zip(probs, forms)}
     depth_by_n = None
     if args.tune_depth:
         chosen = batch.tune_depth(max(args.warmup // 4, 5), depths=(4, 8, 16))
@@ -749,6 +752,7 @@ def run_batch(args):
                        "n_unknowns": int(sum(s.n_n for s in solvers)),
                        "precision": "FP64" if args.precision == 0 else "FP32 inner CG in FP64 refinement",
                        "blocks_scale": best, "block_shares": "unknowns x iterations" if by_work else "unknowns",
+                       "pcg_form_by_N": form_by_n,
                        "l2": "working set larger than L2 (no flush)",
                        "graph_steps": graph_steps,
                        "parallelism": "1 GPU, instances on 32 streams"},
@@ -795,6 +799,9 @@ def batch_sub(args, dev):
     batch = pkg.Batch(solvers)
     scale = batch.tune(trial)                       # 16 x trial warm-up steps (8 candidates, twice)
     by_work = batch.weighting()
+    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
+                                                      for s_ in solvers]   # PCG kernel form per grid size
+    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1])} for p, v in zip(probs, forms)}
     extra = max(args.batch_sub_warmup - 16 * trial, 0)
     if extra:
         batch.step(extra)
@@ -829,6 +836,7 @@ def batch_sub(args, dev):
             "steps": args.batch_sub_steps, "first_step": warm + 1, "ms": ms,
             "precision": "FP32 inner CG in FP64 refinement (FP64 true residual 1e-10 per solve)",
             "blocks_scale": scale, "block_shares": "unknowns x iterations" if by_work else "unknowns",
+            "pcg_form_by_N": form_by_n,
             "inner_iters_per_step": float(its.mean()), "failed_steps": failed,
             "single_instance_fp64": {"value": single, "unit": "instance-steps/s",
                                      "iters_per_step": float(np.mean(its64)),
@@ -1005,6 +1013,9 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
     ap.add_argument("--sweep", type=str, default="",
                     help="comma-separated grid sizes: time zero-start solves at each (roofline evidence)")
+    ap.add_argument("--no-tune-pcg", dest="tune_pcg", action="store_false",
+                    help="batched modes: keep --pcg-variant instead of the kernel-form tuner's choice per N")
+    ap.add_argument("--tune-pcg-trials", type=int, default=3, help="timed trial solves per kernel form")
     ap.add_argument("--block-sweep", type=str, default="",
                     help="comma-separated grid sizes: PCG time per iteration against the block count")
     ap.add_argument("--batch-sub", type=int, default=64,

@@ -189,6 +189,13 @@ typedef struct {
                              steps (|1 - dt lambda| <= 1 for every mode) shrink the
                              alternating part instead.  0: 8 steps; < 0: off (the
                              non-finite test stays). */
+    int    tile_groups;   /* stencil groups per block of the one-reduction FP64
+                             pass (precision 0, pcg_variant 1): each group marches
+                             one 32 x 4 tile of positions at a time.  0 or 2
+                             (default): 320-thread blocks; 3: 480-thread blocks
+                             (more warps to hide latency, fewer registers per
+                             thread).  mqs_tune_pcg chooses it with the form.
+                             Other precisions and forms use 2. */
 } mqs_options;
 
 typedef struct {
@@ -247,10 +254,13 @@ int mqs_layout(const mqs_handle* h, mqs_layout_info* info);
 int mqs_set_dt(mqs_handle* h, double dt);
 int mqs_get_dt(const mqs_handle* h, double* dt, double* lambda_max);
 
-/* mqs_set_options: replaces tol, maxit, start_mode, spe_depth,
- * pod_snapshots, eps_pod, eps_lin, rhs_time (dt is kept unless > 0).
- * Changing start_mode, spe_depth or pod_snapshots clears the history. */
+/* mqs_set_options: replaces every option (dt is kept unless > 0).
+ * Changing start_mode, spe_depth, pod_snapshots, cspe_period or rhs_split
+ * clears the history.
+ * mqs_get_options: the handle's current options (after a tuner's choice);
+ * opts->dt receives the current step.  Errors: MQS_ERR_ARG (NULL). */
 int mqs_set_options(mqs_handle* h, const mqs_options* opts);
+int mqs_get_options(const mqs_handle* h, mqs_options* opts);
 
 /* mqs_lambda_max: eq. (CFL) - power method on M_c^-1/2 K_S(0) M_c^-1/2,
  * Rayleigh quotient, every application of K_S using one PCG solve of K_n
@@ -512,6 +522,10 @@ int mqs_loss(mqs_handle* h, int nsteps, double* objective);
  * keeps the best (its scale in *best_scale, nullable; the weighting through
  * mqs_batch_get_weighting).
  * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts.
+ * mqs_batch_tune_pcg: mqs_tune_pcg on the first handle of every group of
+ * handles with the same grid size and precision (on its batch stream and its
+ * block share), the winner set on the whole group; chosen (host, nullable)
+ * receives every handle's pcg_variant in the batch's order.
  * mqs_batch_set_weighting: by_work 0 (shares by unknowns, the default) or 1
  * (by unknowns x the last call's iterations per step) and reassigns the
  * counts; mqs_batch_get_weighting reads it back.  MQS_ERR_ARG otherwise.
@@ -528,6 +542,21 @@ int mqs_loss(mqs_handle* h, int nsteps, double* objective);
  * handle, in the batch's order.  Other handles keep their options.  Errors:
  * MQS_ERR_ARG, or the status of a failing step. */
 int mqs_set_blocks(mqs_handle* h, int nblk);
+/* mqs_tune_pcg: the PCG kernel form for this handle's grid, precision and block
+ * count.  The candidates compute the same iterates and differ in their tiles'
+ * halo depth, staging and traffic: precision 0, pcg_variant 0 (two reductions
+ * per iteration) and 1 (one fused pass carrying x, p, r, w, s) on 2 and on 3
+ * tile groups per block (tile_groups); precision 1,
+ * pcg_variant 0, 1 (one reduction, five carried vectors) and 2 (three carried
+ * vectors, a two-deep halo staged by cp.async); precision 2 has one form.
+ * Each candidate solves K_n x = b from x = 0, b the coil's pattern at unit
+ * current with the conductors at rest, trials + 1 times on the handle's stream
+ * and block count; the first solve is untimed and the fastest median (CUDA
+ * events) sets opts.pcg_variant (and tile_groups).  The state, the start-vector history and the
+ * step's right-hand side are untouched.  chosen (host, nullable) receives the
+ * variant.  Blocks the host.  Errors: MQS_ERR_ARG (trials < 1), a failing trial
+ * solve's status (the previous variant is kept), MQS_ERR_CUDA. */
+int mqs_tune_pcg(mqs_handle* h, int trials, int* chosen);
 typedef struct mqs_batch mqs_batch;
 int mqs_batch_create(mqs_handle* const* handles, int count, double blocks_scale,
                      mqs_batch** out);
@@ -536,6 +565,7 @@ int mqs_batch_step(mqs_batch* b, int nsteps, mqs_step_stats* per_step);
 int mqs_batch_last_ms(mqs_batch* b, double* ms);
 int mqs_batch_tune(mqs_batch* b, int trial_steps, double* best_scale);
 int mqs_batch_set_weighting(mqs_batch* b, int by_work);
+int mqs_batch_tune_pcg(mqs_batch* b, int trials, int* chosen);
 int mqs_batch_get_weighting(const mqs_batch* b, int* by_work);
 int mqs_batch_tune_depth(mqs_batch* b, int trial_steps, const int* depths, int ndepths,
                          int* chosen);

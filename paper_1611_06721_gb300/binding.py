@@ -35,7 +35,8 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_set_blocks", "mqs_batch_create", "mqs_batch_set_scale", "mqs_batch_step", "mqs_batch_last_ms",
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
            "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth",
-           "mqs_debug_check", "mqs_batch_set_weighting", "mqs_batch_get_weighting")
+           "mqs_debug_check", "mqs_batch_set_weighting", "mqs_batch_get_weighting", "mqs_tune_pcg",
+           "mqs_batch_tune_pcg", "mqs_get_options")
 
 
 class Grid(C.Structure):
@@ -57,7 +58,7 @@ class Options(C.Structure):
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int), ("graph", C.c_int),
-                ("cfl_factor", C.c_double), ("monitor_steps", C.c_int)]
+                ("cfl_factor", C.c_double), ("monitor_steps", C.c_int), ("tile_groups", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -156,6 +157,9 @@ def load():
         "mqs_debug_check": ([H, P(DebugReport)], I),
         "mqs_batch_set_weighting": ([V, I], I),
         "mqs_batch_get_weighting": ([V, P(I)], I),
+        "mqs_tune_pcg": ([H, I, P(I)], I),
+        "mqs_batch_tune_pcg": ([V, I, P(I)], I),
+        "mqs_get_options": ([H, P(Options)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -232,12 +236,13 @@ class SolverOptions:
     graph: int = 1          # steady-state SPE steps from CUDA graphs (bitwise the same results)
     cfl_factor: float = 0.0  # > 0 with dt <= 0: setup sets dt = cfl_factor * 2 / lambda_max (eq. (CFL))
     monitor_steps: int = 0   # instability monitor window (0: 8 steps; < 0: finiteness test only)
+    tile_groups: int = 0     # stencil groups per block of the FP64 one-reduction pass (0/2 or 3)
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
                        self.inner_tol, self.cspe_period, self.rhs_split, self.graph, self.cfl_factor,
-                       self.monitor_steps)
+                       self.monitor_steps, self.tile_groups)
 
 
 class Solver:
@@ -390,6 +395,19 @@ class Solver:
         v = C.c_double()
         self._check(self.lib.mqs_loss(self.h, nsteps, C.byref(v)))
         return v.value
+
+    def tune_pcg(self, trials=2):
+        """The fastest PCG kernel form for this grid, precision and block count
+        (mqs_tune_pcg); sets it and returns (pcg_variant, tile_groups)."""
+        v = C.c_int()
+        self._check(self.lib.mqs_tune_pcg(self.h, trials, C.byref(v)))
+        self._sync_options()
+        return self.options.pcg_variant, self.options.tile_groups
+
+    def _sync_options(self):
+        o = Options()
+        self._check(self.lib.mqs_get_options(self.h, C.byref(o)))
+        self.options = replace(self.options, pcg_variant=o.pcg_variant, tile_groups=o.tile_groups)
 
     def set_blocks(self, nblk):
         """Persistent blocks of this handle's PCG kernels (0 = one per SM)."""
@@ -582,6 +600,15 @@ class Batch:
         v = C.c_double()
         self._check(self.lib.mqs_batch_tune(self.b, trial_steps, C.byref(v)))
         return v.value
+
+    def tune_pcg(self, trials=2):
+        """mqs_batch_tune_pcg: the PCG kernel form per (grid size, precision) group;
+        returns every solver's (pcg_variant, tile_groups)."""
+        out = (C.c_int * len(self.solvers))()
+        self._check(self.lib.mqs_batch_tune_pcg(self.b, trials, out))
+        for sv in self.solvers:
+            sv._sync_options()
+        return [(sv.options.pcg_variant, sv.options.tile_groups) for sv in self.solvers]
 
     def set_weighting(self, by_work):
         """Block shares by unknowns (False) or unknowns x last iterations (True)."""

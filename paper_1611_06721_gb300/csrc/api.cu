@@ -371,7 +371,7 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
   if (H->opt.pcg_variant >= 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
-                            H->nblk, st, init, halt);
+                            H->nblk, st, init, halt, H->opt.tile_groups);
   }
   return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
                     st, init, halt);
@@ -586,6 +586,10 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (!(o->eps_pod > 0.0) || !(o->eps_lin >= 0.0)) { why = "eps_pod must be positive, eps_lin non-negative"; return MQS_ERR_ARG; }
   if (o->rhs_time != 0 && o->rhs_time != 1) { why = "rhs_time must be 0 or 1"; return MQS_ERR_ARG; }
   if (o->pcg_variant < 0 || o->pcg_variant > 2) { why = "pcg_variant must be 0, 1 or 2"; return MQS_ERR_ARG; }
+  if (o->tile_groups != 0 && o->tile_groups != 2 && o->tile_groups != 3) {
+    why = "tile_groups must be 0, 2 or 3";
+    return MQS_ERR_ARG;
+  }
   if (o->precision < 0 || o->precision > 2) { why = "precision must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (!std::isfinite(o->inner_tol) || o->inner_tol >= 1.0) { why = "inner_tol must be < 1"; return MQS_ERR_ARG; }
   if (o->dt < 0.0 || !std::isfinite(o->dt)) { why = "dt must be >= 0"; return MQS_ERR_ARG; }
@@ -1050,6 +1054,13 @@ int mqs_set_options(mqs_handle* H, const mqs_options* o) {
   H->opt = *o;
   H->dt = (o->dt > 0.0) ? o->dt : dt;
   if (reset) clear_history(H);
+  return MQS_OK;
+}
+
+int mqs_get_options(const mqs_handle* H, mqs_options* o) {
+  if (!H || !o) return MQS_ERR_ARG;
+  *o = H->opt;
+  o->dt = H->dt;
   return MQS_OK;
 }
 
@@ -2067,6 +2078,92 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
   return MQS_OK;
 }
 
+// Kernel-form tuner: the PCG forms that compute the same iterates (precision 0: the
+// two-reduction kernel and the one-reduction fused pass; precision 1: the FP32 inner CG
+// with two reductions, with one reduction carrying five vectors, and with one reduction
+// carrying three vectors over a two-deep halo) differ in their tiles' halo depth, staging
+// and traffic, and which is fastest depends on the grid size and the block count.  Each
+// candidate solves K_n x = b_coil (the coil's pattern, unit current, the conductors at
+// rest) from zero, trials + 1 times on the handle's stream and block count (the first
+// untimed); the fastest median keeps its pcg_variant.  The state, the start-vector
+// history and the step's right-hand side are untouched.
+int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
+  if (!H || trials < 1) return MQS_ERR_ARG;
+  const Range range_("mqs_tune_pcg");
+  // candidates (pcg_variant, tile_groups)
+  int cand[3][2], nc = 0;
+  if (H->opt.precision == 0) {
+    cand[0][0] = 0; cand[0][1] = 0;
+    cand[1][0] = 1; cand[1][1] = 2;
+    cand[2][0] = 1; cand[2][1] = 3;
+    nc = 3;
+  } else if (H->opt.precision == 1) {
+    for (int v = 0; v < 3; ++v) { cand[v][0] = v; cand[v][1] = 0; }
+    nc = 3;
+  } else {
+    cand[0][0] = H->opt.pcg_variant; cand[0][1] = 0;    // one float-float inner form
+    nc = 1;
+  }
+  cudaStream_t st = H->st;
+  RK(join_side(H));
+  const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
+  const CoilDrive unit{H->h / H->nu0, 1.0, 0.0, 1.0, 50.0, 1};   // ramp waveform at t = 50 tau: i = 1
+  CK(cudaMemsetAsync(H->tmp, 0, sizeof(double) * H->len, st));
+  CK(cudaMemsetAsync(H->bu, 0, sizeof(double) * H->len, st));
+  RK(launch_rhs(H->dg, H->tmp, H->bu, unit, coil, H->sup, H->nsup, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(H, MQS_ERR_CUDA, "mqs_tune_pcg: event creation failed");
+  }
+  const int saved = H->opt.pcg_variant, saved_groups = H->opt.tile_groups;
+  int best = saved, best_groups = saved_groups, rc = MQS_OK;
+  float best_ms = 0.f;
+  for (int c = 0; c < nc && rc == MQS_OK; ++c) {
+    H->opt.pcg_variant = cand[c][0];
+    H->opt.tile_groups = cand[c][1];
+    std::vector<float> ms;
+    for (int r = 0; r <= trials && rc == MQS_OK; ++r) {
+      if (cudaMemsetAsync(H->derr, 0, sizeof(int), st) != cudaSuccess ||
+          cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st) != cudaSuccess ||
+          cudaEventRecord(e0, st) != cudaSuccess) {
+        rc = fail(H, MQS_ERR_CUDA, "mqs_tune_pcg: enqueue failed");
+        break;
+      }
+      rc = pcg_launch(H, H->bu, H->xu, H->opt.tol, H->opt.maxit, st, 2);
+      if (rc != MQS_OK) break;
+      PcgResult pr{};
+      int derr = 0;
+      if (cudaEventRecord(e1, st) != cudaSuccess ||
+          cudaMemcpyAsync(&pr, H->pres, sizeof pr, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(&derr, H->derr, sizeof derr, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = fail(H, MQS_ERR_CUDA, "mqs_tune_pcg: trial solve failed");
+        break;
+      }
+      if (derr != 0 || pr.status != MQS_OK) {
+        rc = fail(H, derr ? derr : pr.status, "mqs_tune_pcg: trial solve did not converge");
+        break;
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) ms.push_back(t);
+    }
+    if (rc != MQS_OK) break;
+    std::sort(ms.begin(), ms.end());
+    const float med = ms[ms.size() / 2];
+    if (c == 0 || med < best_ms) { best = cand[c][0]; best_groups = cand[c][1]; best_ms = med; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  H->opt.pcg_variant = (rc == MQS_OK) ? best : saved;
+  H->opt.tile_groups = (rc == MQS_OK) ? best_groups : saved_groups;
+  H->lx_valid = false;                   // lx held the trial solves' images
+  if (chosen) *chosen = H->opt.pcg_variant;
+  return rc;
+}
+
 // status-only variants of CK / RK for calls that belong to no single handle
 #define BCK(call)                                         \
   do {                                                    \
@@ -2378,6 +2475,31 @@ int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
   B->by_work = cand[best].by_work;
   BRK(mqs_batch_set_scale(B, cand[best].scale));
   if (best_scale) *best_scale = cand[best].scale;
+  return MQS_OK;
+}
+
+int mqs_batch_tune_pcg(mqs_batch* B, int trials, int* chosen) {
+  if (!B || trials < 1) return MQS_ERR_ARG;
+  for (cudaStream_t s : B->streams) BCK(cudaStreamSynchronize(s));
+  const size_t cnt = B->hs.size();
+  std::vector<int> done(cnt, 0);
+  for (size_t i = 0; i < cnt; ++i) {
+    if (done[i]) continue;
+    mqs_handle* H = B->hs[i];
+    int v = 0;
+    RK(mqs_tune_pcg(H, trials, &v));      // on its batch stream and its share of the blocks
+    for (size_t j = i + 1; j < cnt; ++j) {
+      mqs_handle* G = B->hs[j];
+      if (!done[j] && G->n == H->n && G->opt.precision == H->opt.precision) {
+        G->opt.pcg_variant = v;
+        G->opt.tile_groups = H->opt.tile_groups;
+        done[j] = 1;
+      }
+    }
+    done[i] = 1;
+  }
+  if (chosen)
+    for (size_t i = 0; i < cnt; ++i) chosen[i] = B->hs[i]->opt.pcg_variant;
   return MQS_OK;
 }
 

@@ -205,9 +205,9 @@ struct SweepGroupSmemT {
   T hz[2][kTY];                         // x halo: bz, by at (i0 - 1, j0 + row)
   T hy[2][kTY];
 };
-template <class T>
+template <class T, int G = kGroups>
 struct SweepSmemT {
-  SweepGroupSmemT<T> g[kGroups];
+  SweepGroupSmemT<T> g[G];
 };
 using SweepSmem = SweepSmemT<double>;
 
@@ -232,10 +232,11 @@ __device__ __forceinline__ void group_sync(int grp) {
 // Values are loaded as M (= T by default) and turned into T by cv (the identity by
 // default; the FP64 PCG's direction sweep loads FP64 and runs the stencil in 64-bit
 // fixed point, exactly, on the integer pipes).
-// Must be called by all kBlock threads of the block.
-template <class T, class Epi, class M, class Cv = LoadAs>
+// Must be called by all G x kGroupWarps warps of the block (G groups; kGroups unless the
+// caller's shared memory says otherwise).
+template <class T, class Epi, class M, class Cv = LoadAs, int G = kGroups>
 __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, int part, int nparts,
-                        SweepSmemT<T>& sm, Epi& epi, Cv cv = Cv()) {
+                        SweepSmemT<T, G>& sm, Epi& epi, Cv cv = Cv()) {
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
@@ -245,7 +246,7 @@ __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, 
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
   const long long ntiles = (long long)ntx * nty * nz;
-  const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
+  const long long gp = (long long)part * G + grp, gn = (long long)nparts * G;
   long long u = ntiles * gp / gn;
   const long long u1 = ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);

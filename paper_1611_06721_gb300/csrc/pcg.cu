@@ -300,9 +300,12 @@ __device__ __forceinline__ double fx_below(int e) { return e == 0 ? 0x1.0p-1022 
 //   max |r_{i+2}| <= max |r_{i+1}| + |alpha'| (max |w_{i+1}| + |beta'| max |s_i|).
 // Same iterates as the two-reduction kernel in exact arithmetic; convergence is
 // confirmed on the true residual as there.
-__global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
+// G: stencil groups per block (the tile shape of the sweeps: G tiles of 32 x kTY positions
+// in flight per block, kGroupWarps warps each).
+template <int G>
+__global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
   if (pcg_halted(a.halt, a.out)) return;
-  __shared__ union { SweepSmem s; FusedFxSmemBlock f; } sm;
+  __shared__ union { SweepSmemT<double, G> s; FusedFxSmemBlockG<G> f; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
   __shared__ int gm[3];
@@ -429,9 +432,24 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_fused_kernel(PcgA
   if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{it, status, relres, start_rel};
 }
 
+static int fused_groups_ok(int groups) {
+  if (groups == kGroups) return MQS_OK;
+  if (groups != 3) return MQS_ERR_ARG;
+  // the three-group block (480 threads) must fit once per SM beside nothing else
+  static int occ = -1;
+  if (occ < 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_fused_kernel<3>, 32 * kGroupWarps * 3, 0) !=
+        cudaSuccess)
+      return MQS_ERR_CUDA;
+    occ = o;
+  }
+  return occ >= kPcgBlocksPerSM ? MQS_OK : MQS_ERR_ARG;
+}
+
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
-                     int nblk, cudaStream_t st, int init, const int* halt) {
+                     int nblk, cudaStream_t st, int init, const int* halt, int groups) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -444,7 +462,13 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
   FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1};
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a, &fb};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel, dim3(nblk), dim3(kBlock), args, 0, st);
+  if (groups == 0) groups = kGroups;
+  const int gok = fused_groups_ok(groups);
+  if (gok != MQS_OK) return gok;
+  cudaError_t e = (groups == 3)
+      ? cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<3>, dim3(nblk), dim3(32 * kGroupWarps * 3), args, 0,
+                                    st)
+      : cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<kGroups>, dim3(nblk), dim3(kBlock), args, 0, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -318,13 +318,16 @@ struct FusedFxSmem {
   long long hz[2][kTY];
   long long hy[2][kTY];
 };
-struct FusedFxSmemBlock { FusedFxSmem g[kGroups]; };
+template <int G = kGroups>
+struct FusedFxSmemBlockG { FusedFxSmem g[G]; };
+using FusedFxSmemBlock = FusedFxSmemBlockG<>;
 
 // biased FP64 exponent field of v (|v| < 2^(e - 1022) for e > 0; 0 for zero and subnormals)
 __device__ __forceinline__ int fx_expo(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
 
+template <int G>
 __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, const Box& box, int part, int nparts,
-                               FusedFxSmemBlock& smb, double& gamma, double& delta, int& mer, int& mew,
+                               FusedFxSmemBlockG<G>& smb, double& gamma, double& delta, int& mer, int& mew,
                                int& mes) {
   const FusedVecs& v = fv.v;
   const int shi = fv.sh_in, sho = fv.sh_out;
@@ -337,7 +340,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
   const long long ntiles = (long long)ntx * nty * nz;
-  const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
+  const long long gp = (long long)part * G + grp, gn = (long long)nparts * G;
   long long u = ntiles * gp / gn;
   const long long u1 = ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);

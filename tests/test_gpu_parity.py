@@ -498,13 +498,14 @@ def test_paper_sized_grid(pkg):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_both_pcg_variants_match_the_oracle(pkg, variant):
+@pytest.mark.parametrize("variant,groups", [(0, 0), (1, 2), (1, 3)])
+def test_both_pcg_variants_match_the_oracle(pkg, variant, groups):
+    # groups: stencil tile groups per block of the one-reduction pass (3: 480-thread blocks)
     p = W.scaled_nonlinear(24, amplitude=5e4)
     d = O.Discretization(p)
     dt = O.dt_gershgorin(d)
     ref = O.run_explicit_euler(d, dt, 20, start_mode=START_SPE, spe_depth=8, tol=1e-10)
-    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, pcg_variant=variant)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, pcg_variant=variant, tile_groups=groups)
     stats = s.mqs_step(20)
     a_c, _, _ = s.get_state()
     assert rel(a_c, ref.a_c) < 1e-8
@@ -515,6 +516,33 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant):
     res = O.pcg_jacobi(d.K_n, b_o[d.n_idx], None, d.D, tol=1e-10)
     assert info.status == 0 and abs(info.iterations - res.iterations) <= 3
     assert rel(d.K_cn @ layout_to_oracle(p.N, x)[d.n_idx], d.K_cn @ res.x) < 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("precision,choices", [(0, ((0, 0), (1, 2), (1, 3))), (1, ((0, 0), (1, 0), (2, 0)))])
+def test_pcg_form_tuner_keeps_the_state_and_the_trajectory(pkg, precision, choices):
+    # mqs_tune_pcg times the kernel forms on trial solves between steps: the state, the
+    # step counter and the start-vector history stay as they were, and the steps after it
+    # (in the chosen form) continue the oracle's trajectory
+    p = W.scaled_nonlinear(24, amplitude=5e4)
+    d = O.Discretization(p)
+    dt = O.dt_gershgorin(d)
+    ref = O.run_explicit_euler(d, dt, 16, start_mode=START_SPE, spe_depth=8, tol=1e-10)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, precision=precision)
+    s.mqs_step(8)
+    a0, t0, m0 = s.get_state()
+    v = s.tune_pcg(2)
+    assert v in choices and (s.options.pcg_variant, s.options.tile_groups) == v
+    a1, t1, m1 = s.get_state()
+    assert np.array_equal(a0, a1) and (t0, m0) == (t1, m1)
+    stats = s.mqs_step(8)
+    a_c, _, m = s.get_state()
+    assert m == 16 and all(x.status == 0 for x in stats)
+    assert rel(a_c, ref.a_c) < 1e-8
+    # the SPE history survived the trial solves: the start vectors still cut the iterations
+    assert np.mean([x.iterations for x in stats]) < 0.7 * np.mean(ref.iterations[:2])
+    with pytest.raises(pkg.MqsError):
+        s.tune_pcg(0)
     s.close()
 
 
