@@ -52,10 +52,10 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
 
 }  // namespace
 
-__global__ void adj_mu_kernel(CondGeom cg, const double* F, AdjBufs ab, double dt) {
+__global__ void adj_mu_kernel(CondGeom cg, const double* F, AdjBufs ab, double dt, long long n3) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cg.n_c; q += gridDim.x * blockDim.x) {
     const double f = F[q], l = ab.lam[q], im = cg.inv_mc[q];
-    MQS_STC(ab.mu_full, cg.c_idx[q], 3 * cg.n3, 502, dt * im * fma(2.0, f, -l));
+    MQS_STC(ab.mu_full, cg.c_idx[q], 3 * n3, 502, dt * im * fma(2.0, f, -l));
     ab.gmc[q] += dt * f * (l - f) * im * im;
   }
 }
@@ -236,8 +236,8 @@ static long long cell_count(const CondGeom& cg) {
   return (long long)(cg.chi[0] - cg.clo[0]) * (cg.chi[1] - cg.clo[1]) * (cg.chi[2] - cg.clo[2]);
 }
 
-int launch_adj_mu(const CondGeom& cg, const double* F, const AdjBufs& ab, double dt, cudaStream_t st) {
-  adj_mu_kernel<<<blocks_for(cg.n_c), 256, 0, st>>>(cg, F, ab, dt);
+int launch_adj_mu(const CondGeom& cg, const double* F, const AdjBufs& ab, double dt, long long n3, cudaStream_t st) {
+  adj_mu_kernel<<<blocks_for(cg.n_c), 256, 0, st>>>(cg, F, ab, dt, n3);
   return ok();
 }
 

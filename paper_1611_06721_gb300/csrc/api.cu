@@ -814,7 +814,6 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   H->cg.brauer = H->brauer;
   H->cg.nu = H->nu;
   H->cg.nu0 = H->nu0; H->cg.k1 = H->k1; H->cg.k2 = H->k2; H->cg.k3 = H->k3; H->cg.h = H->h;
-  H->cg.n3 = n3;
   CK(cudaDeviceSynchronize());
   return MQS_OK;
 }
@@ -922,7 +921,7 @@ int power_method(mqs_handle* H, const double* v0, double pcg_tol, double rtol, i
   for (it = 1; it <= maxit; ++it) {
     // u = M_c^-1/2 v scattered to the layout; b = -(L u)|_n, so w = -K_n^+ K_cn^T u
     power_prep_kernel<<<8, 256, 0, st>>>((int)H->n_c, H->cvec, H->isqmc, H->cvec2);
-    RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, st));
+    RK(launch_scatter_c(H->cg, H->cvec2, H->tmp, 1.0, H->dg.g.n3, st));
     RK(launch_rhs(H->dg, H->tmp, H->bu, nodrv, coil, H->sup, H->nsup, st));
     RK(run_pcg(H, H->bu, H->xu, pcg_tol, 100000, st));
     // K_S u = (K(0) [u; w])_c ; z = M_c^-1/2 K_S u ; lambda = v.z ; v = z/|z|
@@ -1613,8 +1612,8 @@ int ensure_ckpt(mqs_handle* H, long count) {
 int adjoint_reverse_step(mqs_handle* H, long mabs, const double* A, const double* F, int slot) {
   cudaStream_t st = H->st;
   const CoilGeom coil{H->coil.plane_k, H->coil.i0, H->coil.j0, H->coil.i1, H->coil.j1};
-  RK(launch_adj_mu(H->cg, F, H->adj, H->dt, st));
-  RK(launch_scatter_c(H->cg, A, H->adj.ap_full, 1.0, st));
+  RK(launch_adj_mu(H->cg, F, H->adj, H->dt, H->dg.g.n3, st));
+  RK(launch_scatter_c(H->cg, A, H->adj.ap_full, 1.0, H->dg.g.n3, st));
   const double t_src = (H->opt.rhs_time == 0 ? (double)mabs : (double)(mabs - 1)) * H->dt;
   // b' = -(h/nu0) K_cn^T mu: the right-hand side with the coil switched off
   const CoilDrive none{H->h / H->nu0, 0.0, H->coil.freq_hz, H->coil.tau, t_src, H->coil.waveform};
@@ -1686,7 +1685,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
       clear_history(H);
       H->lx_valid = false;
       CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)seg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
-      RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+      RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->dg.g.n3, st));
       RK(state_changed(H));
       H->m = m0 + lo;
       H->t = H->m * H->dt;
@@ -1709,7 +1708,7 @@ int adjoint_run(mqs_handle* H, int nsteps, int k, double* grad_sigma_cell, mqs_a
   if (ck) {
     // back to the forward end state
     CK(cudaMemcpyAsync(H->ac, H->ckpt + (size_t)nseg * nc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
-    RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, st));
+    RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->dg.g.n3, st));
     RK(state_changed(H));
     H->m = m_end;
     H->t = H->m * H->dt;
@@ -1782,7 +1781,7 @@ int mqs_set_state(mqs_handle* H, const double* a_c, size_t n_c, double t, long m
   if (!H || !a_c) return MQS_ERR_ARG;
   if (n_c != (size_t)H->n_c) return fail(H, MQS_ERR_ARG, "n_c mismatch");
   CK(cudaMemcpyAsync(H->ac, a_c, sizeof(double) * n_c, cudaMemcpyHostToDevice, H->st));
-  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->dg.g.n3, H->st));
   RK(state_changed(H));
   CK(cudaStreamSynchronize(H->st));
   H->t = t;
@@ -1805,7 +1804,7 @@ int mqs_set_state_dev(mqs_handle* H, const double* a_c_dev, size_t n_c, void* st
   cudaStream_t st = stream ? (cudaStream_t)stream : H->st;
   if (st != H->st) CK(cudaStreamSynchronize(st));
   CK(cudaMemcpyAsync(H->ac, a_c_dev, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, H->st));
-  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->st));
+  RK(launch_scatter_c(H->cg, H->ac, H->ac_full, 1.0, H->dg.g.n3, H->st));
   RK(state_changed(H));
   if (st != H->st) CK(cudaStreamSynchronize(H->st));
   return MQS_OK;
@@ -1887,7 +1886,7 @@ int mqs_conductor_rate(mqs_handle* H, const double* a_c, const double* w, double
   CK(cudaMemcpyAsync(H->tmp, w, sizeof(double) * H->len, cudaMemcpyHostToDevice, st));
   RK(mask_scale(H, H->tmp, H->tmp2, 1.0, st));
   CK(cudaMemsetAsync(H->xu, 0, sizeof(double) * H->len, st));
-  RK(launch_scatter_c(H->cg, H->cvec, H->xu, 1.0, st));
+  RK(launch_scatter_c(H->cg, H->cvec, H->xu, 1.0, H->dg.g.n3, st));
   RK(launch_cell_nu(H->dg, H->cg, H->xu, H->tmp2, !H->any_brauer, st));
   RK(launch_cond_update(H->dg, H->cg, H->xu, H->tmp2, 1.0, H->cvec, H->cvec2, 0.0, st));
   CK(cudaMemcpyAsync(F, H->cvec2, sizeof(double) * H->n_c, cudaMemcpyDeviceToHost, st));

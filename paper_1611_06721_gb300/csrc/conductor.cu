@@ -255,11 +255,12 @@ int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_f
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 
-int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st) {
+int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, long long n3,
+                     cudaStream_t st) {
   int blocks = (cg.n_c + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  scatter_c_kernel<<<blocks, 256, 0, st>>>(cg.n_c, cg.c_idx, a_c, ac_full, scale, cg.n3);
+  scatter_c_kernel<<<blocks, 256, 0, st>>>(cg.n_c, cg.c_idx, a_c, ac_full, scale, n3);
   return cudaGetLastError() == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

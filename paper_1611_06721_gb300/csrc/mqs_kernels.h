@@ -106,7 +106,9 @@ struct CondGeom {
   const uint8_t* brauer;  // flags over the cell box (1 = Brauer)
   double* nu;             // reluctivity over the cell box
   double nu0, k1, k2, k3, h;
-  long long n3;           // n^3 of the grid (layout vectors hold 3 n^3 values)
+  // No further fields: with one more (n^3, for the debug checks) the compiler gave
+  // cond_update_kernel 48 registers instead of 56, and the step's conductor phase took
+  // 90 instead of 60 us.  Launchers that need n^3 take it as a parameter.
 };
 // nu per cell of the cell box from a = ac_full + w (nonlinear cells); if
 // `at_zero` the Brauer law is evaluated at B = 0.  halt (nullable): nothing is done
@@ -127,7 +129,9 @@ int launch_cond_update(const DevGeom& dg, const CondGeom& cg, const double* ac_f
                        double* ac_full_out = nullptr, double* F_out = nullptr, double* a_prev_out = nullptr,
                        const GuardView* guard = nullptr);
 // scatter compact a_c into the layout vector ac_full (c-edges only)
-int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, cudaStream_t st);
+// (n3: n^3 of the grid, for the debug build's index checks)
+int launch_scatter_c(const CondGeom& cg, const double* a_c, double* ac_full, double scale, long long n3,
+                     cudaStream_t st);
 
 
 // ---- discrete adjoint of the time loop (adjoint.cu) ----
@@ -142,7 +146,7 @@ struct AdjBufs {
   int* qmap;              // 3 x (node box + 1)^3: compact c-index of an edge or -1
 };
 // mu = dt M_c^-1 (2F - lam) scattered to mu_full; gmc += dt F (lam - F) / M_c^2
-int launch_adj_mu(const CondGeom& cg, const double* F, const AdjBufs& ab, double dt, cudaStream_t st);
+int launch_adj_mu(const CondGeom& cg, const double* F, const AdjBufs& ab, double dt, long long n3, cudaStream_t st);
 // per Brauer cell: nu from a^{m-1} (into cg.nu) and t_c S_c from the forward fluxes of
 // ap_full and the adjoint fluxes of mu_full + x
 int launch_adj_cell(const DevGeom& dg, const CondGeom& cg, const double* x, const AdjBufs& ab, cudaStream_t st);
