@@ -68,9 +68,10 @@ __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac,
   }
 }
 
-// The per-edge and per-cell kernels of the step are FP64-bound on the SMs they occupy and
-// their work is small (tens of thousands of edges): 64-thread blocks spread it over every
-// SM instead of a few dozen (ncu: 256-thread blocks filled 35-119 of 152 SMs).
+// The per-edge and per-cell kernels of the step have little work (tens of thousands of
+// edges): 64-thread blocks spread it over every SM (256-thread blocks filled 35-119 of the
+// 152).  The step took the same time either way: each thread's chain of dependent loads
+// sets these kernels' time.
 constexpr int kSmallBlock = 64;
 
 static int stencil_grid(const Box& box) {
@@ -146,9 +147,21 @@ __device__ void monitor_finish(const GuardView& gv, double e, double s) {
   __syncthreads();
   if (!last || w != 0) return;
   __threadfence();
-  const volatile double* pv = gv.part;
+  // the partials from L2 (ld.global.cg: another SM wrote them), eight per lane issued
+  // together before they are added (a loop that adds each load before issuing the next
+  // waits one L2 round trip per 32 blocks)
   double E = 0.0, S = 0.0;
-  for (int b = lane; b < (int)gridDim.x; b += 32) { E += pv[2 * b]; S += pv[2 * b + 1]; }
+  const int nb = (int)gridDim.x;
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = b0 + lane + 32 * q;
+      v[q] = (b < nb) ? __ldcg(reinterpret_cast<const double2*>(gv.part) + b) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { E += v[q].x; S += v[q].y; }
+  }
   E = warp_sum(E);
   S = warp_sum(S);
   if (lane != 0) return;
