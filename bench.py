@@ -443,7 +443,9 @@ def run_ours(args, rank, ws, local, dist):
         flops = n_n * (FLOPS_PER_ITER * its.sum() + FLOPS_PER_RESIDUAL * (len(its) + sum(refs)))
     achieved = flops / (tm["ms_pcg"] * 1e-3) / 1e12
     traffic = args.traffic
-    if traffic is None and args.start == "spe" and depth == 8 and (args.precision, args.pcg_variant) in PCG_TRAFFIC:
+    # the capture is of the 64^3 workload: other grids get no traffic figure
+    if traffic is None and args.grid == 64 and args.start == "spe" and depth == 8 and \
+            (args.precision, args.pcg_variant) in PCG_TRAFFIC:
         rd, wr_it = PCG_TRAFFIC[(args.precision, args.pcg_variant)]
         traffic = rd + wr_it * float(its.mean())
     if args.precision == 0:
