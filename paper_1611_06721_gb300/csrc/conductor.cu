@@ -68,11 +68,12 @@ __global__ void __launch_bounds__(256) rhs_list_kernel(Geom g, const double* ac,
   }
 }
 
-// The per-edge and per-cell kernels of the step have little work (tens of thousands of
-// edges): 64-thread blocks spread it over every SM (256-thread blocks filled 35-119 of the
-// 152).  The step took the same time either way: each thread's chain of dependent loads
-// sets these kernels' time.
-constexpr int kSmallBlock = 64;
+// Block size of the per-edge and per-cell kernels of the step (tens of thousands of
+// edges or cells: 35-119 blocks of 256 threads).  64-thread blocks, spread over every SM,
+// took the same time launch by launch but made graph-replayed steps 10% slower (2000 steps:
+// 1891 against 2115 steps/s): beside them the side stream's push, one block per SM,
+// started later.
+constexpr int kSmallBlock = 256;
 
 static int stencil_grid(const Box& box) {
   long long ntx = (box.hi[0] - box.lo[0] + 31) / 32, nty = (box.hi[1] - box.lo[1] + kTY - 1) / kTY;
