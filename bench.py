@@ -701,7 +701,7 @@ def run_batch(args):
             pcg_variant=args.pcg_variant, dt=0.9 * 2.0 / lam, graph=args.graph)))
     setup_s = time.perf_counter() - t0
     batch = pkg.Batch(solvers)
-    best = batch.tune(max(args.warmup // 16, 1))     # 16 trials (8 candidates, twice)
+    best = batch.tune(max(args.warmup // 8, 1))      # 8 trials (4 scales, twice)
     by_work = batch.weighting()
     forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
                                                       for s_ in solvers]   # PCG kernel form per grid size
@@ -799,15 +799,15 @@ def batch_sub(args, dev):
     setup_s = time.perf_counter() - t0
     trial = 1
     batch = pkg.Batch(solvers)
-    scale = batch.tune(trial)                       # 16 x trial warm-up steps (8 candidates, twice)
+    scale = batch.tune(trial)                       # 8 x trial warm-up steps (4 scales, twice)
     by_work = batch.weighting()
     forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
                                                       for s_ in solvers]   # PCG kernel form per grid size
     form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1])} for p, v in zip(probs, forms)}
-    extra = max(args.batch_sub_warmup - 16 * trial, 0)
+    extra = max(args.batch_sub_warmup - 8 * trial, 0)
     if extra:
         batch.step(extra)
-    warm = 16 * trial + extra
+    warm = 8 * trial + extra
     rc, stats = batch.step(args.batch_sub_steps, allow_fail=True)
     ms = batch.last_ms()
     batch.close()

@@ -512,15 +512,12 @@ int mqs_loss(mqs_handle* h, int nsteps, double* objective);
  * mqs_batch_last_ms: device time of the last mqs_batch_step (CUDA events from
  * the fork of the streams to their join).
  *
- * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8, each with block counts
- * proportional to the unknowns and proportional to the unknowns times the
- * PCG iterations per step of the previous call (the work weighting), for
- * trial_steps steps each -- real steps that advance every problem -- once in
- * that order and once in reverse.  A candidate's score is its device time per
- * unit of PCG work (unknowns x iterations) summed over its two trials, so the
- * falling iteration counts of a starting transient favour no candidate.  It
- * keeps the best (its scale in *best_scale, nullable; the weighting through
- * mqs_batch_get_weighting).
+ * mqs_batch_tune: tries blocks_scale 1, 2, 4 and 8 with the current block
+ * shares, for trial_steps steps each -- real steps that advance every problem
+ * -- once in that order and once in reverse.  A candidate's score is its
+ * device time per unit of PCG work (unknowns x iterations) summed over its two
+ * trials, so the falling iteration counts of a starting transient favour no
+ * candidate.  It keeps the best (its scale in *best_scale, nullable).
  * mqs_batch_set_scale: sets blocks_scale (> 0) and reassigns the counts.
  * mqs_batch_tune_pcg: mqs_tune_pcg on the first handle of every group of
  * handles with the same grid size and precision (on its batch stream and its

@@ -2452,14 +2452,16 @@ int mqs_batch_last_ms(mqs_batch* B, double* ms) {
 
 int mqs_batch_tune(mqs_batch* B, int trial_steps, double* best_scale) {
   if (!B || trial_steps < 1) return MQS_ERR_ARG;
-  // candidates: scale x (shares by unknowns, by work); each is scored by device time per
-  // unit of PCG work (unknowns x iterations) of its trial, so that the falling iteration
-  // counts of a starting transient do not favour the candidates tried last, and the
-  // candidates run in the order c_0 .. c_7, then c_7 .. c_0 with both scores added
+  // candidates: the scales, with the current block shares (by unknowns unless
+  // mqs_batch_set_weighting chose the work weighting: in the tuner it measured slower,
+  // 2862-2903 against 3177-3238 instance-steps/s on the 64-problem FP64 set, and won
+  // trials by noise).  Each is scored by device time per unit of PCG work (unknowns x
+  // iterations) of its trial, so that the falling iteration counts of a starting
+  // transient do not favour the candidates tried last, and the candidates run in the
+  // order c_0 .. c_3, then c_3 .. c_0 with both scores added.
   struct Cand { double scale; bool by_work; };
-  static const Cand cand[] = {{1.0, false}, {2.0, false}, {4.0, false}, {8.0, false},
-                              {1.0, true},  {2.0, true},  {4.0, true},  {8.0, true}};
-  constexpr int kc = 8;
+  const Cand cand[] = {{1.0, B->by_work}, {2.0, B->by_work}, {4.0, B->by_work}, {8.0, B->by_work}};
+  constexpr int kc = 4;
   double score[kc] = {};
   for (int r = 0; r < 2 * kc; ++r) {
     const Cand& c = cand[r < kc ? r : 2 * kc - 1 - r];
