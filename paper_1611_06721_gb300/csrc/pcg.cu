@@ -435,15 +435,16 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
 static int fused_groups_ok(int groups) {
   if (groups == kGroups) return MQS_OK;
   if (groups != 3) return MQS_ERR_ARG;
-  // the three-group block (480 threads) must fit once per SM beside nothing else
-  static int occ = -1;
-  if (occ < 0) {
+  // the three-group block (480 threads) must fit once per SM beside nothing else (asked once
+  // per process; a function-local static is initialised once even with concurrent callers)
+  static const int occ = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_fused_kernel<3>, 32 * kGroupWarps * 3, 0) !=
-        cudaSuccess)
-      return MQS_ERR_CUDA;
-    occ = o;
-  }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_fused_kernel<3>, 32 * kGroupWarps * 3, 0) ==
+                   cudaSuccess
+               ? o
+               : -1;
+  }();
+  if (occ < 0) return MQS_ERR_CUDA;
   return occ >= kPcgBlocksPerSM ? MQS_OK : MQS_ERR_ARG;
 }
 
