@@ -66,6 +66,8 @@ struct mqs_handle {
   bool any_brauer = false;
   cudaStream_t st = nullptr;
   int nblk = 0;
+  int2* ptab = nullptr;               // part ranges of the fused pass for (ptab_nblk, ptab_groups)
+  int ptab_nblk = -1, ptab_groups = -1;
   std::string err;
   std::vector<void*> allocs;
   std::vector<size_t> guard_at;   // debug builds: offset of each buffer's guard bytes
@@ -223,6 +225,20 @@ int dalloc(mqs_handle* H, T** ptr, size_t count) {
   return MQS_OK;
 }
 
+// The fused pass's part table for the handle's block count and tile groups (a synchronous
+// upload: called where those change, never inside a stream capture; pcg_launch uses the
+// table only when it matches)
+int ensure_ptab(mqs_handle* H) {
+  const int g = H->opt.tile_groups == 3 ? 3 : 2;
+  if (H->ptab_nblk == H->nblk && H->ptab_groups == g) return MQS_OK;
+  H->ptab_nblk = H->ptab_groups = -1;
+  if (!H->ptab || H->nblk < 1) return MQS_OK;
+  RK(fused_partition(H->n, H->nblk, g, H->ptab, H->st));
+  H->ptab_nblk = H->nblk;
+  H->ptab_groups = g;
+  return MQS_OK;
+}
+
 // ---- small elementwise kernels -------------------------------------------------------
 // y = mask_n * s * v  (layout vectors)
 __global__ void mask_scale_kernel(Geom g, const double* v, double* y, double s) {
@@ -370,8 +386,9 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
   }
   if (H->opt.pcg_variant >= 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
+    const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == (H->opt.tile_groups == 3 ? 3 : 2);
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
-                            H->nblk, st, init, halt, H->opt.tile_groups);
+                            H->nblk, st, init, halt, H->opt.tile_groups, tab ? H->ptab : nullptr);
   }
   return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
                     st, init, halt);
@@ -751,6 +768,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   RK(dalloc(H, &H->pres, 1));
   RK(dalloc(H, &H->guard, 1));
   RK(dalloc(H, &H->mon_part, 2 * kMonBlocks));
+  RK(dalloc(H, &H->ptab, (size_t)3 * H->nblk));
   CK(cudaMemset(H->guard, 0, sizeof(StepGuard)));
   RK(dalloc(H, &H->tspart, (size_t)5 * ts_nblk() * kTileSlots));
   RK(dalloc(H, &H->spe_hpart, (size_t)4 * ts_nblk() * kTileSlots));
@@ -814,6 +832,7 @@ int do_setup(mqs_handle* H, const mqs_grid* grid, const mqs_materials* mat, cons
   H->cg.brauer = H->brauer;
   H->cg.nu = H->nu;
   H->cg.nu0 = H->nu0; H->cg.k1 = H->k1; H->cg.k2 = H->k2; H->cg.k3 = H->k3; H->cg.h = H->h;
+  RK(ensure_ptab(H));
   CK(cudaDeviceSynchronize());
   return MQS_OK;
 }
@@ -1053,7 +1072,7 @@ int mqs_set_options(mqs_handle* H, const mqs_options* o) {
   H->opt = *o;
   H->dt = (o->dt > 0.0) ? o->dt : dt;
   if (reset) clear_history(H);
-  return MQS_OK;
+  return ensure_ptab(H);
 }
 
 int mqs_get_options(const mqs_handle* H, mqs_options* o) {
@@ -2074,7 +2093,7 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
   if (nblk > mx) return fail(H, MQS_ERR_ARG, "more persistent blocks than can be co-resident");
   CK(cudaStreamSynchronize(H->st));     // no solve with the old block count in flight
   H->nblk = nblk == 0 ? mx : nblk;
-  return MQS_OK;
+  return ensure_ptab(H);
 }
 
 // Kernel-form tuner: the PCG forms that compute the same iterates (precision 0: the
@@ -2122,6 +2141,8 @@ int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
   for (int c = 0; c < nc && rc == MQS_OK; ++c) {
     H->opt.pcg_variant = cand[c][0];
     H->opt.tile_groups = cand[c][1];
+    rc = ensure_ptab(H);
+    if (rc != MQS_OK) break;
     std::vector<float> ms;
     for (int r = 0; r <= trials && rc == MQS_OK; ++r) {
       if (cudaMemsetAsync(H->derr, 0, sizeof(int), st) != cudaSuccess ||
@@ -2158,6 +2179,7 @@ int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
   cudaEventDestroy(e1);
   H->opt.pcg_variant = (rc == MQS_OK) ? best : saved;
   H->opt.tile_groups = (rc == MQS_OK) ? best_groups : saved_groups;
+  if (ensure_ptab(H) != MQS_OK && rc == MQS_OK) rc = MQS_ERR_CUDA;
   H->lx_valid = false;                   // lx held the trial solves' images
   if (chosen) *chosen = H->opt.pcg_variant;
   return rc;
@@ -2229,6 +2251,7 @@ int batch_assign(mqs_batch* B) {
     long nb = std::lround(B->scale * mx * w[i] / std::max(wsum, 1.0));
     H->nblk = (int)std::min<long>(std::max<long>(nb, 1), mx);
     H->ts_cap = std::max(2 * H->nblk, 4);    // its tall-skinny kernels: about its share of the SMs
+    BRK(ensure_ptab(H));
   }
   return MQS_OK;
 }
@@ -2240,6 +2263,7 @@ void batch_release(mqs_batch* B) {
     B->hs[i]->st = B->saved_st[i];
     B->hs[i]->nblk = B->saved_nblk[i];
     B->hs[i]->ts_cap = 0;
+    ensure_ptab(B->hs[i]);
     B->hs[i]->in_batch = false;
   }
   if (B->master) cudaStreamSynchronize(B->master);
@@ -2494,6 +2518,7 @@ int mqs_batch_tune_pcg(mqs_batch* B, int trials, int* chosen) {
       if (!done[j] && G->n == H->n && G->opt.precision == H->opt.precision) {
         G->opt.pcg_variant = v;
         G->opt.tile_groups = H->opt.tile_groups;
+        RK(ensure_ptab(G));
         done[j] = 1;
       }
     }

@@ -15,6 +15,7 @@
 // Convergence ||r|| <= tol ||b|| is confirmed on the true residual b - L x,
 // whose stencil output L x is kept for the start-vector history.
 #include <cmath>
+#include <vector>
 #include "mqs_internal.cuh"
 #include "mqs_kernels.h"
 #include "pcg_fused.cuh"
@@ -278,7 +279,7 @@ struct EpiApplyDot {  // w = t on n-edges (0 elsewhere); sums w.r with r the sou
   }
 };
 
-struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; };
+struct FusedBufs { double* r1; double* w0; double* w1; double* s0; double* s1; const int2* ptab; };
 
 // The one-reduction form: after the initial residual r and w = L r, every
 // iteration is one fused pass (sweep_fused) and one grid reduction of
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
                     58 - E, E - 58};
       double g1 = 0.0, d1 = 0.0;
       int er = 0, ew = 0, es = 0;
-      sweep_fused_fx(a.g, v, a.full, bid, nb, sm.f, g1, d1, er, ew, es);
+      sweep_fused_fx(a.g, v, a.full, bid, nb, sm.f, g1, d1, er, ew, es, fb.ptab);
       double gn, dn;
       if (!grid_sum2_max3(g1, d1, er, ew, es, gn, dn, er, ew, es, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs,
                           gm))
@@ -450,7 +451,7 @@ static int fused_groups_ok(int groups) {
 
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
-                     int nblk, cudaStream_t st, int init, const int* halt, int groups) {
+                     int nblk, cudaStream_t st, int init, const int* halt, int groups, const int2* ptab) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -460,7 +461,7 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
   a.spin = 1ll << 21;
   a.init = init;
   a.halt = halt;
-  FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1};
+  FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1, ptab};
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a, &fb};
   if (groups == 0) groups = kGroups;
@@ -507,6 +508,54 @@ int pcg_max_blocks(int* nblk) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<1>, kBlock, 0) != cudaSuccess) return MQS_ERR_CUDA;
   if (occ < 1) return MQS_ERR_CUDA;
   *nblk = nsm * (occ < kPcgBlocksPerSM ? occ : kPcgBlocksPerSM);  // persistent, co-resident blocks
+  return MQS_OK;
+}
+
+// The plane-tile ranges of the fused pass's group parts with the largest part as small as
+// possible.  A part's cost is its plane-tiles plus one warm-up plane per segment (a
+// segment starts at the part's first tile, at every tile column's first plane and after
+// kMaxSeg planes).  The even split of the tile count can give one part two segments and
+// the most tiles (64^3, 304 parts: 7 tiles + 2 warm-ups against 6.74 + 1.05 on average);
+// a binary search on the largest cost with a greedy fill finds the smallest one (8 there).
+// Parts past the last filled one get empty ranges.
+static long long partition_fill(long long ntiles, int nz, long long cap, long long parts, int2* out) {
+  long long u = 0, p = 0;
+  while (u < ntiles) {
+    if (p >= parts) return parts + 1;
+    const long long u0 = u;
+    long long cost = 0, seg = 0;
+    while (u < ntiles) {
+      const bool newseg = (u == u0) || (u % nz == 0) || (seg == kMaxSeg);
+      const long long add = 1 + (newseg ? 1 : 0);
+      if (cost + add > cap && u > u0) break;
+      cost += add;
+      seg = newseg ? 1 : seg + 1;
+      ++u;
+    }
+    if (out) out[p] = make_int2((int)u0, (int)u);
+    ++p;
+  }
+  if (out)
+    for (long long q = p; q < parts; ++q) out[q] = make_int2((int)ntiles, (int)ntiles);
+  return p;
+}
+
+int fused_partition(int n, int nblk, int groups, int2* dev_table, cudaStream_t st) {
+  if (groups == 0) groups = kGroups;
+  const long long ntx = (n + 31) / 32, nty = (n + kTY - 1) / kTY, ntiles = ntx * nty * n;
+  const long long parts = (long long)nblk * groups;
+  if (ntiles >= (1LL << 31) || parts <= 0) return MQS_ERR_ARG;
+  long long lo = 1, hi = 2 * ntiles + 2;
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    if (partition_fill(ntiles, n, mid, parts, nullptr) <= parts) hi = mid;
+    else lo = mid + 1;
+  }
+  std::vector<int2> tab((size_t)parts);
+  partition_fill(ntiles, n, lo, parts, tab.data());
+  if (cudaMemcpyAsync(dev_table, tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MQS_ERR_CUDA;
   return MQS_OK;
 }
 

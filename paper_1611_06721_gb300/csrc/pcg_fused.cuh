@@ -325,10 +325,12 @@ using FusedFxSmemBlock = FusedFxSmemBlockG<>;
 // biased FP64 exponent field of v (|v| < 2^(e - 1022) for e > 0; 0 for zero and subnormals)
 __device__ __forceinline__ int fx_expo(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
 
+// ptab (nullable): plane-tile range [x, y) of every group part (part * G + group), from
+// fused_partition; else the even split of the formula below.
 template <int G>
 __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, const Box& box, int part, int nparts,
                                FusedFxSmemBlockG<G>& smb, double& gamma, double& delta, int& mer, int& mew,
-                               int& mes) {
+                               int& mes, const int2* ptab = nullptr) {
   const FusedVecs& v = fv.v;
   const int shi = fv.sh_in, sho = fv.sh_out;
   const int n = g.n;
@@ -341,8 +343,8 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
   const long long ntiles = (long long)ntx * nty * nz;
   const long long gp = (long long)part * G + grp, gn = (long long)nparts * G;
-  long long u = ntiles * gp / gn;
-  const long long u1 = ntiles * (gp + 1) / gn;
+  long long u = ptab ? (long long)ptab[gp].x : ntiles * gp / gn;
+  const long long u1 = ptab ? (long long)ptab[gp].y : ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
   // owned position: the FP64 update of fused_apply, the exponents of r_{i+1} and s_i
   auto own_apply = [&](int o, const FusedLoadT<double>& L, double* rn) {
