@@ -229,7 +229,8 @@ int dalloc(mqs_handle* H, T** ptr, size_t count) {
 // upload: called where those change, never inside a stream capture; pcg_launch uses the
 // table only when it matches)
 int ensure_ptab(mqs_handle* H) {
-  const int g = H->opt.tile_groups == 3 ? 3 : 2;
+  // three tile groups only in the FP64 one-reduction pass; the refined paths use two
+  const int g = (H->opt.tile_groups == 3 && H->opt.precision == 0) ? 3 : kGroups;
   if (H->ptab_nblk == H->nblk && H->ptab_groups == g) return MQS_OK;
   H->ptab_nblk = H->ptab_groups = -1;
   if (!H->ptab || H->nblk < 1) return MQS_OK;
@@ -374,19 +375,21 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-12;
+    const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == kGroups;
     return launch_pcg_ff(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                         maxit, H->nblk, st, init, halt);
+                         maxit, H->nblk, st, init, halt, tab ? H->ptab : nullptr);
   }
   if (H->opt.precision == 1) {
     RK(ensure_mixed(H));
     const MixedBufs mb{H->r32, H->p32, H->q32, H->d32, H->r32b, H->w32a, H->w32b, H->s32a, H->s32b};
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-5;
+    const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == kGroups;
     return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                            maxit, H->nblk, st, init, H->opt.pcg_variant, halt);
+                            maxit, H->nblk, st, init, H->opt.pcg_variant, halt, tab ? H->ptab : nullptr);
   }
   if (H->opt.pcg_variant >= 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
-    const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == (H->opt.tile_groups == 3 ? 3 : 2);
+    const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == (H->opt.tile_groups == 3 ? 3 : kGroups);
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
                             H->nblk, st, init, halt, H->opt.tile_groups, tab ? H->ptab : nullptr);
   }

@@ -58,13 +58,13 @@ struct MixedBufs {
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                      double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0, int variant = 0,
-                     const int* halt = nullptr);
+                     const int* halt = nullptr, const int2* ptab = nullptr);
 // precision 2: the same refinement with float-float one-reduction inner solves
 // (MixedBufs sized for 8 bytes per value, all nine buffers)
 int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                   double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                   double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0,
-                  const int* halt = nullptr);
+                  const int* halt = nullptr, const int2* ptab = nullptr);
 
 // one-reduction PCG (one fused stencil pass and one grid reduction per
 // iteration); needs five more layout vectors

@@ -115,9 +115,10 @@ __device__ __forceinline__ void fused_apply(const FusedVecsT<T>& v, int o, int n
 
 // One fused pass over `box` for group-part `part` of `nparts` (block level,
 // as in sweep_L).  Accumulates gamma and delta into the caller's registers.
+// ptab (nullable): the part ranges of fused_partition (kGroups groups per block)
 template <class T>
 __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& box, int part, int nparts,
-                            FusedSmemBlockT<T>& smb, T& gamma, T& delta) {
+                            FusedSmemBlockT<T>& smb, T& gamma, T& delta, const int2* ptab = nullptr) {
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
@@ -128,8 +129,8 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
   const int ntx = (bx0 + 31) / 32, nty = (by0 + kTY - 1) / kTY;
   const long long ntiles = (long long)ntx * nty * nz;
   const long long gp = (long long)part * kGroups + grp, gn = (long long)nparts * kGroups;
-  long long u = ntiles * gp / gn;
-  const long long u1 = ntiles * (gp + 1) / gn;
+  long long u = ptab ? (long long)ptab[gp].x : ntiles * gp / gn;
+  const long long u1 = ptab ? (long long)ptab[gp].y : ntiles * (gp + 1) / gn;
   const int cw0 = g.cb_hi[0] - g.cb_lo[0], cw01 = cw0 * (g.cb_hi[1] - g.cb_lo[1]);
   while (u < u1) {
     const long long tc = u / nz;

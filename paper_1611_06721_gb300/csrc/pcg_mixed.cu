@@ -45,6 +45,7 @@ struct MixedArgs {
   long long spin;
   int init;             // as in the FP64 kernel: 0 stencil, 2 zero start
   const int* halt;      // nullable: nonzero = an earlier step of the stepping call failed, skip the solve
+  const int2* ptab;     // nullable: part ranges of the one-reduction pass (fused_partition)
 };
 
 // as in the FP64 kernel: a halted stepping call skips the solve (zero iterations)
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
         FusedVecsT<float> v{a.d32, a.p32, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1),
                             sbuf(cur ^ 1), alpha.hi, bet.hi, first};
         float g1 = 0.f, d1 = 0.f;
-        sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
+        sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1, a.ptab);
         ffv gn, dn;
         if (!reduceF(ffv(g1, 0.f), ffv(d1, 0.f), gn, dn)) return;
         ++it_in; ++inner_total;
@@ -659,7 +660,7 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedAr
       FusedVecsT<ffv> v{df, pf, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1), sbuf(cur ^ 1),
                         alpha, bet, first};
       ffv g1(0), d1(0);
-      sweep_fused<ffv>(a.g, v, a.full, bid, nb, sm.ff, g1, d1);
+      sweep_fused<ffv>(a.g, v, a.full, bid, nb, sm.ff, g1, d1, a.ptab);
       ffv gn, dn;
       if (!reduceF(g1, d1, gn, dn)) return;
       ++it_in; ++inner_total;
@@ -688,7 +689,8 @@ __global__ void __launch_bounds__(kBlock, kPcgBlocksPerSM) pcg_ff_kernel(MixedAr
 
 int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                   double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
-                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init, const int* halt) {
+                  double inner_tol, int maxit, int nblk, cudaStream_t st, int init, const int* halt,
+                  const int2* ptab) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -696,6 +698,7 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
   a.r32 = mb.r32; a.p32 = mb.p32; a.q32 = mb.q32; a.d32 = mb.d32;
   a.r32b = mb.r32b; a.w32a = mb.w32a; a.w32b = mb.w32b; a.s32a = mb.s32a; a.s32b = mb.s32b;
   a.variant = 1;
+  a.ptab = ptab;
   a.part = part; a.bar = bar; a.err = err; a.out = out; a.refinements = refinements;
   a.tol2 = tol * tol; a.inner_tol = inner_tol; a.maxit = maxit;
   a.spin = 1ll << 21;
@@ -711,7 +714,7 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                      double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant,
-                     const int* halt) {
+                     const int* halt, const int2* ptab) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -730,6 +733,7 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   // 64^3 (FP32 vectors in L2): one block per SM; from 96^3 on, two (28% faster per
   // inner iteration at 128^3, 83.6 -> 62.8 us)
   const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;
+  a.ptab = two ? nullptr : ptab;                 // the table is for nblk blocks
   const void* fn = two ? (const void*)pcg_mixed_kernel<2> : (const void*)pcg_mixed_kernel<1>;
   const int smem = (int)sizeof(MixedSmem);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return MQS_ERR_CUDA;
