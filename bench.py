@@ -62,8 +62,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA lan
 # kernel build (a zero-start solve of 221 iterations, profiles/pcg_fused_kernel_...): bytes
 # read per launch (the carried vectors stay in L2) and bytes written per iteration (L2
 # write-back of the ping-pong vectors, which grows with the iterations); keyed by
-# (precision, pcg_variant).  A launch of the benchmark is scaled by its iteration count.
-PCG_TRAFFIC = {(0, 1): (12.947968e6, 233.488384e6 / 221)}
+# (precision, pcg_variant, halo warps per tile group).  A launch of the benchmark is scaled by
+# its iteration count.
+PCG_TRAFFIC = {(0, 1, 2): (12.971008e6, 240.350720e6 / 221)}
 
 
 def measured_peaks():
@@ -348,7 +349,7 @@ def run_ours(args, rank, ws, local, dist):
     opts = pkg.SolverOptions(tol=1e-10, start_mode=mode,
                              spe_depth=depth if args.start in ("spe", "cspe") else 8,
                              pod_snapshots=depth if args.start == "pod" else 20, pcg_variant=args.pcg_variant,
-                             cspe_period=args.cspe_period,
+                             halo_warps=args.halo_warps, cspe_period=args.cspe_period,
                              precision=args.precision, rhs_split=1 if args.rhs_split else 0,
                              eps_lin=args.eps_lin, graph=args.graph)
     s = pkg.Solver.from_problem(p, opts)
@@ -445,11 +446,12 @@ def run_ours(args, rank, ws, local, dist):
     traffic = args.traffic
     # the capture is of the 64^3 workload: other grids get no traffic figure
     if traffic is None and args.grid == 64 and args.start == "spe" and depth == 8 and \
-            (args.precision, args.pcg_variant) in PCG_TRAFFIC:
-        rd, wr_it = PCG_TRAFFIC[(args.precision, args.pcg_variant)]
+            (args.precision, args.pcg_variant, max(args.halo_warps, 1)) in PCG_TRAFFIC:
+        rd, wr_it = PCG_TRAFFIC[(args.precision, args.pcg_variant, max(args.halo_warps, 1))]
         traffic = rd + wr_it * float(its.mean())
     if args.precision == 0:
-        roof = {"bound": "alu", "kernel": "pcg_kernel" if args.pcg_variant == 0 else "pcg_fused_kernel",
+        roof = {"bound": "alu", "kernel": "pcg_kernel" if args.pcg_variant == 0
+                else f"pcg_fused_kernel<2,{max(args.halo_warps, 1)}>",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "note": "FP64 FMA=2 flop; peak derived: 152 SM x 2 FMA/clk x 2 x 2070 MHz"}
@@ -471,8 +473,10 @@ def run_ours(args, rank, ws, local, dist):
                        "start_vector": args.start + (str(depth) if args.start in ("spe", "pod", "cspe") else "")
                                        + (f"/period {args.cspe_period or 25}" if args.start == "cspe" else ""),
                        "tol": 1e-10, "eps_lin": args.eps_lin, "dt_s": dt, "lambda_max": lam,
-                       "pcg": "one reduction per iteration" if (args.pcg_variant == 1 or args.precision == 2)
-                              else "two reductions per iteration",
+                       "pcg": ("one reduction per iteration" if (args.pcg_variant == 1 or args.precision == 2)
+                               else "two reductions per iteration")
+                              + (f", {max(args.halo_warps, 1)} halo warp(s) per tile group"
+                                 if args.pcg_variant == 1 and args.precision == 0 else ""),
                        "right_hand_sides": "separate (conductor and coil types, one history each)" if args.rhs_split
                                            else "fused (one solve per step)",
                        "l2": "flushed between timed steps by a 256 MiB write",
@@ -544,14 +548,15 @@ def coil_rhs(p, amp=100.0):
     return b
 
 
-def single_solve(variant=1):
+def single_solve(variant=1, halo_warps=0):
     """One zero-start PCG solve of K_n w = 100 X_s on the workload (twice)."""
     import __graft_entry__ as g
     g.build()
     import paper_1611_06721_gb300 as pkg
     import workloads as W
     p = W.config_nonlinear_iron()
-    s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, pcg_variant=variant))
+    s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, pcg_variant=variant,
+                                                     halo_warps=halo_warps))
     b = coil_rhs(p)
     for _ in range(2):
         x, info = s.pcg_solve(b, tol=1e-10)
@@ -626,9 +631,9 @@ def size_sweep(sizes):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for n in sizes:
         p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
-        for prec, var, groups in ((0, 1, 0), (0, 1, 3), (1, 1, 0), (1, 2, 0)):
+        for prec, var, groups, halo in ((0, 1, 0, 0), (0, 1, 3, 0), (0, 1, 0, 2), (1, 1, 0, 0), (1, 2, 0, 0)):
             s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
-                                                             pcg_variant=var, tile_groups=groups))
+                                                             pcg_variant=var, tile_groups=groups, halo_warps=halo))
             stream = torch.cuda.Stream(device=dev)
             s.set_stream(stream.cuda_stream)
             with torch.cuda.stream(stream):
@@ -652,7 +657,7 @@ def size_sweep(sizes):
             gbs = BYTES_PER_ITER[prec] * s.n_n / (us_it * 1e-6) / 1e9
             print(json.dumps({"sweep": "zero-start solve", "workload": workload_name(p), "grid": n,
                               "precision": "FP64" if prec == 0 else "FP32 inner CG in FP64 refinement",
-                              "pcg_variant": var, "tile_groups": groups or 2,
+                              "pcg_variant": var, "tile_groups": groups or 2, "halo_warps": halo or 1,
                               "n_unknowns": int(s.n_n), "iterations": int(its), "relres": info.relres,
                               "status": int(info.status), "ms_per_solve": ms, "us_per_iteration": us_it,
                               "algorithmic_GBps": gbs, "hbm_peak_GBps": peaks.get("hbm_gbs"),
@@ -703,9 +708,9 @@ def run_batch(args):
     batch = pkg.Batch(solvers)
     best = batch.tune(max(args.warmup // 8, 1))      # 8 trials (4 scales, twice)
     by_work = batch.weighting()
-    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
-                                                      for s_ in solvers]   # PCG kernel form per grid size
-    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1])} for p, v in zip(probs, forms)}
+    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [s_.pcg_form() for s_ in solvers]   # PCG kernel form per grid size
+    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1]), "halo_warps": int(v[2])}
+                 for p, v in zip(probs, forms)}
     depth_by_n = None
     if args.tune_depth:
         chosen = batch.tune_depth(max(args.warmup // 4, 5), depths=(4, 8, 16))
@@ -801,9 +806,9 @@ def batch_sub(args, dev):
     batch = pkg.Batch(solvers)
     scale = batch.tune(trial)                       # 8 x trial warm-up steps (4 scales, twice)
     by_work = batch.weighting()
-    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [(s_.options.pcg_variant, s_.options.tile_groups)
-                                                      for s_ in solvers]   # PCG kernel form per grid size
-    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1])} for p, v in zip(probs, forms)}
+    forms = batch.tune_pcg(args.tune_pcg_trials) if args.tune_pcg else [s_.pcg_form() for s_ in solvers]   # PCG kernel form per grid size
+    form_by_n = {int(p.N): {"pcg_variant": int(v[0]), "tile_groups": int(v[1]), "halo_warps": int(v[2])}
+                 for p, v in zip(probs, forms)}
     extra = max(args.batch_sub_warmup - 8 * trial, 0)
     if extra:
         batch.step(extra)
@@ -1010,6 +1015,9 @@ def main():
     ap.add_argument("--pcg-variant", type=int, default=1, choices=[0, 1, 2],
                     help="0: two grid reductions per PCG iteration, 1: one (fused pass; default), 2: with "
                          "--precision 1, the inner pass carrying x, r, p only (24 B per unknown)")
+    ap.add_argument("--halo-warps", type=int, default=2, choices=[0, 1, 2],
+                    help="FP64 one-reduction pass: halo warps per tile group (0/1: one; 2: two, in 384-thread "
+                         "blocks, the default)")
     ap.add_argument("--grid", type=int, default=64,
                     help="cells per axis of the iron workload (64: the benchmark; others scale it)")
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")
@@ -1047,7 +1055,7 @@ def main():
               flush=True)
         return
     if args.single_solve:
-        single_solve(args.pcg_variant)
+        single_solve(args.pcg_variant, args.halo_warps)
         return
     if args.sweep:
         size_sweep([int(v) for v in args.sweep.split(",") if v])

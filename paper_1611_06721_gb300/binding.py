@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("pod_snapshots", C.c_int), ("eps_pod", C.c_double), ("eps_lin", C.c_double),
                 ("dt", C.c_double), ("rhs_time", C.c_int), ("pcg_variant", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("cspe_period", C.c_int), ("rhs_split", C.c_int), ("graph", C.c_int),
-                ("cfl_factor", C.c_double), ("monitor_steps", C.c_int), ("tile_groups", C.c_int)]
+                ("cfl_factor", C.c_double), ("monitor_steps", C.c_int), ("tile_groups", C.c_int),
+                ("halo_warps", C.c_int)]
 
 
 class LayoutInfo(C.Structure):
@@ -237,12 +238,13 @@ class SolverOptions:
     cfl_factor: float = 0.0  # > 0 with dt <= 0: setup sets dt = cfl_factor * 2 / lambda_max (eq. (CFL))
     monitor_steps: int = 0   # instability monitor window (0: 8 steps; < 0: finiteness test only)
     tile_groups: int = 0     # stencil groups per block of the FP64 one-reduction pass (0/2 or 3)
+    halo_warps: int = 0      # halo warps per tile group of that pass (0/1, or 2 with two groups)
 
     def c(self):
         return Options(self.tol, self.maxit, self.start_mode, self.spe_depth, self.pod_snapshots,
                        self.eps_pod, self.eps_lin, self.dt, self.rhs_time, self.pcg_variant, self.precision,
                        self.inner_tol, self.cspe_period, self.rhs_split, self.graph, self.cfl_factor,
-                       self.monitor_steps, self.tile_groups)
+                       self.monitor_steps, self.tile_groups, self.halo_warps)
 
 
 class Solver:
@@ -398,16 +400,22 @@ class Solver:
 
     def tune_pcg(self, trials=2):
         """The fastest PCG kernel form for this grid, precision and block count
-        (mqs_tune_pcg); sets it and returns (pcg_variant, tile_groups)."""
+        (mqs_tune_pcg); sets it and returns (pcg_variant, tile_groups, halo_warps)."""
         v = C.c_int()
         self._check(self.lib.mqs_tune_pcg(self.h, trials, C.byref(v)))
         self._sync_options()
-        return self.options.pcg_variant, self.options.tile_groups
+        return self.pcg_form()
+
+    def pcg_form(self):
+        """(pcg_variant, tile_groups, halo_warps) of the options in use."""
+        o = self.options
+        return o.pcg_variant, o.tile_groups, o.halo_warps
 
     def _sync_options(self):
         o = Options()
         self._check(self.lib.mqs_get_options(self.h, C.byref(o)))
-        self.options = replace(self.options, pcg_variant=o.pcg_variant, tile_groups=o.tile_groups)
+        self.options = replace(self.options, pcg_variant=o.pcg_variant, tile_groups=o.tile_groups,
+                               halo_warps=o.halo_warps)
 
     def set_blocks(self, nblk):
         """Persistent blocks of this handle's PCG kernels (0 = one per SM)."""
@@ -603,12 +611,12 @@ class Batch:
 
     def tune_pcg(self, trials=2):
         """mqs_batch_tune_pcg: the PCG kernel form per (grid size, precision) group;
-        returns every solver's (pcg_variant, tile_groups)."""
+        returns every solver's (pcg_variant, tile_groups, halo_warps)."""
         out = (C.c_int * len(self.solvers))()
         self._check(self.lib.mqs_batch_tune_pcg(self.b, trials, out))
         for sv in self.solvers:
             sv._sync_options()
-        return [(sv.options.pcg_variant, sv.options.tile_groups) for sv in self.solvers]
+        return [sv.pcg_form() for sv in self.solvers]
 
     def set_weighting(self, by_work):
         """Block shares by unknowns (False) or unknowns x last iterations (True)."""

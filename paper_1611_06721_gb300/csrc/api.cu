@@ -391,7 +391,8 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
     const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == (H->opt.tile_groups == 3 ? 3 : kGroups);
     return launch_pcg_fused(H->dg, b, x, H->r, H->p, H->lx, ex, H->part, H->bar, H->derr, H->pres, tol, maxit,
-                            H->nblk, st, init, halt, H->opt.tile_groups, tab ? H->ptab : nullptr);
+                            H->nblk, st, init, halt, H->opt.tile_groups, tab ? H->ptab : nullptr,
+                            H->opt.halo_warps);
   }
   return launch_pcg(H->dg, b, x, H->r, H->p, H->q, H->lx, H->part, H->bar, H->derr, H->pres, tol, maxit, H->nblk,
                     st, init, halt);
@@ -608,6 +609,10 @@ int validate_options(const mqs_options* o, std::string& why) {
   if (o->pcg_variant < 0 || o->pcg_variant > 2) { why = "pcg_variant must be 0, 1 or 2"; return MQS_ERR_ARG; }
   if (o->tile_groups != 0 && o->tile_groups != 2 && o->tile_groups != 3) {
     why = "tile_groups must be 0, 2 or 3";
+    return MQS_ERR_ARG;
+  }
+  if (o->halo_warps < 0 || o->halo_warps > 2 || (o->halo_warps == 2 && o->tile_groups == 3)) {
+    why = "halo_warps must be 0, 1 or 2 (2 only with two tile groups)";
     return MQS_ERR_ARG;
   }
   if (o->precision < 0 || o->precision > 2) { why = "precision must be 0, 1 or 2"; return MQS_ERR_ARG; }
@@ -2100,7 +2105,8 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
 }
 
 // Kernel-form tuner: the PCG forms that compute the same iterates (precision 0: the
-// two-reduction kernel and the one-reduction fused pass; precision 1: the FP32 inner CG
+// two-reduction kernel and the one-reduction fused pass on two tile groups with one or two
+// halo warps each and on three; precision 1: the FP32 inner CG
 // with two reductions, with one reduction carrying five vectors, and with one reduction
 // carrying three vectors over a two-deep halo) differ in their tiles' halo depth, staging
 // and traffic, and which is fastest depends on the grid size and the block count.  Each
@@ -2111,18 +2117,17 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
 int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
   if (!H || trials < 1) return MQS_ERR_ARG;
   const Range range_("mqs_tune_pcg");
-  // candidates (pcg_variant, tile_groups)
-  int cand[3][2], nc = 0;
+  // candidates (pcg_variant, tile_groups, halo_warps)
+  int cand[4][3] = {}, nc = 0;
   if (H->opt.precision == 0) {
-    cand[0][0] = 0; cand[0][1] = 0;
-    cand[1][0] = 1; cand[1][1] = 2;
-    cand[2][0] = 1; cand[2][1] = 3;
-    nc = 3;
+    const int f[4][3] = {{0, 0, 0}, {1, 2, 1}, {1, 3, 1}, {1, 2, 2}};
+    for (nc = 0; nc < 4; ++nc)
+      for (int q = 0; q < 3; ++q) cand[nc][q] = f[nc][q];
   } else if (H->opt.precision == 1) {
-    for (int v = 0; v < 3; ++v) { cand[v][0] = v; cand[v][1] = 0; }
+    for (int v = 0; v < 3; ++v) cand[v][0] = v;
     nc = 3;
   } else {
-    cand[0][0] = H->opt.pcg_variant; cand[0][1] = 0;    // one float-float inner form
+    cand[0][0] = H->opt.pcg_variant;    // one float-float inner form
     nc = 1;
   }
   cudaStream_t st = H->st;
@@ -2138,12 +2143,13 @@ int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
     cudaEventDestroy(e0);
     return fail(H, MQS_ERR_CUDA, "mqs_tune_pcg: event creation failed");
   }
-  const int saved = H->opt.pcg_variant, saved_groups = H->opt.tile_groups;
-  int best = saved, best_groups = saved_groups, rc = MQS_OK;
+  const int saved = H->opt.pcg_variant, saved_groups = H->opt.tile_groups, saved_halo = H->opt.halo_warps;
+  int best = saved, best_groups = saved_groups, best_halo = saved_halo, rc = MQS_OK;
   float best_ms = 0.f;
   for (int c = 0; c < nc && rc == MQS_OK; ++c) {
     H->opt.pcg_variant = cand[c][0];
     H->opt.tile_groups = cand[c][1];
+    H->opt.halo_warps = cand[c][2];
     rc = ensure_ptab(H);
     if (rc != MQS_OK) break;
     std::vector<float> ms;
@@ -2176,12 +2182,13 @@ int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
     if (rc != MQS_OK) break;
     std::sort(ms.begin(), ms.end());
     const float med = ms[ms.size() / 2];
-    if (c == 0 || med < best_ms) { best = cand[c][0]; best_groups = cand[c][1]; best_ms = med; }
+    if (c == 0 || med < best_ms) { best = cand[c][0]; best_groups = cand[c][1]; best_halo = cand[c][2]; best_ms = med; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   H->opt.pcg_variant = (rc == MQS_OK) ? best : saved;
   H->opt.tile_groups = (rc == MQS_OK) ? best_groups : saved_groups;
+  H->opt.halo_warps = (rc == MQS_OK) ? best_halo : saved_halo;
   if (ensure_ptab(H) != MQS_OK && rc == MQS_OK) rc = MQS_ERR_CUDA;
   H->lx_valid = false;                   // lx held the trial solves' images
   if (chosen) *chosen = H->opt.pcg_variant;
@@ -2521,6 +2528,7 @@ int mqs_batch_tune_pcg(mqs_batch* B, int trials, int* chosen) {
       if (!done[j] && G->n == H->n && G->opt.precision == H->opt.precision) {
         G->opt.pcg_variant = v;
         G->opt.tile_groups = H->opt.tile_groups;
+        G->opt.halo_warps = H->opt.halo_warps;
         RK(ensure_ptab(G));
         done[j] = 1;
       }

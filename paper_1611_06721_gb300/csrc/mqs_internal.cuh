@@ -215,6 +215,11 @@ using SweepSmem = SweepSmemT<double>;
 __device__ __forceinline__ void group_sync(int grp) {
   asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kGroupWarps * 32) : "memory");
 }
+// the same over NW warps (a group with more than one halo warp)
+template <int NW>
+__device__ __forceinline__ void group_sync_n(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(NW * 32) : "memory");
+}
 
 // Applies t = L s over the positions of `box`, calling
 //   epi(e, mask, tx, ty, tz, sx, sy, sz)
@@ -233,7 +238,7 @@ __device__ __forceinline__ void group_sync(int grp) {
 // default; the FP64 PCG's direction sweep loads FP64 and runs the stencil in 64-bit
 // fixed point, exactly, on the integer pipes).
 // Must be called by all G x kGroupWarps warps of the block (G groups; kGroups unless the
-// caller's shared memory says otherwise).
+// caller's shared memory says otherwise), and by no other warp.
 template <class T, class Epi, class M, class Cv = LoadAs, int G = kGroups>
 __device__ void sweep_L(const Geom& g, const M* __restrict__ s, const Box& box, int part, int nparts,
                         SweepSmemT<T, G>& sm, Epi& epi, Cv cv = Cv()) {

@@ -70,13 +70,14 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
 // iteration); needs five more layout vectors
 struct PcgExtra { double* r1; double* w0; double* w1; double* s0; double* s1; };
 // groups: stencil groups per block (0 or 2: the default 320-thread block; 3: 480 threads,
-// 128 registers a thread); MQS_ERR_ARG for other counts or when 3 does not fit.
+// 128 registers a thread).  halo_warps: halo warps per group of the fused pass (0 or 1; 2
+// with two groups: 384 threads).  MQS_ERR_ARG for other forms or a block that does not fit.
 // ptab (nullable): the fused pass's part ranges from fused_partition for this n, nblk and
 // groups; nullptr splits the plane-tiles evenly.
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
                      int nblk, cudaStream_t st, int init = 0, const int* halt = nullptr, int groups = 0,
-                     const int2* ptab = nullptr);
+                     const int2* ptab = nullptr, int halo_warps = 0);
 // the cost-balanced part ranges of the fused pass (nblk x groups int2 entries) into
 // dev_table; blocks the host (a synchronous upload on st: not for use during stream capture)
 int fused_partition(int n, int nblk, int groups, int2* dev_table, cudaStream_t st);

@@ -302,19 +302,29 @@ __device__ __forceinline__ double fx_below(int e) { return e == 0 ? 0x1.0p-1022 
 // Same iterates as the two-reduction kernel in exact arithmetic; convergence is
 // confirmed on the true residual as there.
 // G: stencil groups per block (the tile shape of the sweeps: G tiles of 32 x kTY positions
-// in flight per block, kGroupWarps warps each).
-template <int G>
-__global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
+// in flight per block, kGroupWarps warps each).  HW: halo warps per group in the fused
+// pass (2: G more warps at the end of the block, which sit out the other sweeps).
+template <int G, int HW = 1>
+__global__ void __launch_bounds__(32 * (kGroupWarps + HW - 1) * G, kPcgBlocksPerSM)
+    pcg_fused_kernel(PcgArgs a, FusedBufs fb) {
   if (pcg_halted(a.halt, a.out)) return;
   __shared__ union { SweepSmemT<double, G> s; FusedFxSmemBlockG<G> f; } sm;
   __shared__ double red[32];
   __shared__ double gs[2];
   __shared__ int gm[3];
+  // the stencil sweeps other than the fused pass run on the G x kGroupWarps group warps
+  const bool in_groups = HW == 1 || threadIdx.x < 32 * kGroupWarps * G;
+  auto sweep_S = [&](const Geom& g, const double* src, const Box& box, int part, int nparts, auto& smem, auto& ep) {
+    if (in_groups) sweep_L(g, src, box, part, nparts, smem, ep);
+  };
   const int nb = gridDim.x, bid = blockIdx.x;
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
-  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  // the elementwise loops run on the group warps only, so that every form with G groups
+  // sums in the same order (the extra halo warps of HW = 2 add exact zeros)
+  const int gth = HW == 1 ? (int)blockDim.x : 32 * kGroupWarps * G;
+  const long long tid = in_groups ? (long long)bid * gth + threadIdx.x : len, nth = (long long)nb * gth;
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
     return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
   };
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
   double rr = 0.0, bb = 0.0, start_rel = 0.0, relres = 0.0;
   if (a.init == 0) {
     EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
-    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    sweep_S(a.g, a.x, a.full, bid, nb, sm.s, ep);
     if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
   } else {
     double s0 = 0.0, s1 = 0.0;
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
   start_rel = sqrt(rr / bb);
   if (a.init != 0 && isfinite(rr) && isfinite(bb) && rr <= a.tol2 * bb) {
     EpiResidual ep{a.b, a.r, a.lx, a.g.n3};
-    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    sweep_S(a.g, a.x, a.full, bid, nb, sm.s, ep);
     double rt, bt;
     if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
     if (rt <= a.tol2 * bb) {
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
     for (;;) {
       if (restart_w) {
         EpiApplyDot ep{wb(cur), a.g.n3};
-        sweep_L(a.g, rb(cur), a.full, bid, nb, sm.s, ep);
+        sweep_S(a.g, rb(cur), a.full, bid, nb, sm.s, ep);
         double delta, dummy;
         if (!reduce2(ep.wr, 0.0, delta, dummy)) return;
         if (!(delta > 0.0)) { status = isnan(delta) ? MQS_ERR_NAN : MQS_ERR_BREAKDOWN; need_true = true; break; }
@@ -387,7 +397,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
                     58 - E, E - 58};
       double g1 = 0.0, d1 = 0.0;
       int er = 0, ew = 0, es = 0;
-      sweep_fused_fx(a.g, v, a.full, bid, nb, sm.f, g1, d1, er, ew, es, fb.ptab);
+      sweep_fused_fx<G, HW>(a.g, v, a.full, bid, nb, sm.f, g1, d1, er, ew, es, fb.ptab);
       double gn, dn;
       if (!grid_sum2_max3(g1, d1, er, ew, es, gn, dn, er, ew, es, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs,
                           gm))
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
       if (!isfinite(gn) || !isfinite(dn)) { status = MQS_ERR_NAN; need_true = true; break; }
       if (gn <= a.tol2 * bb) {
         EpiResidual ep{a.b, rb(cur), a.lx, a.g.n3};
-        sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+        sweep_S(a.g, a.x, a.full, bid, nb, sm.s, ep);
         double rt, bt;
         if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
         if (rt <= a.tol2 * bb || restarts >= 8) {
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
   }
   if (need_true) {
     EpiResidual ep{a.b, rb(cur), a.lx, a.g.n3};
-    sweep_L(a.g, a.x, a.full, bid, nb, sm.s, ep);
+    sweep_S(a.g, a.x, a.full, bid, nb, sm.s, ep);
     double rt, bt;
     if (!reduce2(ep.rr, ep.bb, rt, bt)) return;
     relres = sqrt(rt / bb);
@@ -433,15 +443,14 @@ __global__ void __launch_bounds__(32 * kGroupWarps * G, kPcgBlocksPerSM) pcg_fus
   if (bid == 0 && threadIdx.x == 0) *a.out = PcgResult{it, status, relres, start_rel};
 }
 
-static int fused_groups_ok(int groups) {
-  if (groups == kGroups) return MQS_OK;
-  if (groups != 3) return MQS_ERR_ARG;
-  // the three-group block (480 threads) must fit once per SM beside nothing else (asked once
-  // per process; a function-local static is initialised once even with concurrent callers)
+// the block of a fused-pass form must fit once per SM beside nothing else (asked once per
+// process and form; a function-local static is initialised once even with concurrent callers)
+template <int G, int HW>
+static int fused_form_fits() {
   static const int occ = [] {
     int o = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_fused_kernel<3>, 32 * kGroupWarps * 3, 0) ==
-                   cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_fused_kernel<G, HW>, 32 * (kGroupWarps + HW - 1) * G,
+                                                         0) == cudaSuccess
                ? o
                : -1;
   }();
@@ -451,7 +460,8 @@ static int fused_groups_ok(int groups) {
 
 int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, double* p, double* lx,
                      const PcgExtra& ex, double* part, unsigned* bar, int* err, PcgResult* out, double tol, int maxit,
-                     int nblk, cudaStream_t st, int init, const int* halt, int groups, const int2* ptab) {
+                     int nblk, cudaStream_t st, int init, const int* halt, int groups, const int2* ptab,
+                     int halo_warps) {
   PcgArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -462,15 +472,23 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
   a.init = init;
   a.halt = halt;
   FusedBufs fb{ex.r1, ex.w0, ex.w1, ex.s0, ex.s1, ptab};
+  if (groups == 0) groups = kGroups;
+  if (halo_warps == 0) halo_warps = 1;
+  // forms: (2 groups, 1 halo warp) 320 threads, (3, 1) 480, (2, 2) 384
+  const void* fn = nullptr;
+  int threads = 0, fits = MQS_ERR_ARG;
+  if (groups == kGroups && halo_warps == 1) {
+    fn = (const void*)pcg_fused_kernel<kGroups, 1>; threads = kBlock; fits = MQS_OK;
+  } else if (groups == 3 && halo_warps == 1) {
+    fn = (const void*)pcg_fused_kernel<3, 1>; threads = 32 * kGroupWarps * 3; fits = fused_form_fits<3, 1>();
+  } else if (groups == kGroups && halo_warps == 2) {
+    fn = (const void*)pcg_fused_kernel<kGroups, 2>; threads = 32 * (kGroupWarps + 1) * kGroups;
+    fits = fused_form_fits<kGroups, 2>();
+  }
+  if (fits != MQS_OK) return fits;
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return MQS_ERR_CUDA;
   void* args[] = {&a, &fb};
-  if (groups == 0) groups = kGroups;
-  const int gok = fused_groups_ok(groups);
-  if (gok != MQS_OK) return gok;
-  cudaError_t e = (groups == 3)
-      ? cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<3>, dim3(nblk), dim3(32 * kGroupWarps * 3), args, 0,
-                                    st)
-      : cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<kGroups>, dim3(nblk), dim3(kBlock), args, 0, st);
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblk), dim3(threads), args, 0, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -328,16 +328,30 @@ __device__ __forceinline__ int fx_expo(double v) { return (int)((__double_as_lon
 
 // ptab (nullable): plane-tile range [x, y) of every group part (part * G + group), from
 // fused_partition; else the even split of the formula below.
-template <int G>
+// HW: halo warps per group.  1: warp kTY of each group forms the whole tile halo.  2: the
+// block has G more warps after the G x kGroupWarps (warp G kGroupWarps + grp is group grp's
+// second halo warp); the first forms row j0-1 and column i0-1 of the halo and the halo
+// fluxes, the second row j0+kTY and column i0+32, each over its (position, component)
+// pairs packed 32 to a round.  With G = 2 that is 12 warps, three on each of the SM's four
+// schedulers, each issuing about the same number of FP64 instructions per plane.
+template <int G, int HW = 1>
 __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, const Box& box, int part, int nparts,
                                FusedFxSmemBlockG<G>& smb, double& gamma, double& delta, int& mer, int& mew,
                                int& mes, const int2* ptab = nullptr) {
+  static_assert(HW == 1 || HW == 2, "one or two halo warps per group");
   const FusedVecs& v = fv.v;
   const int shi = fv.sh_in, sho = fv.sh_out;
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
-  const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool extra = HW == 2 && warp >= G * kGroupWarps;     // a second halo warp
+  const int grp = extra ? warp - G * kGroupWarps : warp / kGroupWarps;
+  const int w = extra ? kTY + 1 : warp % kGroupWarps;
+  auto gsync = [&] {
+    if (HW == 1) group_sync(grp);
+    else group_sync_n<kGroupWarps + 1>(grp);
+  };
   FusedFxSmem& sg = smb.g[grp];
   const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
@@ -383,7 +397,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
     const int j0 = box.lo[1] + (int)(tc / ntx) * kTY;
     const int ks = box.lo[2] + ka, ke = ks + len;
     const int i = i0 + lane;
-    group_sync(grp);  // smem reuse across segments
+    gsync();  // smem reuse across segments
     if (w < kTY) {
       const int j = j0 + w;
       const bool act = (i < box.hi[0]) && (j < box.hi[1]);   // owned position
@@ -392,12 +406,36 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
       const bool incb = i >= g.cb_lo[0] && i < g.cb_hi[0] && j >= g.cb_lo[1] && j < g.cb_hi[1];
       const int cfc = incb ? (i - g.cb_lo[0]) + cw0 * (j - g.cb_lo[1]) : 0;
       int o = col ? i + n * (j + n * ks) : 0;
-      // prologue: plane ks (owned: updated), warm-up fluxes at ks - 1 from recomputed sources
+      // prologue: plane ks (owned: updated), warm-up fluxes at ks - 1 from recomputed sources;
+      // the warm-up plane's inputs (x, y, z at the position, z at i+1 and at j+1) are loaded
+      // together with plane ks, before the update's stores
       double skd[3] = {0.0, 0.0, 0.0};
       long long sk[3] = {0, 0, 0};
+      const bool wu = ks >= 1 && col;
+      long long wm[5] = {0, 0, 0, 0, 0};   // the warm-up plane's r_{i+1}, as fused_src forms it
       if (col) {
         FusedLoadT<double> L0;
         fused_load(v, o, n3, act, L0);
+        if (wu) {
+          const int om = o - n2;
+          double wr[5] = {}, ww[5] = {}, ws[5] = {};
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const bool okq = q < 3 || (q == 3 ? i + 1 < n : j + 1 < n);
+            const int oq = q < 3 ? om + q * n3 : (q == 3 ? om + 1 + 2 * n3 : om + n + 2 * n3);
+            if (okq) {
+              ww[q] = MQS_LDC(v.w_in, oq, 3 * n3, 337);
+              ws[q] = v.first ? 0.0 : MQS_LDC(v.s_in, oq, 3 * n3, 338);
+              wr[q] = MQS_LDC(v.r_in, oq, 3 * n3, 339);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const bool okq = q < 3 || (q == 3 ? i + 1 < n : j + 1 < n);
+            const double sv = v.first ? ww[q] : fma(v.beta, ws[q], ww[q]);
+            wm[q] = okq ? fx_from_double(fma(-v.alpha, sv, wr[q]), shi) : 0;
+          }
+        }
         if (act) own_apply(o, L0, skd);
         else other_apply(L0, skd);
       }
@@ -407,18 +445,14 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
         sg.src[ks & 1][c][w + 1][lane + 1] = sk[c];
       }
       long long bxm = 0, bym = 0;
-      if (ks >= 1 && col) {
-        const int om = o - n2;
-        const long long xm = fx_from_double(fused_src(v, om, n3), shi), ym = fx_from_double(fused_src(v, om + n3, n3), shi);
-        const long long zm = fx_from_double(fused_src(v, om + 2 * n3, n3), shi);
-        const long long zim = (i + 1 < n) ? fx_from_double(fused_src(v, om + 1 + 2 * n3, n3), shi) : 0;
-        const long long zjm = (j + 1 < n) ? fx_from_double(fused_src(v, om + n + 2 * n3, n3), shi) : 0;
-        bxm = (ym - zm) + (zjm - sk[1]);
-        bym = (zm - xm) + (sk[0] - zim);
+      if (wu) {
+        bxm = (wm[1] - wm[2]) + (wm[4] - sk[1]);
+        bym = (wm[2] - wm[0]) + (sk[0] - wm[3]);
       }
-      group_sync(grp);
+      // inputs of plane ks+1 (nobody else writes them), in flight across the barrier
       FusedLoadT<double> ld1;
       if (col && ks + 1 < n) fused_load(v, o + n2, n3, act && ks + 1 < ke, ld1);
+      gsync();
       int buf = ks & 1;
       for (int k = ks; k < ke; ++k, o += n2) {
         const int nb = buf ^ 1;
@@ -443,7 +477,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
         const long long bz = (sk[0] - sk[1]) + (yi - xj);
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
-        group_sync(grp);
+        gsync();
         long long bzi = shfl_up1(bz), byi = shfl_up1(by);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
         const long long bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
@@ -463,6 +497,83 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
         bxm = bx; bym = by;
 #pragma unroll
         for (int c = 0; c < 3; ++c) { sk[c] = sk1[c]; skd[c] = sk1d[c]; }
+        buf = nb;
+      }
+    } else if (HW == 2) {
+      // two halo warps: hw 0 forms rows j0-1 (columns i0-1 .. i0+32) and column i0-1 (rows
+      // j0 .. j0+kTY-1) of plane k+1 and the halo fluxes of plane k, which need only its own
+      // plane k+1 values; hw 1 forms row j0+kTY and column i0+32, read from plane k on
+      const int hw = w - kTY;
+      constexpr int kHSlots = 34 + kTY;
+      constexpr int kHPairs = 3 * kHSlots;
+      constexpr int kHR = (kHPairs + 31) / 32;
+      // pair p: component p / kHSlots at the warp's slot p % kHSlots
+      auto pair_pos = [&](int p, int& c, int& hi, int& hj, int& row, int& cl) {
+        c = p / kHSlots;
+        const int sl = p - c * kHSlots;
+        if (sl < 34) { hi = i0 - 1 + sl; hj = hw ? j0 + kTY : j0 - 1; row = hw ? kTY + 1 : 0; cl = sl; }
+        else { hi = hw ? i0 + 32 : i0 - 1; hj = j0 + (sl - 34); row = sl - 34 + 1; cl = hw ? 33 : 0; }
+      };
+      struct HaloIn2 { double r, w, s; };
+      auto halo_load = [&](int kk, HaloIn2* hin) {
+#pragma unroll
+        for (int q = 0; q < kHR; ++q) {
+          const int p = lane + 32 * q;
+          int c = 0, hi = -1, hj = -1, row = 0, cl = 0;
+          if (p < kHPairs) pair_pos(p, c, hi, hj, row, cl);
+          const bool ok = p < kHPairs && hi >= 0 && hj >= 0 && hi < n && hj < n && kk >= 0 && kk < n;
+          const int oo = ok ? hi + n * (hj + n * kk) + c * n3 : 0;
+          hin[q].r = ok ? MQS_LDC(v.r_in, oo, 3 * n3, 334) : 0.0;
+          hin[q].w = ok ? MQS_LDC(v.w_in, oo, 3 * n3, 335) : 0.0;
+          hin[q].s = (ok && !v.first) ? MQS_LDC(v.s_in, oo, 3 * n3, 336) : 0.0;
+        }
+      };
+      auto halo_store = [&](const HaloIn2* hin, int bufw) {
+#pragma unroll
+        for (int q = 0; q < kHR; ++q) {
+          const int p = lane + 32 * q;
+          if (p >= kHPairs) continue;
+          int c, hi, hj, row, cl;
+          pair_pos(p, c, hi, hj, row, cl);
+          const double sv = v.first ? hin[q].w : fma(v.beta, hin[q].s, hin[q].w);
+          sg.src[bufw][c][row][cl] = fx_from_double(fma(-v.alpha, sv, hin[q].r), shi);
+        }
+      };
+      // planes ks and ks+1 loaded together
+      HaloIn2 h[kHR], h1[kHR];
+      halo_load(ks, h);
+      halo_load(ks + 1, h1);
+      halo_store(h, ks & 1);
+#pragma unroll
+      for (int q = 0; q < kHR; ++q) h[q] = h1[q];
+      gsync();
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k) {
+        const int nb = buf ^ 1;
+        halo_store(h, nb);                     // plane k+1, loaded during the previous step
+        if (k + 2 <= ke) halo_load(k + 2, h);  // in flight until the next step
+        if (hw == 0) {
+          __syncwarp();
+          // row j0-1 and column i0-1 fluxes of plane k, as for one halo warp
+          const long long x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
+          const long long z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
+          const long long xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
+          const long long yk = sg.src[nb][1][0][lane + 1];
+          const bool hrow = (j0 >= 1) && (i < n);
+          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : 0;
+          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : 0;
+          if (lane < kTY) {
+            const int r = lane + 1;
+            const long long cx0 = sg.src[buf][0][r][0], cy0 = sg.src[buf][1][r][0], cz0 = sg.src[buf][2][r][0];
+            const long long cyi = sg.src[buf][1][r][1], czi = sg.src[buf][2][r][1];
+            const long long cxj = sg.src[buf][0][r + 1][0];
+            const long long cxk = sg.src[nb][0][r][0];
+            const bool hcol = (i0 >= 1) && (j0 + lane < n);
+            sg.hz[buf][lane] = hcol ? (cx0 - cy0) + (cyi - cxj) : 0;
+            sg.hy[buf][lane] = hcol ? (cz0 - cx0) + (cxk - czi) : 0;
+          }
+        }
+        gsync();
         buf = nb;
       }
     } else {
@@ -511,7 +622,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
       halo_load(ks, h);
       halo_store(h, ks & 1);
       halo_load(ks + 1, h);
-      group_sync(grp);
+      gsync();
       int buf = ks & 1;
       for (int k = ks; k < ke; ++k) {
         const int nb = buf ^ 1;
@@ -537,7 +648,7 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
           sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : 0;
           sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : 0;
         }
-        group_sync(grp);
+        gsync();
         buf = nb;
       }
     }

@@ -142,11 +142,11 @@ def test_batch_tune_and_argument_checks(pkg):
     best = batch.tune(1)
     assert best in (1.0, 2.0, 4.0, 8.0) and batch.weighting() in (False, True)
     forms = batch.tune_pcg(1)                    # one form per (grid size, precision) group
-    assert len(forms) == len(sv) and all(v[0] in (0, 1, 2) and v[1] in (0, 2, 3) for v in forms)
+    assert len(forms) == len(sv) and all(v[0] in (0, 1, 2) and v[1] in (0, 2, 3) and v[2] in (0, 1, 2) for v in forms)
     groups = {}
     for s_, v in zip(sv, forms):
         groups.setdefault((s_.n, s_.options.precision), set()).add(v)
-        assert (s_.options.pcg_variant, s_.options.tile_groups) == v
+        assert s_.pcg_form() == v
     assert all(len(g) == 1 for g in groups.values())
     _, stats = batch.step(3)
     assert all(x.status == 0 for row in stats for x in row)

@@ -434,9 +434,12 @@ def test_bench_configuration_against_the_oracle(pkg):
     dt = g64["dt"]
     steps = 30
     ref = O.run_explicit_euler(d, dt, steps, start_mode=START_SPE, spe_depth=8, tol=1e-10, eps_lin=1e-10)
-    # pcg_variant 1 (one reduction per iteration, the benchmark's kernel) and 0
-    for variant in (1, 0):
-        s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, eps_lin=1e-10, pcg_variant=variant)
+    # pcg_variant 1 (one reduction per iteration, the benchmark's kernel) with one and with
+    # two halo warps per tile group (bitwise the same iterates), and pcg_variant 0
+    fused = None
+    for variant, halo in ((1, 0), (1, 2), (0, 0)):
+        s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, eps_lin=1e-10, pcg_variant=variant,
+                 halo_warps=halo)
         # the benchmark's own step comes from the GPU power method: the same lambda_max
         lam, _ = s.lambda_max(W.power_start_vector(s.n_c), pcg_tol=1e-12, rtol=1e-8, maxit=2000)
         assert lam == pytest.approx(g64["lambda_max"], rel=1e-6)
@@ -452,6 +455,11 @@ def test_bench_configuration_against_the_oracle(pkg):
         assert rel(d.K_cn @ w, d.K_cn @ ref.w) < 1e-8, variant
         its = np.array([st.iterations for st in stats])
         assert np.abs(its - ref.iterations).max() <= 3, (variant, its.tolist(), ref.iterations.tolist())
+        if variant == 1:
+            if fused is None:
+                fused = (a_c, its)
+            else:
+                assert np.array_equal(a_c, fused[0]) and np.array_equal(its, fused[1])
         s.close()
 
 
@@ -498,14 +506,16 @@ def test_paper_sized_grid(pkg):
     s.close()
 
 
-@pytest.mark.parametrize("variant,groups", [(0, 0), (1, 2), (1, 3)])
-def test_both_pcg_variants_match_the_oracle(pkg, variant, groups):
-    # groups: stencil tile groups per block of the one-reduction pass (3: 480-thread blocks)
+@pytest.mark.parametrize("variant,groups,halo", [(0, 0, 0), (1, 2, 1), (1, 3, 1), (1, 2, 2)])
+def test_both_pcg_variants_match_the_oracle(pkg, variant, groups, halo):
+    # groups: stencil tile groups per block of the one-reduction pass (3: 480-thread blocks);
+    # halo: halo warps per group (2: 384-thread blocks)
     p = W.scaled_nonlinear(24, amplitude=5e4)
     d = O.Discretization(p)
     dt = O.dt_gershgorin(d)
     ref = O.run_explicit_euler(d, dt, 20, start_mode=START_SPE, spe_depth=8, tol=1e-10)
-    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, pcg_variant=variant, tile_groups=groups)
+    s = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, tol=1e-10, pcg_variant=variant, tile_groups=groups,
+             halo_warps=halo)
     stats = s.mqs_step(20)
     a_c, _, _ = s.get_state()
     assert rel(a_c, ref.a_c) < 1e-8
@@ -519,7 +529,8 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant, groups):
     s.close()
 
 
-@pytest.mark.parametrize("precision,choices", [(0, ((0, 0), (1, 2), (1, 3))), (1, ((0, 0), (1, 0), (2, 0)))])
+@pytest.mark.parametrize("precision,choices", [(0, ((0, 0, 0), (1, 2, 1), (1, 3, 1), (1, 2, 2))),
+                                               (1, ((0, 0, 0), (1, 0, 0), (2, 0, 0)))])
 def test_pcg_form_tuner_keeps_the_state_and_the_trajectory(pkg, precision, choices):
     # mqs_tune_pcg times the kernel forms on trial solves between steps: the state, the
     # step counter and the start-vector history stay as they were, and the steps after it
@@ -532,7 +543,7 @@ def test_pcg_form_tuner_keeps_the_state_and_the_trajectory(pkg, precision, choic
     s.mqs_step(8)
     a0, t0, m0 = s.get_state()
     v = s.tune_pcg(2)
-    assert v in choices and (s.options.pcg_variant, s.options.tile_groups) == v
+    assert v in choices and s.pcg_form() == v
     a1, t1, m1 = s.get_state()
     assert np.array_equal(a0, a1) and (t0, m0) == (t1, m1)
     stats = s.mqs_step(8)
