@@ -470,6 +470,10 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
         }
         // then issue the loads of plane k+2
         if (col && k + 2 < n && k + 1 < ke) fused_load(v, o + 2 * n2, n3, act && k + 2 < ke, ld1);
+        // conductor flags of plane k (edges of K_c), loaded ahead of their use after the barrier
+        const unsigned cfk = (act && incb && k >= g.cb_lo[2] && k < g.cb_hi[2])
+                                 ? (unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])]
+                                 : 0u;
         const long long yi = sg.src[buf][1][w + 1][lane + 2], zi = sg.src[buf][2][w + 1][lane + 2];
         const long long xj = sg.src[buf][0][w + 2][lane + 1], zj = sg.src[buf][2][w + 2][lane + 1];
         const long long bx = (sk[1] - sk[2]) + (zj - sk1[1]);
@@ -477,19 +481,22 @@ __device__ inline void sweep_fused_fx(const Geom& g, const FusedFxVecs& fv, cons
         const long long bz = (sk[0] - sk[1]) + (yi - xj);
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
+        // gamma needs only this plane's r_{i+1}: summed before the barrier
+        if (act) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gamma = fma(skd[c], skd[c], gamma);
+        }
         gsync();
         long long bzi = shfl_up1(bz), byi = shfl_up1(by);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
         const long long bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
         if (act) {
           const long long t[3] = {(bz - bzj) + (bym - by), (bzi - bz) + (bx - bxm), (bxj - bx) + (by - byi)};
-          unsigned m = mcol & (k > 0 ? 7u : 4u);
-          if (incb && k >= g.cb_lo[2] && k < g.cb_hi[2]) m &= ~(unsigned)g.cflags[cfc + cw01 * (k - g.cb_lo[2])];
+          const unsigned m = mcol & (k > 0 ? 7u : 4u) & ~cfk;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const double wv = (m >> c & 1u) ? fx_to_double(t[c], sho) : 0.0;
             MQS_STC(v.w_out, o + c * n3, 3 * n3, 320, wv);
-            gamma = fma(skd[c], skd[c], gamma);
             delta = fma(wv, skd[c], delta);
             mew = max(mew, fx_expo(wv));
           }
