@@ -47,6 +47,12 @@ def test_setup_rejects_bad_inputs(pkg):
         pkg.Solver.from_problem(bad, pkg.SolverOptions())
     with pytest.raises(pkg.MqsError):
         pkg.Solver.from_problem(p, pkg.SolverOptions(spe_depth=99))
+    # kernel forms that do not exist: a tile-group count other than 2 or 3, halo warps other
+    # than 1 or 2, two halo warps beside three tile groups (576 threads)
+    for bad_form in (dict(tile_groups=4), dict(halo_warps=3), dict(halo_warps=-1),
+                     dict(tile_groups=3, halo_warps=2)):
+        with pytest.raises(pkg.MqsError):
+            pkg.Solver.from_problem(p, pkg.SolverOptions(pcg_variant=1, **bad_form))
     s = pkg.Solver.from_problem(p, pkg.SolverOptions())
     with pytest.raises(pkg.MqsError):
         s.step(1)                                                                     # dt not set
