@@ -60,11 +60,13 @@ def test_apply_kn_matches_assembled_matrix(pkg, N):
 
 
 # ---- (a4) PCG ---------------------------------------------------------------------------
+# kernel forms (pcg_variant, tile_groups, halo_warps); 35 = 32 + 3 leaves ragged tiles in x and y
+@pytest.mark.parametrize("form", [(0, 0, 0), (1, 2, 1), (1, 3, 1), (1, 2, 2)])
 @pytest.mark.parametrize("N", [16, 35])
-def test_pcg_solve_matches_oracle(pkg, N):
+def test_pcg_solve_matches_oracle(pkg, N, form):
     p = W.scaled_nonlinear(N)
     d = O.Discretization(p)
-    s = make(pkg, p)
+    s = make(pkg, p, pcg_variant=form[0], tile_groups=form[1], halo_warps=form[2])
     a_c = W.random_vector(7, d.n_c) * 1e-9
     b_n = 3.0 * d.X_s[d.n_idx] - d.K_cn.T @ a_c
     ref = O.pcg_jacobi(d.K_n, b_n, None, d.D, tol=1e-10)
@@ -93,13 +95,14 @@ def _oracle_solve_96():
     return _REF96
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (1, 1), (1, 2)])
-def test_two_blocks_per_sm_solve_matches_oracle_at_96(pkg, precision, variant):
-    # from 96^3 on the FP64 PCG and the FP32-inner refinement run two blocks per SM
-    # (the kernels' second instantiation); their solve against the oracle's
+@pytest.mark.parametrize("precision,variant,halo", [(0, 0, 0), (0, 1, 0), (0, 1, 2), (1, 1, 0), (1, 2, 0)])
+def test_two_blocks_per_sm_solve_matches_oracle_at_96(pkg, precision, variant, halo):
+    # from 96^3 on the two-reduction FP64 PCG and the FP32-inner refinement run two blocks
+    # per SM (the kernels' second instantiation); the one-reduction FP64 pass keeps one, in
+    # both halo forms; every solve against the oracle's
     r = _oracle_solve_96()
     p, d, b_n, ref = r["p"], r["d"], r["b_n"], r["ref"]
-    s = make(pkg, p, precision=precision, pcg_variant=variant)
+    s = make(pkg, p, precision=precision, pcg_variant=variant, halo_warps=halo)
     b_o = np.zeros(d.grid.n_edges)
     b_o[d.n_idx] = b_n
     x_l, info = s.pcg_solve(oracle_to_layout(96, b_o), tol=1e-10)
