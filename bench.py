@@ -424,8 +424,7 @@ def run_ours(args, rank, ws, local, dist):
                 t1 = time.perf_counter()
                 s.set_state(a_host, t_cur, m_cur)
                 _, st1 = s.step(1, allow_fail=True)
-                a_new, t_cur, m_cur = s.get_state()
-                a_host[:] = a_new
+                _, t_cur, m_cur = s.get_state(out=a_host)
                 el += time.perf_counter() - t1
                 e2e_its.append(st1[0].iterations)
         el_max = reduce_max(el, dist, dev)

@@ -421,8 +421,16 @@ class Solver:
         """Persistent blocks of this handle's PCG kernels (0 = one per SM)."""
         self._check(self.lib.mqs_set_blocks(self.h, nblk))
 
-    def get_state(self):
-        a = np.empty(self.n_c)
+    def get_state(self, out=None):
+        """(a_c, t, m).  out (optional): a C-contiguous float64 array of n_c values (pinned
+        host memory, for one) that receives a_c and is returned."""
+        if out is None:
+            a = np.empty(self.n_c)
+        else:
+            if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+                    and out.flags.writeable and out.size == self.n_c):
+                raise ValueError(f"out must be a writeable C-contiguous float64 array of {self.n_c} values")
+            a = out
         t, m = C.c_double(), C.c_long()
         self._check(self.lib.mqs_get_state(self.h, _dp(a), a.size, C.byref(t), C.byref(m)))
         return a, t.value, m.value

@@ -56,3 +56,15 @@ def test_handle_dev_wrappers_reject_wrong_tensors():
         s.get_state_dev(torch.zeros(s.n_c, dtype=torch.float32))
     with pytest.raises(ValueError, match="CUDA"):
         s.get_state_dev(torch.zeros(s.n_c, dtype=torch.float64))
+
+
+def test_get_state_rejects_a_wrong_output_buffer():
+    # get_state(out=...) writes a_c into the caller's host array: only a writeable
+    # C-contiguous float64 array of n_c values is accepted
+    s = _bare_solver(4)
+    bad = [np.zeros(s.n_c, dtype=np.float32), np.zeros(s.n_c + 1), np.zeros(2 * s.n_c)[::2], [0.0] * s.n_c]
+    ro = np.zeros(s.n_c)
+    ro.flags.writeable = False
+    for out in bad + [ro]:
+        with pytest.raises(ValueError, match="float64"):
+            s.get_state(out=out)
