@@ -319,13 +319,14 @@ def other_arithmetic(args, p, dt, stream, flush, dev):
     for name, prec, var in (("f32+f64", 1, 1), ("ff+f64", 2, 1)):
         so = pkg.Solver.from_problem(p, pkg.SolverOptions(tol=1e-10, start_mode=pkg.START_SPE, spe_depth=8,
                                                           dt=dt, precision=prec, pcg_variant=var,
-                                                          graph=args.graph))
+                                                          halo_warps=args.halo_warps, graph=args.graph))
         so.set_stream(stream.cuda_stream)
         ms, sts = timed_steps(so, args.steps, args.warmup, stream, flush, dev)
         so.close()
         out[name] = {"value": args.steps / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms / args.steps,
                      "iters_per_step": sum(x.iterations for x in sts) / len(sts),
-                     "failed_steps": sum(1 for x in sts if x.status != 0)}
+                     "failed_steps": sum(1 for x in sts if x.status != 0),
+                     "halo_warps": max(args.halo_warps, 1) if (prec, var) == (1, 1) and p.N < 96 else 1}
     return out
 
 
@@ -630,7 +631,8 @@ def size_sweep(sizes):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for n in sizes:
         p = W.config_nonlinear_iron() if n == 64 else W.scaled_nonlinear(n)
-        for prec, var, groups, halo in ((0, 1, 0, 0), (0, 1, 3, 0), (0, 1, 0, 2), (1, 1, 0, 0), (1, 2, 0, 0)):
+        for prec, var, groups, halo in ((0, 1, 0, 0), (0, 1, 3, 0), (0, 1, 0, 2), (1, 1, 0, 0), (1, 1, 0, 2),
+                                        (1, 2, 0, 0)):
             s = pkg.Solver.from_problem(p, pkg.SolverOptions(start_mode=pkg.START_ZERO, dt=1e-7, precision=prec,
                                                              pcg_variant=var, tile_groups=groups, halo_warps=halo))
             stream = torch.cuda.Stream(device=dev)
@@ -1015,8 +1017,8 @@ def main():
                     help="0: two grid reductions per PCG iteration, 1: one (fused pass; default), 2: with "
                          "--precision 1, the inner pass carrying x, r, p only (24 B per unknown)")
     ap.add_argument("--halo-warps", type=int, default=2, choices=[0, 1, 2],
-                    help="FP64 one-reduction pass: halo warps per tile group (0/1: one; 2: two, in 384-thread "
-                         "blocks, the default)")
+                    help="one-reduction passes (FP64, and the FP32 inner pass below 96^3): halo warps per tile "
+                         "group (0/1: one; 2: two, in 384-thread blocks, the default)")
     ap.add_argument("--grid", type=int, default=64,
                     help="cells per axis of the iron workload (64: the benchmark; others scale it)")
     ap.add_argument("--dt", type=float, default=0.0, help="time step in s (default: 0.9 * 2 / lambda_max)")

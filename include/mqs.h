@@ -196,14 +196,16 @@ typedef struct {
                              (more warps to hide latency, fewer registers per
                              thread).  mqs_tune_pcg chooses it with the form.
                              Other precisions and forms use 2. */
-    int    halo_warps;    /* warps per tile group of that pass that form the
-                             tile's halo (the sources and fluxes of the positions
-                             next to the tile, which the neighbouring tiles own).
-                             0 or 1 (default): one; 2 (with two tile groups only):
-                             two, each over half of the halo, in 384-thread blocks
-                             (three warps on each of the SM's four schedulers).
-                             The iterates are bitwise the same.  mqs_tune_pcg
-                             chooses it with the form. */
+    int    halo_warps;    /* warps per tile group of that pass, and of the FP32
+                             inner pass of precision 1 with pcg_variant 1 below
+                             96^3, that form the tile's halo (the sources and
+                             fluxes of the positions next to the tile, which the
+                             neighbouring tiles own).  0 or 1 (default): one; 2
+                             (with two tile groups only): two, each over half of
+                             the halo, in 384-thread blocks (three warps on each
+                             of the SM's four schedulers).  The iterates are
+                             bitwise the same.  Other forms ignore it.
+                             mqs_tune_pcg chooses it with the form. */
 } mqs_options;
 
 typedef struct {
@@ -553,8 +555,9 @@ int mqs_set_blocks(mqs_handle* h, int nblk);
  * per iteration) and 1 (one fused pass carrying x, p, r, w, s) on 2 tile groups
  * per block with one or two halo warps each and on 3 (tile_groups,
  * halo_warps); precision 1,
- * pcg_variant 0, 1 (one reduction, five carried vectors) and 2 (three carried
- * vectors, a two-deep halo staged by cp.async); precision 2 has one form.
+ * pcg_variant 0, 1 (one reduction, five carried vectors; one or two halo warps)
+ * and 2 (three carried vectors, a two-deep halo staged by cp.async); precision 2
+ * has one form.
  * Each candidate solves K_n x = b from x = 0, b the coil's pattern at unit
  * current with the conductors at rest, trials + 1 times on the handle's stream
  * and block count; the first solve is untimed and the fastest median (CUDA

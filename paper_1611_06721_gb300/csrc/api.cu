@@ -385,7 +385,8 @@ int pcg_launch(mqs_handle* H, const double* b, double* x, double tol, int maxit,
     const double itol = H->opt.inner_tol > 0.0 ? H->opt.inner_tol : 1e-5;
     const bool tab = H->ptab_nblk == H->nblk && H->ptab_groups == kGroups;
     return launch_pcg_mixed(H->dg, b, x, H->r, H->lx, mb, H->part, H->bar, H->derr, H->pres, H->refin, tol, itol,
-                            maxit, H->nblk, st, init, H->opt.pcg_variant, halt, tab ? H->ptab : nullptr);
+                            maxit, H->nblk, st, init, H->opt.pcg_variant, halt, tab ? H->ptab : nullptr,
+                            H->opt.halo_warps);
   }
   if (H->opt.pcg_variant >= 1) {
     const PcgExtra ex{H->r1, H->w0, H->w1, H->q, H->s1};
@@ -2106,9 +2107,9 @@ int mqs_set_blocks(mqs_handle* H, int nblk) {
 
 // Kernel-form tuner: the PCG forms that compute the same iterates (precision 0: the
 // two-reduction kernel and the one-reduction fused pass on two tile groups with one or two
-// halo warps each and on three; precision 1: the FP32 inner CG
-// with two reductions, with one reduction carrying five vectors, and with one reduction
-// carrying three vectors over a two-deep halo) differ in their tiles' halo depth, staging
+// halo warps each and on three; precision 1: the FP32 inner CG with two reductions, with
+// one reduction carrying five vectors (one or two halo warps per group), and with one
+// reduction carrying three vectors over a two-deep halo) differ in their tiles' halo depth, staging
 // and traffic, and which is fastest depends on the grid size and the block count.  Each
 // candidate solves K_n x = b_coil (the coil's pattern, unit current, the conductors at
 // rest) from zero, trials + 1 times on the handle's stream and block count (the first
@@ -2124,8 +2125,9 @@ int mqs_tune_pcg(mqs_handle* H, int trials, int* chosen) {
     for (nc = 0; nc < 4; ++nc)
       for (int q = 0; q < 3; ++q) cand[nc][q] = f[nc][q];
   } else if (H->opt.precision == 1) {
-    for (int v = 0; v < 3; ++v) cand[v][0] = v;
-    nc = 3;
+    const int f[4][3] = {{0, 0, 0}, {1, 0, 0}, {1, 0, 2}, {2, 0, 0}};
+    for (nc = 0; nc < 4; ++nc)
+      for (int q = 0; q < 3; ++q) cand[nc][q] = f[nc][q];
   } else {
     cand[0][0] = H->opt.pcg_variant;    // one float-float inner form
     nc = 1;

@@ -55,10 +55,12 @@ struct MixedBufs {
   float* r32; float* p32; float* q32; float* d32;
   float* r32b; float* w32a; float* w32b; float* s32a; float* s32b;   // one-reduction inner CG only
 };
+// halo_warps 2: the one-reduction inner pass (variant 1) with two halo warps per group in
+// 384-thread blocks, at one block per SM (below 96^3); other forms ignore it
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                      double inner_tol, int maxit, int nblk, cudaStream_t st, int init = 0, int variant = 0,
-                     const int* halt = nullptr, const int2* ptab = nullptr);
+                     const int* halt = nullptr, const int2* ptab = nullptr, int halo_warps = 0);
 // precision 2: the same refinement with float-float one-reduction inner solves
 // (MixedBufs sized for 8 bytes per value, all nine buffers)
 int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,

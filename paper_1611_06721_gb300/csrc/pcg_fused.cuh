@@ -116,13 +116,23 @@ __device__ __forceinline__ void fused_apply(const FusedVecsT<T>& v, int o, int n
 // One fused pass over `box` for group-part `part` of `nparts` (block level,
 // as in sweep_L).  Accumulates gamma and delta into the caller's registers.
 // ptab (nullable): the part ranges of fused_partition (kGroups groups per block)
-template <class T>
+// HW: halo warps per group, as in sweep_fused_fx (2: kGroups more warps at the end of the
+// block, each group's second halo warp forming row j0+kTY and column i0+32).
+template <class T, int HW = 1>
 __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& box, int part, int nparts,
                             FusedSmemBlockT<T>& smb, T& gamma, T& delta, const int2* ptab = nullptr) {
+  static_assert(HW == 1 || HW == 2, "one or two halo warps per group");
   const int n = g.n;
   const int n2 = n * n;
   const int n3 = (int)g.n3;
-  const int lane = threadIdx.x & 31, grp = (threadIdx.x >> 5) / kGroupWarps, w = (threadIdx.x >> 5) % kGroupWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool extra = HW == 2 && warp >= kGroups * kGroupWarps;     // a second halo warp
+  const int grp = extra ? warp - kGroups * kGroupWarps : warp / kGroupWarps;
+  const int w = extra ? kTY + 1 : warp % kGroupWarps;
+  auto gsync = [&] {
+    if (HW == 1) group_sync(grp);
+    else group_sync_n<kGroupWarps + 1>(grp);
+  };
   FusedSmemT<T>& sg = smb.g[grp];
   const int bx0 = box.hi[0] - box.lo[0], by0 = box.hi[1] - box.lo[1], nz = box.hi[2] - box.lo[2];
   if (bx0 <= 0 || by0 <= 0 || nz <= 0) return;
@@ -143,7 +153,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
     const int j0 = box.lo[1] + (int)(tc / ntx) * kTY;
     const int ks = box.lo[2] + ka, ke = ks + len;
     const int i = i0 + lane;
-    group_sync(grp);  // smem reuse across segments
+    gsync();  // smem reuse across segments
     if (w < kTY) {
       const int j = j0 + w;
       const bool act = (i < box.hi[0]) && (j < box.hi[1]);   // owned position
@@ -167,7 +177,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
         bxm = (ym - zm) + (zjm - sk[1]);
         bym = (zm - xm) + (sk[0] - zim);
       }
-      group_sync(grp);
+      gsync();
       // inputs of plane ks+1, loaded ahead of use
       FusedLoadT<T> ld1;
       if (col && ks + 1 < n) fused_load(v, o + n2, n3, act && ks + 1 < ke, ld1);
@@ -189,7 +199,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
         const T bz = (sk[0] - sk[1]) + (yi - xj);
         sg.fz[buf][w + 1][lane] = bz;
         sg.fx[buf][w + 1][lane] = bx;
-        group_sync(grp);
+        gsync();
         T bzi = shfl_up1(bz), byi = shfl_up1(by);
         if (lane == 0) { bzi = sg.hz[buf][w]; byi = sg.hy[buf][w]; }
         const T bzj = sg.fz[buf][w][lane], bxj = sg.fx[buf][w][lane];
@@ -211,6 +221,79 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
         bxm = bx; bym = by;
 #pragma unroll
         for (int c = 0; c < 3; ++c) sk[c] = sk1[c];
+        buf = nb;
+      }
+    } else if (HW == 2) {
+      // two halo warps, as in sweep_fused_fx: hw 0 forms row j0-1 and column i0-1 of plane
+      // k+1 and the halo fluxes of plane k; hw 1 row j0+kTY and column i0+32
+      const int hw = w - kTY;
+      constexpr int kHSlots = 34 + kTY;
+      constexpr int kHPairs = 3 * kHSlots;
+      constexpr int kHR = (kHPairs + 31) / 32;
+      auto pair_pos = [&](int p, int& c, int& hi, int& hj, int& row, int& cl) {
+        c = p / kHSlots;
+        const int sl = p - c * kHSlots;
+        if (sl < 34) { hi = i0 - 1 + sl; hj = hw ? j0 + kTY : j0 - 1; row = hw ? kTY + 1 : 0; cl = sl; }
+        else { hi = hw ? i0 + 32 : i0 - 1; hj = j0 + (sl - 34); row = sl - 34 + 1; cl = hw ? 33 : 0; }
+      };
+      struct HaloIn2 { T r, w, s; };
+      auto halo_load = [&](int kk, HaloIn2* hin) {
+#pragma unroll
+        for (int q = 0; q < kHR; ++q) {
+          const int p = lane + 32 * q;
+          int c = 0, hi = -1, hj = -1, row = 0, cl = 0;
+          if (p < kHPairs) pair_pos(p, c, hi, hj, row, cl);
+          const bool ok = p < kHPairs && hi >= 0 && hj >= 0 && hi < n && hj < n && kk >= 0 && kk < n;
+          const int oo = ok ? hi + n * (hj + n * kk) + c * n3 : 0;
+          hin[q].r = ok ? MQS_LDC(v.r_in, oo, 3 * n3, 340) : T(0);
+          hin[q].w = ok ? MQS_LDC(v.w_in, oo, 3 * n3, 341) : T(0);
+          hin[q].s = (ok && !v.first) ? MQS_LDC(v.s_in, oo, 3 * n3, 342) : T(0);
+        }
+      };
+      auto halo_store = [&](const HaloIn2* hin, int bufw) {
+#pragma unroll
+        for (int q = 0; q < kHR; ++q) {
+          const int p = lane + 32 * q;
+          if (p >= kHPairs) continue;
+          int c, hi, hj, row, cl;
+          pair_pos(p, c, hi, hj, row, cl);
+          const T sv = v.first ? hin[q].w : fmaT(v.beta, hin[q].s, hin[q].w);
+          sg.src[bufw][c][row][cl] = fmaT(-v.alpha, sv, hin[q].r);
+        }
+      };
+      HaloIn2 h[kHR], h1[kHR];
+      halo_load(ks, h);
+      halo_load(ks + 1, h1);
+      halo_store(h, ks & 1);
+#pragma unroll
+      for (int q = 0; q < kHR; ++q) h[q] = h1[q];
+      gsync();
+      int buf = ks & 1;
+      for (int k = ks; k < ke; ++k) {
+        const int nb = buf ^ 1;
+        halo_store(h, nb);                     // plane k+1, loaded during the previous step
+        if (k + 2 <= ke) halo_load(k + 2, h);  // in flight until the next step
+        if (hw == 0) {
+          __syncwarp();
+          const T x0 = sg.src[buf][0][0][lane + 1], y0 = sg.src[buf][1][0][lane + 1];
+          const T z0 = sg.src[buf][2][0][lane + 1], yi = sg.src[buf][1][0][lane + 2];
+          const T xj = sg.src[buf][0][1][lane + 1], zj = sg.src[buf][2][1][lane + 1];
+          const T yk = sg.src[nb][1][0][lane + 1];
+          const bool hrow = (j0 >= 1) && (i < n);
+          sg.fz[buf][0][lane] = hrow ? (x0 - y0) + (yi - xj) : T(0);
+          sg.fx[buf][0][lane] = hrow ? (y0 - z0) + (zj - yk) : T(0);
+          if (lane < kTY) {
+            const int r = lane + 1;
+            const T cx0 = sg.src[buf][0][r][0], cy0 = sg.src[buf][1][r][0], cz0 = sg.src[buf][2][r][0];
+            const T cyi = sg.src[buf][1][r][1], czi = sg.src[buf][2][r][1];
+            const T cxj = sg.src[buf][0][r + 1][0];
+            const T cxk = sg.src[nb][0][r][0];
+            const bool hcol = (i0 >= 1) && (j0 + lane < n);
+            sg.hz[buf][lane] = hcol ? (cx0 - cy0) + (cyi - cxj) : T(0);
+            sg.hy[buf][lane] = hcol ? (cz0 - cx0) + (cxk - czi) : T(0);
+          }
+        }
+        gsync();
         buf = nb;
       }
     } else {
@@ -263,7 +346,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
       halo_load(ks, h);
       halo_store(h, ks & 1);
       halo_load(ks + 1, h);
-      group_sync(grp);
+      gsync();
       int buf = ks & 1;
       for (int k = ks; k < ke; ++k) {
         const int nb = buf ^ 1;
@@ -291,7 +374,7 @@ __device__ void sweep_fused(const Geom& g, const FusedVecsT<T>& v, const Box& bo
           sg.hz[buf][lane] = hcol ? (x0 - y0) + (yi - xj) : T(0);
           sg.hy[buf][lane] = hcol ? (z0 - x0) + (xk - zi) : T(0);
         }
-        group_sync(grp);
+        gsync();
         buf = nb;
       }
     }

@@ -362,9 +362,13 @@ union MixedSmem {
 // BPS co-resident blocks per SM: 2 once the FP32 vectors are far beyond L2 (the inner
 // sweep is then bound by memory latency and plane syncs, and 20 warps per SM hide more
 // of both than 10; the register cap of 96 spills a little, in the FP64 passes), else 1.
-template <int BPS>
-__global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
+// HW: halo warps per group of the one-reduction inner pass (2: kGroups more warps at the
+// end of the block, which sit out every other sweep and the elementwise loops, so that
+// the iterates are bitwise those of HW = 1; launched only with pcg_variant 1).
+template <int BPS, int HW = 1>
+__global__ void __launch_bounds__(32 * (kGroupWarps + HW - 1) * kGroups, BPS) pcg_mixed_kernel(MixedArgs a) {
   if (mixed_halted(a)) return;
+  if (HW == 2 && a.variant != 1) return;   // not launched so (launch_pcg_mixed)
   extern __shared__ __align__(16) unsigned char mixed_dyn[];
   MixedSmem& sm = *reinterpret_cast<MixedSmem*>(mixed_dyn);
   __shared__ double red[32];
@@ -373,7 +377,9 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
   unsigned nbar = 0;
   int slot = 0;
   const long long len = 3 * a.g.n3;
-  const long long tid = (long long)bid * blockDim.x + threadIdx.x, nth = (long long)nb * blockDim.x;
+  const bool in_groups = HW == 1 || threadIdx.x < kBlock;
+  const int gth = HW == 1 ? (int)blockDim.x : kBlock;
+  const long long tid = in_groups ? (long long)bid * gth + threadIdx.x : len, nth = (long long)nb * gth;
   auto reduce2 = [&](double v0, double v1, double& s0, double& s1) -> bool {
     return grid_sum2<double>(v0, v1, s0, s1, a.part, slot, nbar, a.bar, a.spin, a.err, red, gs);
   };
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
     double rr;
     {
       EpiResidualM ep{a.b, a.r, a.lx, a.g.n3};
-      sweep_L<double>(a.g, a.x, a.full, bid, nb, sm.d, ep);
+      if (in_groups) sweep_L<double>(a.g, a.x, a.full, bid, nb, sm.d, ep);
       if (!reduce2(ep.rr, ep.bb, rr, bb)) return;
     }
     if (outer == 0) {
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
       ffv delta, dummy;
       {
         EpiApplyDot32 ep{wbuf(0), a.g.n3};
-        sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
+        if (in_groups) sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
         if (!reduceF(ffv(ep.wr, 0.f), ffv(0), delta, dummy)) return;
       }
       ffv gamma = rho;
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
         FusedVecsT<float> v{a.d32, a.p32, rbuf(cur), wbuf(cur), sbuf(cur), rbuf(cur ^ 1), wbuf(cur ^ 1),
                             sbuf(cur ^ 1), alpha.hi, bet.hi, first};
         float g1 = 0.f, d1 = 0.f;
-        sweep_fused<float>(a.g, v, a.full, bid, nb, sm.ff, g1, d1, a.ptab);
+        sweep_fused<float, HW>(a.g, v, a.full, bid, nb, sm.ff, g1, d1, a.ptab);
         ffv gn, dn;
         if (!reduceF(ffv(g1, 0.f), ffv(d1, 0.f), gn, dn)) return;
         ++it_in; ++inner_total;
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
       ffv delta, dummy;
       {
         EpiApplyDot32 ep{a.w32a, a.g.n3};
-        sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
+        if (in_groups) sweep_L<float>(a.g, rbuf(0), a.full, bid, nb, sm.f, ep);
         if (!reduceF(ffv(ep.wr, 0.f), ffv(0), delta, dummy)) return;
       }
       ffv gamma = rho;
@@ -500,7 +506,7 @@ __global__ void __launch_bounds__(kBlock, BPS) pcg_mixed_kernel(MixedArgs a) {
       ffv pq, dummy;
       {
         EpiDirection32 ep{a.p32, a.q32, a.g.n3, beta, first};
-        sweep_L<float>(a.g, a.r32, a.full, bid, nb, sm.f, ep);
+        if (in_groups) sweep_L<float>(a.g, a.r32, a.full, bid, nb, sm.f, ep);
         if (!reduceF(ffv(ep.pq, 0.f), ffv(0), pq, dummy)) return;
       }
       ++it_in; ++inner_total;
@@ -714,7 +720,7 @@ int launch_pcg_ff(const DevGeom& dg, const double* b, double* x, double* r, doub
 int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, double* lx, const MixedBufs& mb,
                      double* part, unsigned* bar, int* err, PcgResult* out, int* refinements, double tol,
                      double inner_tol, int maxit, int nblk, cudaStream_t st, int init, int variant,
-                     const int* halt, const int2* ptab) {
+                     const int* halt, const int2* ptab, int halo_warps) {
   MixedArgs a;
   a.g = dg.g;
   a.full = Box{{0, 0, 0}, {dg.g.n, dg.g.n, dg.g.n}};
@@ -734,10 +740,26 @@ int launch_pcg_mixed(const DevGeom& dg, const double* b, double* x, double* r, d
   // inner iteration at 128^3, 83.6 -> 62.8 us)
   const bool two = 3LL * dg.g.n3 >= kMixedTwoBlocksLen;
   a.ptab = two ? nullptr : ptab;                 // the table is for nblk blocks
-  const void* fn = two ? (const void*)pcg_mixed_kernel<2> : (const void*)pcg_mixed_kernel<1>;
+  // two halo warps per group: the one-reduction inner pass at one block per SM only
+  const bool hw2 = halo_warps == 2 && !two && a.variant == 1;
+  const void* fn = two ? (const void*)pcg_mixed_kernel<2>
+                       : hw2 ? (const void*)pcg_mixed_kernel<1, 2> : (const void*)pcg_mixed_kernel<1>;
+  const int threads = hw2 ? 32 * (kGroupWarps + 1) * kGroups : kBlock;
   const int smem = (int)sizeof(MixedSmem);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return MQS_ERR_CUDA;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(two ? 2 * nblk : nblk), dim3(kBlock), args, (size_t)smem, st);
+  if (hw2) {
+    // the 384-thread block must fit once per SM (asked once per process)
+    static const int occ = [smem] {
+      int o = 0;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pcg_mixed_kernel<1, 2>, 32 * (kGroupWarps + 1) * kGroups,
+                                                           (size_t)smem) == cudaSuccess
+                 ? o
+                 : -1;
+    }();
+    if (occ < 0) return MQS_ERR_CUDA;
+    if (occ < 1) return MQS_ERR_ARG;
+  }
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(two ? 2 * nblk : nblk), dim3(threads), args, (size_t)smem, st);
   return e == cudaSuccess ? MQS_OK : MQS_ERR_CUDA;
 }
 

@@ -533,7 +533,7 @@ def test_both_pcg_variants_match_the_oracle(pkg, variant, groups, halo):
 
 
 @pytest.mark.parametrize("precision,choices", [(0, ((0, 0, 0), (1, 2, 1), (1, 3, 1), (1, 2, 2))),
-                                               (1, ((0, 0, 0), (1, 0, 0), (2, 0, 0)))])
+                                               (1, ((0, 0, 0), (1, 0, 0), (1, 0, 2), (2, 0, 0)))])
 def test_pcg_form_tuner_keeps_the_state_and_the_trajectory(pkg, precision, choices):
     # mqs_tune_pcg times the kernel forms on trial solves between steps: the state, the
     # step counter and the start-vector history stay as they were, and the steps after it
@@ -578,13 +578,13 @@ def test_mixed_precision_solve_meets_the_fp64_tolerance(pkg, precision, variant)
     s.close()
 
 
-@pytest.mark.parametrize("precision,variant", [(1, 0), (1, 1), (1, 2), (2, 1)])
+@pytest.mark.parametrize("precision,variant,halo", [(1, 0, 0), (1, 1, 0), (1, 1, 2), (1, 2, 0), (2, 1, 0)])
 @pytest.mark.parametrize("mode,name", [(START_ZERO, "zero"), (START_SPE, "spe8")])
-def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, precision, variant):
+def test_mixed_precision_steps_match_the_oracle(pkg, mode, name, precision, variant, halo):
     g = golden()
     p = W.config_linear_block()
     s = make(pkg, p, start_mode=mode, spe_depth=8, dt=g["dt"], tol=1e-10, precision=precision,
-             pcg_variant=variant)
+             pcg_variant=variant, halo_warps=halo)
     stats = s.mqs_step(g["steps"])
     a_c, _, _ = s.get_state()
     err = rel(a_c, np.array(g["runs"][name]["a_c"]))
@@ -610,6 +610,14 @@ def test_mixed_precision_full_size_agrees_with_fp64(pkg, precision, variant):
     a32, _, _ = s32.get_state()
     assert rel(a32, a64) < 1e-8
     assert all(x.status == 0 for x in st)
+    if (precision, variant) == (1, 1):
+        # two halo warps per group in the FP32 inner pass: bitwise the same steps
+        s2 = make(pkg, p, start_mode=START_SPE, spe_depth=8, dt=dt, precision=1, pcg_variant=1, halo_warps=2)
+        st2 = s2.mqs_step(30)
+        b32, _, _ = s2.get_state()
+        assert np.array_equal(a32, b32)
+        assert [x.iterations for x in st2] == [x.iterations for x in st]
+        s2.close()
     s64.close()
     s32.close()
 
