@@ -379,6 +379,21 @@ int mqs_timing_get(mqs_handle* h, mqs_timing* out);
  * batch steps (each advances every handle of the batch).  *steps (host). */
 int mqs_graph_steps(const mqs_handle* h, long* steps);
 
+/* mqs_part_ranges: the plane-tile ranges that the one-reduction PCG pass gives
+ * to its tile groups on an n^3 grid with nblk blocks of `groups` tile groups
+ * each (groups 0 counts as 2).  Host only: no CUDA call, no handle.  A plane-tile is 32 x 4
+ * positions of one z-plane; tiles are numbered column by column (tile column
+ * t = x-tile + (n+31)/32 y-tile, plane k: index t n + k), so a group marches z.
+ * Part p = block b x groups + group g gets [ranges[2p], ranges[2p+1]).  The
+ * parts cover every tile once, in order; parts past the last tile are empty.
+ * A part costs its tiles plus one warm-up plane per segment (a segment starts
+ * at the part's first tile, at every column's first plane and after 32 planes
+ * of a column); the ranges minimise the largest part cost (binary search on the
+ * cost with a greedy fill).  ranges: 2 nblk groups ints (host).  Errors:
+ * MQS_ERR_ARG (n, nblk or groups < 1, ranges NULL, or more than 2^31 tiles or
+ * parts). */
+int mqs_part_ranges(int n, int nblk, int groups, int* ranges);
+
 /* mqs_selftest_barrier_timeout: launches the persistent kernels' grid
  * barrier with an arrival count that can never be reached and a wait limit
  * of `polls` polls (about 100 ns each), so every block gives up, records

@@ -36,7 +36,7 @@ EXPORTS = ("mqs_setup", "mqs_destroy", "mqs_last_error", "mqs_layout", "mqs_set_
            "mqs_batch_tune", "mqs_batch_destroy", "mqs_adjoint", "mqs_adjoint_ckpt", "mqs_loss",
            "mqs_solve_an", "mqs_graph_steps", "mqs_batch_graph_steps", "mqs_batch_tune_depth",
            "mqs_debug_check", "mqs_batch_set_weighting", "mqs_batch_get_weighting", "mqs_tune_pcg",
-           "mqs_batch_tune_pcg", "mqs_get_options")
+           "mqs_batch_tune_pcg", "mqs_get_options", "mqs_part_ranges")
 
 
 class Grid(C.Structure):
@@ -141,6 +141,7 @@ def load():
         "mqs_timing_get": ([H, P(Timing)], I),
         "mqs_pcg_solve_noalloc": ([I, D, D, V, V, V, D, I, P(PcgInfo), V], I),
         "mqs_selftest_barrier_timeout": ([C.c_longlong], I),
+        "mqs_part_ranges": ([I, I, I, P(I)], I),
         "mqs_set_blocks": ([H, I], I),
         "mqs_batch_create": ([P(H), I, D, P(V)], I),
         "mqs_batch_set_scale": ([V, D], I),
@@ -545,6 +546,19 @@ def debug_check(solvers=None):
             out.update(site=r.site, index=r.index)
         out["faults"] += r.faults
     return out
+
+
+def part_ranges(n, nblk, groups=2):
+    """Plane-tile ranges of the one-reduction PCG pass's tile groups (mqs_part_ranges,
+    host only): an (nblk * groups, 2) int array of [first, end) per part."""
+    groups = groups or 2                      # 0: the default two groups, as in the library
+    if n < 1 or nblk < 1 or groups < 1:
+        raise ValueError("n, nblk and groups must be positive")
+    out = np.zeros(2 * nblk * groups, dtype=np.int32)
+    rc = load().mqs_part_ranges(n, nblk, groups, out.ctypes.data_as(C.POINTER(C.c_int)))
+    if rc != 0:
+        raise MqsError(rc, f"mqs_part_ranges({n}, {nblk}, {groups}) failed")
+    return out.reshape(-1, 2)
 
 
 def pcg_solve_noalloc(n, h, nu0, cell_mask, b, x, tol=1e-10, maxit=100000, stream=0):

@@ -2087,6 +2087,18 @@ int mqs_debug_check(mqs_handle* H, mqs_debug_report* rep) {
   return MQS_OK;
 }
 
+int mqs_part_ranges(int n, int nblk, int groups, int* ranges) {
+  if (!ranges) return MQS_ERR_ARG;
+  std::vector<int2> tab;
+  const int rc = fused_partition_host(n, nblk, groups, tab);
+  if (rc != MQS_OK) return rc;
+  for (size_t q = 0; q < tab.size(); ++q) {
+    ranges[2 * q] = tab[q].x;
+    ranges[2 * q + 1] = tab[q].y;
+  }
+  return MQS_OK;
+}
+
 }  // extern "C"
 
 namespace mqs {

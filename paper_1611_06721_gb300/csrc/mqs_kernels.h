@@ -1,5 +1,6 @@
 // Host-side declarations shared by the translation units of the library.
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include "mqs_internal.cuh"
 
@@ -83,6 +84,8 @@ int launch_pcg_fused(const DevGeom& dg, const double* b, double* x, double* r, d
 // the cost-balanced part ranges of the fused pass (nblk x groups int2 entries) into
 // dev_table; blocks the host (a synchronous upload on st: not for use during stream capture)
 int fused_partition(int n, int nblk, int groups, int2* dev_table, cudaStream_t st);
+// the same table on the host (no CUDA call): nblk x groups ranges into tab
+int fused_partition_host(int n, int nblk, int groups, std::vector<int2>& tab);
 
 // y = scale * (L s) on n-edges of `box` (zero on other edges of the box).
 int launch_apply_L(const DevGeom& dg, const double* s, double* y, double scale, Box box, cudaStream_t st);

@@ -558,19 +558,27 @@ static long long partition_fill(long long ntiles, int nz, long long cap, long lo
   return p;
 }
 
-int fused_partition(int n, int nblk, int groups, int2* dev_table, cudaStream_t st) {
+int fused_partition_host(int n, int nblk, int groups, std::vector<int2>& tab) {
   if (groups == 0) groups = kGroups;
+  if (n < 1 || nblk < 1 || groups < 1) return MQS_ERR_ARG;
   const long long ntx = (n + 31) / 32, nty = (n + kTY - 1) / kTY, ntiles = ntx * nty * n;
   const long long parts = (long long)nblk * groups;
-  if (ntiles >= (1LL << 31) || parts <= 0) return MQS_ERR_ARG;
+  if (ntiles >= (1LL << 31) || parts >= (1LL << 31)) return MQS_ERR_ARG;
   long long lo = 1, hi = 2 * ntiles + 2;
   while (lo < hi) {
     const long long mid = (lo + hi) / 2;
     if (partition_fill(ntiles, n, mid, parts, nullptr) <= parts) hi = mid;
     else lo = mid + 1;
   }
-  std::vector<int2> tab((size_t)parts);
+  tab.assign((size_t)parts, make_int2(0, 0));
   partition_fill(ntiles, n, lo, parts, tab.data());
+  return MQS_OK;
+}
+
+int fused_partition(int n, int nblk, int groups, int2* dev_table, cudaStream_t st) {
+  std::vector<int2> tab;
+  const int rc = fused_partition_host(n, nblk, groups, tab);
+  if (rc != MQS_OK) return rc;
   if (cudaMemcpyAsync(dev_table, tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MQS_ERR_CUDA;
