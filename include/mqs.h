@@ -379,8 +379,8 @@ int mqs_timing_get(mqs_handle* h, mqs_timing* out);
  * batch steps (each advances every handle of the batch).  *steps (host). */
 int mqs_graph_steps(const mqs_handle* h, long* steps);
 
-/* mqs_part_ranges: the plane-tile ranges that the one-reduction PCG pass gives
- * to its tile groups on an n^3 grid with nblk blocks of `groups` tile groups
+/* mqs_part_ranges: the plane-tile ranges that the one-reduction PCG pass (the
+ * solve of Sec. III, eq. (mrhs), pcg_variant 1) gives to its tile groups on an n^3 grid with nblk blocks of `groups` tile groups
  * each (groups 0 counts as 2).  Host only: no CUDA call, no handle.  A plane-tile is 32 x 4
  * positions of one z-plane; tiles are numbered column by column (tile column
  * t = x-tile + (n+31)/32 y-tile, plane k: index t n + k), so a group marches z.
